@@ -1,0 +1,128 @@
+"""Pins for the oracle's hash families (minhash, Section 4.1; sign random
+projections, Section 4.2), LSH banding (Section 2) and the output steps.
+
+Each is checked against a brute-force restatement in Python or numpy and
+against the LSH property Pr[h(x) = h(y)] = sim (Eq. lshmain)."""
+import math
+from collections import defaultdict
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+
+def test_minhash_brute_force():
+    sets = synth.jaccard_sets(n_sets=50, vocab=500, mean_size=20, n_groups=5, seed=1)
+    a, b = synth.minhash_coeffs(64, seed=2)
+    sig = O.minhash(sets, a, b)
+    p = (1 << 31) - 1
+    for i in range(sets.n):
+        xs = [int(v) for v in sets.row(i)]
+        for j in range(64):
+            assert sig[i, j] == min((int(a[j]) * x + int(b[j])) % p for x in xs)
+
+
+def test_minhash_empty_set_and_bijection():
+    csr = synth.CSR(np.array([0, 0, 3], np.int64), np.array([5, 6, 2 ** 24 - 1], np.uint32), None, 2 ** 24)
+    a, b = synth.minhash_coeffs(16, seed=3)
+    sig = O.minhash(csr, a, b)
+    assert np.all(sig[0] == 0xFFFFFFFF)
+    # h_j is a bijection of [0, p): distinct elements never tie
+    x = np.arange(0, 100000, dtype=np.uint64)
+    h = (np.uint64(a[0]) * x + np.uint64(b[0])) % np.uint64((1 << 31) - 1)
+    assert len(np.unique(h)) == len(x)
+
+
+def test_minhash_collision_rate_is_jaccard():
+    rng = np.random.default_rng(5)
+    A = np.sort(rng.choice(100000, 300, replace=False))
+    B = np.sort(np.concatenate([A[:200], rng.choice(np.setdiff1d(np.arange(100000), A), 100, replace=False)]))
+    J = len(np.intersect1d(A, B)) / len(np.union1d(A, B))
+    csr = synth.CSR(np.array([0, len(A), len(A) + len(B)], np.int64), np.concatenate([A, B]).astype(np.uint32),
+                    None, 100000)
+    a, b = synth.minhash_coeffs(20000, seed=6)
+    sig = O.minhash(csr, a, b)
+    rate = np.mean(sig[0] == sig[1])
+    assert abs(rate - J) < 4 * math.sqrt(J * (1 - J) / 20000) + 0.01
+
+
+def test_srp_sparse_brute_force_and_dense():
+    vecs = synth.tfidf_vectors(n_docs=60, dim=800, mean_nnz=30, n_groups=5, seed=2)
+    R = synth.gaussian_matrix(800, 128, seed=3)
+    sig = O.srp_sparse(vecs, R)
+    dense = np.zeros((60, 800), np.float32)
+    for i in range(60):
+        ix, v = vecs.row(i)
+        dense[i, ix] = v
+    dots = dense.astype(np.float64) @ R.astype(np.float64)
+    bits = np.unpackbits(sig.view(np.uint8), axis=1, bitorder="little")
+    sure = np.abs(dots) > 1e-12
+    assert np.array_equal(bits[sure], (dots >= 0)[sure])
+    sig_d, dd = O.srp_dense(dense, R, want_dots=True)
+    assert np.allclose(dd, dots, atol=1e-12)
+    bits_d = np.unpackbits(sig_d.view(np.uint8), axis=1, bitorder="little")
+    assert np.array_equal(bits_d[sure], bits[sure])
+
+
+def test_srp_zero_row_and_bit_layout():
+    R = np.array([[1.0, -1.0] * 16], np.float32)         # d = 1, 32 bits
+    sig = O.srp_dense(np.array([[0.0], [2.0], [-3.0]], np.float32), R)
+    assert sig[0, 0] == 0xFFFFFFFF                       # dot = 0 gives bit 1
+    assert sig[1, 0] == 0x55555555                       # bit j of word j/32 at position j%32
+    assert sig[2, 0] == 0xAAAAAAAA
+
+
+def test_srp_collision_rate_is_angle():
+    rng = np.random.default_rng(8)
+    d = 64
+    x = rng.standard_normal(d)
+    y = x + 1.2 * rng.standard_normal(d)
+    X = np.stack([x, y]).astype(np.float32)
+    R = synth.gaussian_matrix(d, 32 * 640, seed=9)
+    sig = O.srp_dense(X, R)
+    bits = np.unpackbits(sig.view(np.uint8), axis=1, bitorder="little")
+    xx, yy = X.astype(np.float64)
+    r = 1 - math.acos(xx @ yy / (np.linalg.norm(xx) * np.linalg.norm(yy))) / math.pi
+    n = bits.shape[1]
+    assert abs(np.mean(bits[0] == bits[1]) - r) < 4 * math.sqrt(r * (1 - r) / n)
+
+
+def brute_candidates(sig, kind, rows, bands):
+    out = set()
+    for b in range(bands):
+        buckets = defaultdict(list)
+        for i in range(sig.shape[0]):
+            if kind == O.JACCARD:
+                key = tuple(sig[i, b * rows:(b + 1) * rows].tolist())
+            else:
+                bits = np.unpackbits(sig[i].view(np.uint8), bitorder="little")
+                key = tuple(bits[b * rows:(b + 1) * rows].tolist())
+            buckets[key].append(i)
+        for ids in buckets.values():
+            for u in range(len(ids)):
+                for v in range(u + 1, len(ids)):
+                    out.add((ids[u], ids[v]))
+    return sorted(out)
+
+
+def test_banding_brute_force():
+    sets = synth.jaccard_sets(n_sets=400, vocab=600, mean_size=30, n_groups=60, seed=4)
+    a, b = synth.minhash_coeffs(64, seed=5)
+    sig = O.minhash(sets, a, b)
+    got = O.lsh_candidates(sig, O.JACCARD, 4, 16)
+    assert [tuple(r) for r in got.tolist()] == brute_candidates(sig, O.JACCARD, 4, 16)
+    vecs = synth.tfidf_vectors(n_docs=300, dim=2000, mean_nnz=40, n_groups=40, seed=6)
+    sigc = O.srp_sparse(vecs, synth.gaussian_matrix(2000, 128, seed=7))
+    got = O.lsh_candidates(sigc, O.COSINE, 8, 10)
+    assert len(got) > 100
+    assert [tuple(r) for r in got.tolist()] == brute_candidates(sigc, O.COSINE, 8, 10)
+
+
+def test_banding_edge_cases():
+    sig = np.zeros((5, 8), np.uint32)                    # all identical: every pair
+    assert len(O.lsh_candidates(sig, O.JACCARD, 8, 1)) == 10
+    sig = np.arange(40, dtype=np.uint32).reshape(5, 8)   # all distinct: none
+    assert len(O.lsh_candidates(sig, O.JACCARD, 4, 2)) == 0
+    assert len(O.lsh_candidates(np.zeros((1, 8), np.uint32), O.JACCARD, 4, 2)) == 0
