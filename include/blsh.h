@@ -1,0 +1,272 @@
+/*
+ * blsh.h -- C ABI of libblsh: BayesLSH candidate verification on one GB300
+ * (sm_103a).
+ *
+ * The method is BayesLSH (Satuluri & Parthasarathy, "Bayesian Locality
+ * Sensitive Hashing for Fast Similarity Search").  Given candidate pairs, the
+ * library compares the pairs' LSH signatures k hashes at a time, prunes a pair
+ * as soon as Pr[S >= t | m of n hashes agree] < eps, and stops with the
+ * posterior-mode estimate once Pr[|S - S^| < delta | m, n] >= 1 - gamma
+ * (Algorithm 1).  BayesLSH-Lite (Algorithm 2) prunes the same way with at most
+ * h hashes and computes the exact similarity of the survivors.  Around that
+ * sit the producers of the signatures (minhash, Section 4.1; sign random
+ * projections, Section 4.2), LSH banding (Section 2) and the inference tables
+ * (Section 4.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is a DEVICE pointer to memory the caller owns
+ *     (allocated with cudaMalloc, PyTorch, ...), unless its comment says
+ *     "host".  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous on that stream: they enqueue work and
+ *     return.  Outputs are valid once the stream has reached that point.
+ *   - Every call returns an int status (BLSH_OK = 0 or a BLSH_E* code).
+ *     Argument errors are detected on the host and nothing is enqueued.
+ *     Errors the GPU detects (a pair naming an object index >= N, an output
+ *     larger than its capacity) are recorded in the context and returned by
+ *     the next blsh_status() call.  No kernel traps or asserts.
+ *   - Hot calls (hashing, banding, verify, compaction) allocate no memory;
+ *     blsh_ctx_create and blsh_tables_build allocate once.
+ *   - Calls that share a context must not overlap in time on different
+ *     streams: the context owns a small scratch area (work counters, the
+ *     device error word) that every call reuses.
+ *   - Signature rows are 16-byte aligned: `sig` is 16-byte aligned and
+ *     `sig_words` is a multiple of 4.
+ */
+#ifndef BLSH_H
+#define BLSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BLSH_API __attribute__((visibility("default")))
+#else
+#define BLSH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BLSH_OK 0
+#define BLSH_EINVAL 1   /* invalid scalar argument, NULL or misaligned pointer */
+#define BLSH_ERANGE 2   /* a pair names an object index >= N (device-detected) */
+#define BLSH_ETRUNC 3   /* an output or workspace is smaller than needed */
+#define BLSH_ENOMEM 4   /* a context or table allocation failed */
+#define BLSH_EDEVICE 5  /* a CUDA runtime call failed (message in blsh_last_error) */
+#define BLSH_ENUMERIC 6 /* a table value is non-finite or not monotone in m */
+
+/* ---- similarity kinds (Sections 4.1 and 4.2) ---------------------------- */
+#define BLSH_JACCARD 0  /* uint32 minhash values, one per hash */
+#define BLSH_COSINE 1   /* sign bits: hash j is bit (j % 32) of word (j / 32) */
+
+/* ---- per-pair outcomes (uint8 status arrays) ---------------------------- */
+#define BLSH_PRUNED 0         /* Pr[S >= t | M(m,n)] < eps after the last chunk */
+#define BLSH_ACCEPT 1         /* Pr[|S - S^| < delta | M(m,n)] >= 1 - gamma */
+#define BLSH_ACCEPT_AT_MAX 2  /* n reached n_max unpruned, not concentrated: kept */
+#define BLSH_LITE_REJECT 3    /* Algorithm 2: unpruned, exact similarity <= t */
+#define BLSH_LITE_ACCEPT 4    /* Algorithm 2: unpruned, exact similarity > t */
+#define BLSH_BAD_PAIR 255     /* the pair names an object >= N; nothing computed */
+
+typedef struct blsh_ctx blsh_ctx;
+typedef struct blsh_tables blsh_tables;
+
+/* Parameters of Algorithms 1 and 2 (inputs t, eps, delta, gamma, h; the
+ * chunk size k of "compare hashes n to n+k"; Section 5.1 uses k = 32,
+ * eps = gamma = 0.03, delta = 0.05, h = 64 Jaccard / 128 cosine) and the
+ * Beta(alpha, beta) prior of Section 4.1 (ignored for cosine, whose prior is
+ * uniform on r in [0.5, 1], Section 4.2). */
+typedef struct blsh_params {
+    int32_t kind;   /* BLSH_JACCARD or BLSH_COSINE */
+    int32_t k;      /* hashes per chunk: 32, 64 or 128 */
+    int32_t n_max;  /* most hashes compared per pair: a multiple of k, <= 4096 */
+    int32_t h;      /* Lite: hashes used for pruning, a multiple of k, <= n_max */
+    double t;       /* similarity threshold, in (0, 1) */
+    double eps;     /* recall parameter, in (0, 1) */
+    double delta;   /* accuracy half-width, in (0, 1) */
+    double gamma;   /* accuracy failure probability, in (0, 1) */
+    double alpha;   /* Jaccard prior Beta(alpha, beta), both > 0 */
+    double beta;
+} blsh_params;
+
+/* Launch shape of the verification kernel.  Only speed depends on it; the
+ * outputs are identical for every valid plan. */
+#define BLSH_PLAN_PLAIN 0       /* one launch, one lane group per pair, no refill */
+#define BLSH_PLAN_PERSISTENT 1  /* one CTA wave; warps take pairs from an atomic
+                                 * work counter and refill lanes as pairs stop */
+typedef struct blsh_plan {
+    int32_t mode;           /* BLSH_PLAN_PLAIN or BLSH_PLAN_PERSISTENT */
+    int32_t group;          /* lanes per pair: 1 (cosine, Jaccard) or 4, 8, 16, 32 (Jaccard) */
+    int32_t block;          /* threads per CTA: 128, 256 or 512 */
+    int32_t grab;           /* persistent: pairs a warp takes per counter grab (multiple of 32/group) */
+    int32_t ctas_per_sm;    /* persistent: CTAs per SM in the single wave (0 = as many as fit) */
+} blsh_plan;
+
+/* ---- library and context ------------------------------------------------ */
+
+BLSH_API const char *blsh_version(void);
+BLSH_API const char *blsh_strerror(int code);
+
+/* Creates a context bound to CUDA device `device` (made current for the
+ * call).  Allocates the context's scratch area (a few KB of device memory).
+ * *out receives the handle.  BLSH_EDEVICE if the device does not exist or is
+ * not sm_103. */
+BLSH_API int blsh_ctx_create(blsh_ctx **out, int device);
+BLSH_API int blsh_ctx_destroy(blsh_ctx *ctx);
+
+/* Text of the last host-side error on this context (static storage owned by
+ * the context, valid until the next call). */
+BLSH_API const char *blsh_last_error(const blsh_ctx *ctx);
+
+/* Synchronises `stream`, then returns and clears the first error the GPU
+ * recorded since the previous blsh_status (BLSH_ERANGE, BLSH_ETRUNC) or
+ * BLSH_EDEVICE if the stream reported a CUDA error; BLSH_OK otherwise.
+ * If `counters` (host, 4 x uint64) is not NULL it receives the running
+ * totals since the last call: [0] pairs with an index >= N, [1] outputs
+ * truncated, [2] SRP signs rechecked at higher precision, [3] SRP dot
+ * products that were exactly zero; they are then reset. */
+BLSH_API int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters);
+
+/* ---- Section 4.3 tables -------------------------------------------------- */
+
+/* Builds, in FP64 on the GPU, for n_j = (j+1) k, j = 0 .. n_max/k - 1:
+ *   minMatches[j] = the smallest m with Pr[S >= t | M(m, n_j)] >= eps
+ *                   (n_j + 1 if none), Section 4.3 "Pre-computation of
+ *                   minimum matches";
+ *   conc[j][m]    = [Pr[|S - S^| < delta | M(m, n_j)] >= 1 - gamma] for
+ *                   m >= minMatches[j] (0 below), Section 4.3 "Cache results
+ *                   of inference";
+ *   est[j][m]     = S^(m, n_j), the posterior mode (Equation map), as float.
+ * Jaccard uses the Beta(m+alpha, n-m+beta) posterior (Section 4.1), cosine
+ * the posterior of r on [0.5, 1] mapped by r2c (Section 4.2).
+ * Allocates the tables' device memory (freed by blsh_tables_destroy) and
+ * synchronises `stream` before returning.  BLSH_EINVAL for parameters out
+ * of range; BLSH_ENUMERIC if a probability is non-finite or Pr[S>=t|M] is
+ * not monotone in m (the table is still returned). */
+BLSH_API int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_tables **out, void *stream);
+BLSH_API int blsh_tables_destroy(blsh_tables *tab);
+
+/* Host copies of the tables, for checks.  Any pointer may be NULL.
+ * levels = n_max / k.  min_matches: int32 [levels]; conc: uint8
+ * [levels][n_max+1]; est: float [levels][n_max+1]; prune_prob / conc_prob:
+ * double [levels][n_max+1] (conc_prob is NaN where it was not evaluated).
+ * near_ties: how many evaluated probabilities lie within 1e-9 of their
+ * threshold (eps or 1 - gamma). */
+BLSH_API int blsh_tables_download(const blsh_tables *tab, blsh_params *params, int32_t *levels, int32_t *near_ties,
+                         int32_t *min_matches, uint8_t *conc, float *est, double *prune_prob,
+                         double *conc_prob);
+
+/* ---- signatures ---------------------------------------------------------- */
+
+/* Minhash signatures (Section 4.1, "LSH family"; the family is
+ * h_j(x) = (a_j x + b_j) mod (2^31 - 1)):
+ *   sig[i][j] = min over x in row i of h_j(x),  j < n_hashes,
+ * computed exactly in 64-bit integers.  Rows are CSR: indptr int64 [N+1],
+ * indices uint32 [nnz] (elements < 2^31 - 1).  a, b: uint32 [n_hashes] with
+ * 1 <= a_j < 2^31 - 1 and b_j < 2^31 - 1.  sig: uint32 [N][n_hashes]; an
+ * empty row gives 0xFFFFFFFF.  n_hashes must be a positive multiple of 32. */
+BLSH_API int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, int64_t N, int32_t n_hashes,
+                 const uint32_t *a, const uint32_t *b, uint32_t *sig, void *stream);
+
+/* Sign random projections of sparse rows (Section 4.2, "LSH family"):
+ * bit j of row i = [ sum_e values_e * R[indices_e][j] >= 0 ].  R: float
+ * [dim][bits], row-major.  sig: uint32 [N][bits/32], bit j at word j/32,
+ * position j%32.  The sum is taken in FP32 with a rigorous error bound; a
+ * sign the bound cannot decide is recomputed in FP64 in row order, so every
+ * bit equals the sign of the FP64 row-order sum.  bits: a positive multiple
+ * of 32, at most 4096. */
+BLSH_API int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
+                    int64_t N, const float *R, int64_t dim, int32_t bits, uint32_t *sig, void *stream);
+
+/* Sign random projections of dense rows X [N][d] (float, row-major) with R
+ * [d][bits]: the projection runs in BF16 on the tensor cores with FP32
+ * accumulation; every product with |p| < margin * ||x_i|| * ||r_j|| is
+ * recomputed in FP32 (then FP64 if FP32 cannot decide), so with
+ * margin >= 2^-7 * 1.02 every bit equals the sign of the FP64 sum.  d: a
+ * multiple of 64; bits: a multiple of 128.  X, R 16-byte aligned. */
+BLSH_API int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t d, const float *R, int32_t bits,
+                   float margin, uint32_t *sig, void *stream);
+
+/* ---- candidate generation (Section 2, "Candidate generation via LSH") ---- */
+
+/* Workspace bytes blsh_lsh_candidates needs for these sizes. */
+BLSH_API int blsh_lsh_candidates_workspace(int64_t N, int32_t kind, int32_t rows, int32_t bands, size_t *bytes);
+
+/* Band b of object i is its hashes b*rows .. b*rows+rows-1; objects that
+ * agree on every hash of at least one band become a candidate pair.  Writes
+ * each distinct pair once as (x, y) with x < y, in band order (a pair is
+ * written for the first band it collides in), into pairs uint32 [cap][2],
+ * and the number of distinct pairs into *n_pairs (device int64).  If that
+ * number exceeds cap only the first cap pairs are written and blsh_status
+ * reports BLSH_ETRUNC.  Band keys are compared in full (no hash collisions
+ * can merge buckets).  Cosine: rows <= 32.  workspace: device, at least
+ * blsh_lsh_candidates_workspace() bytes, 256-byte aligned. */
+BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, int32_t sig_words, int32_t kind,
+                        int32_t rows, int32_t bands, uint32_t *pairs, int64_t cap, int64_t *n_pairs,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- verification: Algorithms 1 and 2 ------------------------------------ */
+
+/* Algorithm 1 (BayesLSH) for pairs uint32 [P][2] (x, y) over signatures
+ * sig uint32 [N][sig_words].  Per pair, chunk j compares hashes j*k ..
+ * j*k+k-1 (minhash equality, or XOR + popcount of sign bits) and adds the
+ * agreements to m; after it, with n = (j+1) k:
+ *   m < minMatches[j]            -> BLSH_PRUNED,
+ *   conc[j][m]                   -> BLSH_ACCEPT,
+ *   n == n_max                   -> BLSH_ACCEPT_AT_MAX.
+ * Outputs per pair: status uint8 [P]; n_used uint16 [P] (hashes compared);
+ * m uint16 [P] (agreements); est float [P] (S^(m, n) at the stop).  n_used,
+ * m, est may be NULL.  stop_hist: uint64 [n_max/k] or NULL; entry j counts
+ * the pairs that stopped after chunk j (the call overwrites it).
+ * P_dev: NULL, or a device int64 holding the pair count; the kernel then
+ * reads the count there (clamped to P, which acts as the capacity), so the
+ * call can follow a producer on the same stream without a host sync.
+ * Uses the plan blsh_autotune stored for these tables, else a default. */
+BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
+                const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used,
+                uint16_t *m, float *est, uint64_t *stop_hist, void *stream);
+
+/* The same with an explicit launch plan. */
+BLSH_API int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan, const uint32_t *pairs,
+                     int64_t P, const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                     uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                     void *stream);
+
+/* Algorithm 2 (BayesLSH-Lite): the pruning loop of Algorithm 1 limited to
+ * h = tab's params.h hashes, without the concentration test; a pair that is
+ * not pruned gets its exact similarity from its rows, by a merge of the
+ * sorted index lists: Jaccard |A n B| / |A u B| (values == NULL), or cosine
+ * (values != NULL) as D / sqrt(Nx Ny) where D, Nx, Ny are sums of the FP64
+ * products x_i y_i, x_i^2, y_i^2 each rounded to a multiple of 2^-60 and
+ * added in int64 (independent of summation order; rows need squared norm
+ * < 4).  status: BLSH_PRUNED, BLSH_LITE_ACCEPT (s > t) or BLSH_LITE_REJECT;
+ * sim: double [P] (NaN for pruned pairs); n_used uint16 [P] or NULL.
+ * Rows: indptr int64 [N+1], indices uint32 sorted ascending within a row,
+ * values float or NULL. */
+BLSH_API int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                     const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                     const int64_t *indptr, const uint32_t *indices, const float *values, uint8_t *status,
+                     uint16_t *n_used, double *sim, void *stream);
+
+/* Times candidate plans on the given inputs (outputs are overwritten) and
+ * stores the fastest for `tab` in the context; *best (host) receives it.
+ * Synchronises `stream`. */
+BLSH_API int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const uint32_t *sig,
+                  int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m, float *est,
+                  blsh_plan *best, void *stream);
+
+/* ---- output (the set O of Algorithms 1 and 2) ----------------------------- */
+
+/* Stable compaction: out_idx int64 [cap] receives, in increasing order, the
+ * indices q < P (or < *P_dev) with status[q] < 32 and bit status[q] of
+ * keep_mask set; *n_out (device int64) their number.  If it exceeds cap only
+ * cap indices are written and blsh_status reports BLSH_ETRUNC. */
+BLSH_API int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, const int64_t *P_dev, uint32_t keep_mask,
+                 int64_t *out_idx, int64_t cap, int64_t *n_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLSH_H */

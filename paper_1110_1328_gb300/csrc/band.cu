@@ -1,0 +1,315 @@
+// band.cu -- LSH banding candidate generation (Section 2, "Candidate
+// generation via LSH"): objects whose `rows` hashes agree on a whole band
+// become a candidate pair.
+//
+// The paper's hashtables are replaced by a sort:
+//   1. every (band b, object i) gets a sort key: the band index in the top
+//      bits, below it the band's hashes themselves (cosine: the `rows` sign
+//      bits, exact) or a 64-bit hash of them (Jaccard);
+//   2. an LSD radix sort (8-bit digits, stable) groups equal keys, objects in
+//      increasing order inside a group;
+//   3. for each sorted position p, the pairs (p, q > p) inside its group are
+//      counted, then written at offsets from a prefix sum.  A pair is written
+//      only for the first band in which it collides (earlier bands are
+//      compared), so every distinct pair appears once; Jaccard bands are
+//      compared in full, so hash collisions never merge buckets.
+#include "common.cuh"
+#include "scan.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSortThreads = 256;
+constexpr int kSortPerThread = 16;
+constexpr int kSortTile = kSortThreads * kSortPerThread;   // 4096 items per CTA
+constexpr int kWarps = kSortThreads / 32;
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// `rows` sign bits starting at bit `start` of a row (bit j in word j/32).
+__device__ __forceinline__ uint32_t bit_field(const uint32_t *row, int start, int rows) {
+    const int w = start >> 5, o = start & 31;
+    unsigned long long two = __ldg(row + w);
+    if (o + rows > 32) two |= (unsigned long long)__ldg(row + w + 1) << 32;
+    const unsigned long long mask = rows == 32 ? 0xffffffffull : ((1ull << rows) - 1);
+    return (uint32_t)((two >> o) & mask);
+}
+
+__device__ __forceinline__ unsigned long long band_hash(const uint32_t *row, int start, int rows) {
+    unsigned long long h = 0x243f6a8885a308d3ull;
+    for (int r = 0; r < rows; ++r) h = mix64(h ^ (__ldg(row + start + r) + 0x9e3779b97f4a7c15ull * (r + 1)));
+    return h;
+}
+
+struct BandArgs {
+    const uint32_t *sig;
+    long long N;
+    int W, kind, rows, bands, band_bits, key_shift;
+    unsigned long long *bk;   // Jaccard: [N][bands] band hashes
+};
+
+__global__ void band_keys_kernel(BandArgs A, unsigned long long *keys, uint32_t *vals) {
+    const long long n = A.N * A.bands;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < n;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(it / A.N);
+        const long long i = it - (long long)b * A.N;
+        const uint32_t *row = A.sig + (size_t)i * A.W;
+        unsigned long long key;
+        if (A.kind == BLSH_COSINE) {
+            key = ((unsigned long long)b << A.rows) | bit_field(row, b * A.rows, A.rows);
+        } else {
+            const unsigned long long h = band_hash(row, b * A.rows, A.rows);
+            A.bk[(size_t)i * A.bands + b] = h;
+            key = A.band_bits == 0 ? h : (((unsigned long long)b << A.key_shift) | (h >> A.band_bits));
+        }
+        keys[it] = key;
+        vals[it] = (uint32_t)i;
+    }
+}
+
+// ---- stable LSD radix sort, one 8-bit digit per pass ----------------------
+
+__global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const unsigned long long *keys, long long n,
+                                                                  int shift, uint32_t *hist, int tiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+    for (int i = 0; i < kSortPerThread; ++i) {
+        const long long p = base + (long long)i * kSortThreads + threadIdx.x;
+        if (p < n) atomicAdd(&h[(keys[p] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+}
+
+// Scatter with stable ranks: warp w handles the contiguous items
+// [w*512, (w+1)*512) of the tile, 32 at a time; lanes holding the same digit
+// are ranked with __match_any_sync, running counts per (warp, digit) live in
+// shared memory, and warps are then offset by the counts of lower warps.
+__global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(const unsigned long long *keys_in,
+                                                                     const uint32_t *vals_in, long long n,
+                                                                     int shift, const uint32_t *offsets, int tiles,
+                                                                     unsigned long long *keys_out,
+                                                                     uint32_t *vals_out) {
+    __shared__ uint32_t cnt[kWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    const long long base = (long long)blockIdx.x * kSortTile + (long long)w * (kSortTile / kWarps);
+    unsigned long long k[kSortPerThread];
+    uint32_t v[kSortPerThread], rank[kSortPerThread];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortPerThread; ++r) {
+        const long long p = base + r * 32 + lane;
+        const bool ok = p < n;
+        k[r] = ok ? keys_in[p] : 0ull;
+        v[r] = ok ? vals_in[p] : 0u;
+        const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const uint32_t before = ok ? cnt[w][d] : 0u;
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && (peers & lt) == 0) cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps, per digit
+    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+        uint32_t s = 0;
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t c = cnt[ww][d];
+            cnt[ww][d] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortPerThread; ++r) {
+        const long long p = base + r * 32 + lane;
+        if (p < n) {
+            const uint32_t d = (uint32_t)((k[r] >> shift) & 255u);
+            const long long dst = (long long)offsets[(size_t)d * tiles + blockIdx.x] + cnt[w][d] + rank[r];
+            keys_out[dst] = k[r];
+            vals_out[dst] = v[r];
+        }
+    }
+}
+
+// ---- pair emission -----------------------------------------------------------
+
+__device__ __forceinline__ bool same_band(const BandArgs &A, uint32_t x, uint32_t y, int b) {
+    const uint32_t *rx = A.sig + (size_t)x * A.W, *ry = A.sig + (size_t)y * A.W;
+    if (A.kind == BLSH_COSINE) return bit_field(rx, b * A.rows, A.rows) == bit_field(ry, b * A.rows, A.rows);
+    for (int r = 0; r < A.rows; ++r)
+        if (__ldg(rx + b * A.rows + r) != __ldg(ry + b * A.rows + r)) return false;
+    return true;
+}
+
+// The pair (x, y) met in band b is emitted iff its band-b keys agree in full
+// and no earlier band has them agree.
+__device__ __forceinline__ bool emit_here(const BandArgs &A, uint32_t x, uint32_t y, int b) {
+    if (A.kind == BLSH_COSINE) {
+        for (int c = 0; c < b; ++c)
+            if (same_band(A, x, y, c)) return false;
+        return true;
+    }
+    if (!same_band(A, x, y, b)) return false;
+    const unsigned long long *bx = A.bk + (size_t)x * A.bands, *by = A.bk + (size_t)y * A.bands;
+    for (int c = 0; c < b; ++c)
+        if (__ldg(bx + c) == __ldg(by + c) && same_band(A, x, y, c)) return false;
+    return true;
+}
+
+template <bool WRITE>
+__global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const uint32_t *vals, long long n,
+                            unsigned long long *counts, uint32_t *pairs, long long cap) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[p];
+        const uint32_t x = vals[p];
+        const int b = A.kind == BLSH_COSINE ? (int)(key >> A.rows)
+                                             : (A.band_bits == 0 ? 0 : (int)(key >> A.key_shift));
+        unsigned long long c = 0, out = WRITE ? counts[p] : 0;
+        for (long long q = p + 1; q < n && keys[q] == key; ++q) {
+            const uint32_t y = vals[q];
+            if (emit_here(A, x, y, b)) {
+                if (WRITE) {
+                    const long long o = (long long)(out + c);
+                    if (o < cap) {
+                        pairs[2 * o] = x;
+                        pairs[2 * o + 1] = y;
+                    }
+                }
+                ++c;
+            }
+        }
+        if (!WRITE) counts[p] = c;
+    }
+}
+
+__global__ void check_cap_kernel(const long long *n_pairs, long long cap, blsh_dev_scratch *scratch) {
+    if (*n_pairs > cap) blsh_dev_error(scratch, BLSH_ETRUNC, 1, (unsigned long long)(*n_pairs - cap));
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t keys0, keys1, vals0, vals1, bk, counts, hist, partial, grand, total;
+};
+
+Layout layout(long long N, int kind, int bands) {
+    const long long n = N * bands;
+    const long long tiles = (n + kSortTile - 1) / kSortTile;
+    const long long hist_n = 256 * tiles;
+    const long long part = blsh_scan::tiles_for(hist_n > n ? hist_n : n) + 1;
+    Layout L;
+    size_t o = 0;
+    L.keys0 = o; o = up256(o + n * 8);
+    L.keys1 = o; o = up256(o + n * 8);
+    L.vals0 = o; o = up256(o + n * 4);
+    L.vals1 = o; o = up256(o + n * 4);
+    L.bk = o; o = up256(o + (kind == BLSH_JACCARD ? n * 8 : 0));
+    L.counts = o; o = up256(o + n * 8);
+    L.hist = o; o = up256(o + hist_n * 4);
+    L.partial = o; o = up256(o + part * 8);
+    L.grand = o; o = up256(o + 16);
+    L.total = o;
+    return L;
+}
+
+int band_bits_for(int bands) {
+    int b = 0;
+    while ((1 << b) < bands) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" int blsh_lsh_candidates_workspace(int64_t N, int32_t kind, int32_t rows, int32_t bands, size_t *bytes) {
+    if (!bytes || N < 0 || bands <= 0 || rows <= 0) return BLSH_EINVAL;
+    if (kind != BLSH_JACCARD && kind != BLSH_COSINE) return BLSH_EINVAL;
+    *bytes = layout(N, kind, bands).total;
+    return BLSH_OK;
+}
+
+extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, int32_t sig_words, int32_t kind,
+                                   int32_t rows, int32_t bands, uint32_t *pairs, int64_t cap, int64_t *n_pairs,
+                                   void *workspace, size_t workspace_bytes, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!sig || !n_pairs || (cap > 0 && !pairs)) return blsh_fail(ctx, BLSH_EINVAL, "sig and n_pairs are required");
+    if (kind != BLSH_JACCARD && kind != BLSH_COSINE) return blsh_fail(ctx, BLSH_EINVAL, "bad kind");
+    if (N < 0 || N > (1ll << 32) || rows <= 0 || bands <= 0 || cap < 0)
+        return blsh_fail(ctx, BLSH_EINVAL, "bad N, rows, bands or cap");
+    if (kind == BLSH_COSINE && (rows > 32 || (long long)rows * bands > 32ll * sig_words))
+        return blsh_fail(ctx, BLSH_EINVAL, "cosine bands need rows <= 32 and rows*bands <= 32*sig_words bits");
+    if (kind == BLSH_JACCARD && (long long)rows * bands > sig_words)
+        return blsh_fail(ctx, BLSH_EINVAL, "rows*bands exceeds the signature length");
+    const int band_bits = band_bits_for(bands);
+    if (kind == BLSH_COSINE && band_bits + rows > 64) return blsh_fail(ctx, BLSH_EINVAL, "too many bands");
+    if ((long long)N * bands >= (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "N * bands must be < 2^32");
+    if (!blsh_aligned(n_pairs, 8) || !blsh_aligned(workspace, 256) || !blsh_aligned(pairs, 4))
+        return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    const Layout L = layout(N, kind, bands);
+    if (!workspace || workspace_bytes < L.total)
+        return blsh_fail(ctx, BLSH_ETRUNC, "workspace needs %zu bytes", L.total);
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long n = N * bands;
+    if (n == 0 || N < 2) {
+        BLSH_CUDA(ctx, cudaMemsetAsync(n_pairs, 0, sizeof(int64_t), s));
+        return BLSH_OK;
+    }
+    char *ws = (char *)workspace;
+    unsigned long long *keys[2] = {(unsigned long long *)(ws + L.keys0), (unsigned long long *)(ws + L.keys1)};
+    uint32_t *vals[2] = {(uint32_t *)(ws + L.vals0), (uint32_t *)(ws + L.vals1)};
+    unsigned long long *counts = (unsigned long long *)(ws + L.counts);
+    uint32_t *hist = (uint32_t *)(ws + L.hist);
+
+    BandArgs A;
+    A.sig = sig;
+    A.N = N;
+    A.W = sig_words;
+    A.kind = kind;
+    A.rows = rows;
+    A.bands = bands;
+    A.band_bits = band_bits;
+    A.key_shift = 64 - band_bits;
+    A.bk = kind == BLSH_JACCARD ? (unsigned long long *)(ws + L.bk) : nullptr;
+
+    const unsigned grid = (unsigned)((n + 255) / 256 < 65535ll * 16 ? (n + 255) / 256 : 65535ll * 16);
+    band_keys_kernel<<<grid, 256, 0, s>>>(A, keys[0], vals[0]);
+    BLSH_LAUNCHED(ctx, "band keys");
+
+    const int key_bits = kind == BLSH_COSINE ? band_bits + rows : 64;
+    const int passes = (key_bits + 7) / 8;
+    const long long tiles = (n + kSortTile - 1) / kSortTile;
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        digit_hist_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, (int)tiles);
+        BLSH_LAUNCHED(ctx, "radix histogram");
+        BLSH_CUDA(ctx, blsh_scan::exclusive_scan<uint32_t>(hist, hist, 256 * tiles, (uint32_t *)(ws + L.partial),
+                                                           (uint32_t *)(ws + L.grand), s));
+        digit_scatter_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n, shift, hist,
+                                                                      (int)tiles, keys[cur ^ 1], vals[cur ^ 1]);
+        BLSH_LAUNCHED(ctx, "radix scatter");
+        cur ^= 1;
+    }
+    emit_kernel<false><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
+    BLSH_LAUNCHED(ctx, "pair count");
+    BLSH_CUDA(ctx, blsh_scan::exclusive_scan<unsigned long long>(counts, counts, n,
+                                                                 (unsigned long long *)(ws + L.partial),
+                                                                 (unsigned long long *)n_pairs, s));
+    emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
+    BLSH_LAUNCHED(ctx, "pair write");
+    check_cap_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs, cap, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "capacity check");
+    return BLSH_OK;
+}

@@ -1,0 +1,99 @@
+// common.cuh -- internal definitions shared by the libblsh translation units:
+// the context and table objects, the device scratch area, error helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+
+#include "blsh.h"
+
+#define BLSH_MAX_NMAX 4096
+#define BLSH_COMPACT_MAX_CTAS 2048
+
+// Device-side scratch owned by a context.  Every call zeroes what it uses
+// before its kernels run (cudaMemsetAsync on the caller's stream).
+struct blsh_dev_scratch {
+    unsigned int err_code;             // first device-detected error (0 = none)
+    unsigned int pad0;
+    unsigned long long counters[4];    // bad pairs, truncations, SRP rechecks, SRP zeros
+    unsigned long long work;           // verify: next pair handed out
+    unsigned long long work2;          // lite: next survivor tile handed out
+    long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
+};
+
+struct blsh_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    blsh_dev_scratch *scratch = nullptr;
+    char err[512] = {0};
+    std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
+    std::mutex mu;
+};
+
+struct blsh_tables {
+    blsh_params p;
+    int device = 0;
+    int levels = 0;          // n_max / k
+    int conc_words = 0;      // uint32 words per level of the concentration bitmap
+    int near_ties = 0;
+    int numeric_bad = 0;
+    void *dev = nullptr;     // one allocation holding the arrays below
+    size_t bytes = 0;
+    int32_t *min_matches = nullptr;   // [levels]
+    uint32_t *conc_bits = nullptr;    // [levels][conc_words]
+    float *est = nullptr;             // [levels][n_max+1]
+    double *prune_prob = nullptr;     // [levels][n_max+1]
+    double *conc_prob = nullptr;      // [levels][n_max+1]
+    int *flags = nullptr;             // [2]: near ties, non-finite / non-monotone
+};
+
+// Records `fmt` as the context's last error and returns `code`.
+int blsh_fail(blsh_ctx *ctx, int code, const char *fmt, ...);
+
+// Maps a CUDA error to BLSH_EDEVICE with a message, or returns BLSH_OK.
+int blsh_cuda_check(blsh_ctx *ctx, cudaError_t e, const char *what);
+
+#define BLSH_CUDA(ctx, call)                                      \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return blsh_cuda_check(ctx, e_, #call); \
+    } while (0)
+
+// Checks the launch that was just enqueued.
+#define BLSH_LAUNCHED(ctx, what)                                  \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return blsh_cuda_check(ctx, e_, what); \
+    } while (0)
+
+static inline bool blsh_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Device error reporting: the first error code sticks, counters accumulate.
+__device__ __forceinline__ void blsh_dev_error(blsh_dev_scratch *s, unsigned int code, int counter,
+                                               unsigned long long n) {
+    atomicCAS(&s->err_code, 0u, code);
+    if (counter >= 0) atomicAdd(&s->counters[counter], n);
+}
+
+// Makes ctx->device current for the duration of a call.
+struct blsh_device_guard {
+    int prev = -1;
+    bool ok = true;
+    explicit blsh_device_guard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~blsh_device_guard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static inline cudaStream_t blsh_stream(void *s) { return (cudaStream_t)s; }

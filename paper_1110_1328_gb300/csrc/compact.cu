@@ -1,0 +1,103 @@
+// compact.cu -- the output set O of Algorithms 1 and 2: a stable compaction
+// of the retained pair indices.
+//
+// A fixed grid of C CTAs splits [0, P) into C contiguous ranges.  Pass 1
+// counts the kept items of each range; pass 2 gives each CTA the sum of the
+// counts of the ranges before it and writes its range's indices in order,
+// one tile at a time with a block-wide prefix sum.  The count array (C
+// entries) lives in the context's scratch area.
+#include "common.cuh"
+#include "scan.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPer = 16;
+constexpr int kTile = kThreads * kPer;
+
+__device__ __forceinline__ bool kept(uint8_t st, uint32_t mask) { return st < 32 && ((mask >> st) & 1u); }
+
+__device__ __forceinline__ long long resolve_p(long long P, const long long *P_dev) {
+    if (!P_dev) return P;
+    const long long pd = *P_dev;
+    return pd < 0 ? 0 : (pd < P ? pd : P);
+}
+
+__global__ void __launch_bounds__(kThreads) compact_count(const uint8_t *status, long long P_cap,
+                                                          const long long *P_dev, uint32_t mask,
+                                                          blsh_dev_scratch *scratch) {
+    const long long P = resolve_p(P_cap, P_dev);
+    const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+    long long c = 0;
+    for (long long q = lo + threadIdx.x; q < hi; q += kThreads) c += kept(status[q], mask);
+    long long total;
+    blsh_scan::block_exclusive<long long>(c, &total);
+    if (threadIdx.x == 0) scratch->cta_counts[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) compact_write(const uint8_t *status, long long P_cap,
+                                                          const long long *P_dev, uint32_t mask, int64_t *out,
+                                                          long long cap, long long *n_out,
+                                                          blsh_dev_scratch *scratch) {
+    __shared__ long long s_base;
+    const long long P = resolve_p(P_cap, P_dev);
+    const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+    long long before = 0;
+    for (int c = threadIdx.x; c < (int)blockIdx.x; c += kThreads) before += scratch->cta_counts[c];
+    long long tot;
+    blsh_scan::block_exclusive<long long>(before, &tot);
+    if (threadIdx.x == 0) s_base = tot;
+    __syncthreads();
+    long long base = s_base;
+    for (long long t0 = lo; t0 < hi; t0 += kTile) {
+        // thread owns kPer consecutive items of the tile
+        const long long q0 = t0 + (long long)threadIdx.x * kPer;
+        uint32_t bits = 0;
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const long long q = q0 + i;
+            if (q < hi && kept(status[q], mask)) {
+                bits |= 1u << i;
+                ++c;
+            }
+        }
+        long long tile_total;
+        long long o = base + blsh_scan::block_exclusive<long long>((long long)c, &tile_total);
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if ((bits >> i) & 1u) {
+                if (o < cap) out[o] = q0 + i;
+                ++o;
+            }
+        base += tile_total;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        *n_out = base;
+        if (base > cap) blsh_dev_error(scratch, BLSH_ETRUNC, 1, (unsigned long long)(base - cap));
+    }
+}
+
+}  // namespace
+
+extern "C" int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, const int64_t *P_dev,
+                            uint32_t keep_mask, int64_t *out_idx, int64_t cap, int64_t *n_out, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!status || !n_out || (cap > 0 && !out_idx)) return blsh_fail(ctx, BLSH_EINVAL, "status and n_out required");
+    if (P < 0 || cap < 0) return blsh_fail(ctx, BLSH_EINVAL, "bad P or cap");
+    if (!blsh_aligned(out_idx, 8) || !blsh_aligned(n_out, 8) || !blsh_aligned(P_dev, 8))
+        return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    long long ctas = (P + kTile - 1) / kTile;
+    const long long most = (long long)ctx->sm_count * 4 < BLSH_COMPACT_MAX_CTAS ? (long long)ctx->sm_count * 4
+                                                                                 : BLSH_COMPACT_MAX_CTAS;
+    if (ctas > most) ctas = most;
+    if (ctas < 1) ctas = 1;
+    compact_count<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "compaction count");
+    compact_write<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, out_idx, cap,
+                                                      (long long *)n_out, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "compaction write");
+    return BLSH_OK;
+}

@@ -1,0 +1,278 @@
+// hashing.cu -- the signature producers: minhash (Section 4.1, "LSH family")
+// and sign random projections of sparse rows (Section 4.2, "LSH family").
+#include "common.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kP31 = 0x7fffffffu;   // 2^31 - 1
+
+// (a x + b) mod (2^31 - 1) for a, b < 2^31 - 1 and any 32-bit x, exactly:
+// v < 2^63 + 2^31, and 2^31 = 1 (mod p) lets two folds of the high bits onto
+// the low 31 bits bring v below 2^31 + 3, then one conditional subtraction.
+__device__ __forceinline__ uint32_t mod_mersenne31(uint32_t a, uint32_t b, uint32_t x) {
+    const unsigned long long v = (unsigned long long)a * x + b;
+    unsigned long long r = (v & kP31) + (v >> 31);
+    r = (r & kP31) + (r >> 31);
+    uint32_t h = (uint32_t)r;
+    return h >= kP31 ? h - kP31 : h;
+}
+
+// One warp per set; lane l owns hashes l, l+32, ..., l+32(HPL-1) of the
+// current tile of 32*HPL hashes and keeps their running minima in
+// registers.  The set's elements are read 32 at a time (coalesced) and
+// broadcast with shuffles.
+template <int HPL>
+__global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict__ indptr,
+                                                      const uint32_t *__restrict__ indices, long long N,
+                                                      int n_hashes, const uint32_t *__restrict__ A,
+                                                      const uint32_t *__restrict__ B, uint32_t *__restrict__ sig) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
+        const long long s = __ldg(indptr + i), e = __ldg(indptr + i + 1);
+        for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
+            uint32_t a[HPL], b[HPL], mn[HPL];
+#pragma unroll
+            for (int u = 0; u < HPL; ++u) {
+                a[u] = __ldg(A + t0 + 32 * u + lane);
+                b[u] = __ldg(B + t0 + 32 * u + lane);
+                mn[u] = 0xffffffffu;
+            }
+            for (long long e0 = s; e0 < e; e0 += 32) {
+                const uint32_t mine = e0 + lane < e ? __ldg(indices + e0 + lane) : 0u;
+                const int cnt = (int)min(32ll, e - e0);
+                for (int l = 0; l < cnt; ++l) {
+                    const uint32_t x = __shfl_sync(kFull, mine, l);
+#pragma unroll
+                    for (int u = 0; u < HPL; ++u) mn[u] = min(mn[u], mod_mersenne31(a[u], b[u], x));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < HPL; ++u) sig[(size_t)i * n_hashes + t0 + 32 * u + lane] = mn[u];
+        }
+    }
+}
+
+// Sign random projections of sparse rows.  One CTA per row (grid-stride);
+// thread t owns bits t, t+T, ..., so that the threads of a warp read 128
+// contiguous bytes of a row of R and a warp ballot of one of its bits forms
+// one signature word.  Sums are FP32 with fused multiply-adds in row order;
+// next to each sum the thread keeps sum |v r|.  Recursive summation of n
+// exact products has error at most (n-1) u sum|v r| (u = 2^-24); a sum whose
+// magnitude exceeds 1.25 n u sum|v r| + n 2^-149 has the sign of the exact
+// sum (and of the FP64 row-order sum, whose error is 2^29 times smaller).
+// Otherwise the thread recomputes the sum in FP64 in row order, which
+// reproduces that FP64 sum bit for bit (products of floats are exact in FP64,
+// so one rounding per addition with or without fusion).
+constexpr int kSrpMaxPerThread = 16;
+constexpr int kSrpChunk = 256;
+
+__global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restrict__ indptr,
+                                                         const uint32_t *__restrict__ indices,
+                                                         const float *__restrict__ values, long long N,
+                                                         const float *__restrict__ R, long long dim, int bits,
+                                                         int per_thread,
+                                                         uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
+    __shared__ uint32_t s_idx[kSrpChunk];
+    __shared__ float s_val[kSrpChunk];
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int words = bits >> 5;
+    unsigned long long rechecked = 0, zeros = 0;
+    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+        float acc[kSrpMaxPerThread], mag[kSrpMaxPerThread];
+#pragma unroll
+        for (int u = 0; u < kSrpMaxPerThread; ++u) acc[u] = mag[u] = 0.0f;
+        for (long long c0 = s; c0 < e; c0 += kSrpChunk) {
+            const int cnt = (int)min((long long)kSrpChunk, e - c0);
+            __syncthreads();
+            for (int i = t; i < cnt; i += T) {
+                uint32_t ix = __ldg(indices + c0 + i);
+                float v = __ldg(values + c0 + i);
+                if (ix >= dim) {   // malformed row: record it, contribute nothing
+                    blsh_dev_error(scratch, BLSH_ERANGE, 0, 1ull);
+                    ix = 0;
+                    v = 0.0f;
+                }
+                s_idx[i] = ix;
+                s_val[i] = v;
+            }
+            __syncthreads();
+            for (int i = 0; i < cnt; ++i) {
+                const float v = s_val[i];
+                const float *Rrow = R + (size_t)s_idx[i] * bits + t;
+#pragma unroll
+                for (int u = 0; u < kSrpMaxPerThread; ++u) {
+                    if (u < per_thread) {
+                        const float r = __ldg(Rrow + u * T);
+                        acc[u] = __fmaf_rn(v, r, acc[u]);
+                        mag[u] = __fmaf_rn(fabsf(v), fabsf(r), mag[u]);
+                    }
+                }
+            }
+        }
+        const float n = (float)(e - s);
+        const int w = t >> 5;
+#pragma unroll
+        for (int u = 0; u < kSrpMaxPerThread; ++u) {
+            if (u < per_thread) {
+                const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
+                bool bit;
+                if (fabsf(acc[u]) > bound) {
+                    bit = acc[u] >= 0.0f;
+                } else {
+                    double d = 0.0;
+                    for (long long k = s; k < e; ++k) {
+                        const uint32_t ix = __ldg(indices + k);
+                        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + t + u * T);
+                    }
+                    bit = d >= 0.0;
+                    ++rechecked;
+                    zeros += d == 0.0;
+                }
+                const unsigned word = __ballot_sync(kFull, bit);
+                if ((t & 31) == 0) sig[(size_t)row * words + w + u * (T >> 5)] = word;
+            }
+        }
+    }
+    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
+    if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+
+// Dense rows X [N][d] against R [d][bits], the same FP32 sums with the same
+// error bound and FP64 recheck (coordinates in order 0..d-1).  One CTA per
+// row; the row is staged in shared memory.
+__global__ void __launch_bounds__(256) srp_dense_simt_kernel(const float *__restrict__ X, long long N, int d,
+                                                             const float *__restrict__ R, int bits, int per_thread,
+                                                             uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
+    extern __shared__ float xs[];
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int words = bits >> 5;
+    unsigned long long rechecked = 0, zeros = 0;
+    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+        __syncthreads();
+        for (int c = t; c < d; c += T) xs[c] = __ldg(X + (size_t)row * d + c);
+        __syncthreads();
+        float acc[kSrpMaxPerThread], mag[kSrpMaxPerThread];
+#pragma unroll
+        for (int u = 0; u < kSrpMaxPerThread; ++u) acc[u] = mag[u] = 0.0f;
+        for (int c = 0; c < d; ++c) {
+            const float v = xs[c];
+            const float *Rrow = R + (size_t)c * bits + t;
+#pragma unroll
+            for (int u = 0; u < kSrpMaxPerThread; ++u) {
+                if (u < per_thread) {
+                    const float r = __ldg(Rrow + u * T);
+                    acc[u] = __fmaf_rn(v, r, acc[u]);
+                    mag[u] = __fmaf_rn(fabsf(v), fabsf(r), mag[u]);
+                }
+            }
+        }
+        const float n = (float)d;
+        const int w = t >> 5;
+#pragma unroll
+        for (int u = 0; u < kSrpMaxPerThread; ++u) {
+            if (u < per_thread) {
+                const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
+                bool bit;
+                if (fabsf(acc[u]) > bound) {
+                    bit = acc[u] >= 0.0f;
+                } else {
+                    double dd = 0.0;
+                    for (int c = 0; c < d; ++c) dd += (double)xs[c] * (double)__ldg(R + (size_t)c * bits + t + u * T);
+                    bit = dd >= 0.0;
+                    ++rechecked;
+                    zeros += dd == 0.0;
+                }
+                const unsigned word = __ballot_sync(kFull, bit);
+                if ((t & 31) == 0) sig[(size_t)row * words + w + u * (T >> 5)] = word;
+            }
+        }
+    }
+    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
+    if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+int srp_threads(int bits, int *per_thread) {
+    const int words = bits / 32;
+    int wt = 8;
+    while (words % wt) --wt;
+    *per_thread = bits / (32 * wt);
+    return 32 * wt;
+}
+
+}  // namespace
+
+extern "C" int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, int64_t N,
+                            int32_t n_hashes, const uint32_t *a, const uint32_t *b, uint32_t *sig, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!indptr || !indices || !a || !b || !sig)
+        return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, a, b and sig are required");
+    if (N < 0 || n_hashes <= 0 || n_hashes % 32)
+        return blsh_fail(ctx, BLSH_EINVAL, "n_hashes must be a positive multiple of 32");
+    if (!blsh_aligned(indptr, 8)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned indptr");
+    if (N == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long blocks_needed = (N + 7) / 8;
+    const long long cap = (long long)ctx->sm_count * 8;
+    const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
+    const int words = n_hashes / 32;
+    if (words % 8 == 0)
+        minhash_kernel<8><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    else if (words % 4 == 0)
+        minhash_kernel<4><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    else if (words % 2 == 0)
+        minhash_kernel<2><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    else
+        minhash_kernel<1><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    BLSH_LAUNCHED(ctx, "minhash kernel");
+    return BLSH_OK;
+}
+
+extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
+                               int64_t N, const float *R, int64_t dim, int32_t bits, uint32_t *sig, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!indptr || !indices || !values || !R || !sig)
+        return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, values, R and sig are required");
+    if (N < 0 || dim <= 0 || bits <= 0 || bits % 32 || bits > 4096)
+        return blsh_fail(ctx, BLSH_EINVAL, "bits must be a positive multiple of 32, at most 4096");
+    if (!blsh_aligned(indptr, 8)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned indptr");
+    if (N == 0) return BLSH_OK;
+    // threads = 32 * (largest divisor of bits/32 that is at most 8)
+    const int words = bits / 32;
+    int wt = 8;
+    while (words % wt) --wt;
+    const int T = 32 * wt;
+    const int per_thread = bits / T;
+    if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long cap = (long long)ctx->sm_count * 16;
+    const unsigned grid = (unsigned)(N < cap ? N : cap);
+    srp_sparse_kernel<<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "srp sparse kernel");
+    return BLSH_OK;
+}
+
+int blsh_srp_dense_simt(blsh_ctx *ctx, const float *X, int64_t N, int32_t d, const float *R, int32_t bits,
+                        uint32_t *sig, cudaStream_t s) {
+    int per_thread = 0;
+    const int T = srp_threads(bits, &per_thread);
+    if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");
+    const size_t smem = sizeof(float) * (size_t)d;
+    if (smem > 48 * 1024) {
+        if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "d too large");
+        BLSH_CUDA(ctx, cudaFuncSetAttribute(srp_dense_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    }
+    const long long cap = (long long)ctx->sm_count * 16;
+    const unsigned grid = (unsigned)(N < cap ? N : cap);
+    srp_dense_simt_kernel<<<grid, T, smem, s>>>(X, N, d, R, bits, per_thread, sig, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "srp dense kernel");
+    return BLSH_OK;
+}

@@ -1,0 +1,210 @@
+// lite.cu -- Algorithm 2 (BayesLSH-Lite).
+//
+// Pass 1 is the verification kernel of verify.cu in its Lite form: the
+// pruning loop over at most h hashes, no concentration test; an unpruned
+// pair is marked as a survivor in its status byte.  Pass 2 (this file) gives
+// every survivor its exact similarity: persistent warps take tiles of 32
+// statuses from a work counter, and the warp computes each survivor's
+// similarity cooperatively by intersecting the two sorted index lists (each
+// lane binary-searches elements of the shorter row in the longer one).
+//
+//   Jaccard: s = |A n B| / |A u B|, one FP64 division.
+//   Cosine:  s = D / sqrt(Nx * Ny) with D = sum over common indices of
+//            rn(x_i * y_i * 2^60), Nx = sum rn(x_i^2 * 2^60), Ny likewise,
+//            each term the FP64 product (exact for two floats) rounded to an
+//            integer and added in int64, so the sums do not depend on the
+//            order the lanes add them in.
+// A pair is kept iff s > t.
+#include "verify.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kTwo60 = 1152921504606846976.0;   // 2^60
+
+struct LiteArgs {
+    const uint2 *pairs;
+    long long P;
+    const long long *P_dev;
+    const int64_t *indptr;
+    const uint32_t *indices;
+    const float *values;
+    double t;
+    uint8_t *status;
+    double *sim;
+    blsh_dev_scratch *scratch;
+};
+
+__device__ __forceinline__ long long fixed_term(float u, float v) {
+    return __double2ll_rn(__dmul_rn(__dmul_rn((double)u, (double)v), kTwo60));
+}
+
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// First position in L[0..n) holding a value >= v.
+__device__ __forceinline__ long long lower_bound(const uint32_t *L, long long n, uint32_t v) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <bool COSINE>
+__global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(&A.scratch->work2, 1ull);
+        tile = __shfl_sync(kFull, tile, 0);
+        const long long q0 = (long long)tile * 32;
+        if (q0 >= P) break;
+        const long long mine = q0 + lane;
+        const bool surv = mine < P && A.status[mine] == BLSH_LITE_SURVIVOR;
+        unsigned mask = __ballot_sync(kFull, surv);
+        while (mask) {
+            const int l = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const long long q = q0 + l;
+            const uint2 pr = __ldg(A.pairs + q);
+            const long long ax = __ldg(A.indptr + pr.x), ex = __ldg(A.indptr + pr.x + 1);
+            const long long ay = __ldg(A.indptr + pr.y), ey = __ldg(A.indptr + pr.y + 1);
+            long long na = ex - ax, nb = ey - ay;
+            // iterate over the shorter row S, search in the longer row L
+            long long s0 = ax, ns = na, l0 = ay, nl = nb;
+            if (nb < na) { s0 = ay; ns = nb; l0 = ax; nl = na; }
+            const uint32_t *Lidx = A.indices + l0;
+            double s;
+            if (!COSINE) {
+                long long inter = 0;
+                for (long long i = lane; i < ns; i += 32) {
+                    const uint32_t v = __ldg(A.indices + s0 + i);
+                    const long long pos = lower_bound(Lidx, nl, v);
+                    inter += (pos < nl && __ldg(Lidx + pos) == v);
+                }
+                inter = warp_sum(inter);
+                const long long uni = na + nb - inter;
+                s = uni == 0 ? 0.0 : __ddiv_rn((double)inter, (double)uni);
+            } else {
+                long long D = 0, Nx = 0, Ny = 0;
+                for (long long i = lane; i < na; i += 32) {
+                    const float v = __ldg(A.values + ax + i);
+                    Nx += fixed_term(v, v);
+                }
+                for (long long i = lane; i < nb; i += 32) {
+                    const float v = __ldg(A.values + ay + i);
+                    Ny += fixed_term(v, v);
+                }
+                for (long long i = lane; i < ns; i += 32) {
+                    const uint32_t v = __ldg(A.indices + s0 + i);
+                    const long long pos = lower_bound(Lidx, nl, v);
+                    if (pos < nl && __ldg(Lidx + pos) == v)
+                        D += fixed_term(__ldg(A.values + s0 + i), __ldg(A.values + l0 + pos));
+                }
+                D = warp_sum(D);
+                Nx = warp_sum(Nx);
+                Ny = warp_sum(Ny);
+                if (Nx == 0 || Ny == 0) {
+                    s = 0.0;
+                } else {
+                    s = __ddiv_rn(__ll2double_rn(D),
+                                  __dsqrt_rn(__dmul_rn(__ll2double_rn(Nx), __ll2double_rn(Ny))));
+                }
+            }
+            if (lane == 0) {
+                A.sim[q] = s;
+                A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                                const int64_t *indptr, const uint32_t *indices, const float *values,
+                                uint8_t *status, uint16_t *n_used, double *sim, void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    const blsh_params &p = tab->p;
+    if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
+    if (p.h <= 0) return blsh_fail(ctx, BLSH_EINVAL, "the tables were built with h = 0");
+    if (!pairs || !sig || !status || !sim || !indptr || !indices)
+        return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig, status, sim, indptr and indices are required");
+    if ((p.kind == BLSH_COSINE) != (values != nullptr))
+        return blsh_fail(ctx, BLSH_EINVAL, "values must be given for cosine rows and only for them");
+    if (P < 0 || N < 0 || N > (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "bad P or N");
+    const int need = p.kind == BLSH_JACCARD ? p.h : (p.h + 31) / 32;
+    if (sig_words < need || sig_words % 4)
+        return blsh_fail(ctx, BLSH_EINVAL, "sig_words must be a multiple of 4 covering h hashes");
+    if (!blsh_aligned(sig, 16) || !blsh_aligned(pairs, 8) || !blsh_aligned(sim, 8) || !blsh_aligned(indptr, 8) ||
+        !blsh_aligned(n_used, 2) || !blsh_aligned(P_dev, 8))
+        return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    VerifyArgs A;
+    A.pairs = reinterpret_cast<const uint2 *>(pairs);
+    A.P = P;
+    A.P_dev = reinterpret_cast<const long long *>(P_dev);
+    A.sig = sig;
+    A.N = N;
+    A.W = sig_words;
+    A.k = p.k;
+    A.chunk_words = p.kind == BLSH_JACCARD ? p.k : p.k / 32;
+    A.levels = p.h / p.k;
+    A.lite = 1;
+    A.conc_words = tab->conc_words;
+    A.est_stride = p.n_max + 1;
+    A.min_matches = tab->min_matches;
+    A.conc_bits = tab->conc_bits;
+    A.est_tab = tab->est;
+    A.status = status;
+    A.n_used = n_used;
+    A.m_out = nullptr;
+    A.est_out = nullptr;
+    A.sim_out = sim;
+    A.stop_hist = nullptr;
+    A.scratch = ctx->scratch;
+    blsh_plan plan = blsh_default_plan(p.kind);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->plans.find(tab);
+        if (it != ctx->plans.end()) plan = it->second;
+    }
+    A.grab = plan.grab;
+    int rc = blsh_launch_verify(ctx, A, plan, s);
+    if (rc) return rc;
+    if (P == 0) return BLSH_OK;
+    LiteArgs L;
+    L.pairs = A.pairs;
+    L.P = P;
+    L.P_dev = A.P_dev;
+    L.indptr = indptr;
+    L.indices = indices;
+    L.values = values;
+    L.t = p.t;
+    L.status = status;
+    L.sim = sim;
+    L.scratch = ctx->scratch;
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, sizeof(unsigned long long), s));
+    int occ = 0;
+    if (values) {
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<true>, 256, 0));
+        lite_exact_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, 0, s>>>(L);
+    } else {
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<false>, 256, 0));
+        lite_exact_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, 0, s>>>(L);
+    }
+    BLSH_LAUNCHED(ctx, "lite exact-similarity kernel");
+    return BLSH_OK;
+}

@@ -1,0 +1,408 @@
+// verify.cu -- Algorithm 1 (BayesLSH) verification kernel, its launch plans
+// and the autotuner.
+//
+// One pair is owned by a group of G lanes.  A step loads, per lane, U uint4
+// (4 words) from each of the two signature rows, so a group moves 16*U*G
+// bytes per row per step with coalesced 16-byte loads:
+//   - Jaccard: a chunk is k uint32 minhashes; agreements are counted per
+//     word and summed across the group with xor-shuffles; a chunk takes
+//     k / (4 U G) steps.
+//   - Cosine: a chunk is k/32 words of sign bits; one lane owns a pair
+//     (G = 1) and one uint4 holds 4*32/k chunks, agreements = 32 - popc(x^y)
+//     per word.
+// After every chunk the tables (minMatches and the concentration bitmap of
+// Section 4.3, staged in shared memory) decide: prune, accept, or go on.
+//
+// Two launch forms:
+//   PLAIN      -- one group per pair, grid covers all pairs; a warp lives as
+//                 long as its slowest pair.
+//   PERSISTENT -- one wave of CTAs; each warp takes `grab` pairs at a time
+//                 from an atomic counter and hands a new pair to a group as
+//                 soon as its pair stops (pairs stop after very different
+//                 chunk counts: most after the first chunk).
+#include <vector>
+
+#include "verify.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+template <int KIND, int G, int U, bool PERSIST>
+__global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *s_mm = reinterpret_cast<int32_t *>(smem);
+    unsigned *s_hist = reinterpret_cast<unsigned *>(s_mm + A.levels);
+    uint32_t *s_conc = s_hist + A.levels;
+    for (int i = threadIdx.x; i < A.levels; i += blockDim.x) {
+        s_mm[i] = A.min_matches[i];
+        s_hist[i] = 0;
+    }
+    if (!A.lite)
+        for (int i = threadIdx.x; i < A.levels * A.conc_words; i += blockDim.x) s_conc[i] = A.conc_bits[i];
+    __syncthreads();
+
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const int lane = threadIdx.x & 31;
+    const int g = lane % G;      // lane within its group
+    const int grp = lane / G;    // group within the warp
+    constexpr int kWordsPerStep = 4 * U * G;
+    const int steps_per_chunk = KIND == BLSH_JACCARD ? A.chunk_words / kWordsPerStep : 1;
+
+    bool active = false;
+    long long q = 0;
+    const uint32_t *rx = nullptr, *ry = nullptr;
+    int m = 0, j = 0, w = 0, acc = 0, sub = 0;
+
+    auto finish = [&](int st) {
+        if (g == 0) {
+            A.status[q] = (uint8_t)st;
+            if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
+            if (A.m_out) A.m_out[q] = (uint16_t)m;
+            if (A.est_out) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
+            if (A.sim_out && st == BLSH_PRUNED) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
+            atomicAdd(&s_hist[j], 1u);
+        }
+        active = false;
+    };
+    // Chunk j has just been completed with m agreements in n = (j+1) k hashes.
+    auto decide = [&]() {
+        if (m < s_mm[j]) {
+            finish(BLSH_PRUNED);                                   // Pr[S >= t | M] < eps
+        } else if (!A.lite && ((s_conc[j * A.conc_words + (m >> 5)] >> (m & 31)) & 1u)) {
+            finish(BLSH_ACCEPT);                                   // concentrated
+        } else if (j + 1 == A.levels) {
+            finish(A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX);
+        } else {
+            ++j;
+        }
+    };
+    auto start = [&](long long qq) {
+        q = qq;
+        const uint2 pr = __ldg(A.pairs + qq);
+        if ((long long)pr.x >= A.N || (long long)pr.y >= A.N) {
+            if (g == 0) {
+                A.status[q] = BLSH_BAD_PAIR;
+                if (A.n_used) A.n_used[q] = 0;
+                if (A.m_out) A.m_out[q] = 0;
+                if (A.sim_out) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
+                blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
+            }
+            active = false;
+            return;
+        }
+        rx = A.sig + (size_t)pr.x * A.W;
+        ry = A.sig + (size_t)pr.y * A.W;
+        m = 0; j = 0; w = 0; acc = 0; sub = 0;
+        active = true;
+    };
+    // One step for every group of the warp (all lanes execute it, so the
+    // group reductions may use full-warp shuffles).
+    auto step = [&]() {
+        if constexpr (KIND == BLSH_JACCARD) {
+            int c = 0;
+            if (active) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int off = w + 4 * (u * G + g);
+                    const uint4 a = ldg4(rx + off), b = ldg4(ry + off);
+                    c += (a.x == b.x) + (a.y == b.y) + (a.z == b.z) + (a.w == b.w);
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+            if (active) {
+                w += kWordsPerStep;
+                acc += c;
+                if (++sub == steps_per_chunk) {
+                    m += acc;
+                    acc = 0;
+                    sub = 0;
+                    decide();
+                }
+            }
+        } else {
+            if (active) {
+                const uint4 a = ldg4(rx + w), b = ldg4(ry + w);
+                const uint32_t x[4] = {a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w};
+                w += 4;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (active) {
+                        acc += 32 - __popc(x[i]);
+                        if (++sub == A.chunk_words) {
+                            m += acc;
+                            acc = 0;
+                            sub = 0;
+                            decide();
+                        }
+                    }
+                }
+            }
+        }
+    };
+
+    if constexpr (PERSIST) {
+        unsigned long long cur = 0, end = 0;
+        bool exhausted = false;
+        const unsigned lower = (1u << (grp * G)) - 1u;   // lanes of lower groups
+        for (;;) {
+            for (;;) {
+                const bool need = !active;
+                const unsigned need_mask = __ballot_sync(kFull, need && g == 0);
+                if (need_mask == 0 || exhausted) break;
+                if (cur >= end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&A.scratch->work, (unsigned long long)A.grab);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base >= (unsigned long long)P) {
+                        exhausted = true;
+                        break;
+                    }
+                    cur = base;
+                    end = base + A.grab < (unsigned long long)P ? base + A.grab : (unsigned long long)P;
+                }
+                const unsigned long long avail = end - cur;
+                const unsigned rank = __popc(need_mask & lower);
+                if (need && rank < avail) start((long long)(cur + rank));
+                const unsigned long long want = __popc(need_mask);
+                cur += want < avail ? want : avail;
+            }
+            if (!__any_sync(kFull, active)) break;
+            step();
+        }
+    } else {
+        const long long qq = (long long)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+        if (qq < P) start(qq);
+        while (__any_sync(kFull, active)) step();
+    }
+
+    __syncthreads();
+    if (A.stop_hist)
+        for (int i = threadIdx.x; i < A.levels; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(A.stop_hist + i, (unsigned long long)s_hist[i]);
+}
+
+template <int KIND, int G, int U, bool PERSIST>
+int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
+    auto kern = verify_kernel<KIND, G, U, PERSIST>;
+    const size_t smem = sizeof(int32_t) * A.levels * 2 + (A.lite ? 0 : sizeof(uint32_t) * A.levels * A.conc_words);
+    if (smem > 48 * 1024) {
+        if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "tables too large for shared memory");
+        BLSH_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    long long grid;
+    if (PERSIST) {
+        int occ = 0;
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan.block, smem));
+        if (occ < 1) occ = 1;
+        if (plan.ctas_per_sm > 0 && plan.ctas_per_sm < occ) occ = plan.ctas_per_sm;
+        grid = (long long)occ * ctx->sm_count;
+        BLSH_CUDA(ctx, cudaMemsetAsync(&A.scratch->work, 0, sizeof(unsigned long long), s));
+    } else {
+        const long long per_cta = plan.block / G;
+        grid = (A.P + per_cta - 1) / per_cta;
+        if (grid > 0x7fffffffll) return blsh_fail(ctx, BLSH_EINVAL, "too many pairs for a plain launch");
+    }
+    if (grid == 0) return BLSH_OK;
+    kern<<<(unsigned)grid, plan.block, smem, s>>>(A);
+    BLSH_LAUNCHED(ctx, "verify kernel");
+    return BLSH_OK;
+}
+
+template <bool PERSIST>
+int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind, cudaStream_t s) {
+    if (kind == BLSH_COSINE) return launch_kernel<BLSH_COSINE, 1, 1, PERSIST>(ctx, A, plan, s);
+    switch (plan.group) {
+    case 1: return launch_kernel<BLSH_JACCARD, 1, 8, PERSIST>(ctx, A, plan, s);
+    case 4: return launch_kernel<BLSH_JACCARD, 4, 2, PERSIST>(ctx, A, plan, s);
+    case 8: return launch_kernel<BLSH_JACCARD, 8, 1, PERSIST>(ctx, A, plan, s);
+    case 16: return launch_kernel<BLSH_JACCARD, 16, 1, PERSIST>(ctx, A, plan, s);
+    case 32: return launch_kernel<BLSH_JACCARD, 32, 1, PERSIST>(ctx, A, plan, s);
+    }
+    return blsh_fail(ctx, BLSH_EINVAL, "unsupported group size %d", plan.group);
+}
+
+}  // namespace
+
+blsh_plan blsh_default_plan(int kind) {
+    blsh_plan p;
+    p.mode = BLSH_PLAN_PERSISTENT;
+    p.group = kind == BLSH_COSINE ? 1 : 8;
+    p.block = 256;
+    p.grab = kind == BLSH_COSINE ? 128 : 32;
+    p.ctas_per_sm = 0;
+    return p;
+}
+
+// Words moved per group step must not exceed a Jaccard chunk (k words).
+int blsh_check_plan(const blsh_plan &plan, int kind, int k) {
+    if (plan.mode != BLSH_PLAN_PLAIN && plan.mode != BLSH_PLAN_PERSISTENT) return BLSH_EINVAL;
+    if (plan.block != 128 && plan.block != 256 && plan.block != 512) return BLSH_EINVAL;
+    if (kind == BLSH_COSINE) {
+        if (plan.group != 1) return BLSH_EINVAL;
+    } else {
+        int wps;
+        switch (plan.group) {
+        case 1: wps = 32; break;
+        case 4: wps = 32; break;
+        case 8: wps = 32; break;
+        case 16: wps = 64; break;
+        case 32: wps = 128; break;
+        default: return BLSH_EINVAL;
+        }
+        if (wps > k) return BLSH_EINVAL;
+    }
+    if (plan.mode == BLSH_PLAN_PERSISTENT && (plan.grab < 1 || plan.grab > (1 << 20))) return BLSH_EINVAL;
+    if (plan.ctas_per_sm < 0) return BLSH_EINVAL;
+    return BLSH_OK;
+}
+
+int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
+    const int kind = A.chunk_words == A.k ? BLSH_JACCARD : BLSH_COSINE;
+    if (plan.mode == BLSH_PLAN_PERSISTENT) return dispatch<true>(ctx, A, plan, kind, s);
+    return dispatch<false>(ctx, A, plan, kind, s);
+}
+
+namespace {
+
+int make_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
+              const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
+              float *est, uint64_t *stop_hist, VerifyArgs &A) {
+    const blsh_params &p = tab->p;
+    if (!pairs || !sig || !status) return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig and status are required");
+    if (P < 0 || N < 0 || N > (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "bad P or N");
+    const int need = p.kind == BLSH_JACCARD ? p.n_max : (p.n_max + 31) / 32;
+    if (sig_words < need || sig_words % 4)
+        return blsh_fail(ctx, BLSH_EINVAL, "sig_words must be a multiple of 4 covering n_max hashes");
+    if (!blsh_aligned(sig, 16) || !blsh_aligned(pairs, 8) || !blsh_aligned(n_used, 2) || !blsh_aligned(m, 2) ||
+        !blsh_aligned(est, 4) || !blsh_aligned(stop_hist, 8) || !blsh_aligned(P_dev, 8))
+        return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    A.pairs = reinterpret_cast<const uint2 *>(pairs);
+    A.P = P;
+    A.P_dev = reinterpret_cast<const long long *>(P_dev);
+    A.sig = sig;
+    A.N = N;
+    A.W = sig_words;
+    A.k = p.k;
+    A.chunk_words = p.kind == BLSH_JACCARD ? p.k : p.k / 32;
+    A.levels = tab->levels;
+    A.lite = 0;
+    A.conc_words = tab->conc_words;
+    A.est_stride = p.n_max + 1;
+    A.min_matches = tab->min_matches;
+    A.conc_bits = tab->conc_bits;
+    A.est_tab = tab->est;
+    A.status = status;
+    A.n_used = n_used;
+    A.m_out = m;
+    A.est_out = est;
+    A.sim_out = nullptr;
+    A.stop_hist = reinterpret_cast<unsigned long long *>(stop_hist);
+    A.scratch = ctx->scratch;
+    A.grab = 0;
+    return BLSH_OK;
+}
+
+}  // namespace
+
+extern "C" int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan,
+                                const uint32_t *pairs, int64_t P, const int64_t *P_dev, const uint32_t *sig,
+                                int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
+                                float *est, uint64_t *stop_hist, void *stream) {
+    if (!ctx || !tab || !plan) return BLSH_EINVAL;
+    if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
+    if (blsh_check_plan(*plan, tab->p.kind, tab->p.k) != BLSH_OK)
+        return blsh_fail(ctx, BLSH_EINVAL, "invalid plan for this kind and k");
+    VerifyArgs A;
+    int rc = make_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est, stop_hist, A);
+    if (rc) return rc;
+    A.grab = plan->grab;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    if (stop_hist) BLSH_CUDA(ctx, cudaMemsetAsync(stop_hist, 0, sizeof(uint64_t) * tab->levels, s));
+    return blsh_launch_verify(ctx, A, *plan, s);
+}
+
+extern "C" int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                           const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                           uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                           void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    blsh_plan plan = blsh_default_plan(tab->p.kind);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->plans.find(tab);
+        if (it != ctx->plans.end()) plan = it->second;
+    }
+    return blsh_verify_plan(ctx, tab, &plan, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
+                            stop_hist, stream);
+}
+
+extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                             const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
+                             uint16_t *n_used, uint16_t *m, float *est, blsh_plan *best, void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    std::vector<blsh_plan> cands;
+    const int kind = tab->p.kind;
+    const int groups_c[] = {1};
+    const int groups_j[] = {1, 4, 8, 16, 32};
+    const int *groups = kind == BLSH_COSINE ? groups_c : groups_j;
+    const int ng = kind == BLSH_COSINE ? 1 : 5;
+    for (int gi = 0; gi < ng; ++gi)
+        for (int block : {128, 256, 512}) {
+            blsh_plan p;
+            p.group = groups[gi];
+            p.block = block;
+            p.ctas_per_sm = 0;
+            p.mode = BLSH_PLAN_PLAIN;
+            p.grab = 32;
+            if (blsh_check_plan(p, kind, tab->p.k) == BLSH_OK) cands.push_back(p);
+            p.mode = BLSH_PLAN_PERSISTENT;
+            for (int grab : {32, 128, 512}) {
+                p.grab = grab;
+                if (blsh_check_plan(p, kind, tab->p.k) == BLSH_OK) cands.push_back(p);
+            }
+        }
+    cudaEvent_t e0, e1;
+    BLSH_CUDA(ctx, cudaEventCreate(&e0));
+    BLSH_CUDA(ctx, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    blsh_plan best_plan = blsh_default_plan(kind);
+    int rc = BLSH_OK;
+    for (const blsh_plan &p : cands) {
+        rc = blsh_verify_plan(ctx, tab, &p, pairs, P, nullptr, sig, N, sig_words, status, n_used, m, est,
+                              nullptr, stream);
+        if (rc) break;
+        if ((rc = blsh_cuda_check(ctx, cudaEventRecord(e0, s), "event"))) break;
+        for (int r = 0; r < 3 && !rc; ++r)
+            rc = blsh_verify_plan(ctx, tab, &p, pairs, P, nullptr, sig, N, sig_words, status, n_used, m, est,
+                                  nullptr, stream);
+        if (rc) break;
+        if ((rc = blsh_cuda_check(ctx, cudaEventRecord(e1, s), "event"))) break;
+        if ((rc = blsh_cuda_check(ctx, cudaEventSynchronize(e1), "event sync"))) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_plan = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->plans[tab] = best_plan;
+    }
+    if (best) *best = best_plan;
+    return BLSH_OK;
+}

@@ -1,0 +1,40 @@
+// verify.cuh -- the chunked verification loop of Algorithm 1 (BayesLSH) and
+// the pruning loop of Algorithm 2 (BayesLSH-Lite), shared by verify.cu and
+// lite.cu.
+#pragma once
+
+#include "common.cuh"
+
+// Internal status of a Lite pair that survived pruning and waits for its
+// exact similarity.
+#define BLSH_LITE_SURVIVOR 254
+
+struct VerifyArgs {
+    const uint2 *pairs;
+    long long P;                 // pair count, or capacity when P_dev is set
+    const long long *P_dev;      // device pair count or NULL
+    const uint32_t *sig;
+    long long N;
+    int W;                       // signature row stride in words
+    int k;                       // hashes per chunk
+    int chunk_words;             // words per chunk: Jaccard k, cosine k/32
+    int levels;                  // chunks at most (n_max/k, or h/k for Lite)
+    int lite;                    // Algorithm 2: no concentration test
+    int conc_words;              // bitmap words per level
+    int est_stride;              // n_max + 1
+    const int32_t *min_matches;  // [levels]
+    const uint32_t *conc_bits;   // [levels][conc_words]
+    const float *est_tab;        // [levels][est_stride]
+    uint8_t *status;
+    uint16_t *n_used;
+    uint16_t *m_out;
+    float *est_out;
+    double *sim_out;             // Lite: NaN written for pruned pairs
+    unsigned long long *stop_hist;
+    blsh_dev_scratch *scratch;
+    int grab;                    // persistent: pairs per work-counter grab
+};
+
+int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s);
+blsh_plan blsh_default_plan(int kind);
+int blsh_check_plan(const blsh_plan &plan, int kind, int k);

@@ -1,0 +1,203 @@
+"""GPU parity for the producers and the output step: minhash, sign random
+projections (sparse and dense), LSH banding, Lite's exact similarity, and the
+stable compaction -- all bit-exact against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+dev = torch.device("cuda")
+
+
+def t32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+
+def csr_dev(csr):
+    out = [torch.from_numpy(csr.indptr).to(dev), t32(csr.indices.astype(np.uint32))]
+    out.append(None if csr.values is None else torch.from_numpy(csr.values).to(dev))
+    return out
+
+
+@pytest.mark.parametrize("n_hashes", [32, 96, 256, 512])
+def test_minhash_bit_exact(B, ctx, n_hashes):
+    sets = synth.jaccard_sets(n_sets=1500, vocab=50000, mean_size=50, n_groups=100, seed=n_hashes)
+    # add an empty set and a large one
+    rows = [sets.row(i) for i in range(sets.n)] + [np.zeros(0, np.int64), np.arange(0, 3000 * 7, 7)]
+    lens = np.array([len(r) for r in rows])
+    csr = synth.CSR(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
+                    np.concatenate(rows).astype(np.uint32), None, 50000)
+    a, b = synth.minhash_coeffs(n_hashes, seed=7)
+    want = O.minhash(csr, a, b)
+    ip, ix, _ = csr_dev(csr)
+    sig = torch.zeros((csr.n, n_hashes), dtype=torch.int32, device=dev)
+    B.blsh_minhash(ctx, ip, ix, n_hashes, t32(a), t32(b), sig)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("bits", [64, 96, 2048])
+def test_srp_sparse_bit_exact(B, ctx, bits):
+    vecs = synth.tfidf_vectors(n_docs=900, dim=20000, mean_nnz=80, n_groups=50, seed=bits)
+    R = synth.gaussian_matrix(20000, bits, seed=11)
+    want = O.srp_sparse(vecs, R)
+    ip, ix, val = csr_dev(vecs)
+    sig = torch.zeros((vecs.n, bits // 32), dtype=torch.int32, device=dev)
+    B.blsh_srp_sparse(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig)
+    rc, counters = B.blsh_status(ctx, counters=True)
+    assert rc == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+
+
+def test_srp_sparse_exact_ties_and_zero_rows(B, ctx):
+    # rows whose projections are exactly zero (a zero row; x and -x at the same
+    # index twice would be merged, so use two terms with cancelling products)
+    R = np.ones((4, 32), np.float32)
+    R[1] = -1
+    csr = synth.CSR(np.array([0, 0, 2, 3], np.int64), np.array([0, 1, 2], np.uint32),
+                    np.array([0.5, 0.5, -0.25], np.float32), 4)
+    want = O.srp_sparse(csr, R)
+    ip, ix, val = csr_dev(csr)
+    sig = torch.zeros((3, 1), dtype=torch.int32, device=dev)
+    B.blsh_srp_sparse(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig)
+    rc, c = B.blsh_status(ctx, counters=True)
+    assert rc == 0
+    got = sig.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, want)
+    assert got[0, 0] == 0xFFFFFFFF and got[1, 0] == 0xFFFFFFFF and got[2, 0] == 0
+    assert c[3] == 64 and c[2] >= 64
+
+
+@pytest.mark.parametrize("d,bits", [(64, 128), (256, 1024)])
+def test_srp_dense_bit_exact(B, ctx, d, bits):
+    X = synth.gaussian_mixture(n_points=3000, dim=d, n_centers=50, seed=d)
+    R = synth.gaussian_matrix(d, bits, seed=5)
+    want = O.srp_dense(X, R)
+    sig = torch.zeros((X.shape[0], bits // 32), dtype=torch.int32, device=dev)
+    B.blsh_srp_dense(ctx, torch.from_numpy(X).to(dev), torch.from_numpy(R).to(dev), sig)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+
+
+def gpu_candidates(B, ctx, sig, kind, rows, bands, cap=None):
+    N = sig.shape[0]
+    ws = torch.zeros(B.blsh_lsh_candidates_workspace(N, kind, rows, bands), dtype=torch.uint8, device=dev)
+    if cap is None:
+        cap = 4 * N * bands + 16
+    pairs = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    B.blsh_lsh_candidates(ctx, t32(sig), kind, rows, bands, pairs, n, ws)
+    rc = B.blsh_status(ctx)
+    k = int(n.item())
+    return rc, k, pairs[: min(k, cap)].cpu().numpy().view(np.uint32)
+
+
+def sorted_pairs(p):
+    p = np.asarray(p, np.uint64)
+    key = (p[:, 0] << np.uint64(32)) | p[:, 1]
+    return np.sort(key)
+
+
+def test_banding_jaccard_bit_exact(B, ctx):
+    sets = synth.jaccard_sets(n_sets=2000, vocab=10000, mean_size=50, n_groups=200, seed=1)
+    a, b = synth.minhash_coeffs(256, seed=2)
+    sig = O.minhash(sets, a, b)
+    for rows, bands in ((8, 32), (4, 16), (1, 3)):
+        want = O.lsh_candidates(sig, O.JACCARD, rows, bands)
+        rc, n, got = gpu_candidates(B, ctx, sig, 0, rows, bands)
+        assert rc == 0 and n == len(want)
+        assert np.all(got[:, 0] < got[:, 1])
+        assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+
+
+def test_banding_cosine_bit_exact(B, ctx):
+    vecs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=100, seed=3)
+    sig = O.srp_sparse(vecs, synth.gaussian_matrix(30000, 512, seed=4))
+    for rows, bands in ((8, 35), (12, 20), (32, 4), (5, 7)):
+        want = O.lsh_candidates(sig, O.COSINE, rows, bands)
+        rc, n, got = gpu_candidates(B, ctx, sig, 1, rows, bands)
+        assert rc == 0 and n == len(want)
+        assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+
+
+def test_banding_buckets_and_truncation(B, ctx):
+    # 300 identical rows (one bucket of 44,850 pairs) plus distinct ones
+    sig = np.arange(1000 * 8, dtype=np.uint32).reshape(1000, 8)
+    sig[:300] = 5
+    want = O.lsh_candidates(sig, O.JACCARD, 4, 2)
+    rc, n, got = gpu_candidates(B, ctx, sig, 0, 4, 2)
+    assert rc == 0 and n == len(want) == 300 * 299 // 2
+    assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+    rc, n, got = gpu_candidates(B, ctx, sig, 0, 4, 2, cap=1000)
+    assert rc == B.ETRUNC and n == len(want) and len(got) == 1000
+    rc, n, got = gpu_candidates(B, ctx, sig[:1], 0, 4, 2)
+    assert rc == 0 and n == 0
+
+
+def test_lite_jaccard_bit_exact(B, ctx):
+    sets = synth.jaccard_sets(n_sets=2000, vocab=10000, mean_size=50, n_groups=200, seed=1)
+    a, b = synth.minhash_coeffs(256, seed=2)
+    sig = O.minhash(sets, a, b)
+    pairs = np.concatenate([O.lsh_candidates(sig, O.JACCARD, 8, 32), synth.random_pairs(2000, 5000, seed=3)])
+    p = O.Params(kind=O.JACCARD, n_max=256, h=64, t=0.7)
+    want = O.verify_lite(O.tables(p), pairs, sig, sets)
+    tab = B.blsh_tables_build(ctx, B.make_params(kind=0, t=0.7, n_max=256, h=64))
+    ip, ix, _ = csr_dev(sets)
+    P = len(pairs)
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    nu = torch.zeros(P, dtype=torch.int16, device=dev)
+    B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, None, st, sim, nu)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy(), want.status)
+    assert np.array_equal(nu.cpu().numpy().view(np.uint16), want.n_used)
+    g = sim.cpu().numpy()
+    assert np.array_equal(np.isnan(g), np.isnan(want.sim))
+    ok = ~np.isnan(g)
+    assert np.array_equal(g[ok], want.sim[ok])          # bit-identical doubles
+    assert (want.status == O.LITE_ACCEPT).sum() > 50
+
+
+def test_lite_cosine_bit_exact(B, ctx):
+    vecs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=150, seed=5)
+    sig = O.srp_sparse(vecs, synth.gaussian_matrix(30000, 256, seed=6))
+    pairs = np.concatenate([O.lsh_candidates(sig, O.COSINE, 8, 30), synth.random_pairs(3000, 3000, seed=1)])
+    p = O.Params(kind=O.COSINE, n_max=256, h=128, t=0.7)
+    want = O.verify_lite(O.tables(p), pairs, sig, vecs)
+    tab = B.blsh_tables_build(ctx, B.make_params(kind=1, t=0.7, n_max=256, h=128))
+    ip, ix, val = csr_dev(vecs)
+    P = len(pairs)
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, val, st, sim)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy(), want.status)
+    g = sim.cpu().numpy()
+    ok = ~np.isnan(want.sim)
+    assert np.array_equal(np.isnan(g), ~ok)
+    assert np.array_equal(g[ok], want.sim[ok])
+    assert (want.status == O.LITE_ACCEPT).sum() > 50
+
+
+@pytest.mark.parametrize("P", [0, 1, 31, 4097, 1_000_003])
+def test_compact_stable_and_exact(B, ctx, P):
+    rng = np.random.default_rng(P)
+    st = rng.integers(0, 5, P).astype(np.uint8)
+    if P > 10:
+        st[::7] = 255
+    keep = (1 << 1) | (1 << 2) | (1 << 4)
+    want = O.compact(st, keep)
+    out = torch.full((max(P, 1),), -1, dtype=torch.int64, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    B.blsh_compact(ctx, torch.from_numpy(st).to(dev), keep, out, n)
+    assert B.blsh_status(ctx) == 0
+    assert int(n.item()) == len(want)
+    assert np.array_equal(out[: len(want)].cpu().numpy(), want)
+    if len(want) > 3:
+        small = torch.zeros(3, dtype=torch.int64, device=dev)
+        B.blsh_compact(ctx, torch.from_numpy(st).to(dev), keep, small, n)
+        assert B.blsh_status(ctx) == B.ETRUNC
+        assert np.array_equal(small.cpu().numpy(), want[:3]) and int(n.item()) == len(want)

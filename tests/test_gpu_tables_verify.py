@@ -1,0 +1,202 @@
+"""GPU parity: the Section 4.3 tables and Algorithm 1 against the CPU oracle.
+
+Tables: minMatches and the concentration bitmap bit-exact, estimates within
+1e-6.  Verification: per-pair status, hashes used, agreements bit-exact and
+estimates within 1e-6, for every launch plan (the plan may only change
+speed), for ragged pair counts spanning several CTAs, and for the edge cases
+(no pairs, one pair, identical and disjoint signatures, pairs naming an
+object >= N)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+EST_TOL = 1e-6
+
+TABLE_PARAMS = [
+    dict(kind=0, n_max=256, k=32, t=0.7),
+    dict(kind=0, n_max=512, k=64, t=0.5),
+    dict(kind=0, n_max=384, k=128, t=0.8, eps=0.01, delta=0.03, gamma=0.05),
+    dict(kind=0, n_max=256, k=32, t=0.6, alpha=2.0, beta=5.0),
+    dict(kind=1, n_max=2048, k=32, t=0.7),
+    dict(kind=1, n_max=1024, k=32, t=0.8),
+    dict(kind=1, n_max=4096, k=128, t=0.6),
+    dict(kind=1, n_max=512, k=64, t=0.5, eps=0.05),
+]
+
+
+def oracle_params(d):
+    return O.Params(kind=d["kind"], t=d.get("t", 0.7), eps=d.get("eps", 0.03), delta=d.get("delta", 0.05),
+                    gamma=d.get("gamma", 0.03), alpha=d.get("alpha", 1.0), beta=d.get("beta", 1.0), k=d["k"],
+                    n_max=d["n_max"], h=min(d["n_max"], 64 if d["kind"] == 0 else 128))
+
+
+def gpu_tables(B, ctx, d):
+    p = B.make_params(kind=d["kind"], t=d.get("t", 0.7), eps=d.get("eps", 0.03), delta=d.get("delta", 0.05),
+                      gamma=d.get("gamma", 0.03), alpha=d.get("alpha", 1.0), beta=d.get("beta", 1.0), k=d["k"],
+                      n_max=d["n_max"])
+    return B.blsh_tables_build(ctx, p)
+
+
+@pytest.mark.parametrize("d", TABLE_PARAMS, ids=lambda d: "-".join(f"{k}{v}" for k, v in d.items()))
+def test_tables_bit_exact(B, ctx, d):
+    tab = gpu_tables(B, ctx, d)
+    assert tab.build_status == B.OK
+    g = B.blsh_tables_download(tab)
+    o = O.tables(oracle_params(d))
+    assert g["near_ties"] == 0
+    assert np.array_equal(g["min_matches"], o.min_matches)
+    assert np.array_equal(g["conc"], o.conc)
+    L = o.min_matches.shape[0]
+    for j in range(L):
+        n = (j + 1) * d["k"]
+        assert np.max(np.abs(g["est"][j, : n + 1] - o.est[j, : n + 1])) <= EST_TOL
+        pr_o, pr_g = o.prune_prob[j, : n + 1], g["prune_prob"][j, : n + 1]
+        assert np.allclose(pr_g, pr_o, rtol=1e-10, atol=1e-14)
+        mm = o.min_matches[j]
+        assert np.allclose(g["conc_prob"][j, mm: n + 1], o.conc_prob[j, mm: n + 1], rtol=1e-10, atol=1e-13)
+
+
+def test_tables_reject_bad_params(B, ctx):
+    for bad in (dict(k=48), dict(n_max=100), dict(t=1.5), dict(eps=0.0), dict(n_max=8192)):
+        d = dict(kind=0, n_max=256, k=32, t=0.7)
+        d.update(bad)
+        with pytest.raises(B.BlshError) as e:
+            gpu_tables(B, ctx, d)
+        assert e.value.code == B.EINVAL
+
+
+def run_verify(B, ctx, tab, pairs, sig, plan=None, P_dev=None, cap=None):
+    dev = torch.device("cuda")
+    pairs_t = torch.from_numpy(np.ascontiguousarray(pairs, np.uint32).view(np.int32)).to(dev)
+    if cap is not None and cap > len(pairs):
+        pairs_t = torch.cat([pairs_t, torch.zeros((cap - len(pairs), 2), dtype=torch.int32, device=dev)])
+    sig_t = torch.from_numpy(np.ascontiguousarray(sig, np.uint32).view(np.int32)).to(dev)
+    P = pairs_t.shape[0]
+    status = torch.full((P,), 77, dtype=torch.uint8, device=dev)
+    n_used = torch.zeros(P, dtype=torch.int16, device=dev)
+    m = torch.zeros(P, dtype=torch.int16, device=dev)
+    est = torch.zeros(P, dtype=torch.float32, device=dev)
+    hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
+    pd = None if P_dev is None else torch.tensor([P_dev], dtype=torch.int64, device=dev)
+    B.blsh_verify(ctx, tab, pairs_t, sig_t, status, n_used, m, est, hist, P_dev=pd, plan=plan)
+    rc = B.blsh_status(ctx)
+    return rc, status.cpu().numpy(), n_used.cpu().numpy().view(np.uint16), m.cpu().numpy().view(np.uint16), \
+        est.cpu().numpy(), hist.cpu().numpy()
+
+
+def assert_same(res, want, hist, p):
+    rc, st, nu, m, est, h = res
+    assert rc == 0
+    assert np.array_equal(st, want.status)
+    assert np.array_equal(nu, want.n_used)
+    assert np.array_equal(m, want.m)
+    assert np.max(np.abs(est - want.est), initial=0) <= EST_TOL
+    assert np.array_equal(h, O.stop_hist(want.n_used, p.k, p.levels).astype(np.int64))
+
+
+def all_plans(B, kind, k):
+    plans = []
+    groups = [1] if kind == 1 else [1, 4, 8, 16, 32]
+    for g in groups:
+        if kind == 0 and {1: 32, 4: 32, 8: 32, 16: 64, 32: 128}[g] > k:
+            continue
+        for block in (128, 512):
+            plans.append(B.blsh_plan(B.PLAN_PLAIN, g, block, 32, 0))
+            for grab in (1, 37, 256):
+                plans.append(B.blsh_plan(B.PLAN_PERSISTENT, g, block, grab, 0))
+    plans.append(B.blsh_plan(B.PLAN_PERSISTENT, groups[-1], 256, 64, 1))
+    return plans
+
+
+def model_signatures(kind, n_max, P, seed):
+    rng = np.random.default_rng(seed)
+    sims = np.concatenate([rng.uniform(0, 1, P // 2), rng.uniform(0.55, 0.97, P - P // 2 - 2), [1.0, 0.0]])
+    if kind == 1:
+        sims = np.clip(sims, 0.5, 1.0)
+    return synth.bernoulli_signatures(sims, n_max, "jaccard" if kind == 0 else "cosine", seed=seed)
+
+
+@pytest.mark.parametrize("d", [TABLE_PARAMS[0], TABLE_PARAMS[1], TABLE_PARAMS[2], TABLE_PARAMS[4],
+                               TABLE_PARAMS[6]], ids=lambda d: f"kind{d['kind']}-k{d['k']}-n{d['n_max']}")
+def test_verify_every_plan_matches_oracle(B, ctx, d):
+    p = oracle_params(d)
+    sig, pairs = model_signatures(d["kind"], d["n_max"], 3001, seed=d["k"] + d["kind"])
+    rng = np.random.default_rng(1)
+    pairs = np.concatenate([pairs, rng.integers(0, sig.shape[0], size=(2000, 2)).astype(np.uint32)])
+    want = O.verify(O.tables(p), pairs, sig)
+    tab = gpu_tables(B, ctx, d)
+    for plan in all_plans(B, d["kind"], d["k"]):
+        assert_same(run_verify(B, ctx, tab, pairs, sig, plan=plan), want, None, p)
+    assert_same(run_verify(B, ctx, tab, pairs, sig), want, None, p)
+
+
+def test_verify_device_count_and_capacity(B, ctx):
+    d = TABLE_PARAMS[4]
+    p = oracle_params(d)
+    sig, pairs = model_signatures(1, 2048, 1000, seed=5)
+    want = O.verify(O.tables(p), pairs[:777], sig)
+    tab = gpu_tables(B, ctx, d)
+    for plan in (None, B.blsh_plan(B.PLAN_PLAIN, 1, 256, 32, 0)):
+        rc, st, nu, m, est, h = run_verify(B, ctx, tab, pairs, sig, plan=plan, P_dev=777, cap=1000)
+        assert rc == 0
+        assert np.array_equal(st[:777], want.status) and np.all(st[777:] == 77)
+        assert np.array_equal(nu[:777], want.n_used)
+
+
+def test_verify_edge_cases(B, ctx):
+    d = TABLE_PARAMS[0]
+    p = oracle_params(d)
+    tab = gpu_tables(B, ctx, d)
+    sig, pairs = model_signatures(0, 256, 64, seed=9)
+    # no pairs
+    rc, st, *_ = run_verify(B, ctx, tab, pairs[:0], sig)
+    assert rc == 0 and len(st) == 0
+    # one pair; identical; disjoint
+    for q in (0, len(pairs) - 2, len(pairs) - 1):
+        want = O.verify(O.tables(p), pairs[q:q + 1], sig)
+        assert_same(run_verify(B, ctx, tab, pairs[q:q + 1], sig), want, None, p)
+    # a pair naming an object >= N is flagged; the others are still exact
+    bad = pairs.copy()
+    bad[5] = (0, sig.shape[0])
+    bad[9] = (sig.shape[0] + 3, 1)
+    want = O.verify(O.tables(p), bad, sig)
+    rc, st, nu, m, est, h = run_verify(B, ctx, tab, bad, sig)
+    assert rc == B.ERANGE
+    assert st[5] == B.BAD_PAIR and st[9] == B.BAD_PAIR
+    ok = np.ones(len(bad), bool); ok[[5, 9]] = False
+    assert np.array_equal(st[ok], want.status[ok]) and np.array_equal(m[ok], want.m[ok])
+    assert B.blsh_status(ctx) == 0          # the error was cleared
+
+
+def test_verify_rejects_bad_arguments(B, ctx):
+    tab = gpu_tables(B, ctx, TABLE_PARAMS[0])
+    sig, pairs = model_signatures(0, 256, 8, seed=1)
+    dev = torch.device("cuda")
+    st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
+    short = torch.zeros((sig.shape[0], 128), dtype=torch.int32, device=dev)   # fewer than n_max words
+    with pytest.raises(B.BlshError) as e:
+        B.blsh_verify(ctx, tab, torch.from_numpy(pairs.view(np.int32)).to(dev), short, st)
+    assert e.value.code == B.EINVAL
+    with pytest.raises(B.BlshError):
+        B.blsh_verify(ctx, tab, torch.from_numpy(pairs.view(np.int32)).to(dev),
+                      torch.from_numpy(sig.view(np.int32)).to(dev), st,
+                      plan=B.blsh_plan(B.PLAN_PERSISTENT, 3, 256, 32, 0))
+
+
+def test_autotune_picks_a_valid_plan(B, ctx):
+    d = TABLE_PARAMS[0]
+    p = oracle_params(d)
+    sig, pairs = model_signatures(0, 256, 20000, seed=3)
+    tab = gpu_tables(B, ctx, d)
+    dev = torch.device("cuda")
+    pt = torch.from_numpy(pairs.view(np.int32)).to(dev)
+    stt = torch.from_numpy(sig.view(np.int32)).to(dev)
+    st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
+    best = B.blsh_autotune(ctx, tab, pt, stt, st)
+    assert best.mode in (0, 1) and best.group in (1, 4, 8, 16, 32)
+    want = O.verify(O.tables(p), pairs, sig)
+    assert_same(run_verify(B, ctx, tab, pairs, sig), want, None, p)   # now with the tuned plan
