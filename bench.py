@@ -1,0 +1,557 @@
+#!/usr/bin/env python
+"""Benchmark of BayesLSH candidate verification on GB300.
+
+A step is one pass of the whole verification path over one batch of
+synthetic objects, every stage in libblsh's CUDA kernels:
+  sign random projections of the sparse rows -> LSH banding candidates ->
+  Algorithm 1 (BayesLSH) over every candidate -> Algorithm 2 (Lite) over every
+  candidate -> compaction of both output sets.
+The inference tables (Section 4.3) are built once per parameter set before the
+timed region (their build time is reported separately).
+
+Default workload (cosine-small): 20,000 tf-idf-like sparse float32 vectors,
+dimension 100,000, Zipf(1.1) term ids, lognormal nnz with mean 80, 200 planted
+near-duplicate groups; 2,048 SRP bits; banding 8 bits x 35 bands; t = 0.7,
+eps = 0.03, delta = 0.05, gamma = 0.03, k = 32, Lite h = 128.
+
+Output: one JSON line (rank 0).  `value` is candidate pairs verified per
+second for the whole job; `e2e` the same through the public API with the
+objects copied from pinned host memory and the output sets copied back inside
+the timed region.
+
+  python bench.py [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "candidate pairs verified/s at fixed t,ε,δ,γ; verify HBM GB/s vs peak; hashes/s"
+
+WORKLOADS = {
+    "cosine-small": dict(kind=1, n=20000, dim=100000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
+                         n_max=2048, k=32, h=128, seed=2,
+                         text="cosine, BayesLSH + Lite: N=20,000 tf-idf sparse float32 vectors, dim 100,000, "
+                              "Zipf(1.1) term ids, lognormal nnz (mean 80), 2,048 SRP bits, banding 8x35, "
+                              "t=0.7, eps=0.03, delta=0.05, gamma=0.03, k=32, h=128"),
+    "jaccard-small": dict(kind=0, n=2000, vocab=10000, n_hashes=256, rows=8, bands=32, t=0.7, n_max=256, k=32,
+                          h=64, seed=1,
+                          text="jaccard, BayesLSH + Lite: N=2,000 sets over vocab 10,000, lognormal sizes "
+                               "(mean 50), 200 planted groups, 256 minhashes, banding 8x32, t=0.7"),
+    "batching": dict(kind=0, n=1_000_000, n_hashes=256, rows=8, bands=32, t=0.5, n_max=256, k=32, h=64, seed=3,
+                     text="jaccard, BayesLSH + Lite: Chung-Lu graph N=1,000,000, exponent 2.1, mean degree 30, "
+                          "256 minhashes, banding 8x32, t=0.5"),
+}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_inputs(w: dict, rank: int = 0):
+    seed = w["seed"] + 1000 * rank
+    if w["kind"] == 1:
+        objs = synth.tfidf_vectors(n_docs=w["n"], dim=w["dim"], mean_nnz=w["mean_nnz"], seed=seed)
+        R = synth.gaussian_matrix(w["dim"], w["bits"], seed=seed + 1)
+        return objs, R
+    if "vocab" in w:
+        objs = synth.jaccard_sets(n_sets=w["n"], vocab=w["vocab"], seed=seed)
+    else:
+        objs = synth.chung_lu_sets(n_nodes=w["n"], seed=seed)
+    a, b = synth.minhash_coeffs(w["n_hashes"], seed=seed + 1)
+    return objs, (a, b)
+
+
+class Pipeline:
+    """Device buffers and the library calls of one step."""
+
+    def __init__(self, B, torch, w: dict, objs, hashp, device):
+        self.B, self.torch, self.w, self.dev = B, torch, w, device
+        t = torch
+        self.ctx = B.Context(device.index or 0)
+        self.kind = w["kind"]
+        N = objs.n
+        self.N = N
+        u32 = lambda a: t.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(device)
+        self.indptr = t.from_numpy(objs.indptr).to(device)
+        self.indices = u32(objs.indices) if objs.indices.size else t.zeros(1, dtype=t.int32, device=device)
+        self.values = None if objs.values is None else t.from_numpy(objs.values).to(device)
+        if self.kind == 1:
+            self.R = t.from_numpy(hashp).to(device)
+            self.W = w["bits"] // 32
+        else:
+            self.a, self.b = u32(hashp[0]), u32(hashp[1])
+            self.W = w["n_hashes"]
+        self.sig = t.zeros((N, self.W), dtype=t.int32, device=device)
+        params = B.make_params(kind=self.kind, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+        t0 = time.perf_counter()
+        self.tab = B.blsh_tables_build(self.ctx, params)
+        self.tables_ms = (time.perf_counter() - t0) * 1e3
+        self.ws = t.zeros(B.blsh_lsh_candidates_workspace(N, self.kind, w["rows"], w["bands"]), dtype=t.uint8,
+                          device=device)
+        self.n_pairs = t.zeros(1, dtype=t.int64, device=device)
+        # size the candidate buffer with a count-only pass
+        self.hash()
+        B.blsh_lsh_candidates(self.ctx, self.sig, self.kind, w["rows"], w["bands"], None, self.n_pairs, self.ws)
+        B.blsh_status(self.ctx)
+        self.P = int(self.n_pairs.item())
+        cap = self.P + 1024
+        self.pairs = t.zeros((cap, 2), dtype=t.int32, device=device)
+        self.status = t.zeros(cap, dtype=t.uint8, device=device)
+        self.n_used = t.zeros(cap, dtype=t.int16, device=device)
+        self.m = t.zeros(cap, dtype=t.int16, device=device)
+        self.est = t.zeros(cap, dtype=t.float32, device=device)
+        self.hist = t.zeros(self.tab.levels, dtype=t.int64, device=device)
+        self.lstatus = t.zeros(cap, dtype=t.uint8, device=device)
+        self.sim = t.zeros(cap, dtype=t.float64, device=device)
+        self.out1 = t.zeros(cap, dtype=t.int64, device=device)
+        self.out2 = t.zeros(cap, dtype=t.int64, device=device)
+        self.n_out = t.zeros(2, dtype=t.int64, device=device)
+        self.band()
+        B.blsh_status(self.ctx)
+        # autotune the verification plan on the real candidates
+        self.plan = B.blsh_autotune(self.ctx, self.tab, self.pairs[: self.P], self.sig, self.status[: self.P],
+                                    self.n_used[: self.P], self.m[: self.P], self.est[: self.P])
+        B.blsh_status(self.ctx)
+
+    # the stages of a step, each one library call
+    def hash(self):
+        B = self.B
+        if self.kind == 1:
+            B.blsh_srp_sparse(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig)
+        else:
+            B.blsh_minhash(self.ctx, self.indptr, self.indices, self.W, self.a, self.b, self.sig)
+
+    def band(self):
+        w = self.w
+        self.B.blsh_lsh_candidates(self.ctx, self.sig, self.kind, w["rows"], w["bands"], self.pairs, self.n_pairs,
+                                   self.ws)
+
+    def verify(self):
+        self.B.blsh_verify(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m, self.est,
+                           self.hist, P_dev=self.n_pairs)
+
+    def lite(self):
+        self.B.blsh_verify_lite(self.ctx, self.tab, self.pairs, self.sig, self.indptr, self.indices, self.values,
+                                self.lstatus, self.sim, P_dev=self.n_pairs)
+
+    def compact(self):
+        B = self.B
+        B.blsh_compact(self.ctx, self.status, (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX), self.out1, self.n_out[0:1],
+                       P_dev=self.n_pairs)
+        B.blsh_compact(self.ctx, self.lstatus, 1 << B.LITE_ACCEPT, self.out2, self.n_out[1:2], P_dev=self.n_pairs)
+
+    STAGES = ("hash", "band", "verify", "lite", "compact")
+
+    def step(self):
+        for s in self.STAGES:
+            getattr(self, s)()
+
+
+# ---------------------------------------------------------------------------
+# measurement helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def srp_sparse_bytes(indptr, bits):
+    """Algorithmic bytes of one sparse-SRP launch: every nonzero reads its
+    index, value and one row of R (bits floats); every row reads two indptr
+    entries and writes bits/8 bytes of signature."""
+    nnz = int(indptr[-1])
+    N = len(indptr) - 1
+    return nnz * (4 + 4 + 4 * bits) + N * (8 + bits // 8)
+
+
+def verify_bytes(kind, k, n_used, P):
+    """Algorithmic bytes of one verify launch: per pair 8 B of pair indices,
+    8 B of output record (status 1 + n 2 + m 2 + est 4, rounded as 8 in the
+    survey's figure; here counted exactly as 9), and per compared chunk the two
+    rows' k hashes (Jaccard 2*4k B, cosine 2*k/8 B)."""
+    chunks = n_used.astype(np.int64) // k
+    per_chunk = 8 * k if kind == 0 else k // 4
+    return P * (8 + 9) + int(chunks.sum()) * per_chunk
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, w):
+    import torch
+
+    import paper_1110_1328_gb300 as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    B.lib()
+
+    objs, hashp = make_inputs(w, rank)
+    pipe = Pipeline(B, torch, w, objs, hashp, device)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    for _ in range(args.warmup):
+        pipe.step()
+    rc = B.blsh_status(pipe.ctx)
+    if rc != 0:
+        raise RuntimeError(f"warm-up step failed with {rc}")
+    launches0 = B.blsh_launch_count(pipe.ctx)
+    pipe.step()
+    launches_per_step = B.blsh_launch_count(pipe.ctx) - launches0
+    torch.cuda.synchronize()
+
+    # capture one step in a CUDA graph (all stages, no host sync inside)
+    graph = None
+    if not args.no_graph:
+        try:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                pipe.step()          # warm on the capture stream
+            stream.wait_stream(s)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                pipe.step()
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            graph = g
+        except Exception as e:   # capture is an optimisation; eager launches do the same work
+            print(f"graph capture failed, timing eager launches: {e}", file=sys.stderr)
+            graph = None
+    B.blsh_status(pipe.ctx)
+
+    def one_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            pipe.step()
+
+    # ---- device-timed steps ----
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))            # L2 flush between timed steps (256 MB write)
+        starts[i].record(stream)
+        one_step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    rc = B.blsh_status(pipe.ctx)
+    if rc != 0:
+        raise RuntimeError(f"timed steps reported {rc}")
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    my_ms = float(np.mean(step_ms))
+    P_total = pipe.P
+    ms = my_ms
+    if dist:
+        tt = torch.tensor([my_ms, float(pipe.P)], dtype=torch.float64, device=device)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        ms = float(mx[0].item())
+        P_total = int(tt[1].item())
+    value = P_total / (ms / 1e3)
+
+    # ---- per-stage device times (eager, events around each library call) ----
+    stage_ms = {s: [] for s in pipe.STAGES}
+    for i in range(max(3, min(args.steps, 5))):
+        flush.fill_(float(i))
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(pipe.STAGES) + 1)]
+        evs[0].record(stream)
+        for j, s in enumerate(pipe.STAGES):
+            getattr(pipe, s)()
+            evs[j + 1].record(stream)
+        torch.cuda.synchronize()
+        for j, s in enumerate(pipe.STAGES):
+            stage_ms[s].append(evs[j].elapsed_time(evs[j + 1]))
+    stage_ms = {s: float(np.mean(v)) for s, v in stage_ms.items()}
+
+    # ---- end to end through the public API, host buffers ----
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_indptr = pin(objs.indptr)
+    h_indices = pin(objs.indices.view(np.int32))
+    h_values = None if objs.values is None else pin(objs.values)
+    h_counts = torch.zeros(2, dtype=torch.int64).pin_memory()
+    h_out1 = torch.zeros(pipe.P + 1024, dtype=torch.int64).pin_memory()
+    h_out2 = torch.zeros(pipe.P + 1024, dtype=torch.int64).pin_memory()
+    e2e_ms, h2d, d2h = [], 0, 0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipe.indptr.copy_(h_indptr, non_blocking=True)
+        pipe.indices[: h_indices.numel()].copy_(h_indices, non_blocking=True)
+        nb_in = h_indptr.numel() * 8 + h_indices.numel() * 4
+        if h_values is not None:
+            pipe.values.copy_(h_values, non_blocking=True)
+            nb_in += h_values.numel() * 4
+        one_step()
+        h_counts.copy_(pipe.n_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        n1, n2 = int(h_counts[0]), int(h_counts[1])
+        h_out1[:n1].copy_(pipe.out1[:n1], non_blocking=True)
+        h_out2[:n2].copy_(pipe.out2[:n2], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2d, d2h = nb_in, 16 + 8 * (n1 + n2)
+    e2e_step = float(np.mean(e2e_ms))
+    e2e_val = pipe.P / (e2e_step / 1e3)
+    if dist:
+        tt = torch.tensor([e2e_step], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_val = P_total / (float(tt.item()) / 1e3)
+
+    # ---- outputs of the last step, for the record ----
+    st = pipe.status[: pipe.P].cpu().numpy()
+    nu = pipe.n_used[: pipe.P].cpu().numpy().view(np.uint16)
+    hist = pipe.hist.cpu().numpy()
+    n1, n2 = [int(x) for x in pipe.n_out.cpu()]
+
+    peak, peak_kind = load_peaks()
+    if w["kind"] == 1:
+        hash_bytes = srp_sparse_bytes(objs.indptr, w["bits"])
+        hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
+    else:
+        nnz = int(objs.indptr[-1])
+        hash_bytes = nnz * 4 + w["n"] * (8 + 4 * w["n_hashes"])
+        hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
+    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P)
+    dominant = max(stage_ms, key=stage_ms.get)
+    rooflines = {
+        "hash": {"kernel": "srp_sparse_kernel" if w["kind"] == 1 else "minhash_kernel", "bytes": hash_bytes},
+        "verify": {"kernel": "verify_kernel", "bytes": vbytes},
+    }
+    dom = "verify" if dominant not in rooflines else dominant
+    rl_bytes = rooflines[dom]["bytes"]
+    achieved = rl_bytes / (stage_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes)}
+    v_ach = vbytes / (stage_ms["verify"] / 1e3) / 1e9
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "candidate_pairs": pipe.P,
+                   "l2": "flushed between timed steps (256 MB write)", "cuda_graph": graph is not None,
+                   "plan": pipe.plan.as_dict(), "tables_build_ms": round(pipe.tables_ms, 2),
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "e2e": {"value": round(e2e_val, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "verify_hbm": {"achieved": round(v_ach, 1), "peak": peak, "unit": "GB/s", "frac": round(v_ach / peak, 4),
+                       "algorithmic_bytes": int(vbytes), "ms": round(stage_ms["verify"], 4)},
+        "hashes_per_s": round(hashes_per_s, 1),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "outputs": {"bayeslsh_kept": n1, "lite_kept": n2, "pruned": int((st == B.PRUNED).sum()),
+                    "stop_hist_first4": [int(x) for x in hist[:4]]},
+        "clocks": clk,
+        "wall_s_timed_loop": round(wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, objs, hashp, pipe.P)
+    elif rank == 0 and world > 1:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_pass(O, w, objs, hashp):
+    """One pass of the oracle over the given objects; returns (pairs, seconds)."""
+    t0 = time.perf_counter()
+    if w["kind"] == 1:
+        sig = O.srp_sparse(objs, hashp)
+    else:
+        sig = O.minhash(objs, hashp[0], hashp[1])
+    pairs = O.lsh_candidates(sig, w["kind"], w["rows"], w["bands"])
+    p = O.Params(kind=w["kind"], t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    tab = O.tables(p)
+    t1 = time.perf_counter()
+    r = O.verify(tab, pairs, sig)
+    lr = O.verify_lite(tab, pairs, sig, objs)
+    O.compact(r.status, (1 << O.ACCEPT) | (1 << O.ACCEPT_AT_MAX))
+    O.compact(lr.status, 1 << O.LITE_ACCEPT)
+    t2 = time.perf_counter()
+    return len(pairs), t2 - t0, t1 - t0
+
+
+def sample_objects(objs, n):
+    """The first n objects of a workload (same generator, same distribution)."""
+    e = int(objs.indptr[n])
+    return synth.CSR(objs.indptr[: n + 1].copy(), objs.indices[:e], None if objs.values is None else objs.values[:e],
+                     objs.dim)
+
+
+def cpu_baseline(w, objs, hashp, P_full):
+    import oracle as O
+    O.build()
+    n = objs.n if objs.n <= 20000 else 20000
+    sub = objs if n == objs.n else sample_objects(objs, n)
+    P, secs, _ = oracle_pass(O, w, sub, hashp)
+    return {"value": round(P / secs, 1), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"one single-threaded oracle pass over the first {n} of {objs.n} objects "
+                      f"({P} candidate pairs, {secs:.1f} s)"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    objs, hashp = make_inputs(w, 0)
+    # each step: the oracle on a bounded slice of the same workload, sized for a
+    # few seconds of CPU work per step
+    n = min(objs.n, 4000 if w["kind"] == 1 else 20000)
+    sub = sample_objects(objs, n)
+    for _ in range(args.warmup):
+        oracle_pass(O, w, sub, hashp)
+    t0 = time.perf_counter()
+    P = 0
+    for _ in range(args.steps):
+        p, _, _ = oracle_pass(O, w, sub, hashp)
+        P += p
+    secs = time.perf_counter() - t0
+    value = P / secs
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "pairs/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload + ": " + w["text"]},
+           "cpu_baseline": {"value": round(value, 1), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                            "sample": f"each step: the oracle over the first {n} of {objs.n} objects "
+                                      f"({P // args.steps} candidate pairs)"},
+           "e2e": {"value": round(value, 1), "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cosine-small", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

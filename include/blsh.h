@@ -129,6 +129,11 @@ BLSH_API const char *blsh_last_error(const blsh_ctx *ctx);
  * products that were exactly zero; they are then reset. */
 BLSH_API int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters);
 
+/* Number of kernels this context has launched so far (host-side count of
+ * every launch the library enqueued through it; replays of a captured CUDA
+ * graph are not counted).  -1 for a NULL context. */
+BLSH_API int64_t blsh_launch_count(const blsh_ctx *ctx);
+
 /* ---- Section 4.3 tables -------------------------------------------------- */
 
 /* Builds, in FP64 on the GPU, for n_j = (j+1) k, j = 0 .. n_max/k - 1:

@@ -62,6 +62,7 @@ def lib():
             "blsh_ctx_destroy": ([p], C.c_int),
             "blsh_last_error": ([p], C.c_char_p),
             "blsh_status": ([p, p, p], C.c_int),
+            "blsh_launch_count": ([p], C.c_int64),
             "blsh_tables_build": ([p, p, p, p], C.c_int),
             "blsh_tables_destroy": ([p], C.c_int),
             "blsh_tables_download": ([p, p, p, p, p, p, p, p, p], C.c_int),
@@ -177,7 +178,8 @@ def make_params(kind=JACCARD, t=0.7, eps=0.03, delta=0.05, gamma=0.03, alpha=1.0
                 h=None) -> blsh_params:
     if h is None:
         h = 64 if kind == JACCARD else 128
-    return blsh_params(kind, k, n_max, min(h, n_max), t, eps, delta, gamma, alpha, beta)
+    h = min(n_max, (h + k - 1) // k * k)      # Lite's h: a multiple of k, at most n_max
+    return blsh_params(kind, k, n_max, h, t, eps, delta, gamma, alpha, beta)
 
 
 # ---------------------------------------------------------------------------
@@ -194,6 +196,10 @@ def blsh_status(ctx: Context, stream=None, counters: bool = False):
     if counters:
         return rc, list(buf)
     return rc
+
+
+def blsh_launch_count(ctx: Context) -> int:
+    return int(lib().blsh_launch_count(ctx.handle))
 
 
 def blsh_tables_build(ctx: Context, params: blsh_params, stream=None) -> Tables:

@@ -112,3 +112,7 @@ extern "C" int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters) {
     if (h.err_code != 0) return blsh_fail(ctx, (int)h.err_code, "device error %u", h.err_code);
     return BLSH_OK;
 }
+
+extern "C" int64_t blsh_launch_count(const blsh_ctx *ctx) {
+    return ctx ? (int64_t)ctx->launches.load(std::memory_order_relaxed) : -1;
+}

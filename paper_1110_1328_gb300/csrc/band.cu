@@ -297,6 +297,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
         BLSH_LAUNCHED(ctx, "radix histogram");
         BLSH_CUDA(ctx, blsh_scan::exclusive_scan<uint32_t>(hist, hist, 256 * tiles, (uint32_t *)(ws + L.partial),
                                                            (uint32_t *)(ws + L.grand), s));
+        ctx->launches.fetch_add(3, std::memory_order_relaxed);
         digit_scatter_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n, shift, hist,
                                                                       (int)tiles, keys[cur ^ 1], vals[cur ^ 1]);
         BLSH_LAUNCHED(ctx, "radix scatter");
@@ -307,6 +308,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     BLSH_CUDA(ctx, blsh_scan::exclusive_scan<unsigned long long>(counts, counts, n,
                                                                  (unsigned long long *)(ws + L.partial),
                                                                  (unsigned long long *)n_pairs, s));
+    ctx->launches.fetch_add(3, std::memory_order_relaxed);
     emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     BLSH_LAUNCHED(ctx, "pair write");
     check_cap_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs, cap, ctx->scratch);

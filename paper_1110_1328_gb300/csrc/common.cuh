@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -34,6 +35,7 @@ struct blsh_ctx {
     blsh_dev_scratch *scratch = nullptr;
     char err[512] = {0};
     std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
+    std::atomic<long long> launches{0};            // kernels launched through this context
     std::mutex mu;
 };
 
@@ -66,11 +68,12 @@ int blsh_cuda_check(blsh_ctx *ctx, cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return blsh_cuda_check(ctx, e_, #call); \
     } while (0)
 
-// Checks the launch that was just enqueued.
+// Checks the launch that was just enqueued and counts it.
 #define BLSH_LAUNCHED(ctx, what)                                  \
     do {                                                          \
         cudaError_t e_ = cudaGetLastError();                      \
         if (e_ != cudaSuccess) return blsh_cuda_check(ctx, e_, what); \
+        (ctx)->launches.fetch_add(1, std::memory_order_relaxed);  \
     } while (0)
 
 static inline bool blsh_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }

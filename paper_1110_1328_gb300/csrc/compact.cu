@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(kThreads) compact_write(const uint8_t *status,
 extern "C" int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, const int64_t *P_dev,
                             uint32_t keep_mask, int64_t *out_idx, int64_t cap, int64_t *n_out, void *stream) {
     if (!ctx) return BLSH_EINVAL;
-    if (!status || !n_out || (cap > 0 && !out_idx)) return blsh_fail(ctx, BLSH_EINVAL, "status and n_out required");
+    if (!n_out || (P > 0 && !status) || (cap > 0 && !out_idx))
+        return blsh_fail(ctx, BLSH_EINVAL, "status and n_out required");
     if (P < 0 || cap < 0) return blsh_fail(ctx, BLSH_EINVAL, "bad P or cap");
     if (!blsh_aligned(out_idx, 8) || !blsh_aligned(n_out, 8) || !blsh_aligned(P_dev, 8))
         return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");

@@ -139,7 +139,7 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     const blsh_params &p = tab->p;
     if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
     if (p.h <= 0) return blsh_fail(ctx, BLSH_EINVAL, "the tables were built with h = 0");
-    if (!pairs || !sig || !status || !sim || !indptr || !indices)
+    if (!sig || !indptr || (P > 0 && (!pairs || !status || !sim || !indices)))
         return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig, status, sim, indptr and indices are required");
     if ((p.kind == BLSH_COSINE) != (values != nullptr))
         return blsh_fail(ctx, BLSH_EINVAL, "values must be given for cosine rows and only for them");

@@ -231,6 +231,7 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     if (e == cudaSuccess) {
         build_tables_kernel<<<tab->levels, 256, 0, s>>>(A);
         e = cudaGetLastError();
+        ctx->launches.fetch_add(1, std::memory_order_relaxed);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, tab->flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -276,7 +276,8 @@ int make_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int6
               const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
               float *est, uint64_t *stop_hist, VerifyArgs &A) {
     const blsh_params &p = tab->p;
-    if (!pairs || !sig || !status) return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig and status are required");
+    if (!sig || (P > 0 && (!pairs || !status)))
+        return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig and status are required");
     if (P < 0 || N < 0 || N > (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "bad P or N");
     const int need = p.kind == BLSH_JACCARD ? p.n_max : (p.n_max + 31) / 32;
     if (sig_words < need || sig_words % 4)

@@ -18,6 +18,8 @@ numpy's PCG64 generator.
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -71,7 +73,9 @@ def gaussian_matrix(rows: int, cols: int, seed: int, row_offset: int = 0,
     row range can be regenerated on its own.
     """
     out = np.empty((rows, cols), dtype=np.float32)
-    for r0 in range(0, rows, chunk_rows):
+    chunk_rows = max(1, min(chunk_rows, (1 << 20) // max(cols, 1)))
+
+    def fill(r0):
         r1 = min(rows, r0 + chunk_rows)
         cnt = (r1 - r0) * cols
         z = splitmix64(seed, 2 * cnt, offset=2 * (row_offset + r0) * cols)
@@ -79,6 +83,15 @@ def gaussian_matrix(rows: int, cols: int, seed: int, row_offset: int = 0,
         u2 = (z[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
         g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
         out[r0:r1] = g.reshape(r1 - r0, cols).astype(np.float32)
+
+    starts = range(0, rows, chunk_rows)
+    if rows * cols >= (1 << 22):
+        # numpy releases the GIL inside these ufuncs; chunks are independent
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
+    else:
+        for r0 in starts:
+            fill(r0)
     return out
 
 

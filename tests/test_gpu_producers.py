@@ -85,10 +85,14 @@ def test_srp_dense_bit_exact(B, ctx, d, bits):
 def gpu_candidates(B, ctx, sig, kind, rows, bands, cap=None):
     N = sig.shape[0]
     ws = torch.zeros(B.blsh_lsh_candidates_workspace(N, kind, rows, bands), dtype=torch.uint8, device=dev)
-    if cap is None:
-        cap = 4 * N * bands + 16
-    pairs = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
     n = torch.zeros(1, dtype=torch.int64, device=dev)
+    if cap is None:
+        # count-only call first (capacity 0), then the real one
+        B.blsh_lsh_candidates(ctx, t32(sig), kind, rows, bands, None, n, ws)
+        rc0 = B.blsh_status(ctx)
+        assert rc0 == (B.ETRUNC if int(n.item()) > 0 else 0)
+        cap = max(1, int(n.item()))
+    pairs = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
     B.blsh_lsh_candidates(ctx, t32(sig), kind, rows, bands, pairs, n, ws)
     rc = B.blsh_status(ctx)
     k = int(n.item())

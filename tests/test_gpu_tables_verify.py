@@ -100,10 +100,8 @@ def assert_same(res, want, hist, p):
 
 def all_plans(B, kind, k):
     plans = []
-    groups = [1] if kind == 1 else [1, 4, 8, 16, 32]
+    groups = [1] if kind == 1 else [g for g in (1, 4, 8, 16, 32) if {1: 32, 4: 32, 8: 32, 16: 64, 32: 128}[g] <= k]
     for g in groups:
-        if kind == 0 and {1: 32, 4: 32, 8: 32, 16: 64, 32: 128}[g] > k:
-            continue
         for block in (128, 512):
             plans.append(B.blsh_plan(B.PLAN_PLAIN, g, block, 32, 0))
             for grab in (1, 37, 256):
