@@ -57,6 +57,7 @@ extern "C" {
 #define BLSH_ENOMEM 4   /* a context or table allocation failed */
 #define BLSH_EDEVICE 5  /* a CUDA runtime call failed (message in blsh_last_error) */
 #define BLSH_ENUMERIC 6 /* a table value is non-finite or not monotone in m */
+#define BLSH_ESIZE 7    /* the problem is larger than a fixed-size scratch array of the library */
 
 /* ---- similarity kinds (Sections 4.1 and 4.2) ---------------------------- */
 #define BLSH_JACCARD 0  /* uint32 minhash values, one per hash */
@@ -270,6 +271,34 @@ BLSH_API int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t
  * cap indices are written and blsh_status reports BLSH_ETRUNC. */
 BLSH_API int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, const int64_t *P_dev, uint32_t keep_mask,
                  int64_t *out_idx, int64_t cap, int64_t *n_out, void *stream);
+
+/* The same stable compaction for callers that cannot allocate device memory
+ * (no counterpart in the paper; it exists for how the library is embedded).
+ * Some callers cannot call cudaMalloc at all -- code running inside a host
+ * application that owns every device allocation through its own memory
+ * pool, or a plug-in for which any allocation outside that pool is
+ * forbidden -- so they cannot create a blsh_ctx, whose scratch area is
+ * allocated.  This entry point takes no context and allocates nothing: its
+ * scratch is a fixed array of 16384 int64 (128 KiB) in the library's own
+ * device memory, which every GPU that loads the library holds until the
+ * process exits.  The caller passes the inputs and outputs, as for
+ * blsh_compact: status uint8 [P], out_idx int64 [cap], *n_out (device int64)
+ * = the number of kept indices (only the first cap are written; there is no
+ * context to report truncation, so compare *n_out with cap).
+ *   - P (the capacity when P_dev is given) may be at most 67,108,864
+ *     (16384 tiles of 4096 statuses); larger P returns BLSH_ESIZE and
+ *     enqueues nothing.  BLSH_EINVAL for bad pointers or sizes,
+ *     BLSH_EDEVICE for a CUDA error.
+ *   - The first call on a device, made with that device current, looks up
+ *     the array's device address (cudaGetSymbolAddress); make that first
+ *     call before any stream capture on the device.
+ *   - Every call reuses the same array, which keeps the last call's
+ *     contents; each call overwrites every entry it reads, so nothing needs
+ *     clearing.  Calls that overlap on the GPU (on different streams, or
+ *     from different threads) race on the array and give wrong results:
+ *     serialise them. */
+BLSH_API int blsh_compact_noalloc(const uint8_t *status, int64_t P, const int64_t *P_dev, uint32_t keep_mask,
+                                  int64_t *out_idx, int64_t cap, int64_t *n_out, void *stream);
 
 #ifdef __cplusplus
 }

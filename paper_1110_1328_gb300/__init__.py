@@ -18,7 +18,7 @@ from . import build as _build
 JACCARD, COSINE = 0, 1
 PRUNED, ACCEPT, ACCEPT_AT_MAX, LITE_REJECT, LITE_ACCEPT, BAD_PAIR = 0, 1, 2, 3, 4, 255
 PLAN_PLAIN, PLAN_PERSISTENT = 0, 1
-OK, EINVAL, ERANGE, ETRUNC, ENOMEM, EDEVICE, ENUMERIC = range(7)
+OK, EINVAL, ERANGE, ETRUNC, ENOMEM, EDEVICE, ENUMERIC, ESIZE = range(8)
 
 _lib = None
 
@@ -76,6 +76,7 @@ def lib():
             "blsh_verify_lite": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p], C.c_int),
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
+            "blsh_compact_noalloc": ([p, i64, p, u32, p, i64, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -322,3 +323,15 @@ def blsh_compact(ctx: Context, status, keep_mask: int, out_idx, n_out, P_dev=Non
                             _dev(out_idx, torch.int64) if cap else None, cap, _dev(n_out, torch.int64),
                             _stream(stream))
     _check(rc, ctx)
+
+
+def blsh_compact_noalloc(status, keep_mask: int, out_idx, n_out, P_dev=None, stream=None):
+    """The stable compaction without a context and without any allocation
+    (scratch in a fixed array of the library; see include/blsh.h)."""
+    P = status.numel()
+    cap = out_idx.numel() if out_idx is not None else 0
+    rc = lib().blsh_compact_noalloc(_dev(status, torch.uint8), P, _dev(P_dev, torch.int64), keep_mask,
+                                    _dev(out_idx, torch.int64) if cap else None, cap, _dev(n_out, torch.int64),
+                                    _stream(stream))
+    if rc != OK:
+        raise BlshError(rc, lib().blsh_strerror(rc).decode())

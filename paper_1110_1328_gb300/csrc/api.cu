@@ -34,6 +34,7 @@ extern "C" const char *blsh_strerror(int code) {
     case BLSH_ENOMEM: return "out of memory";
     case BLSH_EDEVICE: return "CUDA error";
     case BLSH_ENUMERIC: return "numerical problem in the inference tables";
+    case BLSH_ESIZE: return "problem larger than a fixed-size scratch array of the library";
     default: return "unknown error";
     }
 }
