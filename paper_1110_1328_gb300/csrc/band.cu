@@ -10,9 +10,13 @@
 //      increasing order inside a group;
 //   3. for each sorted position p, the pairs (p, q > p) inside its group are
 //      counted, then written at offsets from a prefix sum.  A pair is written
-//      only for the first band in which it collides (earlier bands are
-//      compared), so every distinct pair appears once; Jaccard bands are
-//      compared in full, so hash collisions never merge buckets.
+//      only for the first band in which it collides, so every distinct pair
+//      appears once.  To find that band cheaply every object also gets a row
+//      of its band keys in band order: cosine keys packed as bytes, 16-bit
+//      or 32-bit lanes (by `rows`), compared four / two / one band at a time
+//      with a SWAR zero-lane test on the XOR of two rows; Jaccard 64-bit band
+//      hashes, confirmed by comparing the hashes themselves, so a hash
+//      collision never merges buckets.
 #include "common.cuh"
 #include "scan.cuh"
 
@@ -50,7 +54,17 @@ struct BandArgs {
     long long N;
     int W, kind, rows, bands, band_bits, key_shift;
     unsigned long long *bk;   // Jaccard: [N][bands] band hashes
+    uint32_t *ck;             // cosine: [N][ck_words] band keys packed in lanes of ck_lane bytes
+    int ck_lane, ck_words;
 };
+
+// Lane width (bytes) of packed cosine band keys, and 32-bit words per row
+// (rounded up to a multiple of 4 words so rows are 16-byte aligned).
+__host__ __device__ inline int cos_lane_bytes(int rows) { return rows <= 8 ? 1 : (rows <= 16 ? 2 : 4); }
+__host__ __device__ inline int cos_row_words(int rows, int bands) {
+    const int words = (bands * cos_lane_bytes(rows) + 3) / 4;
+    return (words + 3) & ~3;
+}
 
 __global__ void band_keys_kernel(BandArgs A, unsigned long long *keys, uint32_t *vals) {
     const long long n = A.N * A.bands;
@@ -61,7 +75,12 @@ __global__ void band_keys_kernel(BandArgs A, unsigned long long *keys, uint32_t 
         const uint32_t *row = A.sig + (size_t)i * A.W;
         unsigned long long key;
         if (A.kind == BLSH_COSINE) {
-            key = ((unsigned long long)b << A.rows) | bit_field(row, b * A.rows, A.rows);
+            const uint32_t f = bit_field(row, b * A.rows, A.rows);
+            key = ((unsigned long long)b << A.rows) | f;
+            unsigned char *kr = reinterpret_cast<unsigned char *>(A.ck + (size_t)i * A.ck_words);
+            if (A.ck_lane == 1) kr[b] = (unsigned char)f;
+            else if (A.ck_lane == 2) reinterpret_cast<uint16_t *>(kr)[b] = (uint16_t)f;
+            else reinterpret_cast<uint32_t *>(kr)[b] = f;
         } else {
             const unsigned long long h = band_hash(row, b * A.rows, A.rows);
             A.bk[(size_t)i * A.bands + b] = h;
@@ -152,14 +171,34 @@ __device__ __forceinline__ bool same_band(const BandArgs &A, uint32_t x, uint32_
     return true;
 }
 
+// Nonzero iff some lane of v (lanes of 1, 2 or 4 bytes) is zero.  The
+// borrow of the subtraction can also flag a lane above a zero lane, never a
+// lane below the lowest zero lane, so "any zero lane among the low lanes" is
+// exact once the lanes above are masked off.
+__device__ __forceinline__ uint32_t zero_lanes(uint32_t v, int lane) {
+    if (lane == 1) return (v - 0x01010101u) & ~v & 0x80808080u;
+    if (lane == 2) return (v - 0x00010001u) & ~v & 0x80008000u;
+    return v == 0u ? 0x80000000u : 0u;
+}
+
+// Does any band c < b of x and y agree?  Cosine: packed key rows.
+__device__ __forceinline__ bool earlier_band_cos(const BandArgs &A, uint32_t x, uint32_t y, int b) {
+    const uint32_t *kx = A.ck + (size_t)x * A.ck_words, *ky = A.ck + (size_t)y * A.ck_words;
+    const int per_word = 4 / A.ck_lane;
+    const int full = b / per_word, rest = b % per_word;
+    for (int w = 0; w < full; ++w)
+        if (zero_lanes(__ldg(kx + w) ^ __ldg(ky + w), A.ck_lane)) return true;
+    if (rest) {
+        const uint32_t keep = (1u << (8 * A.ck_lane * rest)) - 1u;   // the low `rest` lanes
+        if (zero_lanes(__ldg(kx + full) ^ __ldg(ky + full), A.ck_lane) & keep) return true;
+    }
+    return false;
+}
+
 // The pair (x, y) met in band b is emitted iff its band-b keys agree in full
 // and no earlier band has them agree.
 __device__ __forceinline__ bool emit_here(const BandArgs &A, uint32_t x, uint32_t y, int b) {
-    if (A.kind == BLSH_COSINE) {
-        for (int c = 0; c < b; ++c)
-            if (same_band(A, x, y, c)) return false;
-        return true;
-    }
+    if (A.kind == BLSH_COSINE) return !earlier_band_cos(A, x, y, b);
     if (!same_band(A, x, y, b)) return false;
     const unsigned long long *bx = A.bk + (size_t)x * A.bands, *by = A.bk + (size_t)y * A.bands;
     for (int c = 0; c < b; ++c)
@@ -182,10 +221,7 @@ __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const ui
             if (emit_here(A, x, y, b)) {
                 if (WRITE) {
                     const long long o = (long long)(out + c);
-                    if (o < cap) {
-                        pairs[2 * o] = x;
-                        pairs[2 * o + 1] = y;
-                    }
+                    if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
                 }
                 ++c;
             }
@@ -201,10 +237,10 @@ __global__ void check_cap_kernel(const long long *n_pairs, long long cap, blsh_d
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t keys0, keys1, vals0, vals1, bk, counts, hist, partial, grand, total;
+    size_t keys0, keys1, vals0, vals1, bk, ck, counts, hist, partial, grand, total;
 };
 
-Layout layout(long long N, int kind, int bands) {
+Layout layout(long long N, int kind, int rows, int bands) {
     const long long n = N * bands;
     const long long tiles = (n + kSortTile - 1) / kSortTile;
     const long long hist_n = 256 * tiles;
@@ -216,6 +252,7 @@ Layout layout(long long N, int kind, int bands) {
     L.vals0 = o; o = up256(o + n * 4);
     L.vals1 = o; o = up256(o + n * 4);
     L.bk = o; o = up256(o + (kind == BLSH_JACCARD ? n * 8 : 0));
+    L.ck = o; o = up256(o + (kind == BLSH_COSINE ? (size_t)N * cos_row_words(rows, bands) * 4 : 0));
     L.counts = o; o = up256(o + n * 8);
     L.hist = o; o = up256(o + hist_n * 4);
     L.partial = o; o = up256(o + part * 8);
@@ -235,7 +272,7 @@ int band_bits_for(int bands) {
 extern "C" int blsh_lsh_candidates_workspace(int64_t N, int32_t kind, int32_t rows, int32_t bands, size_t *bytes) {
     if (!bytes || N < 0 || bands <= 0 || rows <= 0) return BLSH_EINVAL;
     if (kind != BLSH_JACCARD && kind != BLSH_COSINE) return BLSH_EINVAL;
-    *bytes = layout(N, kind, bands).total;
+    *bytes = layout(N, kind, rows, bands).total;
     return BLSH_OK;
 }
 
@@ -254,9 +291,9 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     const int band_bits = band_bits_for(bands);
     if (kind == BLSH_COSINE && band_bits + rows > 64) return blsh_fail(ctx, BLSH_EINVAL, "too many bands");
     if ((long long)N * bands >= (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "N * bands must be < 2^32");
-    if (!blsh_aligned(n_pairs, 8) || !blsh_aligned(workspace, 256) || !blsh_aligned(pairs, 4))
+    if (!blsh_aligned(n_pairs, 8) || !blsh_aligned(workspace, 256) || !blsh_aligned(pairs, 8))
         return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
-    const Layout L = layout(N, kind, bands);
+    const Layout L = layout(N, kind, rows, bands);
     if (!workspace || workspace_bytes < L.total)
         return blsh_fail(ctx, BLSH_ETRUNC, "workspace needs %zu bytes", L.total);
     blsh_device_guard g(ctx->device);
@@ -282,6 +319,11 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     A.band_bits = band_bits;
     A.key_shift = 64 - band_bits;
     A.bk = kind == BLSH_JACCARD ? (unsigned long long *)(ws + L.bk) : nullptr;
+    A.ck = kind == BLSH_COSINE ? (uint32_t *)(ws + L.ck) : nullptr;
+    A.ck_lane = cos_lane_bytes(rows);
+    A.ck_words = cos_row_words(rows, bands);
+    if (kind == BLSH_COSINE)   // pad lanes past the last band stay zero
+        BLSH_CUDA(ctx, cudaMemsetAsync(A.ck, 0, (size_t)N * A.ck_words * 4, s));
 
     const unsigned grid = (unsigned)((n + 255) / 256 < 65535ll * 16 ? (n + 255) / 256 : 65535ll * 16);
     band_keys_kernel<<<grid, 256, 0, s>>>(A, keys[0], vals[0]);

@@ -142,6 +142,99 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
 }
 
 
+// The same computation when bits is a multiple of 128: thread t owns the
+// float4 groups t, t+T, ... of each row of R (bits 4t..4t+3, 4(t+T).., ...),
+// so every load moves 16 bytes and a warp reads 512 contiguous bytes; the
+// nonzeros are unrolled so several rows of R are in flight per thread.  The
+// four bits of a group form a nibble; eight lanes OR their nibbles into one
+// signature word with shuffles.
+template <int V>
+__global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
+                                                          const uint32_t *__restrict__ indices,
+                                                          const float *__restrict__ values, long long N,
+                                                          const float *__restrict__ R, long long dim, int bits,
+                                                          uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
+    __shared__ uint32_t s_idx[kSrpChunk];
+    __shared__ float s_val[kSrpChunk];
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int words = bits >> 5;
+    unsigned long long rechecked = 0, zeros = 0;
+    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+        float acc[4 * V], mag[4 * V];
+#pragma unroll
+        for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
+        for (long long c0 = s; c0 < e; c0 += kSrpChunk) {
+            const int cnt = (int)min((long long)kSrpChunk, e - c0);
+            __syncthreads();
+            for (int i = t; i < cnt; i += T) {
+                uint32_t ix = __ldg(indices + c0 + i);
+                float v = __ldg(values + c0 + i);
+                if (ix >= dim) {   // malformed row: record it, contribute nothing
+                    blsh_dev_error(scratch, BLSH_ERANGE, 0, 1ull);
+                    ix = 0;
+                    v = 0.0f;
+                }
+                s_idx[i] = ix;
+                s_val[i] = v;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int i = 0; i < cnt; ++i) {
+                const float v = s_val[i];
+                const float av = fabsf(v);
+                const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)s_idx[i] * bits) + t;
+#pragma unroll
+                for (int g = 0; g < V; ++g) {
+                    const float4 r = __ldg(Rrow + g * T);
+                    acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
+                    acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
+                    acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
+                    acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
+                    mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
+                    mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
+                    mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
+                    mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
+                }
+            }
+        }
+        const float n = (float)(e - s);
+#pragma unroll
+        for (int g = 0; g < V; ++g) {
+            uint32_t nib = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int u = 4 * g + c;
+                const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
+                bool bit;
+                if (fabsf(acc[u]) > bound) {
+                    bit = acc[u] >= 0.0f;
+                } else {
+                    const int j = 4 * (t + g * T) + c;
+                    double d = 0.0;
+                    for (long long k = s; k < e; ++k) {
+                        const uint32_t ix = __ldg(indices + k);
+                        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + j);
+                    }
+                    bit = d >= 0.0;
+                    ++rechecked;
+                    zeros += d == 0.0;
+                }
+                nib |= (uint32_t)bit << c;
+            }
+            uint32_t word = nib << (4 * (lane & 7));
+            word |= __shfl_xor_sync(kFull, word, 1);
+            word |= __shfl_xor_sync(kFull, word, 2);
+            word |= __shfl_xor_sync(kFull, word, 4);
+            if ((lane & 7) == 0) sig[(size_t)row * words + ((t + g * T) >> 3)] = word;
+        }
+    }
+    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
+    if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
 // Dense rows X [N][d] against R [d][bits], the same FP32 sums with the same
 // error bound and FP64 recheck (coordinates in order 0..d-1).  One CTA per
 // row; the row is staged in shared memory.
@@ -254,6 +347,26 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
     cudaStream_t s = blsh_stream(stream);
     const long long cap = (long long)ctx->sm_count * 16;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
+    if (bits % 128 == 0 && blsh_aligned(R, 16)) {
+        // float4 path: T4 = 32 * (largest divisor of groups/32 up to 8) threads,
+        // V = groups / T4 float4 groups per thread
+        const int groups = bits / 4;
+        int wt = 8;
+        while ((groups / 32) % wt) --wt;
+        const int T4 = 32 * wt, V = groups / T4;
+        bool launched = true;
+        switch (V) {
+        case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
+        case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
+        case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
+        case 4: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
+        default: launched = false;
+        }
+        if (launched) {
+            BLSH_LAUNCHED(ctx, "srp sparse kernel");
+            return BLSH_OK;
+        }
+    }
     srp_sparse_kernel<<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp sparse kernel");
     return BLSH_OK;

@@ -3,8 +3,8 @@
 // Pass 1 is the verification kernel of verify.cu in its Lite form: the
 // pruning loop over at most h hashes, no concentration test; an unpruned
 // pair is marked as a survivor in its status byte.  Pass 2 (this file) gives
-// every survivor its exact similarity: persistent warps take tiles of 32
-// statuses from a work counter, and the warp computes each survivor's
+// every survivor its exact similarity: persistent warps take 256 statuses at
+// a time from a work counter, and the warp computes each survivor's
 // similarity cooperatively by intersecting the two sorted index lists (each
 // lane binary-searches elements of the shorter row in the longer one).
 //
@@ -64,10 +64,13 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
     }
     const int lane = threadIdx.x & 31;
     for (;;) {
-        unsigned long long tile = 0;
-        if (lane == 0) tile = atomicAdd(&A.scratch->work2, 1ull);
-        tile = __shfl_sync(kFull, tile, 0);
-        const long long q0 = (long long)tile * 32;
+        // a warp takes 8 tiles of 32 statuses per grab of the work counter
+        unsigned long long grab = 0;
+        if (lane == 0) grab = atomicAdd(&A.scratch->work2, 1ull);
+        grab = __shfl_sync(kFull, grab, 0);
+        if ((long long)grab * 256 >= P) break;
+        for (int sub = 0; sub < 8; ++sub) {
+        const long long q0 = (long long)grab * 256 + sub * 32;
         if (q0 >= P) break;
         const long long mine = q0 + lane;
         const bool surv = mine < P && A.status[mine] == BLSH_LITE_SURVIVOR;
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
             }
         }
+        }
     }
 }
 
@@ -181,7 +185,7 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
         auto it = ctx->plans.find(tab);
         if (it != ctx->plans.end()) plan = it->second;
     }
-    A.grab = plan.grab;
+    A.grab = (plan.grab + 31) / 32 * 32;
     int rc = blsh_launch_verify(ctx, A, plan, s);
     if (rc) return rc;
     if (P == 0) return BLSH_OK;

@@ -83,9 +83,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             ++j;
         }
     };
-    auto start = [&](long long qq) {
+    auto start_pair = [&](long long qq, unsigned px, unsigned py) {
         q = qq;
-        const uint2 pr = __ldg(A.pairs + qq);
+        const uint2 pr = make_uint2(px, py);
         if ((long long)pr.x >= A.N || (long long)pr.y >= A.N) {
             if (g == 0) {
                 A.status[q] = BLSH_BAD_PAIR;
@@ -149,37 +149,74 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     };
 
     if constexpr (PERSIST) {
-        unsigned long long cur = 0, end = 0;
-        bool exhausted = false;
+        // Pair indices reach the lanes through two 32-entry register buffers
+        // per warp: lane l holds entry l of the current block of 32 pairs and
+        // of the next one, which is loaded (coalesced) as soon as the current
+        // block is opened, so a pair's indices are on chip when a group needs
+        // them.  Blocks come from ranges of `grab` pairs (a multiple of 32)
+        // taken from the work counter.
         const unsigned lower = (1u << (grp * G)) - 1u;   // lanes of lower groups
+        unsigned long long gcur = 0, gend = 0;
+        bool no_more = false;
+        // next block of 32 pair indices from the warp's range: base, valid count
+        auto next_block = [&](unsigned long long &base, int &valid) {
+            valid = 0;
+            if (gcur >= gend && !no_more) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(&A.scratch->work, (unsigned long long)A.grab);
+                b = __shfl_sync(kFull, b, 0);
+                if (b >= (unsigned long long)P) {
+                    no_more = true;
+                } else {
+                    gcur = b;
+                    gend = b + A.grab < (unsigned long long)P ? b + A.grab : (unsigned long long)P;
+                }
+            }
+            if (gcur < gend) {
+                base = gcur;
+                valid = (int)(gend - gcur < 32ull ? gend - gcur : 32ull);
+                gcur += valid;
+            }
+        };
+        unsigned long long cbase = 0, nbase = 0;
+        int cvalid = 0, nvalid = 0, cpos = 0;
+        uint2 cur = make_uint2(0u, 0u), nxt = make_uint2(0u, 0u);
+        next_block(cbase, cvalid);
+        if (lane < cvalid) cur = __ldg(A.pairs + cbase + lane);
+        next_block(nbase, nvalid);
+        if (lane < nvalid) nxt = __ldg(A.pairs + nbase + lane);
         for (;;) {
             for (;;) {
                 const bool need = !active;
                 const unsigned need_mask = __ballot_sync(kFull, need && g == 0);
-                if (need_mask == 0 || exhausted) break;
-                if (cur >= end) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&A.scratch->work, (unsigned long long)A.grab);
-                    base = __shfl_sync(kFull, base, 0);
-                    if (base >= (unsigned long long)P) {
-                        exhausted = true;
-                        break;
-                    }
-                    cur = base;
-                    end = base + A.grab < (unsigned long long)P ? base + A.grab : (unsigned long long)P;
+                if (need_mask == 0) break;
+                if (cpos == cvalid) {
+                    if (nvalid == 0) break;   // nothing left anywhere
+                    cur = nxt;
+                    cbase = nbase;
+                    cvalid = nvalid;
+                    cpos = 0;
+                    next_block(nbase, nvalid);
+                    if (lane < nvalid) nxt = __ldg(A.pairs + nbase + lane);
                 }
-                const unsigned long long avail = end - cur;
-                const unsigned rank = __popc(need_mask & lower);
-                if (need && rank < avail) start((long long)(cur + rank));
-                const unsigned long long want = __popc(need_mask);
-                cur += want < avail ? want : avail;
+                const int avail = cvalid - cpos;
+                const int rank = __popc(need_mask & lower);
+                const int src = (cpos + rank) & 31;
+                const unsigned px = __shfl_sync(kFull, cur.x, src);
+                const unsigned py = __shfl_sync(kFull, cur.y, src);
+                if (need && rank < avail) start_pair((long long)(cbase + cpos + rank), px, py);
+                const int want = __popc(need_mask);
+                cpos += want < avail ? want : avail;
             }
             if (!__any_sync(kFull, active)) break;
             step();
         }
     } else {
         const long long qq = (long long)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
-        if (qq < P) start(qq);
+        if (qq < P) {
+            const uint2 pr = __ldg(A.pairs + qq);
+            start_pair(qq, pr.x, pr.y);
+        }
         while (__any_sync(kFull, active)) step();
     }
 
@@ -260,6 +297,7 @@ int blsh_check_plan(const blsh_plan &plan, int kind, int k) {
         if (wps > k) return BLSH_EINVAL;
     }
     if (plan.mode == BLSH_PLAN_PERSISTENT && (plan.grab < 1 || plan.grab > (1 << 20))) return BLSH_EINVAL;
+    // (persistent launches round grab up to a multiple of 32)
     if (plan.ctas_per_sm < 0) return BLSH_EINVAL;
     return BLSH_OK;
 }
@@ -324,7 +362,7 @@ extern "C" int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const bls
     VerifyArgs A;
     int rc = make_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est, stop_hist, A);
     if (rc) return rc;
-    A.grab = plan->grab;
+    A.grab = (plan->grab + 31) / 32 * 32;
     blsh_device_guard g(ctx->device);
     cudaStream_t s = blsh_stream(stream);
     if (stop_hist) BLSH_CUDA(ctx, cudaMemsetAsync(stop_hist, 0, sizeof(uint64_t) * tab->levels, s));

@@ -39,7 +39,7 @@ def test_minhash_bit_exact(B, ctx, n_hashes):
     assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
 
 
-@pytest.mark.parametrize("bits", [64, 96, 2048])
+@pytest.mark.parametrize("bits", [64, 96, 384, 1536, 2048, 4096])
 def test_srp_sparse_bit_exact(B, ctx, bits):
     vecs = synth.tfidf_vectors(n_docs=900, dim=20000, mean_nnz=80, n_groups=50, seed=bits)
     R = synth.gaussian_matrix(20000, bits, seed=11)
