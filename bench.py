@@ -226,13 +226,24 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def srp_sparse_bytes(indptr, bits):
+def srp_sparse_bytes(indptr, indices, bits):
     """Algorithmic bytes of one sparse-SRP launch: every nonzero reads its
     index, value and one row of R (bits floats); every row reads two indptr
-    entries and writes bits/8 bytes of signature."""
+    entries and writes bits/8 bytes of signature.  Also returned: the unique
+    bytes (each distinct row of R once), the least DRAM traffic possible."""
     nnz = int(indptr[-1])
     N = len(indptr) - 1
-    return nnz * (4 + 4 + 4 * bits) + N * (8 + bits // 8)
+    fixed = nnz * 8 + N * (8 + bits // 8)
+    distinct = int(np.unique(indices).size)
+    return fixed + nnz * 4 * bits, fixed + distinct * 4 * bits
+
+
+def band_bytes(N, bands, P, passes):
+    """Algorithmic bytes of one banding call: per (object, band) key and id
+    written once and moved by every radix pass (read + write), per emitted
+    pair 8 bytes written."""
+    n = N * bands
+    return n * 12 * (1 + 2 * passes) + P * 8
 
 
 def verify_bytes(kind, k, n_used, P):
@@ -400,25 +411,31 @@ def run_ours(args, w):
     n1, n2 = [int(x) for x in pipe.n_out.cpu()]
 
     peak, peak_kind = load_peaks()
+    unique = None
     if w["kind"] == 1:
-        hash_bytes = srp_sparse_bytes(objs.indptr, w["bits"])
+        hash_bytes, unique = srp_sparse_bytes(objs.indptr, objs.indices, w["bits"])
         hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
     else:
         nnz = int(objs.indptr[-1])
         hash_bytes = nnz * 4 + w["n"] * (8 + 4 * w["n_hashes"])
         hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
     vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P)
-    dominant = max(stage_ms, key=stage_ms.get)
+    key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
     rooflines = {
-        "hash": {"kernel": "srp_sparse_kernel" if w["kind"] == 1 else "minhash_kernel", "bytes": hash_bytes},
+        "hash": {"kernel": "srp_sparse4_kernel" if w["kind"] == 1 else "minhash_kernel", "bytes": hash_bytes},
+        "band": {"kernel": "emit_kernel + radix sort", "bytes": band_bytes(pipe.N, w["bands"], pipe.P,
+                                                                             (key_bits + 7) // 8)},
         "verify": {"kernel": "verify_kernel", "bytes": vbytes},
     }
-    dom = "verify" if dominant not in rooflines else dominant
+    dom = max(rooflines, key=lambda k: stage_ms[k])
     rl_bytes = rooflines[dom]["bytes"]
     achieved = rl_bytes / (stage_ms[dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes)}
+                "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes), "stage": dom}
+    if dom == "hash" and unique is not None:
+        roofline["unique_bytes"] = int(unique)
+        roofline["unique_frac"] = round(unique / (stage_ms[dom] / 1e3) / 1e9 / peak, 4)
     v_ach = vbytes / (stage_ms["verify"] / 1e3) / 1e9
 
     out = {

@@ -223,8 +223,9 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
  *   conc[j][m]                   -> BLSH_ACCEPT,
  *   n == n_max                   -> BLSH_ACCEPT_AT_MAX.
  * Outputs per pair: status uint8 [P]; n_used uint16 [P] (hashes compared);
- * m uint16 [P] (agreements); est float [P] (S^(m, n) at the stop).  n_used,
- * m, est may be NULL.  stop_hist: uint64 [n_max/k] or NULL; entry j counts
+ * m uint16 [P] (agreements); est float [P]: S^(m, n) at the stop for kept
+ * pairs (Algorithm 1 outputs an estimate only with a kept pair), NaN for
+ * pruned ones.  n_used, m, est may be NULL.  stop_hist: uint64 [n_max/k] or NULL; entry j counts
  * the pairs that stopped after chunk j (the call overwrites it).
  * P_dev: NULL, or a device int64 holding the pair count; the kernel then
  * reads the count there (clamped to P, which acts as the capacity), so the

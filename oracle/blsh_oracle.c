@@ -294,7 +294,8 @@ int64_t orc_verify(int kind, int k, int n_max, const int32_t *min_matches, const
         status[q] = (uint8_t)st;
         n_used[q] = (uint16_t)n;
         m_out[q] = (uint16_t)m;
-        est[q] = est_tab[(size_t)(n / k - 1) * W + m];
+        /* Algorithm 1 outputs S^ only with a kept pair */
+        est[q] = st == ORC_PRUNED ? NAN : est_tab[(size_t)(n / k - 1) * W + m];
     }
     return bad;
 }

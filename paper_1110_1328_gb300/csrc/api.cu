@@ -69,9 +69,16 @@ extern "C" int blsh_ctx_create(blsh_ctx **out, int device) {
         delete ctx;
         return BLSH_ENOMEM;
     }
+    if (cudaMalloc((void **)&ctx->recheck_queue, sizeof(uint2) * BLSH_RECHECK_CAP) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->scratch);
+        delete ctx;
+        return BLSH_ENOMEM;
+    }
     if (cudaMemset(ctx->scratch, 0, sizeof(blsh_dev_scratch)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(ctx->scratch);
+        cudaFree(ctx->recheck_queue);
         delete ctx;
         return BLSH_EDEVICE;
     }
@@ -84,6 +91,7 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
     {
         blsh_device_guard g(ctx->device);
         if (ctx->scratch) cudaFree(ctx->scratch);
+        if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
     }
     delete ctx;
     return BLSH_OK;

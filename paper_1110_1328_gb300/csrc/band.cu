@@ -206,9 +206,41 @@ __device__ __forceinline__ bool emit_here(const BandArgs &A, uint32_t x, uint32_
     return true;
 }
 
+// Cosine rows of packed band keys are at most kCkRegWords words long when
+// they fit the register fast path below (64 one-byte bands, 32 two-byte
+// bands or 16 four-byte bands).
+constexpr int kCkRegWords = 16;
+
+// Cosine emission with x's packed keys held in registers: a pair (x, y) of
+// band b is checked against bands < b with 16-byte loads of y's key row only.
+__device__ __forceinline__ bool earlier_band_cos_reg(const BandArgs &A, const uint4 (&kx)[kCkRegWords / 4],
+                                                     uint32_t y, int b) {
+    const uint4 *ky = reinterpret_cast<const uint4 *>(A.ck + (size_t)y * A.ck_words);
+    const int per_word = 4 / A.ck_lane;
+    const int need = (b + per_word - 1) / per_word;   // words holding bands 0..b-1
+#pragma unroll
+    for (int w4 = 0; w4 < kCkRegWords / 4; ++w4) {
+        if (4 * w4 < need) {
+            const uint4 yv = __ldg(ky + w4);
+            const uint32_t z[4] = {kx[w4].x ^ yv.x, kx[w4].y ^ yv.y, kx[w4].z ^ yv.z, kx[w4].w ^ yv.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int w = 4 * w4 + c;
+                if (w < need) {
+                    const int lanes = (w + 1) * per_word <= b ? per_word : b - w * per_word;
+                    const uint32_t keep = lanes == per_word ? 0xffffffffu : (1u << (8 * A.ck_lane * lanes)) - 1u;
+                    if (zero_lanes(z[c], A.ck_lane) & keep) return true;
+                }
+            }
+        }
+    }
+    return false;
+}
+
 template <bool WRITE>
 __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const uint32_t *vals, long long n,
                             unsigned long long *counts, uint32_t *pairs, long long cap) {
+    const bool reg_path = A.kind == BLSH_COSINE && A.ck_words <= kCkRegWords;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         const unsigned long long key = keys[p];
@@ -216,14 +248,32 @@ __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const ui
         const int b = A.kind == BLSH_COSINE ? (int)(key >> A.rows)
                                              : (A.band_bits == 0 ? 0 : (int)(key >> A.key_shift));
         unsigned long long c = 0, out = WRITE ? counts[p] : 0;
-        for (long long q = p + 1; q < n && keys[q] == key; ++q) {
-            const uint32_t y = vals[q];
-            if (emit_here(A, x, y, b)) {
-                if (WRITE) {
-                    const long long o = (long long)(out + c);
-                    if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+        if (reg_path) {
+            uint4 kx[kCkRegWords / 4];
+            const uint4 *kxp = reinterpret_cast<const uint4 *>(A.ck + (size_t)x * A.ck_words);
+#pragma unroll
+            for (int w4 = 0; w4 < kCkRegWords / 4; ++w4)
+                kx[w4] = 4 * w4 < A.ck_words ? __ldg(kxp + w4) : make_uint4(0u, 0u, 0u, 0u);
+            for (long long q = p + 1; q < n && keys[q] == key; ++q) {
+                const uint32_t y = vals[q];
+                if (!earlier_band_cos_reg(A, kx, y, b)) {
+                    if (WRITE) {
+                        const long long o = (long long)(out + c);
+                        if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+                    }
+                    ++c;
                 }
-                ++c;
+            }
+        } else {
+            for (long long q = p + 1; q < n && keys[q] == key; ++q) {
+                const uint32_t y = vals[q];
+                if (emit_here(A, x, y, b)) {
+                    if (WRITE) {
+                        const long long o = (long long)(out + c);
+                        if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+                    }
+                    ++c;
+                }
             }
         }
         if (!WRITE) counts[p] = c;

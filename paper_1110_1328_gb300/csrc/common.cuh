@@ -15,6 +15,7 @@
 
 #define BLSH_MAX_NMAX 4096
 #define BLSH_COMPACT_MAX_CTAS 2048
+#define BLSH_RECHECK_CAP (1u << 20)   // queued SRP sign rechecks per call (8 MiB per context)
 
 // Device-side scratch owned by a context.  Every call zeroes what it uses
 // before its kernels run (cudaMemsetAsync on the caller's stream).
@@ -24,6 +25,7 @@ struct blsh_dev_scratch {
     unsigned long long counters[4];    // bad pairs, truncations, SRP rechecks, SRP zeros
     unsigned long long work;           // verify: next pair handed out
     unsigned long long work2;          // lite: next survivor tile handed out
+    unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
 };
 
@@ -33,6 +35,7 @@ struct blsh_ctx {
     int cc_major = 0, cc_minor = 0;
     size_t smem_optin = 0;
     blsh_dev_scratch *scratch = nullptr;
+    uint2 *recheck_queue = nullptr;                   // [BLSH_RECHECK_CAP] (row, bit) of undecided SRP signs
     char err[512] = {0};
     std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
     std::atomic<long long> launches{0};            // kernels launched through this context

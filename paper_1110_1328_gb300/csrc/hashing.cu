@@ -142,62 +142,66 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
 }
 
 
+// The FP64 row-order sum of row [s, e) against column j of R, as the oracle
+// forms it (rare: only signs the FP32 bound cannot decide).  Kept out of line
+// so the hot accumulation loop keeps its registers.
+__device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ indices,
+                                                const float *__restrict__ values, long long s, long long e,
+                                                const float *__restrict__ R, long long dim, int bits, int j) {
+    double d = 0.0;
+    for (long long k = s; k < e; ++k) {
+        const uint32_t ix = __ldg(indices + k);
+        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + j);
+    }
+    return d;
+}
+
 // The same computation when bits is a multiple of 128: thread t owns the
 // float4 groups t, t+T, ... of each row of R (bits 4t..4t+3, 4(t+T).., ...),
-// so every load moves 16 bytes and a warp reads 512 contiguous bytes; the
-// nonzeros are unrolled so several rows of R are in flight per thread.  The
-// four bits of a group form a nibble; eight lanes OR their nibbles into one
-// signature word with shuffles.
+// so every load moves 16 bytes and a warp reads 512 contiguous bytes.  A
+// row's indices and values are read straight from global memory (every
+// thread of the CTA reads the same element: one broadcast L1 line), which
+// keeps no barrier in the loop; several rows of R are in flight per thread.
+// The four bits of a group form a nibble; eight lanes OR their nibbles into
+// one signature word with shuffles.
 template <int V>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values, long long N,
                                                           const float *__restrict__ R, long long dim, int bits,
-                                                          uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
-    __shared__ uint32_t s_idx[kSrpChunk];
-    __shared__ float s_val[kSrpChunk];
+                                                          uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
+                                                          uint2 *__restrict__ queue) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int words = bits >> 5;
-    unsigned long long rechecked = 0, zeros = 0;
+    unsigned long long rechecked = 0, zeros = 0, bad = 0;
     for (long long row = blockIdx.x; row < N; row += gridDim.x) {
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
         float acc[4 * V], mag[4 * V];
 #pragma unroll
         for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
-        for (long long c0 = s; c0 < e; c0 += kSrpChunk) {
-            const int cnt = (int)min((long long)kSrpChunk, e - c0);
-            __syncthreads();
-            for (int i = t; i < cnt; i += T) {
-                uint32_t ix = __ldg(indices + c0 + i);
-                float v = __ldg(values + c0 + i);
-                if (ix >= dim) {   // malformed row: record it, contribute nothing
-                    blsh_dev_error(scratch, BLSH_ERANGE, 0, 1ull);
-                    ix = 0;
-                    v = 0.0f;
-                }
-                s_idx[i] = ix;
-                s_val[i] = v;
+        for (long long k = s; k < e; ++k) {
+            uint32_t ix = __ldg(indices + k);
+            float v = __ldg(values + k);
+            if (ix >= dim) {   // malformed row: counted, contributes nothing
+                bad += t == 0;
+                ix = 0;
+                v = 0.0f;
             }
-            __syncthreads();
-#pragma unroll 4
-            for (int i = 0; i < cnt; ++i) {
-                const float v = s_val[i];
-                const float av = fabsf(v);
-                const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)s_idx[i] * bits) + t;
+            const float av = fabsf(v);
+            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits) + t;
 #pragma unroll
-                for (int g = 0; g < V; ++g) {
-                    const float4 r = __ldg(Rrow + g * T);
-                    acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
-                    acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
-                    acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
-                    acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
-                    mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
-                    mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
-                    mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
-                    mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
-                }
+            for (int g = 0; g < V; ++g) {
+                const float4 r = __ldg(Rrow + g * T);
+                acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
+                acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
+                acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
+                acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
+                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
+                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
+                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
+                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
             }
         }
         const float n = (float)(e - s);
@@ -212,15 +216,19 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                 if (fabsf(acc[u]) > bound) {
                     bit = acc[u] >= 0.0f;
                 } else {
-                    const int j = 4 * (t + g * T) + c;
-                    double d = 0.0;
-                    for (long long k = s; k < e; ++k) {
-                        const uint32_t ix = __ldg(indices + k);
-                        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + j);
+                    // undecided: queue it for srp_recheck_kernel (bit left 0 here),
+                    // or recompute in line if the queue is full
+                    const uint32_t j = 4 * (t + g * T) + c;
+                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
+                    if (slot < BLSH_RECHECK_CAP) {
+                        queue[slot] = make_uint2((uint32_t)row, j);
+                        bit = false;
+                    } else {
+                        const double d = srp_recheck_fp64(indices, values, s, e, R, dim, bits, j);
+                        bit = d >= 0.0;
+                        ++rechecked;
+                        zeros += d == 0.0;
                     }
-                    bit = d >= 0.0;
-                    ++rechecked;
-                    zeros += d == 0.0;
                 }
                 nib |= (uint32_t)bit << c;
             }
@@ -231,8 +239,48 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
             if ((lane & 7) == 0) sig[(size_t)row * words + ((t + g * T) >> 3)] = word;
         }
     }
+    if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
     if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
     if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+// The queued signs: one warp per (row, bit).  Lanes load 32 nonzeros at a
+// time and form their exact FP64 products; every lane then adds them in row
+// order (shuffled one by one), so the sum is the FP64 row-order sum bit for
+// bit.  A nonnegative sum sets the bit (the word was written with it clear).
+__global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restrict__ queue,
+                                                          const int64_t *__restrict__ indptr,
+                                                          const uint32_t *__restrict__ indices,
+                                                          const float *__restrict__ values,
+                                                          const float *__restrict__ R, long long dim, int bits,
+                                                          uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
+    const unsigned long long total = scratch->recheck_count;
+    const unsigned long long n = total < BLSH_RECHECK_CAP ? total : BLSH_RECHECK_CAP;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long done = 0, zeros = 0;
+    for (unsigned long long it = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n;
+         it += warps) {
+        const uint2 rj = queue[it];
+        const long long s = __ldg(indptr + rj.x), e = __ldg(indptr + rj.x + 1);
+        double d = 0.0;
+        for (long long c0 = s; c0 < e; c0 += 32) {
+            double p = 0.0;
+            if (c0 + lane < e) {
+                const uint32_t ix = __ldg(indices + c0 + lane);
+                if (ix < dim) p = (double)__ldg(values + c0 + lane) * (double)__ldg(R + (size_t)ix * bits + rj.y);
+            }
+            const int cnt = (int)min(32ll, e - c0);
+            for (int l = 0; l < cnt; ++l) d += __shfl_sync(kFull, p, l);
+        }
+        if (lane == 0) {
+            if (d >= 0.0) atomicOr(sig + (size_t)rj.x * (bits >> 5) + (rj.y >> 5), 1u << (rj.y & 31));
+            ++done;
+            zeros += d == 0.0;
+        }
+    }
+    if (lane == 0 && done) atomicAdd(&scratch->counters[2], done);
+    if (lane == 0 && zeros) atomicAdd(&scratch->counters[3], zeros);
 }
 
 // Dense rows X [N][d] against R [d][bits], the same FP32 sums with the same
@@ -332,8 +380,8 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
     if (!ctx) return BLSH_EINVAL;
     if (!indptr || !indices || !values || !R || !sig)
         return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, values, R and sig are required");
-    if (N < 0 || dim <= 0 || bits <= 0 || bits % 32 || bits > 4096)
-        return blsh_fail(ctx, BLSH_EINVAL, "bits must be a positive multiple of 32, at most 4096");
+    if (N < 0 || N >= (1ll << 32) || dim <= 0 || bits <= 0 || bits % 32 || bits > 4096)
+        return blsh_fail(ctx, BLSH_EINVAL, "bits must be a positive multiple of 32, at most 4096; N < 2^32");
     if (!blsh_aligned(indptr, 8)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned indptr");
     if (N == 0) return BLSH_OK;
     // threads = 32 * (largest divisor of bits/32 that is at most 8)
@@ -354,16 +402,19 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
         int wt = 8;
         while ((groups / 32) % wt) --wt;
         const int T4 = 32 * wt, V = groups / T4;
-        bool launched = true;
-        switch (V) {
-        case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
-        case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
-        case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
-        case 4: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch); break;
-        default: launched = false;
-        }
-        if (launched) {
+        if (V >= 1 && V <= 4) {
+            BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
+            uint2 *q = ctx->recheck_queue;
+            switch (V) {
+            case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            }
             BLSH_LAUNCHED(ctx, "srp sparse kernel");
+            srp_recheck_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig,
+                                                                 ctx->scratch);
+            BLSH_LAUNCHED(ctx, "srp recheck kernel");
             return BLSH_OK;
         }
     }

@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             A.status[q] = (uint8_t)st;
             if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
             if (A.m_out) A.m_out[q] = (uint16_t)m;
-            if (A.est_out) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
+            if (A.est_out)   // the estimate is an output only for pairs that are kept (Algorithm 1)
+                A.est_out[q] = st == BLSH_PRUNED ? __int_as_float(0x7fc00000)
+                                                 : __ldg(A.est_tab + (size_t)j * A.est_stride + m);
             if (A.sim_out && st == BLSH_PRUNED) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
             atomicAdd(&s_hist[j], 1u);
         }

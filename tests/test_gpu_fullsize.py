@@ -1,0 +1,143 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration
+bench.py times (its Pipeline: the autotuned verification plan, device-side
+pair counts, and a CUDA-graph replay of the whole step).
+
+cosine-small (20,000 tf-idf vectors, 2,048 SRP bits, ~2.7e7 candidate pairs)
+and jaccard-small (2,000 sets, 256 minhashes) are compared with the oracle in
+full: signatures, the candidate set, every pair's Algorithm 1 and Algorithm 2
+outcome, and both output sets.  The 1,000,000-node Chung-Lu workload is
+compared on samples the oracle computes one by one, plus properties that hold
+at any size."""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def run_pipeline(B, name, graph=True):
+    w = dict(bench.WORKLOADS[name])
+    objs, hashp = bench.make_inputs(w)
+    pipe = bench.Pipeline(B, torch, w, objs, hashp, torch.device("cuda", 0))
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            pipe.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            pipe.step()
+        # poison the outputs, then replay: the graph must recompute everything
+        pipe.status.fill_(77)
+        pipe.lstatus.fill_(77)
+        pipe.sig.fill_(0)
+        g.replay()
+    else:
+        pipe.step()
+    torch.cuda.synchronize()
+    assert B.blsh_status(pipe.ctx) == 0
+    return w, objs, hashp, pipe
+
+
+def check_outputs_against_oracle(B, w, objs, pipe, sig_o, pairs_gpu):
+    P = len(pairs_gpu)
+    p = O.Params(kind=w["kind"], t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    tab = O.tables(p)
+    want = O.verify(tab, pairs_gpu, sig_o)
+    assert want.bad == 0
+    assert np.array_equal(pipe.status[:P].cpu().numpy(), want.status)
+    assert np.array_equal(pipe.n_used[:P].cpu().numpy().view(np.uint16), want.n_used)
+    assert np.array_equal(pipe.m[:P].cpu().numpy().view(np.uint16), want.m)
+    est = pipe.est[:P].cpu().numpy()
+    assert np.array_equal(np.isnan(est), np.isnan(want.est))
+    ok = ~np.isnan(want.est)
+    assert np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
+    assert np.array_equal(pipe.hist.cpu().numpy(), O.stop_hist(want.n_used, p.k, p.levels).astype(np.int64))
+    lite = O.verify_lite(tab, pairs_gpu, sig_o, objs)
+    assert np.array_equal(pipe.lstatus[:P].cpu().numpy(), lite.status)
+    sim = pipe.sim[:P].cpu().numpy()
+    ok = ~np.isnan(lite.sim)
+    assert np.array_equal(np.isnan(sim), ~ok) and np.array_equal(sim[ok], lite.sim[ok])
+    n1, n2 = [int(x) for x in pipe.n_out.cpu()]
+    keep1 = O.compact(want.status, (1 << O.ACCEPT) | (1 << O.ACCEPT_AT_MAX))
+    keep2 = O.compact(lite.status, 1 << O.LITE_ACCEPT)
+    assert (n1, n2) == (len(keep1), len(keep2))
+    assert np.array_equal(pipe.out1[:n1].cpu().numpy(), keep1)
+    assert np.array_equal(pipe.out2[:n2].cpu().numpy(), keep2)
+    return want, lite
+
+
+@pytest.mark.parametrize("name", ["jaccard-small", "cosine-small"])
+def test_full_pipeline_matches_oracle(B, name):
+    w, objs, hashp, pipe = run_pipeline(B, name)
+    if w["kind"] == 1:
+        sig_o = O.srp_sparse(objs, hashp)
+    else:
+        sig_o = O.minhash(objs, hashp[0], hashp[1])
+    assert np.array_equal(u32(pipe.sig), sig_o)
+    pairs_o = O.lsh_candidates(sig_o, w["kind"], w["rows"], w["bands"])
+    P = pipe.P
+    pairs_gpu = u32(pipe.pairs[:P])
+    assert P == len(pairs_o)
+    key = lambda a: np.sort((a[:, 0].astype(np.uint64) << np.uint64(32)) | a[:, 1])
+    assert np.array_equal(key(pairs_gpu), key(pairs_o))
+    want, lite = check_outputs_against_oracle(B, w, objs, pipe, sig_o, pairs_gpu)
+    assert (want.status == O.PRUNED).any() and (want.status != O.PRUNED).any()
+    assert (lite.status == O.LITE_ACCEPT).sum() > 10
+
+
+def test_batching_workload_sampled(B):
+    """1,000,000 Chung-Lu adjacency sets, ~1e8 candidate pairs: sampled
+    oracle checks (signature rows, pairs' outcomes) and properties of the
+    candidate set."""
+    w, objs, hashp, pipe = run_pipeline(B, "batching", graph=False)
+    P = pipe.P
+    assert P > 1_000_000
+    rng = np.random.default_rng(0)
+    # signature rows: oracle minhash of 3,000 random rows
+    rows = np.sort(rng.choice(objs.n, 3000, replace=False))
+    sub = synth.CSR(np.concatenate([[0], np.cumsum(np.diff(objs.indptr)[rows])]).astype(np.int64),
+                    np.concatenate([objs.row(int(i)) for i in rows]).astype(np.uint32), None, objs.dim)
+    sig_sub = O.minhash(sub, hashp[0], hashp[1])
+    assert np.array_equal(u32(pipe.sig[torch.from_numpy(rows).cuda()]), sig_sub)
+    # sampled pairs: every outcome recomputed by the oracle from its own hashes
+    pairs = u32(pipe.pairs[:P])
+    q = np.sort(rng.choice(P, 20000, replace=False))
+    sp = pairs[q]
+    assert np.all(sp[:, 0] < sp[:, 1])
+    ids, inv = np.unique(sp.reshape(-1), return_inverse=True)
+    sub = synth.CSR(np.concatenate([[0], np.cumsum(np.diff(objs.indptr)[ids])]).astype(np.int64),
+                    np.concatenate([objs.row(int(i)) for i in ids]).astype(np.uint32), None, objs.dim)
+    sig_o = O.minhash(sub, hashp[0], hashp[1])
+    local = inv.reshape(-1, 2).astype(np.uint32)
+    # each sampled pair collides on a whole band of the oracle's hashes
+    r, bands = w["rows"], w["bands"]
+    band_eq = np.stack([(sig_o[local[:, 0], b * r:(b + 1) * r] == sig_o[local[:, 1], b * r:(b + 1) * r]).all(1)
+                        for b in range(bands)], 1)
+    assert band_eq.any(1).all()
+    p = O.Params(kind=0, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    tab = O.tables(p)
+    want = O.verify(tab, local, sig_o)
+    assert np.array_equal(pipe.status[:P].cpu().numpy()[q], want.status)
+    assert np.array_equal(pipe.m[:P].cpu().numpy().view(np.uint16)[q], want.m)
+    lite = O.verify_lite(tab, local, sig_o, sub)
+    assert np.array_equal(pipe.lstatus[:P].cpu().numpy()[q], lite.status)
+    sim = pipe.sim[:P].cpu().numpy()[q]
+    ok = ~np.isnan(lite.sim)
+    assert np.array_equal(sim[ok], lite.sim[ok])
+    # the candidate list has no duplicates
+    key = np.sort((pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1])
+    assert np.all(np.diff(key) > 0)
+    # stop histogram and status counts agree
+    st = pipe.status[:P].cpu().numpy()
+    assert int(pipe.hist.sum()) == P and not np.any(st == 77)

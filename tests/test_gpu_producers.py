@@ -71,6 +71,37 @@ def test_srp_sparse_exact_ties_and_zero_rows(B, ctx):
     assert c[3] == 64 and c[2] >= 64
 
 
+@pytest.mark.parametrize("n_docs", [3, 1100])
+def test_srp_sparse_recheck_queue(B, ctx, n_docs):
+    """Signs the FP32 bound cannot decide go through the recheck queue (and,
+    past its 2^20 entries, through the in-line recheck): rows whose dots are
+    exactly zero for every bit, or cancel to a few ulps."""
+    bits = 2048
+    rng = np.random.default_rng(n_docs)
+    R = rng.standard_normal((6, bits)).astype(np.float32)
+    R[1] = -R[0]
+    R[3] = -R[2] * np.float32(1.0000001)
+    rows, vals = [], []
+    for i in range(n_docs):
+        if i % 3 == 0:
+            rows.append([0, 1]); vals.append([0.5, 0.5])          # exactly 0 for every bit
+        elif i % 3 == 1:
+            rows.append([2, 3]); vals.append([0.25, 0.25])        # nearly cancelling
+        else:
+            rows.append([0, 4, 5]); vals.append([0.3, 0.6, -0.2])
+    csr = synth.CSR(np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64),
+                    np.concatenate(rows).astype(np.uint32), np.concatenate(vals).astype(np.float32), 6)
+    want = O.srp_sparse(csr, R)
+    ip, ix, val = csr_dev(csr)
+    sig = torch.zeros((n_docs, bits // 32), dtype=torch.int32, device=dev)
+    B.blsh_srp_sparse(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig)
+    rc, c = B.blsh_status(ctx, counters=True)
+    assert rc == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+    n_zero_rows = (n_docs + 2) // 3
+    assert c[3] >= n_zero_rows * bits and c[2] >= n_zero_rows * bits
+
+
 @pytest.mark.parametrize("d,bits", [(64, 128), (256, 1024)])
 def test_srp_dense_bit_exact(B, ctx, d, bits):
     X = synth.gaussian_mixture(n_points=3000, dim=d, n_centers=50, seed=d)

@@ -94,7 +94,9 @@ def assert_same(res, want, hist, p):
     assert np.array_equal(st, want.status)
     assert np.array_equal(nu, want.n_used)
     assert np.array_equal(m, want.m)
-    assert np.max(np.abs(est - want.est), initial=0) <= EST_TOL
+    assert np.array_equal(np.isnan(est), np.isnan(want.est))
+    ok = ~np.isnan(want.est)
+    assert np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= EST_TOL
     assert np.array_equal(h, O.stop_hist(want.n_used, p.k, p.levels).astype(np.int64))
 
 
@@ -198,3 +200,25 @@ def test_autotune_picks_a_valid_plan(B, ctx):
     assert best.mode in (0, 1) and best.group in (1, 4, 8, 16, 32)
     want = O.verify(O.tables(p), pairs, sig)
     assert_same(run_verify(B, ctx, tab, pairs, sig), want, None, p)   # now with the tuned plan
+
+
+def test_lite_form_every_cosine_plan(B, ctx):
+    """Algorithm 2's pruning pass runs in whichever plan the context holds."""
+    d = TABLE_PARAMS[4]
+    p = oracle_params(d)
+    sig, pairs = model_signatures(1, 2048, 4001, seed=12)
+    csr = synth.CSR(np.zeros(sig.shape[0] + 1, np.int64), np.zeros(0, np.uint32), np.zeros(0, np.float32), 1)
+    want = O.verify_lite(O.tables(p), pairs, sig, csr)
+    tab = gpu_tables(B, ctx, d)
+    dev = torch.device("cuda")
+    pt = torch.from_numpy(pairs.view(np.int32)).to(dev)
+    stt = torch.from_numpy(sig.view(np.int32)).to(dev)
+    ip = torch.zeros(sig.shape[0] + 1, dtype=torch.int64, device=dev)
+    ix = torch.zeros(1, dtype=torch.int32, device=dev)
+    val = torch.zeros(1, dtype=torch.float32, device=dev)
+    st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
+    sim = torch.zeros(len(pairs), dtype=torch.float64, device=dev)
+    B.blsh_autotune(ctx, tab, pt, stt, st)          # stores some plan for these tables
+    B.blsh_verify_lite(ctx, tab, pt, stt, ip, ix, val, st, sim)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy(), want.status)
