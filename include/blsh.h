@@ -186,14 +186,23 @@ BLSH_API int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *
 BLSH_API int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
                     int64_t N, const float *R, int64_t dim, int32_t bits, uint32_t *sig, void *stream);
 
-/* Sign random projections of dense rows X [N][d] (float, row-major) with R
- * [d][bits]: the projection runs in BF16 on the tensor cores with FP32
- * accumulation; every product with |p| < margin * ||x_i|| * ||r_j|| is
- * recomputed in FP32 (then FP64 if FP32 cannot decide), so with
- * margin >= 2^-7 * 1.02 every bit equals the sign of the FP64 sum.  d: a
- * multiple of 64; bits: a multiple of 128.  X, R 16-byte aligned. */
+/* Sign random projections of dense rows X [N][d] (float, row-major) with
+ * R [d][bits] (float, row-major), Section 4.2: bit j of row i =
+ * [ sum_c X[i][c] R[c][j] >= 0 ], each bit equal to the sign of the FP64 sum
+ * over c = 0..d-1 in order.
+ * With a workspace (blsh_srp_dense_workspace bytes, 256-byte aligned; nonzero
+ * when d is a multiple of 64 and bits a multiple of 256) the projection runs
+ * on the tensor cores: X and R are split into BF16 pairs hi + lo and
+ * hi*hi + hi*lo + lo*hi is accumulated in FP32; every product with
+ * |p| <= margin * |x_i| * |r_j| is recomputed in FP32 with a rigorous bound
+ * and, where that cannot decide it, in FP64.  margin is raised to the
+ * tensor-core error bound (about (2^-14 + 3 d 2^-22) * 1.25) when smaller;
+ * pass 0 for that bound.  Without a workspace (or for other shapes) the
+ * projection runs in FP32 on the CUDA cores with the same rechecks.
+ * X and R 16-byte aligned; bits a multiple of 32, at most 4096. */
+BLSH_API int blsh_srp_dense_workspace(int64_t N, int32_t d, int32_t bits, size_t *bytes);
 BLSH_API int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t d, const float *R, int32_t bits,
-                   float margin, uint32_t *sig, void *stream);
+                            float margin, uint32_t *sig, void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- candidate generation (Section 2, "Candidate generation via LSH") ---- */
 

@@ -68,7 +68,8 @@ def lib():
             "blsh_tables_download": ([p, p, p, p, p, p, p, p, p], C.c_int),
             "blsh_minhash": ([p, p, p, i64, i32, p, p, p, p], C.c_int),
             "blsh_srp_sparse": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
-            "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p], C.c_int),
+            "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
+            "blsh_srp_dense_workspace": ([i64, i32, i32, p], C.c_int),
             "blsh_lsh_candidates_workspace": ([i64, i32, i32, i32, p], C.c_int),
             "blsh_lsh_candidates": ([p, p, i64, i32, i32, i32, i32, p, i64, p, p, sz, p], C.c_int),
             "blsh_verify": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
@@ -251,11 +252,18 @@ def blsh_srp_sparse(ctx: Context, indptr, indices, values, R, sig, stream=None):
     _check(rc, ctx)
 
 
-def blsh_srp_dense(ctx: Context, X, R, sig, margin: float = 0.0079, stream=None):
+def blsh_srp_dense_workspace(N: int, d: int, bits: int) -> int:
+    n = C.c_size_t()
+    _check(lib().blsh_srp_dense_workspace(N, d, bits, C.byref(n)))
+    return n.value
+
+
+def blsh_srp_dense(ctx: Context, X, R, sig, margin: float = 0.0, workspace=None, stream=None):
     N, d = X.shape
     bits = R.shape[1]
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     rc = lib().blsh_srp_dense(ctx.handle, _dev(X, torch.float32), N, d, _dev(R, torch.float32), bits,
-                              float(margin), _dev(sig), _stream(stream))
+                              float(margin), _dev(sig), _dev(workspace), nbytes, _stream(stream))
     _check(rc, ctx)
 
 

@@ -393,7 +393,8 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
     if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");
     blsh_device_guard g(ctx->device);
     cudaStream_t s = blsh_stream(stream);
-    const long long cap = (long long)ctx->sm_count * 16;
+    // many small CTAs (rows have very different lengths): 32 per SM measured best
+    const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
     if (bits % 128 == 0 && blsh_aligned(R, 16)) {
         // float4 path: T4 = 32 * (largest divisor of groups/32 up to 8) threads,

@@ -102,15 +102,29 @@ def test_srp_sparse_recheck_queue(B, ctx, n_docs):
     assert c[3] >= n_zero_rows * bits and c[2] >= n_zero_rows * bits
 
 
-@pytest.mark.parametrize("d,bits", [(64, 128), (256, 1024)])
-def test_srp_dense_bit_exact(B, ctx, d, bits):
-    X = synth.gaussian_mixture(n_points=3000, dim=d, n_centers=50, seed=d)
+@pytest.mark.parametrize("n,d,bits,tc,margin", [
+    (3000, 64, 128, False, 0.0),      # CUDA-core path (bits not a multiple of 256)
+    (300, 64, 256, True, 0.0),        # tensor cores, one K stage, ragged last row tile
+    (3000, 256, 1024, True, 0.0),     # tensor cores, four K stages, four bit tiles
+    (3000, 256, 1024, True, 1e-3),    # the spec margin (wider than the error bound)
+    (1000, 128, 512, True, 0.0),
+])
+def test_srp_dense_bit_exact(B, ctx, n, d, bits, tc, margin):
+    X = synth.gaussian_mixture(n_points=n, dim=d, n_centers=50, seed=d)
+    X[5] = 0.0                                            # a zero row: every dot is exactly 0
     R = synth.gaussian_matrix(d, bits, seed=5)
     want = O.srp_dense(X, R)
-    sig = torch.zeros((X.shape[0], bits // 32), dtype=torch.int32, device=dev)
-    B.blsh_srp_dense(ctx, torch.from_numpy(X).to(dev), torch.from_numpy(R).to(dev), sig)
-    assert B.blsh_status(ctx) == 0
-    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+    sig = torch.zeros((n, bits // 32), dtype=torch.int32, device=dev)
+    nws = B.blsh_srp_dense_workspace(n, d, bits)
+    assert (nws > 0) == tc
+    ws = torch.zeros(max(nws, 1), dtype=torch.uint8, device=dev) if tc else None
+    B.blsh_srp_dense(ctx, torch.from_numpy(X).to(dev), torch.from_numpy(R).to(dev), sig, margin=margin, workspace=ws)
+    rc, c = B.blsh_status(ctx, counters=True)
+    assert rc == 0
+    got = sig.cpu().numpy().view(np.uint32)
+    bad = np.nonzero(got != want)
+    assert np.array_equal(got, want), (len(bad[0]), bad[0][:5], bad[1][:5])
+    assert c[3] >= bits                                   # the zero row went through the exact recheck
 
 
 def gpu_candidates(B, ctx, sig, kind, rows, bands, cap=None):
