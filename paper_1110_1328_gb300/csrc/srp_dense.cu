@@ -14,9 +14,10 @@
 //      lo*hi; four warps read the accumulators back (tcgen05.ld) and set a bit
 //      wherever |p| > margin * |x_i| * |r_j|, queueing every other sign.
 //   3. srp_dense_recheck_kernel: each queued sign is recomputed in FP32 with a
-//      rigorous error bound and, if that cannot decide it, as the FP64 sum
-//      over coordinates 0..d-1 in order -- the oracle's definition -- so
-//      every bit is exact whenever the margin bounds the tensor-core error.
+//      rigorous error bound, then in FP64 with one, and, if neither can decide
+//      it, as the FP64 sum over coordinates 0..d-1 in order -- the oracle's
+//      definition -- so every bit is exact whenever the margin bounds the
+//      tensor-core error.
 // The error of step 2 is at most 3.1 * 2^-16 sum|x_i r_ij| from the split
 // plus the FP32 accumulation of 3d products; the rigorous margin used when
 // the caller passes margin <= 0 is (2^-14 + 3 d 2^-22) * 1.25, applied to
@@ -88,9 +89,11 @@ __global__ void srp_dense_prep_x(const float *__restrict__ X, long long N, long 
 }
 
 // One thread per column j of R (bits): its d values become row j of the B
-// operand (B is stored N-major rows of K values).  rnorm: |r_j| rounded up.
+// operand (B is stored N-major rows of K values) and row j of Rt (FP32 R
+// transposed, read by the rechecks).  rnorm: |r_j| rounded up.
 __global__ void srp_dense_prep_r(const float *__restrict__ R, int d, int bits, unsigned char *__restrict__ Rh,
-                                 unsigned char *__restrict__ Rl, float *__restrict__ rnorm) {
+                                 unsigned char *__restrict__ Rl, float *__restrict__ rnorm,
+                                 float *__restrict__ Rt) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= bits) return;
     const int KT = d / BK;
@@ -101,6 +104,7 @@ __global__ void srp_dense_prep_r(const float *__restrict__ R, int d, int bits, u
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         ss = __fmaf_ru(v, v, ss);
+        Rt[(size_t)j * d + k] = v;   // column j of R, contiguous, for the rechecks
         const size_t tile = ((size_t)nt * KT + k / BK) * TILE_B;
         *reinterpret_cast<__nv_bfloat16 *>(Rh + tile + swz_offset(jj, k % BK)) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(Rl + tile + swz_offset(jj, k % BK)) = lo;
@@ -188,7 +192,8 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 // A sign the tensor-core margin cannot decide, when the recheck queue is
 // full: FP32 with its bound, else the FP64 sum in coordinate order.
 __device__ __noinline__ bool sign_in_line(const float *__restrict__ x, const float *__restrict__ R, int d, int bits,
-                                          int col) {
+                                          int col, blsh_dev_scratch *scratch) {
+    atomicAdd(&scratch->counters[2], 1ull);
     float acc = 0.0f, mag = 0.0f;
     for (int c = 0; c < d; ++c) {
         const float a = __ldg(x + c), b = __ldg(R + (size_t)c * bits + col);
@@ -199,6 +204,7 @@ __device__ __noinline__ bool sign_in_line(const float *__restrict__ x, const flo
     if (fabsf(acc) > bound) return acc >= 0.0f;
     double s = 0.0;
     for (int c = 0; c < d; ++c) s += (double)__ldg(x + c) * (double)__ldg(R + (size_t)c * bits + col);
+    if (s == 0.0) atomicAdd(&scratch->counters[3], 1ull);
     return s >= 0.0;
 }
 
@@ -297,10 +303,16 @@ __global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned cha
     if (!done_ok || s_fail) {
         if (threadIdx.x == 0) blsh_dev_error(scratch, BLSH_EDEVICE, -1, 0ull);
     } else {
-        // epilogue: thread t owns row mt*128 + t (TMEM lane t)
+        // epilogue: thread t owns row mt*128 + t (TMEM lane t).  Undecided
+        // signs collect in a small per-thread buffer and are appended to the
+        // recheck queue with one atomic per warp; past the buffer they are
+        // decided in line.
         const long long row = mt * BM + threadIdx.x;
         const float xn = row < N ? __ldg(xnorm + row) : 0.0f;
         const int words = bits >> 5;
+        constexpr int kBuf = 8;
+        unsigned short pend[kBuf];
+        int npend = 0;
         for (int c = 0; c < BN / 32; ++c) {
             float v[32];
             tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(c * 32), v);
@@ -312,13 +324,34 @@ __global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned cha
                     const float thr = margin * xn * __ldg(rnorm + col);
                     if (fabsf(v[i]) > thr) {
                         word |= (uint32_t)(v[i] >= 0.0f) << i;
+                    } else if (npend < kBuf) {
+                        pend[npend++] = (unsigned short)(c * 32 + i);
                     } else {
-                        const unsigned long long slot = atomicAdd(qcount, 1ull);
-                        if (slot < qcap) queue[slot] = make_uint2((uint32_t)row, (uint32_t)col);
-                        else word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, col) << i;
+                        word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch) << i;
                     }
                 }
                 sig[(size_t)row * words + nt * (BN / 32) + c] = word;
+            }
+        }
+        // warp-aggregated append: exclusive prefix of the counts, one atomic
+        const int lane = threadIdx.x & 31;
+        int incl = npend;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int wtotal = __shfl_sync(kFull, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0 && wtotal) base = atomicAdd(qcount, (unsigned long long)wtotal);
+        base = __shfl_sync(kFull, base, 0);
+        for (int p = 0; p < npend; ++p) {
+            const unsigned long long slot = base + (unsigned long long)(incl - npend + p);
+            const int col = nt * BN + pend[p];
+            if (slot < qcap) {
+                queue[slot] = make_uint2((uint32_t)row, (uint32_t)col);
+            } else if (sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch)) {
+                atomicOr(sig + (size_t)row * words + (col >> 5), 1u << (col & 31));
             }
         }
     }
@@ -328,68 +361,97 @@ __global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned cha
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
-// Queued signs: one warp per (row, bit).  FP32 partial sums per lane plus the
-// sum of |products| give a rigorous bound ((d + 32) u sum|p| for the
-// per-lane-then-tree order); a sign the bound cannot decide is recomputed as
-// the FP64 sum over coordinates 0..d-1 in order (products exact, added one by
-// one after shuffles), which is exactly the oracle's sum.
+// Queued signs: eight lanes per (row, bit), lane g of the group owning
+// coordinates [g d/8, (g+1) d/8).  Three stages, each with a rigorous bound:
+//   FP32 partial sums (any summation order errs by at most (d+8) u sum|p|);
+//   if undecided, FP64 partial sums of the exact products (error at most
+//   (d+8) 2^-53 sum|p|, so a sign it decides is the sign of the exact sum and
+//   of the oracle's sum, which errs by less);
+//   if still undecided (exact ties such as zero rows), the FP64 sum over
+//   coordinates 0..d-1 in order, lane g continuing lane g-1's running sum --
+//   exactly the oracle's sum.
 __global__ void __launch_bounds__(256) srp_dense_recheck_kernel(const uint2 *__restrict__ queue,
                                                                 unsigned long long qcap,
                                                                 const unsigned long long *qcount,
                                                                 const float *__restrict__ X,
-                                                                const float *__restrict__ R, int d, int bits,
+                                                                const float *__restrict__ Rt, int d, int bits,
                                                                 uint32_t *__restrict__ sig,
                                                                 blsh_dev_scratch *scratch) {
     const unsigned long long total = *qcount;
     const unsigned long long n = total < qcap ? total : qcap;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    unsigned long long done = 0, deep = 0, zeros = 0;
-    for (unsigned long long it = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n;
-         it += warps) {
-        const uint2 rj = queue[it];
-        const float *x = X + (size_t)rj.x * d;
-        float acc = 0.0f, mag = 0.0f;
-        for (int c = lane; c < d; c += 32) {
-            const float a = __ldg(x + c), b = __ldg(R + (size_t)c * bits + rj.y);
-            acc = __fmaf_rn(a, b, acc);
-            mag = __fmaf_rn(fabsf(a), fabsf(b), mag);
-        }
+    const int lane = threadIdx.x & 31, g = lane & 7;
+    const int per = d >> 3;   // coordinates per lane (d is a multiple of 64)
+    const unsigned long long groups = (unsigned long long)gridDim.x * (blockDim.x >> 3);
+    unsigned long long done = 0, zeros = 0;
+    const unsigned long long warp_first = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 3) & ~3ull;
+    for (unsigned long long it0 = warp_first; it0 < n; it0 += groups) {
+        const unsigned long long it = it0 + (unsigned long long)(lane >> 3);
+        const bool live = it < n;
+        uint2 rj = make_uint2(0u, 0u);
+        if (live) rj = queue[it];
+        const float *x = X + (size_t)rj.x * d + g * per;
+        const float *r = Rt + (size_t)rj.y * d + g * per;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        if (live)
+            for (int c = 0; c < per; c += 4) {
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(x + c));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(r + c));
+                a0 = __fmaf_rn(u.x, v.x, a0); a1 = __fmaf_rn(u.y, v.y, a1);
+                a2 = __fmaf_rn(u.z, v.z, a2); a3 = __fmaf_rn(u.w, v.w, a3);
+                m0 = __fmaf_rn(fabsf(u.x), fabsf(v.x), m0); m1 = __fmaf_rn(fabsf(u.y), fabsf(v.y), m1);
+                m2 = __fmaf_rn(fabsf(u.z), fabsf(v.z), m2); m3 = __fmaf_rn(fabsf(u.w), fabsf(v.w), m3);
+            }
+        float acc = (a0 + a1) + (a2 + a3), mag = (m0 + m1) + (m2 + m3);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 4; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(kFull, acc, o);
             mag += __shfl_xor_sync(kFull, mag, o);
         }
-        const float bound = 1.25f * (float)(d + 32) * 5.9604644775390625e-8f * mag + (float)(d + 32) * 1.4e-45f;
-        bool bit;
-        if (fabsf(acc) > bound) {
-            bit = acc >= 0.0f;
-        } else {
-            double s = 0.0;
-            for (int c0 = 0; c0 < d; c0 += 32) {
-                double p = 0.0;
-                if (c0 + lane < d) p = (double)__ldg(x + c0 + lane) * (double)__ldg(R + (size_t)(c0 + lane) * bits + rj.y);
-                const int cnt = min(32, d - c0);
-                for (int l = 0; l < cnt; ++l) s += __shfl_sync(kFull, p, l);
+        const float bound = 1.25f * (float)(d + 8) * 5.9604644775390625e-8f * mag + (float)(d + 8) * 1.4e-45f;
+        bool decided = !live || fabsf(acc) > bound;
+        bool bit = acc >= 0.0f;
+        if (__any_sync(kFull, !decided)) {
+            double p = 0.0, q = 0.0;
+            if (!decided)
+                for (int c = 0; c < per; ++c) {
+                    const double t = (double)__ldg(x + c) * (double)__ldg(r + c);
+                    p += t;
+                    q += fabs(t);
+                }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                p += __shfl_xor_sync(kFull, p, o);
+                q += __shfl_xor_sync(kFull, q, o);
             }
-            bit = s >= 0.0;
-            ++deep;
-            zeros += s == 0.0;
+            const double bound64 = 1.25 * (double)(d + 8) * 1.1102230246251565e-16 * q + (double)(d + 8) * 5e-324;
+            const bool decided64 = decided || fabs(p) > bound64;
+            if (!decided && decided64) bit = p >= 0.0;
+            if (__any_sync(kFull, !decided64)) {
+                double s = 0.0;
+                for (int step = 0; step < 8; ++step) {
+                    if (g == step && !decided64)
+                        for (int c = 0; c < per; ++c) s += (double)__ldg(x + c) * (double)__ldg(r + c);
+                    s = __shfl_sync(kFull, s, (lane & 24) | step);
+                }
+                if (!decided64) {
+                    bit = s >= 0.0;
+                    zeros += (g == 0 && s == 0.0);
+                }
+            }
         }
-        if (lane == 0) {
+        if (g == 0 && live) {
             if (bit) atomicOr(sig + (size_t)rj.x * (bits >> 5) + (rj.y >> 5), 1u << (rj.y & 31));
             ++done;
         }
     }
-    if (lane == 0 && done) atomicAdd(&scratch->counters[2], done);
-    if (lane == 0 && zeros) atomicAdd(&scratch->counters[3], zeros);
-    (void)deep;
+    if (done) atomicAdd(&scratch->counters[2], done);
+    if (zeros) atomicAdd(&scratch->counters[3], zeros);
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct DenseLayout {
-    size_t xh, xl, rh, rl, xn, rn, qc, q, total;
+    size_t xh, xl, rh, rl, rt, xn, rn, qc, q, total;
     unsigned long long qcap;
 };
 
@@ -409,6 +471,7 @@ DenseLayout dense_layout(long long N, int d, int bits) {
     L.xl = o; o = up256(o + (size_t)Npad * d * 2);
     L.rh = o; o = up256(o + (size_t)bits * d * 2);
     L.rl = o; o = up256(o + (size_t)bits * d * 2);
+    L.rt = o; o = up256(o + (size_t)bits * d * 4);
     L.xn = o; o = up256(o + (size_t)Npad * 4);
     L.rn = o; o = up256(o + (size_t)bits * 4);
     L.qc = o; o = up256(o + 8);
@@ -453,7 +516,8 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
     srp_dense_prep_x<<<(unsigned)((Npad + 7) / 8 < 65535ll * 8 ? (Npad + 7) / 8 : 65535ll * 8), 256, 0, s>>>(
         X, N, Npad, d, ws + L.xh, ws + L.xl, (float *)(ws + L.xn));
     BLSH_LAUNCHED(ctx, "srp dense prep (X)");
-    srp_dense_prep_r<<<(bits + 127) / 128, 128, 0, s>>>(R, d, bits, ws + L.rh, ws + L.rl, (float *)(ws + L.rn));
+    srp_dense_prep_r<<<(bits + 127) / 128, 128, 0, s>>>(R, d, bits, ws + L.rh, ws + L.rl, (float *)(ws + L.rn),
+                                                        (float *)(ws + L.rt));
     BLSH_LAUNCHED(ctx, "srp dense prep (R)");
     unsigned long long *qcount = (unsigned long long *)(ws + L.qc);
     uint2 *queue = (uint2 *)(ws + L.q);
@@ -470,8 +534,8 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
                                                  (float *)(ws + L.rn), N, d, bits, m, sig, queue, L.qcap, qcount,
                                                  X, R, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp dense tensor-core kernel");
-    srp_dense_recheck_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(queue, L.qcap, qcount, X, R, d, bits, sig,
-                                                                 ctx->scratch);
+    srp_dense_recheck_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(queue, L.qcap, qcount, X, (float *)(ws + L.rt), d,
+                                                                 bits, sig, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp dense recheck kernel");
     return BLSH_OK;
 }
