@@ -56,6 +56,7 @@ struct BandArgs {
     unsigned long long *bk;   // Jaccard: [N][bands] band hashes
     uint32_t *ck;             // cosine: [N][ck_words] band keys packed in lanes of ck_lane bytes
     int ck_lane, ck_words;
+    int vec16;                // rows of sig start 16-byte aligned
 };
 
 // Lane width (bytes) of packed cosine band keys, and 32-bit words per row
@@ -166,9 +167,29 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(const unsig
 __device__ __forceinline__ bool same_band(const BandArgs &A, uint32_t x, uint32_t y, int b) {
     const uint32_t *rx = A.sig + (size_t)x * A.W, *ry = A.sig + (size_t)y * A.W;
     if (A.kind == BLSH_COSINE) return bit_field(rx, b * A.rows, A.rows) == bit_field(ry, b * A.rows, A.rows);
+    const int start = b * A.rows;
+    if (A.vec16 && (A.rows & 3) == 0 && (start & 3) == 0) {   // whole 16-byte groups
+        const uint4 *vx = reinterpret_cast<const uint4 *>(rx + start), *vy = reinterpret_cast<const uint4 *>(ry + start);
+        for (int r = 0; r < (A.rows >> 2); ++r) {
+            const uint4 u = __ldg(vx + r), v = __ldg(vy + r);
+            if (u.x != v.x || u.y != v.y || u.z != v.z || u.w != v.w) return false;
+        }
+        return true;
+    }
     for (int r = 0; r < A.rows; ++r)
-        if (__ldg(rx + b * A.rows + r) != __ldg(ry + b * A.rows + r)) return false;
+        if (__ldg(rx + start + r) != __ldg(ry + start + r)) return false;
     return true;
+}
+
+// Jaccard: the pair (x, y) met in band b is emitted iff b is the first band
+// whose keys agree in full.  The 64-bit band hashes find the candidate bands
+// (equal keys have equal hashes); a hash match is confirmed on the keys
+// themselves before it decides anything.
+__device__ __forceinline__ bool emit_here_jaccard(const BandArgs &A, uint32_t x, uint32_t y, int b) {
+    const unsigned long long *bx = A.bk + (size_t)x * A.bands, *by = A.bk + (size_t)y * A.bands;
+    for (int c = 0; c <= b; ++c)
+        if (__ldg(bx + c) == __ldg(by + c) && same_band(A, x, y, c)) return c == b;
+    return false;   // band b's hashes or keys differ: only a truncated-hash collision put them together
 }
 
 // Nonzero iff some lane of v (lanes of 1, 2 or 4 bytes) is zero.  The
@@ -199,11 +220,7 @@ __device__ __forceinline__ bool earlier_band_cos(const BandArgs &A, uint32_t x, 
 // and no earlier band has them agree.
 __device__ __forceinline__ bool emit_here(const BandArgs &A, uint32_t x, uint32_t y, int b) {
     if (A.kind == BLSH_COSINE) return !earlier_band_cos(A, x, y, b);
-    if (!same_band(A, x, y, b)) return false;
-    const unsigned long long *bx = A.bk + (size_t)x * A.bands, *by = A.bk + (size_t)y * A.bands;
-    for (int c = 0; c < b; ++c)
-        if (__ldg(bx + c) == __ldg(by + c) && same_band(A, x, y, c)) return false;
-    return true;
+    return emit_here_jaccard(A, x, y, b);
 }
 
 // Cosine rows of packed band keys are at most kCkRegWords words long when
@@ -240,43 +257,90 @@ __device__ __forceinline__ bool earlier_band_cos_reg(const BandArgs &A, const ui
 template <bool WRITE>
 __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const uint32_t *vals, long long n,
                             unsigned long long *counts, uint32_t *pairs, long long cap) {
+    // Lanes of a warp take 32 consecutive sorted positions.  A position whose
+    // bucket continues for at most 32 more entries walks them alone; longer
+    // ones are walked afterwards by the whole warp, 32 partners per step, so
+    // a bucket of thousands of objects is not a serial chain of loads.
     const bool reg_path = A.kind == BLSH_COSINE && A.ck_words <= kCkRegWords;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long key = keys[p];
-        const uint32_t x = vals[p];
-        const int b = A.kind == BLSH_COSINE ? (int)(key >> A.rows)
-                                             : (A.band_bits == 0 ? 0 : (int)(key >> A.key_shift));
-        unsigned long long c = 0, out = WRITE ? counts[p] : 0;
-        if (reg_path) {
-            uint4 kx[kCkRegWords / 4];
-            const uint4 *kxp = reinterpret_cast<const uint4 *>(A.ck + (size_t)x * A.ck_words);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long pb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); pb < n; pb += stride) {
+        const long long p = pb + lane;
+        const bool live = p < n;
+        unsigned long long key = 0;
+        uint32_t x = 0;
+        int b = 0;
+        bool longrun = false;
+        unsigned long long c = 0, out = 0;
+        if (live) {
+            key = keys[p];
+            x = vals[p];
+            b = A.kind == BLSH_COSINE ? (int)(key >> A.rows) : (A.band_bits == 0 ? 0 : (int)(key >> A.key_shift));
+            out = WRITE ? counts[p] : 0;
+            longrun = p + 33 < n && keys[p + 33] == key;
+        }
+        if (live && !longrun) {
+            if (reg_path) {
+                uint4 kx[kCkRegWords / 4];
+                const uint4 *kxp = reinterpret_cast<const uint4 *>(A.ck + (size_t)x * A.ck_words);
 #pragma unroll
-            for (int w4 = 0; w4 < kCkRegWords / 4; ++w4)
-                kx[w4] = 4 * w4 < A.ck_words ? __ldg(kxp + w4) : make_uint4(0u, 0u, 0u, 0u);
-            for (long long q = p + 1; q < n && keys[q] == key; ++q) {
-                const uint32_t y = vals[q];
-                if (!earlier_band_cos_reg(A, kx, y, b)) {
-                    if (WRITE) {
-                        const long long o = (long long)(out + c);
-                        if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+                for (int w4 = 0; w4 < kCkRegWords / 4; ++w4)
+                    kx[w4] = 4 * w4 < A.ck_words ? __ldg(kxp + w4) : make_uint4(0u, 0u, 0u, 0u);
+                for (long long q = p + 1; q < n && keys[q] == key; ++q) {
+                    const uint32_t y = vals[q];
+                    if (!earlier_band_cos_reg(A, kx, y, b)) {
+                        if (WRITE) {
+                            const long long o = (long long)(out + c);
+                            if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+                        }
+                        ++c;
                     }
-                    ++c;
                 }
-            }
-        } else {
-            for (long long q = p + 1; q < n && keys[q] == key; ++q) {
-                const uint32_t y = vals[q];
-                if (emit_here(A, x, y, b)) {
-                    if (WRITE) {
-                        const long long o = (long long)(out + c);
-                        if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+            } else {
+                for (long long q = p + 1; q < n && keys[q] == key; ++q) {
+                    const uint32_t y = vals[q];
+                    if (emit_here(A, x, y, b)) {
+                        if (WRITE) {
+                            const long long o = (long long)(out + c);
+                            if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+                        }
+                        ++c;
                     }
-                    ++c;
                 }
             }
         }
-        if (!WRITE) counts[p] = c;
+        // the warp walks the long buckets of its lanes, one position at a time
+        unsigned pending = __ballot_sync(kFull, longrun);
+        while (pending) {
+            const int l = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const long long pl = __shfl_sync(kFull, p, l);
+            const unsigned long long kl = __shfl_sync(kFull, key, l);
+            const uint32_t xl = __shfl_sync(kFull, x, l);
+            const int bl = __shfl_sync(kFull, b, l);
+            const unsigned long long ol = __shfl_sync(kFull, out, l);
+            unsigned long long cl = 0;
+            for (long long q0 = pl + 1;; q0 += 32) {
+                const long long q = q0 + lane;
+                const bool in = q < n && keys[q] == kl;
+                bool ok = false;
+                uint32_t y = 0;
+                if (in) {
+                    y = vals[q];
+                    ok = emit_here(A, xl, y, bl);
+                }
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (WRITE && ok) {
+                    const long long o = (long long)(ol + cl + __popc(m & lt));
+                    if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(xl, y);
+                }
+                cl += __popc(m);
+                if (__ballot_sync(kFull, in) != kFull) break;   // the bucket ended in this step
+            }
+            if (lane == l) c = cl;
+        }
+        if (!WRITE && live) counts[p] = c;
     }
 }
 
@@ -371,6 +435,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     A.bk = kind == BLSH_JACCARD ? (unsigned long long *)(ws + L.bk) : nullptr;
     A.ck = kind == BLSH_COSINE ? (uint32_t *)(ws + L.ck) : nullptr;
     A.ck_lane = cos_lane_bytes(rows);
+    A.vec16 = blsh_aligned(sig, 16) && sig_words % 4 == 0;
     A.ck_words = cos_row_words(rows, bands);
     if (kind == BLSH_COSINE)   // pad lanes past the last band stay zero
         BLSH_CUDA(ctx, cudaMemsetAsync(A.ck, 0, (size_t)N * A.ck_words * 4, s));

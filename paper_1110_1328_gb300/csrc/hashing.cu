@@ -21,7 +21,10 @@ __device__ __forceinline__ uint32_t mod_mersenne31(uint32_t a, uint32_t b, uint3
 // One warp per set; lane l owns hashes l, l+32, ..., l+32(HPL-1) of the
 // current tile of 32*HPL hashes and keeps their running minima in
 // registers.  The set's elements are read 32 at a time (coalesced) and
-// broadcast with shuffles.
+// broadcast with shuffles.  Sets longer than kBigSet are left to
+// minhash_big_kernel.
+constexpr long long kBigSet = 2048;
+
 template <int HPL>
 __global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict__ indptr,
                                                       const uint32_t *__restrict__ indices, long long N,
@@ -31,6 +34,7 @@ __global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict_
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
         const long long s = __ldg(indptr + i), e = __ldg(indptr + i + 1);
+        if (e - s > kBigSet) continue;
         for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
             uint32_t a[HPL], b[HPL], mn[HPL];
 #pragma unroll
@@ -50,6 +54,49 @@ __global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict_
             }
 #pragma unroll
             for (int u = 0; u < HPL; ++u) sig[(size_t)i * n_hashes + t0 + 32 * u + lane] = mn[u];
+        }
+    }
+}
+
+// Sets longer than kBigSet: one CTA of 32 warps per set (grid-stride over
+// the sets, skipping the short ones); warp w takes every 32nd block of 32
+// elements and the warps' minima meet in shared memory (atomicMin; the
+// minimum does not depend on the order).
+template <int HPL>
+__global__ void __launch_bounds__(1024) minhash_big_kernel(const int64_t *__restrict__ indptr,
+                                                           const uint32_t *__restrict__ indices, long long N,
+                                                           int n_hashes, const uint32_t *__restrict__ A,
+                                                           const uint32_t *__restrict__ B,
+                                                           uint32_t *__restrict__ sig) {
+    __shared__ uint32_t smin[32 * HPL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (long long i = blockIdx.x; i < N; i += gridDim.x) {
+        const long long s = __ldg(indptr + i), e = __ldg(indptr + i + 1);
+        if (e - s <= kBigSet) continue;
+        for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x) smin[k] = 0xffffffffu;
+            __syncthreads();
+            uint32_t a[HPL], b[HPL], mn[HPL];
+#pragma unroll
+            for (int u = 0; u < HPL; ++u) {
+                a[u] = __ldg(A + t0 + 32 * u + lane);
+                b[u] = __ldg(B + t0 + 32 * u + lane);
+                mn[u] = 0xffffffffu;
+            }
+            for (long long e0 = s + 32ll * warp; e0 < e; e0 += 32ll * nwarps) {
+                const uint32_t mine = e0 + lane < e ? __ldg(indices + e0 + lane) : 0u;
+                const int cnt = (int)min(32ll, e - e0);
+                for (int l = 0; l < cnt; ++l) {
+                    const uint32_t x = __shfl_sync(kFull, mine, l);
+#pragma unroll
+                    for (int u = 0; u < HPL; ++u) mn[u] = min(mn[u], mod_mersenne31(a[u], b[u], x));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < HPL; ++u) atomicMin(&smin[32 * u + lane], mn[u]);
+            __syncthreads();
+            for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x) sig[(size_t)i * n_hashes + t0 + k] = smin[k];
         }
     }
 }
@@ -363,14 +410,21 @@ extern "C" int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t
     const long long cap = (long long)ctx->sm_count * 8;
     const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
     const int words = n_hashes / 32;
-    if (words % 8 == 0)
+    const unsigned big_grid = (unsigned)(N < (long long)ctx->sm_count * 2 ? N : (long long)ctx->sm_count * 2);
+    if (words % 8 == 0) {
         minhash_kernel<8><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-    else if (words % 4 == 0)
+        minhash_big_kernel<8><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    } else if (words % 4 == 0) {
         minhash_kernel<4><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-    else if (words % 2 == 0)
+        minhash_big_kernel<4><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    } else if (words % 2 == 0) {
         minhash_kernel<2><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-    else
+        minhash_big_kernel<2><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    } else {
         minhash_kernel<1><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+        minhash_big_kernel<1><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+    }
+    ctx->launches.fetch_add(1, std::memory_order_relaxed);   // the second of the two launches
     BLSH_LAUNCHED(ctx, "minhash kernel");
     return BLSH_OK;
 }
