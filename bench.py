@@ -260,6 +260,20 @@ def verify_bytes(kind, k, n_used, P):
     return P * (8 + 9) + int(chunks.sum()) * per_chunk
 
 
+def combine_ranks(dist, step_ms: float, pairs: int, e2e_ms: float, device):
+    """Whole-job numbers of a replicated run: the slowest rank's step and
+    end-to-end times (max over ranks) and the pairs of all ranks (sum).
+    Each rank verifies its own batch, so the units add up (weak scaling)."""
+    if dist is None:
+        return step_ms, pairs, e2e_ms
+    import torch
+    t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), int(p[0].item()), float(t[1].item())
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -348,16 +362,6 @@ def run_ours(args, w):
         raise RuntimeError(f"timed steps reported {rc}")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     my_ms = float(np.mean(step_ms))
-    P_total = pipe.P
-    ms = my_ms
-    if dist:
-        tt = torch.tensor([my_ms, float(pipe.P)], dtype=torch.float64, device=device)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        ms = float(mx[0].item())
-        P_total = int(tt[1].item())
-    value = P_total / (ms / 1e3)
 
     # ---- per-stage device times (eager, events around each library call) ----
     stage_ms = {s: [] for s in pipe.STAGES}
@@ -402,11 +406,9 @@ def run_ours(args, w):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         h2d, d2h = nb_in, 16 + 8 * (n1 + n2)
     e2e_step = float(np.mean(e2e_ms))
-    e2e_val = pipe.P / (e2e_step / 1e3)
-    if dist:
-        tt = torch.tensor([e2e_step], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_val = P_total / (float(tt.item()) / 1e3)
+    ms, P_total, e2e_max = combine_ranks(dist, my_ms, pipe.P, e2e_step, device)
+    value = P_total / (ms / 1e3)
+    e2e_val = P_total / (e2e_max / 1e3)
 
     # ---- outputs of the last step, for the record ----
     st = pipe.status[: pipe.P].cpu().numpy()
