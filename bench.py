@@ -52,6 +52,9 @@ WORKLOADS = {
                            n_max=2048, k=32, h=128, seed=2,
                            text="cosine-small shape at 6,000 vectors over dim 30,000 (R = 245 MB > L2), for "
                                 "ncu captures"),
+    "verify-large": dict(kind=1, n=5_000_000, bits=2048, pairs=200_000_000, t=0.7, n_max=2048, k=32, h=128,
+                         seed=9, text="verification only: 5,000,000 random 2,048-bit signatures (1.3 GB) and "
+                                      "200,000,000 uniform random candidate pairs (HBM-resident, no reuse)"),
     "jaccard-small": dict(kind=0, n=2000, vocab=10000, n_hashes=256, rows=8, bands=32, t=0.7, n_max=256, k=32,
                           h=64, seed=1,
                           text="jaccard, BayesLSH + Lite: N=2,000 sets over vocab 10,000, lognormal sizes "
@@ -491,6 +494,62 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_verify_large(args, w):
+    """Algorithm 1 alone over uniform random pairs of random signatures: every
+    signature gather misses L2, so this measures verification at HBM scale."""
+    import torch
+
+    import paper_1110_1328_gb300 as B
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(w["seed"])
+    N, W, P = w["n"], w["bits"] // 32, w["pairs"]
+    sig = torch.randint(-2 ** 31, 2 ** 31 - 1, (N, W), dtype=torch.int32, device=dev, generator=g)
+    x = torch.randint(0, N, (P,), dtype=torch.int64, device=dev, generator=g)
+    y = torch.randint(0, N, (P,), dtype=torch.int64, device=dev, generator=g)
+    pairs = torch.stack([torch.minimum(x, y), torch.maximum(x, y)], 1).to(torch.int32)
+    del x, y
+    tab = B.blsh_tables_build(ctx, B.make_params(kind=1, t=w["t"], n_max=w["n_max"], k=w["k"], h=w["h"]))
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    nu = torch.zeros(P, dtype=torch.int16, device=dev)
+    m = torch.zeros(P, dtype=torch.int16, device=dev)
+    est = torch.zeros(P, dtype=torch.float32, device=dev)
+    hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    plan = B.blsh_autotune(ctx, tab, pairs[:20_000_000], sig, st[:20_000_000])
+    for _ in range(args.warmup):
+        B.blsh_verify(ctx, tab, pairs, sig, st, nu, m, est, hist)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.blsh_verify(ctx, tab, pairs, sig, st, nu, m, est, hist)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    assert B.blsh_status(ctx) == 0
+    ms = float(np.mean(ts))
+    h = hist.cpu().numpy()
+    chunks = float((h * np.arange(1, len(h) + 1)).sum())
+    peak, peak_kind = load_peaks()
+    alg = P * (8 + 9) + chunks * (w["k"] // 4)
+    sector = P * (8 + 9) + P * 2 * 32
+    print(json.dumps({"metric": METRIC, "value": round(P / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+                      "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": args.workload + ": " + w["text"], "plan": plan.as_dict(),
+                                 "l2": "flushed between timed steps (256 MB write)"},
+                      "verify_hbm": {"algorithmic_bytes": int(alg), "achieved": round(alg / (ms / 1e3) / 1e9, 1),
+                                     "sector_floor_bytes": int(sector),
+                                     "sector_floor_GBps": round(sector / (ms / 1e3) / 1e9, 1),
+                                     "peak": peak, "peak_source": peak_kind, "unit": "GB/s"},
+                      "stop_hist_first4": [int(v) for v in h[:4]], "mean_chunks": round(chunks / P, 4)}),
+          flush=True)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timings (the cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
@@ -536,6 +595,10 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if "pairs" in w:
+        print(json.dumps({"impl": "reference", "unavailable": "verify-large is a GPU measurement workload; "
+                                                               "the oracle arm runs on the pipeline workloads"}))
+        return
     import oracle as O
     O.build()
     objs, hashp = make_inputs(w, 0)
@@ -578,6 +641,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.workload == "verify-large":
+        run_verify_large(args, w)
     else:
         run_ours(args, w)
 
