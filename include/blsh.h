@@ -273,6 +273,31 @@ BLSH_API int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t
                   int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m, float *est,
                   blsh_plan *best, void *stream);
 
+/* ---- the classical estimator and the learned prior ------------------------- */
+
+/* The maximum-likelihood estimate of Section 3 over a fixed number of hashes
+ * (the "LSH Approx" comparison mode of Section 5.1): for each pair,
+ * m = agreements among hashes 0 .. n_hashes-1, est = m / n_hashes (Jaccard)
+ * or cos(pi (1 - m / n_hashes)) (cosine), keep = [est > t] (Section 2), decided
+ * as m > m_star with m_star the largest m whose estimate is <= t (FP64, on
+ * the host).  m uint16 [P], est float [P], keep uint8 [P] (BLSH_BAD_PAIR for
+ * a pair naming an object >= N); any may be NULL.  P_dev as in blsh_verify. */
+BLSH_API int blsh_estimate_mle(blsh_ctx *ctx, int32_t kind, int32_t n_hashes, double t, const uint32_t *pairs,
+                               int64_t P, const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                               uint16_t *m, float *est, uint8_t *keep, void *stream);
+
+/* The learned prior of Section 4.1: exact Jaccard similarities of r sampled
+ * candidate pairs (sims, device double [r]), their mean s and population
+ * variance v (divisor r), and the method-of-moments Beta:
+ *   alpha = s (s (1 - s) / v - 1),  beta = (1 - s) (s (1 - s) / v - 1).
+ * out_device (device double [5]) = {s, v, alpha, beta, fallback}; when v is 0
+ * or v >= s (1 - s) the moments admit no Beta and the uniform Beta(1,1) is
+ * returned with fallback = 1.  If out_host (host double [5]) is not NULL the
+ * call synchronises `stream` and copies the result there. */
+BLSH_API int blsh_fit_beta_prior(blsh_ctx *ctx, const uint32_t *pairs, int64_t r, const int64_t *indptr,
+                                 const uint32_t *indices, int64_t N, double *sims, double *out_device,
+                                 double *out_host, void *stream);
+
 /* ---- output (the set O of Algorithms 1 and 2) ----------------------------- */
 
 /* Stable compaction: out_idx int64 [cap] receives, in increasing order, the

@@ -61,6 +61,8 @@ def lib():
         L.orc_lsh_candidates.argtypes = [p, i64, i, i, i, i, p, i64]; L.orc_lsh_candidates.restype = i64
         L.orc_compact.argtypes = [p, i64, C.c_uint32, p]; L.orc_compact.restype = i64
         L.orc_stop_hist.argtypes = [p, i64, i, i, p]; L.orc_stop_hist.restype = None
+        L.orc_estimate_mle.argtypes = [i, i, d, p, i64, p, i, p, p, p]; L.orc_estimate_mle.restype = None
+        L.orc_fit_beta_prior.argtypes = [p, i64, p]; L.orc_fit_beta_prior.restype = None
         _lib = L
     return _lib
 
@@ -277,3 +279,23 @@ def stop_hist(n_used: np.ndarray, k: int, levels: int) -> np.ndarray:
     h = np.zeros(levels, np.uint64)
     lib().orc_stop_hist(_ptr(n_used), len(n_used), k, levels, _ptr(h))
     return h
+
+
+def estimate_mle(kind: int, n: int, t: float, pairs: np.ndarray, sig: np.ndarray):
+    """Section 3: m of the first n hashes agree, estimate m/n (Jaccard) or
+    cos(pi (1 - m/n)) (cosine); Section 2: keep iff the estimate exceeds t."""
+    pairs = _c(pairs, np.uint32).reshape(-1, 2)
+    sig = _c(sig, np.uint32)
+    P = len(pairs)
+    m = np.zeros(P, np.uint16); est = np.zeros(P, np.float64); keep = np.zeros(P, np.uint8)
+    lib().orc_estimate_mle(kind, n, t, _ptr(pairs), P, _ptr(sig), sig.shape[1], _ptr(m), _ptr(est), _ptr(keep))
+    return m, est, keep
+
+
+def fit_beta_prior(sims: np.ndarray):
+    """Section 4.1: method-of-moments Beta(alpha, beta) from sampled
+    similarities; returns (mean, var, alpha, beta, fallback)."""
+    sims = _c(sims, np.float64)
+    out = np.zeros(5, np.float64)
+    lib().orc_fit_beta_prior(_ptr(sims), len(sims), _ptr(out))
+    return tuple(out.tolist())

@@ -544,3 +544,41 @@ void orc_stop_hist(const uint16_t *n_used, int64_t P, int k, int L, uint64_t *hi
         if (j >= 0 && j < L) hist[j]++;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Section 3: the maximum-likelihood estimate over the first n hashes, and the */
+/* Section 2 output rule (keep iff the estimate exceeds t).                    */
+/* ------------------------------------------------------------------------- */
+void orc_estimate_mle(int kind, int n, double t, const uint32_t *pairs, int64_t P, const uint32_t *sig,
+                      int sig_words, uint16_t *m_out, double *est, uint8_t *keep)
+{
+    for (int64_t q = 0; q < P; q++) {
+        const uint32_t *sx = sig + (size_t)pairs[2 * q] * sig_words, *sy = sig + (size_t)pairs[2 * q + 1] * sig_words;
+        int m = orc_chunk_matches(kind, sx, sy, 0, n);
+        double r = (double)m / (double)n;
+        double e = kind == ORC_JACCARD ? r : cos(ORC_PI * (1.0 - r));
+        m_out[q] = (uint16_t)m;
+        est[q] = e;
+        keep[q] = e > t;
+    }
+}
+
+/* Section 4.1 "Choice of prior": method-of-moments Beta from r similarities.
+ * out = {mean, variance (divisor r), alpha, beta, fallback}; no Beta fits
+ * when the variance is 0 or at least mean (1 - mean): then Beta(1,1). */
+void orc_fit_beta_prior(const double *sims, int64_t r, double *out)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < r; i++) s += sims[i];
+    double mean = s / (double)r;
+    double v = 0.0;
+    for (int64_t i = 0; i < r; i++) v += (sims[i] - mean) * (sims[i] - mean);
+    double var = v / (double)r;
+    out[0] = mean; out[1] = var; out[2] = 1.0; out[3] = 1.0; out[4] = 1.0;
+    if (var > 0.0 && var < mean * (1.0 - mean)) {
+        double k = mean * (1.0 - mean) / var - 1.0;
+        out[2] = mean * k;
+        out[3] = (1.0 - mean) * k;
+        out[4] = 0.0;
+    }
+}

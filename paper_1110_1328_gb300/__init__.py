@@ -78,6 +78,8 @@ def lib():
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
             "blsh_compact_noalloc": ([p, i64, p, u32, p, i64, p, p], C.c_int),
+            "blsh_estimate_mle": ([p, i32, i32, C.c_double, p, i64, p, p, i64, i32, p, p, p, p], C.c_int),
+            "blsh_fit_beta_prior": ([p, p, i64, p, p, i64, p, p, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -343,3 +345,29 @@ def blsh_compact_noalloc(status, keep_mask: int, out_idx, n_out, P_dev=None, str
                                     _stream(stream))
     if rc != OK:
         raise BlshError(rc, lib().blsh_strerror(rc).decode())
+
+
+def blsh_estimate_mle(ctx: Context, kind: int, n_hashes: int, t: float, pairs, sig, m=None, est=None, keep=None,
+                      P_dev=None, stream=None):
+    """The fixed-n maximum-likelihood estimate (Section 3) and [est > t]."""
+    P = pairs.shape[0]
+    N, W = sig.shape
+    rc = lib().blsh_estimate_mle(ctx.handle, kind, n_hashes, float(t), _dev(pairs), P, _dev(P_dev, torch.int64),
+                                 _dev(sig), N, W, _dev(m), _dev(est, torch.float32), _dev(keep, torch.uint8),
+                                 _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_fit_beta_prior(ctx: Context, pairs, indptr, indices, sims=None, stream=None):
+    """Method-of-moments Beta prior from exact similarities of sampled pairs
+    (Section 4.1).  Returns (mean, var, alpha, beta, fallback) and the sims."""
+    r = pairs.shape[0]
+    N = indptr.numel() - 1
+    if sims is None:
+        sims = torch.empty(r, dtype=torch.float64, device=pairs.device)
+    out_dev = torch.empty(5, dtype=torch.float64, device=pairs.device)
+    out = (C.c_double * 5)()
+    rc = lib().blsh_fit_beta_prior(ctx.handle, _dev(pairs), r, _dev(indptr, torch.int64), _dev(indices), N,
+                                   _dev(sims, torch.float64), _dev(out_dev), out, _stream(stream))
+    _check(rc, ctx)
+    return tuple(out), sims
