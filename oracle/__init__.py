@@ -63,6 +63,9 @@ def lib():
         L.orc_stop_hist.argtypes = [p, i64, i, i, p]; L.orc_stop_hist.restype = None
         L.orc_estimate_mle.argtypes = [i, i, d, p, i64, p, i, p, p, p]; L.orc_estimate_mle.restype = None
         L.orc_fit_beta_prior.argtypes = [p, i64, p]; L.orc_fit_beta_prior.restype = None
+        L.orc_quantize_gaussian.argtypes = [p, i64, p]; L.orc_quantize_gaussian.restype = i64
+        L.orc_dequantize_gaussian.argtypes = [C.c_uint16]; L.orc_dequantize_gaussian.restype = d
+        L.orc_srp_sparse_q16.argtypes = [p, p, p, i64, p, i, p]; L.orc_srp_sparse_q16.restype = None
         _lib = L
     return _lib
 
@@ -231,6 +234,36 @@ def srp_sparse(csr, R: np.ndarray) -> np.ndarray:
     N = len(indptr) - 1
     sig = np.zeros((N, bits // 32), np.uint32)
     lib().orc_srp_sparse(_ptr(indptr), _ptr(idx), _ptr(val), N, _ptr(R), bits, _ptr(sig))
+    return sig
+
+
+def quantize_gaussian(x: np.ndarray):
+    """Two-byte storage of Gaussian samples (Section 4.3): q = floor((x + 8)
+    2^16 / 16), clamped to [0, 65535].  Returns (q, number clamped)."""
+    x = _c(x, np.float32)
+    q = np.zeros(x.shape, np.uint16)
+    n = lib().orc_quantize_gaussian(_ptr(x), x.size, _ptr(q))
+    return q, int(n)
+
+
+def dequantize_gaussian(q: np.ndarray) -> np.ndarray:
+    """q * 16 / 2^16 - 8 (Section 4.3)."""
+    f = lib().orc_dequantize_gaussian
+    return np.array([f(int(v)) for v in np.asarray(q).ravel()], np.float64).reshape(np.shape(q))
+
+
+def srp_sparse_q16(csr, Rq: np.ndarray) -> np.ndarray:
+    """Sparse SRP with R stored in two bytes per entry (Section 4.3): bit j of
+    row i = [sum of x_e r(e, j) >= 0], r decoded from Rq [dim][bits] uint16,
+    FP64 sums in row order."""
+    Rq = _c(Rq, np.uint16)
+    bits = Rq.shape[1]
+    if bits % 32:
+        raise ValueError("bits must be a multiple of 32")
+    indptr = _c(csr.indptr, np.int64); idx = _c(csr.indices, np.uint32); val = _c(csr.values, np.float32)
+    N = len(indptr) - 1
+    sig = np.zeros((N, bits // 32), np.uint32)
+    lib().orc_srp_sparse_q16(_ptr(indptr), _ptr(idx), _ptr(val), N, _ptr(Rq), bits, _ptr(sig))
     return sig
 
 

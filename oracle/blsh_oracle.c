@@ -417,6 +417,49 @@ void orc_srp_sparse(const int64_t *indptr, const uint32_t *indices, const float 
     }
 }
 
+/* Section 4.3, "Cheaper storage of hash functions": a standard Gaussian
+ * sample x, assumed to lie in (-8, 8), is stored in two bytes as
+ * q = floor((x + 8) * 2^16 / 16) and read back as q * 16 / 2^16 - 8.
+ * floor((x + 8) 2^12) is formed as floor(x 2^12) + 2^15, which is the same
+ * integer and involves no rounding (x 2^12 is exact).  Values whose code
+ * falls outside [0, 65535] (x < -8, x >= 8) or NaN are clamped (NaN to 0);
+ * their number is returned. */
+int64_t orc_quantize_gaussian(const float *x, int64_t n, uint16_t *q)
+{
+    int64_t outside = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double c = floor((double)x[i] * 4096.0) + 32768.0;
+        if (!(c >= 0.0)) { c = 0.0; outside++; }
+        else if (c > 65535.0) { c = 65535.0; outside++; }
+        q[i] = (uint16_t)c;
+    }
+    return outside;
+}
+
+double orc_dequantize_gaussian(uint16_t q)
+{
+    return (double)q * 16.0 / 65536.0 - 8.0;
+}
+
+/* Sign random projections of sparse rows with R stored in two bytes per
+ * entry (Section 4.3): bit j of row i = [ sum_e values[e] * r(indices[e], j)
+ * >= 0 ], r the decoded value above, the sum in FP64 in row order. */
+void orc_srp_sparse_q16(const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
+                        const uint16_t *Rq, int bits, uint32_t *sig)
+{
+    int W = bits / 32;
+    for (int64_t i = 0; i < N; i++) {
+        uint32_t *row = sig + (size_t)i * W;
+        memset(row, 0, sizeof(uint32_t) * W);
+        for (int j = 0; j < bits; j++) {
+            double acc = 0.0;
+            for (int64_t e = indptr[i]; e < indptr[i + 1]; e++)
+                acc += (double)values[e] * orc_dequantize_gaussian(Rq[(size_t)indices[e] * bits + j]);
+            if (acc >= 0.0) row[j / 32] |= 1u << (j % 32);
+        }
+    }
+}
+
 /* The same for dense rows X [N][d] (sum over coordinates 0..d-1 in order).
  * dots (optional, [N][bits]) receives the FP64 sums. */
 void orc_srp_dense(const float *X, int64_t N, int d, const float *R, int bits, uint32_t *sig, double *dots)

@@ -126,3 +126,59 @@ def test_banding_edge_cases():
     sig = np.arange(40, dtype=np.uint32).reshape(5, 8)   # all distinct: none
     assert len(O.lsh_candidates(sig, O.JACCARD, 4, 2)) == 0
     assert len(O.lsh_candidates(np.zeros((1, 8), np.uint32), O.JACCARD, 4, 2)) == 0
+
+
+# ---- two-byte Gaussian storage (Section 4.3) ----
+
+def test_quantize_hand_values():
+    x = np.array([0.0, 1.0, -0.5, -8.0, 7.99, 2.0 ** -13, -2.0 ** -60, 2.0 ** -60, 8.0 - 2.0 ** -12], np.float32)
+    q, n = O.quantize_gaussian(x)
+    # floor((x + 8) * 4096): 32768, 36864, 30720, 0, floor(15.99 * 4096) = 65495 (x is the float
+    # nearest 7.99), 32768, 32767 (just below 8 * 4096), 32768, 65535
+    want = [32768, 36864, 30720, 0, int(np.floor((np.float64(np.float32(7.99)) + 8) * 4096)), 32768, 32767,
+            32768, 65535]
+    assert q.tolist() == want and n == 0
+
+
+def test_quantize_clamps_and_counts():
+    q, n = O.quantize_gaussian(np.array([8.0, -8.5, 100.0, np.nan, -1e30], np.float32))
+    assert q.tolist() == [65535, 0, 65535, 0, 0] and n == 5
+
+
+def test_quantize_error_bound_brute_force():
+    """Each value decodes to the grid point at or just below it: 0 <= x - r < 2^-12."""
+    x = np.random.default_rng(0).standard_normal(200000).astype(np.float32)
+    q, n = O.quantize_gaussian(x)
+    assert n == 0
+    grid = q.astype(np.float64) / 4096.0 - 8.0
+    d = x.astype(np.float64) - grid
+    assert d.min() >= 0.0 and d.max() < 2.0 ** -12
+    assert np.array_equal(O.dequantize_gaussian(q[:1000]), grid[:1000])
+
+
+def test_srp_q16_exact_sign_brute_force():
+    """The two-byte projection's bits against exactly rounded sums (fsum) of
+    the decoded products, wherever the sum is not within a rounding of 0."""
+    vecs = synth.tfidf_vectors(n_docs=60, dim=500, mean_nnz=30, seed=8)
+    Rq, _ = O.quantize_gaussian(synth.gaussian_matrix(500, 64, seed=9))
+    sig = O.srp_sparse_q16(vecs, Rq)
+    checked = 0
+    for i in range(vecs.n):
+        s, e = vecs.indptr[i], vecs.indptr[i + 1]
+        for j in range(64):
+            terms = [float(vecs.values[k]) * (int(Rq[vecs.indices[k], j]) / 4096.0 - 8.0) for k in range(s, e)]
+            exact = math.fsum(terms)
+            if abs(exact) > 1e-12 * (sum(abs(t) for t in terms) + 1e-300):
+                assert ((int(sig[i, j // 32]) >> (j % 32)) & 1) == (exact >= 0.0)
+                checked += 1
+    assert checked > 0.99 * vecs.n * 64
+
+
+def test_srp_q16_matches_float_path_on_grid_values():
+    """R whose entries lie on the two-byte grid: the float projection of the
+    decoded matrix and the two-byte projection are the same function."""
+    vecs = synth.tfidf_vectors(n_docs=200, dim=3000, mean_nnz=40, seed=10)
+    Rq, _ = O.quantize_gaussian(synth.gaussian_matrix(3000, 128, seed=11))
+    R = (Rq.astype(np.float64) / 4096.0 - 8.0).astype(np.float32)
+    assert np.array_equal(R.astype(np.float64), Rq.astype(np.float64) / 4096.0 - 8.0)   # exact in float32
+    assert np.array_equal(O.srp_sparse_q16(vecs, Rq), O.srp_sparse(vecs, R))
