@@ -122,7 +122,8 @@ BLSH_API int blsh_ctx_destroy(blsh_ctx *ctx);
 BLSH_API const char *blsh_last_error(const blsh_ctx *ctx);
 
 /* Synchronises `stream`, then returns and clears the first error the GPU
- * recorded since the previous blsh_status (BLSH_ERANGE, BLSH_ETRUNC) or
+ * recorded since the previous blsh_status (BLSH_ERANGE, BLSH_ETRUNC,
+ * BLSH_ENUMERIC) or
  * BLSH_EDEVICE if the stream reported a CUDA error; BLSH_OK otherwise.
  * If `counters` (host, 4 x uint64) is not NULL it receives the running
  * totals since the last call: [0] pairs with an index >= N, [1] outputs
@@ -185,6 +186,26 @@ BLSH_API int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *
  * of 32, at most 4096. */
 BLSH_API int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
                     int64_t N, const float *R, int64_t dim, int32_t bits, uint32_t *sig, void *stream);
+
+/* Two-byte storage of the Gaussian projection matrix (Section 4.3, "Cheaper
+ * storage of hash functions"): q[i] = floor((x[i] + 8) * 2^16 / 16), the code
+ * of a sample assumed to lie in (-8, 8); a code q stands for q * 2^-12 - 8.
+ * Codes outside [0, 65535] (x < -8, x >= 8) and NaN inputs are clamped (NaN
+ * to 0) and make the next blsh_status return BLSH_ENUMERIC.  x: n floats,
+ * q: n uint16 (device, caller-owned).  Asynchronous on `stream`. */
+BLSH_API int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, uint16_t *q, void *stream);
+
+/* blsh_srp_sparse with R stored as two-byte codes Rq [dim][bits] (uint16,
+ * row-major, from blsh_quantize_gaussian): bit j of row i = [ sum_e
+ * values[e] * (Rq[indices[e]][j] * 2^-12 - 8) >= 0 ], each bit equal to the
+ * sign of the FP64 sum in row order (the decoded values and the products are
+ * exact in FP64).  Half the bytes of the float form are gathered per
+ * nonzero.  bits: a positive multiple of 32, at most 4096 (multiples of 256
+ * with Rq 16-byte aligned take the 16-byte load path).  Errors as
+ * blsh_srp_sparse. */
+BLSH_API int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                 const float *values, int64_t N, const uint16_t *Rq, int64_t dim, int32_t bits,
+                                 uint32_t *sig, void *stream);
 
 /* Sign random projections of dense rows X [N][d] (float, row-major) with
  * R [d][bits] (float, row-major), Section 4.2: bit j of row i =

@@ -68,6 +68,8 @@ def lib():
             "blsh_tables_download": ([p, p, p, p, p, p, p, p, p], C.c_int),
             "blsh_minhash": ([p, p, p, i64, i32, p, p, p, p], C.c_int),
             "blsh_srp_sparse": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
+    "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
+    "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
             "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
             "blsh_srp_dense_workspace": ([i64, i32, i32, p], C.c_int),
             "blsh_lsh_candidates_workspace": ([i64, i32, i32, i32, p], C.c_int),
@@ -251,6 +253,27 @@ def blsh_srp_sparse(ctx: Context, indptr, indices, values, R, sig, stream=None):
     val = values if values.numel() else torch.zeros(1, dtype=torch.float32, device=indptr.device)
     rc = lib().blsh_srp_sparse(ctx.handle, _dev(indptr, torch.int64), _dev(idx), _dev(val, torch.float32), N,
                                _dev(R, torch.float32), dim, bits, _dev(sig), _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_quantize_gaussian(ctx: Context, x, q=None, stream=None):
+    """Two-byte codes of Gaussian samples (Section 4.3); returns q (int16
+    tensor holding the uint16 codes, same shape as x)."""
+    if q is None:
+        q = torch.empty(x.shape, dtype=torch.int16, device=x.device)
+    rc = lib().blsh_quantize_gaussian(ctx.handle, _dev(x, torch.float32), x.numel(), _dev(q), _stream(stream))
+    _check(rc, ctx)
+    return q
+
+
+def blsh_srp_sparse_q16(ctx: Context, indptr, indices, values, Rq, sig, stream=None):
+    """blsh_srp_sparse with R as two-byte codes Rq [dim][bits] (Section 4.3)."""
+    N = indptr.numel() - 1
+    dim, bits = Rq.shape
+    idx = indices if indices.numel() else torch.zeros(1, dtype=torch.int32, device=indptr.device)
+    val = values if values.numel() else torch.zeros(1, dtype=torch.float32, device=indptr.device)
+    rc = lib().blsh_srp_sparse_q16(ctx.handle, _dev(indptr, torch.int64), _dev(idx), _dev(val, torch.float32), N,
+                                   _dev(Rq), dim, bits, _dev(sig), _stream(stream))
     _check(rc, ctx)
 
 

@@ -112,13 +112,25 @@ __global__ void __launch_bounds__(1024) minhash_big_kernel(const int64_t *__rest
 // Otherwise the thread recomputes the sum in FP64 in row order, which
 // reproduces that FP64 sum bit for bit (products of floats are exact in FP64,
 // so one rounding per addition with or without fusion).
+// Entry (i) of R as FP64: a float, or a two-byte code q read back as
+// q 2^-12 - 8 (Section 4.3), which is exact in FP64 (and in FP32).
+__device__ __forceinline__ double r_fp64(const float *R, size_t i) { return (double)__ldg(R + i); }
+__device__ __forceinline__ double r_fp64(const uint16_t *R, size_t i) {
+    return (double)__ldg(R + i) * (1.0 / 4096.0) - 8.0;
+}
+__device__ __forceinline__ float r_fp32(const float *R, size_t i) { return __ldg(R + i); }
+__device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
+    return __fmaf_rn((float)__ldg(R + i), 1.0f / 4096.0f, -8.0f);
+}
+
 constexpr int kSrpMaxPerThread = 16;
 constexpr int kSrpChunk = 256;
 
+template <typename RT>
 __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restrict__ indptr,
                                                          const uint32_t *__restrict__ indices,
                                                          const float *__restrict__ values, long long N,
-                                                         const float *__restrict__ R, long long dim, int bits,
+                                                         const RT *__restrict__ R, long long dim, int bits,
                                                          int per_thread,
                                                          uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
     __shared__ uint32_t s_idx[kSrpChunk];
@@ -149,11 +161,11 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
             __syncthreads();
             for (int i = 0; i < cnt; ++i) {
                 const float v = s_val[i];
-                const float *Rrow = R + (size_t)s_idx[i] * bits + t;
+                const RT *Rrow = R + (size_t)s_idx[i] * bits + t;
 #pragma unroll
                 for (int u = 0; u < kSrpMaxPerThread; ++u) {
                     if (u < per_thread) {
-                        const float r = __ldg(Rrow + u * T);
+                        const float r = r_fp32(Rrow, (size_t)u * T);
                         acc[u] = __fmaf_rn(v, r, acc[u]);
                         mag[u] = __fmaf_rn(fabsf(v), fabsf(r), mag[u]);
                     }
@@ -161,19 +173,20 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
             }
         }
         const float n = (float)(e - s);
+        const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
         const int w = t >> 5;
 #pragma unroll
         for (int u = 0; u < kSrpMaxPerThread; ++u) {
             if (u < per_thread) {
                 const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
                 bool bit;
-                if (fabsf(acc[u]) > bound) {
+                if (!long_row && fabsf(acc[u]) > bound) {
                     bit = acc[u] >= 0.0f;
                 } else {
                     double d = 0.0;
                     for (long long k = s; k < e; ++k) {
                         const uint32_t ix = __ldg(indices + k);
-                        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + t + u * T);
+                        if (ix < dim) d += (double)__ldg(values + k) * r_fp64(R, (size_t)ix * bits + t + u * T);
                     }
                     bit = d >= 0.0;
                     ++rechecked;
@@ -192,13 +205,14 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
 // The FP64 row-order sum of row [s, e) against column j of R, as the oracle
 // forms it (rare: only signs the FP32 bound cannot decide).  Kept out of line
 // so the hot accumulation loop keeps its registers.
+template <typename RT>
 __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ indices,
                                                 const float *__restrict__ values, long long s, long long e,
-                                                const float *__restrict__ R, long long dim, int bits, int j) {
+                                                const RT *__restrict__ R, long long dim, int bits, int j) {
     double d = 0.0;
     for (long long k = s; k < e; ++k) {
         const uint32_t ix = __ldg(indices + k);
-        if (ix < dim) d += (double)__ldg(values + k) * (double)__ldg(R + (size_t)ix * bits + j);
+        if (ix < dim) d += (double)__ldg(values + k) * r_fp64(R, (size_t)ix * bits + j);
     }
     return d;
 }
@@ -252,6 +266,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
             }
         }
         const float n = (float)(e - s);
+        const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
 #pragma unroll
         for (int g = 0; g < V; ++g) {
             uint32_t nib = 0;
@@ -260,7 +275,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                 const int u = 4 * g + c;
                 const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
                 bool bit;
-                if (fabsf(acc[u]) > bound) {
+                if (!long_row && fabsf(acc[u]) > bound) {
                     bit = acc[u] >= 0.0f;
                 } else {
                     // undecided: queue it for srp_recheck_kernel (bit left 0 here),
@@ -271,7 +286,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                         queue[slot] = make_uint2((uint32_t)row, j);
                         bit = false;
                     } else {
-                        const double d = srp_recheck_fp64(indices, values, s, e, R, dim, bits, j);
+                        const double d = srp_recheck_fp64<float>(indices, values, s, e, R, dim, bits, j);
                         bit = d >= 0.0;
                         ++rechecked;
                         zeros += d == 0.0;
@@ -295,11 +310,12 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
 // time and form their exact FP64 products; every lane then adds them in row
 // order (shuffled one by one), so the sum is the FP64 row-order sum bit for
 // bit.  A nonnegative sum sets the bit (the word was written with it clear).
+template <typename RT>
 __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restrict__ queue,
                                                           const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values,
-                                                          const float *__restrict__ R, long long dim, int bits,
+                                                          const RT *__restrict__ R, long long dim, int bits,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch) {
     const unsigned long long total = scratch->recheck_count;
     const unsigned long long n = total < BLSH_RECHECK_CAP ? total : BLSH_RECHECK_CAP;
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
             double p = 0.0;
             if (c0 + lane < e) {
                 const uint32_t ix = __ldg(indices + c0 + lane);
-                if (ix < dim) p = (double)__ldg(values + c0 + lane) * (double)__ldg(R + (size_t)ix * bits + rj.y);
+                if (ix < dim) p = (double)__ldg(values + c0 + lane) * r_fp64(R, (size_t)ix * bits + rj.y);
             }
             const int cnt = (int)min(32ll, e - c0);
             for (int l = 0; l < cnt; ++l) d += __shfl_sync(kFull, p, l);
@@ -328,6 +344,121 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
     }
     if (lane == 0 && done) atomicAdd(&scratch->counters[2], done);
     if (lane == 0 && zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+// Sign random projections with R stored in two bytes per entry (Section 4.3,
+// "Cheaper storage of hash functions").  Thread t owns the groups of 8 bits
+// t, t+T, ...: one 16-byte load brings the 8 codes of a group for a nonzero.
+// A code q stands for (q - 2^15) 2^-12.  The sums are formed over the
+// integers q - 2^15 instead (the float with bit pattern 0x4b000000 | q is
+// 2^23 + q, and subtracting 2^23 + 2^15 is exact), which scales every sum by
+// 2^12 and changes neither its sign nor the relative error bound.  Since
+// |q - 2^15| <= 2^15, sum |v (q - 2^15)| <= 2^15 sum |v|: one magnitude per
+// row stands in for the per-bit magnitudes of srp_sparse4_kernel, and the
+// bound becomes 1.25 n u 2^15 sum|v| + n 2^-149.  Undecided signs go to the
+// same queue and FP64 recheck as the float path (the decoded values are
+// exact in FP64, so the recheck reproduces the oracle's sum bit for bit).
+__device__ __forceinline__ float q16_lo(uint32_t w) { return __int_as_float(0x4b000000u | (w & 0xffffu)) - 8421376.0f; }
+__device__ __forceinline__ float q16_hi(uint32_t w) { return __int_as_float(0x4b000000u | (w >> 16)) - 8421376.0f; }
+
+template <int V>
+__global__ void __launch_bounds__(256) srp_sparse_q16_kernel(const int64_t *__restrict__ indptr,
+                                                             const uint32_t *__restrict__ indices,
+                                                             const float *__restrict__ values, long long N,
+                                                             const uint16_t *__restrict__ R, long long dim, int bits,
+                                                             uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
+                                                             uint2 *__restrict__ queue) {
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int words = bits >> 5;
+    unsigned long long rechecked = 0, zeros = 0, bad = 0;
+    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+        float acc[8 * V];
+#pragma unroll
+        for (int u = 0; u < 8 * V; ++u) acc[u] = 0.0f;
+        float asum = 0.0f;
+        for (long long k = s; k < e; ++k) {
+            uint32_t ix = __ldg(indices + k);
+            float v = __ldg(values + k);
+            if (ix >= dim) {   // malformed row: counted, contributes nothing
+                bad += t == 0;
+                ix = 0;
+                v = 0.0f;
+            }
+            asum += fabsf(v);
+            const uint4 *Rrow = reinterpret_cast<const uint4 *>(R + (size_t)ix * bits) + t;
+#pragma unroll
+            for (int g = 0; g < V; ++g) {
+                const uint4 w = __ldg(Rrow + g * T);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[8 * g + 2 * c] = __fmaf_rn(v, q16_lo(ws[c]), acc[8 * g + 2 * c]);
+                    acc[8 * g + 2 * c + 1] = __fmaf_rn(v, q16_hi(ws[c]), acc[8 * g + 2 * c + 1]);
+                }
+            }
+        }
+        const float n = (float)(e - s);
+        // asum is itself an FP32 sum (relative error below n u); the 1.25
+        // covers it and the second-order terms while n u <= 0.05
+        const float bound = n * 5.9604644775390625e-8f > 0.05f
+                                ? INFINITY
+                                : 1.25f * n * 5.9604644775390625e-8f * 32768.0f * asum + n * 1.4e-45f;
+#pragma unroll
+        for (int g = 0; g < V; ++g) {
+            uint32_t byte = 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int u = 8 * g + c;
+                bool bit;
+                if (fabsf(acc[u]) > bound) {
+                    bit = acc[u] >= 0.0f;
+                } else {
+                    const uint32_t j = 8 * (t + g * T) + c;
+                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
+                    if (slot < BLSH_RECHECK_CAP) {
+                        queue[slot] = make_uint2((uint32_t)row, j);
+                        bit = false;
+                    } else {
+                        const double d = srp_recheck_fp64<uint16_t>(indices, values, s, e, R, dim, bits, j);
+                        bit = d >= 0.0;
+                        ++rechecked;
+                        zeros += d == 0.0;
+                    }
+                }
+                byte |= (uint32_t)bit << c;
+            }
+            uint32_t word = byte << (8 * (lane & 3));
+            word |= __shfl_xor_sync(kFull, word, 1);
+            word |= __shfl_xor_sync(kFull, word, 2);
+            if ((lane & 3) == 0) sig[(size_t)row * words + ((t + g * T) >> 2)] = word;
+        }
+    }
+    if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
+    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
+    if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+// Two-byte codes of Gaussian samples (Section 4.3): q = floor((x + 8) 2^12),
+// formed as floor(x 2^12) + 2^15 (exact in FP32).  Codes outside [0, 65535]
+// (x < -8 or x >= 8) and NaN are clamped (NaN to 0) and reported.
+__global__ void __launch_bounds__(256) quantize_gaussian_kernel(const float *__restrict__ x, long long n,
+                                                                uint16_t *__restrict__ q, blsh_dev_scratch *scratch) {
+    unsigned long long outside = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float c = floorf(__ldg(x + i) * 4096.0f) + 32768.0f;
+        if (!(c >= 0.0f)) {
+            c = 0.0f;
+            ++outside;
+        } else if (c > 65535.0f) {
+            c = 65535.0f;
+            ++outside;
+        }
+        q[i] = (uint16_t)c;
+    }
+    if (outside) blsh_dev_error(scratch, BLSH_ENUMERIC, -1, outside);
 }
 
 // Dense rows X [N][d] against R [d][bits], the same FP32 sums with the same
@@ -467,13 +598,13 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
             default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
             }
             BLSH_LAUNCHED(ctx, "srp sparse kernel");
-            srp_recheck_kernel<<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig,
+            srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig,
                                                                  ctx->scratch);
             BLSH_LAUNCHED(ctx, "srp recheck kernel");
             return BLSH_OK;
         }
     }
-    srp_sparse_kernel<<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
+    srp_sparse_kernel<float><<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp sparse kernel");
     return BLSH_OK;
 }
@@ -493,5 +624,60 @@ int blsh_srp_dense_simt(blsh_ctx *ctx, const float *X, int64_t N, int32_t d, con
     const unsigned grid = (unsigned)(N < cap ? N : cap);
     srp_dense_simt_kernel<<<grid, T, smem, s>>>(X, N, d, R, bits, per_thread, sig, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp dense kernel");
+    return BLSH_OK;
+}
+
+extern "C" int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, uint16_t *q, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !q))) return blsh_fail(ctx, BLSH_EINVAL, "x and q are required");
+    if (n == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long blocks = (n + 255) / 256;
+    const long long cap = (long long)ctx->sm_count * 16;
+    quantize_gaussian_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, n, q, ctx->scratch);
+    BLSH_LAUNCHED(ctx, "quantize kernel");
+    return BLSH_OK;
+}
+
+extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                   const float *values, int64_t N, const uint16_t *Rq, int64_t dim, int32_t bits,
+                                   uint32_t *sig, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!indptr || !indices || !values || !Rq || !sig)
+        return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, values, Rq and sig are required");
+    if (N < 0 || N >= (1ll << 32) || dim <= 0 || bits <= 0 || bits % 32 || bits > 4096)
+        return blsh_fail(ctx, BLSH_EINVAL, "bits must be a positive multiple of 32, at most 4096; N < 2^32");
+    if (!blsh_aligned(indptr, 8) || !blsh_aligned(Rq, 2)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    if (N == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long cap = (long long)ctx->sm_count * 32;
+    const unsigned grid = (unsigned)(N < cap ? N : cap);
+    if (bits % 256 == 0 && blsh_aligned(Rq, 16)) {
+        // 16-byte path: T8 = 32 * (largest divisor of groups/32 up to 8) threads,
+        // V = groups / T8 groups of 8 bits per thread (1 or 2 for bits <= 4096)
+        const int groups = bits / 8;
+        int wt = 8;
+        while ((groups / 32) % wt) --wt;
+        const int T8 = 32 * wt, V = groups / T8;
+        BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
+        uint2 *q = ctx->recheck_queue;
+        if (V == 1)
+            srp_sparse_q16_kernel<1><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
+        else
+            srp_sparse_q16_kernel<2><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
+        BLSH_LAUNCHED(ctx, "srp sparse q16 kernel");
+        srp_recheck_kernel<uint16_t><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, Rq, dim, bits,
+                                                                         sig, ctx->scratch);
+        BLSH_LAUNCHED(ctx, "srp recheck kernel");
+        return BLSH_OK;
+    }
+    int per_thread;
+    const int T = srp_threads(bits, &per_thread);
+    if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");
+    srp_sparse_kernel<uint16_t><<<grid, T, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, per_thread, sig,
+                                                   ctx->scratch);
+    BLSH_LAUNCHED(ctx, "srp sparse q16 kernel");
     return BLSH_OK;
 }
