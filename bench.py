@@ -48,6 +48,11 @@ WORKLOADS = {
                          text="cosine, BayesLSH + Lite: N=20,000 tf-idf sparse float32 vectors, dim 100,000, "
                               "Zipf(1.1) term ids, lognormal nnz (mean 80), 2,048 SRP bits, banding 8x35, "
                               "t=0.7, eps=0.03, delta=0.05, gamma=0.03, k=32, h=128"),
+    "cosine-small-q16": dict(kind=1, n=20000, dim=100000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
+                             n_max=2048, k=32, h=128, seed=2, r_format="q16",
+                             text="cosine-small with the projection matrix stored as two-byte codes "
+                                  "(Section 4.3): N=20,000 tf-idf vectors, dim 100,000, 2,048 SRP bits, "
+                                  "banding 8x35, t=0.7"),
     "cosine-profile": dict(kind=1, n=6000, dim=30000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
                            n_max=2048, k=32, h=128, seed=2,
                            text="cosine-small shape at 6,000 vectors over dim 30,000 (R = 245 MB > L2), for "
@@ -59,9 +64,16 @@ WORKLOADS = {
                           h=64, seed=1,
                           text="jaccard, BayesLSH + Lite: N=2,000 sets over vocab 10,000, lognormal sizes "
                                "(mean 50), 200 planted groups, 256 minhashes, banding 8x32, t=0.7"),
-    "batching": dict(kind=0, n=1_000_000, n_hashes=256, rows=8, bands=32, t=0.5, n_max=256, k=32, h=64, seed=3,
+    "precision": dict(kind=1, dense=True, n=1_000_000, d=256, n_centers=10000, sigma=0.15, bits=1024, rows=16,
+                      bands=64, t=0.8, n_max=1024, k=32, h=128, margin=1e-3, seed=4,
+                      stages=("hash", "band", "verify", "compact"),
+                      text="cosine, BayesLSH + Lite on dense rows: N=1,000,000 float32 embeddings, d=256, "
+                           "10,000-component Gaussian mixture (noise norm 0.15), 1,024 SRP bits by the BF16 "
+                           "tensor-core projection with FP32/FP64 recheck below 1e-3 |x||r|, banding 16x64, t=0.8 "
+                           "(BayesLSH; no Lite pass)"),
+    "batching": dict(kind=0, n=1_000_000, n_hashes=256, rows=3, bands=32, t=0.5, n_max=256, k=32, h=64, seed=3,
                      text="jaccard, BayesLSH + Lite: Chung-Lu graph N=1,000,000, exponent 2.1, mean degree 30, "
-                          "256 minhashes, banding 8x32, t=0.5"),
+                          "256 minhashes, banding 3x32 (power-law buckets, about 1e8 candidate pairs), t=0.5"),
 }
 
 
@@ -69,8 +81,22 @@ WORKLOADS = {
 # workload
 # ---------------------------------------------------------------------------
 
+def dense_csr(X: np.ndarray) -> synth.CSR:
+    """Dense rows as CSR (every coordinate present), for Lite's exact cosine."""
+    N, d = X.shape
+    return synth.CSR(np.arange(0, N * d + 1, d, dtype=np.int64), np.tile(np.arange(d, dtype=np.uint32), N),
+                     X.reshape(-1), d)
+
+
 def make_inputs(w: dict, rank: int = 0):
     seed = w["seed"] + 1000 * rank
+    if w.get("dense"):
+        X = synth.gaussian_mixture(n_points=w["n"], dim=w["d"], n_centers=w["n_centers"],
+                                   sigma_within=w["sigma"], seed=seed)
+        R = synth.gaussian_matrix(w["d"], w["bits"], seed=seed + 1)
+        objs = dense_csr(X)
+        objs.X = X
+        return objs, R
     if w["kind"] == 1:
         objs = synth.tfidf_vectors(n_docs=w["n"], dim=w["dim"], mean_nnz=w["mean_nnz"], seed=seed)
         R = synth.gaussian_matrix(w["dim"], w["bits"], seed=seed + 1)
@@ -97,9 +123,19 @@ class Pipeline:
         self.indptr = t.from_numpy(objs.indptr).to(device)
         self.indices = u32(objs.indices) if objs.indices.size else t.zeros(1, dtype=t.int32, device=device)
         self.values = None if objs.values is None else t.from_numpy(objs.values).to(device)
+        self.dense = bool(w.get("dense"))
+        if self.dense:
+            # X [N][d] shares its storage with the CSR values Lite reads
+            self.X = self.values.view(N, w["d"])
+            self.dense_ws = t.zeros(max(1, B.blsh_srp_dense_workspace(N, w["d"], w["bits"])), dtype=t.uint8,
+                                    device=device)
         if self.kind == 1:
             self.R = t.from_numpy(hashp).to(device)
             self.W = w["bits"] // 32
+            if w.get("r_format") == "q16":
+                self.Rq = B.blsh_quantize_gaussian(self.ctx, self.R)
+                B.blsh_status(self.ctx)
+                del self.R
         else:
             self.a, self.b = u32(hashp[0]), u32(hashp[1])
             self.W = w["n_hashes"]
@@ -138,7 +174,11 @@ class Pipeline:
     # the stages of a step, each one library call
     def hash(self):
         B = self.B
-        if self.kind == 1:
+        if self.dense:
+            B.blsh_srp_dense(self.ctx, self.X, self.R, self.sig, margin=self.w["margin"], workspace=self.dense_ws)
+        elif self.kind == 1 and self.w.get("r_format") == "q16":
+            B.blsh_srp_sparse_q16(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig)
+        elif self.kind == 1:
             B.blsh_srp_sparse(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig)
         else:
             B.blsh_minhash(self.ctx, self.indptr, self.indices, self.W, self.a, self.b, self.sig)
@@ -160,9 +200,13 @@ class Pipeline:
         B = self.B
         B.blsh_compact(self.ctx, self.status, (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX), self.out1, self.n_out[0:1],
                        P_dev=self.n_pairs)
-        B.blsh_compact(self.ctx, self.lstatus, 1 << B.LITE_ACCEPT, self.out2, self.n_out[1:2], P_dev=self.n_pairs)
+        if "lite" in self.STAGES:
+            B.blsh_compact(self.ctx, self.lstatus, 1 << B.LITE_ACCEPT, self.out2, self.n_out[1:2],
+                           P_dev=self.n_pairs)
 
-    STAGES = ("hash", "band", "verify", "lite", "compact")
+    @property
+    def STAGES(self):
+        return tuple(self.w.get("stages", ("hash", "band", "verify", "lite", "compact")))
 
     def step(self):
         for s in self.STAGES:
@@ -224,6 +268,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def load_tensor_peak():
+    """Dense BF16 tensor peak: the sustained figure (a kernel inside a long
+    step), else the burst figure, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        if "bf16_tflops_sustained" in d:
+            return d["bf16_tflops_sustained"], "measured (sustained)"
+        return d["bf16_tflops"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 2):
+    """The plain GPU form of the same step: eager launches (no CUDA graph),
+    the plain verification launch (one thread per pair, no persistence or
+    work stealing, no autotuning) and, for dense rows, the FP32 CUDA-core
+    projection instead of the BF16 tensor cores.  Same outputs (both forms
+    are bit-exact to the oracle); returns the times and the speedups."""
+    plain = B.blsh_plan(B.PLAN_PLAIN, 1, 256, 0, 0)
+    times = {"hash": [], "verify": [], "step": []}
+    for i in range(reps):
+        flush.fill_(float(i))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        if pipe.dense:
+            B.blsh_srp_dense(pipe.ctx, pipe.X, pipe.R, pipe.sig, margin=pipe.w["margin"], workspace=None)
+        else:
+            pipe.hash()
+        ev[1].record(stream)
+        pipe.band()
+        ev[2].record(stream)
+        B.blsh_verify(pipe.ctx, pipe.tab, pipe.pairs, pipe.sig, pipe.status, pipe.n_used, pipe.m, pipe.est,
+                      pipe.hist, P_dev=pipe.n_pairs, plan=plain)
+        ev[3].record(stream)
+        if "lite" in pipe.STAGES:
+            pipe.lite()
+        pipe.compact()
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        times["hash"].append(ev[0].elapsed_time(ev[1]))
+        times["verify"].append(ev[2].elapsed_time(ev[3]))
+        times["step"].append(ev[0].elapsed_time(ev[4]))
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("plain-form step failed")
+    t = {k: float(np.mean(v)) for k, v in times.items()}
+    return {"form": "eager launches, plain verify launch" + (", FP32 CUDA-core projection" if pipe.dense else ""),
+            "step_ms": round(t["step"], 4), "verify_ms": round(t["verify"], 4), "hash_ms": round(t["hash"], 4),
+            "speedup_step": round(t["step"] / step_ms, 3),
+            "speedup_verify": round(t["verify"] / stage_ms["verify"], 3),
+            "speedup_hash": round(t["hash"] / stage_ms["hash"], 3)}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -233,7 +330,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def srp_sparse_bytes(indptr, indices, bits):
+def srp_sparse_bytes(indptr, indices, bits, esize=4):
     """Algorithmic bytes of one sparse-SRP launch: every nonzero reads its
     index, value and one row of R (bits floats); every row reads two indptr
     entries and writes bits/8 bytes of signature.  Also returned: the unique
@@ -242,7 +339,7 @@ def srp_sparse_bytes(indptr, indices, bits):
     N = len(indptr) - 1
     fixed = nnz * 8 + N * (8 + bits // 8)
     distinct = int(np.unique(indices).size)
-    return fixed + nnz * 4 * bits, fixed + distinct * 4 * bits
+    return fixed + nnz * esize * bits, fixed + distinct * esize * bits
 
 
 def band_bytes(N, bands, P, passes):
@@ -380,6 +477,8 @@ def run_ours(args, w):
             stage_ms[s].append(evs[j].elapsed_time(evs[j + 1]))
     stage_ms = {s: float(np.mean(v)) for s, v in stage_ms.items()}
 
+    vs_plain = measure_plain(B, torch, pipe, flush, stream, stage_ms, my_ms)
+
     # ---- end to end through the public API, host buffers ----
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_indptr = pin(objs.indptr)
@@ -393,12 +492,17 @@ def run_ours(args, w):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pipe.indptr.copy_(h_indptr, non_blocking=True)
-        pipe.indices[: h_indices.numel()].copy_(h_indices, non_blocking=True)
-        nb_in = h_indptr.numel() * 8 + h_indices.numel() * 4
-        if h_values is not None:
+        if pipe.dense:
+            # the step's input is X; Lite's row structure is fixed by the shape
             pipe.values.copy_(h_values, non_blocking=True)
-            nb_in += h_values.numel() * 4
+            nb_in = h_values.numel() * 4
+        else:
+            pipe.indptr.copy_(h_indptr, non_blocking=True)
+            pipe.indices[: h_indices.numel()].copy_(h_indices, non_blocking=True)
+            nb_in = h_indptr.numel() * 8 + h_indices.numel() * 4
+            if h_values is not None:
+                pipe.values.copy_(h_values, non_blocking=True)
+                nb_in += h_values.numel() * 4
         one_step()
         h_counts.copy_(pipe.n_out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -421,8 +525,12 @@ def run_ours(args, w):
 
     peak, peak_kind = load_peaks()
     unique = None
-    if w["kind"] == 1:
-        hash_bytes, unique = srp_sparse_bytes(objs.indptr, objs.indices, w["bits"])
+    if pipe.dense:
+        hash_bytes = pipe.N * w["d"] * 4 + w["d"] * w["bits"] * 4 + pipe.N * w["bits"] // 8
+        hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
+    elif w["kind"] == 1:
+        hash_bytes, unique = srp_sparse_bytes(objs.indptr, objs.indices, w["bits"],
+                                              2 if w.get("r_format") == "q16" else 4)
         hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
     else:
         nnz = int(objs.indptr[-1])
@@ -430,8 +538,11 @@ def run_ours(args, w):
         hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
     vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P)
     key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
+    hash_kernel = ("srp_dense_tc_kernel" if pipe.dense else
+                   "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else
+                   "srp_sparse4_kernel" if w["kind"] == 1 else "minhash_kernel")
     rooflines = {
-        "hash": {"kernel": "srp_sparse4_kernel" if w["kind"] == 1 else "minhash_kernel", "bytes": hash_bytes},
+        "hash": {"kernel": hash_kernel, "bytes": hash_bytes},
         "band": {"kernel": "emit_kernel + radix sort", "bytes": band_bytes(pipe.N, w["bands"], pipe.P,
                                                                              (key_bits + 7) // 8)},
         "verify": {"kernel": "verify_kernel", "bytes": vbytes},
@@ -444,9 +555,18 @@ def run_ours(args, w):
     dom = max(rooflines, key=lambda k: stage_ms[k])
     rl_bytes = rooflines[dom]["bytes"]
     achieved = rl_bytes / (stage_ms[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes), "stage": dom}
+    if dom == "hash" and pipe.dense:
+        # a contraction: three BF16 products (hi*hi, hi*lo, lo*hi) of 2 N d bits flops each
+        flops = 3 * 2 * pipe.N * w["d"] * w["bits"]
+        tf_peak, tf_kind = load_tensor_peak()
+        ach = flops / (stage_ms[dom] / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": hash_kernel, "achieved": round(ach, 1), "peak": tf_peak,
+                    "unit": "TFLOP/s", "frac": round(ach / tf_peak, 4), "traffic": None, "peak_source": tf_kind,
+                    "algorithmic_flops": int(flops), "stage": dom}
+    else:
+        roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes), "stage": dom}
     if "gathered_bytes" in rooflines[dom]:
         gb = rooflines[dom]["gathered_bytes"]
         roofline["gathered_bytes"] = int(gb)
@@ -482,6 +602,7 @@ def run_ours(args, w):
                     "stop_hist_first4": [int(x) for x in hist[:4]]},
         "clocks": clk,
         "wall_s_timed_loop": round(wall, 3),
+        "vs_plain": vs_plain,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, objs, hashp, pipe.P)
@@ -557,7 +678,11 @@ def run_verify_large(args, w):
 def oracle_pass(O, w, objs, hashp):
     """One pass of the oracle over the given objects; returns (pairs, seconds)."""
     t0 = time.perf_counter()
-    if w["kind"] == 1:
+    if getattr(objs, "X", None) is not None:
+        sig = O.srp_dense(objs.X, hashp)
+    elif w["kind"] == 1 and w.get("r_format") == "q16":
+        sig = O.srp_sparse_q16(objs, O.quantize_gaussian(hashp)[0])
+    elif w["kind"] == 1:
         sig = O.srp_sparse(objs, hashp)
     else:
         sig = O.minhash(objs, hashp[0], hashp[1])
@@ -566,9 +691,10 @@ def oracle_pass(O, w, objs, hashp):
     tab = O.tables(p)
     t1 = time.perf_counter()
     r = O.verify(tab, pairs, sig)
-    lr = O.verify_lite(tab, pairs, sig, objs)
     O.compact(r.status, (1 << O.ACCEPT) | (1 << O.ACCEPT_AT_MAX))
-    O.compact(lr.status, 1 << O.LITE_ACCEPT)
+    if "lite" in w.get("stages", ("lite",)):
+        lr = O.verify_lite(tab, pairs, sig, objs)
+        O.compact(lr.status, 1 << O.LITE_ACCEPT)
     t2 = time.perf_counter()
     return len(pairs), t2 - t0, t1 - t0
 
@@ -576,8 +702,11 @@ def oracle_pass(O, w, objs, hashp):
 def sample_objects(objs, n):
     """The first n objects of a workload (same generator, same distribution)."""
     e = int(objs.indptr[n])
-    return synth.CSR(objs.indptr[: n + 1].copy(), objs.indices[:e], None if objs.values is None else objs.values[:e],
-                     objs.dim)
+    sub = synth.CSR(objs.indptr[: n + 1].copy(), objs.indices[:e], None if objs.values is None else objs.values[:e],
+                    objs.dim)
+    if getattr(objs, "X", None) is not None:
+        sub.X = objs.X[:n]
+    return sub
 
 
 def cpu_baseline(w, objs, hashp, P_full):

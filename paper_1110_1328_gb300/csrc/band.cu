@@ -57,6 +57,7 @@ struct BandArgs {
     uint32_t *ck;             // cosine: [N][ck_words] band keys packed in lanes of ck_lane bytes
     int ck_lane, ck_words;
     int vec16;                // rows of sig start 16-byte aligned
+    int exact_classes;        // Jaccard: class ids in ck (4-byte lanes), 32-bit sort keys, no bk
 };
 
 // Lane width (bytes) of packed cosine band keys, and 32-bit words per row
@@ -84,8 +85,14 @@ __global__ void band_keys_kernel(BandArgs A, unsigned long long *keys, uint32_t 
             else reinterpret_cast<uint32_t *>(kr)[b] = f;
         } else {
             const unsigned long long h = band_hash(row, b * A.rows, A.rows);
-            A.bk[(size_t)i * A.bands + b] = h;
-            key = A.band_bits == 0 ? h : (((unsigned long long)b << A.key_shift) | (h >> A.band_bits));
+            if (A.exact_classes) {
+                // 32-bit key: the band, then the top bits of its hash (equal
+                // keys are sorted together; the class ids split collisions)
+                key = ((unsigned long long)b << (32 - A.band_bits)) | (h >> (32 + A.band_bits));
+            } else {
+                A.bk[(size_t)i * A.bands + b] = h;
+                key = A.band_bits == 0 ? h : (((unsigned long long)b << A.key_shift) | (h >> A.band_bits));
+            }
         }
         keys[it] = key;
         vals[it] = (uint32_t)i;
@@ -344,6 +351,235 @@ __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const ui
     }
 }
 
+// Cosine emission staged in shared memory.  A CTA owns a tile of
+// kEmitTile sorted positions and stages kEmitWin positions from the tile's
+// start (the tile and what follows it): keys, object ids and packed key
+// rows.  Lane l of warp w owns position i = 32 w + l of the tile (its object
+// x, band b and key row in registers) and finds the end of its bucket by a
+// binary search of the staged keys (continued in global memory when the
+// bucket runs past the window).  The warp then walks the partners j of its
+// 32 positions in order; each step reads one staged key row (the same
+// address for every lane: a broadcast) and every lane tests its own pair
+// (x, y_j) on the bands before its b, with the per-lane masks of those
+// bands fixed before the walk.  Pairs of position i are counted, or
+// written, in partner order, the order emit_kernel uses.
+constexpr int kEmitTile = 256;
+constexpr int kEmitWinMax = 768;
+constexpr int kStageWords = 32;          // key rows of up to 128 bytes take this path
+constexpr size_t kEmitSmemBudget = 72 * 1024;
+
+// Positions staged per tile: the tile and up to 512 after it, within the
+// shared-memory budget.
+int emit_cos_win(int ck_words) {
+    const size_t per = (size_t)ck_words * 4 + 8 + 4;
+    size_t w = kEmitSmemBudget / per;
+    if (w > (size_t)kEmitWinMax) w = kEmitWinMax;
+    return (int)w;
+}
+size_t emit_cos_smem(int ck_words) { return (size_t)emit_cos_win(ck_words) * (ck_words * 4 + 8 + 4); }
+
+// First position q >= from with q == n or keys[q] != key, given
+// keys[from - 1] == key: galloping, then a binary search.
+__device__ long long run_end_global(const unsigned long long *keys, long long n, long long from,
+                                    unsigned long long key) {
+    long long lo = from, step = 1;
+    while (lo < n && keys[lo] == key) {
+        const long long probe = lo + step;
+        if (probe >= n || keys[probe] != key) {
+            long long hi = probe < n ? probe : n;
+            ++lo;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (keys[mid] == key) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+        }
+        lo = probe;
+        step <<= 1;
+    }
+    return lo;
+}
+
+// The walk of one warp over partners [jmin, jmax) (tile-relative), NW4
+// 16-byte words of key rows compared per pair.  Word w of a lane's row
+// holds bands below its b in full when w < full, in part (the low lanes
+// kept by pmask) when w == full.
+template <int NW4, bool WRITE>
+__device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
+                                          const uint32_t *vals, long long p0, int win, int cw4, unsigned jmin,
+                                          unsigned jmax, bool live, int i, long long end, uint32_t x,
+                                          const uint4 *kx, int full, uint32_t pmask, int eqw,
+                                          uint32_t one, uint32_t high, unsigned long long out,
+                                          unsigned long long &cnt, uint32_t *pairs, long long cap) {
+    for (unsigned j = jmin; j < jmax; ++j) {
+        const bool staged = (int)j < win;
+        const uint32_t y = staged ? s_val[j] : __ldg(vals + p0 + j);
+        const uint4 *yrow = staged ? s_ck + (size_t)j * cw4 : reinterpret_cast<const uint4 *>(A.ck + (size_t)y * A.ck_words);
+        uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
+#pragma unroll
+        for (int c = 0; c < NW4; ++c) {
+            const uint4 yv = staged ? yrow[c] : __ldg(yrow + c);
+            const uint32_t z[4] = {kx[c].x ^ yv.x, kx[c].y ^ yv.y, kx[c].z ^ yv.z, kx[c].w ^ yv.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = 4 * c + q;
+                const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
+                const uint32_t zl = (z[q] - one) & ~z[q];
+                hit |= zl & m;
+                if (w == eqw) eq = zl & high;
+            }
+        }
+        const bool ok = live && (int)j > i && p0 + (long long)j < end && hit == 0 && eq != 0;
+        if (WRITE && ok) {
+            const long long o = (long long)(out + cnt);
+            if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+        }
+        cnt += ok;
+    }
+}
+
+// Cosine emission staged in shared memory.  A CTA owns a tile of
+// kEmitTile sorted positions and stages `win` positions from the tile's
+// start (the tile and what follows it): keys, object ids and packed key
+// rows.  Lane l of warp w owns position i = 32 w + l of the tile (its object
+// x, band b and key row in registers) and finds the end of its bucket by a
+// binary search of the staged keys (continued in global memory when the
+// bucket runs past the window).  The warp then walks the partners j of its
+// 32 positions in order; each step reads one staged key row (the same
+// address for every lane: a broadcast) and every lane tests its own pair
+// (x, y_j) on the bands before its b.  Pairs of position i are counted, or
+// written, in partner order, the order emit_kernel uses.
+template <bool WRITE, int KW4>
+__global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(BandArgs A, const unsigned long long *keys,
+                                                               const uint32_t *vals, long long n,
+                                                               unsigned long long *counts, uint32_t *pairs,
+                                                               long long cap, int win_cap) {
+    extern __shared__ uint4 s_ck[];                       // [win_cap][cw4]
+    const int cw4 = A.ck_words >> 2;
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_ck + (size_t)win_cap * cw4);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + win_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // SWAR zero-lane test constants for lanes of 1, 2 or 4 bytes
+    const uint32_t one = A.ck_lane == 1 ? 0x01010101u : (A.ck_lane == 2 ? 0x00010001u : 1u);
+    const uint32_t high = one << (8 * A.ck_lane - 1);
+    const int per_word = 4 / A.ck_lane;
+    for (long long p0 = (long long)blockIdx.x * kEmitTile; p0 < n; p0 += (long long)gridDim.x * kEmitTile) {
+        const int win = (int)(n - p0 < win_cap ? n - p0 : win_cap);
+        __syncthreads();                                  // the previous tile is done with the stage
+        for (int k = threadIdx.x; k < win; k += blockDim.x) {
+            const uint32_t v = vals[p0 + k];
+            s_key[k] = keys[p0 + k];
+            s_val[k] = v;
+            const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
+            for (int c = 0; c < cw4; ++c) s_ck[(size_t)k * cw4 + c] = __ldg(src + c);
+        }
+        __syncthreads();
+        const int tile = win < kEmitTile ? win : kEmitTile;
+        const int i = warp * 32 + lane;
+        if (warp * 32 >= tile) continue;                  // no position of this warp (uniform)
+        const bool live = i < tile;
+        unsigned long long key = 0;
+        uint32_t x = 0;
+        int b = 0;
+        long long end = p0;
+        uint4 kx[KW4];                                    // KW4 >= cw4
+#pragma unroll
+        for (int c = 0; c < KW4; ++c) kx[c] = make_uint4(0u, 0u, 0u, 0u);
+        if (live) {
+            key = s_key[i];
+            x = s_val[i];
+            b = A.exact_classes ? (A.band_bits == 0 ? 0 : (int)(key >> (32 - A.band_bits))) : (int)(key >> A.rows);
+            int lo = i + 1, hi = win;                     // first staged position past the bucket
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_key[mid] == key) lo = mid + 1; else hi = mid;
+            }
+            end = p0 + lo;
+            if (lo == win && end < n) end = run_end_global(keys, n, end, key);
+#pragma unroll
+            for (int c = 0; c < KW4; ++c)
+                if (c < cw4) kx[c] = s_ck[(size_t)i * cw4 + c];
+        }
+        const int full = b / per_word, rest = b % per_word;   // bands 0..b-1: `full` words and `rest` lanes
+        const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
+        // Jaccard class ids: word b must match too (a key collision is not a bucket)
+        const int eqw = A.exact_classes ? b : -1;
+        const int need = A.exact_classes ? b + 1 : full + (rest ? 1 : 0);
+        const int nw4 = (__reduce_max_sync(kFull, (unsigned)(live ? need : 0)) + 3) >> 2;
+        const unsigned jmin = (unsigned)(warp * 32 + 1);
+        const unsigned jmax = __reduce_max_sync(kFull, live ? (unsigned)(end - p0) : 0u);
+        const unsigned long long out = WRITE && live ? counts[p0 + i] : 0;
+        unsigned long long cnt = 0;
+#define BLSH_WALK(NW) emit_walk<NW, WRITE>(A, s_ck, s_val, vals, p0, win, cw4, jmin, jmax, live, i, end, x, kx, \
+                                           full, pmask, eqw, one, high, out, cnt, pairs, cap)
+        if constexpr (KW4 <= 4) {
+            switch (nw4) {
+            case 0: BLSH_WALK(0); break;
+            case 1: BLSH_WALK(1); break;
+            case 2: BLSH_WALK(2); break;
+            case 3: BLSH_WALK(3); break;
+            default: BLSH_WALK(4); break;
+            }
+        } else {
+            switch (nw4) {
+            case 0: BLSH_WALK(0); break;
+            case 1: case 2: BLSH_WALK(2); break;
+            case 3: case 4: BLSH_WALK(4); break;
+            case 5: case 6: BLSH_WALK(6); break;
+            default: BLSH_WALK(8); break;
+            }
+        }
+#undef BLSH_WALK
+        if (!WRITE && live) counts[p0 + i] = cnt;
+    }
+}
+
+// First position of the run of `key` that contains p (keys[p] == key):
+// galloping backwards, then a binary search.
+__device__ long long run_start_global(const unsigned long long *keys, long long p, unsigned long long key) {
+    long long hi = p, step = 1;                           // keys[hi] == key
+    for (;;) {
+        const long long probe = hi - step;
+        if (probe < 0 || keys[probe] != key) {
+            long long lo = probe < 0 ? 0 : probe + 1;     // the start is in [lo, hi]
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (keys[mid] == key) hi = mid; else lo = mid + 1;
+            }
+            return lo;
+        }
+        hi = probe;
+        step <<= 1;
+    }
+}
+
+// Jaccard class ids: for sorted position p (object v, band b) the id is the
+// first position of its run whose band-b hashes equal v's, so two objects
+// share an id in band b iff they agree on the whole band.  Almost always
+// that is the run's first position; a hash collision inside a run is split
+// off by comparing the hashes themselves.
+__global__ void __launch_bounds__(256) class_id_kernel(BandArgs A, const unsigned long long *keys,
+                                                       const uint32_t *vals, long long n) {
+    const int shift = 32 - A.band_bits;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[p];
+        const uint32_t v = vals[p];
+        const int b = A.band_bits == 0 ? 0 : (int)(key >> shift);
+        long long cid = p;
+        if (p > 0 && keys[p - 1] == key) {
+            const long long h = run_start_global(keys, p, key);
+            if (same_band(A, v, vals[h], b)) {
+                cid = h;
+            } else {
+                for (long long q = h + 1; q < p; ++q)
+                    if (same_band(A, v, vals[q], b)) { cid = q; break; }
+            }
+        }
+        A.ck[(size_t)v * A.ck_words + b] = (uint32_t)cid;
+    }
+}
+
 __global__ void check_cap_kernel(const long long *n_pairs, long long cap, blsh_dev_scratch *scratch) {
     if (*n_pairs > cap) blsh_dev_error(scratch, BLSH_ETRUNC, 1, (unsigned long long)(*n_pairs - cap));
 }
@@ -353,6 +589,9 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t keys0, keys1, vals0, vals1, bk, ck, counts, hist, partial, grand, total;
 };
+
+// Jaccard class-id rows: one 32-bit id per band, rounded to 16 bytes.
+int jac_row_words(int bands) { return (bands + 3) & ~3; }
 
 Layout layout(long long N, int kind, int rows, int bands) {
     const long long n = N * bands;
@@ -365,8 +604,10 @@ Layout layout(long long N, int kind, int rows, int bands) {
     L.keys1 = o; o = up256(o + n * 8);
     L.vals0 = o; o = up256(o + n * 4);
     L.vals1 = o; o = up256(o + n * 4);
-    L.bk = o; o = up256(o + (kind == BLSH_JACCARD ? n * 8 : 0));
-    L.ck = o; o = up256(o + (kind == BLSH_COSINE ? (size_t)N * cos_row_words(rows, bands) * 4 : 0));
+    const bool classes = kind == BLSH_JACCARD && jac_row_words(bands) <= kStageWords;
+    L.bk = o; o = up256(o + (kind == BLSH_JACCARD && !classes ? n * 8 : 0));
+    L.ck = o; o = up256(o + (kind == BLSH_COSINE ? (size_t)N * cos_row_words(rows, bands) * 4
+                                                  : (classes ? (size_t)N * jac_row_words(bands) * 4 : 0)));
     L.counts = o; o = up256(o + n * 8);
     L.hist = o; o = up256(o + hist_n * 4);
     L.partial = o; o = up256(o + part * 8);
@@ -432,11 +673,12 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     A.bands = bands;
     A.band_bits = band_bits;
     A.key_shift = 64 - band_bits;
-    A.bk = kind == BLSH_JACCARD ? (unsigned long long *)(ws + L.bk) : nullptr;
-    A.ck = kind == BLSH_COSINE ? (uint32_t *)(ws + L.ck) : nullptr;
-    A.ck_lane = cos_lane_bytes(rows);
+    A.exact_classes = kind == BLSH_JACCARD && jac_row_words(bands) <= kStageWords;
+    A.bk = kind == BLSH_JACCARD && !A.exact_classes ? (unsigned long long *)(ws + L.bk) : nullptr;
+    A.ck = kind == BLSH_COSINE || A.exact_classes ? (uint32_t *)(ws + L.ck) : nullptr;
+    A.ck_lane = A.exact_classes ? 4 : cos_lane_bytes(rows);
     A.vec16 = blsh_aligned(sig, 16) && sig_words % 4 == 0;
-    A.ck_words = cos_row_words(rows, bands);
+    A.ck_words = A.exact_classes ? jac_row_words(bands) : cos_row_words(rows, bands);
     if (kind == BLSH_COSINE)   // pad lanes past the last band stay zero
         BLSH_CUDA(ctx, cudaMemsetAsync(A.ck, 0, (size_t)N * A.ck_words * 4, s));
 
@@ -444,7 +686,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     band_keys_kernel<<<grid, 256, 0, s>>>(A, keys[0], vals[0]);
     BLSH_LAUNCHED(ctx, "band keys");
 
-    const int key_bits = kind == BLSH_COSINE ? band_bits + rows : 64;
+    const int key_bits = kind == BLSH_COSINE ? band_bits + rows : (A.exact_classes ? 32 : 64);
     const int passes = (key_bits + 7) / 8;
     const long long tiles = (n + kSortTile - 1) / kSortTile;
     int cur = 0;
@@ -460,13 +702,48 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
         BLSH_LAUNCHED(ctx, "radix scatter");
         cur ^= 1;
     }
-    emit_kernel<false><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
+    if (A.exact_classes) {
+        class_id_kernel<<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n);
+        BLSH_LAUNCHED(ctx, "class ids");
+    }
+    const bool staged = (kind == BLSH_COSINE || A.exact_classes) && A.ck_words <= kStageWords;
+    const size_t smem = staged ? emit_cos_smem(A.ck_words) : 0;
+    const int win_cap = staged ? emit_cos_win(A.ck_words) : 0;
+    const long long etiles = (n + kEmitTile - 1) / kEmitTile;
+    const long long ecap = (long long)ctx->sm_count * (A.ck_words <= 16 ? 3 : 2);
+    const unsigned egrid = (unsigned)(etiles < ecap ? etiles : ecap);
+    if (staged) {
+        if (A.ck_words <= 16) {
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<false, 4>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 4>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            emit_cos_tile_kernel<false, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                    win_cap);
+        } else {
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<false, 8>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 8>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            emit_cos_tile_kernel<false, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                    win_cap);
+        }
+    } else {
+        emit_kernel<false><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
+    }
     BLSH_LAUNCHED(ctx, "pair count");
     BLSH_CUDA(ctx, blsh_scan::exclusive_scan<unsigned long long>(counts, counts, n,
                                                                  (unsigned long long *)(ws + L.partial),
                                                                  (unsigned long long *)n_pairs, s));
     ctx->launches.fetch_add(3, std::memory_order_relaxed);
-    emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
+    if (staged && A.ck_words <= 16)
+        emit_cos_tile_kernel<true, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                               win_cap);
+    else if (staged)
+        emit_cos_tile_kernel<true, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                               win_cap);
+    else
+        emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     BLSH_LAUNCHED(ctx, "pair write");
     check_cap_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs, cap, ctx->scratch);
     BLSH_LAUNCHED(ctx, "capacity check");

@@ -124,6 +124,8 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 }
 
 constexpr int kSrpMaxPerThread = 16;
+constexpr int kSrpBatch = 1;       // nonzeros per load batch (float rows)
+constexpr int kSrpQ16Batch = 1;    // the same for two-byte rows
 constexpr int kSrpChunk = 256;
 
 template <typename RT>
@@ -225,7 +227,7 @@ __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ ind
 // keeps no barrier in the loop; several rows of R are in flight per thread.
 // The four bits of a group form a nibble; eight lanes OR their nibbles into
 // one signature word with shuffles.
-template <int V>
+template <int V, int U>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values, long long N,
@@ -242,27 +244,47 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
         float acc[4 * V], mag[4 * V];
 #pragma unroll
         for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
-        for (long long k = s; k < e; ++k) {
-            uint32_t ix = __ldg(indices + k);
-            float v = __ldg(values + k);
-            if (ix >= dim) {   // malformed row: counted, contributes nothing
-                bad += t == 0;
-                ix = 0;
-                v = 0.0f;
-            }
-            const float av = fabsf(v);
-            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits) + t;
+        // nonzeros in batches of U: the U row loads of a batch are issued
+        // before any of their sums, so U * V 16-byte loads are in flight
+        for (long long k0 = s; k0 < e; k0 += U) {
+            const int cnt = (int)(e - k0 < U ? e - k0 : U);
+            uint32_t ix[U];
+            float v[U];
+            float4 r[U][V];
 #pragma unroll
-            for (int g = 0; g < V; ++g) {
-                const float4 r = __ldg(Rrow + g * T);
-                acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
-                acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
-                acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
-                acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
-                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
-                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
-                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
-                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
+            for (int q = 0; q < U; ++q) {
+                ix[q] = 0;
+                v[q] = 0.0f;
+                if (q < cnt) {
+                    ix[q] = __ldg(indices + k0 + q);
+                    v[q] = __ldg(values + k0 + q);
+                    if (ix[q] >= dim) {   // malformed row: counted, contributes nothing
+                        bad += t == 0;
+                        ix[q] = 0;
+                        v[q] = 0.0f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix[q] * bits) + t;
+#pragma unroll
+                for (int g = 0; g < V; ++g) r[q][g] = q < cnt ? __ldg(Rrow + g * T) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const float av = fabsf(v[q]);
+#pragma unroll
+                for (int g = 0; g < V; ++g) {
+                    acc[4 * g + 0] = __fmaf_rn(v[q], r[q][g].x, acc[4 * g + 0]);
+                    acc[4 * g + 1] = __fmaf_rn(v[q], r[q][g].y, acc[4 * g + 1]);
+                    acc[4 * g + 2] = __fmaf_rn(v[q], r[q][g].z, acc[4 * g + 2]);
+                    acc[4 * g + 3] = __fmaf_rn(v[q], r[q][g].w, acc[4 * g + 3]);
+                    mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[q][g].x), mag[4 * g + 0]);
+                    mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[q][g].y), mag[4 * g + 1]);
+                    mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[q][g].z), mag[4 * g + 2]);
+                    mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[q][g].w), mag[4 * g + 3]);
+                }
             }
         }
         const float n = (float)(e - s);
@@ -361,7 +383,7 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
 __device__ __forceinline__ float q16_lo(uint32_t w) { return __int_as_float(0x4b000000u | (w & 0xffffu)) - 8421376.0f; }
 __device__ __forceinline__ float q16_hi(uint32_t w) { return __int_as_float(0x4b000000u | (w >> 16)) - 8421376.0f; }
 
-template <int V>
+template <int V, int U>
 __global__ void __launch_bounds__(256) srp_sparse_q16_kernel(const int64_t *__restrict__ indptr,
                                                              const uint32_t *__restrict__ indices,
                                                              const float *__restrict__ values, long long N,
@@ -379,24 +401,43 @@ __global__ void __launch_bounds__(256) srp_sparse_q16_kernel(const int64_t *__re
 #pragma unroll
         for (int u = 0; u < 8 * V; ++u) acc[u] = 0.0f;
         float asum = 0.0f;
-        for (long long k = s; k < e; ++k) {
-            uint32_t ix = __ldg(indices + k);
-            float v = __ldg(values + k);
-            if (ix >= dim) {   // malformed row: counted, contributes nothing
-                bad += t == 0;
-                ix = 0;
-                v = 0.0f;
+        // nonzeros in batches of U (U * V loads in flight)
+        for (long long k0 = s; k0 < e; k0 += U) {
+            const int cnt = (int)(e - k0 < U ? e - k0 : U);
+            uint32_t ix[U];
+            float v[U];
+            uint4 w[U][V];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                ix[q] = 0;
+                v[q] = 0.0f;
+                if (q < cnt) {
+                    ix[q] = __ldg(indices + k0 + q);
+                    v[q] = __ldg(values + k0 + q);
+                    if (ix[q] >= dim) {   // malformed row: counted, contributes nothing
+                        bad += t == 0;
+                        ix[q] = 0;
+                        v[q] = 0.0f;
+                    }
+                }
             }
-            asum += fabsf(v);
-            const uint4 *Rrow = reinterpret_cast<const uint4 *>(R + (size_t)ix * bits) + t;
 #pragma unroll
-            for (int g = 0; g < V; ++g) {
-                const uint4 w = __ldg(Rrow + g * T);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+            for (int q = 0; q < U; ++q) {
+                const uint4 *Rrow = reinterpret_cast<const uint4 *>(R + (size_t)ix[q] * bits) + t;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    acc[8 * g + 2 * c] = __fmaf_rn(v, q16_lo(ws[c]), acc[8 * g + 2 * c]);
-                    acc[8 * g + 2 * c + 1] = __fmaf_rn(v, q16_hi(ws[c]), acc[8 * g + 2 * c + 1]);
+                for (int g = 0; g < V; ++g) w[q][g] = q < cnt ? __ldg(Rrow + g * T) : make_uint4(0x80008000u, 0x80008000u, 0x80008000u, 0x80008000u);
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                asum += fabsf(v[q]);
+#pragma unroll
+                for (int g = 0; g < V; ++g) {
+                    const uint32_t ws[4] = {w[q][g].x, w[q][g].y, w[q][g].z, w[q][g].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        acc[8 * g + 2 * c] = __fmaf_rn(v[q], q16_lo(ws[c]), acc[8 * g + 2 * c]);
+                        acc[8 * g + 2 * c + 1] = __fmaf_rn(v[q], q16_hi(ws[c]), acc[8 * g + 2 * c + 1]);
+                    }
                 }
             }
         }
@@ -592,10 +633,10 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
             BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
             uint2 *q = ctx->recheck_queue;
             switch (V) {
-            case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            case 1: srp_sparse4_kernel<1, kSrpBatch><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            case 2: srp_sparse4_kernel<2, kSrpBatch><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            case 3: srp_sparse4_kernel<3, 1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
+            default: srp_sparse4_kernel<4, 1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
             }
             BLSH_LAUNCHED(ctx, "srp sparse kernel");
             srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig,
@@ -664,9 +705,9 @@ extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const u
         BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
         uint2 *q = ctx->recheck_queue;
         if (V == 1)
-            srp_sparse_q16_kernel<1><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
+            srp_sparse_q16_kernel<1, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
         else
-            srp_sparse_q16_kernel<2><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
+            srp_sparse_q16_kernel<2, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
         BLSH_LAUNCHED(ctx, "srp sparse q16 kernel");
         srp_recheck_kernel<uint16_t><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, Rq, dim, bits,
                                                                          sig, ctx->scratch);

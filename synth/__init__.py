@@ -255,8 +255,10 @@ def chung_lu_sets(n_nodes: int = 1_000_000, exponent: float = 2.1, mean_degree: 
 
     Node weights w_i = (i + i0)^(-1/(exponent-1)) scaled to the given mean
     degree; n_nodes*mean_degree/2 edges are drawn with both endpoints
-    proportional to w; self-loops and duplicate edges are dropped.  Row i is
-    the sorted neighbour set of node i (possibly empty).
+    proportional to w; self-loops and duplicate edges are dropped.  A node
+    left without edges gets one, to a node drawn proportional to w, so that
+    no adjacency set is empty (graph datasets list only nodes with edges).
+    Row i is the sorted neighbour set of node i.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     w = (np.arange(n_nodes, dtype=np.float64) + i0) ** (-1.0 / (exponent - 1.0))
@@ -271,6 +273,12 @@ def chung_lu_sets(n_nodes: int = 1_000_000, exponent: float = 2.1, mean_degree: 
     b = np.maximum(u, v)
     key = np.unique(a * n_nodes + b)
     a, b = key // n_nodes, key % n_nodes
+    lonely = np.setdiff1d(np.arange(n_nodes, dtype=np.int64), np.concatenate([a, b]))
+    if lonely.size:
+        partner = np.searchsorted(cdf, rng.random(lonely.size), side="right").astype(np.int64)
+        partner = np.where(partner == lonely, (partner + 1) % n_nodes, partner)
+        key = np.unique(np.concatenate([key, np.minimum(lonely, partner) * n_nodes + np.maximum(lonely, partner)]))
+        a, b = key // n_nodes, key % n_nodes
     src = np.concatenate([a, b])
     dst = np.concatenate([b, a])
     order = np.lexsort((dst, src))

@@ -34,8 +34,12 @@ def test_library_exports_every_declared_symbol(B):
 def test_host_checks_without_device(B):
     lib = B.lib()
     n = C.c_size_t()
+    # per (object, band): two key buffers, two id buffers, the pair counts
+    # and a 4-byte class id (up to 32 bands) or an 8-byte band hash (more)
     assert lib.blsh_lsh_candidates_workspace(1000, B.JACCARD, 8, 32, C.byref(n)) == 0
-    assert n.value >= 1000 * 32 * (8 + 8 + 4 + 4 + 8 + 8)
+    assert n.value >= 1000 * 32 * (8 + 8 + 4 + 4 + 8 + 4)
+    assert lib.blsh_lsh_candidates_workspace(1000, B.JACCARD, 2, 40, C.byref(n)) == 0
+    assert n.value >= 1000 * 40 * (8 + 8 + 4 + 4 + 8 + 8)
     assert lib.blsh_lsh_candidates_workspace(-1, B.JACCARD, 8, 32, C.byref(n)) == B.EINVAL
     assert lib.blsh_lsh_candidates_workspace(10, 7, 8, 32, C.byref(n)) == B.EINVAL
     assert lib.blsh_strerror(B.ERANGE) == b"pair index out of range"

@@ -141,3 +141,41 @@ def test_batching_workload_sampled(B):
     # stop histogram and status counts agree
     st = pipe.status[:P].cpu().numpy()
     assert int(pipe.hist.sum()) == P and not np.any(st == 77)
+
+
+def test_precision_workload_sampled(B):
+    """1,000,000 dense 256-d embeddings, 1,024 bits by the tensor-core
+    projection, about 6e8 candidate pairs: sampled signature rows bit-exact
+    to the oracle's FP64 signs, sampled pairs' outcomes recomputed by the
+    oracle, and the candidate list free of duplicates."""
+    w, objs, R, pipe = run_pipeline(B, "precision", graph=False)
+    P = pipe.P
+    assert P > 100_000_000
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(objs.n, 2000, replace=False))
+    assert np.array_equal(u32(pipe.sig[torch.from_numpy(rows).cuda()]), O.srp_dense(objs.X[rows], R))
+    q = np.sort(rng.choice(P, 4000, replace=False))
+    sp = u32(pipe.pairs[torch.from_numpy(q).cuda()])
+    assert np.all(sp[:, 0] < sp[:, 1])
+    ids, inv = np.unique(sp.reshape(-1), return_inverse=True)
+    sig_o = O.srp_dense(objs.X[ids], R)
+    local = inv.reshape(-1, 2).astype(np.uint32)
+    r, bands = w["rows"], w["bands"]
+
+    def band_bits(s, b):
+        return (s[:, (b * r) // 32] >> np.uint32((b * r) % 32)) & np.uint32((1 << r) - 1)
+
+    band_eq = np.stack([band_bits(sig_o[local[:, 0]], b) == band_bits(sig_o[local[:, 1]], b) for b in range(bands)], 1)
+    assert band_eq.any(1).all()
+    p = O.Params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    want = O.verify(O.tables(p), local, sig_o)
+    qd = torch.from_numpy(q).cuda()
+    assert np.array_equal(pipe.status[qd].cpu().numpy(), want.status)
+    assert np.array_equal(pipe.m[qd].cpu().numpy().view(np.uint16), want.m)
+    est = pipe.est[qd].cpu().numpy()
+    ok = ~np.isnan(want.est)
+    assert np.array_equal(np.isnan(est), ~ok) and np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
+    # no duplicates (sorted on the device: object ids are below 2^31)
+    dp = pipe.pairs[:P].long()
+    key, _ = torch.sort((dp[:, 0] << 32) | dp[:, 1])
+    assert bool((key[1:] > key[:-1]).all())

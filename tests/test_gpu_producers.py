@@ -166,10 +166,43 @@ def test_banding_jaccard_bit_exact(B, ctx):
         assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
 
 
+def test_banding_jaccard_wide_and_fallback(B, ctx):
+    """Many bands: up to 32 bands take the class-id path, more bands the
+    per-pair hash check."""
+    sets = synth.jaccard_sets(n_sets=1500, vocab=3000, mean_size=40, n_groups=200, seed=5)
+    a, b = synth.minhash_coeffs(256, seed=6)
+    sig = O.minhash(sets, a, b)
+    for rows, bands in ((3, 32), (2, 40), (2, 100)):
+        want = O.lsh_candidates(sig, O.JACCARD, rows, bands)
+        rc, n, got = gpu_candidates(B, ctx, sig, 0, rows, bands)
+        assert rc == 0 and n == len(want)
+        assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+
+
+def test_banding_jaccard_key_collision(B, ctx):
+    """146089 and 154344 have the same top 32 bits of the one-row band hash,
+    so their objects share a sort key; they must not become candidates of
+    each other (the class ids compare the hashes themselves)."""
+    sig = np.zeros((600, 4), np.uint32)
+    sig[:200, :] = 146089
+    sig[200:400, :] = 154344
+    sig[400:, :] = np.arange(1, 201, dtype=np.uint32)[:, None] * 7919
+    sig = sig[np.random.default_rng(0).permutation(600)]
+    for rows, bands in ((1, 1), (1, 2), (1, 4)):
+        want = O.lsh_candidates(sig, O.JACCARD, rows, bands)
+        assert len(want) == 2 * 200 * 199 // 2
+        rc, n, got = gpu_candidates(B, ctx, sig, 0, rows, bands)
+        assert rc == 0 and n == len(want)
+        assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+
+
 def test_banding_cosine_bit_exact(B, ctx):
     vecs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=100, seed=3)
     sig = O.srp_sparse(vecs, synth.gaussian_matrix(30000, 512, seed=4))
-    for rows, bands in ((8, 35), (12, 20), (32, 4), (5, 7)):
+    # (2, 3) and (1, 4): buckets of 750 and 1,500 objects, longer than the
+    # staged window of the cosine emission kernel; (12, 40) and (17, 30):
+    # packed key rows of 80 and 120 bytes (the wide-row form of that kernel)
+    for rows, bands in ((8, 35), (12, 20), (32, 4), (5, 7), (2, 3), (1, 4), (12, 40), (17, 30)):
         want = O.lsh_candidates(sig, O.COSINE, rows, bands)
         rc, n, got = gpu_candidates(B, ctx, sig, 1, rows, bands)
         assert rc == 0 and n == len(want)
