@@ -457,9 +457,11 @@ def run_ours(args, w):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    rc = B.blsh_status(pipe.ctx)
+    rc, ctr = B.blsh_status(pipe.ctx, counters=True)
     if rc != 0:
         raise RuntimeError(f"timed steps reported {rc}")
+    # signs the FP32 bound left to the FP64 recheck, and exactly-zero dots
+    rechecks = {"rechecked_per_step": ctr[2] / args.steps, "zero_dots_per_step": ctr[3] / args.steps}
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     my_ms = float(np.mean(step_ms))
 
@@ -603,6 +605,7 @@ def run_ours(args, w):
         "clocks": clk,
         "wall_s_timed_loop": round(wall, 3),
         "vs_plain": vs_plain,
+        "srp_signs": rechecks,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, objs, hashp, pipe.P)

@@ -351,32 +351,28 @@ __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const ui
     }
 }
 
-// Cosine emission staged in shared memory.  A CTA owns a tile of
-// kEmitTile sorted positions and stages kEmitWin positions from the tile's
-// start (the tile and what follows it): keys, object ids and packed key
-// rows.  Lane l of warp w owns position i = 32 w + l of the tile (its object
-// x, band b and key row in registers) and finds the end of its bucket by a
-// binary search of the staged keys (continued in global memory when the
-// bucket runs past the window).  The warp then walks the partners j of its
-// 32 positions in order; each step reads one staged key row (the same
-// address for every lane: a broadcast) and every lane tests its own pair
-// (x, y_j) on the bands before its b, with the per-lane masks of those
-// bands fixed before the walk.  Pairs of position i are counted, or
-// written, in partner order, the order emit_kernel uses.
 constexpr int kEmitTile = 256;
 constexpr int kEmitWinMax = 768;
 constexpr int kStageWords = 32;          // key rows of up to 128 bytes take this path
 constexpr size_t kEmitSmemBudget = 72 * 1024;
 
+// Staged key rows are cws = (ck_words / 4) | 1 16-byte words apart: an odd
+// stride, so lanes reading different rows hit different banks.
+__host__ __device__ inline int stage_stride(int ck_words) { return (ck_words >> 2) | 1; }
+
 // Positions staged per tile: the tile and up to 512 after it, within the
 // shared-memory budget.
 int emit_cos_win(int ck_words) {
-    const size_t per = (size_t)ck_words * 4 + 8 + 4;
+    const size_t per = (size_t)stage_stride(ck_words) * 16 + 8 + 4;
     size_t w = kEmitSmemBudget / per;
     if (w > (size_t)kEmitWinMax) w = kEmitWinMax;
     return (int)w;
 }
-size_t emit_cos_smem(int ck_words) { return (size_t)emit_cos_win(ck_words) * (ck_words * 4 + 8 + 4); }
+// The stage, plus each warp's buffer of 32 partner rows and ids.
+size_t emit_cos_smem(int ck_words) {
+    const int kw4 = ck_words <= 16 ? 4 : 8;
+    return (size_t)emit_cos_win(ck_words) * (stage_stride(ck_words) * 16 + 8 + 4) + 8 * 32 * (16 * kw4 + 4);
+}
 
 // First position q >= from with q == n or keys[q] != key, given
 // keys[from - 1] == key: galloping, then a binary search.
@@ -400,41 +396,148 @@ __device__ long long run_end_global(const unsigned long long *keys, long long n,
     return lo;
 }
 
+template <int NW4, bool WRITE>
+__device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigned j, bool live, int i,
+                                          long long p0, long long end, uint32_t x, const uint4 *kx, int full,
+                                          uint32_t pmask, int eqw, uint32_t one, uint32_t high,
+                                          unsigned long long out, unsigned long long &cnt, uint32_t *pairs,
+                                          long long cap) {
+    uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
+#pragma unroll
+    for (int c = 0; c < NW4; ++c) {
+        const uint4 yv = yrow[c];
+        const uint32_t z[4] = {kx[c].x ^ yv.x, kx[c].y ^ yv.y, kx[c].z ^ yv.z, kx[c].w ^ yv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = 4 * c + q;
+            const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
+            const uint32_t zl = (z[q] - one) & ~z[q];
+            hit |= zl & m;
+            if (w == eqw) eq = zl & high;
+        }
+    }
+    const bool ok = live && (int)j > i && p0 + (long long)j < end && hit == 0 && eq != 0;
+    if (WRITE && ok) {
+        const long long o = (long long)(out + cnt);
+        if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+    }
+    cnt += ok;
+}
+
 // The walk of one warp over partners [jmin, jmax) (tile-relative), NW4
 // 16-byte words of key rows compared per pair.  Word w of a lane's row
 // holds bands below its b in full when w < full, in part (the low lanes
-// kept by pmask) when w == full.
+// kept by pmask) when w == full; word eqw (class ids) must match.
+// Partners inside the window come from the stage; partners past it (long
+// buckets) are fetched 32 at a time into the warp's own buffer, one row per
+// lane, so that their loads overlap.
 template <int NW4, bool WRITE>
 __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
-                                          const uint32_t *vals, long long p0, int win, int cw4, unsigned jmin,
-                                          unsigned jmax, bool live, int i, long long end, uint32_t x,
-                                          const uint4 *kx, int full, uint32_t pmask, int eqw,
-                                          uint32_t one, uint32_t high, unsigned long long out,
+                                          uint4 *w_rows, uint32_t *w_ids, const uint32_t *vals, long long p0,
+                                          int win, int stride, unsigned jmin, unsigned jmax, bool live, int i,
+                                          long long end, uint32_t x, const uint4 *kx, int full, uint32_t pmask,
+                                          int eqw, uint32_t one, uint32_t high, unsigned long long out,
                                           unsigned long long &cnt, uint32_t *pairs, long long cap) {
-    for (unsigned j = jmin; j < jmax; ++j) {
-        const bool staged = (int)j < win;
-        const uint32_t y = staged ? s_val[j] : __ldg(vals + p0 + j);
-        const uint4 *yrow = staged ? s_ck + (size_t)j * cw4 : reinterpret_cast<const uint4 *>(A.ck + (size_t)y * A.ck_words);
-        uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
+    const unsigned wend = jmax < (unsigned)win ? jmax : (unsigned)win;
+    for (unsigned j = jmin; j < wend; ++j)
+        emit_step<NW4, WRITE>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, full, pmask, eqw, one,
+                              high, out, cnt, pairs, cap);
+    const int lane = threadIdx.x & 31;
+    for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
+        __syncwarp();
+        if (j0 + lane < jmax) {
+            const uint32_t yv = __ldg(vals + p0 + j0 + lane);
+            w_ids[lane] = yv;
+            const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
 #pragma unroll
-        for (int c = 0; c < NW4; ++c) {
-            const uint4 yv = staged ? yrow[c] : __ldg(yrow + c);
-            const uint32_t z[4] = {kx[c].x ^ yv.x, kx[c].y ^ yv.y, kx[c].z ^ yv.z, kx[c].w ^ yv.w};
+            for (int c = 0; c < NW4; ++c) w_rows[lane * NW4 + c] = __ldg(g + c);
+        }
+        __syncwarp();
+        const unsigned n = jmax - j0 < 32u ? jmax - j0 : 32u;
+        for (unsigned u = 0; u < n; ++u)
+            emit_step<NW4, WRITE>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, full, pmask, eqw,
+                                  one, high, out, cnt, pairs, cap);
+    }
+}
+
+// The flat walk for warps whose buckets are small: the pairs (i, j) of the
+// warp's 32 positions are numbered in order (position, then partner) and
+// lane l takes pairs l, l + 32, ...; the owner of pair t is found by a
+// binary search of the lanes' exclusive prefix of partner counts.  Every
+// lane reads both rows from the stage.  A kept pair's slot is its owner's
+// output offset plus the kept pairs of that owner before it: those of
+// earlier steps (acc[owner], kept in shared memory) and those of lower lanes
+// in this step (lanes of one owner are contiguous).  All partners are
+// staged (the caller checks).
+template <int NW4, bool WRITE>
+__device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
+                                          const unsigned long long *s_key, uint32_t *acc, int cws, int warp,
+                                          bool live, int i, long long end, long long p0, unsigned long long out,
+                                          uint32_t one, uint32_t high, int per_word, uint32_t *pairs,
+                                          long long cap) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned mine = live ? (unsigned)(end - p0 - i - 1) : 0u;
+    unsigned incl = mine;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int w = 4 * c + q;
-                const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
-                const uint32_t zl = (z[q] - one) & ~z[q];
-                hit |= zl & m;
-                if (w == eqw) eq = zl & high;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned off = incl - mine;
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    acc[lane] = 0;
+    __syncwarp();
+    for (unsigned t0 = 0; t0 < total; t0 += 32) {
+        const unsigned t = t0 + lane;
+        const bool valid = t < total;
+        int o = 0;                                        // the last lane whose prefix is <= t
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const unsigned oc = __shfl_sync(kFull, off, o + step);
+            if (oc <= t) o += step;
+        }
+        const unsigned off_o = __shfl_sync(kFull, off, o);
+        const unsigned long long out_o = __shfl_sync(kFull, out, o);
+        const int io = warp * 32 + o;
+        const int j = io + 1 + (int)(t - off_o);
+        bool ok = false;
+        uint32_t x = 0, y = 0;
+        if (valid) {
+            const unsigned long long key = s_key[io];
+            const int b = A.exact_classes ? (A.band_bits == 0 ? 0 : (int)(key >> (32 - A.band_bits)))
+                                          : (int)(key >> A.rows);
+            const int full = b / per_word, rest = b % per_word;
+            const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
+            const int eqw = A.exact_classes ? b : -1;
+            const uint4 *xr = s_ck + (size_t)io * cws, *yr = s_ck + (size_t)j * cws;
+            uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
+#pragma unroll
+            for (int c = 0; c < NW4; ++c) {
+                const uint4 xv = xr[c], yv = yr[c];
+                const uint32_t z[4] = {xv.x ^ yv.x, xv.y ^ yv.y, xv.z ^ yv.z, xv.w ^ yv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int w = 4 * c + q;
+                    const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
+                    const uint32_t zl = (z[q] - one) & ~z[q];
+                    hit |= zl & m;
+                    if (w == eqw) eq = zl & high;
+                }
             }
+            ok = hit == 0 && eq != 0;
+            x = s_val[io];
+            y = s_val[j];
         }
-        const bool ok = live && (int)j > i && p0 + (long long)j < end && hit == 0 && eq != 0;
+        const unsigned okm = __ballot_sync(kFull, ok);
+        const unsigned seg = __match_any_sync(kFull, valid ? o : 32 + lane);
         if (WRITE && ok) {
-            const long long o = (long long)(out + cnt);
-            if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+            const long long slot = (long long)(out_o + acc[o] + __popc(okm & seg & lt));
+            if (slot < cap) reinterpret_cast<uint2 *>(pairs)[slot] = make_uint2(x, y);
         }
-        cnt += ok;
+        __syncwarp();
+        if (valid && (seg >> lane) == 1u) acc[o] += __popc(okm & seg);   // the segment's highest lane
+        __syncwarp();
     }
 }
 
@@ -454,11 +557,13 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
                                                                const uint32_t *vals, long long n,
                                                                unsigned long long *counts, uint32_t *pairs,
                                                                long long cap, int win_cap) {
-    extern __shared__ uint4 s_ck[];                       // [win_cap][cw4]
-    const int cw4 = A.ck_words >> 2;
-    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_ck + (size_t)win_cap * cw4);
-    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + win_cap);
+    extern __shared__ uint4 s_ck[];                       // [win_cap][cws]
+    const int cw4 = A.ck_words >> 2, cws = stage_stride(A.ck_words);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *w_rows = s_ck + (size_t)win_cap * cws + (size_t)warp * 32 * KW4;   // per warp [32][KW4]
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_ck + (size_t)win_cap * cws + 8 * 32 * KW4);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + win_cap);
+    uint32_t *w_ids = s_val + win_cap + warp * 32;                            // per warp [32]
     // SWAR zero-lane test constants for lanes of 1, 2 or 4 bytes
     const uint32_t one = A.ck_lane == 1 ? 0x01010101u : (A.ck_lane == 2 ? 0x00010001u : 1u);
     const uint32_t high = one << (8 * A.ck_lane - 1);
@@ -471,7 +576,7 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
             s_key[k] = keys[p0 + k];
             s_val[k] = v;
             const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
-            for (int c = 0; c < cw4; ++c) s_ck[(size_t)k * cw4 + c] = __ldg(src + c);
+            for (int c = 0; c < cw4; ++c) s_ck[(size_t)k * cws + c] = __ldg(src + c);
         }
         __syncthreads();
         const int tile = win < kEmitTile ? win : kEmitTile;
@@ -498,7 +603,7 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
             if (lo == win && end < n) end = run_end_global(keys, n, end, key);
 #pragma unroll
             for (int c = 0; c < KW4; ++c)
-                if (c < cw4) kx[c] = s_ck[(size_t)i * cw4 + c];
+                if (c < cw4) kx[c] = s_ck[(size_t)i * cws + c];
         }
         const int full = b / per_word, rest = b % per_word;   // bands 0..b-1: `full` words and `rest` lanes
         const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
@@ -510,8 +615,35 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
         const unsigned jmax = __reduce_max_sync(kFull, live ? (unsigned)(end - p0) : 0u);
         const unsigned long long out = WRITE && live ? counts[p0 + i] : 0;
         unsigned long long cnt = 0;
-#define BLSH_WALK(NW) emit_walk<NW, WRITE>(A, s_ck, s_val, vals, p0, win, cw4, jmin, jmax, live, i, end, x, kx, \
-                                           full, pmask, eqw, one, high, out, cnt, pairs, cap)
+        // small buckets: number the pairs and give each lane one (the walk
+        // below would spend a step per partner position on mostly idle lanes)
+        const unsigned pairs_w = __reduce_add_sync(kFull, live ? (unsigned)(end - p0 - i - 1) : 0u);
+        if (jmax <= (unsigned)win && 5ull * ((pairs_w + 31) / 32) < 2ull * (jmax - jmin)) {
+#define BLSH_FLAT(NW) emit_flat<NW, WRITE>(A, s_ck, s_val, s_key, w_ids, cws, warp, live, i, end, p0, out, one, high, \
+                                           per_word, pairs, cap)
+            if constexpr (KW4 <= 4) {
+                switch (nw4) {
+                case 0: BLSH_FLAT(0); break;
+                case 1: BLSH_FLAT(1); break;
+                case 2: BLSH_FLAT(2); break;
+                case 3: BLSH_FLAT(3); break;
+                default: BLSH_FLAT(4); break;
+                }
+            } else {
+                switch (nw4) {
+                case 0: BLSH_FLAT(0); break;
+                case 1: case 2: BLSH_FLAT(2); break;
+                case 3: case 4: BLSH_FLAT(4); break;
+                case 5: case 6: BLSH_FLAT(6); break;
+                default: BLSH_FLAT(8); break;
+                }
+            }
+#undef BLSH_FLAT
+            if (!WRITE && live) counts[p0 + i] = w_ids[lane];
+            continue;
+        }
+#define BLSH_WALK(NW) emit_walk<NW, WRITE>(A, s_ck, s_val, w_rows, w_ids, vals, p0, win, cws, jmin, jmax, live, i, \
+                                           end, x, kx, full, pmask, eqw, one, high, out, cnt, pairs, cap)
         if constexpr (KW4 <= 4) {
             switch (nw4) {
             case 0: BLSH_WALK(0); break;

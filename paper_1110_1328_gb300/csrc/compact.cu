@@ -1,7 +1,8 @@
 // compact.cu -- the output set O of Algorithms 1 and 2: a stable compaction
 // of the retained pair indices.
 //
-// A fixed grid of C CTAs splits [0, P) into C contiguous ranges.  Pass 1
+// A fixed grid of C CTAs splits [0, P) into C contiguous ranges (starting
+// at multiples of 16 statuses, read 16 at a time).  Pass 1
 // counts the kept items of each range; pass 2 gives each CTA the sum of the
 // counts of the ranges before it and writes its range's indices in order,
 // one tile at a time with a block-wide prefix sum.  The count array (C
@@ -23,25 +24,53 @@ __device__ __forceinline__ long long resolve_p(long long P, const long long *P_d
     return pd < 0 ? 0 : (pd < P ? pd : P);
 }
 
+// CTA b owns [lo, hi): P * b / C rounded down to a multiple of 16, so that
+// with a 16-byte aligned status array every thread reads its 16 statuses
+// with one 16-byte load.
+__device__ __forceinline__ void cta_range(long long P, long long &lo, long long &hi) {
+    lo = (P * blockIdx.x / gridDim.x) & ~15ll;
+    hi = blockIdx.x + 1 == gridDim.x ? P : (P * (blockIdx.x + 1) / gridDim.x) & ~15ll;
+}
+
+// Bit i of the result: status q0 + i is kept (q0 + i < hi).
+__device__ __forceinline__ uint32_t kept16(const uint8_t *status, long long q0, long long hi, uint32_t mask,
+                                           bool vec) {
+    uint32_t bits = 0;
+    if (vec && q0 + 16 <= hi) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(status + q0));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bits |= (uint32_t)kept((uint8_t)(w[i >> 2] >> (8 * (i & 3))), mask) << i;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (q0 + i < hi) bits |= (uint32_t)kept(status[q0 + i], mask) << i;
+    }
+    return bits;
+}
+
 __global__ void __launch_bounds__(kThreads) compact_count(const uint8_t *status, long long P_cap,
-                                                          const long long *P_dev, uint32_t mask,
+                                                          const long long *P_dev, uint32_t mask, bool vec,
                                                           blsh_dev_scratch *scratch) {
     const long long P = resolve_p(P_cap, P_dev);
-    const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+    long long lo, hi;
+    cta_range(P, lo, hi);
     long long c = 0;
-    for (long long q = lo + threadIdx.x; q < hi; q += kThreads) c += kept(status[q], mask);
+    for (long long q0 = lo + 16ll * threadIdx.x; q0 < hi; q0 += 16ll * kThreads)
+        c += __popc(kept16(status, q0, hi, mask, vec));
     long long total;
     blsh_scan::block_exclusive<long long>(c, &total);
     if (threadIdx.x == 0) scratch->cta_counts[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kThreads) compact_write(const uint8_t *status, long long P_cap,
-                                                          const long long *P_dev, uint32_t mask, int64_t *out,
-                                                          long long cap, long long *n_out,
+                                                          const long long *P_dev, uint32_t mask, bool vec,
+                                                          int64_t *out, long long cap, long long *n_out,
                                                           blsh_dev_scratch *scratch) {
     __shared__ long long s_base;
     const long long P = resolve_p(P_cap, P_dev);
-    const long long lo = P * blockIdx.x / gridDim.x, hi = P * (blockIdx.x + 1) / gridDim.x;
+    long long lo, hi;
+    cta_range(P, lo, hi);
     long long before = 0;
     for (int c = threadIdx.x; c < (int)blockIdx.x; c += kThreads) before += scratch->cta_counts[c];
     long long tot;
@@ -52,16 +81,8 @@ __global__ void __launch_bounds__(kThreads) compact_write(const uint8_t *status,
     for (long long t0 = lo; t0 < hi; t0 += kTile) {
         // thread owns kPer consecutive items of the tile
         const long long q0 = t0 + (long long)threadIdx.x * kPer;
-        uint32_t bits = 0;
-        int c = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const long long q = q0 + i;
-            if (q < hi && kept(status[q], mask)) {
-                bits |= 1u << i;
-                ++c;
-            }
-        }
+        const uint32_t bits = q0 < hi ? kept16(status, q0, hi, mask, vec) : 0u;
+        const int c = __popc(bits);
         long long tile_total;
         long long o = base + blsh_scan::block_exclusive<long long>((long long)c, &tile_total);
 #pragma unroll
@@ -95,10 +116,12 @@ extern "C" int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, con
                                                                                  : BLSH_COMPACT_MAX_CTAS;
     if (ctas > most) ctas = most;
     if (ctas < 1) ctas = 1;
-    compact_count<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, ctx->scratch);
+    const bool vec = blsh_aligned(status, 16);
+    compact_count<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, vec,
+                                                      ctx->scratch);
     BLSH_LAUNCHED(ctx, "compaction count");
-    compact_write<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, out_idx, cap,
-                                                      (long long *)n_out, ctx->scratch);
+    compact_write<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, vec, out_idx,
+                                                      cap, (long long *)n_out, ctx->scratch);
     BLSH_LAUNCHED(ctx, "compaction write");
     return BLSH_OK;
 }

@@ -3,7 +3,7 @@
 // Pass 1 is the verification kernel of verify.cu in its Lite form: the
 // pruning loop over at most h hashes, no concentration test; an unpruned
 // pair is marked as a survivor in its status byte.  Pass 2 (this file) gives
-// every survivor its exact similarity: persistent warps take 256 statuses at
+// every survivor its exact similarity: persistent warps take 8,192 statuses at
 // a time from a work counter, and the warp computes each survivor's
 // similarity cooperatively by intersecting the two sorted index lists (each
 // lane binary-searches elements of the shorter row in the longer one).
@@ -33,7 +33,10 @@ struct LiteArgs {
     uint8_t *status;
     double *sim;
     blsh_dev_scratch *scratch;
+    int vec;                  // status is 16-byte aligned
 };
+
+constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab of the work counter
 
 __device__ __forceinline__ long long fixed_term(float u, float v) {
     return __double2ll_rn(__dmul_rn(__dmul_rn((double)u, (double)v), kTwo60));
@@ -63,22 +66,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
         P = pd < 0 ? 0 : (pd < P ? pd : P);
     }
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        // a warp takes 8 tiles of 32 statuses per grab of the work counter
-        unsigned long long grab = 0;
-        if (lane == 0) grab = atomicAdd(&A.scratch->work2, 1ull);
-        grab = __shfl_sync(kFull, grab, 0);
-        if ((long long)grab * 256 >= P) break;
-        for (int sub = 0; sub < 8; ++sub) {
-        const long long q0 = (long long)grab * 256 + sub * 32;
-        if (q0 >= P) break;
-        const long long mine = q0 + lane;
-        const bool surv = mine < P && A.status[mine] == BLSH_LITE_SURVIVOR;
-        unsigned mask = __ballot_sync(kFull, surv);
-        while (mask) {
-            const int l = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const long long q = q0 + l;
+    auto exact = [&](long long q) {
             const uint2 pr = __ldg(A.pairs + q);
             const long long ax = __ldg(A.indptr + pr.x), ex = __ldg(A.indptr + pr.x + 1);
             const long long ay = __ldg(A.indptr + pr.y), ey = __ldg(A.indptr + pr.y + 1);
@@ -128,7 +116,42 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 A.sim[q] = s;
                 A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
             }
-        }
+    };
+    // A warp takes kLiteGrab tiles of 512 statuses per grab of the work
+    // counter; a lane reads 16 statuses with one 16-byte load, and the warp
+    // then computes the survivors of the tile one after the other.
+    for (;;) {
+        unsigned long long grab = 0;
+        if (lane == 0) grab = atomicAdd(&A.scratch->work2, 1ull);
+        grab = __shfl_sync(kFull, grab, 0);
+        const long long g0 = (long long)grab * kLiteGrab * 512;
+        if (g0 >= P) break;
+        for (int tt = 0; tt < kLiteGrab; ++tt) {
+            const long long q0 = g0 + 512ll * tt;
+            if (q0 >= P) break;
+            const long long qs = q0 + 16ll * lane;
+            uint32_t surv = 0;
+            if (A.vec && qs + 16 <= P) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(A.status + qs));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    surv |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_LITE_SURVIVOR) << i;
+            } else {
+                for (int i = 0; i < 16; ++i)
+                    if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv |= 1u << i;
+            }
+            unsigned lanes = __ballot_sync(kFull, surv != 0);
+            while (lanes) {
+                const int l = __ffs(lanes) - 1;
+                lanes &= lanes - 1;
+                uint32_t bits = __shfl_sync(kFull, surv, l);
+                while (bits) {
+                    const int i = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    exact(q0 + 16ll * l + i);
+                }
+            }
         }
     }
 }
@@ -200,6 +223,7 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     L.status = status;
     L.sim = sim;
     L.scratch = ctx->scratch;
+    L.vec = blsh_aligned(status, 16);
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, sizeof(unsigned long long), s));
     int occ = 0;
     if (values) {

@@ -32,16 +32,16 @@ __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterp
 
 template <int KIND, int G, int U, bool PERSIST>
 __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
+    // minMatches is staged in shared memory; the concentration bitmap (up to
+    // tens of KB, consulted only by pairs that pass the pruning test) is
+    // read through L1.
     extern __shared__ __align__(16) unsigned char smem[];
     int32_t *s_mm = reinterpret_cast<int32_t *>(smem);
     unsigned *s_hist = reinterpret_cast<unsigned *>(s_mm + A.levels);
-    uint32_t *s_conc = s_hist + A.levels;
     for (int i = threadIdx.x; i < A.levels; i += blockDim.x) {
         s_mm[i] = A.min_matches[i];
         s_hist[i] = 0;
     }
-    if (!A.lite)
-        for (int i = threadIdx.x; i < A.levels * A.conc_words; i += blockDim.x) s_conc[i] = A.conc_bits[i];
     __syncthreads();
 
     long long P = A.P;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     auto decide = [&]() {
         if (m < s_mm[j]) {
             finish(BLSH_PRUNED);                                   // Pr[S >= t | M] < eps
-        } else if (!A.lite && ((s_conc[j * A.conc_words + (m >> 5)] >> (m & 31)) & 1u)) {
+        } else if (!A.lite && ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u)) {
             finish(BLSH_ACCEPT);                                   // concentrated
         } else if (j + 1 == A.levels) {
             finish(A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX);
@@ -214,12 +214,23 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             step();
         }
     } else {
-        const long long qq = (long long)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
-        if (qq < P) {
-            const uint2 pr = __ldg(A.pairs + qq);
-            start_pair(qq, pr.x, pr.y);
+        // a fixed share of the pairs per warp: blocks of 32 / G pairs in
+        // grid-stride order; a warp moves to its next block when the
+        // slowest pair of the current one has stopped
+        // (the next block's pair indices are loaded before the current
+        // block is worked on)
+        const long long per_warp = 32 / G;
+        const long long stride = (((long long)gridDim.x * blockDim.x) >> 5) * per_warp;
+        long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per_warp;
+        uint2 nxt = make_uint2(0u, 0u);
+        if (base + grp < P) nxt = __ldg(A.pairs + base + grp);
+        for (; base < P; base += stride) {
+            const uint2 pr = nxt;
+            const long long qq = base + grp;
+            if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
+            if (qq < P) start_pair(qq, pr.x, pr.y);
+            while (__any_sync(kFull, active)) step();
         }
-        while (__any_sync(kFull, active)) step();
     }
 
     __syncthreads();
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
 template <int KIND, int G, int U, bool PERSIST>
 int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
     auto kern = verify_kernel<KIND, G, U, PERSIST>;
-    const size_t smem = sizeof(int32_t) * A.levels * 2 + (A.lite ? 0 : sizeof(uint32_t) * A.levels * A.conc_words);
+    const size_t smem = sizeof(int32_t) * A.levels * 2;
     if (smem > 48 * 1024) {
         if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "tables too large for shared memory");
         BLSH_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -245,9 +256,11 @@ int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cud
         grid = (long long)occ * ctx->sm_count;
         BLSH_CUDA(ctx, cudaMemsetAsync(&A.scratch->work, 0, sizeof(unsigned long long), s));
     } else {
+        // enough CTAs for two full waves; each warp then loops over its blocks
         const long long per_cta = plan.block / G;
         grid = (A.P + per_cta - 1) / per_cta;
-        if (grid > 0x7fffffffll) return blsh_fail(ctx, BLSH_EINVAL, "too many pairs for a plain launch");
+        const long long cap = (long long)ctx->sm_count * (2 * 2048 / plan.block);
+        if (grid > cap) grid = cap;
     }
     if (grid == 0) return BLSH_OK;
     kern<<<(unsigned)grid, plan.block, smem, s>>>(A);
