@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kThreads) compact_count(const uint8_t *status,
     long long lo, hi;
     cta_range(P, lo, hi);
     long long c = 0;
+#pragma unroll 4
     for (long long q0 = lo + 16ll * threadIdx.x; q0 < hi; q0 += 16ll * kThreads)
         c += __popc(kept16(status, q0, hi, mask, vec));
     long long total;
@@ -78,20 +79,28 @@ __global__ void __launch_bounds__(kThreads) compact_write(const uint8_t *status,
     if (threadIdx.x == 0) s_base = tot;
     __syncthreads();
     long long base = s_base;
-    for (long long t0 = lo; t0 < hi; t0 += kTile) {
-        // thread owns kPer consecutive items of the tile
-        const long long q0 = t0 + (long long)threadIdx.x * kPer;
-        const uint32_t bits = q0 < hi ? kept16(status, q0, hi, mask, vec) : 0u;
-        const int c = __popc(bits);
-        long long tile_total;
-        long long o = base + blsh_scan::block_exclusive<long long>((long long)c, &tile_total);
+    // kBatch tiles at a time: their loads are issued together, then each
+    // tile gets its block-wide prefix sum and writes its indices in order
+    constexpr int kBatch = 8;
+    for (long long t0 = lo; t0 < hi; t0 += (long long)kBatch * kTile) {
+        uint32_t bits[kBatch];
 #pragma unroll
-        for (int i = 0; i < kPer; ++i)
-            if ((bits >> i) & 1u) {
-                if (o < cap) out[o] = q0 + i;
+        for (int u = 0; u < kBatch; ++u) {
+            const long long q0 = t0 + (long long)u * kTile + (long long)threadIdx.x * kPer;
+            bits[u] = q0 < hi ? kept16(status, q0, hi, mask, vec) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (t0 + (long long)u * kTile >= hi) break;      // uniform across the CTA
+            const long long q0 = t0 + (long long)u * kTile + (long long)threadIdx.x * kPer;
+            long long tile_total;
+            long long o = base + blsh_scan::block_exclusive<long long>((long long)__popc(bits[u]), &tile_total);
+            for (uint32_t b = bits[u]; b; b &= b - 1) {
+                if (o < cap) out[o] = q0 + __ffs(b) - 1;
                 ++o;
             }
-        base += tile_total;
+            base += tile_total;
+        }
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         *n_out = base;

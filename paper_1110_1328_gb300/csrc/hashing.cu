@@ -328,10 +328,15 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
     if (zeros) atomicAdd(&scratch->counters[3], zeros);
 }
 
-// The queued signs: one warp per (row, bit).  Lanes load 32 nonzeros at a
-// time and form their exact FP64 products; every lane then adds them in row
-// order (shuffled one by one), so the sum is the FP64 row-order sum bit for
-// bit.  A nonnegative sum sets the bit (the word was written with it clear).
+// The queued signs: one warp per (row, bit).  The lanes form the row's exact
+// FP64 products (coalesced reads of the row, gathers of R) and sum them in
+// parallel, together with their magnitudes: that sum errs by at most
+// (n/32 + 5) u sum|p| (u = 2^-53), the oracle's row-order sum by at most
+// (n - 1) u sum|p|, so a parallel sum larger than 1.25 (2n + 8) u sum|p| has
+// the sign of the exact sum and of the oracle's.  Only the rest (exact zeros
+// and ties within that bound) are summed in row order, one product at a
+// time, which is the oracle's sum bit for bit.  A nonnegative sum sets the
+// bit (the word was written with it clear).
 template <typename RT>
 __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restrict__ queue,
                                                           const int64_t *__restrict__ indptr,
@@ -348,20 +353,40 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
          it += warps) {
         const uint2 rj = queue[it];
         const long long s = __ldg(indptr + rj.x), e = __ldg(indptr + rj.x + 1);
-        double d = 0.0;
-        for (long long c0 = s; c0 < e; c0 += 32) {
-            double p = 0.0;
-            if (c0 + lane < e) {
-                const uint32_t ix = __ldg(indices + c0 + lane);
-                if (ix < dim) p = (double)__ldg(values + c0 + lane) * r_fp64(R, (size_t)ix * bits + rj.y);
+        double ps = 0.0, qs = 0.0;
+        for (long long k = s + lane; k < e; k += 32) {
+            const uint32_t ix = __ldg(indices + k);
+            if (ix < dim) {
+                const double p = (double)__ldg(values + k) * r_fp64(R, (size_t)ix * bits + rj.y);
+                ps += p;
+                qs += fabs(p);
             }
-            const int cnt = (int)min(32ll, e - c0);
-            for (int l = 0; l < cnt; ++l) d += __shfl_sync(kFull, p, l);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ps += __shfl_xor_sync(kFull, ps, o);
+            qs += __shfl_xor_sync(kFull, qs, o);
+        }
+        const double len = (double)(e - s);
+        bool bit = ps >= 0.0;
+        if (!(fabs(ps) > 1.25 * (2.0 * len + 8.0) * 1.1102230246251565e-16 * qs + (2.0 * len + 8.0) * 5e-324)) {
+            // row order: lanes load 32 products at a time, every lane adds them in order
+            double d = 0.0;
+            for (long long c0 = s; c0 < e; c0 += 32) {
+                double p = 0.0;
+                if (c0 + lane < e) {
+                    const uint32_t ix = __ldg(indices + c0 + lane);
+                    if (ix < dim) p = (double)__ldg(values + c0 + lane) * r_fp64(R, (size_t)ix * bits + rj.y);
+                }
+                const int cnt = (int)min(32ll, e - c0);
+                for (int l = 0; l < cnt; ++l) d += __shfl_sync(kFull, p, l);
+            }
+            bit = d >= 0.0;
+            zeros += lane == 0 && d == 0.0;
         }
         if (lane == 0) {
-            if (d >= 0.0) atomicOr(sig + (size_t)rj.x * (bits >> 5) + (rj.y >> 5), 1u << (rj.y & 31));
+            if (bit) atomicOr(sig + (size_t)rj.x * (bits >> 5) + (rj.y >> 5), 1u << (rj.y & 31));
             ++done;
-            zeros += d == 0.0;
         }
     }
     if (lane == 0 && done) atomicAdd(&scratch->counters[2], done);
@@ -475,177 +500,6 @@ __global__ void __launch_bounds__(256) srp_sparse_q16_kernel(const int64_t *__re
             word |= __shfl_xor_sync(kFull, word, 1);
             word |= __shfl_xor_sync(kFull, word, 2);
             if ((lane & 3) == 0) sig[(size_t)row * words + ((t + g * T) >> 2)] = word;
-        }
-    }
-    if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
-    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
-    if (zeros) atomicAdd(&scratch->counters[3], zeros);
-}
-
-// Slice-major forms of the two kernels above.  The bits are cut into slices
-// of 128 V (float) or 256 V (two-byte) columns; one warp computes one slice
-// of one row, and the work items run slice by slice (item = slice * N +
-// row), so the rows of R touched at any time are those of one slice: dim *
-// 512 V bytes, which stays in L2 where the whole of R would not.  The sums,
-// bounds and the queue of undecided signs are those of the row-wise kernels.
-template <int V>
-__global__ void __launch_bounds__(256) srp_slice_kernel(const int64_t *__restrict__ indptr,
-                                                        const uint32_t *__restrict__ indices,
-                                                        const float *__restrict__ values, long long N,
-                                                        const float *__restrict__ R, long long dim, int bits,
-                                                        uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
-                                                        uint2 *__restrict__ queue) {
-    constexpr int S = 128 * V;
-    const int lane = threadIdx.x & 31;
-    const int words = bits >> 5;
-    const long long slices = bits / S;
-    const long long items = slices * N;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-        const int sl = (int)(it / N);
-        const long long row = it - (long long)sl * N;
-        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-        float acc[4 * V], mag[4 * V];
-#pragma unroll
-        for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
-        for (long long k = s; k < e; ++k) {
-            uint32_t ix = __ldg(indices + k);
-            float v = __ldg(values + k);
-            if (ix >= dim) {   // malformed row: counted, contributes nothing
-                bad += lane == 0 && sl == 0;
-                ix = 0;
-                v = 0.0f;
-            }
-            const float av = fabsf(v);
-            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + (size_t)sl * S) + lane;
-#pragma unroll
-            for (int g = 0; g < V; ++g) {
-                const float4 r = __ldg(Rrow + g * 32);
-                acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
-                acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
-                acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
-                acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
-                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
-                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
-                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
-                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
-            }
-        }
-        const float n = (float)(e - s);
-        const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
-#pragma unroll
-        for (int g = 0; g < V; ++g) {
-            uint32_t nib = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int u = 4 * g + c;
-                const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
-                bool bit;
-                if (!long_row && fabsf(acc[u]) > bound) {
-                    bit = acc[u] >= 0.0f;
-                } else {
-                    const uint32_t j = sl * S + 4 * (g * 32 + lane) + c;
-                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
-                    if (slot < BLSH_RECHECK_CAP) {
-                        queue[slot] = make_uint2((uint32_t)row, j);
-                        bit = false;
-                    } else {
-                        const double d = srp_recheck_fp64<float>(indices, values, s, e, R, dim, bits, j);
-                        bit = d >= 0.0;
-                        ++rechecked;
-                        zeros += d == 0.0;
-                    }
-                }
-                nib |= (uint32_t)bit << c;
-            }
-            uint32_t word = nib << (4 * (lane & 7));
-            word |= __shfl_xor_sync(kFull, word, 1);
-            word |= __shfl_xor_sync(kFull, word, 2);
-            word |= __shfl_xor_sync(kFull, word, 4);
-            if ((lane & 7) == 0) sig[(size_t)row * words + ((sl * S + 4 * (g * 32 + lane)) >> 5)] = word;
-        }
-    }
-    if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
-    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
-    if (zeros) atomicAdd(&scratch->counters[3], zeros);
-}
-
-template <int V>
-__global__ void __launch_bounds__(256) srp_slice_q16_kernel(const int64_t *__restrict__ indptr,
-                                                            const uint32_t *__restrict__ indices,
-                                                            const float *__restrict__ values, long long N,
-                                                            const uint16_t *__restrict__ R, long long dim, int bits,
-                                                            uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
-                                                            uint2 *__restrict__ queue) {
-    constexpr int S = 256 * V;
-    const int lane = threadIdx.x & 31;
-    const int words = bits >> 5;
-    const long long slices = bits / S;
-    const long long items = slices * N;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    for (long long it = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-        const int sl = (int)(it / N);
-        const long long row = it - (long long)sl * N;
-        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-        float acc[8 * V];
-#pragma unroll
-        for (int u = 0; u < 8 * V; ++u) acc[u] = 0.0f;
-        float asum = 0.0f;
-        for (long long k = s; k < e; ++k) {
-            uint32_t ix = __ldg(indices + k);
-            float v = __ldg(values + k);
-            if (ix >= dim) {
-                bad += lane == 0 && sl == 0;
-                ix = 0;
-                v = 0.0f;
-            }
-            asum += fabsf(v);
-            const uint4 *Rrow = reinterpret_cast<const uint4 *>(R + (size_t)ix * bits + (size_t)sl * S) + lane;
-#pragma unroll
-            for (int g = 0; g < V; ++g) {
-                const uint4 w = __ldg(Rrow + g * 32);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    acc[8 * g + 2 * c] = __fmaf_rn(v, q16_lo(ws[c]), acc[8 * g + 2 * c]);
-                    acc[8 * g + 2 * c + 1] = __fmaf_rn(v, q16_hi(ws[c]), acc[8 * g + 2 * c + 1]);
-                }
-            }
-        }
-        const float n = (float)(e - s);
-        const float bound = n * 5.9604644775390625e-8f > 0.05f
-                                ? INFINITY
-                                : 1.25f * n * 5.9604644775390625e-8f * 32768.0f * asum + n * 1.4e-45f;
-#pragma unroll
-        for (int g = 0; g < V; ++g) {
-            uint32_t byte = 0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int u = 8 * g + c;
-                bool bit;
-                if (fabsf(acc[u]) > bound) {
-                    bit = acc[u] >= 0.0f;
-                } else {
-                    const uint32_t j = sl * S + 8 * (g * 32 + lane) + c;
-                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
-                    if (slot < BLSH_RECHECK_CAP) {
-                        queue[slot] = make_uint2((uint32_t)row, j);
-                        bit = false;
-                    } else {
-                        const double d = srp_recheck_fp64<uint16_t>(indices, values, s, e, R, dim, bits, j);
-                        bit = d >= 0.0;
-                        ++rechecked;
-                        zeros += d == 0.0;
-                    }
-                }
-                byte |= (uint32_t)bit << c;
-            }
-            uint32_t word = byte << (8 * (lane & 3));
-            word |= __shfl_xor_sync(kFull, word, 1);
-            word |= __shfl_xor_sync(kFull, word, 2);
-            if ((lane & 3) == 0) sig[(size_t)row * words + ((sl * S + 8 * (g * 32 + lane)) >> 5)] = word;
         }
     }
     if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);

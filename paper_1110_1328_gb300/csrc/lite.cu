@@ -38,8 +38,33 @@ struct LiteArgs {
 
 constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab of the work counter
 
+// rn(u v 2^60) for two floats, by integer arithmetic: u = mu 2^eu and
+// v = mv 2^ev with 24-bit integer mantissas, so u v 2^60 = mu mv 2^(eu+ev+60)
+// and the 48-bit product is shifted with round-half-to-even (symmetric, as
+// the FP64 conversion rounds).  The same value as the FP64 expression
+// rn((double)u * (double)v * 2^60) (the product of two floats is exact in
+// FP64); that expression is kept for |u v| >= 2^3, where the result would not
+// fit and the conversion saturates.
 __device__ __forceinline__ long long fixed_term(float u, float v) {
-    return __double2ll_rn(__dmul_rn(__dmul_rn((double)u, (double)v), kTwo60));
+    const uint32_t bu = __float_as_uint(u), bv = __float_as_uint(v);
+    int eu = (int)((bu >> 23) & 0xffu), ev = (int)((bv >> 23) & 0xffu);
+    uint32_t mu = bu & 0x7fffffu, mv = bv & 0x7fffffu;
+    if (eu) mu |= 0x800000u; else eu = 1;   // subnormals: exponent 1 - 150
+    if (ev) mv |= 0x800000u; else ev = 1;
+    const unsigned long long prod = (unsigned long long)mu * mv;   // < 2^48
+    const int sh = eu + ev - 300 + 60;                               // u v 2^60 = prod 2^sh
+    unsigned long long r;
+    if (sh >= 0) {
+        if (sh > 15) return __double2ll_rn(__dmul_rn(__dmul_rn((double)u, (double)v), kTwo60));
+        r = prod << sh;
+    } else if (-sh > 48) {
+        r = 0;                                                       // below half of 2^0
+    } else {
+        const int k = -sh;
+        const unsigned long long q = prod >> k, rem = prod & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+        r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    }
+    return ((bu ^ bv) >> 31) ? -(long long)r : (long long)r;
 }
 
 __device__ __forceinline__ long long warp_sum(long long v) {
@@ -48,15 +73,18 @@ __device__ __forceinline__ long long warp_sum(long long v) {
     return v;
 }
 
-// First position in L[0..n) holding a value >= v.
+// First position in L[0..n) holding a value >= v (L in global or shared
+// memory).
 __device__ __forceinline__ long long lower_bound(const uint32_t *L, long long n, uint32_t v) {
     long long lo = 0, hi = n;
     while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
-        if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
+        if (L[mid] < v) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
+
+constexpr int kLiteStage = 512;   // longer-row elements a warp stages in shared memory
 
 template <bool COSINE>
 __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
@@ -66,6 +94,11 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
         P = pd < 0 ? 0 : (pd < P ? pd : P);
     }
     const int lane = threadIdx.x & 31;
+    // per warp: the longer row's indices and values, when it has at most
+    // kLiteStage elements (binary searches then run in shared memory)
+    extern __shared__ uint32_t lite_smem[];
+    uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
+    float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
     auto exact = [&](long long q) {
             const uint2 pr = __ldg(A.pairs + q);
             const long long ax = __ldg(A.indptr + pr.x), ex = __ldg(A.indptr + pr.x + 1);
@@ -75,13 +108,24 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
             long long s0 = ax, ns = na, l0 = ay, nl = nb;
             if (nb < na) { s0 = ay; ns = nb; l0 = ax; nl = na; }
             const uint32_t *Lidx = A.indices + l0;
+            const float *Lval = COSINE ? A.values + l0 : nullptr;
+            __syncwarp();                                  // the previous pair is done with the stage
+            if (nl <= kLiteStage) {
+                for (long long i = lane; i < nl; i += 32) {
+                    w_idx[i] = __ldg(A.indices + l0 + i);
+                    if (COSINE) w_val[i] = __ldg(A.values + l0 + i);
+                }
+                __syncwarp();
+                Lidx = w_idx;
+                if (COSINE) Lval = w_val;
+            }
             double s;
             if (!COSINE) {
                 long long inter = 0;
                 for (long long i = lane; i < ns; i += 32) {
                     const uint32_t v = __ldg(A.indices + s0 + i);
                     const long long pos = lower_bound(Lidx, nl, v);
-                    inter += (pos < nl && __ldg(Lidx + pos) == v);
+                    inter += (pos < nl && Lidx[pos] == v);
                 }
                 inter = warp_sum(inter);
                 const long long uni = na + nb - inter;
@@ -99,8 +143,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 for (long long i = lane; i < ns; i += 32) {
                     const uint32_t v = __ldg(A.indices + s0 + i);
                     const long long pos = lower_bound(Lidx, nl, v);
-                    if (pos < nl && __ldg(Lidx + pos) == v)
-                        D += fixed_term(__ldg(A.values + s0 + i), __ldg(A.values + l0 + pos));
+                    if (pos < nl && Lidx[pos] == v) D += fixed_term(__ldg(A.values + s0 + i), Lval[pos]);
                 }
                 D = warp_sum(D);
                 Nx = warp_sum(Nx);
@@ -226,12 +269,13 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     L.vec = blsh_aligned(status, 16);
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, sizeof(unsigned long long), s));
     int occ = 0;
+    const size_t smem = 8 * 2 * kLiteStage * sizeof(uint32_t);   // 32 KB per CTA of 8 warps
     if (values) {
-        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<true>, 256, 0));
-        lite_exact_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, 0, s>>>(L);
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<true>, 256, smem));
+        lite_exact_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
     } else {
-        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<false>, 256, 0));
-        lite_exact_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, 0, s>>>(L);
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<false>, 256, smem));
+        lite_exact_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
     }
     BLSH_LAUNCHED(ctx, "lite exact-similarity kernel");
     return BLSH_OK;

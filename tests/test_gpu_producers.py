@@ -268,6 +268,40 @@ def test_lite_cosine_bit_exact(B, ctx):
     assert (want.status == O.LITE_ACCEPT).sum() > 50
 
 
+def test_lite_cosine_fixed_point_edges(B, ctx):
+    """Lite's exact cosine on rows built to exercise the fixed-point products:
+    ties at half (1.5 and 2.5 after scaling), negative terms, subnormals,
+    products far below 2^-60, rows longer than the shared-memory stage (600
+    and 700 terms), and signed unit-norm rows of mixed magnitudes."""
+    rng = np.random.default_rng(7)
+    rows, vals = [], []
+    t = np.float32(2.0 ** -30)
+    rows.append(np.arange(8)); vals.append(np.array([1.5 * 2 ** -30, 2.5 * 2 ** -30, -2.5 * 2 ** -30, 3.5 * 2 ** -30,
+                                                     1e-40, -3e-39, 0.25, -0.5], np.float32))
+    rows.append(np.arange(8)); vals.append(np.array([t, t, t, -t, 1e-38, 2e-38, 1e-20, 0.125], np.float32))
+    for n in (600, 700, 40, 90):
+        idx = np.sort(rng.choice(1000, n, replace=False))
+        v = rng.standard_normal(n) * rng.choice([1e-12, 1e-3, 1.0], n)
+        rows.append(idx); vals.append((v / np.linalg.norm(v)).astype(np.float32))   # rows of norm 1
+    lens = [len(r) for r in rows]
+    csr = synth.CSR(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64), np.concatenate(rows).astype(np.uint32),
+                    np.concatenate(vals).astype(np.float32), 1000)
+    n_obj = len(rows)
+    sig = np.zeros((n_obj, 8), np.uint32)                 # identical signatures: every pair survives pruning
+    pairs = np.array([(i, j) for i in range(n_obj) for j in range(i + 1, n_obj)], np.uint32)
+    p = O.Params(kind=O.COSINE, n_max=256, h=128, t=0.1)
+    want = O.verify_lite(O.tables(p), pairs, sig, csr)
+    assert np.all(want.status != O.PRUNED)
+    tab = B.blsh_tables_build(ctx, B.make_params(kind=1, t=0.1, n_max=256, h=128))
+    ip, ix, val = csr_dev(csr)
+    st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
+    sim = torch.zeros(len(pairs), dtype=torch.float64, device=dev)
+    B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, val, st, sim)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy(), want.status)
+    assert np.array_equal(sim.cpu().numpy(), want.sim)     # bit-identical doubles
+
+
 @pytest.mark.parametrize("P", [0, 1, 31, 4097, 1_000_003])
 def test_compact_stable_and_exact(B, ctx, P):
     rng = np.random.default_rng(P)
