@@ -57,7 +57,7 @@ WORKLOADS = {
                            n_max=2048, k=32, h=128, seed=2,
                            text="cosine-small shape at 6,000 vectors over dim 30,000 (R = 245 MB > L2), for "
                                 "ncu captures"),
-    "verify-large": dict(kind=1, n=5_000_000, bits=2048, pairs=200_000_000, t=0.7, n_max=2048, k=32, h=128,
+    "verify-large": dict(kind=1, gpu_only=True, n=5_000_000, bits=2048, pairs=200_000_000, t=0.7, n_max=2048, k=32, h=128,
                          seed=9, text="verification only: 5,000,000 random 2,048-bit signatures (1.3 GB) and "
                                       "200,000,000 uniform random candidate pairs (HBM-resident, no reuse)"),
     "jaccard-small": dict(kind=0, n=2000, vocab=10000, n_hashes=256, rows=8, bands=32, t=0.7, n_max=256, k=32,
@@ -71,6 +71,8 @@ WORKLOADS = {
                            "10,000-component Gaussian mixture (noise norm 0.15), 1,024 SRP bits by the BF16 "
                            "tensor-core projection with FP32/FP64 recheck below 1e-3 |x||r|, banding 16x64, t=0.8 "
                            "(BayesLSH; no Lite pass)"),
+    "sweep": dict(kind=1, seed=2, gpu_only=True, text="cosine-small candidates (2.66e7 pairs), gamma, delta, epsilon each "
+                                         "over 0.01..0.09 with the others at 0.05, t = 0.7"),
     "batching": dict(kind=0, n=1_000_000, n_hashes=256, rows=3, bands=32, t=0.5, n_max=256, k=32, h=64, seed=3,
                      text="jaccard, BayesLSH + Lite: Chung-Lu graph N=1,000,000, exponent 2.1, mean degree 30, "
                           "256 minhashes, banding 3x32 (power-law buckets, about 1e8 candidate pairs), t=0.5"),
@@ -189,8 +191,13 @@ class Pipeline:
                                    self.ws)
 
     def verify(self):
-        self.B.blsh_verify(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m, self.est,
-                           self.hist, P_dev=self.n_pairs)
+        if self.with_lite:   # Algorithms 1 and 2 in one pass over the candidates
+            self.B.blsh_verify_both(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
+                                    self.est, self.hist, self.indptr, self.indices, self.values, self.lstatus,
+                                    self.sim, P_dev=self.n_pairs)
+        else:
+            self.B.blsh_verify(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
+                               self.est, self.hist, P_dev=self.n_pairs)
 
     def lite(self):
         self.B.blsh_verify_lite(self.ctx, self.tab, self.pairs, self.sig, self.indptr, self.indices, self.values,
@@ -200,13 +207,16 @@ class Pipeline:
         B = self.B
         B.blsh_compact(self.ctx, self.status, (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX), self.out1, self.n_out[0:1],
                        P_dev=self.n_pairs)
-        if "lite" in self.STAGES:
+        if self.with_lite:
             B.blsh_compact(self.ctx, self.lstatus, 1 << B.LITE_ACCEPT, self.out2, self.n_out[1:2],
                            P_dev=self.n_pairs)
 
     @property
-    def STAGES(self):
-        return tuple(self.w.get("stages", ("hash", "band", "verify", "lite", "compact")))
+    def with_lite(self):
+        return "lite" in self.w.get("stages", ("lite",))
+
+    # the stages of a step ("verify" runs both algorithms when the workload has Lite)
+    STAGES = ("hash", "band", "verify", "compact")
 
     def step(self):
         for s in self.STAGES:
@@ -302,9 +312,11 @@ def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 
         ev[2].record(stream)
         B.blsh_verify(pipe.ctx, pipe.tab, pipe.pairs, pipe.sig, pipe.status, pipe.n_used, pipe.m, pipe.est,
                       pipe.hist, P_dev=pipe.n_pairs, plan=plain)
-        ev[3].record(stream)
-        if "lite" in pipe.STAGES:
+        if pipe.with_lite:   # Algorithm 2 as its own pass, under the same plain plan
+            B.blsh_set_plan(pipe.ctx, pipe.tab, plain)
             pipe.lite()
+            B.blsh_set_plan(pipe.ctx, pipe.tab, pipe.plan)
+        ev[3].record(stream)
         pipe.compact()
         ev[4].record(stream)
         torch.cuda.synchronize()
@@ -314,7 +326,8 @@ def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("plain-form step failed")
     t = {k: float(np.mean(v)) for k, v in times.items()}
-    return {"form": "eager launches, plain verify launch" + (", FP32 CUDA-core projection" if pipe.dense else ""),
+    return {"form": "eager launches, plain verify launches, Algorithms 1 and 2 as separate passes"
+                    + (", FP32 CUDA-core projection" if pipe.dense else ""),
             "step_ms": round(t["step"], 4), "verify_ms": round(t["verify"], 4), "hash_ms": round(t["hash"], 4),
             "speedup_step": round(t["step"] / step_ms, 3),
             "speedup_verify": round(t["verify"] / stage_ms["verify"], 3),
@@ -538,7 +551,8 @@ def run_ours(args, w):
         nnz = int(objs.indptr[-1])
         hash_bytes = nnz * 4 + w["n"] * (8 + 4 * w["n_hashes"])
         hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
-    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P)
+    # the fused pass also writes Algorithm 2's status (1 B) and similarity (8 B) per pair
+    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P) + (9 * pipe.P if pipe.with_lite else 0)
     key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
     hash_kernel = ("srp_dense_tc_kernel" if pipe.dense else
                    "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else
@@ -547,7 +561,8 @@ def run_ours(args, w):
         "hash": {"kernel": hash_kernel, "bytes": hash_bytes},
         "band": {"kernel": "emit_kernel + radix sort", "bytes": band_bytes(pipe.N, w["bands"], pipe.P,
                                                                              (key_bits + 7) // 8)},
-        "verify": {"kernel": "verify_kernel", "bytes": vbytes},
+        "verify": {"kernel": "verify_kernel (Algorithms 1 and 2 in one pass)" if pipe.with_lite else "verify_kernel",
+                   "bytes": vbytes},
     }
     if unique is not None:
         # the least DRAM traffic of the SRP launch: each distinct row of R once;
@@ -607,6 +622,13 @@ def run_ours(args, w):
         "vs_plain": vs_plain,
         "srp_signs": rechecks,
     }
+    if args.profile_step:
+        # one more eager step inside an NVTX range, for ncu --nvtx-include "blsh_step/"
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("blsh_step")
+        pipe.step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, objs, hashp, pipe.P)
     elif rank == 0 and world > 1:
@@ -616,6 +638,85 @@ def run_ours(args, w):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_sweep(args, w):
+    """The paper's parameter study (Section 5, "Effect of varying parameters"):
+    gamma, delta and epsilon varied one at a time over 0.01 .. 0.09 with the
+    other two at 0.05, Algorithm 1 on the cosine-small candidates at t = 0.7;
+    per setting the verification time and the quality measure the study
+    reports (fraction of output estimates off by more than 0.05, mean error,
+    recall).  The exact similarity of every candidate comes from Algorithm 2's
+    exact pass with a threshold that prunes nothing; the fixed-n estimator
+    over all 2,048 hashes ("LSH Approx") is measured beside it."""
+    import torch
+
+    import paper_1110_1328_gb300 as B
+    dev = torch.device("cuda", 0)
+    base = WORKLOADS["cosine-small"]
+    objs, R = make_inputs(base)
+    pipe = Pipeline(B, torch, base, objs, R, dev)
+    pipe.hash()
+    pipe.band()
+    assert B.blsh_status(pipe.ctx) == 0
+    P = pipe.P
+    pairs, sig = pipe.pairs[:P], pipe.sig
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    # exact similarity of every candidate: Lite with t = 0.01 prunes nothing
+    tab0 = B.blsh_tables_build(pipe.ctx, B.make_params(kind=1, t=0.01, k=32, n_max=2048, h=32))
+    lst = torch.zeros(P, dtype=torch.uint8, device=dev)
+    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    exact_ms = timed(lambda: B.blsh_verify_lite(pipe.ctx, tab0, pairs, sig, pipe.indptr, pipe.indices, pipe.values,
+                                                lst, sim))
+    assert B.blsh_status(pipe.ctx) == 0
+    s_exact = sim.cpu().numpy()
+    assert not np.isnan(s_exact).any()
+    t = 0.7
+    truth = s_exact >= t
+    n_true = int(truth.sum())
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    est = torch.zeros(P, dtype=torch.float32, device=dev)
+    nu = torch.zeros(P, dtype=torch.int16, device=dev)
+    rows = []
+    for name in ("gamma", "delta", "eps"):
+        for v in (0.01, 0.03, 0.05, 0.07, 0.09):
+            kw = dict(gamma=0.05, delta=0.05, eps=0.05)
+            kw[name] = v
+            tab = B.blsh_tables_build(pipe.ctx, B.make_params(kind=1, t=t, k=32, n_max=2048, h=128, **kw))
+            ms = timed(lambda: B.blsh_verify(pipe.ctx, tab, pairs, sig, st, nu, None, est))
+            assert B.blsh_status(pipe.ctx) == 0
+            out = np.isin(st.cpu().numpy(), (B.ACCEPT, B.ACCEPT_AT_MAX))
+            err = np.abs(est.cpu().numpy()[out].astype(np.float64) - s_exact[out])
+            rows.append({"vary": name, "value": v, "verify_ms": round(ms, 4), "output_pairs": int(out.sum()),
+                         "frac_err_gt_0.05": round(float((err > 0.05).mean()), 5) if out.any() else None,
+                         "mean_err": round(float(err.mean()), 5) if out.any() else None,
+                         "recall": round(float((out & truth).sum() / max(n_true, 1)), 5),
+                         "mean_hashes": round(float(nu.cpu().numpy().view(np.uint16).mean()), 1)})
+    # the fixed-n estimator over all 2,048 hashes
+    m = torch.zeros(P, dtype=torch.int16, device=dev)
+    keep = torch.zeros(P, dtype=torch.uint8, device=dev)
+    ms = timed(lambda: B.blsh_estimate_mle(pipe.ctx, 1, 2048, t, pairs, sig, m, est, keep))
+    assert B.blsh_status(pipe.ctx) == 0
+    out = keep.cpu().numpy() == 1
+    err = np.abs(est.cpu().numpy()[out].astype(np.float64) - s_exact[out])
+    approx = {"verify_ms": round(ms, 4), "output_pairs": int(out.sum()),
+              "frac_err_gt_0.05": round(float((err > 0.05).mean()), 5), "mean_err": round(float(err.mean()), 5),
+              "recall": round(float((out & truth).sum() / max(n_true, 1)), 5)}
+    print(json.dumps({"metric": "parameter study (gamma, delta, epsilon) on cosine-small candidates, t = 0.7",
+                      "candidate_pairs": P, "true_pairs": n_true, "exact_all_ms": round(exact_ms, 4),
+                      "lsh_approx_2048": approx, "bayeslsh": rows,
+                      "config": {"workload": "sweep: " + w["text"]}}), flush=True)
 
 
 def run_verify_large(args, w):
@@ -727,8 +828,8 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if "pairs" in w:
-        print(json.dumps({"impl": "reference", "unavailable": "verify-large is a GPU measurement workload; "
+    if w.get("gpu_only"):
+        print(json.dumps({"impl": "reference", "unavailable": "a GPU measurement workload; "
                                                                "the oracle arm runs on the pipeline workloads"}))
         return
     import oracle as O
@@ -767,6 +868,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one extra eager step inside the NVTX range blsh_step (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -775,6 +878,8 @@ def main():
         run_reference(args, w)
     elif args.workload == "verify-large":
         run_verify_large(args, w)
+    elif args.workload == "sweep":
+        run_sweep(args, w)
     else:
         run_ours(args, w)
 

@@ -265,6 +265,11 @@ BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *
                 const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used,
                 uint16_t *m, float *est, uint64_t *stop_hist, void *stream);
 
+/* Stores `plan` as the launch plan blsh_verify, blsh_verify_lite and
+ * blsh_verify_both use for these tables (what blsh_autotune does with the
+ * plan it finds).  BLSH_EINVAL for a plan invalid for the tables' kind and k. */
+BLSH_API int blsh_set_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan);
+
 /* The same with an explicit launch plan. */
 BLSH_API int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan, const uint32_t *pairs,
                      int64_t P, const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
@@ -286,6 +291,18 @@ BLSH_API int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint3
                      const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
                      const int64_t *indptr, const uint32_t *indices, const float *values, uint8_t *status,
                      uint16_t *n_used, double *sim, void *stream);
+
+/* Algorithms 1 and 2 over the same candidate pairs in one pass: the outputs
+ * of blsh_verify (status, n_used, m, est, stop_hist) and of blsh_verify_lite
+ * (lite_status, lite_n_used, sim), identical to the two calls made one after
+ * the other, with each pair's indices and signature words read once (Algorithm
+ * 2's pruning test over the first h hashes is the test Algorithm 1 makes on
+ * them).  Arguments and errors as those two calls; lite_n_used may be NULL. */
+BLSH_API int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                              const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                              uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                              const int64_t *indptr, const uint32_t *indices, const float *values,
+                              uint8_t *lite_status, uint16_t *lite_n_used, double *sim, void *stream);
 
 /* Times candidate plans on the given inputs (outputs are overwritten) and
  * stores the fastest for `tab` in the context; *best (host) receives it.

@@ -77,6 +77,8 @@ def lib():
             "blsh_verify": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_plan": ([p, p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_lite": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p], C.c_int),
+    "blsh_verify_both": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
+    "blsh_set_plan": ([p, p, p], C.c_int),
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
             "blsh_compact_noalloc": ([p, i64, p, u32, p, i64, p, p], C.c_int),
@@ -334,6 +336,26 @@ def blsh_verify_lite(ctx: Context, tab: Tables, pairs, sig, indptr, indices, val
     rc = lib().blsh_verify_lite(ctx.handle, tab.handle, _dev(pairs), P, _dev(P_dev, torch.int64), _dev(sig), N, W,
                                 _dev(indptr, torch.int64), _dev(indices), _dev(values, torch.float32),
                                 _dev(status, torch.uint8), _dev(n_used), _dev(sim, torch.float64),
+                                _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_set_plan(ctx: Context, tab: Tables, plan: blsh_plan):
+    """Make `plan` the launch plan used for these tables."""
+    _check(lib().blsh_set_plan(ctx.handle, tab.handle, C.byref(plan)), ctx)
+
+
+def blsh_verify_both(ctx: Context, tab: Tables, pairs, sig, status, n_used, m, est, stop_hist, indptr, indices,
+                     values, lite_status, sim, lite_n_used=None, P_dev=None, stream=None):
+    """Algorithms 1 and 2 over the same pairs in one pass (outputs of
+    blsh_verify and blsh_verify_lite)."""
+    P = pairs.shape[0]
+    N, W = sig.shape
+    rc = lib().blsh_verify_both(ctx.handle, tab.handle, _dev(pairs), P, _dev(P_dev, torch.int64), _dev(sig), N, W,
+                                _dev(status, torch.uint8), _dev(n_used), _dev(m), _dev(est, torch.float32),
+                                _dev(stop_hist), _dev(indptr, torch.int64), _dev(indices),
+                                None if values is None else _dev(values, torch.float32),
+                                _dev(lite_status, torch.uint8), _dev(lite_n_used), _dev(sim, torch.float64),
                                 _stream(stream))
     _check(rc, ctx)
 

@@ -25,6 +25,7 @@ struct blsh_dev_scratch {
     unsigned long long counters[4];    // bad pairs, truncations, SRP rechecks, SRP zeros
     unsigned long long work;           // verify: next pair handed out
     unsigned long long work2;          // lite: next survivor tile handed out
+    unsigned long long work3;          // lite: survivors queued
     unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
 };

@@ -3,17 +3,21 @@
 // Pass 1 is the verification kernel of verify.cu in its Lite form: the
 // pruning loop over at most h hashes, no concentration test; an unpruned
 // pair is marked as a survivor in its status byte.  Pass 2 (this file) gives
-// every survivor its exact similarity: persistent warps take 8,192 statuses at
-// a time from a work counter, and the warp computes each survivor's
-// similarity cooperatively by intersecting the two sorted index lists (each
-// lane binary-searches elements of the shorter row in the longer one).
+// every survivor its exact similarity: the survivors are collected into a
+// queue (one atomic per tile of 512 statuses) and warps take them in
+// grid-stride order, so the many survivors of one bucket of near-duplicates
+// spread over the GPU; a warp computes a survivor's similarity
+// cooperatively by intersecting the two sorted index lists (each lane
+// binary-searches elements of the shorter row in the longer one, staged in
+// shared memory when it is short).  Survivors beyond the queue's capacity
+// are found by a scan of the statuses in tiles handed out by a counter.
 //
 //   Jaccard: s = |A n B| / |A u B|, one FP64 division.
 //   Cosine:  s = D / sqrt(Nx * Ny) with D = sum over common indices of
 //            rn(x_i * y_i * 2^60), Nx = sum rn(x_i^2 * 2^60), Ny likewise,
-//            each term the FP64 product (exact for two floats) rounded to an
-//            integer and added in int64, so the sums do not depend on the
-//            order the lanes add them in.
+//            each term the exact product of two floats rounded to an
+//            integer (formed with integer arithmetic) and added in int64, so
+//            the sums do not depend on the order the lanes add them in.
 // A pair is kept iff s > t.
 #include "verify.cuh"
 
@@ -36,7 +40,7 @@ struct LiteArgs {
     int vec;                  // status is 16-byte aligned
 };
 
-constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab of the work counter
+constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab (this pass sees only survivors the queue missed)
 
 // rn(u v 2^60) for two floats, by integer arithmetic: u = mu 2^eu and
 // v = mv 2^ev with 24-bit integer mantissas, so u v 2^60 = mu mv 2^(eu+ev+60)
@@ -86,20 +90,11 @@ __device__ __forceinline__ long long lower_bound(const uint32_t *L, long long n,
 
 constexpr int kLiteStage = 512;   // longer-row elements a warp stages in shared memory
 
+// The exact similarity of survivor q (the whole warp; w_idx, w_val: the
+// warp's staging area).
 template <bool COSINE>
-__global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
-    long long P = A.P;
-    if (A.P_dev) {
-        const long long pd = *A.P_dev;
-        P = pd < 0 ? 0 : (pd < P ? pd : P);
-    }
+__device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, uint32_t *w_idx, float *w_val) {
     const int lane = threadIdx.x & 31;
-    // per warp: the longer row's indices and values, when it has at most
-    // kLiteStage elements (binary searches then run in shared memory)
-    extern __shared__ uint32_t lite_smem[];
-    uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
-    float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
-    auto exact = [&](long long q) {
             const uint2 pr = __ldg(A.pairs + q);
             const long long ax = __ldg(A.indptr + pr.x), ex = __ldg(A.indptr + pr.x + 1);
             const long long ay = __ldg(A.indptr + pr.y), ey = __ldg(A.indptr + pr.y + 1);
@@ -110,7 +105,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
             const uint32_t *Lidx = A.indices + l0;
             const float *Lval = COSINE ? A.values + l0 : nullptr;
             __syncwarp();                                  // the previous pair is done with the stage
-            if (nl <= kLiteStage) {
+            if (nl <= kLiteStage && ns >= 32) {                 // worth staging: every lane searches
                 for (long long i = lane; i < nl; i += 32) {
                     w_idx[i] = __ldg(A.indices + l0 + i);
                     if (COSINE) w_val[i] = __ldg(A.values + l0 + i);
@@ -159,7 +154,21 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 A.sim[q] = s;
                 A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
             }
-    };
+}
+
+template <bool COSINE>
+__global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const int lane = threadIdx.x & 31;
+    // per warp: the longer row's indices and values, when it has at most
+    // kLiteStage elements (binary searches then run in shared memory)
+    extern __shared__ uint32_t lite_smem[];
+    uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
+    float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
     // A warp takes kLiteGrab tiles of 512 statuses per grab of the work
     // counter; a lane reads 16 statuses with one 16-byte load, and the warp
     // then computes the survivors of the tile one after the other.
@@ -192,12 +201,75 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 while (bits) {
                     const int i = __ffs(bits) - 1;
                     bits &= bits - 1;
-                    exact(q0 + 16ll * l + i);
+                    lite_exact_pair<COSINE>(A, q0 + 16ll * l + i, w_idx, w_val);
                 }
             }
         }
     }
 }
+
+// Survivors into a queue (the context's work queue, BLSH_RECHECK_CAP
+// entries): warps scan tiles of 512 statuses in grid-stride order and append
+// their survivors' indices with one atomic per tile.  Survivors beyond the
+// queue are left for lite_exact_kernel.
+__global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, unsigned long long *queue) {
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long q0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 512; q0 < P; q0 += nwarps * 512) {
+        const long long qs = q0 + 16ll * lane;
+        uint32_t surv = 0;
+        if (A.vec && qs + 16 <= P) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(A.status + qs));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                surv |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_LITE_SURVIVOR) << i;
+        } else {
+            for (int i = 0; i < 16; ++i)
+                if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv |= 1u << i;
+        }
+        const unsigned c = __popc(surv);
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&A.scratch->work3, (unsigned long long)total);
+        base = __shfl_sync(kFull, base, 31);
+        unsigned long long slot = base + incl - c;
+        for (uint32_t b = surv; b; b &= b - 1, ++slot)
+            if (slot < BLSH_RECHECK_CAP) queue[slot] = (unsigned long long)(qs + __ffs(b) - 1);
+    }
+}
+
+// The queued survivors, one per warp at a time in grid-stride order: the
+// survivors of one dense tile (a bucket of near-duplicates) spread over many
+// warps.
+template <bool COSINE>
+__global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const unsigned long long *queue) {
+    const unsigned long long total = A.scratch->work3;
+    const unsigned long long n = total < BLSH_RECHECK_CAP ? total : BLSH_RECHECK_CAP;
+    extern __shared__ uint32_t lite_smem[];
+    uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
+    float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long it = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n;
+         it += nwarps)
+        lite_exact_pair<COSINE>(A, (long long)queue[it], w_idx, w_val);
+}
+
+int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, const int64_t *indptr,
+                    const uint32_t *indices, const float *values, double t, uint8_t *status, double *sim,
+                    cudaStream_t s);
 
 }  // namespace
 
@@ -245,38 +317,91 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     A.sim_out = sim;
     A.stop_hist = nullptr;
     A.scratch = ctx->scratch;
-    blsh_plan plan = blsh_default_plan(p.kind);
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        auto it = ctx->plans.find(tab);
-        if (it != ctx->plans.end()) plan = it->second;
-    }
+    A.lite_levels = 0;
+    A.lstatus = nullptr;
+    A.ln_used = nullptr;
+    A.lsim = nullptr;
+    const blsh_plan plan = blsh_plan_for(ctx, tab);
     A.grab = (plan.grab + 31) / 32 * 32;
     int rc = blsh_launch_verify(ctx, A, plan, s);
     if (rc) return rc;
     if (P == 0) return BLSH_OK;
+    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, indptr, indices, values, p.t, status, sim, s);
+}
+
+namespace {
+
+// Pass 2 of Algorithm 2: the exact similarity of every survivor.
+int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, const int64_t *indptr,
+                    const uint32_t *indices, const float *values, double t, uint8_t *status, double *sim,
+                    cudaStream_t s) {
     LiteArgs L;
-    L.pairs = A.pairs;
+    L.pairs = pairs;
     L.P = P;
-    L.P_dev = A.P_dev;
+    L.P_dev = P_dev;
     L.indptr = indptr;
     L.indices = indices;
     L.values = values;
-    L.t = p.t;
+    L.t = t;
     L.status = status;
     L.sim = sim;
     L.scratch = ctx->scratch;
     L.vec = blsh_aligned(status, 16);
-    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, sizeof(unsigned long long), s));
+    // survivors: queued (balanced over warps), then any beyond the queue in place
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, 2 * sizeof(unsigned long long), s));   // work2, work3
+    unsigned long long *queue = reinterpret_cast<unsigned long long *>(ctx->recheck_queue);
+    lite_collect_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(L, queue);
+    BLSH_LAUNCHED(ctx, "lite survivor queue");
     int occ = 0;
     const size_t smem = 8 * 2 * kLiteStage * sizeof(uint32_t);   // 32 KB per CTA of 8 warps
     if (values) {
-        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<true>, 256, smem));
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_queue_kernel<true>, 256, smem));
+        lite_queue_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L, queue);
+        BLSH_LAUNCHED(ctx, "lite queued exact similarities");
         lite_exact_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
     } else {
-        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_exact_kernel<false>, 256, smem));
+        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_queue_kernel<false>, 256, smem));
+        lite_queue_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L, queue);
+        BLSH_LAUNCHED(ctx, "lite queued exact similarities");
         lite_exact_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
     }
     BLSH_LAUNCHED(ctx, "lite exact-similarity kernel");
     return BLSH_OK;
 }
+
+}  // namespace
+
+extern "C" int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                                uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                                const int64_t *indptr, const uint32_t *indices, const float *values,
+                                uint8_t *lite_status, uint16_t *lite_n_used, double *sim, void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    const blsh_params &p = tab->p;
+    if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
+    if (p.h <= 0) return blsh_fail(ctx, BLSH_EINVAL, "the tables were built with h = 0");
+    if (!indptr || (P > 0 && (!lite_status || !sim || !indices)))
+        return blsh_fail(ctx, BLSH_EINVAL, "lite_status, sim, indptr and indices are required");
+    if ((p.kind == BLSH_COSINE) != (values != nullptr))
+        return blsh_fail(ctx, BLSH_EINVAL, "values must be given for cosine rows and only for them");
+    if (!blsh_aligned(sim, 8) || !blsh_aligned(indptr, 8) || !blsh_aligned(lite_n_used, 2))
+        return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    VerifyArgs A;
+    int rc = blsh_make_verify_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
+                                   stop_hist, A);
+    if (rc) return rc;
+    A.lite_levels = p.h / p.k;
+    A.lstatus = lite_status;
+    A.ln_used = lite_n_used;
+    A.lsim = sim;
+    const blsh_plan plan = blsh_plan_for(ctx, tab);
+    A.grab = (plan.grab + 31) / 32 * 32;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    if (stop_hist) BLSH_CUDA(ctx, cudaMemsetAsync(stop_hist, 0, sizeof(uint64_t) * tab->levels, s));
+    rc = blsh_launch_verify(ctx, A, plan, s);
+    if (rc) return rc;
+    if (P == 0) return BLSH_OK;
+    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, indptr, indices, values, p.t, lite_status, sim, s);
+}
+

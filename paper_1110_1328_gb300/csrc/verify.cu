@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     constexpr int kWordsPerStep = 4 * U * G;
     const int steps_per_chunk = KIND == BLSH_JACCARD ? A.chunk_words / kWordsPerStep : 1;
 
-    bool active = false;
+    bool active = false, a1 = false, al = false;   // a pair is active while either algorithm is undecided
     long long q = 0;
     const uint32_t *rx = nullptr, *ry = nullptr;
     int m = 0, j = 0, w = 0, acc = 0, sub = 0;
@@ -71,19 +71,36 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             if (A.sim_out && st == BLSH_PRUNED) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
             atomicAdd(&s_hist[j], 1u);
         }
-        active = false;
+        a1 = false;
+        active = al;
+    };
+    // Algorithm 2's verdict when both run in one pass
+    auto finish_lite = [&](int st) {
+        if (g == 0) {
+            A.lstatus[q] = (uint8_t)st;
+            if (A.ln_used) A.ln_used[q] = (uint16_t)((j + 1) * A.k);
+            if (A.lsim && st == BLSH_PRUNED) A.lsim[q] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        al = false;
+        active = a1;
     };
     // Chunk j has just been completed with m agreements in n = (j+1) k hashes.
     auto decide = [&]() {
-        if (m < s_mm[j]) {
-            finish(BLSH_PRUNED);                                   // Pr[S >= t | M] < eps
-        } else if (!A.lite && ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u)) {
-            finish(BLSH_ACCEPT);                                   // concentrated
-        } else if (j + 1 == A.levels) {
-            finish(A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX);
-        } else {
-            ++j;
+        const bool pruned = m < s_mm[j];                           // Pr[S >= t | M] < eps
+        if (a1) {
+            if (pruned) {
+                finish(BLSH_PRUNED);
+            } else if (!A.lite && ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u)) {
+                finish(BLSH_ACCEPT);                               // concentrated
+            } else if (j + 1 == A.levels) {
+                finish(A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX);
+            }
         }
+        if (al) {                                                  // Algorithm 2: the same test, h hashes
+            if (pruned) finish_lite(BLSH_PRUNED);
+            else if (j + 1 == A.lite_levels) finish_lite(BLSH_LITE_SURVIVOR);
+        }
+        if (active) ++j;
     };
     auto start_pair = [&](long long qq, unsigned px, unsigned py) {
         q = qq;
@@ -93,16 +110,23 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 A.status[q] = BLSH_BAD_PAIR;
                 if (A.n_used) A.n_used[q] = 0;
                 if (A.m_out) A.m_out[q] = 0;
+                if (A.est_out) A.est_out[q] = __int_as_float(0x7fc00000);
                 if (A.sim_out) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
+                if (A.lite_levels) {
+                    A.lstatus[q] = BLSH_BAD_PAIR;
+                    if (A.ln_used) A.ln_used[q] = 0;
+                    if (A.lsim) A.lsim[q] = __longlong_as_double(0x7ff8000000000000ll);
+                }
                 blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
             }
-            active = false;
+            active = a1 = al = false;
             return;
         }
         rx = A.sig + (size_t)pr.x * A.W;
         ry = A.sig + (size_t)pr.y * A.W;
         m = 0; j = 0; w = 0; acc = 0; sub = 0;
-        active = true;
+        active = a1 = true;
+        al = A.lite_levels > 0;
     };
     // One step for every group of the warp (all lanes execute it, so the
     // group reductions may use full-warp shuffles).
@@ -323,11 +347,9 @@ int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan
     return dispatch<false>(ctx, A, plan, kind, s);
 }
 
-namespace {
-
-int make_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
-              const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
-              float *est, uint64_t *stop_hist, VerifyArgs &A) {
+int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                          const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
+                          uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist, VerifyArgs &A) {
     const blsh_params &p = tab->p;
     if (!sig || (P > 0 && (!pairs || !status)))
         return blsh_fail(ctx, BLSH_EINVAL, "pairs, sig and status are required");
@@ -361,10 +383,21 @@ int make_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int6
     A.stop_hist = reinterpret_cast<unsigned long long *>(stop_hist);
     A.scratch = ctx->scratch;
     A.grab = 0;
+    A.lite_levels = 0;
+    A.lstatus = nullptr;
+    A.ln_used = nullptr;
+    A.lsim = nullptr;
     return BLSH_OK;
 }
 
-}  // namespace
+// The plan the autotuner chose for these tables, else the default.
+blsh_plan blsh_plan_for(blsh_ctx *ctx, const blsh_tables *tab) {
+    blsh_plan plan = blsh_default_plan(tab->p.kind);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->plans.find(tab);
+    if (it != ctx->plans.end()) plan = it->second;
+    return plan;
+}
 
 extern "C" int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan,
                                 const uint32_t *pairs, int64_t P, const int64_t *P_dev, const uint32_t *sig,
@@ -375,7 +408,8 @@ extern "C" int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const bls
     if (blsh_check_plan(*plan, tab->p.kind, tab->p.k) != BLSH_OK)
         return blsh_fail(ctx, BLSH_EINVAL, "invalid plan for this kind and k");
     VerifyArgs A;
-    int rc = make_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est, stop_hist, A);
+    int rc = blsh_make_verify_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
+                                   stop_hist, A);
     if (rc) return rc;
     A.grab = (plan->grab + 31) / 32 * 32;
     blsh_device_guard g(ctx->device);
@@ -397,6 +431,15 @@ extern "C" int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t
     }
     return blsh_verify_plan(ctx, tab, &plan, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
                             stop_hist, stream);
+}
+
+extern "C" int blsh_set_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_plan *plan) {
+    if (!ctx || !tab || !plan) return BLSH_EINVAL;
+    if (blsh_check_plan(*plan, tab->p.kind, tab->p.k) != BLSH_OK)
+        return blsh_fail(ctx, BLSH_EINVAL, "invalid plan for this kind and k");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->plans[tab] = *plan;
+    return BLSH_OK;
 }
 
 extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,

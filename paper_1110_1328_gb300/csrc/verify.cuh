@@ -33,8 +33,19 @@ struct VerifyArgs {
     unsigned long long *stop_hist;
     blsh_dev_scratch *scratch;
     int grab;                    // persistent: pairs per work-counter grab
+    // Algorithms 1 and 2 in one pass over the pairs: Algorithm 2's pruning
+    // over the first lite_levels chunks (h/k), its outputs below; 0 = one
+    // algorithm only
+    int lite_levels;
+    uint8_t *lstatus;
+    uint16_t *ln_used;
+    double *lsim;
 };
 
 int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s);
 blsh_plan blsh_default_plan(int kind);
 int blsh_check_plan(const blsh_plan &plan, int kind, int k);
+int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                          const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
+                          uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist, VerifyArgs &A);
+blsh_plan blsh_plan_for(blsh_ctx *ctx, const blsh_tables *tab);

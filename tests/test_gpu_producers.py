@@ -302,6 +302,26 @@ def test_lite_cosine_fixed_point_edges(B, ctx):
     assert np.array_equal(sim.cpu().numpy(), want.sim)     # bit-identical doubles
 
 
+def test_lite_survivors_beyond_queue(B, ctx):
+    """1.1 million survivors (identical signatures): more than the survivor
+    queue holds (2^20), so the rest go through the in-place pass."""
+    sets = synth.jaccard_sets(n_sets=3000, vocab=400, mean_size=12, n_groups=300, seed=11)
+    sig = np.zeros((sets.n, 64), np.uint32)
+    pairs = synth.random_pairs(sets.n, 1_100_000, seed=12)
+    p = O.Params(kind=O.JACCARD, n_max=64, h=64, t=0.3)
+    want = O.verify_lite(O.tables(p), pairs, sig, sets)
+    assert np.all(want.status != O.PRUNED)
+    tab = B.blsh_tables_build(ctx, B.make_params(kind=0, t=0.3, n_max=64, h=64))
+    ip, ix, _ = csr_dev(sets)
+    P = len(pairs)
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, None, st, sim)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy(), want.status)
+    assert np.array_equal(sim.cpu().numpy(), want.sim)
+
+
 @pytest.mark.parametrize("P", [0, 1, 31, 4097, 1_000_003])
 def test_compact_stable_and_exact(B, ctx, P):
     rng = np.random.default_rng(P)

@@ -222,3 +222,64 @@ def test_lite_form_every_cosine_plan(B, ctx):
     B.blsh_verify_lite(ctx, tab, pt, stt, ip, ix, val, st, sim)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(st.cpu().numpy(), want.status)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_verify_both_matches_oracle_and_separate_calls(B, ctx, kind, mode):
+    """The fused pass gives Algorithm 1's and Algorithm 2's outputs exactly,
+    in both launch forms, with bad pairs and a device pair count."""
+    dev = torch.device("cuda")
+    if kind == 0:
+        objs = synth.jaccard_sets(n_sets=2000, vocab=10000, mean_size=50, n_groups=200, seed=21)
+        a, b = synth.minhash_coeffs(256, seed=22)
+        sig = O.minhash(objs, a, b)
+        pairs = np.concatenate([O.lsh_candidates(sig, O.JACCARD, 8, 32), synth.random_pairs(2000, 3001, seed=23)])
+        d = dict(kind=0, n_max=256, k=32, t=0.7)
+    else:
+        objs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=150, seed=24)
+        sig = O.srp_sparse(objs, synth.gaussian_matrix(30000, 512, seed=25))
+        pairs = np.concatenate([O.lsh_candidates(sig, O.COSINE, 8, 30), synth.random_pairs(3000, 3001, seed=26)])
+        d = dict(kind=1, n_max=512, k=32, t=0.7)
+    pairs = pairs.copy()
+    pairs[5, 1] = objs.n + 3                     # a pair naming an object >= N
+    P = len(pairs)
+    p = oracle_params(d)
+    tab_o = O.tables(p)
+    want = O.verify(tab_o, pairs, sig)
+    lite = O.verify_lite(tab_o, pairs, sig, objs)
+    tab = gpu_tables(B, ctx, d)
+    B.blsh_set_plan(ctx, tab, B.blsh_plan(mode, 1 if kind == 1 else 8, 256, 64, 0))
+    t32 = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.uint32).view(np.int32)).to(dev)
+    ip = torch.from_numpy(objs.indptr).to(dev)
+    ix = t32(objs.indices)
+    val = None if objs.values is None else torch.from_numpy(objs.values).to(dev)
+    cap = P + 100
+    pt = torch.cat([t32(pairs), torch.zeros((100, 2), dtype=torch.int32, device=dev)])
+    pd = torch.tensor([P], dtype=torch.int64, device=dev)
+    st = torch.full((cap,), 77, dtype=torch.uint8, device=dev)
+    nu = torch.zeros(cap, dtype=torch.int16, device=dev)
+    m = torch.zeros(cap, dtype=torch.int16, device=dev)
+    est = torch.zeros(cap, dtype=torch.float32, device=dev)
+    hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
+    lst = torch.full((cap,), 77, dtype=torch.uint8, device=dev)
+    lnu = torch.zeros(cap, dtype=torch.int16, device=dev)
+    sim = torch.zeros(cap, dtype=torch.float64, device=dev)
+    B.blsh_verify_both(ctx, tab, pt, t32(sig), st, nu, m, est, hist, ip, ix, val, lst, sim, lite_n_used=lnu, P_dev=pd)
+    assert B.blsh_status(ctx) == B.ERANGE
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(st.cpu().numpy()[:P], want.status) and np.all(st.cpu().numpy()[P:] == 77)
+    assert np.array_equal(nu.cpu().numpy().view(np.uint16)[:P], want.n_used)
+    assert np.array_equal(m.cpu().numpy().view(np.uint16)[:P], want.m)
+    e = est.cpu().numpy()[:P]
+    ok = ~np.isnan(want.est)
+    assert np.array_equal(np.isnan(e), ~ok) and np.max(np.abs(e[ok] - want.est[ok]), initial=0) <= EST_TOL
+    good = np.arange(P) != 5
+    assert np.array_equal(hist.cpu().numpy(), O.stop_hist(want.n_used[good], p.k, p.levels).astype(np.int64))
+    assert np.array_equal(lst.cpu().numpy()[:P], lite.status) and np.all(lst.cpu().numpy()[P:] == 77)
+    assert np.array_equal(lnu.cpu().numpy().view(np.uint16)[:P], lite.n_used)
+    g = sim.cpu().numpy()[:P]
+    assert np.array_equal(np.isnan(g), np.isnan(lite.sim))
+    okl = ~np.isnan(lite.sim)
+    assert np.array_equal(g[okl], lite.sim[okl])
+    assert (lite.status == O.LITE_ACCEPT).sum() > 10 and (want.status != O.PRUNED).sum() > 10
