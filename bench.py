@@ -159,10 +159,10 @@ class Pipeline:
         self.status = t.zeros(cap, dtype=t.uint8, device=device)
         self.n_used = t.zeros(cap, dtype=t.int16, device=device)
         self.m = t.zeros(cap, dtype=t.int16, device=device)
-        self.est = t.zeros(cap, dtype=t.float32, device=device)
+        self.est = t.full((cap,), float("nan"), dtype=t.float32, device=device)   # pruned pairs' entries stay NaN
         self.hist = t.zeros(self.tab.levels, dtype=t.int64, device=device)
         self.lstatus = t.zeros(cap, dtype=t.uint8, device=device)
-        self.sim = t.zeros(cap, dtype=t.float64, device=device)
+        self.sim = t.full((cap,), float("nan"), dtype=t.float64, device=device)
         self.out1 = t.zeros(cap, dtype=t.int64, device=device)
         self.out2 = t.zeros(cap, dtype=t.int64, device=device)
         self.n_out = t.zeros(2, dtype=t.int64, device=device)
@@ -363,14 +363,14 @@ def band_bytes(N, bands, P, passes):
     return n * 12 * (1 + 2 * passes) + P * 8
 
 
-def verify_bytes(kind, k, n_used, P):
-    """Algorithmic bytes of one verify launch: per pair 8 B of pair indices,
-    8 B of output record (status 1 + n 2 + m 2 + est 4, rounded as 8 in the
-    survey's figure; here counted exactly as 9), and per compared chunk the two
-    rows' k hashes (Jaccard 2*4k B, cosine 2*k/8 B)."""
+def verify_bytes(kind, k, n_used, P, kept):
+    """Algorithmic bytes of one verify launch: per pair 8 B of pair indices
+    and 5 B of output (status 1 + n 2 + m 2), 4 B of estimate per kept pair,
+    and per compared chunk the two rows' k hashes (Jaccard 2*4k B, cosine
+    2*k/8 B)."""
     chunks = n_used.astype(np.int64) // k
     per_chunk = 8 * k if kind == 0 else k // 4
-    return P * (8 + 9) + int(chunks.sum()) * per_chunk
+    return P * (8 + 5) + 4 * kept + int(chunks.sum()) * per_chunk
 
 
 def combine_ranks(dist, step_ms: float, pairs: int, e2e_ms: float, device):
@@ -551,8 +551,12 @@ def run_ours(args, w):
         nnz = int(objs.indptr[-1])
         hash_bytes = nnz * 4 + w["n"] * (8 + 4 * w["n_hashes"])
         hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
-    # the fused pass also writes Algorithm 2's status (1 B) and similarity (8 B) per pair
-    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P) + (9 * pipe.P if pipe.with_lite else 0)
+    kept = int(((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).sum())
+    # the fused pass also writes Algorithm 2's status (1 B per pair) and the
+    # survivors' similarities (8 B each)
+    lst = pipe.lstatus[: pipe.P].cpu().numpy() if pipe.with_lite else None
+    survivors = int(((lst == B.LITE_ACCEPT) | (lst == B.LITE_REJECT)).sum()) if pipe.with_lite else 0
+    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P, kept) + ((pipe.P + 8 * survivors) if pipe.with_lite else 0)
     key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
     hash_kernel = ("srp_dense_tc_kernel" if pipe.dense else
                    "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else
@@ -760,7 +764,9 @@ def run_verify_large(args, w):
     h = hist.cpu().numpy()
     chunks = float((h * np.arange(1, len(h) + 1)).sum())
     peak, peak_kind = load_peaks()
-    alg = P * (8 + 9) + chunks * (w["k"] // 4)
+    stn = st.cpu().numpy()
+    kept = int(((stn == B.ACCEPT) | (stn == B.ACCEPT_AT_MAX)).sum())
+    alg = P * (8 + 5) + 4 * kept + chunks * (w["k"] // 4)
     sector = P * (8 + 9) + P * 2 * 32
     print(json.dumps({"metric": METRIC, "value": round(P / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),

@@ -254,8 +254,9 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
  *   n == n_max                   -> BLSH_ACCEPT_AT_MAX.
  * Outputs per pair: status uint8 [P]; n_used uint16 [P] (hashes compared);
  * m uint16 [P] (agreements); est float [P]: S^(m, n) at the stop for kept
- * pairs (Algorithm 1 outputs an estimate only with a kept pair), NaN for
- * pruned ones.  n_used, m, est may be NULL.  stop_hist: uint64 [n_max/k] or NULL; entry j counts
+ * pairs (Algorithm 1 outputs an estimate only with a kept pair); the entries
+ * of pruned pairs and of BLSH_BAD_PAIR pairs are not written.  n_used, m,
+ * est may be NULL.  stop_hist: uint64 [n_max/k] or NULL; entry j counts
  * the pairs that stopped after chunk j (the call overwrites it).
  * P_dev: NULL, or a device int64 holding the pair count; the kernel then
  * reads the count there (clamped to P, which acts as the capacity), so the
@@ -284,7 +285,8 @@ BLSH_API int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_
  * products x_i y_i, x_i^2, y_i^2 each rounded to a multiple of 2^-60 and
  * added in int64 (independent of summation order; rows need squared norm
  * < 4).  status: BLSH_PRUNED, BLSH_LITE_ACCEPT (s > t) or BLSH_LITE_REJECT;
- * sim: double [P] (NaN for pruned pairs); n_used uint16 [P] or NULL.
+ * sim: double [P], written for the pairs that survive pruning (the entries
+ * of pruned and bad pairs are not written); n_used uint16 [P] or NULL.
  * Rows: indptr int64 [N+1], indices uint32 sorted ascending within a row,
  * values float or NULL. */
 BLSH_API int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,

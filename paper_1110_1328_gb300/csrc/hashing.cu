@@ -8,13 +8,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kP31 = 0x7fffffffu;   // 2^31 - 1
 
 // (a x + b) mod (2^31 - 1) for a, b < 2^31 - 1 and any 32-bit x, exactly:
-// v < 2^63 + 2^31, and 2^31 = 1 (mod p) lets two folds of the high bits onto
-// the low 31 bits bring v below 2^31 + 3, then one conditional subtraction.
+// v < 2^63, and 2^31 = 1 (mod p) lets a fold of the high bits onto the low
+// 31 bits bring v below 2^32 + 2^31, a second fold (in 32 bits) below
+// 2^31 + 2, then one conditional subtraction.
 __device__ __forceinline__ uint32_t mod_mersenne31(uint32_t a, uint32_t b, uint32_t x) {
     const unsigned long long v = (unsigned long long)a * x + b;
-    unsigned long long r = (v & kP31) + (v >> 31);
-    r = (r & kP31) + (r >> 31);
-    uint32_t h = (uint32_t)r;
+    const unsigned long long r = (v & kP31) + (v >> 31);
+    const uint32_t h = ((uint32_t)r & kP31) + (uint32_t)(r >> 31);
     return h >= kP31 ? h - kP31 : h;
 }
 
@@ -25,16 +25,30 @@ __device__ __forceinline__ uint32_t mod_mersenne31(uint32_t a, uint32_t b, uint3
 // minhash_big_kernel.
 constexpr long long kBigSet = 2048;
 
+constexpr long long kBigChunk = 4096;   // elements of a long set per CTA task
+
 template <int HPL>
 __global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict__ indptr,
                                                       const uint32_t *__restrict__ indices, long long N,
                                                       int n_hashes, const uint32_t *__restrict__ A,
-                                                      const uint32_t *__restrict__ B, uint32_t *__restrict__ sig) {
+                                                      const uint32_t *__restrict__ B, uint32_t *__restrict__ sig,
+                                                      blsh_dev_scratch *scratch, uint2 *__restrict__ big) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += warps) {
         const long long s = __ldg(indptr + i), e = __ldg(indptr + i + 1);
-        if (e - s > kBigSet) continue;
+        if (e - s > kBigSet) {
+            // a long set: its row starts at the identity of min, the chunks of
+            // minhash_big_kernel lower it; queued unless the queue is full
+            for (int k = lane; k < n_hashes; k += 32) sig[(size_t)i * n_hashes + k] = 0xffffffffu;
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(&scratch->work3, 1ull);
+            slot = __shfl_sync(kFull, slot, 0);
+            if (slot < BLSH_RECHECK_CAP) {
+                if (lane == 0) big[slot] = make_uint2((uint32_t)i, (uint32_t)((e - s + kBigChunk - 1) / kBigChunk));
+                continue;
+            }
+        }
         for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
             uint32_t a[HPL], b[HPL], mn[HPL];
 #pragma unroll
@@ -58,45 +72,61 @@ __global__ void __launch_bounds__(256) minhash_kernel(const int64_t *__restrict_
     }
 }
 
-// Sets longer than kBigSet: one CTA of 32 warps per set (grid-stride over
-// the sets, skipping the short ones); warp w takes every 32nd block of 32
-// elements and the warps' minima meet in shared memory (atomicMin; the
-// minimum does not depend on the order).
+// Sets longer than kBigSet, queued by minhash_kernel as (set, chunks of
+// kBigChunk elements).  Every CTA walks the queue and takes the chunks of
+// each set that fall to it (chunk c of queue entry q goes to CTA
+// (c + 7919 q) mod gridDim), so one set with thousands of elements is
+// hashed by many SMs.  In a chunk, warp w takes every 32nd block of 32
+// elements; the warps' minima meet in shared memory, and the chunk's minima
+// in the set's row in global memory (atomicMin: the minimum does not depend
+// on the order).
 template <int HPL>
 __global__ void __launch_bounds__(1024) minhash_big_kernel(const int64_t *__restrict__ indptr,
-                                                           const uint32_t *__restrict__ indices, long long N,
-                                                           int n_hashes, const uint32_t *__restrict__ A,
+                                                           const uint32_t *__restrict__ indices, int n_hashes,
+                                                           const uint32_t *__restrict__ A,
                                                            const uint32_t *__restrict__ B,
-                                                           uint32_t *__restrict__ sig) {
+                                                           uint32_t *__restrict__ sig, const blsh_dev_scratch *scratch,
+                                                           const uint2 *__restrict__ big) {
     __shared__ uint32_t smin[32 * HPL];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (long long i = blockIdx.x; i < N; i += gridDim.x) {
-        const long long s = __ldg(indptr + i), e = __ldg(indptr + i + 1);
-        if (e - s <= kBigSet) continue;
-        for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
-            __syncthreads();
-            for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x) smin[k] = 0xffffffffu;
-            __syncthreads();
-            uint32_t a[HPL], b[HPL], mn[HPL];
+    const unsigned long long total = scratch->work3;
+    const unsigned long long nq = total < BLSH_RECHECK_CAP ? total : BLSH_RECHECK_CAP;
+    const unsigned G = gridDim.x;
+    for (unsigned long long qi = 0; qi < nq; ++qi) {
+        const uint2 ent = big[qi];
+        const long long i = ent.x;
+        const unsigned chunks = ent.y;
+        const unsigned first = (unsigned)((blockIdx.x + (unsigned long long)G * chunks - (qi * 7919ull) % G) % G);
+        for (unsigned c = first; c < chunks; c += G) {
+            const long long s0 = __ldg(indptr + i) + (long long)c * kBigChunk;
+            const long long e1 = __ldg(indptr + i + 1);
+            const long long e = e1 < s0 + kBigChunk ? e1 : s0 + kBigChunk;
+            for (int t0 = 0; t0 < n_hashes; t0 += 32 * HPL) {
+                __syncthreads();
+                for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x) smin[k] = 0xffffffffu;
+                __syncthreads();
+                uint32_t a[HPL], b[HPL], mn[HPL];
 #pragma unroll
-            for (int u = 0; u < HPL; ++u) {
-                a[u] = __ldg(A + t0 + 32 * u + lane);
-                b[u] = __ldg(B + t0 + 32 * u + lane);
-                mn[u] = 0xffffffffu;
-            }
-            for (long long e0 = s + 32ll * warp; e0 < e; e0 += 32ll * nwarps) {
-                const uint32_t mine = e0 + lane < e ? __ldg(indices + e0 + lane) : 0u;
-                const int cnt = (int)min(32ll, e - e0);
-                for (int l = 0; l < cnt; ++l) {
-                    const uint32_t x = __shfl_sync(kFull, mine, l);
-#pragma unroll
-                    for (int u = 0; u < HPL; ++u) mn[u] = min(mn[u], mod_mersenne31(a[u], b[u], x));
+                for (int u = 0; u < HPL; ++u) {
+                    a[u] = __ldg(A + t0 + 32 * u + lane);
+                    b[u] = __ldg(B + t0 + 32 * u + lane);
+                    mn[u] = 0xffffffffu;
                 }
-            }
+                for (long long e0 = s0 + 32ll * warp; e0 < e; e0 += 32ll * nwarps) {
+                    const uint32_t mine = e0 + lane < e ? __ldg(indices + e0 + lane) : 0u;
+                    const int cnt = (int)min(32ll, e - e0);
+                    for (int l = 0; l < cnt; ++l) {
+                        const uint32_t x = __shfl_sync(kFull, mine, l);
 #pragma unroll
-            for (int u = 0; u < HPL; ++u) atomicMin(&smin[32 * u + lane], mn[u]);
-            __syncthreads();
-            for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x) sig[(size_t)i * n_hashes + t0 + k] = smin[k];
+                        for (int u = 0; u < HPL; ++u) mn[u] = min(mn[u], mod_mersenne31(a[u], b[u], x));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < HPL; ++u) atomicMin(&smin[32 * u + lane], mn[u]);
+                __syncthreads();
+                for (int k = threadIdx.x; k < 32 * HPL; k += blockDim.x)
+                    atomicMin(&sig[(size_t)i * n_hashes + t0 + k], smin[k]);
+            }
         }
     }
 }
@@ -607,19 +637,23 @@ extern "C" int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t
     const long long cap = (long long)ctx->sm_count * 8;
     const unsigned grid = (unsigned)(blocks_needed < cap ? blocks_needed : cap);
     const int words = n_hashes / 32;
-    const unsigned big_grid = (unsigned)(N < (long long)ctx->sm_count * 2 ? N : (long long)ctx->sm_count * 2);
+    const unsigned big_grid = (unsigned)ctx->sm_count * 2;
+    // long sets go to minhash_big_kernel through the context's work queue
+    uint2 *big = ctx->recheck_queue;
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work3, 0, sizeof(unsigned long long), s));
+    blsh_dev_scratch *scr = ctx->scratch;
     if (words % 8 == 0) {
-        minhash_kernel<8><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-        minhash_big_kernel<8><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+        minhash_kernel<8><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
+        minhash_big_kernel<8><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
     } else if (words % 4 == 0) {
-        minhash_kernel<4><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-        minhash_big_kernel<4><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+        minhash_kernel<4><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
+        minhash_big_kernel<4><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
     } else if (words % 2 == 0) {
-        minhash_kernel<2><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-        minhash_big_kernel<2><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+        minhash_kernel<2><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
+        minhash_big_kernel<2><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
     } else {
-        minhash_kernel<1><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
-        minhash_big_kernel<1><<<big_grid, 1024, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig);
+        minhash_kernel<1><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
+        minhash_big_kernel<1><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
     }
     ctx->launches.fetch_add(1, std::memory_order_relaxed);   // the second of the two launches
     BLSH_LAUNCHED(ctx, "minhash kernel");

@@ -65,10 +65,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             A.status[q] = (uint8_t)st;
             if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
             if (A.m_out) A.m_out[q] = (uint16_t)m;
-            if (A.est_out)   // the estimate is an output only for pairs that are kept (Algorithm 1)
-                A.est_out[q] = st == BLSH_PRUNED ? __int_as_float(0x7fc00000)
-                                                 : __ldg(A.est_tab + (size_t)j * A.est_stride + m);
-            if (A.sim_out && st == BLSH_PRUNED) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
+            // the estimate is an output only for pairs that are kept (Algorithm 1);
+            // a pruned pair's entry is left as it was
+            if (A.est_out && st != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
             atomicAdd(&s_hist[j], 1u);
         }
         a1 = false;
@@ -79,7 +78,6 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         if (g == 0) {
             A.lstatus[q] = (uint8_t)st;
             if (A.ln_used) A.ln_used[q] = (uint16_t)((j + 1) * A.k);
-            if (A.lsim && st == BLSH_PRUNED) A.lsim[q] = __longlong_as_double(0x7ff8000000000000ll);
         }
         al = false;
         active = a1;
@@ -110,12 +108,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 A.status[q] = BLSH_BAD_PAIR;
                 if (A.n_used) A.n_used[q] = 0;
                 if (A.m_out) A.m_out[q] = 0;
-                if (A.est_out) A.est_out[q] = __int_as_float(0x7fc00000);
-                if (A.sim_out) A.sim_out[q] = __longlong_as_double(0x7ff8000000000000ll);
                 if (A.lite_levels) {
                     A.lstatus[q] = BLSH_BAD_PAIR;
                     if (A.ln_used) A.ln_used[q] = 0;
-                    if (A.lsim) A.lsim[q] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
             }

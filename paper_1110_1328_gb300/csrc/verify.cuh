@@ -29,7 +29,7 @@ struct VerifyArgs {
     uint16_t *n_used;
     uint16_t *m_out;
     float *est_out;
-    double *sim_out;             // Lite: NaN written for pruned pairs
+    double *sim_out;             // Lite: unused by the pruning pass (the exact pass writes survivors')
     unsigned long long *stop_hist;
     blsh_dev_scratch *scratch;
     int grab;                    // persistent: pairs per work-counter grab

@@ -25,11 +25,14 @@ def csr_dev(csr):
 @pytest.mark.parametrize("n_hashes", [32, 96, 256, 512])
 def test_minhash_bit_exact(B, ctx, n_hashes):
     sets = synth.jaccard_sets(n_sets=1500, vocab=50000, mean_size=50, n_groups=100, seed=n_hashes)
-    # add an empty set and a large one
-    rows = [sets.row(i) for i in range(sets.n)] + [np.zeros(0, np.int64), np.arange(0, 3000 * 7, 7)]
+    # add an empty set and long ones: one chunk, several chunks (10,000 and
+    # 25,000 elements), and element ids just below 2^32
+    rows = [sets.row(i) for i in range(sets.n)] + [np.zeros(0, np.int64), np.arange(0, 3000 * 7, 7),
+                                                     np.arange(5, 10000 * 3 + 5, 3), np.arange(0, 25000),
+                                                     np.arange(2 ** 32 - 15000, 2 ** 32 - 1, 3)]
     lens = np.array([len(r) for r in rows])
     csr = synth.CSR(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
-                    np.concatenate(rows).astype(np.uint32), None, 50000)
+                    np.concatenate(rows).astype(np.uint32), None, 2 ** 32)
     a, b = synth.minhash_coeffs(n_hashes, seed=7)
     want = O.minhash(csr, a, b)
     ip, ix, _ = csr_dev(csr)
@@ -234,7 +237,7 @@ def test_lite_jaccard_bit_exact(B, ctx):
     ip, ix, _ = csr_dev(sets)
     P = len(pairs)
     st = torch.zeros(P, dtype=torch.uint8, device=dev)
-    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    sim = torch.full((P,), float('nan'), dtype=torch.float64, device=dev)   # entries not written stay NaN
     nu = torch.zeros(P, dtype=torch.int16, device=dev)
     B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, None, st, sim, nu)
     assert B.blsh_status(ctx) == 0
@@ -257,7 +260,7 @@ def test_lite_cosine_bit_exact(B, ctx):
     ip, ix, val = csr_dev(vecs)
     P = len(pairs)
     st = torch.zeros(P, dtype=torch.uint8, device=dev)
-    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    sim = torch.full((P,), float('nan'), dtype=torch.float64, device=dev)   # entries not written stay NaN
     B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, val, st, sim)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(st.cpu().numpy(), want.status)
@@ -295,7 +298,7 @@ def test_lite_cosine_fixed_point_edges(B, ctx):
     tab = B.blsh_tables_build(ctx, B.make_params(kind=1, t=0.1, n_max=256, h=128))
     ip, ix, val = csr_dev(csr)
     st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
-    sim = torch.zeros(len(pairs), dtype=torch.float64, device=dev)
+    sim = torch.full((len(pairs),), float('nan'), dtype=torch.float64, device=dev)
     B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, val, st, sim)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(st.cpu().numpy(), want.status)
@@ -315,7 +318,7 @@ def test_lite_survivors_beyond_queue(B, ctx):
     ip, ix, _ = csr_dev(sets)
     P = len(pairs)
     st = torch.zeros(P, dtype=torch.uint8, device=dev)
-    sim = torch.zeros(P, dtype=torch.float64, device=dev)
+    sim = torch.full((P,), float('nan'), dtype=torch.float64, device=dev)   # entries not written stay NaN
     B.blsh_verify_lite(ctx, tab, t32(pairs), t32(sig), ip, ix, None, st, sim)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(st.cpu().numpy(), want.status)

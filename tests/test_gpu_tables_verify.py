@@ -79,7 +79,7 @@ def run_verify(B, ctx, tab, pairs, sig, plan=None, P_dev=None, cap=None):
     status = torch.full((P,), 77, dtype=torch.uint8, device=dev)
     n_used = torch.zeros(P, dtype=torch.int16, device=dev)
     m = torch.zeros(P, dtype=torch.int16, device=dev)
-    est = torch.zeros(P, dtype=torch.float32, device=dev)
+    est = torch.full((P,), float('nan'), dtype=torch.float32, device=dev)   # entries not written stay NaN
     hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
     pd = None if P_dev is None else torch.tensor([P_dev], dtype=torch.int64, device=dev)
     B.blsh_verify(ctx, tab, pairs_t, sig_t, status, n_used, m, est, hist, P_dev=pd, plan=plan)
@@ -217,7 +217,7 @@ def test_lite_form_every_cosine_plan(B, ctx):
     ix = torch.zeros(1, dtype=torch.int32, device=dev)
     val = torch.zeros(1, dtype=torch.float32, device=dev)
     st = torch.zeros(len(pairs), dtype=torch.uint8, device=dev)
-    sim = torch.zeros(len(pairs), dtype=torch.float64, device=dev)
+    sim = torch.full((len(pairs),), float('nan'), dtype=torch.float64, device=dev)
     B.blsh_autotune(ctx, tab, pt, stt, st)          # stores some plan for these tables
     B.blsh_verify_lite(ctx, tab, pt, stt, ip, ix, val, st, sim)
     assert B.blsh_status(ctx) == 0
@@ -260,11 +260,11 @@ def test_verify_both_matches_oracle_and_separate_calls(B, ctx, kind, mode):
     st = torch.full((cap,), 77, dtype=torch.uint8, device=dev)
     nu = torch.zeros(cap, dtype=torch.int16, device=dev)
     m = torch.zeros(cap, dtype=torch.int16, device=dev)
-    est = torch.zeros(cap, dtype=torch.float32, device=dev)
+    est = torch.full((cap,), float('nan'), dtype=torch.float32, device=dev)
     hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
     lst = torch.full((cap,), 77, dtype=torch.uint8, device=dev)
     lnu = torch.zeros(cap, dtype=torch.int16, device=dev)
-    sim = torch.zeros(cap, dtype=torch.float64, device=dev)
+    sim = torch.full((cap,), float('nan'), dtype=torch.float64, device=dev)
     B.blsh_verify_both(ctx, tab, pt, t32(sig), st, nu, m, est, hist, ip, ix, val, lst, sim, lite_n_used=lnu, P_dev=pd)
     assert B.blsh_status(ctx) == B.ERANGE
     assert B.blsh_status(ctx) == 0
