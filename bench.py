@@ -278,6 +278,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum of the
+# bench step under --profile-step); reported as the roofline's traffic for
+# the workload it was taken on, and to be taken again whenever the kernel
+# changes.
+NCU_TRAFFIC = {("cosine-small", "srp_sparse4_kernel"): 3391.8e6 + 8.0e6}
+
+
 def load_tensor_peak():
     """Dense BF16 tensor peak: the sustained figure (a kernel inside a long
     step), else the burst figure, else the fallback."""
@@ -586,7 +594,8 @@ def run_ours(args, w):
                     "algorithmic_flops": int(flops), "stage": dom}
     else:
         roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": NCU_TRAFFIC.get((args.workload, rooflines[dom]["kernel"])),
                     "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes), "stage": dom}
     if "gathered_bytes" in rooflines[dom]:
         gb = rooflines[dom]["gathered_bytes"]
