@@ -73,6 +73,10 @@ WORKLOADS = {
                            "(BayesLSH; no Lite pass)"),
     "sweep": dict(kind=1, seed=2, gpu_only=True, text="cosine-small candidates (2.66e7 pairs), gamma, delta, epsilon each "
                                          "over 0.01..0.09 with the others at 0.05, t = 0.7"),
+    "precision-profile": dict(kind=1, dense=True, n=200_000, d=256, n_centers=2000, sigma=0.15, bits=1024, rows=16,
+                              bands=64, t=0.8, n_max=1024, k=32, h=128, margin=1e-3, seed=4,
+                              stages=("hash", "band", "verify", "compact"),
+                              text="precision shape at 200,000 points (X = 205 MB > L2), for ncu captures"),
     "batching": dict(kind=0, n=1_000_000, n_hashes=256, rows=3, bands=32, t=0.5, n_max=256, k=32, h=64, seed=3,
                      text="jaccard, BayesLSH + Lite: Chung-Lu graph N=1,000,000, exponent 2.1, mean degree 30, "
                           "256 minhashes, banding 3x32 (power-law buckets, about 1e8 candidate pairs), t=0.5"),

@@ -361,6 +361,210 @@ __global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned cha
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
+// ---- the persistent, warp-specialised tensor-core kernel -------------------------
+//
+// One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (tile t: rows 128 (t / tiles_n), bits 256 (t % tiles_n), so consecutive
+// tiles of a CTA share their rows of X).  Six warps:
+//   warp 0  producer: bulk copies of each K stage into the two-stage ring;
+//   warp 1  MMA issuer (one thread): 12 tcgen05.mma per K stage into one of
+//           two 256-column accumulators in tensor memory (512 columns), so
+//           the epilogue of one tile runs while the next tile accumulates;
+//   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. rows
+//           of the tile, and sets the signature bits as the one-tile kernel
+//           does (same margin test, same queue of undecided signs).
+// Barriers: full/empty per ring stage (bulk-copy bytes / MMA commit), and
+// acc_full/acc_empty per accumulator (MMA commit / 128 epilogue arrivals).
+// Every wait is bounded; a role that gives up records the failure and
+// stops, and the others give up in turn.
+constexpr int kEpiWarps = 4;
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) srp_dense_tc_persistent(
+    const unsigned char *__restrict__ Xh, const unsigned char *__restrict__ Xl, const unsigned char *__restrict__ Rh,
+    const unsigned char *__restrict__ Rl, const float *__restrict__ xnorm, const float *__restrict__ rnorm,
+    long long N, int d, int bits, float margin, uint32_t *__restrict__ sig, uint2 *__restrict__ queue,
+    unsigned long long qcap, unsigned long long *qcount, const float *__restrict__ X, const float *__restrict__ R,
+    long long tiles_total, blsh_dev_scratch *scratch) {
+    extern __shared__ __align__(1024) unsigned char dyn_smem[];
+    unsigned char *ring = reinterpret_cast<unsigned char *>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) unsigned long long full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2];
+    __shared__ __align__(8) unsigned long long mma_done;
+    __shared__ unsigned tmem_base;
+    __shared__ volatile int s_fail;
+    const int KT = d / BK;
+    const int tiles_n = bits / BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full_bar[st], 1);
+            mbar_init(&empty_bar[st], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 32 * kEpiWarps);
+        }
+        mbar_init(&mma_done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            long long it = 0;
+            for (long long t = blockIdx.x; t < tiles_total && !s_fail; t += gridDim.x) {
+                const long long mt = t / tiles_n;
+                const int nt = (int)(t % tiles_n);
+                for (int kb = 0; kb < KT; ++kb, ++it) {
+                    const int st = (int)(it % STAGES);
+                    const unsigned use = (unsigned)(it / STAGES);
+                    if (!mbar_wait(&empty_bar[st], (use & 1u) ^ 1u)) {   // the MMAs reading stage st are done
+                        s_fail = 1;
+                        break;
+                    }
+                    unsigned char *sp = ring + (size_t)st * STAGE_BYTES;
+                    const size_t ta = ((size_t)mt * KT + kb) * TILE_A, tb = ((size_t)nt * KT + kb) * TILE_B;
+                    mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+                    bulk_g2s(sp, Xh + ta, TILE_A, &full_bar[st]);
+                    bulk_g2s(sp + TILE_A, Xl + ta, TILE_A, &full_bar[st]);
+                    bulk_g2s(sp + 2 * TILE_A, Rh + tb, TILE_B, &full_bar[st]);
+                    bulk_g2s(sp + 2 * TILE_A + TILE_B, Rl + tb, TILE_B, &full_bar[st]);
+                }
+            }
+            // the last copy into each stage has landed before the CTA ends
+            // (at once when its MMAs consumed it; a bounded wait otherwise)
+            for (int st = 0; st < STAGES; ++st)
+                if (it > st) mbar_wait(&full_bar[st], (unsigned)(((it - 1 - st) / STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            long long it = 0, tc = 0;
+            for (long long t = blockIdx.x; t < tiles_total && !s_fail; t += gridDim.x, ++tc) {
+                const int buf = (int)(tc & 1);
+                const unsigned use_acc = (unsigned)(tc >> 1);
+                if (!mbar_wait(&acc_empty[buf], (use_acc & 1u) ^ 1u)) {   // the epilogue is done with it
+                    s_fail = 1;
+                    break;
+                }
+                fence_after();
+                const unsigned acc = tmem + (unsigned)(buf * BN);
+                bool ok = true;
+                for (int kb = 0; kb < KT; ++kb, ++it) {
+                    const int st = (int)(it % STAGES);
+                    const unsigned use = (unsigned)(it / STAGES);
+                    if (!mbar_wait(&full_bar[st], use & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    unsigned char *sp = ring + (size_t)st * STAGE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {   // K = 16 per MMA: 32 bytes along the 128-byte row
+                        const unsigned long long ah = smem_desc(sp + kk * 32), al = smem_desc(sp + TILE_A + kk * 32);
+                        const unsigned long long bh = smem_desc(sp + 2 * TILE_A + kk * 32);
+                        const unsigned long long bl = smem_desc(sp + 2 * TILE_A + TILE_B + kk * 32);
+                        mma_bf16(acc, ah, bh, (kb | kk) != 0);
+                        mma_bf16(acc, ah, bl, 1u);
+                        mma_bf16(acc, al, bh, 1u);
+                    }
+                    mma_commit(&empty_bar[st]);   // stage st is free once these MMAs finish
+                }
+                if (!ok) {
+                    s_fail = 1;
+                    break;
+                }
+                mma_commit(&acc_full[buf]);       // the tile's accumulator is final once all its MMAs finish
+            }
+            // every MMA issued has finished before tensor memory is freed
+            mma_commit(&mma_done);
+            mbar_wait(&mma_done, 0u);
+        }
+    } else {   // epilogue warps
+        const int ew = warp & 3;                  // TMEM lanes 32 ew .. 32 ew + 31
+        const int words = bits >> 5;
+        long long tc = 0;
+        for (long long t = blockIdx.x; t < tiles_total && !s_fail; t += gridDim.x, ++tc) {
+            const long long mt = t / tiles_n;
+            const int nt = (int)(t % tiles_n);
+            const int buf = (int)(tc & 1);
+            const unsigned use_acc = (unsigned)(tc >> 1);
+            if (!__all_sync(kFull, mbar_wait(&acc_full[buf], use_acc & 1u))) {   // the same verdict for the warp
+                s_fail = 1;
+                break;
+            }
+            fence_after();
+            const long long row = mt * BM + ew * 32 + lane;
+            const float xn = row < N ? __ldg(xnorm + row) : 0.0f;
+            constexpr int kBuf = 8;
+            unsigned short pend[kBuf];
+            int npend = 0;
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((unsigned)(ew * 32) << 16) + (unsigned)(buf * BN + c * 32), v);
+                if (row < N) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = nt * BN + c * 32 + i;
+                        const float thr = margin * xn * __ldg(rnorm + col);
+                        if (fabsf(v[i]) > thr) {
+                            word |= (uint32_t)(v[i] >= 0.0f) << i;
+                        } else if (npend < kBuf) {
+                            pend[npend++] = (unsigned short)(c * 32 + i);
+                        } else {
+                            word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch) << i;
+                        }
+                    }
+                    sig[(size_t)row * words + nt * (BN / 32) + c] = word;
+                }
+            }
+            // the accumulator may be overwritten now
+            fence_before();
+            mbar_arrive(&acc_empty[buf]);
+            // warp-aggregated append of the undecided signs: one atomic per warp
+            int incl = npend;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtotal = __shfl_sync(kFull, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 0 && wtotal) base = atomicAdd(qcount, (unsigned long long)wtotal);
+            base = __shfl_sync(kFull, base, 0);
+            for (int p = 0; p < npend; ++p) {
+                const unsigned long long slot = base + (unsigned long long)(incl - npend + p);
+                const int col = nt * BN + pend[p];
+                if (slot < qcap) {
+                    queue[slot] = make_uint2((uint32_t)row, (uint32_t)col);
+                } else if (sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch)) {
+                    atomicOr(sig + (size_t)row * words + (col >> 5), 1u << (col & 31));
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) blsh_dev_error(scratch, BLSH_EDEVICE, -1, 0ull);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+}
+
 // Queued signs: eight lanes per (row, bit), lane g of the group owning
 // coordinates [g d/8, (g+1) d/8).  Three stages, each with a rigorous bound:
 //   FP32 partial sums (any summation order errs by at most (d+8) u sum|p|);
@@ -525,14 +729,15 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
     static std::atomic<unsigned long long> opted{0};
     if (ctx->device < 64 && !((opted.load() >> ctx->device) & 1ull)) {
-        BLSH_CUDA(ctx, cudaFuncSetAttribute(srp_dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BLSH_CUDA(ctx, cudaFuncSetAttribute(srp_dense_tc_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         opted.fetch_or(1ull << ctx->device);
     }
-    dim3 grid(bits / BN, (unsigned)(Npad / BM));
-    srp_dense_tc_kernel<<<grid, 128, smem, s>>>(ws + L.xh, ws + L.xl, ws + L.rh, ws + L.rl, (float *)(ws + L.xn),
-                                                 (float *)(ws + L.rn), N, d, bits, m, sig, queue, L.qcap, qcount,
-                                                 X, R, ctx->scratch);
+    const long long tiles = (long long)(bits / BN) * (Npad / BM);
+    const unsigned grid = (unsigned)(tiles < ctx->sm_count ? tiles : ctx->sm_count);
+    srp_dense_tc_persistent<<<grid, kTcThreads, smem, s>>>(ws + L.xh, ws + L.xl, ws + L.rh, ws + L.rl,
+                                                          (float *)(ws + L.xn), (float *)(ws + L.rn), N, d, bits, m,
+                                                          sig, queue, L.qcap, qcount, X, R, tiles, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp dense tensor-core kernel");
     srp_dense_recheck_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(queue, L.qcap, qcount, X, (float *)(ws + L.rt), d,
                                                                  bits, sig, ctx->scratch);
