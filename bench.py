@@ -570,7 +570,7 @@ def run_ours(args, w):
     survivors = int(((lst == B.LITE_ACCEPT) | (lst == B.LITE_REJECT)).sum()) if pipe.with_lite else 0
     vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P, kept) + ((pipe.P + 8 * survivors) if pipe.with_lite else 0)
     key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
-    hash_kernel = ("srp_dense_tc_kernel" if pipe.dense else
+    hash_kernel = ("srp_dense_tc_persistent" if pipe.dense else
                    "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else
                    "srp_sparse4_kernel" if w["kind"] == 1 else "minhash_kernel")
     rooflines = {

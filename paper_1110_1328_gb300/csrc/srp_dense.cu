@@ -7,11 +7,12 @@
 //      the tile layout the tensor cores read (128- and 256-row tiles of 64
 //      K-values, 128-byte rows, 16-byte chunks XOR-swizzled by row), plus the
 //      L2 norms of the rows of X and the columns of R.
-//   2. srp_dense_tc_kernel: one CTA per 128 rows x 256 bits; the K dimension
-//      streams through a two-stage shared-memory ring filled by bulk copies
-//      (cp.async.bulk, completion on mbarriers); one thread issues
-//      tcgen05.mma (BF16 x BF16 -> FP32 in tensor memory) for hi*hi, hi*lo and
-//      lo*hi; four warps read the accumulators back (tcgen05.ld) and set a bit
+//   2. srp_dense_tc_persistent: one CTA per SM walks tiles of 128 rows x 256
+//      bits; the K dimension streams through a two-stage shared-memory ring
+//      filled by bulk copies (cp.async.bulk, completion on mbarriers); one
+//      thread issues tcgen05.mma (BF16 x BF16 -> FP32 in tensor memory) for
+//      hi*hi, hi*lo and lo*hi into one of two accumulators; four epilogue
+//      warps read the other accumulator back (tcgen05.ld) and set a bit
 //      wherever |p| > margin * |x_i| * |r_j|, queueing every other sign.
 //   3. srp_dense_recheck_kernel: each queued sign is recomputed in FP32 with a
 //      rigorous error bound, then in FP64 with one, and, if neither can decide
@@ -208,159 +209,6 @@ __device__ __noinline__ bool sign_in_line(const float *__restrict__ x, const flo
     return s >= 0.0;
 }
 
-// ---- the tensor-core kernel -----------------------------------------------------
-
-__global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned char *__restrict__ Xh,
-                                                              const unsigned char *__restrict__ Xl,
-                                                              const unsigned char *__restrict__ Rh,
-                                                              const unsigned char *__restrict__ Rl,
-                                                              const float *__restrict__ xnorm,
-                                                              const float *__restrict__ rnorm, long long N, int d,
-                                                              int bits, float margin, uint32_t *__restrict__ sig,
-                                                              uint2 *__restrict__ queue, unsigned long long qcap,
-                                                              unsigned long long *qcount, const float *__restrict__ X,
-                                                              const float *__restrict__ R,
-                                                              blsh_dev_scratch *scratch) {
-    extern __shared__ __align__(1024) unsigned char dyn_smem[];
-    // the ring must start on a 1024-byte boundary for the swizzle pattern
-    unsigned char *ring = reinterpret_cast<unsigned char *>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) unsigned long long full_bar[STAGES], empty_bar[STAGES], done_bar;
-    __shared__ unsigned tmem_base;
-    __shared__ int s_fail;
-    const int nt = blockIdx.x;        // 256-bit tile
-    const long long mt = blockIdx.y;  // 128-row tile
-    const int KT = d / BK;
-    const int warp = threadIdx.x >> 5;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(BN)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
-        }
-        mbar_init(&done_bar, 1);
-        s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const unsigned tmem = tmem_base;
-
-    if (threadIdx.x == 0) {
-        auto load = [&](int kb, int s) {
-            unsigned char *st = ring + (size_t)s * STAGE_BYTES;
-            const size_t ta = ((size_t)mt * KT + kb) * TILE_A, tb = ((size_t)nt * KT + kb) * TILE_B;
-            mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-            bulk_g2s(st, Xh + ta, TILE_A, &full_bar[s]);
-            bulk_g2s(st + TILE_A, Xl + ta, TILE_A, &full_bar[s]);
-            bulk_g2s(st + 2 * TILE_A, Rh + tb, TILE_B, &full_bar[s]);
-            bulk_g2s(st + 2 * TILE_A + TILE_B, Rl + tb, TILE_B, &full_bar[s]);
-        };
-        bool ok = true;
-        load(0, 0);
-        if (KT > 1) load(1, 1);
-        for (int kb = 0; kb < KT && ok; ++kb) {
-            const int s = kb & 1;
-            const unsigned ph = (unsigned)((kb >> 1) & 1);
-            if (!mbar_wait(&full_bar[s], ph)) {
-                ok = false;
-                break;
-            }
-            fence_after();
-            unsigned char *st = ring + (size_t)s * STAGE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {   // K = 16 per MMA: 32 bytes along the 128-byte row
-                const unsigned long long ah = smem_desc(st + kk * 32), al = smem_desc(st + TILE_A + kk * 32);
-                const unsigned long long bh = smem_desc(st + 2 * TILE_A + kk * 32);
-                const unsigned long long bl = smem_desc(st + 2 * TILE_A + TILE_B + kk * 32);
-                mma_bf16(tmem, ah, bh, (kb | kk) != 0);
-                mma_bf16(tmem, ah, bl, 1u);
-                mma_bf16(tmem, al, bh, 1u);
-            }
-            mma_commit(&empty_bar[s]);
-            if (kb + 2 < KT) {
-                if (!mbar_wait(&empty_bar[s], ph)) {   // the MMAs reading stage s are done
-                    ok = false;
-                    break;
-                }
-                load(kb + 2, s);
-            }
-        }
-        mma_commit(&done_bar);   // completes once every MMA issued above has finished
-        if (!ok) s_fail = 1;
-    }
-    __syncwarp();
-    // every thread: the accumulator is final
-    const bool done_ok = mbar_wait(&done_bar, 0u);
-    fence_after();
-    __syncthreads();
-    if (!done_ok || s_fail) {
-        if (threadIdx.x == 0) blsh_dev_error(scratch, BLSH_EDEVICE, -1, 0ull);
-    } else {
-        // epilogue: thread t owns row mt*128 + t (TMEM lane t).  Undecided
-        // signs collect in a small per-thread buffer and are appended to the
-        // recheck queue with one atomic per warp; past the buffer they are
-        // decided in line.
-        const long long row = mt * BM + threadIdx.x;
-        const float xn = row < N ? __ldg(xnorm + row) : 0.0f;
-        const int words = bits >> 5;
-        constexpr int kBuf = 8;
-        unsigned short pend[kBuf];
-        int npend = 0;
-        for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(c * 32), v);
-            if (row < N) {
-                uint32_t word = 0;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int col = nt * BN + c * 32 + i;
-                    const float thr = margin * xn * __ldg(rnorm + col);
-                    if (fabsf(v[i]) > thr) {
-                        word |= (uint32_t)(v[i] >= 0.0f) << i;
-                    } else if (npend < kBuf) {
-                        pend[npend++] = (unsigned short)(c * 32 + i);
-                    } else {
-                        word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch) << i;
-                    }
-                }
-                sig[(size_t)row * words + nt * (BN / 32) + c] = word;
-            }
-        }
-        // warp-aggregated append: exclusive prefix of the counts, one atomic
-        const int lane = threadIdx.x & 31;
-        int incl = npend;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int wtotal = __shfl_sync(kFull, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 0 && wtotal) base = atomicAdd(qcount, (unsigned long long)wtotal);
-        base = __shfl_sync(kFull, base, 0);
-        for (int p = 0; p < npend; ++p) {
-            const unsigned long long slot = base + (unsigned long long)(incl - npend + p);
-            const int col = nt * BN + pend[p];
-            if (slot < qcap) {
-                queue[slot] = make_uint2((uint32_t)row, (uint32_t)col);
-            } else if (sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch)) {
-                atomicOr(sig + (size_t)row * words + (col >> 5), 1u << (col & 31));
-            }
-        }
-    }
-    fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
-}
-
 // ---- the persistent, warp-specialised tensor-core kernel -------------------------
 //
 // One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -370,14 +218,15 @@ __global__ void __launch_bounds__(128, 1) srp_dense_tc_kernel(const unsigned cha
 //   warp 1  MMA issuer (one thread): 12 tcgen05.mma per K stage into one of
 //           two 256-column accumulators in tensor memory (512 columns), so
 //           the epilogue of one tile runs while the next tile accumulates;
-//   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. rows
-//           of the tile, and sets the signature bits as the one-tile kernel
-//           does (same margin test, same queue of undecided signs).
+//   warps 2-9 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of
+//           the tile) in columns 128 ((w - 2) / 4) .. +127, tests each value
+//           against margin |x_i| |r_j| (margin |r_j| staged in shared memory
+//           for all bits), writes the decided bits and queues the others.
 // Barriers: full/empty per ring stage (bulk-copy bytes / MMA commit), and
 // acc_full/acc_empty per accumulator (MMA commit / 128 epilogue arrivals).
 // Every wait is bounded; a role that gives up records the failure and
 // stops, and the others give up in turn.
-constexpr int kEpiWarps = 4;
+constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each taking half of a tile's 256 columns
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
@@ -392,6 +241,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) srp_dense_tc_persistent(
     long long tiles_total, blsh_dev_scratch *scratch) {
     extern __shared__ __align__(1024) unsigned char dyn_smem[];
     unsigned char *ring = reinterpret_cast<unsigned char *>(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    float *s_mr = reinterpret_cast<float *>(ring + (size_t)STAGES * STAGE_BYTES);   // [bits]: margin |r_j|
+    for (int j = threadIdx.x; j < bits; j += blockDim.x) s_mr[j] = margin * __ldg(rnorm + j);
     __shared__ __align__(8) unsigned long long full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2];
     __shared__ __align__(8) unsigned long long mma_done;
     __shared__ unsigned tmem_base;
@@ -496,6 +347,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) srp_dense_tc_persistent(
         }
     } else {   // epilogue warps
         const int ew = warp & 3;                  // TMEM lanes 32 ew .. 32 ew + 31
+        const int half = (warp - 2) >> 2;         // columns 128 half .. 128 half + 127
         const int words = bits >> 5;
         long long tc = 0;
         for (long long t = blockIdx.x; t < tiles_total && !s_fail; t += gridDim.x, ++tc) {
@@ -513,21 +365,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) srp_dense_tc_persistent(
             constexpr int kBuf = 8;
             unsigned short pend[kBuf];
             int npend = 0;
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = half * 4; c < half * 4 + 4; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((unsigned)(ew * 32) << 16) + (unsigned)(buf * BN + c * 32), v);
-                if (row < N) {
-                    uint32_t word = 0;
+                const float *mr = s_mr + nt * BN + c * 32;
+                uint32_t word = 0, und = 0;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int col = nt * BN + c * 32 + i;
-                        const float thr = margin * xn * __ldg(rnorm + col);
-                        if (fabsf(v[i]) > thr) {
-                            word |= (uint32_t)(v[i] >= 0.0f) << i;
-                        } else if (npend < kBuf) {
+                for (int i = 0; i < 32; ++i) {
+                    word |= (uint32_t)(v[i] >= 0.0f) << i;
+                    und |= (uint32_t)!(fabsf(v[i]) > xn * mr[i]) << i;   // inside the margin (or NaN): recheck
+                }
+                if (row < N) {
+                    word &= ~und;
+                    for (uint32_t u = und; u; u &= u - 1) {
+                        const int i = __ffs(u) - 1;
+                        if (npend < kBuf) {
                             pend[npend++] = (unsigned short)(c * 32 + i);
                         } else {
-                            word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, col, scratch) << i;
+                            word |= (uint32_t)sign_in_line(X + (size_t)row * d, R, d, bits, nt * BN + c * 32 + i,
+                                                           scratch) << i;
                         }
                     }
                     sig[(size_t)row * words + nt * (BN / 32) + c] = word;
@@ -726,11 +582,12 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
     unsigned long long *qcount = (unsigned long long *)(ws + L.qc);
     uint2 *queue = (uint2 *)(ws + L.q);
     BLSH_CUDA(ctx, cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), s));
-    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + (size_t)bits * sizeof(float);
+    const size_t smem_max = (size_t)STAGES * STAGE_BYTES + 1024 + 4096 * sizeof(float);   // bits <= 4096
     static std::atomic<unsigned long long> opted{0};
     if (ctx->device < 64 && !((opted.load() >> ctx->device) & 1ull)) {
         BLSH_CUDA(ctx, cudaFuncSetAttribute(srp_dense_tc_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
+                                            (int)smem_max));
         opted.fetch_or(1ull << ctx->device);
     }
     const long long tiles = (long long)(bits / BN) * (Npad / BM);
