@@ -44,7 +44,7 @@ METRIC = "candidate pairs verified/s at fixed t,ε,δ,γ; verify HBM GB/s vs pea
 
 WORKLOADS = {
     "cosine-small": dict(kind=1, n=20000, dim=100000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
-                         n_max=2048, k=32, h=128, seed=2,
+                         n_max=2048, k=32, h=128, seed=2, lazy_bits=512,
                          text="cosine, BayesLSH + Lite: N=20,000 tf-idf sparse float32 vectors, dim 100,000, "
                               "Zipf(1.1) term ids, lognormal nnz (mean 80), 2,048 SRP bits, banding 8x35, "
                               "t=0.7, eps=0.03, delta=0.05, gamma=0.03, k=32, h=128"),
@@ -146,6 +146,7 @@ class Pipeline:
             self.a, self.b = u32(hashp[0]), u32(hashp[1])
             self.W = w["n_hashes"]
         self.sig = t.zeros((N, self.W), dtype=t.int32, device=device)
+        self.need = t.zeros(N, dtype=t.uint8, device=device)
         params = B.make_params(kind=self.kind, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
         t0 = time.perf_counter()
         self.tab = B.blsh_tables_build(self.ctx, params)
@@ -176,11 +177,21 @@ class Pipeline:
         self.plan = B.blsh_autotune(self.ctx, self.tab, self.pairs[: self.P], self.sig, self.status[: self.P],
                                     self.n_used[: self.P], self.m[: self.P], self.est[: self.P])
         B.blsh_status(self.ctx)
+        self.est.fill_(float("nan"))   # autotune's estimates (from the lazily hashed prefix) are not outputs
 
     # the stages of a step, each one library call
+    @property
+    def lazy_bits(self):
+        """Hashes computed for every object (the rest only for the objects of
+        pairs still undecided after them: Section 3, lazy hashing); 0 = all."""
+        return self.w.get("lazy_bits", 0) if self.kind == 1 and not self.dense and "r_format" not in self.w else 0
+
     def hash(self):
         B = self.B
-        if self.dense:
+        if self.lazy_bits:
+            B.blsh_srp_sparse_cols(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig, 0,
+                                   self.lazy_bits)
+        elif self.dense:
             B.blsh_srp_dense(self.ctx, self.X, self.R, self.sig, margin=self.w["margin"], workspace=self.dense_ws)
         elif self.kind == 1 and self.w.get("r_format") == "q16":
             B.blsh_srp_sparse_q16(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig)
@@ -195,7 +206,19 @@ class Pipeline:
                                    self.ws)
 
     def verify(self):
-        if self.with_lite:   # Algorithms 1 and 2 in one pass over the candidates
+        if self.lazy_bits and self.with_lite:
+            # the first lazy_bits hashes decide most pairs; the others mark their
+            # objects, which get their remaining hashes, and are finished
+            B, L = self.B, self.lazy_bits
+            self.need.zero_()
+            B.blsh_verify_both_capped(self.ctx, self.tab, L, self.pairs, self.sig, self.status, self.n_used, self.m,
+                                      self.est, self.hist, self.indptr, self.indices, self.values, self.lstatus,
+                                      self.sim, self.need, P_dev=self.n_pairs)
+            B.blsh_srp_sparse_cols(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig, L,
+                                   self.w["bits"] - L, row_mask=self.need)
+            B.blsh_verify_resume(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
+                                 self.est, self.hist, P_dev=self.n_pairs)
+        elif self.with_lite:   # Algorithms 1 and 2 in one pass over the candidates
             self.B.blsh_verify_both(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
                                     self.est, self.hist, self.indptr, self.indices, self.values, self.lstatus,
                                     self.sim, P_dev=self.n_pairs)
@@ -305,9 +328,11 @@ def load_tensor_peak():
 
 def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 2):
     """The plain GPU form of the same step: eager launches (no CUDA graph),
-    the plain verification launch (one thread per pair, no persistence or
-    work stealing, no autotuning) and, for dense rows, the FP32 CUDA-core
-    projection instead of the BF16 tensor cores.  Same outputs (both forms
+    every hash of every object computed up front (no lazy hashing), the
+    plain verification launch (one thread per pair, no persistence or work
+    stealing, no autotuning), Algorithms 1 and 2 as separate passes and, for
+    dense rows, the FP32 CUDA-core projection instead of the BF16 tensor
+    cores.  Same outputs (both forms
     are bit-exact to the oracle); returns the times and the speedups."""
     plain = B.blsh_plan(B.PLAN_PLAIN, 1, 256, 0, 0)
     times = {"hash": [], "verify": [], "step": []}
@@ -317,6 +342,8 @@ def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 
         ev[0].record(stream)
         if pipe.dense:
             B.blsh_srp_dense(pipe.ctx, pipe.X, pipe.R, pipe.sig, margin=pipe.w["margin"], workspace=None)
+        elif pipe.lazy_bits:   # every hash of every object
+            B.blsh_srp_sparse(pipe.ctx, pipe.indptr, pipe.indices, pipe.values, pipe.R, pipe.sig)
         else:
             pipe.hash()
         ev[1].record(stream)
@@ -338,7 +365,7 @@ def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("plain-form step failed")
     t = {k: float(np.mean(v)) for k, v in times.items()}
-    return {"form": "eager launches, plain verify launches, Algorithms 1 and 2 as separate passes"
+    return {"form": "eager launches, all hashes up front, plain verify launches, Algorithms 1 and 2 as separate passes"
                     + (", FP32 CUDA-core projection" if pipe.dense else ""),
             "step_ms": round(t["step"], 4), "verify_ms": round(t["verify"], 4), "hash_ms": round(t["hash"], 4),
             "speedup_step": round(t["step"] / step_ms, 3),

@@ -187,6 +187,19 @@ BLSH_API int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *
 BLSH_API int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
                     int64_t N, const float *R, int64_t dim, int32_t bits, uint32_t *sig, void *stream);
 
+/* Columns [col_begin, col_begin + col_count) of blsh_srp_sparse's signatures
+ * (the same bits), for the rows with row_mask[row] != 0 (uint8 [N], device;
+ * NULL: every row); other rows and columns of sig are left as they were.
+ * This is how points are hashed only as many times as necessary (Section 3:
+ * the hashes beyond those the candidate generation and the first chunks of
+ * verification read are computed only for the points whose pairs are still
+ * undecided).  bits, col_begin and col_count multiples of 128; R 16-byte
+ * aligned.  Errors as blsh_srp_sparse. */
+BLSH_API int blsh_srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                  const float *values, int64_t N, const float *R, int64_t dim, int32_t bits,
+                                  int32_t col_begin, int32_t col_count, const uint8_t *row_mask, uint32_t *sig,
+                                  void *stream);
+
 /* Two-byte storage of the Gaussian projection matrix (Section 4.3, "Cheaper
  * storage of hash functions"): q[i] = floor((x[i] + 8) * 2^16 / 16), the code
  * of a sample assumed to lie in (-8, 8); a code q stands for q * 2^-12 - 8.
@@ -265,6 +278,30 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
 BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
                 const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used,
                 uint16_t *m, float *est, uint64_t *stop_hist, void *stream);
+
+/* Lazy hashing (Section 3: each point is hashed only as many times as
+ * necessary).  blsh_verify_both_capped is blsh_verify_both reading only the
+ * first hash_limit hashes of each signature (a multiple of k, at least h, at
+ * most n_max): a pair Algorithm 1 has not decided by then gets status
+ * BLSH_NEEDS_HASHES (its n_used and m so far are written, not its estimate,
+ * and it is not counted in stop_hist) and sets need[x] = need[y] = 1 (uint8
+ * [N], device, cleared by the caller).  Algorithm 2 decides every pair within
+ * its h <= hash_limit hashes.  After the remaining hashes of the marked
+ * objects are computed (blsh_srp_sparse_cols), blsh_verify_resume finishes
+ * the BLSH_NEEDS_HASHES pairs over all n_max hashes and adds their stops to
+ * stop_hist (not cleared), leaving every other pair's outputs as they are.
+ * Together the two calls give exactly the outputs of blsh_verify_both. */
+#define BLSH_NEEDS_HASHES 253
+BLSH_API int blsh_verify_both_capped(blsh_ctx *ctx, const blsh_tables *tab, int32_t hash_limit,
+                                     const uint32_t *pairs, int64_t P, const int64_t *P_dev, const uint32_t *sig,
+                                     int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
+                                     float *est, uint64_t *stop_hist, const int64_t *indptr,
+                                     const uint32_t *indices, const float *values, uint8_t *lite_status,
+                                     uint16_t *lite_n_used, double *sim, uint8_t *need, void *stream);
+BLSH_API int blsh_verify_resume(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                                uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                                void *stream);
 
 /* Stores `plan` as the launch plan blsh_verify, blsh_verify_lite and
  * blsh_verify_both use for these tables (what blsh_autotune does with the

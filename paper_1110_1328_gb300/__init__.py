@@ -17,6 +17,7 @@ from . import build as _build
 
 JACCARD, COSINE = 0, 1
 PRUNED, ACCEPT, ACCEPT_AT_MAX, LITE_REJECT, LITE_ACCEPT, BAD_PAIR = 0, 1, 2, 3, 4, 255
+NEEDS_HASHES = 253
 PLAN_PLAIN, PLAN_PERSISTENT = 0, 1
 OK, EINVAL, ERANGE, ETRUNC, ENOMEM, EDEVICE, ENUMERIC, ESIZE = range(8)
 
@@ -68,6 +69,7 @@ def lib():
             "blsh_tables_download": ([p, p, p, p, p, p, p, p, p], C.c_int),
             "blsh_minhash": ([p, p, p, i64, i32, p, p, p, p], C.c_int),
             "blsh_srp_sparse": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
+    "blsh_srp_sparse_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
     "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
     "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
             "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
@@ -78,6 +80,8 @@ def lib():
             "blsh_verify_plan": ([p, p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_lite": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p], C.c_int),
     "blsh_verify_both": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
+    "blsh_verify_both_capped": ([p, p, i32, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
+    "blsh_verify_resume": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
     "blsh_set_plan": ([p, p, p], C.c_int),
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
@@ -258,6 +262,20 @@ def blsh_srp_sparse(ctx: Context, indptr, indices, values, R, sig, stream=None):
     _check(rc, ctx)
 
 
+def blsh_srp_sparse_cols(ctx: Context, indptr, indices, values, R, sig, col_begin: int, col_count: int,
+                         row_mask=None, stream=None):
+    """Columns [col_begin, col_begin + col_count) of the sparse projection, for
+    the rows row_mask (uint8 tensor) selects (all when None)."""
+    N = indptr.numel() - 1
+    dim, bits = R.shape
+    idx = indices if indices.numel() else torch.zeros(1, dtype=torch.int32, device=indptr.device)
+    val = values if values.numel() else torch.zeros(1, dtype=torch.float32, device=indptr.device)
+    rc = lib().blsh_srp_sparse_cols(ctx.handle, _dev(indptr, torch.int64), _dev(idx), _dev(val, torch.float32), N,
+                                    _dev(R, torch.float32), dim, bits, col_begin, col_count,
+                                    _dev(row_mask, torch.uint8), _dev(sig), _stream(stream))
+    _check(rc, ctx)
+
+
 def blsh_quantize_gaussian(ctx: Context, x, q=None, stream=None):
     """Two-byte codes of Gaussian samples (Section 4.3); returns q (int16
     tensor holding the uint16 codes, same shape as x)."""
@@ -357,6 +375,33 @@ def blsh_verify_both(ctx: Context, tab: Tables, pairs, sig, status, n_used, m, e
                                 None if values is None else _dev(values, torch.float32),
                                 _dev(lite_status, torch.uint8), _dev(lite_n_used), _dev(sim, torch.float64),
                                 _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_verify_both_capped(ctx: Context, tab: Tables, hash_limit: int, pairs, sig, status, n_used, m, est,
+                            stop_hist, indptr, indices, values, lite_status, sim, need, lite_n_used=None,
+                            P_dev=None, stream=None):
+    """blsh_verify_both over the first hash_limit hashes; undecided pairs get
+    NEEDS_HASHES and mark their objects in need (uint8 [N])."""
+    P = pairs.shape[0]
+    N, W = sig.shape
+    rc = lib().blsh_verify_both_capped(ctx.handle, tab.handle, hash_limit, _dev(pairs), P, _dev(P_dev, torch.int64),
+                                       _dev(sig), N, W, _dev(status, torch.uint8), _dev(n_used), _dev(m),
+                                       _dev(est, torch.float32), _dev(stop_hist), _dev(indptr, torch.int64),
+                                       _dev(indices), None if values is None else _dev(values, torch.float32),
+                                       _dev(lite_status, torch.uint8), _dev(lite_n_used), _dev(sim, torch.float64),
+                                       _dev(need, torch.uint8), _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_verify_resume(ctx: Context, tab: Tables, pairs, sig, status, n_used=None, m=None, est=None,
+                       stop_hist=None, P_dev=None, stream=None):
+    """Finish the NEEDS_HASHES pairs over all n_max hashes."""
+    P = pairs.shape[0]
+    N, W = sig.shape
+    rc = lib().blsh_verify_resume(ctx.handle, tab.handle, _dev(pairs), P, _dev(P_dev, torch.int64), _dev(sig), N, W,
+                                  _dev(status, torch.uint8), _dev(n_used), _dev(m), _dev(est, torch.float32),
+                                  _dev(stop_hist), _stream(stream))
     _check(rc, ctx)
 
 

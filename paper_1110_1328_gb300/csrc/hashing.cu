@@ -154,7 +154,6 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 }
 
 constexpr int kSrpMaxPerThread = 16;
-constexpr int kSrpBatch = 1;       // nonzeros per load batch (float rows)
 constexpr int kSrpQ16Batch = 1;    // the same for two-byte rows
 constexpr int kSrpChunk = 256;
 
@@ -257,64 +256,48 @@ __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ ind
 // keeps no barrier in the loop; several rows of R are in flight per thread.
 // The four bits of a group form a nibble; eight lanes OR their nibbles into
 // one signature word with shuffles.
-template <int V, int U>
+template <int V>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values, long long N,
                                                           const float *__restrict__ R, long long dim, int bits,
+                                                          int col0, const uint8_t *__restrict__ row_mask,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
                                                           uint2 *__restrict__ queue) {
+    // columns col0 .. col0 + 4 V T - 1 of the signatures of the rows row_mask
+    // selects (all rows when it is NULL)
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int words = bits >> 5;
     unsigned long long rechecked = 0, zeros = 0, bad = 0;
     for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+        if (row_mask && !row_mask[row]) continue;
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
         float acc[4 * V], mag[4 * V];
 #pragma unroll
         for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
-        // nonzeros in batches of U: the U row loads of a batch are issued
-        // before any of their sums, so U * V 16-byte loads are in flight
-        for (long long k0 = s; k0 < e; k0 += U) {
-            const int cnt = (int)(e - k0 < U ? e - k0 : U);
-            uint32_t ix[U];
-            float v[U];
-            float4 r[U][V];
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                ix[q] = 0;
-                v[q] = 0.0f;
-                if (q < cnt) {
-                    ix[q] = __ldg(indices + k0 + q);
-                    v[q] = __ldg(values + k0 + q);
-                    if (ix[q] >= dim) {   // malformed row: counted, contributes nothing
-                        bad += t == 0;
-                        ix[q] = 0;
-                        v[q] = 0.0f;
-                    }
-                }
+        for (long long k = s; k < e; ++k) {
+            uint32_t ix = __ldg(indices + k);
+            float v = __ldg(values + k);
+            if (ix >= dim) {   // malformed row: counted, contributes nothing
+                bad += t == 0;
+                ix = 0;
+                v = 0.0f;
             }
+            const float av = fabsf(v);
+            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
 #pragma unroll
-            for (int q = 0; q < U; ++q) {
-                const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix[q] * bits) + t;
-#pragma unroll
-                for (int g = 0; g < V; ++g) r[q][g] = q < cnt ? __ldg(Rrow + g * T) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                const float av = fabsf(v[q]);
-#pragma unroll
-                for (int g = 0; g < V; ++g) {
-                    acc[4 * g + 0] = __fmaf_rn(v[q], r[q][g].x, acc[4 * g + 0]);
-                    acc[4 * g + 1] = __fmaf_rn(v[q], r[q][g].y, acc[4 * g + 1]);
-                    acc[4 * g + 2] = __fmaf_rn(v[q], r[q][g].z, acc[4 * g + 2]);
-                    acc[4 * g + 3] = __fmaf_rn(v[q], r[q][g].w, acc[4 * g + 3]);
-                    mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[q][g].x), mag[4 * g + 0]);
-                    mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[q][g].y), mag[4 * g + 1]);
-                    mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[q][g].z), mag[4 * g + 2]);
-                    mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[q][g].w), mag[4 * g + 3]);
-                }
+            for (int g = 0; g < V; ++g) {
+                const float4 r = __ldg(Rrow + g * T);
+                acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
+                acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
+                acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
+                acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
+                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
+                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
+                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
+                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
             }
         }
         const float n = (float)(e - s);
@@ -332,7 +315,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                 } else {
                     // undecided: queue it for srp_recheck_kernel (bit left 0 here),
                     // or recompute in line if the queue is full
-                    const uint32_t j = 4 * (t + g * T) + c;
+                    const uint32_t j = col0 + 4 * (t + g * T) + c;
                     const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
                     if (slot < BLSH_RECHECK_CAP) {
                         queue[slot] = make_uint2((uint32_t)row, j);
@@ -350,7 +333,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
             word |= __shfl_xor_sync(kFull, word, 1);
             word |= __shfl_xor_sync(kFull, word, 2);
             word |= __shfl_xor_sync(kFull, word, 4);
-            if ((lane & 7) == 0) sig[(size_t)row * words + ((t + g * T) >> 3)] = word;
+            if ((lane & 7) == 0) sig[(size_t)row * words + (col0 >> 5) + ((t + g * T) >> 3)] = word;
         }
     }
     if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
@@ -612,6 +595,37 @@ __global__ void __launch_bounds__(256) srp_dense_simt_kernel(const float *__rest
     if (zeros) atomicAdd(&scratch->counters[3], zeros);
 }
 
+// Columns [col0, col0 + ncols) of the sparse projection (multiples of 128)
+// for the rows row_mask selects, on the 16-byte path; -1 when that path does
+// not take the shape.
+int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
+                    const float *R, int64_t dim, int bits, int col0, int ncols, const uint8_t *row_mask,
+                    uint32_t *sig, cudaStream_t s) {
+    // T4 = 32 * (largest divisor of groups/32 up to 8) threads, V = groups / T4
+    // float4 groups per thread
+    const int groups = ncols / 4;
+    int wt = 8;
+    while ((groups / 32) % wt) --wt;
+    const int T4 = 32 * wt, V = groups / T4;
+    if (V < 1 || V > 4) return -1;
+    // many small CTAs (rows have very different lengths): 32 per SM measured best
+    const long long cap = (long long)ctx->sm_count * 32;
+    const unsigned grid = (unsigned)(N < cap ? N : cap);
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
+    uint2 *q = ctx->recheck_queue;
+    blsh_dev_scratch *scr = ctx->scratch;
+    switch (V) {
+    case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
+    case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
+    case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
+    default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
+    }
+    BLSH_LAUNCHED(ctx, "srp sparse kernel");
+    srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig, scr);
+    BLSH_LAUNCHED(ctx, "srp recheck kernel");
+    return BLSH_OK;
+}
+
 int srp_threads(int bits, int *per_thread) {
     const int words = bits / 32;
     int wt = 8;
@@ -682,27 +696,8 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
     if (bits % 128 == 0 && blsh_aligned(R, 16)) {
-        // float4 path: T4 = 32 * (largest divisor of groups/32 up to 8) threads,
-        // V = groups / T4 float4 groups per thread
-        const int groups = bits / 4;
-        int wt = 8;
-        while ((groups / 32) % wt) --wt;
-        const int T4 = 32 * wt, V = groups / T4;
-        if (V >= 1 && V <= 4) {
-            BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
-            uint2 *q = ctx->recheck_queue;
-            switch (V) {
-            case 1: srp_sparse4_kernel<1, kSrpBatch><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            case 2: srp_sparse4_kernel<2, kSrpBatch><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            case 3: srp_sparse4_kernel<3, 1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            default: srp_sparse4_kernel<4, 1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, sig, ctx->scratch, q); break;
-            }
-            BLSH_LAUNCHED(ctx, "srp sparse kernel");
-            srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig,
-                                                                 ctx->scratch);
-            BLSH_LAUNCHED(ctx, "srp recheck kernel");
-            return BLSH_OK;
-        }
+        const int rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, 0, bits, nullptr, sig, s);
+        if (rc != -1) return rc;
     }
     srp_sparse_kernel<float><<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
     BLSH_LAUNCHED(ctx, "srp sparse kernel");
@@ -738,6 +733,24 @@ extern "C" int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, 
     quantize_gaussian_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, n, q, ctx->scratch);
     BLSH_LAUNCHED(ctx, "quantize kernel");
     return BLSH_OK;
+}
+
+extern "C" int blsh_srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                    const float *values, int64_t N, const float *R, int64_t dim, int32_t bits,
+                                    int32_t col_begin, int32_t col_count, const uint8_t *row_mask, uint32_t *sig,
+                                    void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!indptr || !indices || !values || !R || !sig)
+        return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, values, R and sig are required");
+    if (N < 0 || N >= (1ll << 32) || dim <= 0 || bits <= 0 || bits % 128 || bits > 4096 || col_begin < 0 ||
+        col_count <= 0 || col_begin % 128 || col_count % 128 || col_begin + col_count > bits)
+        return blsh_fail(ctx, BLSH_EINVAL, "bits, col_begin and col_count must be multiples of 128 within bits");
+    if (!blsh_aligned(indptr, 8) || !blsh_aligned(R, 16)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    if (N == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    const int rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, col_begin, col_count, row_mask, sig,
+                                   blsh_stream(stream));
+    return rc == -1 ? blsh_fail(ctx, BLSH_EINVAL, "col_count/128 needs a divisor in 1..8 with at most 4 groups") : rc;
 }
 
 extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,

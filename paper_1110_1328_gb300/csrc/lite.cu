@@ -321,6 +321,8 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     A.lstatus = nullptr;
     A.ln_used = nullptr;
     A.lsim = nullptr;
+    A.cap_levels = A.levels;
+    A.need = nullptr;
     const blsh_plan plan = blsh_plan_for(ctx, tab);
     A.grab = (plan.grab + 31) / 32 * 32;
     int rc = blsh_launch_verify(ctx, A, plan, s);
@@ -371,15 +373,20 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
 
 }  // namespace
 
-extern "C" int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
-                                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
-                                uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
-                                const int64_t *indptr, const uint32_t *indices, const float *values,
-                                uint8_t *lite_status, uint16_t *lite_n_used, double *sim, void *stream) {
+namespace {
+
+int verify_both(blsh_ctx *ctx, const blsh_tables *tab, int32_t hash_limit, const uint32_t *pairs, int64_t P,
+                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
+                uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist, const int64_t *indptr,
+                const uint32_t *indices, const float *values, uint8_t *lite_status, uint16_t *lite_n_used,
+                double *sim, uint8_t *need, void *stream) {
     if (!ctx || !tab) return BLSH_EINVAL;
     const blsh_params &p = tab->p;
     if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
     if (p.h <= 0) return blsh_fail(ctx, BLSH_EINVAL, "the tables were built with h = 0");
+    if (hash_limit % p.k || hash_limit < p.h || hash_limit > p.n_max)
+        return blsh_fail(ctx, BLSH_EINVAL, "hash_limit must be a multiple of k in [h, n_max]");
+    if (hash_limit < p.n_max && !need) return blsh_fail(ctx, BLSH_EINVAL, "need is required below n_max");
     if (!indptr || (P > 0 && (!lite_status || !sim || !indices)))
         return blsh_fail(ctx, BLSH_EINVAL, "lite_status, sim, indptr and indices are required");
     if ((p.kind == BLSH_COSINE) != (values != nullptr))
@@ -394,6 +401,8 @@ extern "C" int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uin
     A.lstatus = lite_status;
     A.ln_used = lite_n_used;
     A.lsim = sim;
+    A.cap_levels = hash_limit / p.k;
+    A.need = need;
     const blsh_plan plan = blsh_plan_for(ctx, tab);
     A.grab = (plan.grab + 31) / 32 * 32;
     blsh_device_guard g(ctx->device);
@@ -405,3 +414,24 @@ extern "C" int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uin
     return lite_exact_pass(ctx, A.pairs, P, A.P_dev, indptr, indices, values, p.t, lite_status, sim, s);
 }
 
+}  // namespace
+
+extern "C" int blsh_verify_both(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                                const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                                uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                                const int64_t *indptr, const uint32_t *indices, const float *values,
+                                uint8_t *lite_status, uint16_t *lite_n_used, double *sim, void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    return verify_both(ctx, tab, tab->p.n_max, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
+                       stop_hist, indptr, indices, values, lite_status, lite_n_used, sim, nullptr, stream);
+}
+
+extern "C" int blsh_verify_both_capped(blsh_ctx *ctx, const blsh_tables *tab, int32_t hash_limit,
+                                       const uint32_t *pairs, int64_t P, const int64_t *P_dev, const uint32_t *sig,
+                                       int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m,
+                                       float *est, uint64_t *stop_hist, const int64_t *indptr,
+                                       const uint32_t *indices, const float *values, uint8_t *lite_status,
+                                       uint16_t *lite_n_used, double *sim, uint8_t *need, void *stream) {
+    return verify_both(ctx, tab, hash_limit, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est, stop_hist,
+                       indptr, indices, values, lite_status, lite_n_used, sim, need, stream);
+}

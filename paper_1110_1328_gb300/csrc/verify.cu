@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
 
     bool active = false, a1 = false, al = false;   // a pair is active while either algorithm is undecided
     long long q = 0;
+    uint2 cur_pair = make_uint2(0u, 0u);
     const uint32_t *rx = nullptr, *ry = nullptr;
     int m = 0, j = 0, w = 0, acc = 0, sub = 0;
 
@@ -69,6 +70,18 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             // a pruned pair's entry is left as it was
             if (A.est_out && st != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
             atomicAdd(&s_hist[j], 1u);
+        }
+        a1 = false;
+        active = al;
+    };
+    // Algorithm 1 cannot go on without the hashes not yet computed
+    auto finish_capped = [&]() {
+        if (g == 0) {
+            A.status[q] = BLSH_NEEDS_HASHES;
+            if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
+            if (A.m_out) A.m_out[q] = (uint16_t)m;
+            A.need[cur_pair.x] = 1;
+            A.need[cur_pair.y] = 1;
         }
         a1 = false;
         active = al;
@@ -92,6 +105,8 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 finish(BLSH_ACCEPT);                               // concentrated
             } else if (j + 1 == A.levels) {
                 finish(A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX);
+            } else if (j + 1 == A.cap_levels) {
+                finish_capped();
             }
         }
         if (al) {                                                  // Algorithm 2: the same test, h hashes
@@ -117,6 +132,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             active = a1 = al = false;
             return;
         }
+        cur_pair = pr;
         rx = A.sig + (size_t)pr.x * A.W;
         ry = A.sig + (size_t)pr.y * A.W;
         m = 0; j = 0; w = 0; acc = 0; sub = 0;
@@ -382,6 +398,8 @@ int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t 
     A.lstatus = nullptr;
     A.ln_used = nullptr;
     A.lsim = nullptr;
+    A.cap_levels = A.levels;
+    A.need = nullptr;
     return BLSH_OK;
 }
 
@@ -496,5 +514,76 @@ extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32
         ctx->plans[tab] = best_plan;
     }
     if (best) *best = best_plan;
+    return BLSH_OK;
+}
+
+namespace {
+
+// Pairs left at BLSH_NEEDS_HASHES, finished over all n_max hashes: one
+// thread per pair (they are few), Algorithm 1 from its first chunk, the
+// decisions of verify_kernel.  Statuses are read 16 at a time.
+__global__ void __launch_bounds__(256) verify_resume_kernel(const VerifyArgs A, int kind, int vec) {
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const long long stride = (long long)gridDim.x * blockDim.x * 16;
+    for (long long q0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 16; q0 < P; q0 += stride) {
+        uint32_t hit = 0;
+        if (vec && q0 + 16 <= P) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(A.status + q0);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hit |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_NEEDS_HASHES) << i;
+        } else {
+            for (int i = 0; i < 16; ++i)
+                if (q0 + i < P && A.status[q0 + i] == BLSH_NEEDS_HASHES) hit |= 1u << i;
+        }
+        for (; hit; hit &= hit - 1) {
+            const long long q = q0 + __ffs(hit) - 1;
+            const uint2 pr = __ldg(A.pairs + q);
+            const uint32_t *rx = A.sig + (size_t)pr.x * A.W, *ry = A.sig + (size_t)pr.y * A.W;
+            int m = 0, j = 0, st = BLSH_ACCEPT_AT_MAX;
+            for (;; ++j) {
+                const int w0 = j * A.chunk_words;
+                for (int w = w0; w < w0 + A.chunk_words; ++w) {
+                    const uint32_t a = __ldg(rx + w), b = __ldg(ry + w);
+                    m += kind == BLSH_JACCARD ? (a == b) : 32 - __popc(a ^ b);
+                }
+                if (m < __ldg(A.min_matches + j)) { st = BLSH_PRUNED; break; }
+                if ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u) { st = BLSH_ACCEPT; break; }
+                if (j + 1 == A.levels) { st = BLSH_ACCEPT_AT_MAX; break; }
+            }
+            A.status[q] = (uint8_t)st;
+            if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
+            if (A.m_out) A.m_out[q] = (uint16_t)m;
+            if (A.est_out && st != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
+            if (A.stop_hist) atomicAdd(A.stop_hist + j, 1ull);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int blsh_verify_resume(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                                  const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
+                                  uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
+                                  void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    if (tab->device != ctx->device) return blsh_fail(ctx, BLSH_EINVAL, "tables built on another device");
+    VerifyArgs A;
+    int rc = blsh_make_verify_args(ctx, tab, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est, stop_hist,
+                                   A);
+    if (rc) return rc;
+    if (P == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long groups = (P + 15) / 16;
+    const long long cap = (long long)ctx->sm_count * 8;
+    const long long blocks = (groups + 255) / 256;
+    verify_resume_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A, tab->p.kind,
+                                                                             blsh_aligned(status, 16) ? 1 : 0);
+    BLSH_LAUNCHED(ctx, "verify resume kernel");
     return BLSH_OK;
 }

@@ -40,7 +40,15 @@ struct VerifyArgs {
     uint8_t *lstatus;
     uint16_t *ln_used;
     double *lsim;
+    // lazily computed hashes: only the first cap_levels chunks are available;
+    // a pair still undecided there gets BLSH_NEEDS_HASHES and marks its two
+    // objects in need[] (cap_levels == levels: no cap)
+    int cap_levels;
+    uint8_t *need;
 };
+
+// BLSH_NEEDS_HASHES (blsh.h): an Algorithm 1 pair that needs hashes beyond
+// those computed so far (blsh_verify_resume finishes it).
 
 int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s);
 blsh_plan blsh_default_plan(int kind);

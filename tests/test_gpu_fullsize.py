@@ -41,6 +41,7 @@ def run_pipeline(B, name, graph=True):
         pipe.status.fill_(77)
         pipe.lstatus.fill_(77)
         pipe.sig.fill_(0)
+        pipe.need.fill_(0)
         g.replay()
     else:
         pipe.step()
@@ -58,16 +59,18 @@ def check_outputs_against_oracle(B, w, objs, pipe, sig_o, pairs_gpu):
     assert np.array_equal(pipe.status[:P].cpu().numpy(), want.status)
     assert np.array_equal(pipe.n_used[:P].cpu().numpy().view(np.uint16), want.n_used)
     assert np.array_equal(pipe.m[:P].cpu().numpy().view(np.uint16), want.m)
+    # estimates are outputs of kept pairs only (the entries of pruned pairs
+    # are not written, and the pipeline's buffers are reused across calls)
     est = pipe.est[:P].cpu().numpy()
-    assert np.array_equal(np.isnan(est), np.isnan(want.est))
     ok = ~np.isnan(want.est)
+    assert not np.isnan(est[ok]).any()
     assert np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
     assert np.array_equal(pipe.hist.cpu().numpy(), O.stop_hist(want.n_used, p.k, p.levels).astype(np.int64))
     lite = O.verify_lite(tab, pairs_gpu, sig_o, objs)
     assert np.array_equal(pipe.lstatus[:P].cpu().numpy(), lite.status)
     sim = pipe.sim[:P].cpu().numpy()
-    ok = ~np.isnan(lite.sim)
-    assert np.array_equal(np.isnan(sim), ~ok) and np.array_equal(sim[ok], lite.sim[ok])
+    ok = ~np.isnan(lite.sim)   # survivors only
+    assert np.array_equal(sim[ok], lite.sim[ok])
     n1, n2 = [int(x) for x in pipe.n_out.cpu()]
     keep1 = O.compact(want.status, (1 << O.ACCEPT) | (1 << O.ACCEPT_AT_MAX))
     keep2 = O.compact(lite.status, 1 << O.LITE_ACCEPT)
@@ -84,7 +87,16 @@ def test_full_pipeline_matches_oracle(B, name):
         sig_o = O.srp_sparse(objs, hashp)
     else:
         sig_o = O.minhash(objs, hashp[0], hashp[1])
-    assert np.array_equal(u32(pipe.sig), sig_o)
+    if pipe.lazy_bits:
+        # lazy hashing: the first lazy_bits hashes of every object, all of them
+        # for the objects of pairs that needed more (and at least some did)
+        lw = pipe.lazy_bits // 32
+        need = pipe.need.cpu().numpy() == 1
+        assert need.any()
+        assert np.array_equal(u32(pipe.sig)[:, :lw], sig_o[:, :lw])
+        assert np.array_equal(u32(pipe.sig)[need], sig_o[need])
+    else:
+        assert np.array_equal(u32(pipe.sig), sig_o)
     pairs_o = O.lsh_candidates(sig_o, w["kind"], w["rows"], w["bands"])
     P = pipe.P
     pairs_gpu = u32(pipe.pairs[:P])
@@ -173,8 +185,8 @@ def test_precision_workload_sampled(B):
     assert np.array_equal(pipe.status[qd].cpu().numpy(), want.status)
     assert np.array_equal(pipe.m[qd].cpu().numpy().view(np.uint16), want.m)
     est = pipe.est[qd].cpu().numpy()
-    ok = ~np.isnan(want.est)
-    assert np.array_equal(np.isnan(est), ~ok) and np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
+    ok = ~np.isnan(want.est)   # kept pairs only
+    assert np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
     # no duplicates (sorted on the device: object ids are below 2^31)
     dp = pipe.pairs[:P].long()
     key, _ = torch.sort((dp[:, 0] << 32) | dp[:, 1])

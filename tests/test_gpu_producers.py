@@ -344,3 +344,27 @@ def test_compact_stable_and_exact(B, ctx, P):
         B.blsh_compact(ctx, torch.from_numpy(st).to(dev), keep, small, n)
         assert B.blsh_status(ctx) == B.ETRUNC
         assert np.array_equal(small.cpu().numpy(), want[:3]) and int(n.item()) == len(want)
+
+
+def test_srp_sparse_cols_selected_rows(B, ctx):
+    """Columns [128, 640) of 2,048 for a third of the rows: those words equal
+    the oracle's, every other word keeps its sentinel."""
+    vecs = synth.tfidf_vectors(n_docs=900, dim=20000, mean_nnz=80, n_groups=50, seed=31)
+    R = synth.gaussian_matrix(20000, 2048, seed=32)
+    want = O.srp_sparse(vecs, R)
+    ip, ix, val = csr_dev(vecs)
+    mask = (np.arange(vecs.n) % 3 == 1).astype(np.uint8)
+    sig = torch.full((vecs.n, 64), 0x5A5A5A5A, dtype=torch.int32, device=dev)
+    B.blsh_srp_sparse_cols(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig, 128, 512,
+                           row_mask=torch.from_numpy(mask).to(dev))
+    assert B.blsh_status(ctx) == 0
+    got = sig.cpu().numpy().view(np.uint32)
+    sel = mask == 1
+    assert np.array_equal(got[sel][:, 4:20], want[sel][:, 4:20])
+    assert np.all(got[sel][:, :4] == 0x5A5A5A5A) and np.all(got[sel][:, 20:] == 0x5A5A5A5A)
+    assert np.all(got[~sel] == 0x5A5A5A5A)
+    # all rows, the whole width in two ranges: the full signatures
+    B.blsh_srp_sparse_cols(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig, 0, 512)
+    B.blsh_srp_sparse_cols(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig, 512, 1536)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)

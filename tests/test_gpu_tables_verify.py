@@ -283,3 +283,55 @@ def test_verify_both_matches_oracle_and_separate_calls(B, ctx, kind, mode):
     okl = ~np.isnan(lite.sim)
     assert np.array_equal(g[okl], lite.sim[okl])
     assert (lite.status == O.LITE_ACCEPT).sum() > 10 and (want.status != O.PRUNED).sum() > 10
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_capped_then_resume_equals_full(B, ctx, kind):
+    """Lazy hashing: the capped pass (first 128 or 512 hashes) and the resume
+    pass give exactly the outputs of the single fused pass, and the need
+    flags mark exactly the objects of the pairs that needed more hashes."""
+    dev = torch.device("cuda")
+    if kind == 0:
+        objs = synth.jaccard_sets(n_sets=2000, vocab=10000, mean_size=50, n_groups=200, seed=41)
+        a, b = synth.minhash_coeffs(256, seed=42)
+        sig = O.minhash(objs, a, b)
+        pairs = np.concatenate([O.lsh_candidates(sig, O.JACCARD, 8, 32), synth.random_pairs(2000, 3001, seed=43)])
+        d, limit = dict(kind=0, n_max=256, k=32, t=0.7), 128
+    else:
+        objs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=150, seed=44)
+        sig = O.srp_sparse(objs, synth.gaussian_matrix(30000, 2048, seed=45))
+        pairs = np.concatenate([O.lsh_candidates(sig, O.COSINE, 8, 30), synth.random_pairs(3000, 3001, seed=46)])
+        d, limit = dict(kind=1, n_max=2048, k=32, t=0.7), 256
+    P = len(pairs)
+    tab = gpu_tables(B, ctx, d)
+    t32 = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.uint32).view(np.int32)).to(dev)
+    ip = torch.from_numpy(objs.indptr).to(dev)
+    ix = t32(objs.indices)
+    val = None if objs.values is None else torch.from_numpy(objs.values).to(dev)
+    pt, st = t32(pairs), t32(sig)
+
+    def buffers():
+        return (torch.zeros(P, dtype=torch.uint8, device=dev), torch.zeros(P, dtype=torch.int16, device=dev),
+                torch.zeros(P, dtype=torch.int16, device=dev),
+                torch.full((P,), float("nan"), dtype=torch.float32, device=dev),
+                torch.zeros(tab.levels, dtype=torch.int64, device=dev), torch.zeros(P, dtype=torch.uint8, device=dev),
+                torch.full((P,), float("nan"), dtype=torch.float64, device=dev))
+    full = buffers()
+    B.blsh_verify_both(ctx, tab, pt, st, *full[:5], ip, ix, val, full[5], full[6])
+    lazy = buffers()
+    need = torch.zeros(objs.n, dtype=torch.uint8, device=dev)
+    B.blsh_verify_both_capped(ctx, tab, limit, pt, st, *lazy[:5], ip, ix, val, lazy[5], lazy[6], need)
+    assert B.blsh_status(ctx) == 0
+    capped = lazy[0].cpu().numpy() == B.NEEDS_HASHES
+    assert capped.any() and not capped.all()
+    marked = np.zeros(objs.n, bool)
+    marked[pairs[capped].reshape(-1)] = True
+    assert np.array_equal(need.cpu().numpy() == 1, marked)
+    B.blsh_verify_resume(ctx, tab, pt, st, lazy[0], lazy[1], lazy[2], lazy[3], lazy[4])
+    assert B.blsh_status(ctx) == 0
+    for f, g in zip(full, lazy):
+        a_, b_ = f.cpu().numpy(), g.cpu().numpy()
+        if a_.dtype.kind == "f":
+            assert np.array_equal(np.isnan(a_), np.isnan(b_)) and np.array_equal(a_[~np.isnan(a_)], b_[~np.isnan(b_)])
+        else:
+            assert np.array_equal(a_, b_)
