@@ -184,7 +184,11 @@ class Pipeline:
     def lazy_bits(self):
         """Hashes computed for every object (the rest only for the objects of
         pairs still undecided after them: Section 3, lazy hashing); 0 = all."""
-        return self.w.get("lazy_bits", 0) if self.kind == 1 and not self.dense and "r_format" not in self.w else 0
+        lazy = self.kind == 1 and not self.dense and "r_format" not in self.w and self.with_lite
+        L = self.w.get("lazy_bits", 0) if lazy else 0
+        if 0 < L < self.w["rows"] * self.w["bands"]:
+            raise ValueError(f"lazy_bits={L} leaves hashes that banding reads ({self.w['rows']} x {self.w['bands']})")
+        return L if 0 < L < self.w["bits"] else 0
 
     def hash(self):
         B = self.B
@@ -207,17 +211,12 @@ class Pipeline:
 
     def verify(self):
         if self.lazy_bits and self.with_lite:
-            # the first lazy_bits hashes decide most pairs; the others mark their
-            # objects, which get their remaining hashes, and are finished
-            B, L = self.B, self.lazy_bits
+            # the first lazy_bits hashes decide most pairs; the others mark
+            # their objects in `need` and are finished by hash_rest + resume
             self.need.zero_()
-            B.blsh_verify_both_capped(self.ctx, self.tab, L, self.pairs, self.sig, self.status, self.n_used, self.m,
-                                      self.est, self.hist, self.indptr, self.indices, self.values, self.lstatus,
-                                      self.sim, self.need, P_dev=self.n_pairs)
-            B.blsh_srp_sparse_cols(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig, L,
-                                   self.w["bits"] - L, row_mask=self.need)
-            B.blsh_verify_resume(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
-                                 self.est, self.hist, P_dev=self.n_pairs)
+            self.B.blsh_verify_both_capped(self.ctx, self.tab, self.lazy_bits, self.pairs, self.sig, self.status,
+                                           self.n_used, self.m, self.est, self.hist, self.indptr, self.indices,
+                                           self.values, self.lstatus, self.sim, self.need, P_dev=self.n_pairs)
         elif self.with_lite:   # Algorithms 1 and 2 in one pass over the candidates
             self.B.blsh_verify_both(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
                                     self.est, self.hist, self.indptr, self.indices, self.values, self.lstatus,
@@ -225,6 +224,17 @@ class Pipeline:
         else:
             self.B.blsh_verify(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
                                self.est, self.hist, P_dev=self.n_pairs)
+
+    def hash_rest(self):
+        """The remaining hashes of the objects marked in `need`."""
+        L = self.lazy_bits
+        self.B.blsh_srp_sparse_cols(self.ctx, self.indptr, self.indices, self.values, self.R, self.sig, L,
+                                    self.w["bits"] - L, row_mask=self.need)
+
+    def resume(self):
+        """Algorithm 1 for the pairs the first lazy_bits hashes left open."""
+        self.B.blsh_verify_resume(self.ctx, self.tab, self.pairs, self.sig, self.status, self.n_used, self.m,
+                                  self.est, self.hist, P_dev=self.n_pairs)
 
     def lite(self):
         self.B.blsh_verify_lite(self.ctx, self.tab, self.pairs, self.sig, self.indptr, self.indices, self.values,
@@ -242,8 +252,14 @@ class Pipeline:
     def with_lite(self):
         return "lite" in self.w.get("stages", ("lite",))
 
-    # the stages of a step ("verify" runs both algorithms when the workload has Lite)
-    STAGES = ("hash", "band", "verify", "compact")
+    @property
+    def STAGES(self):
+        """The stages of a step, each one library call ("verify" runs both
+        algorithms when the workload has Lite; with lazy hashing it stops at
+        lazy_bits hashes and hash_rest + resume finish the open pairs)."""
+        if self.lazy_bits and self.with_lite:
+            return ("hash", "band", "verify", "hash_rest", "resume", "compact")
+        return ("hash", "band", "verify", "compact")
 
     def step(self):
         for s in self.STAGES:
@@ -310,7 +326,7 @@ class ClockSampler:
 # bench step under --profile-step); reported as the roofline's traffic for
 # the workload it was taken on, and to be taken again whenever the kernel
 # changes.
-NCU_TRAFFIC = {("cosine-small", "srp_sparse4_kernel"): 3391.8e6 + 8.0e6}
+NCU_TRAFFIC = {}
 
 
 def load_tensor_peak():
@@ -369,8 +385,8 @@ def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 
                     + (", FP32 CUDA-core projection" if pipe.dense else ""),
             "step_ms": round(t["step"], 4), "verify_ms": round(t["verify"], 4), "hash_ms": round(t["hash"], 4),
             "speedup_step": round(t["step"] / step_ms, 3),
-            "speedup_verify": round(t["verify"] / stage_ms["verify"], 3),
-            "speedup_hash": round(t["hash"] / stage_ms["hash"], 3)}
+            "speedup_verify": round(t["verify"] / (stage_ms["verify"] + stage_ms.get("resume", 0.0)), 3),
+            "speedup_hash": round(t["hash"] / (stage_ms["hash"] + stage_ms.get("hash_rest", 0.0)), 3)}
 
 
 def load_peaks():
@@ -382,34 +398,90 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def srp_sparse_bytes(indptr, indices, bits, esize=4):
-    """Algorithmic bytes of one sparse-SRP launch: every nonzero reads its
-    index, value and one row of R (bits floats); every row reads two indptr
-    entries and writes bits/8 bytes of signature.  Also returned: the unique
-    bytes (each distinct row of R once), the least DRAM traffic possible."""
-    nnz = int(indptr[-1])
-    N = len(indptr) - 1
-    fixed = nnz * 8 + N * (8 + bits // 8)
-    distinct = int(np.unique(indices).size)
-    return fixed + nnz * esize * bits, fixed + distinct * esize * bits
+def csr_rows_bytes(indptr, indices, rows, ncols, esize):
+    """Sparse SRP over the objects `rows` (bool mask or None = all) and ncols
+    hash columns: per object two indptr entries and ncols/8 signature bytes
+    written, per nonzero its index and value, and each distinct row of R
+    that those nonzeros touch once (ncols * esize bytes)."""
+    if rows is None:
+        nnz, n, idx = int(indptr[-1]), len(indptr) - 1, indices
+    else:
+        sel = np.flatnonzero(rows)
+        lo, hi = indptr[sel], indptr[sel + 1]
+        nnz, n = int((hi - lo).sum()), sel.size
+        idx = indices[np.concatenate([np.arange(a, b) for a, b in zip(lo, hi)])] if n else indices[:0]
+    return nnz * 8 + n * (16 + ncols // 8) + int(np.unique(idx).size) * ncols * esize
 
 
-def band_bytes(N, bands, P, passes):
-    """Algorithmic bytes of one banding call: per (object, band) key and id
-    written once and moved by every radix pass (read + write), per emitted
-    pair 8 bytes written."""
-    n = N * bands
-    return n * 12 * (1 + 2 * passes) + P * 8
-
-
-def verify_bytes(kind, k, n_used, P, kept):
-    """Algorithmic bytes of one verify launch: per pair 8 B of pair indices
-    and 5 B of output (status 1 + n 2 + m 2), 4 B of estimate per kept pair,
-    and per compared chunk the two rows' k hashes (Jaccard 2*4k B, cosine
-    2*k/8 B)."""
-    chunks = n_used.astype(np.int64) // k
-    per_chunk = 8 * k if kind == 0 else k // 4
-    return P * (8 + 5) + 4 * kept + int(chunks.sum()) * per_chunk
+def kernel_work(B, pipe, w, objs, st, nu, lst, need):
+    """Algorithmic work of one step per kernel name: {name: (amount, unit)}
+    with unit "B" (bytes moved at least once) or "flop".  Counts what each
+    launch must read and write; re-reads (L2 hits or not) are not counted."""
+    P, N, k = pipe.P, pipe.N, w["k"]
+    work = {}
+    kept = (st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)
+    per_chunk = 8 * k if w["kind"] == 0 else k // 4          # both rows' k hashes
+    lazy = pipe.lazy_bits
+    if lazy:
+        capped = np.minimum(nu.astype(np.int64), lazy) // k
+        resumed = nu.astype(np.int64) > lazy
+        work["verify_kernel"] = (P * (8 + 5 + 1) + 4 * int((kept & ~resumed).sum())
+                                 + int(capped.sum()) * per_chunk, "B")
+        r = int(resumed.sum())
+        work["verify_resume_kernel"] = (P + r * (8 + 5) + 4 * int((kept & resumed).sum())
+                                        + int((nu[resumed].astype(np.int64) // k).sum()) * per_chunk, "B")
+    else:
+        work["verify_kernel"] = (P * (8 + 5 + (1 if pipe.with_lite else 0)) + 4 * int(kept.sum())
+                                 + int((nu.astype(np.int64) // k).sum()) * per_chunk, "B")
+    if pipe.with_lite:
+        surv = (lst == B.LITE_ACCEPT) | (lst == B.LITE_REJECT)
+        pr = pipe.pairs[:P].cpu().numpy().astype(np.int64)[surv]
+        row_nnz = np.diff(objs.indptr)
+        vb = 8 if objs.values is not None else 4
+        work["lite_collect_kernel"] = (P + 8 * int(surv.sum()), "B")
+        work["lite_queue_kernel"] = (int(surv.sum()) * (8 + 32 + 9)
+                                     + int((row_nnz[pr[:, 0]] + row_nnz[pr[:, 1]]).sum()) * vb, "B")
+    if pipe.dense:
+        work["srp_dense_tc_persistent"] = (3 * 2 * N * w["d"] * w["bits"], "flop")
+    elif w["kind"] == 1:
+        es = 2 if w.get("r_format") == "q16" else 4
+        name = "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else "srp_sparse4_kernel"
+        b = csr_rows_bytes(objs.indptr, objs.indices, None, lazy or w["bits"], es)
+        rows_nnz = np.diff(objs.indptr)
+        gathered = int(rows_nnz.sum()) * (lazy or w["bits"]) * es
+        if lazy:
+            b += csr_rows_bytes(objs.indptr, objs.indices, need, w["bits"] - lazy, es)
+            gathered += int(rows_nnz[need].sum()) * (w["bits"] - lazy) * es
+        work[name] = (b, "B")
+        # every nonzero reads its row of R (L2 hits for the rows other objects
+        # brought in): the traffic between L2 and the SMs
+        work[name + " gathered"] = (gathered, "B")
+        work["srp_sparse_kernel"] = work[name]    # the generic form (other column counts)
+    else:
+        nnz = int(objs.indptr[-1])
+        work["minhash_kernel"] = (nnz * 4 + N * (8 + 4 * w["n_hashes"]), "B")
+    # banding: n = N * bands (object, band) entries
+    n, rows, bands = N * w["bands"], w["rows"], w["bands"]
+    if w["kind"] == 1:
+        kb = 4 if max(1, (bands - 1).bit_length()) + rows <= 32 else 8
+        obj_rows = N * bands * ((rows + 7) // 8)
+    else:   # 32-bit class keys while a row of class ids fits the staging (32 words), else 64-bit band hashes
+        kb = 4 if ((bands + 3) & ~3) <= 32 else 8
+        obj_rows = N * bands * 4
+    emit = "emit_cos_tile_kernel"
+    passes = (8 * kb + 7) // 8 if w["kind"] == 0 else (max(1, (bands - 1).bit_length()) + rows + 7) // 8
+    sig_bytes = N * bands * rows // 8 if w["kind"] == 1 else N * bands * rows * 4   # the banded hashes
+    work["band_keys_kernel"] = (sig_bytes + n * (kb + 4) + obj_rows, "B")
+    work["digit_hist_kernel"] = (passes * n * kb, "B")
+    work["digit_scatter_kernel"] = (passes * 2 * n * (kb + 4), "B")
+    work[emit + " (count pass)"] = (n * (kb + 4) + obj_rows + n * 8, "B")
+    work[emit + " (write pass)"] = (n * (kb + 4 + 8) + obj_rows + P * 8, "B")
+    for ps in (" (count pass)", " (write pass)"):    # the unstaged form
+        work["emit_kernel" + ps] = work[emit + ps]
+    n_keep = int(kept.sum())
+    work["compact_count"] = ((2 if pipe.with_lite else 1) * P, "B")
+    work["compact_write"] = ((2 if pipe.with_lite else 1) * P + 8 * n_keep, "B")
+    return work
 
 
 def combine_ranks(dist, step_ms: float, pairs: int, e2e_ms: float, device):
@@ -517,9 +589,12 @@ def run_ours(args, w):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     my_ms = float(np.mean(step_ms))
 
-    # ---- per-stage device times (eager, events around each library call) ----
+    # ---- per-stage and per-kernel device times (eager steps: events around
+    # each library call, and the library's own events around each launch) ----
     stage_ms = {s: [] for s in pipe.STAGES}
-    for i in range(max(3, min(args.steps, 5))):
+    reps = max(3, min(args.steps, 5))
+    B.blsh_timing_begin(pipe.ctx)
+    for i in range(reps):
         flush.fill_(float(i))
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(pipe.STAGES) + 1)]
         evs[0].record(stream)
@@ -529,7 +604,14 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         for j, s in enumerate(pipe.STAGES):
             stage_ms[s].append(evs[j].elapsed_time(evs[j + 1]))
+    records = B.blsh_timing_end(pipe.ctx)
     stage_ms = {s: float(np.mean(v)) for s, v in stage_ms.items()}
+    kernel_ms = {}   # name -> [launches per step, device ms per step]
+    for name, t_ms in records:
+        k = kernel_ms.setdefault(name, [0, 0.0])
+        k[0] += 1
+        k[1] += t_ms
+    kernel_ms = {n: [c / reps, t / reps] for n, (c, t) in kernel_ms.items()}
 
     vs_plain = measure_plain(B, torch, pipe, flush, stream, stage_ms, my_ms)
 
@@ -578,61 +660,52 @@ def run_ours(args, w):
     n1, n2 = [int(x) for x in pipe.n_out.cpu()]
 
     peak, peak_kind = load_peaks()
-    unique = None
-    if pipe.dense:
-        hash_bytes = pipe.N * w["d"] * 4 + w["d"] * w["bits"] * 4 + pipe.N * w["bits"] // 8
-        hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
-    elif w["kind"] == 1:
-        hash_bytes, unique = srp_sparse_bytes(objs.indptr, objs.indices, w["bits"],
-                                              2 if w.get("r_format") == "q16" else 4)
-        hashes_per_s = w["n"] * w["bits"] / (stage_ms["hash"] / 1e3)
-    else:
-        nnz = int(objs.indptr[-1])
-        hash_bytes = nnz * 4 + w["n"] * (8 + 4 * w["n_hashes"])
-        hashes_per_s = nnz * w["n_hashes"] / (stage_ms["hash"] / 1e3)
-    kept = int(((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).sum())
-    # the fused pass also writes Algorithm 2's status (1 B per pair) and the
-    # survivors' similarities (8 B each)
     lst = pipe.lstatus[: pipe.P].cpu().numpy() if pipe.with_lite else None
+    need = pipe.need.cpu().numpy().astype(bool) if pipe.lazy_bits else None
+    kept = int(((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).sum())
     survivors = int(((lst == B.LITE_ACCEPT) | (lst == B.LITE_REJECT)).sum()) if pipe.with_lite else 0
-    vbytes = verify_bytes(w["kind"], w["k"], nu, pipe.P, kept) + ((pipe.P + 8 * survivors) if pipe.with_lite else 0)
-    key_bits = (max(1, (w["bands"] - 1).bit_length()) + w["rows"]) if w["kind"] == 1 else 64
-    hash_kernel = ("srp_dense_tc_persistent" if pipe.dense else
-                   "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else
-                   "srp_sparse4_kernel" if w["kind"] == 1 else "minhash_kernel")
-    rooflines = {
-        "hash": {"kernel": hash_kernel, "bytes": hash_bytes},
-        "band": {"kernel": "emit_kernel + radix sort", "bytes": band_bytes(pipe.N, w["bands"], pipe.P,
-                                                                             (key_bits + 7) // 8)},
-        "verify": {"kernel": "verify_kernel (Algorithms 1 and 2 in one pass)" if pipe.with_lite else "verify_kernel",
-                   "bytes": vbytes},
-    }
-    if unique is not None:
-        # the least DRAM traffic of the SRP launch: each distinct row of R once;
-        # the rows gathered per nonzero (mostly L2 hits) are reported beside it
-        rooflines["hash"]["gathered_bytes"] = rooflines["hash"]["bytes"]
-        rooflines["hash"]["bytes"] = unique
-    dom = max(rooflines, key=lambda k: stage_ms[k])
-    rl_bytes = rooflines[dom]["bytes"]
-    achieved = rl_bytes / (stage_ms[dom] / 1e3) / 1e9
-    if dom == "hash" and pipe.dense:
-        # a contraction: three BF16 products (hi*hi, hi*lo, lo*hi) of 2 N d bits flops each
-        flops = 3 * 2 * pipe.N * w["d"] * w["bits"]
-        tf_peak, tf_kind = load_tensor_peak()
-        ach = flops / (stage_ms[dom] / 1e3) / 1e12
-        roofline = {"bound": "tensor", "kernel": hash_kernel, "achieved": round(ach, 1), "peak": tf_peak,
-                    "unit": "TFLOP/s", "frac": round(ach / tf_peak, 4), "traffic": None, "peak_source": tf_kind,
-                    "algorithmic_flops": int(flops), "stage": dom}
+    # hashes computed per step (with lazy hashing: the prefix for every
+    # object, the rest for the objects of the pairs it left open)
+    hash_ms = stage_ms["hash"] + stage_ms.get("hash_rest", 0.0)
+    if w["kind"] == 1:
+        lazy = pipe.lazy_bits
+        hashes = pipe.N * (lazy or w["bits"]) + (int(need.sum()) * (w["bits"] - lazy) if lazy else 0)
     else:
-        roofline = {"bound": "hbm", "kernel": rooflines[dom]["kernel"], "achieved": round(achieved, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": NCU_TRAFFIC.get((args.workload, rooflines[dom]["kernel"])),
-                    "peak_source": peak_kind, "algorithmic_bytes": int(rl_bytes), "stage": dom}
-    if "gathered_bytes" in rooflines[dom]:
-        gb = rooflines[dom]["gathered_bytes"]
+        hashes = int(objs.indptr[-1]) * w["n_hashes"]
+    hashes_per_s = hashes / (hash_ms / 1e3)
+    work = kernel_work(B, pipe, w, objs, st, nu, lst, need)
+    # the dominant kernel: the most device time per step of the launches the
+    # library timed (the exclusive scan helper is three small launches)
+    timed = {n: v for n, v in kernel_ms.items() if not n.startswith("exclusive scan")}
+    dom = max(timed, key=lambda n: timed[n][1])
+    dom_launches, dom_ms = timed[dom]
+    amount, unit = work.get(dom, (None, None))
+    if unit == "flop":
+        tf_peak, tf_kind = load_tensor_peak()
+        ach = amount / (dom_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": tf_peak,
+                    "unit": "TFLOP/s", "frac": round(ach / tf_peak, 4), "traffic": None, "peak_source": tf_kind,
+                    "algorithmic_flops": int(amount)}
+    else:
+        ach = amount / (dom_ms / 1e3) / 1e9 if amount is not None else None
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": None if ach is None else round(ach, 1),
+                    "peak": peak, "unit": "GB/s", "frac": None if ach is None else round(ach / peak, 4),
+                    "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_source": peak_kind,
+                    "algorithmic_bytes": amount}
+    if dom + " gathered" in work:
+        gb = work[dom + " gathered"][0]
         roofline["gathered_bytes"] = int(gb)
-        roofline["gathered_GBps"] = round(gb / (stage_ms[dom] / 1e3) / 1e9, 1)
-    v_ach = vbytes / (stage_ms["verify"] / 1e3) / 1e9
+        roofline["gathered_GBps"] = round(gb / (dom_ms / 1e3) / 1e9, 1)
+    roofline.update({"launches_per_step": dom_launches, "ms_per_step": round(dom_ms, 4),
+                     "timing": "library CUDA events around each launch on its stream, eager steps"})
+    kernels = {n: {"launches": c, "ms": round(t, 4),
+                   **({"GBps": round(work[n][0] / (t / 1e3) / 1e9, 1)} if n in work and work[n][1] == "B" else {}),
+                   **({"TFLOPs": round(work[n][0] / (t / 1e3) / 1e12, 1)} if n in work and work[n][1] == "flop"
+                      else {})}
+               for n, (c, t) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
+    vbytes = work["verify_kernel"][0] + work.get("verify_resume_kernel", (0, "B"))[0]
+    v_ms = kernel_ms["verify_kernel"][1] + kernel_ms.get("verify_resume_kernel", [0, 0.0])[1]
+    v_ach = vbytes / (v_ms / 1e3) / 1e9
 
     out = {
         "metric": METRIC,
@@ -650,14 +723,18 @@ def run_ours(args, w):
         "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "candidate_pairs": pipe.P,
                    "l2": "flushed between timed steps (256 MB write)", "cuda_graph": graph is not None,
                    "plan": pipe.plan.as_dict(), "tables_build_ms": round(pipe.tables_ms, 2),
+                   "lazy_bits": pipe.lazy_bits,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": {"value": round(e2e_val, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4)},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": roofline,
         "verify_hbm": {"achieved": round(v_ach, 1), "peak": peak, "unit": "GB/s", "frac": round(v_ach / peak, 4),
-                       "algorithmic_bytes": int(vbytes), "ms": round(stage_ms["verify"], 4)},
+                       "algorithmic_bytes": int(vbytes), "ms": round(v_ms, 4),
+                       "kernels": "verify_kernel" + (" + verify_resume_kernel" if pipe.lazy_bits else "")},
+        "kernels": kernels,
         "hashes_per_s": round(hashes_per_s, 1),
+        "hashes_per_step": int(hashes),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "outputs": {"bayeslsh_kept": n1, "lite_kept": n2, "pruned": int((st == B.PRUNED).sum()),
                     "stop_hist_first4": [int(x) for x in hist[:4]]},
@@ -916,10 +993,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one extra eager step inside the NVTX range blsh_step (for ncu captures)")
+    ap.add_argument("--lazy-bits", type=int, default=None,
+                    help="sparse cosine: hashes computed for every object before verification (a multiple of 128; "
+                         "0 = all up front); the workload's setting otherwise")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.lazy_bits is not None:
+        w["lazy_bits"] = args.lazy_bits
     if args.impl == "reference":
         run_reference(args, w)
     elif args.workload == "verify-large":

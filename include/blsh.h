@@ -136,6 +136,25 @@ BLSH_API int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters);
  * graph are not counted).  -1 for a NULL context. */
 BLSH_API int64_t blsh_launch_count(const blsh_ctx *ctx);
 
+/* Per-launch device timing, for profiling a step from the host without a
+ * profiler.  blsh_timing_begin allocates 2 * max_launches CUDA events and
+ * switches recording on: from then on every kernel the library launches
+ * through `ctx` (up to max_launches of them) is bracketed by a start and a
+ * stop event recorded on the launch's stream.  Launches enqueued while their
+ * stream is being captured into a CUDA graph are not recorded.  Recording
+ * costs two event records per launch; it is off by default.  One host thread
+ * at a time may launch through a context that is recording.
+ * blsh_timing_end waits for the recorded stop events, writes up to `max`
+ * records in launch order -- names[i] = the kernel's name (a static string
+ * owned by the library; a multi-launch helper such as the exclusive scan
+ * is one record), ms[i] = its device time in milliseconds -- sets *n to the
+ * number written, releases the events and switches recording off.
+ * Errors: BLSH_EINVAL for max_launches outside 1..65536 or missing outputs;
+ * BLSH_EDEVICE if an event could not be created or read (recording is then
+ * off and the records are dropped). */
+BLSH_API int blsh_timing_begin(blsh_ctx *ctx, int32_t max_launches);
+BLSH_API int blsh_timing_end(blsh_ctx *ctx, int32_t max, const char **names, float *ms, int32_t *n);
+
 /* ---- Section 4.3 tables -------------------------------------------------- */
 
 /* Builds, in FP64 on the GPU, for n_j = (j+1) k, j = 0 .. n_max/k - 1:

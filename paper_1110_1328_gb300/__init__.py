@@ -64,14 +64,16 @@ def lib():
             "blsh_last_error": ([p], C.c_char_p),
             "blsh_status": ([p, p, p], C.c_int),
             "blsh_launch_count": ([p], C.c_int64),
+            "blsh_timing_begin": ([p, i32], C.c_int),
+            "blsh_timing_end": ([p, i32, p, p, p], C.c_int),
             "blsh_tables_build": ([p, p, p, p], C.c_int),
             "blsh_tables_destroy": ([p], C.c_int),
             "blsh_tables_download": ([p, p, p, p, p, p, p, p, p], C.c_int),
             "blsh_minhash": ([p, p, p, i64, i32, p, p, p, p], C.c_int),
             "blsh_srp_sparse": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
-    "blsh_srp_sparse_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
-    "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
-    "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
+            "blsh_srp_sparse_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
+            "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
+            "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
             "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
             "blsh_srp_dense_workspace": ([i64, i32, i32, p], C.c_int),
             "blsh_lsh_candidates_workspace": ([i64, i32, i32, i32, p], C.c_int),
@@ -79,10 +81,10 @@ def lib():
             "blsh_verify": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_plan": ([p, p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_lite": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p], C.c_int),
-    "blsh_verify_both": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
-    "blsh_verify_both_capped": ([p, p, i32, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
-    "blsh_verify_resume": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
-    "blsh_set_plan": ([p, p, p], C.c_int),
+            "blsh_verify_both": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
+            "blsh_verify_both_capped": ([p, p, i32, p, i64, p, p, i64, i32, p, p, p, p, p, p, p, p, p, p, p, p, p], C.c_int),
+            "blsh_verify_resume": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
+            "blsh_set_plan": ([p, p, p], C.c_int),
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
             "blsh_compact_noalloc": ([p, i64, p, u32, p, i64, p, p], C.c_int),
@@ -212,6 +214,21 @@ def blsh_status(ctx: Context, stream=None, counters: bool = False):
 
 def blsh_launch_count(ctx: Context) -> int:
     return int(lib().blsh_launch_count(ctx.handle))
+
+
+def blsh_timing_begin(ctx: Context, max_launches: int = 4096) -> None:
+    """Switches per-launch device timing on for the kernels launched through ctx."""
+    _check(lib().blsh_timing_begin(ctx.handle, int(max_launches)), ctx)
+
+
+def blsh_timing_end(ctx: Context, max_records: int = 4096) -> list[tuple[str, float]]:
+    """(kernel name, device ms) of each launch recorded since blsh_timing_begin,
+    in launch order; switches timing off."""
+    names = (C.c_char_p * max_records)()
+    ms = (C.c_float * max_records)()
+    n = C.c_int32(0)
+    _check(lib().blsh_timing_end(ctx.handle, int(max_records), names, ms, C.byref(n)), ctx)
+    return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
 
 def blsh_tables_build(ctx: Context, params: blsh_params, stream=None) -> Tables:

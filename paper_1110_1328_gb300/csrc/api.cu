@@ -86,10 +86,13 @@ extern "C" int blsh_ctx_create(blsh_ctx **out, int device) {
     return BLSH_OK;
 }
 
+static void timing_release(blsh_ctx *ctx);
+
 extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
     if (!ctx) return BLSH_OK;
     {
         blsh_device_guard g(ctx->device);
+        timing_release(ctx);
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
     }
@@ -124,4 +127,57 @@ extern "C" int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters) {
 
 extern "C" int64_t blsh_launch_count(const blsh_ctx *ctx) {
     return ctx ? (int64_t)ctx->launches.load(std::memory_order_relaxed) : -1;
+}
+
+static void timing_release(blsh_ctx *ctx) {
+    auto &T = ctx->timing;
+    for (cudaEvent_t e : T.ev)
+        if (e) cudaEventDestroy(e);
+    T.ev.clear();
+    T.name.clear();
+    T.on = T.open = false;
+    T.cap = T.n = 0;
+}
+
+extern "C" int blsh_timing_begin(blsh_ctx *ctx, int32_t max_launches) {
+    if (!ctx) return BLSH_EINVAL;
+    if (max_launches <= 0 || max_launches > 65536) return blsh_fail(ctx, BLSH_EINVAL, "max_launches outside 1..65536");
+    blsh_device_guard g(ctx->device);
+    timing_release(ctx);
+    auto &T = ctx->timing;
+    T.ev.assign(2 * (size_t)max_launches, nullptr);
+    T.name.assign((size_t)max_launches, nullptr);
+    for (auto &e : T.ev) {
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            e = nullptr;
+            timing_release(ctx);
+            return blsh_cuda_check(ctx, r, "cudaEventCreate");
+        }
+    }
+    T.cap = max_launches;
+    T.on = true;
+    return BLSH_OK;
+}
+
+extern "C" int blsh_timing_end(blsh_ctx *ctx, int32_t max, const char **names, float *ms, int32_t *n) {
+    if (!ctx) return BLSH_EINVAL;
+    if (max < 0 || (max > 0 && (!names || !ms)) || !n) return blsh_fail(ctx, BLSH_EINVAL, "bad output arrays");
+    blsh_device_guard g(ctx->device);
+    auto &T = ctx->timing;
+    int out = 0, rc = BLSH_OK;
+    for (int i = 0; i < T.n && out < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(T.ev[2 * i + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, T.ev[2 * i], T.ev[2 * i + 1]);
+        if (e != cudaSuccess) {
+            rc = blsh_cuda_check(ctx, e, "cudaEventElapsedTime");
+            break;
+        }
+        names[out] = T.name[i];
+        ms[out++] = t;
+    }
+    *n = out;
+    timing_release(ctx);
+    return rc;
 }

@@ -815,8 +815,9 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
         BLSH_CUDA(ctx, cudaMemsetAsync(A.ck, 0, (size_t)N * A.ck_words * 4, s));
 
     const unsigned grid = (unsigned)((n + 255) / 256 < 65535ll * 16 ? (n + 255) / 256 : 65535ll * 16);
+    blsh_time_start(ctx, s);
     band_keys_kernel<<<grid, 256, 0, s>>>(A, keys[0], vals[0]);
-    BLSH_LAUNCHED(ctx, "band keys");
+    BLSH_LAUNCHED(ctx, "band_keys_kernel");
 
     const int key_bits = kind == BLSH_COSINE ? band_bits + rows : (A.exact_classes ? 32 : 64);
     const int passes = (key_bits + 7) / 8;
@@ -824,19 +825,24 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
+        blsh_time_start(ctx, s);
         digit_hist_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, (int)tiles);
-        BLSH_LAUNCHED(ctx, "radix histogram");
+        BLSH_LAUNCHED(ctx, "digit_hist_kernel");
+        blsh_time_start(ctx, s);
         BLSH_CUDA(ctx, blsh_scan::exclusive_scan<uint32_t>(hist, hist, 256 * tiles, (uint32_t *)(ws + L.partial),
                                                            (uint32_t *)(ws + L.grand), s));
         ctx->launches.fetch_add(3, std::memory_order_relaxed);
+        blsh_time_stop(ctx, "exclusive scan (3 launches)");
+        blsh_time_start(ctx, s);
         digit_scatter_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n, shift, hist,
                                                                       (int)tiles, keys[cur ^ 1], vals[cur ^ 1]);
-        BLSH_LAUNCHED(ctx, "radix scatter");
+        BLSH_LAUNCHED(ctx, "digit_scatter_kernel");
         cur ^= 1;
     }
     if (A.exact_classes) {
+        blsh_time_start(ctx, s);
         class_id_kernel<<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n);
-        BLSH_LAUNCHED(ctx, "class ids");
+        BLSH_LAUNCHED(ctx, "class_id_kernel");
     }
     const bool staged = (kind == BLSH_COSINE || A.exact_classes) && A.ck_words <= kStageWords;
     const size_t smem = staged ? emit_cos_smem(A.ck_words) : 0;
@@ -850,6 +856,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 4>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            blsh_time_start(ctx, s);
             emit_cos_tile_kernel<false, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
                                                                     win_cap);
         } else {
@@ -857,17 +864,22 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 8>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            blsh_time_start(ctx, s);
             emit_cos_tile_kernel<false, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
                                                                     win_cap);
         }
     } else {
+        blsh_time_start(ctx, s);
         emit_kernel<false><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     }
-    BLSH_LAUNCHED(ctx, "pair count");
+    BLSH_LAUNCHED(ctx, staged ? "emit_cos_tile_kernel (count pass)" : "emit_kernel (count pass)");
+    blsh_time_start(ctx, s);
     BLSH_CUDA(ctx, blsh_scan::exclusive_scan<unsigned long long>(counts, counts, n,
                                                                  (unsigned long long *)(ws + L.partial),
                                                                  (unsigned long long *)n_pairs, s));
     ctx->launches.fetch_add(3, std::memory_order_relaxed);
+    blsh_time_stop(ctx, "exclusive scan (3 launches)");
+    blsh_time_start(ctx, s);
     if (staged && A.ck_words <= 16)
         emit_cos_tile_kernel<true, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
                                                                win_cap);
@@ -876,8 +888,9 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
                                                                win_cap);
     else
         emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
-    BLSH_LAUNCHED(ctx, "pair write");
+    BLSH_LAUNCHED(ctx, staged ? "emit_cos_tile_kernel (write pass)" : "emit_kernel (write pass)");
+    blsh_time_start(ctx, s);
     check_cap_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs, cap, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "capacity check");
+    BLSH_LAUNCHED(ctx, "check_cap_kernel");
     return BLSH_OK;
 }

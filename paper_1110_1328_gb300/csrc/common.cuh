@@ -10,6 +10,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "blsh.h"
 
@@ -41,6 +42,15 @@ struct blsh_ctx {
     std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
     std::atomic<long long> launches{0};            // kernels launched through this context
     std::mutex mu;
+    // per-launch device timing (blsh_timing_begin/_end): while `on`, each
+    // launch is bracketed by a pair of events on its stream
+    struct {
+        bool on = false, open = false;
+        int cap = 0, n = 0;
+        cudaStream_t s = nullptr;
+        std::vector<cudaEvent_t> ev;        // [2 cap]: start, stop of record i
+        std::vector<const char *> name;     // [cap]: kernel name of record i
+    } timing;
 };
 
 struct blsh_tables {
@@ -73,11 +83,38 @@ int blsh_cuda_check(blsh_ctx *ctx, cudaError_t e, const char *what);
     } while (0)
 
 // Checks the launch that was just enqueued and counts it.
+// Timing of the next launch on stream s: its start event (only while timing
+// is on, records remain and s is not being captured into a graph).
+static inline void blsh_time_start(blsh_ctx *ctx, cudaStream_t s) {
+    auto &T = ctx->timing;
+    T.open = false;
+    if (!T.on || T.n >= T.cap) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventRecord(T.ev[2 * T.n], s) != cudaSuccess) return;
+    T.open = true;
+    T.s = s;
+}
+
+// The stop event of the launch started by blsh_time_start, named `what`.
+static inline void blsh_time_stop(blsh_ctx *ctx, const char *what) {
+    auto &T = ctx->timing;
+    if (!T.open) return;
+    T.open = false;
+    if (cudaEventRecord(T.ev[2 * T.n + 1], T.s) == cudaSuccess) T.name[T.n++] = what;
+}
+
+// After each kernel launch: the launch error check, the launch count and the
+// timing record (`what` is the kernel's name).
 #define BLSH_LAUNCHED(ctx, what)                                  \
     do {                                                          \
         cudaError_t e_ = cudaGetLastError();                      \
-        if (e_ != cudaSuccess) return blsh_cuda_check(ctx, e_, what); \
+        if (e_ != cudaSuccess) {                                  \
+            (ctx)->timing.open = false;                           \
+            return blsh_cuda_check(ctx, e_, what);                \
+        }                                                         \
         (ctx)->launches.fetch_add(1, std::memory_order_relaxed);  \
+        blsh_time_stop(ctx, what);                                \
     } while (0)
 
 static inline bool blsh_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }

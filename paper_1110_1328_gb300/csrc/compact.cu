@@ -126,11 +126,13 @@ extern "C" int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, con
     if (ctas > most) ctas = most;
     if (ctas < 1) ctas = 1;
     const bool vec = blsh_aligned(status, 16);
+    blsh_time_start(ctx, s);
     compact_count<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, vec,
                                                       ctx->scratch);
-    BLSH_LAUNCHED(ctx, "compaction count");
+    BLSH_LAUNCHED(ctx, "compact_count");
+    blsh_time_start(ctx, s);
     compact_write<<<(unsigned)ctas, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, vec, out_idx,
                                                       cap, (long long *)n_out, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "compaction write");
+    BLSH_LAUNCHED(ctx, "compact_write");
     return BLSH_OK;
 }

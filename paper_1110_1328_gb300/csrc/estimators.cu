@@ -198,10 +198,11 @@ extern "C" int blsh_estimate_mle(blsh_ctx *ctx, int32_t kind, int32_t n_hashes, 
     const long long groups = (P + 3) / 4 * 4;
     const long long blocks = (groups * 8 + 255) / 256;
     const long long cap = (long long)ctx->sm_count * 16;
+    blsh_time_start(ctx, s);
     mle_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
         reinterpret_cast<const uint2 *>(pairs), P, reinterpret_cast<const long long *>(P_dev), sig, N, sig_words,
         kind, n_hashes, m_star, m, est, keep, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "mle kernel");
+    BLSH_LAUNCHED(ctx, "mle_kernel");
     return BLSH_OK;
 }
 
@@ -217,11 +218,13 @@ extern "C" int blsh_fit_beta_prior(blsh_ctx *ctx, const uint32_t *pairs, int64_t
     cudaStream_t s = blsh_stream(stream);
     const long long cap = (long long)ctx->sm_count * 8;
     const long long blocks = (r + 7) / 8;
+    blsh_time_start(ctx, s);
     sample_jaccard_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
         reinterpret_cast<const uint2 *>(pairs), r, indptr, indices, N, sims, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "sample jaccard kernel");
+    BLSH_LAUNCHED(ctx, "sample_jaccard_kernel");
+    blsh_time_start(ctx, s);
     prior_moments_kernel<<<1, 256, 0, s>>>(sims, r, out_device);
-    BLSH_LAUNCHED(ctx, "prior moments kernel");
+    BLSH_LAUNCHED(ctx, "prior_moments_kernel");
     if (out_host) {
         BLSH_CUDA(ctx, cudaMemcpyAsync(out_host, out_device, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
         BLSH_CUDA(ctx, cudaStreamSynchronize(s));

@@ -154,6 +154,7 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 }
 
 constexpr int kSrpMaxPerThread = 16;
+constexpr int kSrpBatch = 8;       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
 constexpr int kSrpQ16Batch = 1;    // the same for two-byte rows
 constexpr int kSrpChunk = 256;
 
@@ -277,27 +278,50 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
         float acc[4 * V], mag[4 * V];
 #pragma unroll
         for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
-        for (long long k = s; k < e; ++k) {
-            uint32_t ix = __ldg(indices + k);
-            float v = __ldg(values + k);
-            if (ix >= dim) {   // malformed row: counted, contributes nothing
-                bad += t == 0;
-                ix = 0;
-                v = 0.0f;
+        // the row's nonzeros 32 at a time: lane l of every warp loads entry
+        // l (coalesced), then the gathers of kSrpBatch / V entries are issued
+        // together (their indices come by shuffle), so that a long row is not
+        // a chain of dependent loads
+        constexpr int NB = kSrpBatch / V > 0 ? kSrpBatch / V : 1;
+        for (long long k0 = s; k0 < e; k0 += 32) {
+            const int cnt = e - k0 < 32 ? (int)(e - k0) : 32;
+            uint32_t my_ix = 0;
+            float my_v = 0.0f;
+            if (lane < cnt) {
+                my_ix = __ldg(indices + k0 + lane);
+                my_v = __ldg(values + k0 + lane);
+                if (my_ix >= dim) {   // malformed entry: counted once, contributes nothing
+                    bad += t < 32;
+                    my_ix = 0;
+                    my_v = 0.0f;
+                }
             }
-            const float av = fabsf(v);
-            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
+            for (int u0 = 0; u0 < cnt; u0 += NB) {
+                float4 r[NB][V];
+                float vb[NB];
 #pragma unroll
-            for (int g = 0; g < V; ++g) {
-                const float4 r = __ldg(Rrow + g * T);
-                acc[4 * g + 0] = __fmaf_rn(v, r.x, acc[4 * g + 0]);
-                acc[4 * g + 1] = __fmaf_rn(v, r.y, acc[4 * g + 1]);
-                acc[4 * g + 2] = __fmaf_rn(v, r.z, acc[4 * g + 2]);
-                acc[4 * g + 3] = __fmaf_rn(v, r.w, acc[4 * g + 3]);
-                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r.x), mag[4 * g + 0]);
-                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r.y), mag[4 * g + 1]);
-                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r.z), mag[4 * g + 2]);
-                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r.w), mag[4 * g + 3]);
+                for (int b = 0; b < NB; ++b) {
+                    const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                    vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
+                    const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
+#pragma unroll
+                    for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const float v = vb[b], av = fabsf(v);
+#pragma unroll
+                    for (int g = 0; g < V; ++g) {
+                        acc[4 * g + 0] = __fmaf_rn(v, r[b][g].x, acc[4 * g + 0]);
+                        acc[4 * g + 1] = __fmaf_rn(v, r[b][g].y, acc[4 * g + 1]);
+                        acc[4 * g + 2] = __fmaf_rn(v, r[b][g].z, acc[4 * g + 2]);
+                        acc[4 * g + 3] = __fmaf_rn(v, r[b][g].w, acc[4 * g + 3]);
+                        mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[b][g].x), mag[4 * g + 0]);
+                        mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[b][g].y), mag[4 * g + 1]);
+                        mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[b][g].z), mag[4 * g + 2]);
+                        mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[b][g].w), mag[4 * g + 3]);
+                    }
+                }
             }
         }
         const float n = (float)(e - s);
@@ -614,15 +638,17 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
     uint2 *q = ctx->recheck_queue;
     blsh_dev_scratch *scr = ctx->scratch;
+    blsh_time_start(ctx, s);
     switch (V) {
     case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
     case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
     case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
     default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
     }
-    BLSH_LAUNCHED(ctx, "srp sparse kernel");
+    BLSH_LAUNCHED(ctx, "srp_sparse4_kernel");
+    blsh_time_start(ctx, s);
     srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig, scr);
-    BLSH_LAUNCHED(ctx, "srp recheck kernel");
+    BLSH_LAUNCHED(ctx, "srp_recheck_kernel");
     return BLSH_OK;
 }
 
@@ -635,6 +661,22 @@ int srp_threads(int bits, int *per_thread) {
 }
 
 }  // namespace
+
+// minhash_kernel over every set, then minhash_big_kernel over the long sets
+// the first one queued.
+template <int WV>
+int minhash_launch(blsh_ctx *ctx, cudaStream_t s, unsigned grid, unsigned big_grid, const int64_t *indptr,
+                   const uint32_t *indices, int64_t N, int n_hashes, const uint32_t *a, const uint32_t *b,
+                   uint32_t *sig, uint2 *big) {
+    blsh_dev_scratch *scr = ctx->scratch;
+    blsh_time_start(ctx, s);
+    minhash_kernel<WV><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
+    BLSH_LAUNCHED(ctx, "minhash_kernel");
+    blsh_time_start(ctx, s);
+    minhash_big_kernel<WV><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
+    BLSH_LAUNCHED(ctx, "minhash_big_kernel");
+    return BLSH_OK;
+}
 
 extern "C" int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, int64_t N,
                             int32_t n_hashes, const uint32_t *a, const uint32_t *b, uint32_t *sig, void *stream) {
@@ -655,23 +697,13 @@ extern "C" int blsh_minhash(blsh_ctx *ctx, const int64_t *indptr, const uint32_t
     // long sets go to minhash_big_kernel through the context's work queue
     uint2 *big = ctx->recheck_queue;
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work3, 0, sizeof(unsigned long long), s));
-    blsh_dev_scratch *scr = ctx->scratch;
-    if (words % 8 == 0) {
-        minhash_kernel<8><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
-        minhash_big_kernel<8><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
-    } else if (words % 4 == 0) {
-        minhash_kernel<4><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
-        minhash_big_kernel<4><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
-    } else if (words % 2 == 0) {
-        minhash_kernel<2><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
-        minhash_big_kernel<2><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
-    } else {
-        minhash_kernel<1><<<grid, 256, 0, s>>>(indptr, indices, N, n_hashes, a, b, sig, scr, big);
-        minhash_big_kernel<1><<<big_grid, 1024, 0, s>>>(indptr, indices, n_hashes, a, b, sig, scr, big);
+    const int wv = words % 8 == 0 ? 8 : words % 4 == 0 ? 4 : words % 2 == 0 ? 2 : 1;
+    switch (wv) {
+    case 8: return minhash_launch<8>(ctx, s, grid, big_grid, indptr, indices, N, n_hashes, a, b, sig, big);
+    case 4: return minhash_launch<4>(ctx, s, grid, big_grid, indptr, indices, N, n_hashes, a, b, sig, big);
+    case 2: return minhash_launch<2>(ctx, s, grid, big_grid, indptr, indices, N, n_hashes, a, b, sig, big);
+    default: return minhash_launch<1>(ctx, s, grid, big_grid, indptr, indices, N, n_hashes, a, b, sig, big);
     }
-    ctx->launches.fetch_add(1, std::memory_order_relaxed);   // the second of the two launches
-    BLSH_LAUNCHED(ctx, "minhash kernel");
-    return BLSH_OK;
 }
 
 extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values,
@@ -699,8 +731,9 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
         const int rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, 0, bits, nullptr, sig, s);
         if (rc != -1) return rc;
     }
+    blsh_time_start(ctx, s);
     srp_sparse_kernel<float><<<grid, T, 0, s>>>(indptr, indices, values, N, R, dim, bits, per_thread, sig, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "srp sparse kernel");
+    BLSH_LAUNCHED(ctx, "srp_sparse_kernel");
     return BLSH_OK;
 }
 
@@ -717,8 +750,9 @@ int blsh_srp_dense_simt(blsh_ctx *ctx, const float *X, int64_t N, int32_t d, con
     }
     const long long cap = (long long)ctx->sm_count * 16;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
+    blsh_time_start(ctx, s);
     srp_dense_simt_kernel<<<grid, T, smem, s>>>(X, N, d, R, bits, per_thread, sig, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "srp dense kernel");
+    BLSH_LAUNCHED(ctx, "srp_dense_simt_kernel");
     return BLSH_OK;
 }
 
@@ -730,8 +764,9 @@ extern "C" int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, 
     cudaStream_t s = blsh_stream(stream);
     const long long blocks = (n + 255) / 256;
     const long long cap = (long long)ctx->sm_count * 16;
+    blsh_time_start(ctx, s);
     quantize_gaussian_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, n, q, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "quantize kernel");
+    BLSH_LAUNCHED(ctx, "quantize_gaussian_kernel");
     return BLSH_OK;
 }
 
@@ -748,9 +783,22 @@ extern "C" int blsh_srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const 
     if (!blsh_aligned(indptr, 8) || !blsh_aligned(R, 16)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
     if (N == 0) return BLSH_OK;
     blsh_device_guard g(ctx->device);
-    const int rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, col_begin, col_count, row_mask, sig,
-                                   blsh_stream(stream));
-    return rc == -1 ? blsh_fail(ctx, BLSH_EINVAL, "col_count/128 needs a divisor in 1..8 with at most 4 groups") : rc;
+    // a column count the kernel cannot take in one launch (col_count / 128
+    // without a divisor in 1..8 that leaves at most 4 float4 groups per
+    // thread) is split: the largest piece it can take first, and so on
+    // (128 columns always can)
+    for (int c0 = col_begin, left = col_count; left > 0;) {
+        int rc = -1, piece = left;
+        for (; piece > 0; piece -= 128) {
+            rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, c0, piece, row_mask, sig,
+                                 blsh_stream(stream));
+            if (rc != -1) break;
+        }
+        if (rc != BLSH_OK) return rc == -1 ? blsh_fail(ctx, BLSH_EINVAL, "no launch shape") : rc;
+        c0 += piece;
+        left -= piece;
+    }
+    return BLSH_OK;
 }
 
 extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
@@ -776,21 +824,24 @@ extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const u
         const int T8 = 32 * wt, V = groups / T8;
         BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
         uint2 *q = ctx->recheck_queue;
+        blsh_time_start(ctx, s);
         if (V == 1)
             srp_sparse_q16_kernel<1, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
         else
             srp_sparse_q16_kernel<2, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
-        BLSH_LAUNCHED(ctx, "srp sparse q16 kernel");
+        BLSH_LAUNCHED(ctx, "srp_sparse_q16_kernel");
+        blsh_time_start(ctx, s);
         srp_recheck_kernel<uint16_t><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, Rq, dim, bits,
                                                                          sig, ctx->scratch);
-        BLSH_LAUNCHED(ctx, "srp recheck kernel");
+        BLSH_LAUNCHED(ctx, "srp_recheck_kernel");
         return BLSH_OK;
     }
     int per_thread;
     const int T = srp_threads(bits, &per_thread);
     if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");
+    blsh_time_start(ctx, s);
     srp_sparse_kernel<uint16_t><<<grid, T, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, per_thread, sig,
                                                    ctx->scratch);
-    BLSH_LAUNCHED(ctx, "srp sparse q16 kernel");
+    BLSH_LAUNCHED(ctx, "srp_sparse_kernel");
     return BLSH_OK;
 }

@@ -352,22 +352,28 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
     // survivors: queued (balanced over warps), then any beyond the queue in place
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, 2 * sizeof(unsigned long long), s));   // work2, work3
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(ctx->recheck_queue);
+    blsh_time_start(ctx, s);
     lite_collect_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(L, queue);
-    BLSH_LAUNCHED(ctx, "lite survivor queue");
+    BLSH_LAUNCHED(ctx, "lite_collect_kernel");
     int occ = 0;
     const size_t smem = 8 * 2 * kLiteStage * sizeof(uint32_t);   // 32 KB per CTA of 8 warps
     if (values) {
         BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_queue_kernel<true>, 256, smem));
+        blsh_time_start(ctx, s);
         lite_queue_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L, queue);
-        BLSH_LAUNCHED(ctx, "lite queued exact similarities");
+        BLSH_LAUNCHED(ctx, "lite_queue_kernel");
+        blsh_time_start(ctx, s);
         lite_exact_kernel<true><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
+        BLSH_LAUNCHED(ctx, "lite_exact_kernel");
     } else {
         BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_queue_kernel<false>, 256, smem));
+        blsh_time_start(ctx, s);
         lite_queue_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L, queue);
-        BLSH_LAUNCHED(ctx, "lite queued exact similarities");
+        BLSH_LAUNCHED(ctx, "lite_queue_kernel");
+        blsh_time_start(ctx, s);
         lite_exact_kernel<false><<<(occ > 0 ? occ : 1) * ctx->sm_count, 256, smem, s>>>(L);
+        BLSH_LAUNCHED(ctx, "lite_exact_kernel");
     }
-    BLSH_LAUNCHED(ctx, "lite exact-similarity kernel");
     return BLSH_OK;
 }
 

@@ -573,12 +573,14 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
     const float m = margin > rigorous ? margin : rigorous;
     unsigned char *ws = (unsigned char *)workspace;
     const long long Npad = (N + BM - 1) / BM * BM;
+    blsh_time_start(ctx, s);
     srp_dense_prep_x<<<(unsigned)((Npad + 7) / 8 < 65535ll * 8 ? (Npad + 7) / 8 : 65535ll * 8), 256, 0, s>>>(
         X, N, Npad, d, ws + L.xh, ws + L.xl, (float *)(ws + L.xn));
-    BLSH_LAUNCHED(ctx, "srp dense prep (X)");
+    BLSH_LAUNCHED(ctx, "srp_dense_prep_x");
+    blsh_time_start(ctx, s);
     srp_dense_prep_r<<<(bits + 127) / 128, 128, 0, s>>>(R, d, bits, ws + L.rh, ws + L.rl, (float *)(ws + L.rn),
                                                         (float *)(ws + L.rt));
-    BLSH_LAUNCHED(ctx, "srp dense prep (R)");
+    BLSH_LAUNCHED(ctx, "srp_dense_prep_r");
     unsigned long long *qcount = (unsigned long long *)(ws + L.qc);
     uint2 *queue = (uint2 *)(ws + L.q);
     BLSH_CUDA(ctx, cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), s));
@@ -592,12 +594,14 @@ extern "C" int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t 
     }
     const long long tiles = (long long)(bits / BN) * (Npad / BM);
     const unsigned grid = (unsigned)(tiles < ctx->sm_count ? tiles : ctx->sm_count);
+    blsh_time_start(ctx, s);
     srp_dense_tc_persistent<<<grid, kTcThreads, smem, s>>>(ws + L.xh, ws + L.xl, ws + L.rh, ws + L.rl,
                                                           (float *)(ws + L.xn), (float *)(ws + L.rn), N, d, bits, m,
                                                           sig, queue, L.qcap, qcount, X, R, tiles, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "srp dense tensor-core kernel");
+    BLSH_LAUNCHED(ctx, "srp_dense_tc_persistent");
+    blsh_time_start(ctx, s);
     srp_dense_recheck_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(queue, L.qcap, qcount, X, (float *)(ws + L.rt), d,
                                                                  bits, sig, ctx->scratch);
-    BLSH_LAUNCHED(ctx, "srp dense recheck kernel");
+    BLSH_LAUNCHED(ctx, "srp_dense_recheck_kernel");
     return BLSH_OK;
 }

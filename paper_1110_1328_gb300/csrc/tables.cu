@@ -229,9 +229,12 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     int flags[2] = {0, 0};
     e = cudaMemsetAsync(tab->flags, 0, 2 * sizeof(int), s);
     if (e == cudaSuccess) {
+        blsh_time_start(ctx, s);
         build_tables_kernel<<<tab->levels, 256, 0, s>>>(A);
         e = cudaGetLastError();
         ctx->launches.fetch_add(1, std::memory_order_relaxed);
+        if (e == cudaSuccess) blsh_time_stop(ctx, "build_tables_kernel");
+        ctx->timing.open = false;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, tab->flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -298,8 +298,9 @@ int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cud
         if (grid > cap) grid = cap;
     }
     if (grid == 0) return BLSH_OK;
+    blsh_time_start(ctx, s);
     kern<<<(unsigned)grid, plan.block, smem, s>>>(A);
-    BLSH_LAUNCHED(ctx, "verify kernel");
+    BLSH_LAUNCHED(ctx, "verify_kernel");
     return BLSH_OK;
 }
 
@@ -582,8 +583,9 @@ extern "C" int blsh_verify_resume(blsh_ctx *ctx, const blsh_tables *tab, const u
     const long long groups = (P + 15) / 16;
     const long long cap = (long long)ctx->sm_count * 8;
     const long long blocks = (groups + 255) / 256;
+    blsh_time_start(ctx, s);
     verify_resume_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A, tab->p.kind,
                                                                              blsh_aligned(status, 16) ? 1 : 0);
-    BLSH_LAUNCHED(ctx, "verify resume kernel");
+    BLSH_LAUNCHED(ctx, "verify_resume_kernel");
     return BLSH_OK;
 }

@@ -368,3 +368,31 @@ def test_srp_sparse_cols_selected_rows(B, ctx):
     B.blsh_srp_sparse_cols(ctx, ip, ix, val, torch.from_numpy(R).to(dev), sig, 512, 1536)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("cols", [(0, 384, 1664), (0, 128, 1920), (256, 640, 1152)])
+def test_srp_sparse_cols_ragged_rows_and_split_ranges(B, ctx, cols):
+    """Rows of 0, 1, 7, 31, 32, 33, 200 and 1,500 nonzeros (the kernel reads
+    a row's entries 32 at a time and issues several gathers together), and
+    column ranges that take more than one launch (1,664 = 13 x 128 columns):
+    bit-exact to the oracle."""
+    rng = np.random.default_rng(sum(cols))
+    dim, bits = 5000, 2048
+    lengths = [0, 1, 7, 31, 32, 33, 200, 1500, 64, 95]
+    indptr = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    indices = np.concatenate([np.sort(rng.choice(dim, n, replace=False)) for n in lengths]).astype(np.uint32)
+    values = rng.standard_normal(int(indptr[-1])).astype(np.float32)
+    vecs = synth.CSR(indptr, indices, values, dim)
+    R = synth.gaussian_matrix(dim, bits, seed=33)
+    want = O.srp_sparse(vecs, R)
+    ip, ix, val = csr_dev(vecs)
+    Rd = torch.from_numpy(R).to(dev)
+    sig = torch.full((len(lengths), bits // 32), 0x5A5A5A5A, dtype=torch.int32, device=dev)
+    c0, c1, c2 = cols
+    B.blsh_srp_sparse_cols(ctx, ip, ix, val, Rd, sig, c0, c1 - c0)
+    B.blsh_srp_sparse_cols(ctx, ip, ix, val, Rd, sig, c1, c2)
+    assert B.blsh_status(ctx) == 0
+    got = sig.cpu().numpy().view(np.uint32)
+    w0, w1 = c0 // 32, (c1 + c2) // 32
+    assert np.array_equal(got[:, w0:w1], want[:, w0:w1])
+    assert np.all(got[:, :w0] == 0x5A5A5A5A) and np.all(got[:, w1:] == 0x5A5A5A5A)
