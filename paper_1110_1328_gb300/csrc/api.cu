@@ -93,6 +93,7 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
     {
         blsh_device_guard g(ctx->device);
         timing_release(ctx);
+        if (ctx->plane) cudaFree(ctx->plane);
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
     }

@@ -38,6 +38,8 @@ struct blsh_ctx {
     size_t smem_optin = 0;
     blsh_dev_scratch *scratch = nullptr;
     uint2 *recheck_queue = nullptr;                   // [BLSH_RECHECK_CAP] (row, bit) of undecided SRP signs
+    void *plane = nullptr;                            // verification: [plane_cap] first two words of each row
+    long long plane_cap = 0;
     char err[512] = {0};
     std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
     std::atomic<long long> launches{0};            // kernels launched through this context

@@ -262,17 +262,22 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values, long long N,
                                                           const float *__restrict__ R, long long dim, int bits,
-                                                          int col0, const uint8_t *__restrict__ row_mask,
+                                                          int col_first, int pieces,
+                                                          const uint8_t *__restrict__ row_mask,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
                                                           uint2 *__restrict__ queue) {
-    // columns col0 .. col0 + 4 V T - 1 of the signatures of the rows row_mask
-    // selects (all rows when it is NULL)
+    // columns col_first .. col_first + pieces 4 V T - 1 of the signatures of
+    // the rows row_mask selects (all rows when it is NULL); a CTA takes one
+    // (row, piece of 4 V T columns) at a time, so that a few selected rows
+    // still spread over many CTAs
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int words = bits >> 5;
     unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
+    for (long long item = blockIdx.x; item < N * pieces; item += gridDim.x) {
+        const long long row = item / pieces;
+        const int col0 = col_first + (int)(item - row * pieces) * 4 * V * T;
         if (row_mask && !row_mask[row]) continue;
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
         float acc[4 * V], mag[4 * V];
@@ -625,25 +630,28 @@ __global__ void __launch_bounds__(256) srp_dense_simt_kernel(const float *__rest
 int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
                     const float *R, int64_t dim, int bits, int col0, int ncols, const uint8_t *row_mask,
                     uint32_t *sig, cudaStream_t s) {
-    // T4 = 32 * (largest divisor of groups/32 up to 8) threads, V = groups / T4
-    // float4 groups per thread
-    const int groups = ncols / 4;
+    // selected rows (usually few): pieces of 512 columns, one per CTA; all
+    // rows: the whole range per CTA.  T4 = 32 * (largest divisor of
+    // groups/32 up to 8) threads, V = groups / T4 float4 groups per thread
+    const int piece = row_mask && ncols % 512 == 0 ? 512 : ncols;
+    const int pieces = ncols / piece;
+    const int groups = piece / 4;
     int wt = 8;
     while ((groups / 32) % wt) --wt;
     const int T4 = 32 * wt, V = groups / T4;
     if (V < 1 || V > 4) return -1;
     // many small CTAs (rows have very different lengths): 32 per SM measured best
     const long long cap = (long long)ctx->sm_count * 32;
-    const unsigned grid = (unsigned)(N < cap ? N : cap);
+    const unsigned grid = (unsigned)(N * pieces < cap ? N * pieces : cap);
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
     uint2 *q = ctx->recheck_queue;
     blsh_dev_scratch *scr = ctx->scratch;
     blsh_time_start(ctx, s);
     switch (V) {
-    case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
-    case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
-    case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
-    default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, row_mask, sig, scr, q); break;
+    case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
     }
     BLSH_LAUNCHED(ctx, "srp_sparse4_kernel");
     blsh_time_start(ctx, s);

@@ -30,7 +30,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
-template <int KIND, int G, int U, bool PERSIST>
+template <int KIND, int G, int U, bool PERSIST, bool PLANE>
 __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     // minMatches is staged in shared memory; the concentration bitmap (up to
     // tens of KB, consulted only by pairs that pass the pruning test) is
@@ -166,20 +166,76 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             }
         } else {
             if (active) {
-                const uint4 a = ldg4(rx + w), b = ldg4(ry + w);
-                const uint32_t x[4] = {a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w};
-                w += 4;
+                // The step's words (four, or the plane's two) are counted and
+                // every completed chunk is tested, recording where each
+                // algorithm stops and why; the outputs of a stop are written
+                // once, after the words.
+                int st1 = -1, j1 = 0, m1 = 0, stl = -1, jl = 0;
+                auto words = [&](uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3, int i0, int i1) {
+                    const uint32_t x[4] = {x0, x1, x2, x3};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (active) {
+                    for (int i = 0; i < 4; ++i) {
+                        if (i < i0 || i >= i1 || !active) continue;
                         acc += 32 - __popc(x[i]);
-                        if (++sub == A.chunk_words) {
-                            m += acc;
-                            acc = 0;
-                            sub = 0;
-                            decide();
+                        if (++sub < A.chunk_words) continue;
+                        m += acc;
+                        acc = 0;
+                        sub = 0;
+                        const bool pruned = m < s_mm[j];
+                        if (a1) {
+                            int st = -1;
+                            if (pruned) st = BLSH_PRUNED;
+                            else if (!A.lite && ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u))
+                                st = BLSH_ACCEPT;
+                            else if (j + 1 == A.levels) st = A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX;
+                            else if (j + 1 == A.cap_levels) st = BLSH_NEEDS_HASHES;
+                            if (st >= 0) {
+                                st1 = st;
+                                j1 = j;
+                                m1 = m;
+                                a1 = false;
+                            }
                         }
+                        if (al) {
+                            if (pruned || j + 1 == A.lite_levels) {
+                                stl = pruned ? BLSH_PRUNED : BLSH_LITE_SURVIVOR;
+                                jl = j;
+                                al = false;
+                            }
+                        }
+                        active = a1 || al;
+                        if (active) ++j;
                     }
+                };
+                if (PLANE && w == 0) {   // the first two words from the plane (L2-resident)
+                    const uint2 a = __ldg(A.plane + cur_pair.x), b = __ldg(A.plane + cur_pair.y);
+                    words(a.x ^ b.x, a.y ^ b.y, 0u, 0u, 0, 2);
+                    if (active) {
+                        const uint4 c = ldg4(rx), d = ldg4(ry);
+                        words(0u, 0u, c.z ^ d.z, c.w ^ d.w, 2, 4);
+                    }
+                } else {
+                    const uint4 a = ldg4(rx + w), b = ldg4(ry + w);
+                    words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
+                }
+                w += 4;
+                if (st1 >= 0 && g == 0) {
+                    A.status[q] = (uint8_t)st1;
+                    if (A.n_used) A.n_used[q] = (uint16_t)((j1 + 1) * A.k);
+                    if (A.m_out) A.m_out[q] = (uint16_t)m1;
+                    if (st1 == BLSH_NEEDS_HASHES) {   // Algorithm 1 needs hashes not yet computed
+                        A.need[cur_pair.x] = 1;
+                        A.need[cur_pair.y] = 1;
+                    } else {
+                        // the estimate is an output only for pairs that are kept
+                        if (A.est_out && st1 != BLSH_PRUNED)
+                            A.est_out[q] = __ldg(A.est_tab + (size_t)j1 * A.est_stride + m1);
+                        atomicAdd(&s_hist[j1], 1u);
+                    }
+                }
+                if (stl >= 0 && g == 0) {
+                    A.lstatus[q] = (uint8_t)stl;
+                    if (A.ln_used) A.ln_used[q] = (uint16_t)((jl + 1) * A.k);
                 }
             }
         }
@@ -274,9 +330,16 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             if (s_hist[i]) atomicAdd(A.stop_hist + i, (unsigned long long)s_hist[i]);
 }
 
-template <int KIND, int G, int U, bool PERSIST>
+// plane[i] = words 0 and 1 of row i
+__global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restrict__ sig, long long N, int W,
+                                                         uint2 *__restrict__ plane) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        plane[i] = __ldg(reinterpret_cast<const uint2 *>(sig + (size_t)i * W));
+}
+
+template <int KIND, int G, int U, bool PERSIST, bool PLANE = false>
 int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
-    auto kern = verify_kernel<KIND, G, U, PERSIST>;
+    auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE>;
     const size_t smem = sizeof(int32_t) * A.levels * 2;
     if (smem > 48 * 1024) {
         if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "tables too large for shared memory");
@@ -306,7 +369,9 @@ int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cud
 
 template <bool PERSIST>
 int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind, cudaStream_t s) {
-    if (kind == BLSH_COSINE) return launch_kernel<BLSH_COSINE, 1, 1, PERSIST>(ctx, A, plan, s);
+    if (kind == BLSH_COSINE)
+        return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, PERSIST, true>(ctx, A, plan, s)
+                       : launch_kernel<BLSH_COSINE, 1, 1, PERSIST, false>(ctx, A, plan, s);
     switch (plan.group) {
     case 1: return launch_kernel<BLSH_JACCARD, 1, 8, PERSIST>(ctx, A, plan, s);
     case 4: return launch_kernel<BLSH_JACCARD, 4, 2, PERSIST>(ctx, A, plan, s);
@@ -353,8 +418,38 @@ int blsh_check_plan(const blsh_plan &plan, int kind, int k) {
     return BLSH_OK;
 }
 
-int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
-    const int kind = A.chunk_words == A.k ? BLSH_JACCARD : BLSH_COSINE;
+// Cosine signatures larger than this do not stay in L2 between the random
+// row reads of the pairs; the first two words of every row then go into a
+// dense plane (8 bytes per object) that does, and the first step of every
+// pair reads them there.
+constexpr long long kPlaneMinBytes = 64ll << 20;
+
+int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A0, const blsh_plan &plan, cudaStream_t s) {
+    const int kind = A0.chunk_words == A0.k ? BLSH_JACCARD : BLSH_COSINE;
+    VerifyArgs A = A0;
+    A.plane = nullptr;
+    if (kind == BLSH_COSINE && A.N * (long long)A.W * 4 > kPlaneMinBytes) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BLSH_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
+        if (ctx->plane_cap < A.N && cs == cudaStreamCaptureStatusNone) {
+            // grown outside stream capture only (a captured call with a
+            // larger N reads its rows instead)
+            BLSH_CUDA(ctx, cudaStreamSynchronize(s));
+            if (ctx->plane) BLSH_CUDA(ctx, cudaFree(ctx->plane));
+            ctx->plane = nullptr;
+            ctx->plane_cap = 0;
+            BLSH_CUDA(ctx, cudaMalloc(&ctx->plane, (size_t)A.N * sizeof(uint2)));
+            ctx->plane_cap = A.N;
+        }
+        if (ctx->plane_cap >= A.N) {
+            const long long blocks = (A.N + 255) / 256, cap = (long long)ctx->sm_count * 8;
+            blsh_time_start(ctx, s);
+            plane_copy_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A.sig, A.N, A.W,
+                                                                                      (uint2 *)ctx->plane);
+            BLSH_LAUNCHED(ctx, "plane_copy_kernel");
+            A.plane = (const uint2 *)ctx->plane;
+        }
+    }
     if (plan.mode == BLSH_PLAN_PERSISTENT) return dispatch<true>(ctx, A, plan, kind, s);
     return dispatch<false>(ctx, A, plan, kind, s);
 }
@@ -401,6 +496,7 @@ int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t 
     A.lsim = nullptr;
     A.cap_levels = A.levels;
     A.need = nullptr;
+    A.plane = nullptr;
     return BLSH_OK;
 }
 

@@ -134,6 +134,30 @@ def test_verify_every_plan_matches_oracle(B, ctx, d):
     assert_same(run_verify(B, ctx, tab, pairs, sig), want, None, p)
 
 
+@pytest.mark.parametrize("d", [TABLE_PARAMS[4], TABLE_PARAMS[7]], ids=["k32-n2048", "k64-n512"])
+def test_verify_large_signature_set_matches_oracle(B, ctx, d):
+    """Cosine signature sets too large for L2 (> 64 MB) are verified with the
+    first two words of every row read from a dense plane: the same outputs
+    as the oracle, every plan."""
+    p = oracle_params(d)
+    sig, pairs = model_signatures(1, d["n_max"], 3001, seed=11)
+    W = sig.shape[1]
+    rows = (64 << 20) // (4 * W) + 4096                   # just past the plane threshold
+    rng = np.random.default_rng(2)
+    big = rng.integers(0, 1 << 32, size=(rows, W), dtype=np.uint64).astype(np.uint32)
+    big[-sig.shape[0]:] = sig                             # the model pairs at the end of the set
+    pairs = pairs + np.uint32(rows - sig.shape[0])
+    pairs = np.concatenate([pairs, rng.integers(0, rows, size=(20000, 2)).astype(np.uint32)])
+    want = O.verify(O.tables(p), pairs, big)
+    tab = gpu_tables(B, ctx, d)
+    for plan in (B.blsh_plan(B.PLAN_PLAIN, 1, 128, 32, 0), B.blsh_plan(B.PLAN_PERSISTENT, 1, 256, 37, 0)):
+        assert_same(run_verify(B, ctx, tab, pairs, big, plan=plan), want, None, p)
+    B.blsh_timing_begin(ctx)
+    res = run_verify(B, ctx, tab, pairs, big)
+    assert [n for n, _ in B.blsh_timing_end(ctx)] == ["plane_copy_kernel", "verify_kernel"]
+    assert_same(res, want, None, p)
+
+
 def test_verify_device_count_and_capacity(B, ctx):
     d = TABLE_PARAMS[4]
     p = oracle_params(d)
