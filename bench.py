@@ -468,7 +468,7 @@ def kernel_work(B, pipe, w, objs, st, nu, lst, need):
     else:   # 32-bit class keys while a row of class ids fits the staging (32 words), else 64-bit band hashes
         kb = 4 if ((bands + 3) & ~3) <= 32 else 8
         obj_rows = N * bands * 4
-    emit = "emit_cos_tile_kernel"
+    emit = "emit_warp_kernel"
     passes = (8 * kb + 7) // 8 if w["kind"] == 0 else (max(1, (bands - 1).bit_length()) + rows + 7) // 8
     sig_bytes = N * bands * rows // 8 if w["kind"] == 1 else N * bands * rows * 4   # the banded hashes
     work["band_keys_kernel"] = (sig_bytes + n * (kb + 4) + obj_rows, "B")

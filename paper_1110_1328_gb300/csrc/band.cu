@@ -351,27 +351,27 @@ __global__ void emit_kernel(BandArgs A, const unsigned long long *keys, const ui
     }
 }
 
-constexpr int kEmitTile = 256;
 constexpr int kEmitWinMax = 768;
 constexpr int kStageWords = 32;          // key rows of up to 128 bytes take this path
-constexpr size_t kEmitSmemBudget = 72 * 1024;
 
 // Staged key rows are cws = (ck_words / 4) | 1 16-byte words apart: an odd
 // stride, so lanes reading different rows hit different banks.
 __host__ __device__ inline int stage_stride(int ck_words) { return (ck_words >> 2) | 1; }
 
-// Positions staged per tile: the tile and up to 512 after it, within the
-// shared-memory budget.
-int emit_cos_win(int ck_words) {
-    const size_t per = (size_t)stage_stride(ck_words) * 16 + 8 + 4;
-    size_t w = kEmitSmemBudget / per;
-    if (w > (size_t)kEmitWinMax) w = kEmitWinMax;
-    return (int)w;
-}
-// The stage, plus each warp's buffer of 32 partner rows and ids.
-size_t emit_cos_smem(int ck_words) {
+// emit_warp_kernel: one warp's part of shared memory (16-byte aligned) for a
+// window of `win` positions, and the largest window (a multiple of 32) that
+// fits the warp's budget.
+__host__ __device__ inline size_t emit_warp_region(int ck_words, int win) {
     const int kw4 = ck_words <= 16 ? 4 : 8;
-    return (size_t)emit_cos_win(ck_words) * (stage_stride(ck_words) * 16 + 8 + 4) + 8 * 32 * (16 * kw4 + 4);
+    const size_t b = (size_t)win * (stage_stride(ck_words) * 16 + 8 + 4) + 32 * 16 * kw4 + 32 * 4;
+    return (b + 15) & ~(size_t)15;
+}
+// (rows up to 64 bytes: two CTAs of eight warps per SM; longer rows: one)
+inline size_t emit_warp_budget(int ck_words) { return ck_words <= 16 ? 13 * 1024 : 26 * 1024; }
+int emit_warp_win(int ck_words) {
+    int w = 32;
+    while (w < kEmitWinMax && emit_warp_region(ck_words, w + 32) <= emit_warp_budget(ck_words)) w += 32;
+    return w;
 }
 
 // First position q >= from with q == n or keys[q] != key, given
@@ -541,47 +541,59 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
     }
 }
 
-// Cosine emission staged in shared memory.  A CTA owns a tile of
-// kEmitTile sorted positions and stages `win` positions from the tile's
-// start (the tile and what follows it): keys, object ids and packed key
-// rows.  Lane l of warp w owns position i = 32 w + l of the tile (its object
-// x, band b and key row in registers) and finds the end of its bucket by a
-// binary search of the staged keys (continued in global memory when the
-// bucket runs past the window).  The warp then walks the partners j of its
-// 32 positions in order; each step reads one staged key row (the same
-// address for every lane: a broadcast) and every lane tests its own pair
-// (x, y_j) on the bands before its b.  Pairs of position i are counted, or
+// Emission staged in shared memory, with warps as independent workers.  A
+// warp takes the next chunk of 32 sorted positions from a counter and
+// stages its own window (the chunk and the positions after it: keys, object
+// ids and the objects' key rows) in its own part of shared memory; no
+// barrier ties it to the other warps, so a warp with long buckets holds up
+// no one.  Lane l owns position l of the chunk (its object x, band b and key
+// row in registers) and finds the end of its bucket by a binary search of
+// the staged keys (continued in global memory when the bucket runs past the
+// window).  Where buckets are long the warp walks the partners j of its 32
+// positions in order: each step reads one staged key row (the same address
+// for every lane: a broadcast) and every lane tests its own pair (x, y_j) on
+// the bands before its b.  Where they are short it numbers the pairs and
+// gives each lane one (emit_flat).  Pairs of position i are counted, or
 // written, in partner order, the order emit_kernel uses.
 template <bool WRITE, int KW4>
-__global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(BandArgs A, const unsigned long long *keys,
-                                                               const uint32_t *vals, long long n,
-                                                               unsigned long long *counts, uint32_t *pairs,
-                                                               long long cap, int win_cap) {
-    extern __shared__ uint4 s_ck[];                       // [win_cap][cws]
+__global__ void __launch_bounds__(256, KW4 <= 4 ? 2 : 1) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
+                                                             const uint32_t *vals, long long n,
+                                                             unsigned long long *counts, uint32_t *pairs,
+                                                             long long cap, int win_cap,
+                                                             unsigned long long *next_chunk) {
+    extern __shared__ uint4 s_all[];
     const int cw4 = A.ck_words >> 2, cws = stage_stride(A.ck_words);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *w_rows = s_ck + (size_t)win_cap * cws + (size_t)warp * 32 * KW4;   // per warp [32][KW4]
-    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_ck + (size_t)win_cap * cws + 8 * 32 * KW4);
+    // the warp's region: [win_cap][cws] key rows, [32][KW4] partner rows,
+    // keys [win_cap], object ids [win_cap], ids or counts [32]
+    const size_t region = emit_warp_region(A.ck_words, win_cap);
+    uint4 *s_ck = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(s_all) + warp * region);
+    uint4 *w_rows = s_ck + (size_t)win_cap * cws;
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(w_rows + 32 * KW4);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + win_cap);
-    uint32_t *w_ids = s_val + win_cap + warp * 32;                            // per warp [32]
-    // SWAR zero-lane test constants for lanes of 1, 2 or 4 bytes
+    uint32_t *w_ids = s_val + win_cap;
     const uint32_t one = A.ck_lane == 1 ? 0x01010101u : (A.ck_lane == 2 ? 0x00010001u : 1u);
     const uint32_t high = one << (8 * A.ck_lane - 1);
     const int per_word = 4 / A.ck_lane;
-    for (long long p0 = (long long)blockIdx.x * kEmitTile; p0 < n; p0 += (long long)gridDim.x * kEmitTile) {
+    const long long chunks = (n + 31) >> 5;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(next_chunk, 1ull);
+        c = __shfl_sync(kFull, c, 0);
+        if ((long long)c >= chunks) break;
+        const long long p0 = (long long)c << 5;
         const int win = (int)(n - p0 < win_cap ? n - p0 : win_cap);
-        __syncthreads();                                  // the previous tile is done with the stage
-        for (int k = threadIdx.x; k < win; k += blockDim.x) {
+        __syncwarp();                                     // the previous chunk is done with the stage
+        for (int k = lane; k < win; k += 32) {
             const uint32_t v = vals[p0 + k];
             s_key[k] = keys[p0 + k];
             s_val[k] = v;
             const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
-            for (int c = 0; c < cw4; ++c) s_ck[(size_t)k * cws + c] = __ldg(src + c);
+            for (int q = 0; q < cw4; ++q) s_ck[(size_t)k * cws + q] = __ldg(src + q);
         }
-        __syncthreads();
-        const int tile = win < kEmitTile ? win : kEmitTile;
-        const int i = warp * 32 + lane;
-        if (warp * 32 >= tile) continue;                  // no position of this warp (uniform)
+        __syncwarp();
+        const int tile = win < 32 ? win : 32;
+        const int i = lane;
         const bool live = i < tile;
         unsigned long long key = 0;
         uint32_t x = 0;
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
         const int eqw = A.exact_classes ? b : -1;
         const int need = A.exact_classes ? b + 1 : full + (rest ? 1 : 0);
         const int nw4 = (__reduce_max_sync(kFull, (unsigned)(live ? need : 0)) + 3) >> 2;
-        const unsigned jmin = (unsigned)(warp * 32 + 1);
+        const unsigned jmin = 1u;
         const unsigned jmax = __reduce_max_sync(kFull, live ? (unsigned)(end - p0) : 0u);
         const unsigned long long out = WRITE && live ? counts[p0 + i] : 0;
         unsigned long long cnt = 0;
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 3 : 2) emit_cos_tile_kernel(Ba
         // below would spend a step per partner position on mostly idle lanes)
         const unsigned pairs_w = __reduce_add_sync(kFull, live ? (unsigned)(end - p0 - i - 1) : 0u);
         if (jmax <= (unsigned)win && 5ull * ((pairs_w + 31) / 32) < 2ull * (jmax - jmin)) {
-#define BLSH_FLAT(NW) emit_flat<NW, WRITE>(A, s_ck, s_val, s_key, w_ids, cws, warp, live, i, end, p0, out, one, high, \
+#define BLSH_FLAT(NW) emit_flat<NW, WRITE>(A, s_ck, s_val, s_key, w_ids, cws, 0, live, i, end, p0, out, one, high, \
                                            per_word, pairs, cap)
             if constexpr (KW4 <= 4) {
                 switch (nw4) {
@@ -845,34 +857,35 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
         BLSH_LAUNCHED(ctx, "class_id_kernel");
     }
     const bool staged = (kind == BLSH_COSINE || A.exact_classes) && A.ck_words <= kStageWords;
-    const size_t smem = staged ? emit_cos_smem(A.ck_words) : 0;
-    const int win_cap = staged ? emit_cos_win(A.ck_words) : 0;
-    const long long etiles = (n + kEmitTile - 1) / kEmitTile;
-    const long long ecap = (long long)ctx->sm_count * (A.ck_words <= 16 ? 3 : 2);
-    const unsigned egrid = (unsigned)(etiles < ecap ? etiles : ecap);
+    const int win_cap = staged ? emit_warp_win(A.ck_words) : 0;
+    const size_t smem = staged ? 8 * emit_warp_region(A.ck_words, win_cap) : 0;
+    const unsigned egrid = (unsigned)ctx->sm_count * (A.ck_words <= 16 ? 2 : 1);
+    // the two chunk counters (count pass, write pass)
+    unsigned long long *next_chunk = &ctx->scratch->band_work[0];
+    BLSH_CUDA(ctx, cudaMemsetAsync(next_chunk, 0, 2 * sizeof(unsigned long long), s));
     if (staged) {
         if (A.ck_words <= 16) {
-            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<false, 4>,
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 4>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 4>,
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<true, 4>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             blsh_time_start(ctx, s);
-            emit_cos_tile_kernel<false, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                    win_cap);
+            emit_warp_kernel<false, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                win_cap, next_chunk);
         } else {
-            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<false, 8>,
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 8>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_cos_tile_kernel<true, 8>,
+            BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<true, 8>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             blsh_time_start(ctx, s);
-            emit_cos_tile_kernel<false, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                    win_cap);
+            emit_warp_kernel<false, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                win_cap, next_chunk);
         }
     } else {
         blsh_time_start(ctx, s);
         emit_kernel<false><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     }
-    BLSH_LAUNCHED(ctx, staged ? "emit_cos_tile_kernel (count pass)" : "emit_kernel (count pass)");
+    BLSH_LAUNCHED(ctx, staged ? "emit_warp_kernel (count pass)" : "emit_kernel (count pass)");
     blsh_time_start(ctx, s);
     BLSH_CUDA(ctx, blsh_scan::exclusive_scan<unsigned long long>(counts, counts, n,
                                                                  (unsigned long long *)(ws + L.partial),
@@ -881,14 +894,14 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     blsh_time_stop(ctx, "exclusive scan (3 launches)");
     blsh_time_start(ctx, s);
     if (staged && A.ck_words <= 16)
-        emit_cos_tile_kernel<true, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                               win_cap);
+        emit_warp_kernel<true, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                           win_cap, next_chunk + 1);
     else if (staged)
-        emit_cos_tile_kernel<true, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                               win_cap);
+        emit_warp_kernel<true, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                           win_cap, next_chunk + 1);
     else
         emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
-    BLSH_LAUNCHED(ctx, staged ? "emit_cos_tile_kernel (write pass)" : "emit_kernel (write pass)");
+    BLSH_LAUNCHED(ctx, staged ? "emit_warp_kernel (write pass)" : "emit_kernel (write pass)");
     blsh_time_start(ctx, s);
     check_cap_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs, cap, ctx->scratch);
     BLSH_LAUNCHED(ctx, "check_cap_kernel");

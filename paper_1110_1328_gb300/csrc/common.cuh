@@ -28,6 +28,7 @@ struct blsh_dev_scratch {
     unsigned long long work2;          // lite: next survivor tile handed out
     unsigned long long work3;          // lite: survivors queued
     unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
+    unsigned long long band_work[2];   // banding: next chunk of positions (count pass, write pass)
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
 };
 
