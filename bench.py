@@ -321,12 +321,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
-# the kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum of the
-# bench step under --profile-step); reported as the roofline's traffic for
-# the workload it was taken on, and to be taken again whenever the kernel
-# changes.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of a kernel's launches in one step, from one ncu
+# capture of the kernel as it stands (dram__bytes_read.sum +
+# dram__bytes_write.sum of the bench step under --profile-step); reported as
+# the roofline's traffic for the workload it was taken on (per step, like the
+# algorithmic bytes), and to be taken again whenever the kernel changes.
+NCU_TRAFFIC = {("cosine-small", "srp_sparse4_kernel"): 436.4e6 + 4.1e6}
 
 
 def load_tensor_peak():

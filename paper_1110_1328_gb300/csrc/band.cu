@@ -582,11 +582,27 @@ __global__ void __launch_bounds__(256, KW4 <= 4 ? 2 : 1) emit_warp_kernel(BandAr
         c = __shfl_sync(kFull, c, 0);
         if ((long long)c >= chunks) break;
         const long long p0 = (long long)c << 5;
-        const int win = (int)(n - p0 < win_cap ? n - p0 : win_cap);
+        int win = (int)(n - p0 < win_cap ? n - p0 : win_cap);
         __syncwarp();                                     // the previous chunk is done with the stage
+        // keys first; ids and key rows only as far as the chunk's buckets
+        // reach inside the window (all of it if one runs past it)
+        for (int k = lane; k < win; k += 32) s_key[k] = keys[p0 + k];
+        __syncwarp();
+        {
+            int lo = lane + 1, hi = win;
+            if (lane < win) {
+                const unsigned long long kl = s_key[lane];
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_key[mid] == kl) lo = mid + 1; else hi = mid;
+                }
+            } else {
+                lo = 0;
+            }
+            win = (int)__reduce_max_sync(kFull, (unsigned)lo);
+        }
         for (int k = lane; k < win; k += 32) {
             const uint32_t v = vals[p0 + k];
-            s_key[k] = keys[p0 + k];
             s_val[k] = v;
             const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
             for (int q = 0; q < cw4; ++q) s_ck[(size_t)k * cws + q] = __ldg(src + q);

@@ -230,10 +230,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                         // the estimate is an output only for pairs that are kept
                         if (A.est_out && st1 != BLSH_PRUNED)
                             A.est_out[q] = __ldg(A.est_tab + (size_t)j1 * A.est_stride + m1);
-                        // one shared-memory add per stop level among the lanes here
-                        const unsigned here = __activemask();
-                        const unsigned same = __match_any_sync(here, j1);
-                        if ((same & ((1u << lane) - 1u)) == 0) atomicAdd(&s_hist[j1], (unsigned)__popc(same));
+                        atomicAdd(&s_hist[j1], 1u);
                     }
                 }
                 if (stl >= 0 && g == 0) {
