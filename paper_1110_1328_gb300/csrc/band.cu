@@ -366,8 +366,8 @@ __host__ __device__ inline size_t emit_warp_region(int ck_words, int win) {
     const size_t b = (size_t)win * (stage_stride(ck_words) * 16 + 8 + 4) + 32 * 16 * kw4 + 32 * 4;
     return (b + 15) & ~(size_t)15;
 }
-// (rows up to 64 bytes: two CTAs of eight warps per SM; longer rows: one)
-inline size_t emit_warp_budget(int ck_words) { return ck_words <= 16 ? 13 * 1024 : 26 * 1024; }
+// (two CTAs of eight warps per SM)
+inline size_t emit_warp_budget(int ck_words) { return ck_words <= 16 ? 13 * 1024 : 14 * 1024; }
 int emit_warp_win(int ck_words) {
     int w = 32;
     while (w < kEmitWinMax && emit_warp_region(ck_words, w + 32) <= emit_warp_budget(ck_words)) w += 32;
@@ -556,7 +556,7 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
 // gives each lane one (emit_flat).  Pairs of position i are counted, or
 // written, in partner order, the order emit_kernel uses.
 template <bool WRITE, int KW4>
-__global__ void __launch_bounds__(256, KW4 <= 4 ? 2 : 1) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
+__global__ void __launch_bounds__(256, 2) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
                                                              const uint32_t *vals, long long n,
                                                              unsigned long long *counts, uint32_t *pairs,
                                                              long long cap, int win_cap,
@@ -875,7 +875,7 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     const bool staged = (kind == BLSH_COSINE || A.exact_classes) && A.ck_words <= kStageWords;
     const int win_cap = staged ? emit_warp_win(A.ck_words) : 0;
     const size_t smem = staged ? 8 * emit_warp_region(A.ck_words, win_cap) : 0;
-    const unsigned egrid = (unsigned)ctx->sm_count * (A.ck_words <= 16 ? 2 : 1);
+    const unsigned egrid = (unsigned)ctx->sm_count * 2;
     // the two chunk counters (count pass, write pass)
     unsigned long long *next_chunk = &ctx->scratch->band_work[0];
     BLSH_CUDA(ctx, cudaMemsetAsync(next_chunk, 0, 2 * sizeof(unsigned long long), s));
