@@ -293,7 +293,14 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
  * P_dev: NULL, or a device int64 holding the pair count; the kernel then
  * reads the count there (clamped to P, which acts as the capacity), so the
  * call can follow a producer on the same stream without a host sync.
- * Uses the plan blsh_autotune stored for these tables, else a default. */
+ * Uses the plan blsh_autotune stored for these tables, else a default.
+ * Cosine signature sets larger than 64 MB (N * sig_words * 4 bytes): the
+ * call first copies words 0 and 1 of every row into a context-owned plane of
+ * N uint2 that stays in L2, and every pair's first step reads them there.
+ * The plane is allocated (cudaMalloc, after synchronizing the stream) by the
+ * first such call with a larger N than before that is not being captured
+ * into a graph; a captured call whose N exceeds it reads the rows instead.
+ * This holds for every verification entry point below. */
 BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
                 const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used,
                 uint16_t *m, float *est, uint64_t *stop_hist, void *stream);
