@@ -66,6 +66,8 @@ def lib():
         L.orc_quantize_gaussian.argtypes = [p, i64, p]; L.orc_quantize_gaussian.restype = i64
         L.orc_dequantize_gaussian.argtypes = [C.c_uint16]; L.orc_dequantize_gaussian.restype = d
         L.orc_srp_sparse_q16.argtypes = [p, p, p, i64, p, i, p]; L.orc_srp_sparse_q16.restype = None
+        L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]; L.orc_splitmix64_at.restype = C.c_uint64
+        L.orc_gaussian_codes.argtypes = [C.c_uint64, i64, i, p]; L.orc_gaussian_codes.restype = None
         _lib = L
     return _lib
 
@@ -250,6 +252,22 @@ def dequantize_gaussian(q: np.ndarray) -> np.ndarray:
     """q * 16 / 2^16 - 8 (Section 4.3)."""
     f = lib().orc_dequantize_gaussian
     return np.array([f(int(v)) for v in np.asarray(q).ravel()], np.float64).reshape(np.shape(q))
+
+
+def splitmix64_at(seed: int, k: int) -> int:
+    """Output k of the SplitMix64 stream started at `seed` (Steele, Lea and
+    Flood 2014)."""
+    return int(lib().orc_splitmix64_at(seed & (2 ** 64 - 1), k))
+
+
+def gaussian_codes(seed: int, dim: int, bits: int) -> np.ndarray:
+    """Two-byte codes (Section 4.3) of an R [dim][bits] generated from a
+    counter: entry c from SplitMix64 outputs 3c..3c+2 of `seed`, twelve
+    16-bit integers summed (Irwin-Hall), x = (S - 393210) / 65536, code
+    floor((x + 8) 2^16 / 16)."""
+    codes = np.zeros((dim, bits), np.uint16)
+    lib().orc_gaussian_codes(seed & (2 ** 64 - 1), dim, bits, _ptr(codes))
+    return codes
 
 
 def srp_sparse_q16(csr, Rq: np.ndarray) -> np.ndarray:

@@ -21,7 +21,10 @@
  *     (BayesLSH-Lite);
  *   - minhash (Section 4.1 "LSH family", with h(x) = (a x + b) mod (2^31-1)),
  *     sign random projections (Section 4.2 "LSH family"), LSH banding
- *     (Section 2, "Candidate generation via LSH").
+ *     (Section 2, "Candidate generation via LSH");
+ *   - the two-byte storage of Gaussian samples (Section 4.3), and codes
+ *     generated from a counter (SplitMix64, implemented here and in the
+ *     library each from its published definition).
  *
  * Readings of points the paper leaves open or states inconsistently:
  *   - a chunk compares exactly k hashes, n .. n+k-1 (Algorithms 1-2 print a
@@ -439,6 +442,43 @@ int64_t orc_quantize_gaussian(const float *x, int64_t n, uint16_t *q)
 double orc_dequantize_gaussian(uint16_t q)
 {
     return (double)q * 16.0 / 65536.0 - 8.0;
+}
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014), as a counter-based generator: output k (k = 0,
+ * 1, ...) of the stream started at `seed` is the finaliser applied to
+ * seed + (k + 1) * 0x9E3779B97F4A7C15 (mod 2^64). */
+uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Two-byte codes (Section 4.3) of the projection matrix R [dim][bits],
+ * generated from a counter instead of stored: entry c = t * bits + j takes
+ * SplitMix64 outputs 3c, 3c + 1, 3c + 2 of the stream `seed`, splits them
+ * into twelve 16-bit integers u_1..u_12 and sums them (Irwin-Hall: S has
+ * mean 12 * 32767.5 = 393210 and standard deviation sqrt(65536^2 - 1), so
+ * (S - 393210) / 65536 is a standard normal to within the Irwin-Hall
+ * approximation, truncated at +-6).  The code is the Section 4.3 encoding
+ * floor((x + 8) 2^16 / 16) of x = (S - 393210) / 65536, i.e.
+ * floor((S - 393210) / 16) + 32768, always inside [8192, 57343]. */
+void orc_gaussian_codes(uint64_t seed, int64_t dim, int bits, uint16_t *codes)
+{
+    for (int64_t t = 0; t < dim; t++)
+        for (int j = 0; j < bits; j++) {
+            uint64_t c = (uint64_t)t * (uint64_t)bits + (uint64_t)j;
+            int64_t S = 0;
+            for (int w = 0; w < 3; w++) {
+                uint64_t o = orc_splitmix64_at(seed, 3u * c + (uint64_t)w);
+                for (int h = 0; h < 4; h++) S += (int64_t)((o >> (16 * h)) & 0xFFFFu);
+            }
+            int64_t num = S - 393210;                 /* floor division by 16 */
+            int64_t fl = num >= 0 ? num / 16 : -((-num + 15) / 16);
+            codes[(size_t)t * bits + j] = (uint16_t)(fl + 32768);
+        }
 }
 
 /* Sign random projections of sparse rows with R stored in two bytes per

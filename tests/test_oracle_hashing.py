@@ -182,3 +182,49 @@ def test_srp_q16_matches_float_path_on_grid_values():
     R = (Rq.astype(np.float64) / 4096.0 - 8.0).astype(np.float32)
     assert np.array_equal(R.astype(np.float64), Rq.astype(np.float64) / 4096.0 - 8.0)   # exact in float32
     assert np.array_equal(O.srp_sparse_q16(vecs, Rq), O.srp_sparse(vecs, R))
+
+
+# ---- counter-generated two-byte Gaussian codes (Section 4.3 storage) ----
+
+def test_splitmix64_published_outputs():
+    """The first outputs of SplitMix64 from seed 0, as published with the
+    generator's reference code."""
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    assert [O.splitmix64_at(0, k) for k in range(4)] == want
+
+
+def test_gaussian_code_of_the_first_entry_by_hand():
+    """Entry (0, 0) of seed 0 uses the first three published outputs: the sum
+    of their twelve 16-bit pieces, centred and floored onto the 1/4096 grid
+    of the two-byte encoding."""
+    outs = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    S = sum((o >> (16 * h)) & 0xFFFF for o in outs for h in range(4))
+    assert S == 397544
+    code = (S - 393210) // 16 + 32768          # floor((x + 8) 2^16 / 16), x = (S - 393210) / 2^16
+    assert code == 33038
+    assert O.gaussian_codes(0, 1, 32)[0, 0] == code
+
+
+def test_gaussian_codes_are_standard_normal_to_irwin_hall_accuracy():
+    """Decoded values of a million codes: mean (the floor onto the grid
+    shifts it by 7.5/16 of a step), variance 1, excess kurtosis -0.1 (the
+    Irwin-Hall sum of twelve uniforms), no correlation between neighbours,
+    everything inside +-6."""
+    q = O.gaussian_codes(12345, 500, 2048)
+    x = q.astype(np.float64) / 4096.0 - 8.0
+    n = x.size
+    assert abs(x.mean() - (-7.5 / 16 / 4096)) < 5.0 / np.sqrt(n)
+    var = x.var()
+    assert abs(var - 1.0) < 0.01
+    kurt = ((x - x.mean()) ** 4).mean() / var ** 2 - 3.0
+    assert abs(kurt - (-0.1)) < 0.03
+    flat = x.ravel()
+    assert abs(np.corrcoef(flat[:-1], flat[1:])[0, 1]) < 0.005
+    assert q.min() >= 8192 and q.max() <= 57343
+
+
+def test_gaussian_codes_depend_on_seed_and_position_only():
+    a = O.gaussian_codes(7, 40, 128)
+    assert np.array_equal(a, O.gaussian_codes(7, 40, 128))
+    assert np.array_equal(a[:10, :64], O.gaussian_codes(7, 10, 128)[:, :64])
+    assert (a != O.gaussian_codes(8, 40, 128)).mean() > 0.99
