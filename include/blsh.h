@@ -227,6 +227,21 @@ BLSH_API int blsh_srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const ui
  * q: n uint16 (device, caller-owned).  Asynchronous on `stream`. */
 BLSH_API int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, uint16_t *q, void *stream);
 
+/* The two-byte codes of a Gaussian R [dim][bits] generated from a counter,
+ * so that an R too large to store or to copy (a 2^24-term vocabulary at
+ * 2,048 bits is 68.7 GB of codes) is made on the device: entry
+ * c = t * bits + j sums the twelve 16-bit pieces of SplitMix64 outputs 3c,
+ * 3c + 1 and 3c + 2 of the stream `seed` (output k = the SplitMix64
+ * finaliser of seed + (k + 1) * 0x9E3779B97F4A7C15; Steele, Lea and Flood,
+ * OOPSLA 2014), S, whose (S - 393210) / 65536 is a standard normal to the
+ * accuracy of the Irwin-Hall sum of twelve uniforms (truncated at +-6); the
+ * code is that value's Section 4.3 encoding, floor((S - 393210) / 16) +
+ * 32768, in [8192, 57343].  codes: device uint16 [dim][bits], 16-byte
+ * aligned; bits a positive multiple of 8.  The codes feed
+ * blsh_srp_sparse_q16. */
+BLSH_API int blsh_gaussian_codes(blsh_ctx *ctx, uint64_t seed, int64_t dim, int32_t bits, uint16_t *codes,
+                                 void *stream);
+
 /* blsh_srp_sparse with R stored as two-byte codes Rq [dim][bits] (uint16,
  * row-major, from blsh_quantize_gaussian): bit j of row i = [ sum_e
  * values[e] * (Rq[indices[e]][j] * 2^-12 - 8) >= 0 ], each bit equal to the

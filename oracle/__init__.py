@@ -67,7 +67,7 @@ def lib():
         L.orc_dequantize_gaussian.argtypes = [C.c_uint16]; L.orc_dequantize_gaussian.restype = d
         L.orc_srp_sparse_q16.argtypes = [p, p, p, i64, p, i, p]; L.orc_srp_sparse_q16.restype = None
         L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]; L.orc_splitmix64_at.restype = C.c_uint64
-        L.orc_gaussian_codes.argtypes = [C.c_uint64, i64, i, p]; L.orc_gaussian_codes.restype = None
+        L.orc_gaussian_codes.argtypes = [C.c_uint64, i64, i64, i, p]; L.orc_gaussian_codes.restype = None
         _lib = L
     return _lib
 
@@ -260,13 +260,13 @@ def splitmix64_at(seed: int, k: int) -> int:
     return int(lib().orc_splitmix64_at(seed & (2 ** 64 - 1), k))
 
 
-def gaussian_codes(seed: int, dim: int, bits: int) -> np.ndarray:
-    """Two-byte codes (Section 4.3) of an R [dim][bits] generated from a
-    counter: entry c from SplitMix64 outputs 3c..3c+2 of `seed`, twelve
-    16-bit integers summed (Irwin-Hall), x = (S - 393210) / 65536, code
-    floor((x + 8) 2^16 / 16)."""
+def gaussian_codes(seed: int, dim: int, bits: int, row0: int = 0) -> np.ndarray:
+    """Two-byte codes (Section 4.3) of rows row0 .. row0+dim-1 of an R
+    [.][bits] generated from a counter: entry c = t bits + j from SplitMix64
+    outputs 3c..3c+2 of `seed`, twelve 16-bit integers summed (Irwin-Hall),
+    x = (S - 393210) / 65536, code floor((x + 8) 2^16 / 16)."""
     codes = np.zeros((dim, bits), np.uint16)
-    lib().orc_gaussian_codes(seed & (2 ** 64 - 1), dim, bits, _ptr(codes))
+    lib().orc_gaussian_codes(seed & (2 ** 64 - 1), row0, dim, bits, _ptr(codes))
     return codes
 
 

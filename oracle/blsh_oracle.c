@@ -464,12 +464,13 @@ uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k)
  * (S - 393210) / 65536 is a standard normal to within the Irwin-Hall
  * approximation, truncated at +-6).  The code is the Section 4.3 encoding
  * floor((x + 8) 2^16 / 16) of x = (S - 393210) / 65536, i.e.
- * floor((S - 393210) / 16) + 32768, always inside [8192, 57343]. */
-void orc_gaussian_codes(uint64_t seed, int64_t dim, int bits, uint16_t *codes)
+ * floor((S - 393210) / 16) + 32768, always inside [8192, 57343].  Rows
+ * row0 .. row0 + rows - 1 are written to codes [rows][bits]. */
+void orc_gaussian_codes(uint64_t seed, int64_t row0, int64_t rows, int bits, uint16_t *codes)
 {
-    for (int64_t t = 0; t < dim; t++)
+    for (int64_t r = 0; r < rows; r++)
         for (int j = 0; j < bits; j++) {
-            uint64_t c = (uint64_t)t * (uint64_t)bits + (uint64_t)j;
+            uint64_t c = (uint64_t)(row0 + r) * (uint64_t)bits + (uint64_t)j;
             int64_t S = 0;
             for (int w = 0; w < 3; w++) {
                 uint64_t o = orc_splitmix64_at(seed, 3u * c + (uint64_t)w);
@@ -477,7 +478,7 @@ void orc_gaussian_codes(uint64_t seed, int64_t dim, int bits, uint16_t *codes)
             }
             int64_t num = S - 393210;                 /* floor division by 16 */
             int64_t fl = num >= 0 ? num / 16 : -((-num + 15) / 16);
-            codes[(size_t)t * bits + j] = (uint16_t)(fl + 32768);
+            codes[(size_t)r * bits + j] = (uint16_t)(fl + 32768);
         }
 }
 

@@ -74,6 +74,7 @@ def lib():
             "blsh_srp_sparse_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
             "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
             "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
+            "blsh_gaussian_codes": ([p, C.c_uint64, i64, i32, p, p], C.c_int),
             "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
             "blsh_srp_dense_workspace": ([i64, i32, i32, p], C.c_int),
             "blsh_lsh_candidates_workspace": ([i64, i32, i32, i32, p], C.c_int),
@@ -301,6 +302,16 @@ def blsh_quantize_gaussian(ctx: Context, x, q=None, stream=None):
     rc = lib().blsh_quantize_gaussian(ctx.handle, _dev(x, torch.float32), x.numel(), _dev(q), _stream(stream))
     _check(rc, ctx)
     return q
+
+
+def blsh_gaussian_codes(ctx: Context, seed: int, dim: int, bits: int, stream=None):
+    """Two-byte Gaussian codes R [dim][bits] generated on the device from a
+    counter (SplitMix64 + Irwin-Hall); returns an int16 tensor holding the
+    uint16 codes."""
+    codes = torch.empty((dim, bits), dtype=torch.int16, device=torch.device("cuda", ctx.device))
+    _check(lib().blsh_gaussian_codes(ctx.handle, int(seed) & (2 ** 64 - 1), int(dim), int(bits), _dev(codes),
+                                     _stream(stream)), ctx)
+    return codes
 
 
 def blsh_srp_sparse_q16(ctx: Context, indptr, indices, values, Rq, sig, stream=None):

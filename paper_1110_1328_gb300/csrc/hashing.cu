@@ -569,6 +569,43 @@ __global__ void __launch_bounds__(256) quantize_gaussian_kernel(const float *__r
     if (outside) blsh_dev_error(scratch, BLSH_ENUMERIC, -1, outside);
 }
 
+// SplitMix64 (Steele, Lea and Flood 2014) read as a counter-based
+// generator: output k of the stream `seed` is the finaliser of
+// seed + (k + 1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long k) {
+    unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Eight codes per thread (one 16-byte store): entry c = t * bits + j sums
+// the twelve 16-bit pieces of outputs 3c .. 3c+2 (Irwin-Hall, mean 393210,
+// standard deviation 65536 to 1e-10) and encodes x = (S - 393210) / 2^16 as
+// floor((x + 8) 2^16 / 16) = floor((S - 393210) / 16) + 32768.
+__global__ void __launch_bounds__(256) gaussian_codes_kernel(unsigned long long seed, long long groups,
+                                                             uint16_t *__restrict__ codes) {
+    for (long long gidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; gidx < groups;
+         gidx += (long long)gridDim.x * blockDim.x) {
+        uint32_t packed[4];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const unsigned long long c = (unsigned long long)gidx * 8ull + (unsigned long long)e;
+            int S = 0;
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                const unsigned long long o = splitmix64_at(seed, 3ull * c + (unsigned long long)w);
+                S += (int)(o & 0xFFFFull) + (int)((o >> 16) & 0xFFFFull) + (int)((o >> 32) & 0xFFFFull) +
+                     (int)(o >> 48);
+            }
+            const int code = ((S - 393210) >> 4) + 32768;   // arithmetic shift: floor division by 16
+            if (e & 1) packed[e >> 1] |= (uint32_t)code << 16;
+            else packed[e >> 1] = (uint32_t)code;
+        }
+        reinterpret_cast<uint4 *>(codes)[gidx] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+}
+
 // Dense rows X [N][d] against R [d][bits], the same FP32 sums with the same
 // error bound and FP64 recheck (coordinates in order 0..d-1).  One CTA per
 // row; the row is staged in shared memory.
@@ -775,6 +812,25 @@ extern "C" int blsh_quantize_gaussian(blsh_ctx *ctx, const float *x, int64_t n, 
     blsh_time_start(ctx, s);
     quantize_gaussian_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, n, q, ctx->scratch);
     BLSH_LAUNCHED(ctx, "quantize_gaussian_kernel");
+    return BLSH_OK;
+}
+
+extern "C" int blsh_gaussian_codes(blsh_ctx *ctx, uint64_t seed, int64_t dim, int32_t bits, uint16_t *codes,
+                                   void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (dim < 0 || bits <= 0 || bits % 8 || (dim > 0 && !codes))
+        return blsh_fail(ctx, BLSH_EINVAL, "bits must be a positive multiple of 8; codes are required");
+    if (!blsh_aligned(codes, 16)) return blsh_fail(ctx, BLSH_EINVAL, "codes must be 16-byte aligned");
+    if (dim == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    cudaStream_t s = blsh_stream(stream);
+    const long long groups = dim * (long long)(bits / 8);
+    const long long blocks = (groups + 255) / 256;
+    const long long cap = (long long)ctx->sm_count * 32;
+    blsh_time_start(ctx, s);
+    gaussian_codes_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>((unsigned long long)seed, groups,
+                                                                                  codes);
+    BLSH_LAUNCHED(ctx, "gaussian_codes_kernel");
     return BLSH_OK;
 }
 

@@ -94,3 +94,37 @@ def test_srp_q16_matches_float_path_on_grid_values(B, ctx):
     B.blsh_srp_sparse(ctx, ip, ix, val, torch.from_numpy(R).to(dev), s2)
     assert B.blsh_status(ctx) == 0
     assert torch.equal(s1, s2)
+
+
+@pytest.mark.parametrize("seed,dim,bits", [(0, 1, 8), (1, 777, 2048), (2 ** 63 + 5, 3, 1032)])
+def test_gaussian_codes_bit_exact(B, ctx, seed, dim, bits):
+    """Codes generated on the device from the counter equal the oracle's."""
+    got = B.blsh_gaussian_codes(ctx, seed, dim, bits)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(got.cpu().numpy().view(np.uint16), O.gaussian_codes(seed, dim, bits))
+
+
+def test_gaussian_codes_large_sampled(B, ctx):
+    """A 2^20 x 2,048 code matrix (4 GB of codes; counters past 2^32): sampled
+    rows equal the oracle's, and the decoded values have unit variance."""
+    dim, bits, seed = 1 << 20, 2048, 77
+    got = B.blsh_gaussian_codes(ctx, seed, dim, bits)
+    assert B.blsh_status(ctx) == 0
+    for r in (0, 1, 65535, 524287, dim - 1):
+        assert np.array_equal(got[r].cpu().numpy().view(np.uint16), O.gaussian_codes(seed, 1, bits, row0=r)[0])
+    x = got[::997].cpu().numpy().view(np.uint16).astype(np.float64) / 4096.0 - 8.0
+    assert abs(x.var() - 1.0) < 0.01
+    del got
+
+
+def test_srp_q16_on_generated_codes(B, ctx):
+    """The sparse projection over device-generated codes equals the oracle's
+    over its own codes for the same seed."""
+    vecs = synth.tfidf_vectors(n_docs=600, dim=30000, mean_nnz=80, n_groups=40, seed=21)
+    Rq = B.blsh_gaussian_codes(ctx, 1234, 30000, 2048)
+    want = O.srp_sparse_q16(vecs, O.gaussian_codes(1234, 30000, 2048))
+    ip, ix, val = csr_dev(vecs)
+    sig = torch.zeros((vecs.n, 64), dtype=torch.int32, device=dev)
+    B.blsh_srp_sparse_q16(ctx, ip, ix, val, Rq, sig)
+    assert B.blsh_status(ctx) == 0
+    assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)

@@ -228,3 +228,8 @@ def test_gaussian_codes_depend_on_seed_and_position_only():
     assert np.array_equal(a, O.gaussian_codes(7, 40, 128))
     assert np.array_equal(a[:10, :64], O.gaussian_codes(7, 10, 128)[:, :64])
     assert (a != O.gaussian_codes(8, 40, 128)).mean() > 0.99
+
+
+def test_gaussian_code_rows_from_any_offset():
+    whole = O.gaussian_codes(99, 30, 64)
+    assert np.array_equal(O.gaussian_codes(99, 7, 64, row0=11), whole[11:18])
