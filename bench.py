@@ -60,6 +60,14 @@ WORKLOADS = {
     "verify-large": dict(kind=1, gpu_only=True, n=5_000_000, bits=2048, pairs=200_000_000, t=0.7, n_max=2048, k=32, h=128,
                          seed=9, text="verification only: 5,000,000 random 2,048-bit signatures (1.3 GB) and "
                                       "200,000,000 uniform random candidate pairs (HBM-resident, no reuse)"),
+    "large-mixed": dict(kind=1, gpu_only=True, n=5_000_000, dim=1 << 24, bits=2048, rows=16, bands=5, t=0.6,
+                        n_max=2048, k=32, h=128, seed=9, r_seed=31,
+                        text="cosine, BayesLSH + Lite on N=5,000,000 tf-idf sparse float32 vectors over a 2^24-term "
+                             "vocabulary (Zipf(1.1) ranks, power-law lengths l^-2 on [5, 20,000], 100,000 planted "
+                             "near-duplicate groups; drawn on the GPU), 2,048 SRP bits over R as two-byte Gaussian "
+                             "codes generated on the device (68.7 GB), banding 16x5, t=0.6, eps=0.03, delta=0.05, "
+                             "gamma=0.03, k=32, h=128; candidates verified in device-resident batches sized by "
+                             "free HBM"),
     "jaccard-small": dict(kind=0, n=2000, vocab=10000, n_hashes=256, rows=8, bands=32, t=0.7, n_max=256, k=32,
                           h=64, seed=1,
                           text="jaccard, BayesLSH + Lite: N=2,000 sets over vocab 10,000, lognormal sizes "
@@ -920,6 +928,150 @@ def run_verify_large(args, w):
           flush=True)
 
 
+class LargePipeline:
+    """The 5e6-vector mixed workload: inputs drawn on the GPU, R generated on
+    the device as two-byte codes, one step = hash, band, Algorithms 1 and 2
+    over the candidates in batches sized by free HBM, compaction."""
+
+    def __init__(self, B, torch, w, device):
+        import synth
+        self.B, self.w, self.dev = B, w, device
+        self.ctx = B.Context(device.index or 0)
+        self.indptr, self.indices, self.values = synth.large_tfidf_device(n_docs=w["n"], dim=w["dim"],
+                                                                          seed=w["seed"], device=device)
+        torch.cuda.synchronize()
+        self.N, self.W = w["n"], w["bits"] // 32
+        self.Rq = B.blsh_gaussian_codes(self.ctx, w["r_seed"], w["dim"], w["bits"])
+        self.sig = torch.zeros((self.N, self.W), dtype=torch.int32, device=device)
+        self.tab = B.blsh_tables_build(self.ctx, B.make_params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"],
+                                                               h=w["h"]))
+        self.ws = torch.zeros(B.blsh_lsh_candidates_workspace(self.N, 1, w["rows"], w["bands"]), dtype=torch.uint8,
+                              device=device)
+        self.n_pairs = torch.zeros(1, dtype=torch.int64, device=device)
+        self.hash()
+        B.blsh_lsh_candidates(self.ctx, self.sig, 1, w["rows"], w["bands"], None, self.n_pairs, self.ws)
+        B.blsh_status(self.ctx)
+        self.P = int(self.n_pairs.item())
+        if self.P > 4_000_000_000:
+            raise RuntimeError(f"{self.P} candidates: more than this workload's pair buffer is sized for")
+        self.pairs = torch.zeros((self.P + 1024, 2), dtype=torch.int32, device=device)
+        # per pair of a batch: status, n_used, m, est, Lite status, sim (18 B) and two compaction indices
+        free, _ = torch.cuda.mem_get_info(device)
+        per_pair = 1 + 2 + 2 + 4 + 1 + 8
+        self.batch = int(max(1 << 20, min(self.P, (free - (4 << 30)) // (2 * per_pair + 16))))
+        bsz = min(self.batch, self.P)
+        self.status = torch.zeros(bsz, dtype=torch.uint8, device=device)
+        self.n_used = torch.zeros(bsz, dtype=torch.int16, device=device)
+        self.m = torch.zeros(bsz, dtype=torch.int16, device=device)
+        self.est = torch.zeros(bsz, dtype=torch.float32, device=device)
+        self.lstatus = torch.zeros(bsz, dtype=torch.uint8, device=device)
+        self.sim = torch.zeros(bsz, dtype=torch.float64, device=device)
+        self.hist = torch.zeros(self.tab.levels, dtype=torch.int64, device=device)
+        self.hist_total = torch.zeros(self.tab.levels, dtype=torch.int64, device=device)
+        self.out1 = torch.zeros(bsz, dtype=torch.int64, device=device)
+        self.out2 = torch.zeros(bsz, dtype=torch.int64, device=device)
+        self.n_out = torch.zeros(2, dtype=torch.int64, device=device)
+        self.kept = torch.zeros(2, dtype=torch.int64, device=device)
+
+    def hash(self):
+        self.B.blsh_srp_sparse_q16(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig)
+
+    def band(self):
+        w = self.w
+        self.B.blsh_lsh_candidates(self.ctx, self.sig, 1, w["rows"], w["bands"], self.pairs, self.n_pairs, self.ws)
+
+    def verify(self):
+        """Algorithms 1 and 2 and the compaction of each batch of pairs (the
+        kept pairs' indices of a batch are counted into `kept`)."""
+        B = self.B
+        self.hist_total.zero_()
+        self.kept.zero_()
+        for b0 in range(0, self.P, self.batch):
+            n = min(self.batch, self.P - b0)
+            B.blsh_verify_both(self.ctx, self.tab, self.pairs[b0:b0 + n], self.sig, self.status[:n],
+                               self.n_used[:n], self.m[:n], self.est[:n], self.hist, self.indptr, self.indices,
+                               self.values, self.lstatus[:n], self.sim[:n])
+            self.hist_total += self.hist
+            B.blsh_compact(self.ctx, self.status[:n], (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX), self.out1[:n],
+                           self.n_out[0:1])
+            B.blsh_compact(self.ctx, self.lstatus[:n], 1 << B.LITE_ACCEPT, self.out2[:n], self.n_out[1:2])
+            self.kept += self.n_out
+
+    STAGES = ("hash", "band", "verify")
+
+    def step(self):
+        for s_ in self.STAGES:
+            getattr(self, s_)()
+
+
+def run_large(args, w):
+    """The 5e6-vector mixed workload (one GPU): K timed steps of hash, band,
+    batched verification and compaction."""
+    import torch
+
+    import paper_1110_1328_gb300 as B
+    dev = torch.device("cuda", 0)
+    B.lib()
+    t0 = time.perf_counter()
+    pipe = LargePipeline(B, torch, w, dev)
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pipe.step()
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("warm-up step failed")
+    launches0 = B.blsh_launch_count(pipe.ctx)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ts = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pipe.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = B.blsh_launch_count(pipe.ctx) - launches0
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("timed steps failed")
+    ms = float(np.mean(ts))
+    # per-stage and per-kernel device times of one more eager step
+    B.blsh_timing_begin(pipe.ctx, 8192)
+    stage = {}
+    for s_ in pipe.STAGES:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        getattr(pipe, s_)()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        stage[s_] = round(e0.elapsed_time(e1), 3)
+    kern = {}
+    for name, t_ms in B.blsh_timing_end(pipe.ctx, 8192):
+        k = kern.setdefault(name, [0, 0.0])
+        k[0] += 1
+        k[1] += t_ms
+    kern = {n: {"launches": c, "ms": round(t, 3)} for n, (c, t) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    nnz = int(pipe.indptr[-1].item())
+    hist = pipe.hist_total.cpu().numpy()
+    kept = [int(x) for x in pipe.kept.cpu()]
+    print(json.dumps({"metric": METRIC, "value": round(pipe.P / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+                      "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "nnz": nnz,
+                                 "candidate_pairs": pipe.P, "batch_pairs": pipe.batch,
+                                 "batches": -(-pipe.P // pipe.batch), "setup_s": round(setup_s, 1),
+                                 "l2": "flushed between timed steps (256 MB write)", "cuda_graph": False},
+                      "gpu_launches": int(launches), "stage_ms": stage, "kernels": kern,
+                      "hashes_per_s": round(pipe.N * w["bits"] / (stage["hash"] / 1e3), 1),
+                      "outputs": {"bayeslsh_kept": kept[0], "lite_kept": kept[1],
+                                  "stop_hist_first4": [int(v) for v in hist[:4]]},
+                      "clocks": clk}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timings (the cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
@@ -1028,6 +1180,8 @@ def main():
         run_reference(args, w)
     elif args.workload == "verify-large":
         run_verify_large(args, w)
+    elif args.workload == "large-mixed":
+        run_large(args, w)
     elif args.workload == "sweep":
         run_sweep(args, w)
     else:

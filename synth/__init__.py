@@ -346,3 +346,88 @@ def bernoulli_signatures(sims: np.ndarray, n_hashes: int, kind: str, seed: int =
         sig[0::2], sig[1::2] = pack(xb), pack(yb)
     pairs = np.stack([np.arange(0, 2 * P, 2), np.arange(1, 2 * P, 2)], axis=1).astype(np.uint32)
     return sig, pairs
+
+
+def large_tfidf_device(n_docs: int = 5_000_000, dim: int = 1 << 24, zipf_s: float = 1.1,
+                       nnz_min: int = 5, nnz_max: int = 20000, nnz_exp: float = 2.0,
+                       n_groups: int = 100_000, group_size=(2, 5), frac=(0.1, 0.4), seed: int = 9,
+                       device=None):
+    """tf-idf-like sparse vectors at a scale the host cannot draw quickly
+    (5e6 documents, ~2e8 nonzeros), drawn on the GPU with torch's seeded
+    generator and returned as device tensors (indptr int64 [N+1], indices
+    int32 holding uint32 term ids, values float32).
+
+    Row lengths follow a power law p(l) ~ l^-nnz_exp on [nnz_min, nnz_max]
+    (inverse CDF of the continuous law, floored).  Term ranks follow
+    Zipf(zipf_s) over dim ranks by the inverse CDF of the continuous law
+    (rank = floor((1 + u (dim^(1-s) - 1))^(1/(1-s)))), mapped to ids by a
+    fixed random permutation; repeated draws within a row merge into one term
+    whose tf is the number of draws plus a Geometric(0.5) extra.  The first
+    rows form n_groups planted groups: a base document followed by 1..4
+    variants that redraw a fraction f ~ U[frac] of its draws.  weight =
+    log(1+tf) ln(N/df), each row scaled to unit L2 norm (in float64, rounded
+    to float32; a row whose weights are all 0 keeps them).
+    """
+    import torch
+
+    dev = torch.device("cuda", 0) if device is None else device
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    f64 = torch.float64
+
+    def lengths(k):
+        u = torch.rand(k, generator=g, device=dev, dtype=f64)
+        e = 1.0 - nnz_exp
+        lo, hi = float(nnz_min), float(nnz_max + 1)
+        x = (lo ** e + u * (hi ** e - lo ** e)) ** (1.0 / e)
+        return x.floor().clamp(nnz_min, nnz_max).to(torch.int64)
+
+    perm = torch.randperm(dim, generator=g, device=dev)
+
+    def terms(k):
+        u = torch.rand(k, generator=g, device=dev, dtype=f64)
+        e = 1.0 - zipf_s
+        r = (1.0 + u * (float(dim) ** e - 1.0)) ** (1.0 / e)
+        return perm[(r.floor().clamp(1, dim) - 1).to(torch.int64)]
+
+    # group structure: rows [0, n_grouped) are groups (base first), the rest independent
+    sizes = torch.randint(group_size[0], group_size[1] + 1, (n_groups,), generator=g, device=dev)
+    starts = torch.cumsum(sizes, 0) - sizes
+    n_grouped = int(sizes.sum().item())
+    if n_grouped > n_docs:
+        raise ValueError("planted groups exceed the document count")
+    member = torch.arange(n_grouped, device=dev)
+    group_of = torch.repeat_interleave(torch.arange(n_groups, device=dev), sizes)
+    base_row = starts[group_of]                          # row of each grouped member's base
+    is_base = member == base_row
+    # draws of every base and independent row
+    own = torch.ones(n_docs, dtype=torch.bool, device=dev)
+    own[:n_grouped] = is_base
+    lens = lengths(n_docs)
+    lens = torch.where(own, lens, lens[torch.cat([base_row, torch.arange(n_grouped, n_docs, device=dev)])])
+    row_of = torch.repeat_interleave(torch.arange(n_docs, device=dev), lens)
+    total = row_of.numel()
+    ids = terms(total)
+    # variants copy their base's draws and redraw a fraction f of them
+    first = torch.cumsum(lens, 0) - lens
+    var = ~own
+    if bool(var.any()):
+        f = torch.empty(n_docs, device=dev, dtype=f64).uniform_(frac[0], frac[1], generator=g)
+        pos = torch.arange(total, device=dev) - first[row_of]          # draw index within the row
+        src_row = torch.cat([base_row, torch.arange(n_grouped, n_docs, device=dev)])[row_of]
+        copied = ids[first[src_row] + pos]
+        keep = torch.rand(total, generator=g, device=dev, dtype=f64) >= f[row_of]
+        ids = torch.where(var[row_of] & keep, copied, ids)
+    # merge repeated terms within a row; tf = draws + Geometric(0.5)
+    key, draws = torch.unique(row_of * dim + ids, sorted=True, return_counts=True)
+    rows = key // dim
+    ids = key - rows * dim
+    u = torch.rand(key.numel(), generator=g, device=dev, dtype=f64).clamp_min(1e-300)
+    tf = draws.to(f64) + torch.floor(torch.log(u) / math.log(0.5))
+    df = torch.bincount(ids, minlength=dim)
+    w = torch.log1p(tf) * torch.log(n_docs / df[ids].clamp_min(1).to(f64))
+    nrm = torch.zeros(n_docs, dtype=f64, device=dev).index_add_(0, rows, w * w).sqrt()
+    w = torch.where(nrm[rows] > 0, w / nrm[rows].clamp_min(1e-300), w)
+    indptr = torch.zeros(n_docs + 1, dtype=torch.int64, device=dev)
+    indptr[1:] = torch.cumsum(torch.bincount(rows, minlength=n_docs), 0)
+    return indptr, ids.to(torch.int32), w.to(torch.float32)
