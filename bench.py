@@ -1036,7 +1036,8 @@ def run_large(args, w):
         ts.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     launches = B.blsh_launch_count(pipe.ctx) - launches0
-    if B.blsh_status(pipe.ctx) != 0:
+    rc, ctr = B.blsh_status(pipe.ctx, counters=True)
+    if rc != 0:
         raise RuntimeError("timed steps failed")
     ms = float(np.mean(ts))
     # per-stage and per-kernel device times of one more eager step
@@ -1067,6 +1068,7 @@ def run_large(args, w):
                                  "l2": "flushed between timed steps (256 MB write)", "cuda_graph": False},
                       "gpu_launches": int(launches), "stage_ms": stage, "kernels": kern,
                       "hashes_per_s": round(pipe.N * w["bits"] / (stage["hash"] / 1e3), 1),
+                      "srp_signs": {"rechecked_per_step": ctr[2] / args.steps, "zero_dots_per_step": ctr[3] / args.steps},
                       "outputs": {"bayeslsh_kept": kept[0], "lite_kept": kept[1],
                                   "stop_hist_first4": [int(v) for v in hist[:4]]},
                       "clocks": clk}), flush=True)

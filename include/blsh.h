@@ -254,6 +254,15 @@ BLSH_API int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uin
                                  const float *values, int64_t N, const uint16_t *Rq, int64_t dim, int32_t bits,
                                  uint32_t *sig, void *stream);
 
+/* Columns [col_begin, col_begin + col_count) of blsh_srp_sparse_q16's
+ * signatures for the rows with row_mask[row] != 0 (NULL: every row), as
+ * blsh_srp_sparse_cols does for a float R.  bits, col_begin and col_count
+ * multiples of 128; Rq 8-byte aligned.  Errors as blsh_srp_sparse_q16. */
+BLSH_API int blsh_srp_sparse_q16_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                      const float *values, int64_t N, const uint16_t *Rq, int64_t dim, int32_t bits,
+                                      int32_t col_begin, int32_t col_count, const uint8_t *row_mask, uint32_t *sig,
+                                      void *stream);
+
 /* Sign random projections of dense rows X [N][d] (float, row-major) with
  * R [d][bits] (float, row-major), Section 4.2: bit j of row i =
  * [ sum_c X[i][c] R[c][j] >= 0 ], each bit equal to the sign of the FP64 sum

@@ -73,6 +73,7 @@ def lib():
             "blsh_srp_sparse": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
             "blsh_srp_sparse_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
             "blsh_srp_sparse_q16": ([p, p, p, p, i64, p, i64, i32, p, p], C.c_int),
+            "blsh_srp_sparse_q16_cols": ([p, p, p, p, i64, p, i64, i32, i32, i32, p, p, p], C.c_int),
             "blsh_quantize_gaussian": ([p, p, i64, p, p], C.c_int),
             "blsh_gaussian_codes": ([p, C.c_uint64, i64, i32, p, p], C.c_int),
             "blsh_srp_dense": ([p, p, i64, i32, p, i32, C.c_float, p, p, sz, p], C.c_int),
@@ -322,6 +323,18 @@ def blsh_srp_sparse_q16(ctx: Context, indptr, indices, values, Rq, sig, stream=N
     val = values if values.numel() else torch.zeros(1, dtype=torch.float32, device=indptr.device)
     rc = lib().blsh_srp_sparse_q16(ctx.handle, _dev(indptr, torch.int64), _dev(idx), _dev(val, torch.float32), N,
                                    _dev(Rq), dim, bits, _dev(sig), _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_srp_sparse_q16_cols(ctx: Context, indptr, indices, values, Rq, sig, col_begin: int, col_count: int,
+                             row_mask=None, stream=None):
+    """Columns [col_begin, col_begin + col_count) of blsh_srp_sparse_q16's
+    signatures for the rows row_mask (uint8 [N], or None: all) selects."""
+    N = indptr.numel() - 1
+    dim, bits = Rq.shape
+    rc = lib().blsh_srp_sparse_q16_cols(ctx.handle, _dev(indptr, torch.int64), _dev(indices),
+                                        _dev(values, torch.float32), N, _dev(Rq), dim, bits, int(col_begin),
+                                        int(col_count), _dev(row_mask, torch.uint8), _dev(sig), _stream(stream))
     _check(rc, ctx)
 
 

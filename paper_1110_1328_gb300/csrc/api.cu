@@ -75,10 +75,18 @@ extern "C" int blsh_ctx_create(blsh_ctx **out, int device) {
         delete ctx;
         return BLSH_ENOMEM;
     }
+    if (cudaMalloc((void **)&ctx->lite_queue, sizeof(unsigned long long) * BLSH_LITE_QUEUE_CAP) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->scratch);
+        cudaFree(ctx->recheck_queue);
+        delete ctx;
+        return BLSH_ENOMEM;
+    }
     if (cudaMemset(ctx->scratch, 0, sizeof(blsh_dev_scratch)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(ctx->scratch);
         cudaFree(ctx->recheck_queue);
+        cudaFree(ctx->lite_queue);
         delete ctx;
         return BLSH_EDEVICE;
     }
@@ -96,6 +104,7 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
         if (ctx->plane) cudaFree(ctx->plane);
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
+        if (ctx->lite_queue) cudaFree(ctx->lite_queue);
     }
     delete ctx;
     return BLSH_OK;

@@ -17,6 +17,7 @@
 #define BLSH_MAX_NMAX 4096
 #define BLSH_COMPACT_MAX_CTAS 2048
 #define BLSH_RECHECK_CAP (1u << 20)   // queued SRP sign rechecks per call (8 MiB per context)
+#define BLSH_LITE_QUEUE_CAP (1u << 23) // queued Lite survivors per call (64 MiB per context)
 
 // Device-side scratch owned by a context.  Every call zeroes what it uses
 // before its kernels run (cudaMemsetAsync on the caller's stream).
@@ -39,6 +40,7 @@ struct blsh_ctx {
     size_t smem_optin = 0;
     blsh_dev_scratch *scratch = nullptr;
     uint2 *recheck_queue = nullptr;                   // [BLSH_RECHECK_CAP] (row, bit) of undecided SRP signs
+    unsigned long long *lite_queue = nullptr;         // [BLSH_LITE_QUEUE_CAP] Lite survivors (pair indices)
     void *plane = nullptr;                            // verification: [plane_cap] first two words of each row
     long long plane_cap = 0;
     char err[512] = {0};

@@ -155,7 +155,6 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 
 constexpr int kSrpMaxPerThread = 16;
 constexpr int kSrpBatch = 8;       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
-constexpr int kSrpQ16Batch = 1;    // the same for two-byte rows
 constexpr int kSrpChunk = 256;
 
 template <typename RT>
@@ -257,11 +256,11 @@ __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ ind
 // keeps no barrier in the loop; several rows of R are in flight per thread.
 // The four bits of a group form a nibble; eight lanes OR their nibbles into
 // one signature word with shuffles.
-template <int V>
+template <int V, typename RT>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
                                                           const float *__restrict__ values, long long N,
-                                                          const float *__restrict__ R, long long dim, int bits,
+                                                          const RT *__restrict__ R, long long dim, int bits,
                                                           int col_first, int pieces,
                                                           const uint8_t *__restrict__ row_mask,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
@@ -280,6 +279,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
         const int col0 = col_first + (int)(item - row * pieces) * 4 * V * T;
         if (row_mask && !row_mask[row]) continue;
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+        constexpr bool Q16 = sizeof(RT) == 2;
         float acc[4 * V], mag[4 * V];
 #pragma unroll
         for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
@@ -308,9 +308,24 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                 for (int b = 0; b < NB; ++b) {
                     const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
                     vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
-                    const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
+                    if constexpr (Q16) {
+                        // four codes per load; a code q stands for (q - 2^15) 2^-12, and
+                        // the float with bit pattern 0x4b000000 | q is 2^23 + q, so
+                        // subtracting 2^23 + 2^15 gives q - 2^15 exactly (sums scaled by 2^12)
+                        const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
 #pragma unroll
-                    for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
+                        for (int g = 0; g < V; ++g) {
+                            const uint2 q = __ldg(Rrow + g * T);
+                            r[b][g] = make_float4(__int_as_float(0x4b000000u | (q.x & 0xffffu)) - 8421376.0f,
+                                                  __int_as_float(0x4b000000u | (q.x >> 16)) - 8421376.0f,
+                                                  __int_as_float(0x4b000000u | (q.y & 0xffffu)) - 8421376.0f,
+                                                  __int_as_float(0x4b000000u | (q.y >> 16)) - 8421376.0f);
+                        }
+                    } else {
+                        const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
+#pragma unroll
+                        for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
+                    }
                 }
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                         queue[slot] = make_uint2((uint32_t)row, j);
                         bit = false;
                     } else {
-                        const double d = srp_recheck_fp64<float>(indices, values, s, e, R, dim, bits, j);
+                        const double d = srp_recheck_fp64<RT>(indices, values, s, e, R, dim, bits, j);
                         bit = d >= 0.0;
                         ++rechecked;
                         zeros += d == 0.0;
@@ -438,116 +453,6 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
 // Sign random projections with R stored in two bytes per entry (Section 4.3,
 // "Cheaper storage of hash functions").  Thread t owns the groups of 8 bits
 // t, t+T, ...: one 16-byte load brings the 8 codes of a group for a nonzero.
-// A code q stands for (q - 2^15) 2^-12.  The sums are formed over the
-// integers q - 2^15 instead (the float with bit pattern 0x4b000000 | q is
-// 2^23 + q, and subtracting 2^23 + 2^15 is exact), which scales every sum by
-// 2^12 and changes neither its sign nor the relative error bound.  Since
-// |q - 2^15| <= 2^15, sum |v (q - 2^15)| <= 2^15 sum |v|: one magnitude per
-// row stands in for the per-bit magnitudes of srp_sparse4_kernel, and the
-// bound becomes 1.25 n u 2^15 sum|v| + n 2^-149.  Undecided signs go to the
-// same queue and FP64 recheck as the float path (the decoded values are
-// exact in FP64, so the recheck reproduces the oracle's sum bit for bit).
-__device__ __forceinline__ float q16_lo(uint32_t w) { return __int_as_float(0x4b000000u | (w & 0xffffu)) - 8421376.0f; }
-__device__ __forceinline__ float q16_hi(uint32_t w) { return __int_as_float(0x4b000000u | (w >> 16)) - 8421376.0f; }
-
-template <int V, int U>
-__global__ void __launch_bounds__(256) srp_sparse_q16_kernel(const int64_t *__restrict__ indptr,
-                                                             const uint32_t *__restrict__ indices,
-                                                             const float *__restrict__ values, long long N,
-                                                             const uint16_t *__restrict__ R, long long dim, int bits,
-                                                             uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
-                                                             uint2 *__restrict__ queue) {
-    const int T = blockDim.x;
-    const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int words = bits >> 5;
-    unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    for (long long row = blockIdx.x; row < N; row += gridDim.x) {
-        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-        float acc[8 * V];
-#pragma unroll
-        for (int u = 0; u < 8 * V; ++u) acc[u] = 0.0f;
-        float asum = 0.0f;
-        // nonzeros in batches of U (U * V loads in flight)
-        for (long long k0 = s; k0 < e; k0 += U) {
-            const int cnt = (int)(e - k0 < U ? e - k0 : U);
-            uint32_t ix[U];
-            float v[U];
-            uint4 w[U][V];
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                ix[q] = 0;
-                v[q] = 0.0f;
-                if (q < cnt) {
-                    ix[q] = __ldg(indices + k0 + q);
-                    v[q] = __ldg(values + k0 + q);
-                    if (ix[q] >= dim) {   // malformed row: counted, contributes nothing
-                        bad += t == 0;
-                        ix[q] = 0;
-                        v[q] = 0.0f;
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                const uint4 *Rrow = reinterpret_cast<const uint4 *>(R + (size_t)ix[q] * bits) + t;
-#pragma unroll
-                for (int g = 0; g < V; ++g) w[q][g] = q < cnt ? __ldg(Rrow + g * T) : make_uint4(0x80008000u, 0x80008000u, 0x80008000u, 0x80008000u);
-            }
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                asum += fabsf(v[q]);
-#pragma unroll
-                for (int g = 0; g < V; ++g) {
-                    const uint32_t ws[4] = {w[q][g].x, w[q][g].y, w[q][g].z, w[q][g].w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        acc[8 * g + 2 * c] = __fmaf_rn(v[q], q16_lo(ws[c]), acc[8 * g + 2 * c]);
-                        acc[8 * g + 2 * c + 1] = __fmaf_rn(v[q], q16_hi(ws[c]), acc[8 * g + 2 * c + 1]);
-                    }
-                }
-            }
-        }
-        const float n = (float)(e - s);
-        // asum is itself an FP32 sum (relative error below n u); the 1.25
-        // covers it and the second-order terms while n u <= 0.05
-        const float bound = n * 5.9604644775390625e-8f > 0.05f
-                                ? INFINITY
-                                : 1.25f * n * 5.9604644775390625e-8f * 32768.0f * asum + n * 1.4e-45f;
-#pragma unroll
-        for (int g = 0; g < V; ++g) {
-            uint32_t byte = 0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int u = 8 * g + c;
-                bool bit;
-                if (fabsf(acc[u]) > bound) {
-                    bit = acc[u] >= 0.0f;
-                } else {
-                    const uint32_t j = 8 * (t + g * T) + c;
-                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
-                    if (slot < BLSH_RECHECK_CAP) {
-                        queue[slot] = make_uint2((uint32_t)row, j);
-                        bit = false;
-                    } else {
-                        const double d = srp_recheck_fp64<uint16_t>(indices, values, s, e, R, dim, bits, j);
-                        bit = d >= 0.0;
-                        ++rechecked;
-                        zeros += d == 0.0;
-                    }
-                }
-                byte |= (uint32_t)bit << c;
-            }
-            uint32_t word = byte << (8 * (lane & 3));
-            word |= __shfl_xor_sync(kFull, word, 1);
-            word |= __shfl_xor_sync(kFull, word, 2);
-            if ((lane & 3) == 0) sig[(size_t)row * words + ((t + g * T) >> 2)] = word;
-        }
-    }
-    if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
-    if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
-    if (zeros) atomicAdd(&scratch->counters[3], zeros);
-}
 
 // Two-byte codes of Gaussian samples (Section 4.3): q = floor((x + 8) 2^12),
 // formed as floor(x 2^12) + 2^15 (exact in FP32).  Codes outside [0, 65535]
@@ -662,14 +567,16 @@ __global__ void __launch_bounds__(256) srp_dense_simt_kernel(const float *__rest
 }
 
 // Columns [col0, col0 + ncols) of the sparse projection (multiples of 128)
-// for the rows row_mask selects, on the 16-byte path; -1 when that path does
-// not take the shape.
+// for the rows row_mask selects, on the 16-byte path (R float or two-byte
+// codes); -1 when that path does not take the shape.
+template <typename RT>
 int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
-                    const float *R, int64_t dim, int bits, int col0, int ncols, const uint8_t *row_mask,
+                    const RT *R, int64_t dim, int bits, int col0, int ncols, const uint8_t *row_mask,
                     uint32_t *sig, cudaStream_t s) {
     // selected rows (usually few): pieces of 512 columns, one per CTA; all
     // rows: the whole range per CTA.  T4 = 32 * (largest divisor of
-    // groups/32 up to 8) threads, V = groups / T4 float4 groups per thread
+    // groups/32 up to 8) threads, V = groups / T4 groups of four columns per
+    // thread
     const int piece = row_mask && ncols % 512 == 0 ? 512 : ncols;
     const int pieces = ncols / piece;
     const int groups = piece / 4;
@@ -683,17 +590,38 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
     uint2 *q = ctx->recheck_queue;
     blsh_dev_scratch *scr = ctx->scratch;
+    const char *name = sizeof(RT) == 2 ? "srp_sparse4_kernel (two-byte codes)" : "srp_sparse4_kernel";
     blsh_time_start(ctx, s);
     switch (V) {
-    case 1: srp_sparse4_kernel<1><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    case 2: srp_sparse4_kernel<2><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    case 3: srp_sparse4_kernel<3><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    default: srp_sparse4_kernel<4><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 1: srp_sparse4_kernel<1, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 2: srp_sparse4_kernel<2, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 3: srp_sparse4_kernel<3, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    default: srp_sparse4_kernel<4, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
     }
-    BLSH_LAUNCHED(ctx, "srp_sparse4_kernel");
+    BLSH_LAUNCHED(ctx, name);
     blsh_time_start(ctx, s);
-    srp_recheck_kernel<float><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig, scr);
+    srp_recheck_kernel<RT><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, R, dim, bits, sig, scr);
     BLSH_LAUNCHED(ctx, "srp_recheck_kernel");
+    return BLSH_OK;
+}
+
+// Column ranges the kernel cannot take in one launch (col_count / 128 with no
+// divisor in 1..8 that leaves at most 4 groups per thread) are split: the
+// largest piece it can take first, and so on (128 columns always can).
+template <typename RT>
+int srp_sparse_range(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
+                     const RT *R, int64_t dim, int bits, int col_begin, int col_count, const uint8_t *row_mask,
+                     uint32_t *sig, cudaStream_t s) {
+    for (int c0 = col_begin, left = col_count; left > 0;) {
+        int rc = -1, piece = left;
+        for (; piece > 0; piece -= 128) {
+            rc = srp_sparse_cols<RT>(ctx, indptr, indices, values, N, R, dim, bits, c0, piece, row_mask, sig, s);
+            if (rc != -1) break;
+        }
+        if (rc != BLSH_OK) return rc == -1 ? blsh_fail(ctx, BLSH_EINVAL, "no launch shape") : rc;
+        c0 += piece;
+        left -= piece;
+    }
     return BLSH_OK;
 }
 
@@ -773,7 +701,7 @@ extern "C" int blsh_srp_sparse(blsh_ctx *ctx, const int64_t *indptr, const uint3
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
     if (bits % 128 == 0 && blsh_aligned(R, 16)) {
-        const int rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, 0, bits, nullptr, sig, s);
+        const int rc = srp_sparse_cols<float>(ctx, indptr, indices, values, N, R, dim, bits, 0, bits, nullptr, sig, s);
         if (rc != -1) return rc;
     }
     blsh_time_start(ctx, s);
@@ -847,22 +775,25 @@ extern "C" int blsh_srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const 
     if (!blsh_aligned(indptr, 8) || !blsh_aligned(R, 16)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
     if (N == 0) return BLSH_OK;
     blsh_device_guard g(ctx->device);
-    // a column count the kernel cannot take in one launch (col_count / 128
-    // without a divisor in 1..8 that leaves at most 4 float4 groups per
-    // thread) is split: the largest piece it can take first, and so on
-    // (128 columns always can)
-    for (int c0 = col_begin, left = col_count; left > 0;) {
-        int rc = -1, piece = left;
-        for (; piece > 0; piece -= 128) {
-            rc = srp_sparse_cols(ctx, indptr, indices, values, N, R, dim, bits, c0, piece, row_mask, sig,
-                                 blsh_stream(stream));
-            if (rc != -1) break;
-        }
-        if (rc != BLSH_OK) return rc == -1 ? blsh_fail(ctx, BLSH_EINVAL, "no launch shape") : rc;
-        c0 += piece;
-        left -= piece;
-    }
-    return BLSH_OK;
+    return srp_sparse_range<float>(ctx, indptr, indices, values, N, R, dim, bits, col_begin, col_count, row_mask,
+                                   sig, blsh_stream(stream));
+}
+
+extern "C" int blsh_srp_sparse_q16_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                        const float *values, int64_t N, const uint16_t *Rq, int64_t dim,
+                                        int32_t bits, int32_t col_begin, int32_t col_count,
+                                        const uint8_t *row_mask, uint32_t *sig, void *stream) {
+    if (!ctx) return BLSH_EINVAL;
+    if (!indptr || !indices || !values || !Rq || !sig)
+        return blsh_fail(ctx, BLSH_EINVAL, "indptr, indices, values, Rq and sig are required");
+    if (N < 0 || N >= (1ll << 32) || dim <= 0 || bits <= 0 || bits % 128 || bits > 4096 || col_begin < 0 ||
+        col_count <= 0 || col_begin % 128 || col_count % 128 || col_begin + col_count > bits)
+        return blsh_fail(ctx, BLSH_EINVAL, "bits, col_begin and col_count must be multiples of 128 within bits");
+    if (!blsh_aligned(indptr, 8) || !blsh_aligned(Rq, 8)) return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
+    if (N == 0) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    return srp_sparse_range<uint16_t>(ctx, indptr, indices, values, N, Rq, dim, bits, col_begin, col_count, row_mask,
+                                      sig, blsh_stream(stream));
 }
 
 extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
@@ -879,27 +810,8 @@ extern "C" int blsh_srp_sparse_q16(blsh_ctx *ctx, const int64_t *indptr, const u
     cudaStream_t s = blsh_stream(stream);
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N < cap ? N : cap);
-    if (bits % 256 == 0 && blsh_aligned(Rq, 16)) {
-        // 16-byte path: T8 = 32 * (largest divisor of groups/32 up to 8) threads,
-        // V = groups / T8 groups of 8 bits per thread (1 or 2 for bits <= 4096)
-        const int groups = bits / 8;
-        int wt = 8;
-        while ((groups / 32) % wt) --wt;
-        const int T8 = 32 * wt, V = groups / T8;
-        BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
-        uint2 *q = ctx->recheck_queue;
-        blsh_time_start(ctx, s);
-        if (V == 1)
-            srp_sparse_q16_kernel<1, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
-        else
-            srp_sparse_q16_kernel<2, kSrpQ16Batch><<<grid, T8, 0, s>>>(indptr, indices, values, N, Rq, dim, bits, sig, ctx->scratch, q);
-        BLSH_LAUNCHED(ctx, "srp_sparse_q16_kernel");
-        blsh_time_start(ctx, s);
-        srp_recheck_kernel<uint16_t><<<ctx->sm_count * 4, 256, 0, s>>>(q, indptr, indices, values, Rq, dim, bits,
-                                                                         sig, ctx->scratch);
-        BLSH_LAUNCHED(ctx, "srp_recheck_kernel");
-        return BLSH_OK;
-    }
+    if (bits % 128 == 0 && blsh_aligned(Rq, 8))   // 8-byte loads of four codes
+        return srp_sparse_range<uint16_t>(ctx, indptr, indices, values, N, Rq, dim, bits, 0, bits, nullptr, sig, s);
     int per_thread;
     const int T = srp_threads(bits, &per_thread);
     if (per_thread > kSrpMaxPerThread) return blsh_fail(ctx, BLSH_EINVAL, "bits/32 needs a divisor in 2..8");

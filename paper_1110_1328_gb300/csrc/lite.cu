@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
     }
 }
 
-// Survivors into a queue (the context's work queue, BLSH_RECHECK_CAP
+// Survivors into a queue (the context's survivor queue, BLSH_LITE_QUEUE_CAP
 // entries): warps scan tiles of 512 statuses in grid-stride order and append
 // their survivors' indices with one atomic per tile.  Survivors beyond the
 // queue are left for lite_exact_kernel.
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, uns
         base = __shfl_sync(kFull, base, 31);
         unsigned long long slot = base + incl - c;
         for (uint32_t b = surv; b; b &= b - 1, ++slot)
-            if (slot < BLSH_RECHECK_CAP) queue[slot] = (unsigned long long)(qs + __ffs(b) - 1);
+            if (slot < BLSH_LITE_QUEUE_CAP) queue[slot] = (unsigned long long)(qs + __ffs(b) - 1);
     }
 }
 
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, uns
 template <bool COSINE>
 __global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const unsigned long long *queue) {
     const unsigned long long total = A.scratch->work3;
-    const unsigned long long n = total < BLSH_RECHECK_CAP ? total : BLSH_RECHECK_CAP;
+    const unsigned long long n = total < BLSH_LITE_QUEUE_CAP ? total : BLSH_LITE_QUEUE_CAP;
     extern __shared__ uint32_t lite_smem[];
     uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
     float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
@@ -351,7 +351,7 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
     L.vec = blsh_aligned(status, 16);
     // survivors: queued (balanced over warps), then any beyond the queue in place
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, 2 * sizeof(unsigned long long), s));   // work2, work3
-    unsigned long long *queue = reinterpret_cast<unsigned long long *>(ctx->recheck_queue);
+    unsigned long long *queue = ctx->lite_queue;
     blsh_time_start(ctx, s);
     lite_collect_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(L, queue);
     BLSH_LAUNCHED(ctx, "lite_collect_kernel");

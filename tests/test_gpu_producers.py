@@ -306,11 +306,11 @@ def test_lite_cosine_fixed_point_edges(B, ctx):
 
 
 def test_lite_survivors_beyond_queue(B, ctx):
-    """1.1 million survivors (identical signatures): more than the survivor
-    queue holds (2^20), so the rest go through the in-place pass."""
+    """8.5 million survivors (identical signatures): more than the survivor
+    queue holds (2^23), so the rest go through the in-place pass."""
     sets = synth.jaccard_sets(n_sets=3000, vocab=400, mean_size=12, n_groups=300, seed=11)
     sig = np.zeros((sets.n, 64), np.uint32)
-    pairs = synth.random_pairs(sets.n, 1_100_000, seed=12)
+    pairs = synth.random_pairs(sets.n, 8_500_000, seed=12)
     p = O.Params(kind=O.JACCARD, n_max=64, h=64, t=0.3)
     want = O.verify_lite(O.tables(p), pairs, sig, sets)
     assert np.all(want.status != O.PRUNED)

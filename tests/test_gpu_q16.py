@@ -128,3 +128,26 @@ def test_srp_q16_on_generated_codes(B, ctx):
     B.blsh_srp_sparse_q16(ctx, ip, ix, val, Rq, sig)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(sig.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("cols", [(0, 512), (384, 1664), (128, 1024)])
+def test_srp_q16_cols_selected_rows(B, ctx, cols):
+    """A column range of the two-byte projection for every third row (1,664
+    columns take two launches): those words equal the oracle's, the rest keep
+    their sentinel."""
+    vecs = synth.tfidf_vectors(n_docs=900, dim=20000, mean_nnz=80, n_groups=50, seed=33)
+    Rq = O.gaussian_codes(5, 20000, 2048)
+    want = O.srp_sparse_q16(vecs, Rq)
+    ip, ix, val = csr_dev(vecs)
+    mask = (np.arange(vecs.n) % 3 == 1).astype(np.uint8)
+    sig = torch.full((vecs.n, 64), 0x5A5A5A5A, dtype=torch.int32, device=dev)
+    c0, cn = cols
+    B.blsh_srp_sparse_q16_cols(ctx, ip, ix, val, torch.from_numpy(Rq.view(np.int16)).to(dev), sig, c0, cn,
+                               row_mask=torch.from_numpy(mask).to(dev))
+    assert B.blsh_status(ctx) == 0
+    got = sig.cpu().numpy().view(np.uint32)
+    sel = mask == 1
+    w0, w1 = c0 // 32, (c0 + cn) // 32
+    assert np.array_equal(got[sel][:, w0:w1], want[sel][:, w0:w1])
+    assert np.all(got[sel][:, :w0] == 0x5A5A5A5A) and np.all(got[sel][:, w1:] == 0x5A5A5A5A)
+    assert np.all(got[~sel] == 0x5A5A5A5A)
