@@ -191,3 +191,72 @@ def test_precision_workload_sampled(B):
     dp = pipe.pairs[:P].long()
     key, _ = torch.sort((dp[:, 0] << 32) | dp[:, 1])
     assert bool((key[1:] > key[:-1]).all())
+
+
+def test_large_mixed_workload_sampled(B):
+    """5,000,000 tf-idf vectors over a 2^24-term vocabulary, R generated on
+    the device as two-byte codes (68.7 GB), about 1e9 candidates verified by
+    Algorithms 1 and 2 in batches: sampled signature rows bit-exact to the
+    oracle's (its own codes for the terms those rows use), sampled pairs'
+    outcomes of both algorithms recomputed by the oracle, every sampled pair
+    colliding in a band, the candidate list free of duplicates, and the
+    kept counts equal to the statuses."""
+    w = dict(bench.WORKLOADS["large-mixed"])
+    dev = torch.device("cuda", 0)
+    pipe = bench.LargePipeline(B, torch, w, dev)
+    pipe.step()
+    assert B.blsh_status(pipe.ctx) == 0
+    P = pipe.P
+    assert P > 100_000_000 and pipe.batch >= P          # one batch: every pair's outcome is kept
+    rng = np.random.default_rng(3)
+    q = np.sort(rng.choice(P, 3000, replace=False))
+    qd = torch.from_numpy(q).to(dev)
+    sp = u32(pipe.pairs[qd])
+    assert np.all(sp[:, 0] < sp[:, 1])
+    extra = rng.choice(pipe.N, 300, replace=False)
+    ids, inv = np.unique(np.concatenate([sp.reshape(-1), extra]), return_inverse=True)
+    # the sampled objects' rows, with their terms renumbered 0..T-1
+    indptr = pipe.indptr.cpu().numpy()
+    rows = [np.arange(indptr[i], indptr[i + 1]) for i in ids]
+    sel = torch.from_numpy(np.concatenate(rows)).to(dev)
+    terms = pipe.indices[sel].cpu().numpy().view(np.uint32)
+    vals = pipe.values[sel].cpu().numpy()
+    uterm, tinv = np.unique(terms, return_inverse=True)
+    local = synth.CSR(np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64),
+                      tinv.astype(np.uint32), vals, len(uterm))
+    bits = w["bits"]
+    Rq = np.stack([O.gaussian_codes(w["r_seed"], 1, bits, row0=int(t))[0] for t in uterm])
+    sig_o = O.srp_sparse_q16(local, Rq)
+    assert np.array_equal(u32(pipe.sig[torch.from_numpy(ids).to(dev)]), sig_o)
+    lp = inv[: 2 * len(q)].reshape(-1, 2).astype(np.uint32)
+    r, bands = w["rows"], w["bands"]
+
+    def band_bits(s, b):
+        return (s[:, (b * r) // 32] >> np.uint32((b * r) % 32)) & np.uint32((1 << r) - 1)
+
+    band_eq = np.stack([band_bits(sig_o[lp[:, 0]], b) == band_bits(sig_o[lp[:, 1]], b) for b in range(bands)], 1)
+    assert band_eq.any(1).all()
+    p = O.Params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    tab = O.tables(p)
+    want = O.verify(tab, lp, sig_o)
+    assert np.array_equal(pipe.status[qd].cpu().numpy(), want.status)
+    assert np.array_equal(pipe.n_used[qd].cpu().numpy().view(np.uint16), want.n_used)
+    assert np.array_equal(pipe.m[qd].cpu().numpy().view(np.uint16), want.m)
+    est = pipe.est[qd].cpu().numpy()
+    ok = ~np.isnan(want.est)
+    assert np.max(np.abs(est[ok] - want.est[ok]), initial=0) <= 1e-6
+    lite = O.verify_lite(tab, lp, sig_o, local)
+    assert np.array_equal(pipe.lstatus[qd].cpu().numpy(), lite.status)
+    sim = pipe.sim[qd].cpu().numpy()
+    ok = ~np.isnan(lite.sim)
+    assert np.array_equal(sim[ok], lite.sim[ok])
+    # each distinct pair once (sorted on the device)
+    dp = pipe.pairs[:P].long()
+    key, _ = torch.sort((dp[:, 0] << 32) | dp[:, 1])
+    assert bool((key[1:] > key[:-1]).all())
+    del key, dp
+    # the kept counts are those of the statuses
+    st = pipe.status[:P]
+    n1 = int(((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).sum().item())
+    n2 = int((pipe.lstatus[:P] == B.LITE_ACCEPT).sum().item())
+    assert [int(x) for x in pipe.kept.cpu()] == [n1, n2]
