@@ -206,6 +206,26 @@ def blsh_ctx_create(device: int | None = None) -> Context:
     return Context(device)
 
 
+def blsh_ctx_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def blsh_tables_destroy(tab: "Tables") -> None:
+    tab.close()
+
+
+def blsh_last_error(ctx: Context | None) -> str:
+    return (lib().blsh_last_error(ctx.handle if ctx is not None else None) or b"").decode()
+
+
+def blsh_strerror(rc: int) -> str:
+    return (lib().blsh_strerror(int(rc)) or b"").decode()
+
+
+def blsh_version() -> str:
+    return lib().blsh_version().decode()
+
+
 def blsh_status(ctx: Context, stream=None, counters: bool = False):
     buf = (C.c_uint64 * 4)()
     rc = lib().blsh_status(ctx.handle, _stream(stream), buf)

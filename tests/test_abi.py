@@ -25,10 +25,14 @@ def test_library_exports_every_declared_symbol(B):
     lib = C.CDLL(B.lib_path())
     missing = [n for n in declared() if not hasattr(lib, n)]
     assert not missing
-    # the binding declares a Python function of the same name for each
+    # the binding declares each symbol's signature and has a Python function
+    # of the same name for each
     import paper_1110_1328_gb300 as pkg
     assert not [n for n in declared() if not hasattr(pkg.lib(), n)]
+    assert not [n for n in declared() if not callable(getattr(pkg, n, None))]
     assert B.lib().blsh_version().startswith(b"libblsh")
+    assert pkg.blsh_version().startswith("libblsh") and pkg.blsh_strerror(B.ERANGE) == "pair index out of range"
+    assert pkg.blsh_last_error(None) == "no context"
 
 
 def test_host_checks_without_device(B):
