@@ -102,6 +102,7 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
         blsh_device_guard g(ctx->device);
         timing_release(ctx);
         if (ctx->plane) cudaFree(ctx->plane);
+        if (ctx->norm2) cudaFree(ctx->norm2);
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
         if (ctx->lite_queue) cudaFree(ctx->lite_queue);

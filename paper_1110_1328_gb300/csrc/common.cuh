@@ -30,6 +30,7 @@ struct blsh_dev_scratch {
     unsigned long long work3;          // lite: survivors queued
     unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
     unsigned long long band_work[2];   // banding: next chunk of positions (count pass, write pass)
+    unsigned int norm2_valid;          // Lite: the rows' squared norms were formed for this call
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
 };
 
@@ -43,6 +44,8 @@ struct blsh_ctx {
     unsigned long long *lite_queue = nullptr;         // [BLSH_LITE_QUEUE_CAP] Lite survivors (pair indices)
     void *plane = nullptr;                            // verification: [plane_cap] first two words of each row
     long long plane_cap = 0;
+    void *norm2 = nullptr;                            // Lite (cosine): [norm2_cap] rows' squared norms
+    long long norm2_cap = 0;
     char err[512] = {0};
     std::map<const blsh_tables *, blsh_plan> plans;   // autotuned plans
     std::atomic<long long> launches{0};            // kernels launched through this context

@@ -38,6 +38,7 @@ struct LiteArgs {
     double *sim;
     blsh_dev_scratch *scratch;
     int vec;                  // status is 16-byte aligned
+    const long long *norm2;   // cosine: each row's sum of fixed_term(v, v), or NULL (formed per pair)
 };
 
 constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab (this pass sees only survivors the queue missed)
@@ -127,13 +128,20 @@ __device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, 
                 s = uni == 0 ? 0.0 : __ddiv_rn((double)inter, (double)uni);
             } else {
                 long long D = 0, Nx = 0, Ny = 0;
-                for (long long i = lane; i < na; i += 32) {
-                    const float v = __ldg(A.values + ax + i);
-                    Nx += fixed_term(v, v);
-                }
-                for (long long i = lane; i < nb; i += 32) {
-                    const float v = __ldg(A.values + ay + i);
-                    Ny += fixed_term(v, v);
+                if (A.norm2 && A.scratch->norm2_valid) {     // the rows' squared norms, formed once per call
+                    Nx = __ldg(A.norm2 + pr.x);
+                    Ny = __ldg(A.norm2 + pr.y);
+                } else {
+                    for (long long i = lane; i < na; i += 32) {
+                        const float v = __ldg(A.values + ax + i);
+                        Nx += fixed_term(v, v);
+                    }
+                    for (long long i = lane; i < nb; i += 32) {
+                        const float v = __ldg(A.values + ay + i);
+                        Ny += fixed_term(v, v);
+                    }
+                    Nx = warp_sum(Nx);
+                    Ny = warp_sum(Ny);
                 }
                 for (long long i = lane; i < ns; i += 32) {
                     const uint32_t v = __ldg(A.indices + s0 + i);
@@ -141,8 +149,6 @@ __device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, 
                     if (pos < nl && Lidx[pos] == v) D += fixed_term(__ldg(A.values + s0 + i), Lval[pos]);
                 }
                 D = warp_sum(D);
-                Nx = warp_sum(Nx);
-                Ny = warp_sum(Ny);
                 if (Nx == 0 || Ny == 0) {
                     s = 0.0;
                 } else {
@@ -154,6 +160,32 @@ __device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, 
                 A.sim[q] = s;
                 A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
             }
+}
+
+// Each row's sum of fixed_term(v, v) (the squared norm of the exact cosine,
+// an integer: independent of the order of the terms): one warp per row.
+// Formed only when there are more survivors than half the rows (the
+// collection pass has counted them); otherwise each survivor forms its two
+// norms itself, which is less work.
+__global__ void __launch_bounds__(256) row_norm2_kernel(const int64_t *__restrict__ indptr,
+                                                        const float *__restrict__ values, long long N,
+                                                        long long *__restrict__ norm2,
+                                                        blsh_dev_scratch *scratch) {
+    const bool form = scratch->work3 * 2ull > (unsigned long long)N;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scratch->norm2_valid = form ? 1u : 0u;
+    if (!form) return;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nwarps) {
+        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+        long long acc = 0;
+        for (long long i = s + lane; i < e; i += 32) {
+            const float v = __ldg(values + i);
+            acc += fixed_term(v, v);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) norm2[row] = acc;
+    }
 }
 
 template <bool COSINE>
@@ -267,9 +299,9 @@ __global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const
         lite_exact_pair<COSINE>(A, (long long)queue[it], w_idx, w_val);
 }
 
-int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, const int64_t *indptr,
-                    const uint32_t *indices, const float *values, double t, uint8_t *status, double *sim,
-                    cudaStream_t s);
+int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, int64_t N,
+                    const int64_t *indptr, const uint32_t *indices, const float *values, double t, uint8_t *status,
+                    double *sim, cudaStream_t s);
 
 }  // namespace
 
@@ -328,15 +360,15 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     int rc = blsh_launch_verify(ctx, A, plan, s);
     if (rc) return rc;
     if (P == 0) return BLSH_OK;
-    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, indptr, indices, values, p.t, status, sim, s);
+    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, N, indptr, indices, values, p.t, status, sim, s);
 }
 
 namespace {
 
 // Pass 2 of Algorithm 2: the exact similarity of every survivor.
-int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, const int64_t *indptr,
-                    const uint32_t *indices, const float *values, double t, uint8_t *status, double *sim,
-                    cudaStream_t s) {
+int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, int64_t N,
+                    const int64_t *indptr, const uint32_t *indices, const float *values, double t, uint8_t *status,
+                    double *sim, cudaStream_t s) {
     LiteArgs L;
     L.pairs = pairs;
     L.P = P;
@@ -349,12 +381,36 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
     L.sim = sim;
     L.scratch = ctx->scratch;
     L.vec = blsh_aligned(status, 16);
+    L.norm2 = nullptr;
+    if (values && N > 0) {
+        // the rows' squared norms once per call, in a context-owned buffer
+        // grown outside stream capture (a captured call with a larger N forms
+        // them per pair instead)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BLSH_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
+        if (ctx->norm2_cap < N && cs == cudaStreamCaptureStatusNone) {
+            BLSH_CUDA(ctx, cudaStreamSynchronize(s));
+            if (ctx->norm2) BLSH_CUDA(ctx, cudaFree(ctx->norm2));
+            ctx->norm2 = nullptr;
+            ctx->norm2_cap = 0;
+            BLSH_CUDA(ctx, cudaMalloc(&ctx->norm2, (size_t)N * sizeof(long long)));
+            ctx->norm2_cap = N;
+        }
+        if (ctx->norm2_cap >= N) L.norm2 = (const long long *)ctx->norm2;
+    }
     // survivors: queued (balanced over warps), then any beyond the queue in place
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, 2 * sizeof(unsigned long long), s));   // work2, work3
     unsigned long long *queue = ctx->lite_queue;
     blsh_time_start(ctx, s);
     lite_collect_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(L, queue);
     BLSH_LAUNCHED(ctx, "lite_collect_kernel");
+    if (L.norm2) {
+        const long long blocks = (N + 7) / 8, cap = (long long)ctx->sm_count * 16;
+        blsh_time_start(ctx, s);
+        row_norm2_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
+            indptr, values, N, const_cast<long long *>(L.norm2), ctx->scratch);
+        BLSH_LAUNCHED(ctx, "row_norm2_kernel");
+    }
     int occ = 0;
     const size_t smem = 8 * 2 * kLiteStage * sizeof(uint32_t);   // 32 KB per CTA of 8 warps
     if (values) {
@@ -417,7 +473,7 @@ int verify_both(blsh_ctx *ctx, const blsh_tables *tab, int32_t hash_limit, const
     rc = blsh_launch_verify(ctx, A, plan, s);
     if (rc) return rc;
     if (P == 0) return BLSH_OK;
-    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, indptr, indices, values, p.t, lite_status, sim, s);
+    return lite_exact_pass(ctx, A.pairs, P, A.P_dev, N, indptr, indices, values, p.t, lite_status, sim, s);
 }
 
 }  // namespace
