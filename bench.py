@@ -1056,6 +1056,13 @@ def run_large(args, w):
         k[0] += 1
         k[1] += t_ms
     kern = {n: {"launches": c, "ms": round(t, 3)} for n, (c, t) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    if args.profile_step:
+        # one more eager step inside an NVTX range, for ncu --nvtx-include "blsh_step/"
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("blsh_step")
+        pipe.step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     nnz = int(pipe.indptr[-1].item())
     hist = pipe.hist_total.cpu().numpy()
     kept = [int(x) for x in pipe.kept.cpu()]
