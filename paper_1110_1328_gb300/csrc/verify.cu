@@ -625,8 +625,16 @@ __global__ void __launch_bounds__(256) verify_resume_kernel(const VerifyArgs A, 
         const long long pd = *A.P_dev;
         P = pd < 0 ? 0 : (pd < P ? pd : P);
     }
-    const long long stride = (long long)gridDim.x * blockDim.x * 16;
-    for (long long q0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 16; q0 < P; q0 += stride) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    // a warp scans 512 statuses (16 per lane), then works each open pair of
+    // them with all its lanes: lane l takes chunk j0 + l of 32 chunks at a
+    // time, an inclusive scan gives m after every chunk, and the first chunk
+    // whose test stops the pair (the tests of Algorithm 1, in its order) is
+    // the one the sequential loop would stop at
+    for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 512; base < P;
+         base += nwarps * 512) {
+        const long long q0 = base + 16ll * lane;
         uint32_t hit = 0;
         if (vec && q0 + 16 <= P) {
             const uint4 v = *reinterpret_cast<const uint4 *>(A.status + q0);
@@ -637,26 +645,53 @@ __global__ void __launch_bounds__(256) verify_resume_kernel(const VerifyArgs A, 
             for (int i = 0; i < 16; ++i)
                 if (q0 + i < P && A.status[q0 + i] == BLSH_NEEDS_HASHES) hit |= 1u << i;
         }
-        for (; hit; hit &= hit - 1) {
-            const long long q = q0 + __ffs(hit) - 1;
-            const uint2 pr = __ldg(A.pairs + q);
-            const uint32_t *rx = A.sig + (size_t)pr.x * A.W, *ry = A.sig + (size_t)pr.y * A.W;
-            int m = 0, j = 0, st = BLSH_ACCEPT_AT_MAX;
-            for (;; ++j) {
-                const int w0 = j * A.chunk_words;
-                for (int w = w0; w < w0 + A.chunk_words; ++w) {
-                    const uint32_t a = __ldg(rx + w), b = __ldg(ry + w);
-                    m += kind == BLSH_JACCARD ? (a == b) : 32 - __popc(a ^ b);
+        for (unsigned lanes = __ballot_sync(kFull, hit != 0); lanes; lanes &= lanes - 1) {
+            const int l = __ffs(lanes) - 1;
+            for (uint32_t bits = __shfl_sync(kFull, hit, l); bits; bits &= bits - 1) {
+                const long long q = base + 16ll * l + (__ffs(bits) - 1);
+                const uint2 pr = __ldg(A.pairs + q);
+                const uint32_t *rx = A.sig + (size_t)pr.x * A.W, *ry = A.sig + (size_t)pr.y * A.W;
+                int carry = 0, jstop = A.levels - 1, mstop = 0, st = BLSH_ACCEPT_AT_MAX;
+                for (int j0 = 0; j0 < A.levels; j0 += 32) {
+                    const int j = j0 + lane;
+                    int c = 0;
+                    if (j < A.levels)
+                        for (int w = j * A.chunk_words; w < (j + 1) * A.chunk_words; ++w) {
+                            const uint32_t a = __ldg(rx + w), b = __ldg(ry + w);
+                            c += kind == BLSH_JACCARD ? (a == b) : 32 - __popc(a ^ b);
+                        }
+                    int m = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(kFull, m, o);
+                        if (lane >= o) m += t;
+                    }
+                    m += carry;
+                    int s = -1;
+                    if (j < A.levels) {
+                        if (m < __ldg(A.min_matches + j)) s = BLSH_PRUNED;
+                        else if ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u) s = BLSH_ACCEPT;
+                        else if (j + 1 == A.levels) s = BLSH_ACCEPT_AT_MAX;
+                    }
+                    const unsigned stop = __ballot_sync(kFull, s >= 0);
+                    if (stop) {
+                        const int f = __ffs(stop) - 1;
+                        jstop = j0 + f;
+                        mstop = __shfl_sync(kFull, m, f);
+                        st = __shfl_sync(kFull, s, f);
+                        break;
+                    }
+                    carry = __shfl_sync(kFull, m, 31);
                 }
-                if (m < __ldg(A.min_matches + j)) { st = BLSH_PRUNED; break; }
-                if ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u) { st = BLSH_ACCEPT; break; }
-                if (j + 1 == A.levels) { st = BLSH_ACCEPT_AT_MAX; break; }
+                if (lane == 0) {
+                    A.status[q] = (uint8_t)st;
+                    if (A.n_used) A.n_used[q] = (uint16_t)((jstop + 1) * A.k);
+                    if (A.m_out) A.m_out[q] = (uint16_t)mstop;
+                    if (A.est_out && st != BLSH_PRUNED)
+                        A.est_out[q] = __ldg(A.est_tab + (size_t)jstop * A.est_stride + mstop);
+                    if (A.stop_hist) atomicAdd(A.stop_hist + jstop, 1ull);
+                }
             }
-            A.status[q] = (uint8_t)st;
-            if (A.n_used) A.n_used[q] = (uint16_t)((j + 1) * A.k);
-            if (A.m_out) A.m_out[q] = (uint16_t)m;
-            if (A.est_out && st != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + (size_t)j * A.est_stride + m);
-            if (A.stop_hist) atomicAdd(A.stop_hist + j, 1ull);
         }
     }
 }
@@ -676,9 +711,9 @@ extern "C" int blsh_verify_resume(blsh_ctx *ctx, const blsh_tables *tab, const u
     if (P == 0) return BLSH_OK;
     blsh_device_guard g(ctx->device);
     cudaStream_t s = blsh_stream(stream);
-    const long long groups = (P + 15) / 16;
+    const long long warps = (P + 511) / 512;
     const long long cap = (long long)ctx->sm_count * 8;
-    const long long blocks = (groups + 255) / 256;
+    const long long blocks = (warps + 7) / 8;
     blsh_time_start(ctx, s);
     verify_resume_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A, tab->p.kind,
                                                                              blsh_aligned(status, 16) ? 1 : 0);
