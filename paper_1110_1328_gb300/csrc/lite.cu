@@ -132,10 +132,12 @@ __device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, 
                     Nx = __ldg(A.norm2 + pr.x);
                     Ny = __ldg(A.norm2 + pr.y);
                 } else {
+#pragma unroll 4
                     for (long long i = lane; i < na; i += 32) {
                         const float v = __ldg(A.values + ax + i);
                         Nx += fixed_term(v, v);
                     }
+#pragma unroll 4
                     for (long long i = lane; i < nb; i += 32) {
                         const float v = __ldg(A.values + ay + i);
                         Ny += fixed_term(v, v);
@@ -143,6 +145,7 @@ __device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, 
                     Nx = warp_sum(Nx);
                     Ny = warp_sum(Ny);
                 }
+#pragma unroll 4
                 for (long long i = lane; i < ns; i += 32) {
                     const uint32_t v = __ldg(A.indices + s0 + i);
                     const long long pos = lower_bound(Lidx, nl, v);
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256) row_norm2_kernel(const int64_t *__restric
     for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nwarps) {
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
         long long acc = 0;
+#pragma unroll 4
         for (long long i = s + lane; i < e; i += 32) {
             const float v = __ldg(values + i);
             acc += fixed_term(v, v);
