@@ -120,9 +120,10 @@ def test_boundaries_with_mpmath():
                 assert prune(p, mm - 1, n) < p.eps
 
 
-def test_survey_cross_check_values():
-    """Values regenerated independently while planning (scipy); a sanity
-    check that the readings of Sections 4.1-4.3 are the intended ones."""
+def test_tables_cross_check_values():
+    """Table entries computed independently with scipy's regularised
+    incomplete beta; a check that the readings of Sections 4.1-4.3 are the
+    intended ones."""
     tj = O.tables(O.Params(kind=O.JACCARD, n_max=256))
     assert tj.min_matches.tolist() == [18, 38, 59, 80, 102, 123, 144, 166]
     c = np.nonzero(tj.conc[7])[0]
