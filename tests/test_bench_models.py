@@ -1,0 +1,67 @@
+"""Host-side logic of bench.py without a GPU: the algorithmic-byte model the
+roofline divides by, and the lazy-hashing prefix rule."""
+import types
+
+import numpy as np
+import pytest
+import torch
+
+import bench
+import paper_1110_1328_gb300 as B
+import synth
+
+
+def test_csr_rows_bytes_by_hand():
+    # rows {0: [1, 3], 1: [3], 2: []} over 4 terms, 128 columns of float R
+    indptr = np.array([0, 2, 3, 3], np.int64)
+    indices = np.array([1, 3, 3], np.uint32)
+    # 3 nonzeros (8 B each), 3 rows (16 B + 16 B of signature each), 2 distinct terms x 512 B
+    assert bench.csr_rows_bytes(indptr, indices, None, 128, 4) == 3 * 8 + 3 * (16 + 16) + 2 * 512
+    # only row 1: one nonzero, one row, one distinct term
+    mask = np.array([False, True, False])
+    assert bench.csr_rows_bytes(indptr, indices, mask, 128, 4) == 8 + (16 + 16) + 512
+    # two-byte codes halve the R bytes
+    assert bench.csr_rows_bytes(indptr, indices, None, 128, 2) == 3 * 8 + 3 * 32 + 2 * 256
+
+
+def _fake_pipe(w, P, lazy):
+    rng = np.random.default_rng(0)
+    return types.SimpleNamespace(P=P, N=w["n"], lazy_bits=lazy, with_lite=True, dense=False,
+                                 pairs=torch.from_numpy(rng.integers(0, w["n"], (P, 2)).astype(np.int32)))
+
+
+def test_kernel_work_covers_every_timed_kernel_of_a_cosine_step():
+    w = dict(bench.WORKLOADS["cosine-small"], n=500)
+    objs = synth.tfidf_vectors(n_docs=500, dim=5000, mean_nnz=40, n_groups=20, seed=1)
+    P = 10_000
+    rng = np.random.default_rng(1)
+    st = rng.integers(0, 4, P).astype(np.uint8)
+    nu = (rng.integers(4, 64, P) * 32).astype(np.uint16)
+    lst = rng.integers(0, 4, P).astype(np.uint8)
+    need = rng.random(500) < 0.1
+    work = bench.kernel_work(B, _fake_pipe(w, P, 512), w, objs, st, nu, lst, need)
+    for k in ("srp_sparse4_kernel", "verify_kernel", "verify_resume_kernel", "emit_warp_kernel (count pass)",
+              "emit_warp_kernel (write pass)", "digit_scatter_kernel", "compact_write", "lite_queue_kernel"):
+        assert work[k][1] == "B" and work[k][0] > 0
+    # the resume kernel reads the chunks of the open pairs only; the capped
+    # kernel at most lazy_bits / k chunks of each pair
+    capped = np.minimum(nu.astype(np.int64), 512) // 32
+    assert work["verify_kernel"][0] >= int(capped.sum()) * 8
+    # gathered bytes of the two SRP launches: every nonzero's row slice
+    nnz_rows = np.diff(objs.indptr)
+    want = int(nnz_rows.sum()) * 512 * 4 + int(nnz_rows[need].sum()) * (2048 - 512) * 4
+    assert work["srp_sparse4_kernel gathered"][0] == want
+
+
+def test_lazy_prefix_must_cover_the_banded_hashes():
+    prop = bench.Pipeline.lazy_bits.fget
+    w = dict(bench.WORKLOADS["cosine-small"])                 # 8 x 35 bands read 280 bits
+    ok = types.SimpleNamespace(w=dict(w, lazy_bits=512), kind=1, dense=False, with_lite=True)
+    assert prop(ok) == 512
+    assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=0), kind=1, dense=False, with_lite=True)) == 0
+    assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=2048), kind=1, dense=False, with_lite=True)) == 0
+    with pytest.raises(ValueError):
+        prop(types.SimpleNamespace(w=dict(w, lazy_bits=256), kind=1, dense=False, with_lite=True))
+    # no lazy hashing without the fused Lite pass, for dense rows or two-byte R
+    assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=512), kind=1, dense=False, with_lite=False)) == 0
+    assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=512), kind=1, dense=True, with_lite=True)) == 0
