@@ -249,13 +249,17 @@ __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ ind
 }
 
 // The same computation when bits is a multiple of 128: thread t owns the
-// float4 groups t, t+T, ... of each row of R (bits 4t..4t+3, 4(t+T).., ...),
-// so every load moves 16 bytes and a warp reads 512 contiguous bytes.  A
-// row's indices and values are read straight from global memory (every
-// thread of the CTA reads the same element: one broadcast L1 line), which
-// keeps no barrier in the loop; several rows of R are in flight per thread.
-// The four bits of a group form a nibble; eight lanes OR their nibbles into
-// one signature word with shuffles.
+// groups of four columns t, t+T, ... of each row of R (bits 4t..4t+3,
+// 4(t+T).., ...), so every load moves 16 bytes (float R) or 8 bytes (RT =
+// uint16_t: the two-byte codes of Section 4.3) and a warp reads 512 or 256
+// contiguous bytes.  A row's indices and values are read 32 at a time, one
+// per lane (coalesced), and reach the other lanes by shuffles; the gathers
+// of several nonzeros are issued together, so a long row is not a chain of
+// dependent loads, and no barrier is needed.  Every column keeps its sum and
+// the sum of the products' magnitudes for the error bound.  The four bits of
+// a group form a nibble; eight lanes OR their nibbles into one signature
+// word with shuffles.  A CTA takes one (row, piece of 4 V T columns) at a
+// time.
 template <int V, typename RT>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
