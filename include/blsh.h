@@ -337,7 +337,8 @@ BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *
  * and it is not counted in stop_hist) and sets need[x] = need[y] = 1 (uint8
  * [N], device, cleared by the caller).  Algorithm 2 decides every pair within
  * its h <= hash_limit hashes.  After the remaining hashes of the marked
- * objects are computed (blsh_srp_sparse_cols), blsh_verify_resume finishes
+ * objects are computed (blsh_srp_sparse_cols or blsh_srp_sparse_q16_cols
+ * with row_mask = need), blsh_verify_resume finishes
  * the BLSH_NEEDS_HASHES pairs over all n_max hashes and adds their stops to
  * stop_hist (not cleared), leaving every other pair's outputs as they are.
  * Together the two calls give exactly the outputs of blsh_verify_both. */
@@ -375,7 +376,13 @@ BLSH_API int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_
  * sim: double [P], written for the pairs that survive pruning (the entries
  * of pruned and bad pairs are not written); n_used uint16 [P] or NULL.
  * Rows: indptr int64 [N+1], indices uint32 sorted ascending within a row,
- * values float or NULL. */
+ * values float or NULL.  Cosine: when the survivors outnumber half the rows,
+ * each row's Nx is formed once per call into a context-owned int64 [N]
+ * buffer, allocated (after synchronizing the stream) by the first call with
+ * a larger N that is not being captured into a graph; otherwise each
+ * survivor forms its two sums itself.  Survivors are queued (up to 2^23 per
+ * call) and spread over the warps; any beyond the queue are finished by a
+ * second pass over the statuses. */
 BLSH_API int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
                      const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
                      const int64_t *indptr, const uint32_t *indices, const float *values, uint8_t *status,
