@@ -51,6 +51,17 @@ def test_host_checks_without_device(B):
     assert lib.blsh_verify(None, None, None, 0, None, None, 0, 0, None, None, None, None, None, None) == B.EINVAL
     assert lib.blsh_compact(None, None, 0, None, 0, None, 0, None, None) == B.EINVAL
     assert lib.blsh_minhash(None, None, None, 0, 32, None, None, None, None) == B.EINVAL
+    assert lib.blsh_gaussian_codes(None, 1, 10, 128, None, None) == B.EINVAL
+    assert lib.blsh_srp_sparse_q16_cols(None, None, None, None, 0, None, 1, 128, 0, 128, None, None, None) == B.EINVAL
+    assert lib.blsh_srp_sparse_cols(None, None, None, None, 0, None, 1, 128, 0, 128, None, None, None) == B.EINVAL
+    assert lib.blsh_verify_both_capped(None, None, 128, None, 0, None, None, 0, 0, None, None, None, None, None,
+                                       None, None, None, None, None, None, None, None) == B.EINVAL
+    assert lib.blsh_verify_resume(None, None, None, 0, None, None, 0, 0, None, None, None, None, None,
+                                  None) == B.EINVAL
+    assert lib.blsh_timing_begin(None, 16) == B.EINVAL
+    n_rec = C.c_int32(-1)
+    assert lib.blsh_timing_end(None, 0, None, None, C.byref(n_rec)) == B.EINVAL
+    assert lib.blsh_launch_count(None) == -1
 
 
 def test_ctx_create_fails_cleanly_without_gpu(B):
