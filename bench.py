@@ -453,7 +453,7 @@ def kernel_work(B, pipe, w, objs, st, nu, lst, need):
         work["srp_dense_tc_persistent"] = (3 * 2 * N * w["d"] * w["bits"], "flop")
     elif w["kind"] == 1:
         es = 2 if w.get("r_format") == "q16" else 4
-        name = "srp_sparse_q16_kernel" if w.get("r_format") == "q16" else "srp_sparse4_kernel"
+        name = "srp_sparse4_kernel (two-byte codes)" if w.get("r_format") == "q16" else "srp_sparse4_kernel"
         b = csr_rows_bytes(objs.indptr, objs.indices, None, lazy or w["bits"], es)
         rows_nnz = np.diff(objs.indptr)
         gathered = int(rows_nnz.sum()) * (lazy or w["bits"]) * es
