@@ -65,3 +65,44 @@ def test_lazy_prefix_must_cover_the_banded_hashes():
     # no lazy hashing without the fused Lite pass, for dense rows or two-byte R
     assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=512), kind=1, dense=False, with_lite=False)) == 0
     assert prop(types.SimpleNamespace(w=dict(w, lazy_bits=512), kind=1, dense=True, with_lite=True)) == 0
+
+
+def _recorded_names():
+    """Kernel names the library gives its timing records (the strings passed
+    to BLSH_LAUNCHED / blsh_time_stop, directly or through a name variable)."""
+    import os
+    import re
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1110_1328_gb300", "csrc")
+    names = set()
+    for f in os.listdir(root):
+        if f.endswith((".cu", ".cuh")):
+            src = open(os.path.join(root, f)).read()
+            for call in re.findall(r"(?:BLSH_LAUNCHED|blsh_time_stop)\(ctx, ([^;]*)\);", src):
+                names.update(re.findall(r'"([^"]+)"', call))
+            names.update(re.findall(r'const char \*name = [^;]*?"([^"]+)"', src))
+            names.update(re.findall(r'const char \*name = [^;]*?: "([^"]+)"', src))
+    return names
+
+
+@pytest.mark.parametrize("workload", ["cosine-small", "cosine-small-q16", "jaccard-small"])
+def test_modelled_kernels_are_the_recorded_ones(workload):
+    """Every kernel the byte model names is a name the library records, so
+    the roofline finds its bytes."""
+    w = dict(bench.WORKLOADS[workload])
+    if w["kind"] == 1:
+        w["n"] = 300
+        objs = synth.tfidf_vectors(n_docs=300, dim=3000, mean_nnz=30, n_groups=10, seed=2)
+    else:
+        w["n"] = 300
+        objs = synth.jaccard_sets(n_sets=300, vocab=2000, mean_size=20, n_groups=10, seed=2)
+    P = 1000
+    rng = np.random.default_rng(0)
+    st = rng.integers(0, 4, P).astype(np.uint8)
+    nu = (rng.integers(1, 8, P) * w["k"]).astype(np.uint16)
+    lst = rng.integers(0, 4, P).astype(np.uint8)
+    pipe = _fake_pipe(w, P, 512 if workload == "cosine-small" else 0)
+    pipe.with_lite = "lite" in w.get("stages", ("lite",))
+    work = bench.kernel_work(B, pipe, w, objs, st, nu, lst, rng.random(300) < 0.1)
+    names = _recorded_names()
+    missing = [k for k in work if not k.endswith(" gathered") and k not in names]
+    assert not missing, missing
