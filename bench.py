@@ -3,9 +3,12 @@
 
 A step is one pass of the whole verification path over one batch of
 synthetic objects, every stage in libblsh's CUDA kernels:
-  sign random projections of the sparse rows -> LSH banding candidates ->
-  Algorithm 1 (BayesLSH) over every candidate -> Algorithm 2 (Lite) over every
-  candidate -> compaction of both output sets.
+  sign random projections of the sparse rows (the first 512 bits of every
+  object; Section 3's lazy hashing) -> LSH banding candidates ->
+  Algorithms 1 (BayesLSH) and 2 (Lite) over every candidate in one pass,
+  Algorithm 1 stopping at the computed hashes -> the remaining hashes of the
+  objects of the pairs still open -> Algorithm 1 finished for those pairs ->
+  compaction of both output sets.
 The inference tables (Section 4.3) are built once per parameter set before the
 timed region (their build time is reported separately).
 
@@ -20,6 +23,12 @@ objects copied from pinned host memory and the output sets copied back inside
 the timed region.
 
   python bench.py [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+                  [--lazy-bits L] [--profile-step] [--no-graph] [--no-cpu-baseline]
+
+Other workloads: jaccard-small, batching (1M Chung-Lu sets), precision (1M
+dense points, tensor-core projection), cosine-small-q16 (two-byte R),
+verify-large (Algorithm 1 alone at HBM scale), large-mixed (5e6 vectors over
+2^24 terms, R generated on the device), sweep (the gamma/delta/eps study).
 """
 from __future__ import annotations
 
