@@ -3,8 +3,8 @@
 
 A step is one pass of the whole verification path over one batch of
 synthetic objects, every stage in libblsh's CUDA kernels:
-  sign random projections of the sparse rows (the first 512 bits of every
-  object; Section 3's lazy hashing) -> LSH banding candidates ->
+  sign random projections of the sparse rows (the first lazy_bits bits of
+  every object; Section 3's lazy hashing) -> LSH banding candidates ->
   Algorithms 1 (BayesLSH) and 2 (Lite) over every candidate in one pass,
   Algorithm 1 stopping at the computed hashes -> the remaining hashes of the
   objects of the pairs still open -> Algorithm 1 finished for those pairs ->
@@ -12,23 +12,29 @@ synthetic objects, every stage in libblsh's CUDA kernels:
 The inference tables (Section 4.3) are built once per parameter set before the
 timed region (their build time is reported separately).
 
-Default workload (cosine-small): 20,000 tf-idf-like sparse float32 vectors,
-dimension 100,000, Zipf(1.1) term ids, lognormal nnz with mean 80, 200 planted
-near-duplicate groups; 2,048 SRP bits; banding 8 bits x 35 bands; t = 0.7,
-eps = 0.03, delta = 0.05, gamma = 0.03, k = 32, Lite h = 128.
+Default workload (large-mixed): 5,000,000 tf-idf-like sparse float32 vectors
+over a 2^24-term vocabulary (Zipf(1.1) term ids, power-law lengths on
+[5, 20,000], 100,000 planted near-duplicate groups; drawn on the GPU), 2,048
+SRP bits over a projection matrix stored as two-byte Gaussian codes generated
+on the device (68.7 GB), banding 16 bits x 5 bands (about 1e9 candidates),
+t = 0.6, eps = 0.03, delta = 0.05, gamma = 0.03, k = 32, Lite h = 128, the
+first 512 bits hashed for every object; candidates verified in device-resident
+batches sized by free HBM (--batch-pairs caps them).
 
 Output: one JSON line (rank 0).  `value` is candidate pairs verified per
 second for the whole job; `e2e` the same through the public API with the
 objects copied from pinned host memory and the output sets copied back inside
-the timed region.
+the timed region; `cpu_baseline` the oracle on the host cores on a seeded
+sample, extrapolated to the whole step.
 
   python bench.py [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
-                  [--lazy-bits L] [--profile-step] [--no-graph] [--no-cpu-baseline]
+                  [--lazy-bits L] [--batch-pairs B] [--profile-step] [--no-graph] [--no-cpu-baseline]
 
-Other workloads: jaccard-small, batching (1M Chung-Lu sets), precision (1M
-dense points, tensor-core projection), cosine-small-q16 (two-byte R),
-verify-large (Algorithm 1 alone at HBM scale), large-mixed (5e6 vectors over
-2^24 terms, R generated on the device), sweep (the gamma/delta/eps study).
+Other workloads: cosine-small (20,000 tf-idf vectors, dim 100,000), jaccard-small,
+batching (1M Chung-Lu sets), precision (1M dense points, tensor-core
+projection), cosine-small-q16 (two-byte R), verify-large (Algorithm 1 alone at
+HBM scale), sweep (the gamma/delta/eps study), and the small *-profile shapes
+for ncu captures.
 """
 from __future__ import annotations
 
@@ -70,7 +76,7 @@ WORKLOADS = {
                          seed=9, text="verification only: 5,000,000 random 2,048-bit signatures (1.3 GB) and "
                                       "200,000,000 uniform random candidate pairs (HBM-resident, no reuse)"),
     "large-mixed": dict(kind=1, gpu_only=True, n=5_000_000, dim=1 << 24, bits=2048, rows=16, bands=5, t=0.6,
-                        n_max=2048, k=32, h=128, seed=9, r_seed=31,
+                        n_max=2048, k=32, h=128, seed=9, r_seed=31, lazy_bits=512,
                         text="cosine, BayesLSH + Lite on N=5,000,000 tf-idf sparse float32 vectors over a 2^24-term "
                              "vocabulary (Zipf(1.1) ranks, power-law lengths l^-2 on [5, 20,000], 100,000 planted "
                              "near-duplicate groups; drawn on the GPU), 2,048 SRP bits over R as two-byte Gaussian "
@@ -142,6 +148,7 @@ class Pipeline:
         self.kind = w["kind"]
         N = objs.n
         self.N = N
+        B.blsh_ctx_reserve(self.ctx, N)          # the hot calls allocate nothing
         u32 = lambda a: t.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(device)
         self.indptr = t.from_numpy(objs.indptr).to(device)
         self.indices = u32(objs.indices) if objs.indices.size else t.zeros(1, dtype=t.int32, device=device)
@@ -870,6 +877,7 @@ def run_verify_large(args, w):
     g = torch.Generator(device=dev)
     g.manual_seed(w["seed"])
     N, W, P = w["n"], w["bits"] // 32, w["pairs"]
+    B.blsh_ctx_reserve(ctx, N)
     sig = torch.randint(-2 ** 31, 2 ** 31 - 1, (N, W), dtype=torch.int32, device=dev, generator=g)
     x = torch.randint(0, N, (P,), dtype=torch.int64, device=dev, generator=g)
     y = torch.randint(0, N, (P,), dtype=torch.int64, device=dev, generator=g)
@@ -941,72 +949,152 @@ def run_verify_large(args, w):
 
 class LargePipeline:
     """The 5e6-vector mixed workload: inputs drawn on the GPU, R generated on
-    the device as two-byte codes, one step = hash, band, Algorithms 1 and 2
-    over the candidates in batches sized by free HBM, compaction."""
+    the device as two-byte codes (68.7 GB).  One step: the first lazy_bits
+    hashes of every object, banding, then for every batch of candidates
+    (sized by free HBM, or capped) Algorithms 1 and 2 over those hashes, the
+    remaining hashes of the objects of the pairs still open, Algorithm 1
+    finished for those pairs, and the compaction of both output sets into
+    the batch's segment of the global output arrays (indices relative to the
+    batch's first pair)."""
 
-    def __init__(self, B, torch, w, device):
+    def __init__(self, B, torch, w, device, batch_cap=None):
         import synth
-        self.B, self.w, self.dev = B, w, device
+        self.B, self.torch, self.w, self.dev = B, torch, w, device
+        t = torch
         self.ctx = B.Context(device.index or 0)
         self.indptr, self.indices, self.values = synth.large_tfidf_device(n_docs=w["n"], dim=w["dim"],
                                                                           seed=w["seed"], device=device)
         torch.cuda.synchronize()
-        self.N, self.W = w["n"], w["bits"] // 32
+        self.N, self.W, self.bits = w["n"], w["bits"] // 32, w["bits"]
+        self.nnz = int(self.indptr[-1].item())
+        B.blsh_ctx_reserve(self.ctx, self.N)           # the hot calls below allocate nothing
         self.Rq = B.blsh_gaussian_codes(self.ctx, w["r_seed"], w["dim"], w["bits"])
-        self.sig = torch.zeros((self.N, self.W), dtype=torch.int32, device=device)
+        self.sig = t.zeros((self.N, self.W), dtype=t.int32, device=device)
+        self.need = t.zeros(self.N, dtype=t.uint8, device=device)
         self.tab = B.blsh_tables_build(self.ctx, B.make_params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"],
                                                                h=w["h"]))
-        self.ws = torch.zeros(B.blsh_lsh_candidates_workspace(self.N, 1, w["rows"], w["bands"]), dtype=torch.uint8,
-                              device=device)
-        self.n_pairs = torch.zeros(1, dtype=torch.int64, device=device)
+        self.ws = t.zeros(B.blsh_lsh_candidates_workspace(self.N, 1, w["rows"], w["bands"]), dtype=t.uint8,
+                          device=device)
+        self.n_pairs = t.zeros(1, dtype=t.int64, device=device)
         self.hash()
         B.blsh_lsh_candidates(self.ctx, self.sig, 1, w["rows"], w["bands"], None, self.n_pairs, self.ws)
-        B.blsh_status(self.ctx)
+        if B.blsh_status(self.ctx) != 0:
+            raise RuntimeError("candidate count pass failed")
         self.P = int(self.n_pairs.item())
         if self.P > 4_000_000_000:
             raise RuntimeError(f"{self.P} candidates: more than this workload's pair buffer is sized for")
-        self.pairs = torch.zeros((self.P + 1024, 2), dtype=torch.int32, device=device)
-        # per pair of a batch: status, n_used, m, est, Lite status, sim (18 B) and two compaction indices
-        free, _ = torch.cuda.mem_get_info(device)
+        self.pairs = t.zeros((self.P + 1024, 2), dtype=t.int32, device=device)
+        # the output sets: each batch writes its kept indices into its own
+        # segment [b0, b0 + n) of these
+        self.out1 = t.zeros(max(self.P, 1), dtype=t.int64, device=device)
+        self.out2 = t.zeros(max(self.P, 1), dtype=t.int64, device=device)
+        self.set_batch(batch_cap)
+        self.keep1 = (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX)
+        self.keep2 = 1 << B.LITE_ACCEPT
+        self.band()
+        if B.blsh_status(self.ctx) != 0:
+            raise RuntimeError("banding failed")
+        # the verification plan, tuned on a prefix of the real candidates
+        n_t = min(self.P, 20_000_000, self.batch)
+        self.plan = B.blsh_autotune(self.ctx, self.tab, self.pairs[:n_t], self.sig, self.status[:n_t],
+                                    self.n_used[:n_t], self.m[:n_t], self.est[:n_t])
+        if B.blsh_status(self.ctx) != 0:
+            raise RuntimeError("autotune failed")
+
+    def set_batch(self, batch_cap=None):
+        """Sizes the per-batch buffers: as many pairs per batch as free HBM
+        allows (4 GB kept free), at most batch_cap."""
+        from paper_1110_1328_gb300.batches import batch_ranges
+        t, device = self.torch, self.dev
+        for name in ("status", "n_used", "m", "est", "lstatus", "sim"):
+            setattr(self, name, None)
+        t.cuda.empty_cache()
+        # per pair of a batch: status, n_used, m, est, Lite status, sim (18 B)
+        free, _ = t.cuda.mem_get_info(device)
         per_pair = 1 + 2 + 2 + 4 + 1 + 8
-        self.batch = int(max(1 << 20, min(self.P, (free - (4 << 30)) // (2 * per_pair + 16))))
-        bsz = min(self.batch, self.P)
-        self.status = torch.zeros(bsz, dtype=torch.uint8, device=device)
-        self.n_used = torch.zeros(bsz, dtype=torch.int16, device=device)
-        self.m = torch.zeros(bsz, dtype=torch.int16, device=device)
-        self.est = torch.zeros(bsz, dtype=torch.float32, device=device)
-        self.lstatus = torch.zeros(bsz, dtype=torch.uint8, device=device)
-        self.sim = torch.zeros(bsz, dtype=torch.float64, device=device)
-        self.hist = torch.zeros(self.tab.levels, dtype=torch.int64, device=device)
-        self.hist_total = torch.zeros(self.tab.levels, dtype=torch.int64, device=device)
-        self.out1 = torch.zeros(bsz, dtype=torch.int64, device=device)
-        self.out2 = torch.zeros(bsz, dtype=torch.int64, device=device)
-        self.n_out = torch.zeros(2, dtype=torch.int64, device=device)
-        self.kept = torch.zeros(2, dtype=torch.int64, device=device)
+        batch = int(max(1 << 20, (free - (4 << 30)) // per_pair))
+        if batch_cap:
+            batch = min(batch, int(batch_cap))
+        self.batch = max(1, min(batch, self.P))
+        self.ranges = batch_ranges(self.P, self.batch)
+        bsz = self.batch
+        self.status = t.zeros(bsz, dtype=t.uint8, device=device)
+        self.n_used = t.zeros(bsz, dtype=t.int16, device=device)
+        self.m = t.zeros(bsz, dtype=t.int16, device=device)
+        self.est = t.zeros(bsz, dtype=t.float32, device=device)
+        self.lstatus = t.zeros(bsz, dtype=t.uint8, device=device)
+        self.sim = t.zeros(bsz, dtype=t.float64, device=device)
+        self.hist = t.zeros((len(self.ranges), self.tab.levels), dtype=t.int64, device=device)
+        self.n_out = t.zeros((len(self.ranges), 2), dtype=t.int64, device=device)
+
+    @property
+    def lazy_bits(self):
+        """Hashes computed for every object before verification (Section 3:
+        the rest only for the objects of the pairs still undecided); 0 = all."""
+        L = self.w.get("lazy_bits", 0)
+        if 0 < L < max(self.w["rows"] * self.w["bands"], self.w["h"]):
+            raise ValueError(f"lazy_bits={L} leaves hashes that banding or Lite read")
+        return L if 0 < L < self.bits else 0
 
     def hash(self):
-        self.B.blsh_srp_sparse_q16(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig)
+        L = self.lazy_bits
+        if L:
+            self.B.blsh_srp_sparse_q16_cols(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig, 0, L)
+        else:
+            self.B.blsh_srp_sparse_q16(self.ctx, self.indptr, self.indices, self.values, self.Rq, self.sig)
 
     def band(self):
         w = self.w
         self.B.blsh_lsh_candidates(self.ctx, self.sig, 1, w["rows"], w["bands"], self.pairs, self.n_pairs, self.ws)
 
+    def verify_batch(self, b, b0, n, P_dev=None):
+        """Algorithms 1 and 2 and the two compactions for pairs [b0, b0 + n)."""
+        B, ctx, tab = self.B, self.ctx, self.tab
+        pairs = self.pairs[b0:b0 + n]
+        st, nu, m, est = self.status[:n], self.n_used[:n], self.m[:n], self.est[:n]
+        lst, sim, hist = self.lstatus[:n], self.sim[:n], self.hist[b]
+        L = self.lazy_bits
+        if L:
+            self.need.zero_()
+            B.blsh_verify_both_capped(ctx, tab, L, pairs, self.sig, st, nu, m, est, hist, self.indptr, self.indices,
+                                      self.values, lst, sim, self.need, P_dev=P_dev)
+            B.blsh_srp_sparse_q16_cols(ctx, self.indptr, self.indices, self.values, self.Rq, self.sig, L,
+                                       self.bits - L, row_mask=self.need)
+            B.blsh_verify_resume(ctx, tab, pairs, self.sig, st, nu, m, est, hist, P_dev=P_dev)
+        else:
+            B.blsh_verify_both(ctx, tab, pairs, self.sig, st, nu, m, est, hist, self.indptr, self.indices,
+                               self.values, lst, sim, P_dev=P_dev)
+        B.blsh_compact(ctx, st, self.keep1, self.out1[b0:b0 + n], self.n_out[b, 0:1], P_dev=P_dev)
+        B.blsh_compact(ctx, lst, self.keep2, self.out2[b0:b0 + n], self.n_out[b, 1:2], P_dev=P_dev)
+
     def verify(self):
-        """Algorithms 1 and 2 and the compaction of each batch of pairs (the
-        kept pairs' indices of a batch are counted into `kept`)."""
-        B = self.B
-        self.hist_total.zero_()
-        self.kept.zero_()
-        for b0 in range(0, self.P, self.batch):
-            n = min(self.batch, self.P - b0)
-            B.blsh_verify_both(self.ctx, self.tab, self.pairs[b0:b0 + n], self.sig, self.status[:n],
-                               self.n_used[:n], self.m[:n], self.est[:n], self.hist, self.indptr, self.indices,
-                               self.values, self.lstatus[:n], self.sim[:n])
-            self.hist_total += self.hist
-            B.blsh_compact(self.ctx, self.status[:n], (1 << B.ACCEPT) | (1 << B.ACCEPT_AT_MAX), self.out1[:n],
-                           self.n_out[0:1])
-            B.blsh_compact(self.ctx, self.lstatus[:n], 1 << B.LITE_ACCEPT, self.out2[:n], self.n_out[1:2])
-            self.kept += self.n_out
+        # one batch: the candidate count is read on the device (no host sync
+        # between banding and verification); several: fixed host ranges
+        single = len(self.ranges) == 1
+        for b, (b0, n) in enumerate(self.ranges):
+            self.verify_batch(b, b0, n, P_dev=self.n_pairs if single else None)
+
+    def verify_streamed(self, checkpoint=None, on_batch=None):
+        """The verification stage batch by batch, eagerly, with the host-side
+        record of progress saved after every batch (an interrupted job
+        resumes at its first unfinished batch).  on_batch(b, b0, n), if
+        given, runs after batch b's calls (its outputs are then on the
+        device)."""
+        from paper_1110_1328_gb300.batches import stream_batches
+        w = self.w
+        job = {"workload": "large-mixed", "n": self.N, "seed": w["seed"], "r_seed": w["r_seed"], "P": self.P,
+               "batch": self.batch, "lazy_bits": self.lazy_bits}
+
+        def run(b, b0, n):
+            self.verify_batch(b, b0, n)
+            if on_batch is not None:
+                on_batch(b, b0, n)
+            rc = self.B.blsh_status(self.ctx)
+            if rc != 0:
+                raise RuntimeError(f"batch {b} failed with {rc}")
+            return [int(x) for x in self.n_out[b].cpu()], [int(x) for x in self.hist[b].cpu()]
+
+        return stream_batches(self.P, self.batch, run, job, checkpoint, 2, self.tab.levels)
 
     STAGES = ("hash", "band", "verify")
 
@@ -1014,17 +1102,114 @@ class LargePipeline:
         for s_ in self.STAGES:
             getattr(self, s_)()
 
+    def kept_counts(self):
+        return [int(x) for x in self.n_out.sum(0).cpu()]
+
+    def kept_indices(self):
+        """The two output sets as global pair indices (host arrays)."""
+        counts = self.n_out.cpu().numpy()
+        o1, o2 = [], []
+        for (b0, n), (c1, c2) in zip(self.ranges, counts):
+            o1.append(self.out1[b0:b0 + int(c1)].cpu().numpy() + b0)
+            o2.append(self.out2[b0:b0 + int(c2)].cpu().numpy() + b0)
+        return np.concatenate(o1) if o1 else np.zeros(0, np.int64), np.concatenate(o2) if o2 else np.zeros(0, np.int64)
+
+
+def large_kernel_work(pipe):
+    """Algorithmic bytes of one large-mixed step per kernel name (each launch
+    counted for what it must read and write at least once; L2 re-reads not
+    counted), from the last step's outputs (exact with one batch; with
+    several, the last batch's figures scaled to all pairs)."""
+    torch, B, w = pipe.torch, pipe.B, pipe.w
+    k, bits, L = w["k"], pipe.bits, pipe.lazy_bits
+    P, N, nnz = pipe.P, pipe.N, pipe.nnz
+    n_last = pipe.ranges[-1][1] if pipe.ranges else 0
+    scale = P / max(n_last, 1)
+    st = pipe.status[:n_last]
+    nu = pipe.n_used[:n_last].to(torch.int64) & 0xFFFF
+    lst = pipe.lstatus[:n_last]
+    work = {}
+    kept = (st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)
+    chunks = nu // k
+    per_chunk = k // 4
+    if L:
+        Lk = L // k
+        resumed = nu > L
+        capped = torch.clamp(chunks, max=Lk)
+        work["verify_kernel"] = (scale * (n_last * 14 + 4 * int((kept & ~resumed).sum())
+                                          + int(capped.sum()) * per_chunk), "B")
+        r = int(resumed.sum())
+        work["verify_resume_kernel"] = (scale * (n_last + r * 13 + 4 * int((kept & resumed).sum())
+                                                 + int(chunks[resumed].sum()) * per_chunk), "B")
+    else:
+        work["verify_kernel"] = (scale * (n_last * 14 + 4 * int(kept.sum()) + int(chunks.sum()) * per_chunk), "B")
+    # the projection: per nonzero its index and value, per row its indptr
+    # pair and the signature bytes written, each distinct code row once
+    row_len = pipe.indptr[1:] - pipe.indptr[:-1]
+    distinct = int(torch.unique(pipe.indices).numel())
+    cols = L or bits
+    b_proj = nnz * 8 + N * (16 + cols // 8) + distinct * cols * 2
+    gathered = nnz * cols * 2
+    if L:
+        sel = pipe.need.bool()
+        n_sel = int(sel.sum())
+        nnz_sel = int(row_len[sel].sum())
+        rows_of = torch.repeat_interleave(sel, row_len)
+        d_sel = int(torch.unique(pipe.indices[rows_of]).numel()) if n_sel else 0
+        del rows_of
+        b_proj += nnz_sel * 8 + n_sel * (16 + (bits - L) // 8) + d_sel * (bits - L) * 2
+        gathered += nnz_sel * (bits - L) * 2
+    name = "srp_sparse4_kernel (two-byte codes)"
+    work[name] = (b_proj, "B")
+    work[name + " gathered"] = (gathered, "B")
+    # Lite's exact pass over the survivors
+    surv = (lst == B.LITE_ACCEPT) | (lst == B.LITE_REJECT)
+    ns = int(surv.sum())
+    b0_last = pipe.ranges[-1][0] if pipe.ranges else 0
+    pr = pipe.pairs[b0_last:b0_last + n_last][surv].to(torch.int64) if ns else None
+    surv_nnz = int((row_len[pr[:, 0]] + row_len[pr[:, 1]]).sum()) if ns else 0
+    work["lite_collect_kernel"] = (scale * (n_last + 8 * ns), "B")
+    work["lite_queue_kernel"] = (scale * (ns * (8 + 16 + 16 + 9) + surv_nnz * 8), "B")
+    work["row_norm2_kernel"] = (nnz * 4 + N * 8, "B")
+    # banding (cosine: packed band keys, LSD radix passes, emission)
+    rows, bands = w["rows"], w["bands"]
+    n = N * bands
+    kb = 4 if max(1, (bands - 1).bit_length()) + rows <= 32 else 8
+    obj_rows = N * bands * ((rows + 7) // 8)
+    passes = (max(1, (bands - 1).bit_length()) + rows + 7) // 8
+    work["band_keys_kernel"] = (N * bands * rows // 8 + n * (kb + 4) + obj_rows, "B")
+    work["digit_hist_kernel"] = (passes * n * kb, "B")
+    work["digit_scatter_kernel"] = (passes * 2 * n * (kb + 4), "B")
+    work["emit_warp_kernel (count pass)"] = (n * (kb + 4) + obj_rows + n * 8, "B")
+    work["emit_warp_kernel (write pass)"] = (n * (kb + 4 + 8) + obj_rows + P * 8, "B")
+    n_keep = scale * int(kept.sum()) + scale * int((lst == B.LITE_ACCEPT).sum())
+    work["compact_count"] = (2 * P, "B")
+    work["compact_write"] = (2 * P + 8 * n_keep, "B")
+    return {key: (int(v), u) for key, (v, u) in work.items()}
+
 
 def run_large(args, w):
-    """The 5e6-vector mixed workload (one GPU): K timed steps of hash, band,
-    batched verification and compaction."""
+    """The 5e6-vector mixed workload (one GPU): K timed replays of one
+    captured step (hash, band, batched verification and compaction), the
+    per-kernel breakdown of eager steps, the end-to-end time through the
+    API with host buffers, and the oracle's extrapolated throughput."""
     import torch
 
     import paper_1110_1328_gb300 as B
-    dev = torch.device("cuda", 0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     B.lib()
+    if world > 1:      # replicas: each rank its own batch of objects
+        w = dict(w, seed=w["seed"] + 1000 * rank)
     t0 = time.perf_counter()
-    pipe = LargePipeline(B, torch, w, dev)
+    pipe = LargePipeline(B, torch, w, dev, batch_cap=args.batch_pairs)
     setup_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -1033,63 +1218,397 @@ def run_large(args, w):
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("warm-up step failed")
     launches0 = B.blsh_launch_count(pipe.ctx)
-    clocks = ClockSampler(0)
+    pipe.step()
+    launches_per_step = B.blsh_launch_count(pipe.ctx) - launches0
+    torch.cuda.synchronize()
+
+    # one step captured in a CUDA graph (no host sync inside)
+    graph = None
+    if not args.no_graph:
+        try:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                pipe.step()
+            stream.wait_stream(s)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                pipe.step()
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            graph = g
+        except Exception as e:   # capture is an optimisation; eager launches do the same work
+            print(f"graph capture failed, timing eager launches: {e}", file=sys.stderr)
+            graph = None
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("graph step failed")
+
+    def one_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            pipe.step()
+
+    # ---- device-timed steps ----
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ts = []
+    wall0 = time.perf_counter()
     for i in range(args.steps):
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pipe.step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        flush.fill_(float(i))            # L2 flush between timed steps (256 MB write)
+        starts[i].record(stream)
+        one_step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
-    launches = B.blsh_launch_count(pipe.ctx) - launches0
     rc, ctr = B.blsh_status(pipe.ctx, counters=True)
     if rc != 0:
-        raise RuntimeError("timed steps failed")
-    ms = float(np.mean(ts))
-    # per-stage and per-kernel device times of one more eager step
+        raise RuntimeError(f"timed steps reported {rc}")
+    my_ms = float(np.mean([s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]))
+    kept = pipe.kept_counts()
+    hist = pipe.hist.sum(0).cpu().numpy()
+
+    # ---- per-stage and per-kernel device times of eager steps ----
+    reps = 2
     B.blsh_timing_begin(pipe.ctx, 8192)
-    stage = {}
-    for s_ in pipe.STAGES:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        getattr(pipe, s_)()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        stage[s_] = round(e0.elapsed_time(e1), 3)
+    stage = {s_: 0.0 for s_ in pipe.STAGES}
+    for i in range(reps):
+        flush.fill_(float(i))
+        for s_ in pipe.STAGES:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            getattr(pipe, s_)()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            stage[s_] += e0.elapsed_time(e1) / reps
     kern = {}
     for name, t_ms in B.blsh_timing_end(pipe.ctx, 8192):
-        k = kern.setdefault(name, [0, 0.0])
-        k[0] += 1
-        k[1] += t_ms
-    kern = {n: {"launches": c, "ms": round(t, 3)} for n, (c, t) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+        k_ = kern.setdefault(name, [0, 0.0])
+        k_[0] += 1
+        k_[1] += t_ms
+    kern = {n: [c / reps, t_ / reps] for n, (c, t_) in kern.items()}
     if args.profile_step:
-        # one more eager step inside an NVTX range, for ncu --nvtx-include "blsh_step/"
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("blsh_step")
         pipe.step()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-    nnz = int(pipe.indptr[-1].item())
-    hist = pipe.hist_total.cpu().numpy()
-    kept = [int(x) for x in pipe.kept.cpu()]
-    print(json.dumps({"metric": METRIC, "value": round(pipe.P / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-                      "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-                      "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "nnz": nnz,
-                                 "candidate_pairs": pipe.P, "batch_pairs": pipe.batch,
-                                 "batches": -(-pipe.P // pipe.batch), "setup_s": round(setup_s, 1),
-                                 "l2": "flushed between timed steps (256 MB write)", "cuda_graph": False},
-                      "gpu_launches": int(launches), "stage_ms": stage, "kernels": kern,
-                      "hashes_per_s": round(pipe.N * w["bits"] / (stage["hash"] / 1e3), 1),
-                      "srp_signs": {"rechecked_per_step": ctr[2] / args.steps, "zero_dots_per_step": ctr[3] / args.steps},
-                      "outputs": {"bayeslsh_kept": kept[0], "lite_kept": kept[1],
-                                  "stop_hist_first4": [int(v) for v in hist[:4]]},
-                      "clocks": clk}), flush=True)
+
+    # ---- end to end through the public API, host buffers ----
+    pin = lambda x: x.cpu().pin_memory()
+    h_indptr, h_indices, h_values = pin(pipe.indptr), pin(pipe.indices), pin(pipe.values)
+    nb = len(pipe.ranges)
+    h_counts = torch.zeros((nb, 2), dtype=torch.int64).pin_memory()
+    h_out1 = torch.zeros(kept[0] + 1024, dtype=torch.int64).pin_memory()
+    h_out2 = torch.zeros(kept[1] + 1024, dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    h2d = h_indptr.numel() * 8 + h_indices.numel() * 4 + h_values.numel() * 4
+    d2h = 0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipe.indptr.copy_(h_indptr, non_blocking=True)
+        pipe.indices.copy_(h_indices, non_blocking=True)
+        pipe.values.copy_(h_values, non_blocking=True)
+        one_step()
+        h_counts.copy_(pipe.n_out, non_blocking=True)
+        stream.synchronize()
+        o1 = o2 = 0
+        for (b0, _), (c1, c2) in zip(pipe.ranges, h_counts.tolist()):
+            c1, c2 = min(int(c1), h_out1.numel() - o1), min(int(c2), h_out2.numel() - o2)
+            if c1:
+                h_out1[o1:o1 + c1].copy_(pipe.out1[b0:b0 + c1], non_blocking=True)
+            if c2:
+                h_out2[o2:o2 + c2].copy_(pipe.out2[b0:b0 + c2], non_blocking=True)
+            o1, o2 = o1 + c1, o2 + c2
+        stream.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        d2h = 16 * nb + 8 * (o1 + o2)
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("end-to-end steps failed")
+    e2e_step = float(np.mean(e2e_ms))
+    ms, P_total, e2e_max = combine_ranks(dist, my_ms, pipe.P, e2e_step, dev)
+    value = P_total / (ms / 1e3)
+    e2e_val = P_total / (e2e_max / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    peak, peak_kind = load_peaks()
+    work = large_kernel_work(pipe)
+    timed = {n: v for n, v in kern.items() if not n.startswith("exclusive scan")}
+    dom = max(timed, key=lambda n: timed[n][1])
+    dom_launches, dom_ms = timed[dom]
+    amount, unit = work.get(dom, (None, None))
+    ach = amount / (dom_ms / 1e3) / 1e9 if amount is not None else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": None if ach is None else round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": None if ach is None else round(ach / peak, 4),
+                "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_source": peak_kind,
+                "algorithmic_bytes": amount, "launches_per_step": dom_launches, "ms_per_step": round(dom_ms, 4),
+                "timing": "library CUDA events around each launch on its stream, eager steps"}
+    if dom + " gathered" in work:
+        gb = work[dom + " gathered"][0]
+        roofline["gathered_bytes"] = int(gb)
+        roofline["gathered_GBps"] = round(gb / (dom_ms / 1e3) / 1e9, 1)
+    kernels = {n: {"launches": c, "ms": round(t_, 4),
+                   **({"GBps": round(work[n][0] / (t_ / 1e3) / 1e9, 1)} if n in work else {})}
+               for n, (c, t_) in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    vbytes = work["verify_kernel"][0] + work.get("verify_resume_kernel", (0, "B"))[0]
+    v_ms = kern.get("verify_kernel", [0, 0.0])[1] + kern.get("verify_resume_kernel", [0, 0.0])[1]
+    v_ach = vbytes / (v_ms / 1e3) / 1e9 if v_ms else 0.0
+    L = pipe.lazy_bits
+    need_rows = int(pipe.need.sum().item()) if L else 0
+    hashes = pipe.N * (L or pipe.bits) + need_rows * (pipe.bits - L if L else 0)
+    hash_ms = kern.get("srp_sparse4_kernel (two-byte codes)", [0, 0.0])[1] + kern.get("srp_recheck_kernel", [0, 0.0])[1]
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "nnz": pipe.nnz,
+                   "candidate_pairs": pipe.P, "batch_pairs": pipe.batch, "batches": nb,
+                   "setup_s": round(setup_s, 1), "l2": "flushed between timed steps (256 MB write); the 68.7 GB "
+                   "of codes and 1.3 GB of signatures exceed L2", "cuda_graph": graph is not None,
+                   "plan": dict(pipe.plan.as_dict(), k=w["k"]), "lazy_bits": L,
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "e2e": {"value": round(e2e_val, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "verify_hbm": {"achieved": round(v_ach, 1), "peak": peak, "unit": "GB/s", "frac": round(v_ach / peak, 4),
+                       "algorithmic_bytes": int(vbytes), "ms": round(v_ms, 4),
+                       "kernels": "verify_kernel" + (" + verify_resume_kernel" if L else "")},
+        "kernels": kernels,
+        "hashes_per_s": round(hashes / (hash_ms / 1e3), 1) if hash_ms else None,
+        "hashes_per_step": int(hashes),
+        "stage_ms": {k_: round(v, 4) for k_, v in stage.items()},
+        "outputs": {"bayeslsh_kept": kept[0], "lite_kept": kept[1], "objects_hashed_in_full": need_rows,
+                    "stop_hist_first4": [int(v) for v in hist[:4]]},
+        "clocks": clk,
+        "wall_s_timed_loop": round(wall, 3),
+        "srp_signs": {"rechecked_per_step": ctr[2] / args.steps, "zero_dots_per_step": ctr[3] / args.steps},
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = large_cpu_baseline(pipe, w, seed=1)
+    elif rank == 0 and world > 1:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_codes(O, seed, terms, bits, threads=1):
+    """The oracle's own two-byte codes for the given rows of R (its generator,
+    from the same counter definition as the library's)."""
+    import concurrent.futures as cf
+    out = np.zeros((len(terms), bits), np.uint16)
+
+    def fill(lo, hi):
+        for i in range(lo, hi):
+            out[i] = O.gaussian_codes(seed, 1, bits, row0=int(terms[i]))[0]
+
+    step = -(-len(terms) // max(threads, 1))
+    with cf.ThreadPoolExecutor(max(threads, 1)) as ex:
+        list(ex.map(lambda lo: fill(lo, min(lo + step, len(terms))), range(0, len(terms), step or 1)))
+    return out
+
+
+def large_oracle_inputs(pipe, w, seed, n_pairs=20_000, n_hash=2_000, threads=1):
+    """The oracle's inputs for a seeded sample of the large workload:
+      - n_hash objects drawn uniformly (their rows copied from the device,
+        terms renumbered) with the oracle's own codes for their terms: the
+        hashing and banding sample;
+      - n_pairs candidate pairs drawn uniformly from the candidate list, their
+        objects' rows and the oracle's own signatures of them (from its own
+        codes, computed here, untimed): the verification sample."""
+    import oracle as O
+    import synth
+    torch = pipe.torch
+    rng = np.random.default_rng(seed)
+
+    def rows_of(ids):
+        ids_t = torch.from_numpy(ids.astype(np.int64)).to(pipe.dev)
+        lo, hi = pipe.indptr[ids_t].cpu().numpy(), pipe.indptr[ids_t + 1].cpu().numpy()
+        sel = np.concatenate([np.arange(a, b) for a, b in zip(lo, hi)]) if len(ids) else np.zeros(0, np.int64)
+        sel_t = torch.from_numpy(sel).to(pipe.dev)
+        terms = pipe.indices[sel_t].cpu().numpy().view(np.uint32)
+        vals = pipe.values[sel_t].cpu().numpy()
+        uterm, tinv = np.unique(terms, return_inverse=True)
+        csr = synth.CSR(np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64), tinv.astype(np.uint32), vals,
+                        len(uterm))
+        return csr, oracle_codes(O, w["r_seed"], uterm, w["bits"], threads)
+
+    hash_ids = np.sort(rng.choice(pipe.N, min(n_hash, pipe.N), replace=False))
+    hash_csr, hash_codes = rows_of(hash_ids)
+    q = np.sort(rng.choice(pipe.P, min(n_pairs, pipe.P), replace=False))
+    sp = pipe.pairs[torch.from_numpy(q).to(pipe.dev)].cpu().numpy().view(np.uint32)
+    ids, inv = np.unique(sp.reshape(-1), return_inverse=True)
+    pair_csr, pair_codes = rows_of(ids)
+    sig = oracle_signatures(O, pair_csr, pair_codes, threads)
+    del pair_codes
+    return {"hash_csr": hash_csr, "hash_codes": hash_codes, "pair_csr": pair_csr, "pair_sig": sig,
+            "pairs": inv.reshape(-1, 2).astype(np.uint32)}
+
+
+def sub_csr(csr, lo, hi):
+    import synth
+    a, b = int(csr.indptr[lo]), int(csr.indptr[hi])
+    return synth.CSR(csr.indptr[lo:hi + 1] - a, csr.indices[a:b], csr.values[a:b], csr.dim)
+
+
+def oracle_signatures(O, csr, codes, threads=1):
+    """The oracle's two-byte-code signatures of all bits of every row, the
+    rows split over `threads` host threads."""
+    import concurrent.futures as cf
+    cuts = np.linspace(0, csr.n, threads + 1).astype(int)
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda i: O.srp_sparse_q16(sub_csr(csr, cuts[i], cuts[i + 1]), codes), range(threads)))
+    return np.concatenate(parts)
+
+
+def large_oracle_times(O, w, inp, threads=1, min_verify_s=1.0):
+    """Seconds the oracle takes on `threads` host threads for: the signatures
+    (all bits) of the hashing sample, the banding of those signatures (one
+    thread: the oracle's sort is sequential), and one pass of Algorithms 1
+    and 2 with both compactions over the sampled pairs (repeated until
+    min_verify_s, averaged).  Also counts the sampled pairs that do not
+    collide in any band under the oracle's own signatures (0 expected)."""
+    import concurrent.futures as cf
+    p = O.Params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"])
+    tab = O.tables(p)
+    t0 = time.perf_counter()
+    hsig = oracle_signatures(O, inp["hash_csr"], inp["hash_codes"], threads)
+    t_hash = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.lsh_candidates(hsig, 1, w["rows"], w["bands"])
+    t_band = time.perf_counter() - t0
+    lp, sig, csr = inp["pairs"], inp["pair_sig"], inp["pair_csr"]
+    r, bands = w["rows"], w["bands"]
+    band = lambda s, b: (s[:, (b * r) // 32] >> np.uint32((b * r) % 32)) & np.uint32((1 << r) - 1)
+    collide = np.zeros(len(lp), bool)
+    for b in range(bands):
+        collide |= band(sig[lp[:, 0]], b) == band(sig[lp[:, 1]], b)
+    keep1 = (1 << O.ACCEPT) | (1 << O.ACCEPT_AT_MAX)
+    cuts = np.linspace(0, len(lp), threads + 1).astype(int)
+
+    def one(i):
+        sl = lp[cuts[i]:cuts[i + 1]]
+        res = O.verify(tab, sl, sig)
+        O.compact(res.status, keep1)
+        lres = O.verify_lite(tab, sl, sig, csr)
+        O.compact(lres.status, 1 << O.LITE_ACCEPT)
+        return res
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            res = list(ex.map(one, range(threads)))
+            reps += 1
+            if time.perf_counter() - t0 >= min_verify_s:
+                break
+        t_verify = (time.perf_counter() - t0) / reps
+    return {"hash_s": t_hash, "band_s": t_band, "verify_s": t_verify, "objects": inp["hash_csr"].n,
+            "nnz": int(inp["hash_csr"].indptr[-1]), "pairs": len(lp), "not_colliding": int((~collide).sum())}
+
+
+def extrapolate(t, N, nnz, P):
+    """Seconds of one whole step over the full workload: hashing scaled by
+    the nonzeros, banding by the objects, verification by the pairs."""
+    return nnz * t["hash_s"] / max(t["nnz"], 1) + N * t["band_s"] / max(t["objects"], 1) + P * t["verify_s"] / max(
+        t["pairs"], 1)
+
+
+def large_cpu_baseline(pipe, w, seed=1):
+    """The oracle timed on the host cores on a seeded sample of the large
+    workload (its own signatures from its own codes), single-threaded and on
+    all cores, extrapolated to the whole step: candidate pairs verified per
+    second."""
+    import oracle as O
+    O.build()
+    cores = len(os.sched_getaffinity(0))
+    inp = large_oracle_inputs(pipe, w, seed, threads=cores)
+    t1 = large_oracle_times(O, w, inp, threads=1)
+    tc = large_oracle_times(O, w, inp, threads=cores)
+    T1, TC = extrapolate(t1, pipe.N, pipe.nnz, pipe.P), extrapolate(tc, pipe.N, pipe.nnz, pipe.P)
+    comp = lambda t: {"hash_s_per_1e6_nnz": round(t["hash_s"] / t["nnz"] * 1e6, 4),
+                      "band_s_per_1e6_objects": round(t["band_s"] / t["objects"] * 1e6, 4),
+                      "verify_pairs_per_s": round(t["pairs"] / t["verify_s"], 1)}
+    return {"value": round(pipe.P / T1, 1), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"seeded uniform samples of the workload: {t1['objects']} objects ({t1['nnz']} nonzeros) hashed "
+                      f"over all {w['bits']} bits and banded, {t1['pairs']} of the {pipe.P} candidate pairs through "
+                      f"Algorithms 1 and 2 and both compactions (the oracle's own signatures from its own codes); "
+                      f"hashing scaled by nonzeros, banding by objects, verification by pairs to the full step "
+                      f"({T1:.0f} s single-threaded); sampled pairs not colliding under the oracle's signatures: "
+                      f"{t1['not_colliding']}",
+            "components": comp(t1),
+            "all_cores": {"value": round(pipe.P / TC, 1), "cores": cores, "step_s": round(TC, 1),
+                          "components": comp(tc),
+                          "form": "the same oracle calls over chunks of objects (hashing) and of pairs "
+                                  "(verification) in host threads; banding single-threaded"}}
+
+
+def run_reference_large(args, w):
+    """The reference arm on the large workload: each step the single-threaded
+    oracle over a bounded sample (hashing and banding of 2,000 objects,
+    Algorithms 1 and 2 over 20,000 candidate pairs), extrapolated to the
+    whole step as in the cpu_baseline leg.  The workload and its candidate
+    list come from the GPU pipeline (inputs); the oracle checks that every
+    sampled pair collides in a band under its own signatures."""
+    import torch
+
+    import oracle as O
+    import paper_1110_1328_gb300 as B
+    O.build()
+    dev = torch.device("cuda", 0)
+    B.lib()
+    pipe = LargePipeline(B, torch, w, dev)
+    pipe.step()
+    if B.blsh_status(pipe.ctx) != 0:
+        raise RuntimeError("workload step failed")
+    cores = len(os.sched_getaffinity(0))
+    inp = large_oracle_inputs(pipe, w, seed=1, threads=cores)
+    for _ in range(args.warmup):
+        large_oracle_times(O, w, inp, threads=1, min_verify_s=0.0)
+    secs, ext = 0.0, 0.0
+    nc = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        t = large_oracle_times(O, w, inp, threads=1, min_verify_s=0.0)
+        secs += time.perf_counter() - t0
+        ext += extrapolate(t, pipe.N, pipe.nnz, pipe.P)
+        nc += t["not_colliding"]
+    value = pipe.P * args.steps / ext
+    sample = (f"each step: the single-threaded oracle over {inp['hash_csr'].n} objects (hashed over all {w['bits']} "
+              f"bits, banded) and {len(inp['pairs'])} of the {pipe.P} candidate pairs (Algorithms 1 and 2, both "
+              f"compactions), extrapolated to the whole step ({ext / args.steps:.0f} s); sampled pairs not colliding "
+              f"under the oracle's signatures: {nc // max(args.steps, 1)}")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "pairs/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload + ": " + w["text"], "extrapolated_step_s": round(ext / args.steps, 1)},
+           "cpu_baseline": {"value": round(value, 1), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 1), "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -1145,6 +1664,9 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "large-mixed":
+        run_reference_large(args, w)
+        return
     if w.get("gpu_only"):
         print(json.dumps({"impl": "reference", "unavailable": "a GPU measurement workload; "
                                                                "the oracle arm runs on the pipeline workloads"}))
@@ -1181,7 +1703,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="cosine-small", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large-mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1190,6 +1712,8 @@ def main():
     ap.add_argument("--lazy-bits", type=int, default=None,
                     help="sparse cosine: hashes computed for every object before verification (a multiple of 128; "
                          "0 = all up front); the workload's setting otherwise")
+    ap.add_argument("--batch-pairs", type=int, default=None,
+                    help="large-mixed: at most this many candidate pairs per device batch (default: sized by free HBM)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -25,8 +25,9 @@
  *     Errors the GPU detects (a pair naming an object index >= N, an output
  *     larger than its capacity) are recorded in the context and returned by
  *     the next blsh_status() call.  No kernel traps or asserts.
- *   - Hot calls (hashing, banding, verify, compaction) allocate no memory;
- *     blsh_ctx_create and blsh_tables_build allocate once.
+ *   - Hot calls (hashing, banding, verify, compaction) allocate no memory
+ *     and never synchronise the stream; blsh_ctx_create, blsh_ctx_reserve
+ *     and blsh_tables_build allocate (and synchronise) once, at set-up.
  *   - Calls that share a context must not overlap in time on different
  *     streams: the context owns a small scratch area (work counters, the
  *     device error word) that every call reuses.
@@ -116,6 +117,21 @@ BLSH_API const char *blsh_strerror(int code);
  * not sm_103. */
 BLSH_API int blsh_ctx_create(blsh_ctx **out, int device);
 BLSH_API int blsh_ctx_destroy(blsh_ctx *ctx);
+
+/* Reserves the context's per-object buffers for signature sets of up to
+ * max_objects rows, so that the hot calls need no allocation: the
+ * first-words plane of the verification calls (8 bytes per object; words 0
+ * and 1 of every cosine signature row, Algorithm 1's first step) and Lite's
+ * squared-norm buffer (8 bytes per object; Algorithm 2's exact cosine).  A
+ * set-up call: it synchronises the device, frees the previous buffers and
+ * allocates the new ones (it never shrinks them; 0 releases them).  A
+ * verification call over more objects than were reserved takes the slower
+ * route with the same outputs (rows read directly, norms formed per pair).
+ * BLSH_EINVAL for max_objects outside 0..2^32, BLSH_ENOMEM if the
+ * allocation fails.  blsh_ctx_reserved returns the reservation (-1 for a
+ * NULL context). */
+BLSH_API int blsh_ctx_reserve(blsh_ctx *ctx, int64_t max_objects);
+BLSH_API int64_t blsh_ctx_reserved(const blsh_ctx *ctx);
 
 /* Text of the last host-side error on this context (static storage owned by
  * the context, valid until the next call). */
@@ -318,13 +334,13 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
  * reads the count there (clamped to P, which acts as the capacity), so the
  * call can follow a producer on the same stream without a host sync.
  * Uses the plan blsh_autotune stored for these tables, else a default.
- * Cosine signature sets larger than 64 MB (N * sig_words * 4 bytes): the
- * call first copies words 0 and 1 of every row into a context-owned plane of
- * N uint2 that stays in L2, and every pair's first step reads them there.
- * The plane is allocated (cudaMalloc, after synchronizing the stream) by the
- * first such call with a larger N than before that is not being captured
- * into a graph; a captured call whose N exceeds it reads the rows instead.
- * This holds for every verification entry point below. */
+ * Cosine signature sets larger than 64 MB (N * sig_words * 4 bytes) with
+ * N <= blsh_ctx_reserved(ctx): the call first copies words 0 and 1 of every
+ * row into the context's plane of N uint2, which stays in L2, and every
+ * pair's first step reads them there; with N above the reservation each
+ * pair reads its rows (same outputs).  The call allocates nothing and does
+ * not synchronise, so it can be captured into a CUDA graph.  This holds for
+ * every verification entry point below. */
 BLSH_API int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const int64_t *P_dev,
                 const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used,
                 uint16_t *m, float *est, uint64_t *stop_hist, void *stream);
@@ -376,13 +392,12 @@ BLSH_API int blsh_verify_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_
  * sim: double [P], written for the pairs that survive pruning (the entries
  * of pruned and bad pairs are not written); n_used uint16 [P] or NULL.
  * Rows: indptr int64 [N+1], indices uint32 sorted ascending within a row,
- * values float or NULL.  Cosine: when the survivors outnumber half the rows,
- * each row's Nx is formed once per call into a context-owned int64 [N]
- * buffer, allocated (after synchronizing the stream) by the first call with
- * a larger N that is not being captured into a graph; otherwise each
- * survivor forms its two sums itself.  Survivors are queued (up to 2^23 per
- * call) and spread over the warps; any beyond the queue are finished by a
- * second pass over the statuses. */
+ * values float or NULL.  Cosine: when the survivors outnumber half the rows
+ * and N <= blsh_ctx_reserved(ctx), each row's Nx is formed once per call
+ * into the context's int64 [N] norm buffer; otherwise each survivor forms
+ * its two sums itself (same bits: the sums are order-independent).
+ * Survivors are queued (up to 2^23 per call) and spread over the warps; any
+ * beyond the queue are finished by a second pass over the statuses. */
 BLSH_API int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
                      const int64_t *P_dev, const uint32_t *sig, int64_t N, int32_t sig_words,
                      const int64_t *indptr, const uint32_t *indices, const float *values, uint8_t *status,
@@ -458,9 +473,18 @@ BLSH_API int blsh_compact(blsh_ctx *ctx, const uint8_t *status, int64_t P, const
  *     (16384 tiles of 4096 statuses); larger P returns BLSH_ESIZE and
  *     enqueues nothing.  BLSH_EINVAL for bad pointers or sizes,
  *     BLSH_EDEVICE for a CUDA error.
- *   - The first call on a device, made with that device current, looks up
- *     the array's device address (cudaGetSymbolAddress); make that first
- *     call before any stream capture on the device.
+ *   - The array's device address belongs to the CUDA context the library's
+ *     module is loaded into.  The first call made in each context (the
+ *     device's primary context, a context the caller created, or the new
+ *     primary context after cudaDeviceReset) looks that address up
+ *     (cudaGetSymbolAddress, with the context current) and remembers it for
+ *     the context (the last 64 contexts are remembered).  Make that first
+ *     call before any stream capture in the context: a first call made while
+ *     its stream is being captured returns BLSH_EDEVICE and enqueues
+ *     nothing.
+ *   - Launch errors are taken from each launch's own return code: an error
+ *     left on the calling thread by earlier work is neither returned by this
+ *     call nor cleared.
  *   - Every call reuses the same array, which keeps the last call's
  *     contents; each call overwrites every entry it reads, so nothing needs
  *     clearing.  Calls that overlap on the GPU (on different streams, or

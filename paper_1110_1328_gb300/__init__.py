@@ -61,6 +61,8 @@ def lib():
             "blsh_strerror": ([C.c_int], C.c_char_p),
             "blsh_ctx_create": ([p, C.c_int], C.c_int),
             "blsh_ctx_destroy": ([p], C.c_int),
+            "blsh_ctx_reserve": ([p, i64], C.c_int),
+            "blsh_ctx_reserved": ([p], C.c_int64),
             "blsh_last_error": ([p], C.c_char_p),
             "blsh_status": ([p, p, p], C.c_int),
             "blsh_launch_count": ([p], C.c_int64),
@@ -208,6 +210,16 @@ def blsh_ctx_create(device: int | None = None) -> Context:
 
 def blsh_ctx_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def blsh_ctx_reserve(ctx: Context, max_objects: int) -> None:
+    """Set-up: the context's per-object buffers (verification plane, Lite
+    norms) for up to max_objects rows, so hot calls never allocate."""
+    _check(lib().blsh_ctx_reserve(ctx.handle, int(max_objects)), ctx)
+
+
+def blsh_ctx_reserved(ctx: Context) -> int:
+    return int(lib().blsh_ctx_reserved(ctx.handle))
 
 
 def blsh_tables_destroy(tab: "Tables") -> None:

@@ -111,6 +111,34 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
     return BLSH_OK;
 }
 
+extern "C" int blsh_ctx_reserve(blsh_ctx *ctx, int64_t max_objects) {
+    if (!ctx) return BLSH_EINVAL;
+    if (max_objects < 0 || max_objects > (1ll << 32)) return blsh_fail(ctx, BLSH_EINVAL, "max_objects outside 0..2^32");
+    if (max_objects > 0 && max_objects <= ctx->plane_cap && max_objects <= ctx->norm2_cap) return BLSH_OK;
+    blsh_device_guard g(ctx->device);
+    // work already enqueued may still read the old buffers
+    BLSH_CUDA(ctx, cudaDeviceSynchronize());
+    if (ctx->plane) BLSH_CUDA(ctx, cudaFree(ctx->plane));
+    if (ctx->norm2) BLSH_CUDA(ctx, cudaFree(ctx->norm2));
+    ctx->plane = ctx->norm2 = nullptr;
+    ctx->plane_cap = ctx->norm2_cap = 0;
+    if (max_objects == 0) return BLSH_OK;
+    BLSH_CUDA(ctx, cudaMalloc(&ctx->plane, (size_t)max_objects * sizeof(uint2)));
+    const cudaError_t e = cudaMalloc(&ctx->norm2, (size_t)max_objects * sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->plane);
+        ctx->plane = nullptr;
+        return blsh_cuda_check(ctx, e, "cudaMalloc(norm2)");
+    }
+    ctx->plane_cap = ctx->norm2_cap = max_objects;
+    return BLSH_OK;
+}
+
+extern "C" int64_t blsh_ctx_reserved(const blsh_ctx *ctx) {
+    if (!ctx) return -1;
+    return ctx->plane_cap < ctx->norm2_cap ? ctx->plane_cap : ctx->norm2_cap;
+}
+
 extern "C" const char *blsh_last_error(const blsh_ctx *ctx) { return ctx ? ctx->err : "no context"; }
 
 extern "C" int blsh_status(blsh_ctx *ctx, void *stream, uint64_t *counters) {

@@ -10,9 +10,13 @@
 // array until the process exits.
 //
 // In host code the array's name is only a host-side stand-in, not a device
-// address; the device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call on that device, with the device
-// current) and passed to the kernels.
+// address.  The device address belongs to the CUDA context the module was
+// loaded into, so it is looked up with cudaGetSymbolAddress on the first call
+// made in each context (identified by the driver's unique context id, so that
+// a context created after cudaDeviceReset, or a second context on the same
+// device, gets its own lookup) and cached for later calls.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -25,12 +29,17 @@ constexpr int kPer = 16;
 constexpr long long kTile = kThreads * kPer;            // statuses per tile
 constexpr long long kMaxTiles = 16384;                  // scratch: 16384 int64 = 128 KiB
 constexpr long long kMaxItems = kTile * kMaxTiles;      // 67,108,864 statuses
-constexpr int kMaxDevices = 64;
+constexpr int kCacheSlots = 64;   // contexts remembered (the oldest entry is replaced)
 
 __device__ __align__(256) long long g_tile_scratch[kMaxTiles];
 
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;   // 0: empty (the driver's ids start at 1)
+    long long *ptr = nullptr;
+};
 std::mutex g_mu;
-long long *g_scratch_ptr[kMaxDevices] = {nullptr};
+ScratchSlot g_slots[kCacheSlots];
+int g_next_slot = 0;
 
 __device__ __forceinline__ bool kept(uint8_t st, uint32_t mask) { return st < 32 && ((mask >> st) & 1u); }
 
@@ -101,17 +110,56 @@ __global__ void __launch_bounds__(kThreads) tile_write(const uint8_t *status, lo
         }
 }
 
-// Device address of g_tile_scratch on the current device, looked up once.
-cudaError_t scratch_for(int device, long long **ptr) {
+// The driver's id of the calling thread's current context (0 if none),
+// through the runtime's driver entry points, so the library needs no link
+// against libcuda.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_tile_scratch in the current context: cached per
+// context; looked up (cudaGetSymbolAddress) only outside stream capture, since
+// the lookup may load the module.  Returns BLSH_OK or BLSH_EDEVICE.
+int scratch_for(cudaStream_t s, long long **ptr) {
+    // any runtime call binds the device's primary context to a thread that
+    // has no current context yet; a capturing stream implies a context
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return BLSH_EDEVICE;
+    unsigned long long id = current_context_id();
+    if (id == 0 && cs == cudaStreamCaptureStatusNone && cudaFree(nullptr) == cudaSuccess) id = current_context_id();
+    if (id == 0) return BLSH_EDEVICE;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_tile_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = (long long *)p;
-    }
-    *ptr = g_scratch_ptr[device];
-    return cudaSuccess;
+    for (const ScratchSlot &e : g_slots)
+        if (e.ctx_id == id) {
+            *ptr = e.ptr;
+            return BLSH_OK;
+        }
+    if (cs != cudaStreamCaptureStatusNone) return BLSH_EDEVICE;   // first call in this context made under capture
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tile_scratch) != cudaSuccess) return BLSH_EDEVICE;
+    g_slots[g_next_slot] = ScratchSlot{id, (long long *)p};
+    g_next_slot = (g_next_slot + 1) % kCacheSlots;
+    *ptr = (long long *)p;
+    return BLSH_OK;
 }
 
 }  // namespace
@@ -121,22 +169,29 @@ extern "C" int blsh_compact_noalloc(const uint8_t *status, int64_t P, const int6
     if (!n_out || (P > 0 && !status) || (cap > 0 && !out_idx) || P < 0 || cap < 0) return BLSH_EINVAL;
     if (P > kMaxItems) return BLSH_ESIZE;   // more statuses than the fixed scratch covers
     if (!blsh_aligned(out_idx, 8) || !blsh_aligned(n_out, 8) || !blsh_aligned(P_dev, 8)) return BLSH_EINVAL;
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
-        cudaGetLastError();
-        return BLSH_EDEVICE;
-    }
-    long long *counts = nullptr;
-    if (scratch_for(device, &counts) != cudaSuccess) {
-        cudaGetLastError();
-        return BLSH_EDEVICE;
-    }
     cudaStream_t s = blsh_stream(stream);
+    long long *counts = nullptr;
+    if (scratch_for(s, &counts) != BLSH_OK) return BLSH_EDEVICE;
     long long tiles = (P + kTile - 1) / kTile;
     if (tiles < 1) tiles = 1;
-    tile_count<<<(unsigned)tiles, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, counts);
-    tile_offsets<<<1, 1024, 0, s>>>(counts, tiles, (long long *)n_out);
-    tile_write<<<(unsigned)tiles, kThreads, 0, s>>>(status, P, (const long long *)P_dev, keep_mask, counts,
-                                                    out_idx, cap);
-    return cudaGetLastError() == cudaSuccess ? BLSH_OK : BLSH_EDEVICE;
+    // each launch's own error code (cudaLaunchKernel returns it), so an error
+    // left on the thread by earlier, unrelated work is neither reported as
+    // this call's nor cleared
+    const long long *pd = (const long long *)P_dev;
+    long long P_cap = P;
+    void *count_args[] = {(void *)&status, (void *)&P_cap, (void *)&pd, (void *)&keep_mask, (void *)&counts};
+    void *offset_args[] = {(void *)&counts, (void *)&tiles, (void *)&n_out};
+    long long cap_ll = cap;
+    void *write_args[] = {(void *)&status, (void *)&P_cap, (void *)&pd, (void *)&keep_mask, (void *)&counts,
+                          (void *)&out_idx, (void *)&cap_ll};
+    cudaError_t e = cudaLaunchKernel((const void *)tile_count, dim3((unsigned)tiles), dim3(kThreads), count_args, 0, s);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel((const void *)tile_offsets, dim3(1), dim3(1024), offset_args, 0, s);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel((const void *)tile_write, dim3((unsigned)tiles), dim3(kThreads), write_args, 0, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // the slot now holds this call's launch error
+        return BLSH_EDEVICE;
+    }
+    return BLSH_OK;
 }

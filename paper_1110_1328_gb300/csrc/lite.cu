@@ -386,22 +386,10 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
     L.scratch = ctx->scratch;
     L.vec = blsh_aligned(status, 16);
     L.norm2 = nullptr;
-    if (values && N > 0) {
-        // the rows' squared norms once per call, in a context-owned buffer
-        // grown outside stream capture (a captured call with a larger N forms
-        // them per pair instead)
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        BLSH_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
-        if (ctx->norm2_cap < N && cs == cudaStreamCaptureStatusNone) {
-            BLSH_CUDA(ctx, cudaStreamSynchronize(s));
-            if (ctx->norm2) BLSH_CUDA(ctx, cudaFree(ctx->norm2));
-            ctx->norm2 = nullptr;
-            ctx->norm2_cap = 0;
-            BLSH_CUDA(ctx, cudaMalloc(&ctx->norm2, (size_t)N * sizeof(long long)));
-            ctx->norm2_cap = N;
-        }
-        if (ctx->norm2_cap >= N) L.norm2 = (const long long *)ctx->norm2;
-    }
+    // the rows' squared norms once per call, in the buffer blsh_ctx_reserve
+    // allocated; with more rows than were reserved each survivor forms its
+    // two sums itself (no allocation here: this is a hot call)
+    if (values && N > 0 && ctx->norm2_cap >= N) L.norm2 = (const long long *)ctx->norm2;
     // survivors: queued (balanced over warps), then any beyond the queue in place
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->work2, 0, 2 * sizeof(unsigned long long), s));   // work2, work3
     unsigned long long *queue = ctx->lite_queue;

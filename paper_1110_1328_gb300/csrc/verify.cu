@@ -428,27 +428,16 @@ int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A0, const blsh_plan &pla
     const int kind = A0.chunk_words == A0.k ? BLSH_JACCARD : BLSH_COSINE;
     VerifyArgs A = A0;
     A.plane = nullptr;
-    if (kind == BLSH_COSINE && A.N * (long long)A.W * 4 > kPlaneMinBytes) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        BLSH_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
-        if (ctx->plane_cap < A.N && cs == cudaStreamCaptureStatusNone) {
-            // grown outside stream capture only (a captured call with a
-            // larger N reads its rows instead)
-            BLSH_CUDA(ctx, cudaStreamSynchronize(s));
-            if (ctx->plane) BLSH_CUDA(ctx, cudaFree(ctx->plane));
-            ctx->plane = nullptr;
-            ctx->plane_cap = 0;
-            BLSH_CUDA(ctx, cudaMalloc(&ctx->plane, (size_t)A.N * sizeof(uint2)));
-            ctx->plane_cap = A.N;
-        }
-        if (ctx->plane_cap >= A.N) {
-            const long long blocks = (A.N + 255) / 256, cap = (long long)ctx->sm_count * 8;
-            blsh_time_start(ctx, s);
-            plane_copy_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A.sig, A.N, A.W,
-                                                                                      (uint2 *)ctx->plane);
-            BLSH_LAUNCHED(ctx, "plane_copy_kernel");
-            A.plane = (const uint2 *)ctx->plane;
-        }
+    // the plane lives in the buffer blsh_ctx_reserve allocated; a call with
+    // more objects than were reserved reads the rows instead (no allocation
+    // here: this is a hot call)
+    if (kind == BLSH_COSINE && A.N * (long long)A.W * 4 > kPlaneMinBytes && ctx->plane_cap >= A.N) {
+        const long long blocks = (A.N + 255) / 256, cap = (long long)ctx->sm_count * 8;
+        blsh_time_start(ctx, s);
+        plane_copy_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A.sig, A.N, A.W,
+                                                                                  (uint2 *)ctx->plane);
+        BLSH_LAUNCHED(ctx, "plane_copy_kernel");
+        A.plane = (const uint2 *)ctx->plane;
     }
     if (plan.mode == BLSH_PLAN_PERSISTENT) return dispatch<true>(ctx, A, plan, kind, s);
     return dispatch<false>(ctx, A, plan, kind, s);

@@ -106,3 +106,64 @@ def test_modelled_kernels_are_the_recorded_ones(workload):
     names = _recorded_names()
     missing = [k for k in work if not k.endswith(" gathered") and k not in names]
     assert not missing, missing
+
+
+def _fake_large_pipe(n_docs=3000, P=20_000, lazy=512, seed=3, n_groups=200):
+    """A stand-in for bench.LargePipeline on the CPU: the workload's generator
+    at a small size, random candidate pairs and random per-pair outputs."""
+    w = dict(bench.WORKLOADS["large-mixed"], n=n_docs, dim=1 << 16, lazy_bits=lazy)
+    indptr, indices, values = synth.large_tfidf_device(n_docs=n_docs, dim=1 << 16, nnz_min=5, nnz_max=400,
+                                                       n_groups=n_groups, seed=seed, device=torch.device("cpu"))
+    rng = np.random.default_rng(seed)
+    pr = np.sort(rng.integers(0, n_docs, (P, 2)), axis=1).astype(np.int32)
+    levels = w["n_max"] // w["k"]
+    pipe = types.SimpleNamespace(
+        torch=torch, B=B, w=w, dev=torch.device("cpu"), indptr=indptr, indices=indices, values=values, N=n_docs,
+        nnz=int(indptr[-1]), P=P, bits=w["bits"], lazy_bits=lazy, pairs=torch.from_numpy(pr), ranges=[(0, P)],
+        status=torch.from_numpy(rng.integers(0, 3, P).astype(np.uint8)),
+        n_used=torch.from_numpy((rng.integers(1, levels + 1, P) * w["k"]).astype(np.int16)),
+        lstatus=torch.from_numpy(rng.choice([0, 3, 4], P).astype(np.uint8)),
+        need=torch.from_numpy((rng.random(n_docs) < 0.2).astype(np.uint8)))
+    return w, pipe
+
+
+def test_large_kernel_work_by_hand():
+    w, pipe = _fake_large_pipe()
+    work = bench.large_kernel_work(pipe)
+    L, bits, k = 512, w["bits"], w["k"]
+    nu = pipe.n_used.numpy().astype(np.int64)
+    st = pipe.status.numpy()
+    kept = (st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)
+    resumed = nu > L
+    want_v = pipe.P * 14 + 4 * int((kept & ~resumed).sum()) + int(np.minimum(nu // k, L // k).sum()) * (k // 4)
+    assert work["verify_kernel"] == (want_v, "B")
+    want_r = pipe.P + int(resumed.sum()) * 13 + 4 * int((kept & resumed).sum()) + int((nu[resumed] // k).sum()) * 8
+    assert work["verify_resume_kernel"] == (want_r, "B")
+    # projection: the prefix of every row, the rest of the rows marked in need
+    ip, ix = pipe.indptr.numpy(), pipe.indices.numpy()
+    need = pipe.need.numpy().astype(bool)
+    sel = np.concatenate([np.arange(ip[i], ip[i + 1]) for i in np.flatnonzero(need)])
+    want_p = (pipe.nnz * 8 + pipe.N * (16 + L // 8) + len(np.unique(ix)) * L * 2
+              + len(sel) * 8 + int(need.sum()) * (16 + (bits - L) // 8) + len(np.unique(ix[sel])) * (bits - L) * 2)
+    assert work["srp_sparse4_kernel (two-byte codes)"] == (want_p, "B")
+    for name in ("lite_queue_kernel", "emit_warp_kernel (write pass)", "compact_write", "band_keys_kernel"):
+        assert work[name][0] > 0
+
+
+def test_large_oracle_sample_times_and_extrapolation():
+    """The cpu_baseline leg's sampling on a small stand-in: the oracle's inputs
+    come from the sampled rows (terms renumbered, its own codes), the timings
+    are positive, and the extrapolation scales each part by its own unit."""
+    import oracle as O
+    w, pipe = _fake_large_pipe(n_docs=600, P=3000, n_groups=50)
+    w = dict(w, bits=256, n_max=256, h=128)
+    inp = bench.large_oracle_inputs(pipe, w, seed=1, n_pairs=500, n_hash=100, threads=2)
+    assert inp["hash_csr"].n == 100 and len(inp["pairs"]) == 500
+    assert inp["pair_sig"].shape == (inp["pair_csr"].n, 8)
+    t1 = bench.large_oracle_times(O, w, inp, threads=1, min_verify_s=0.0)
+    t2 = bench.large_oracle_times(O, w, inp, threads=2, min_verify_s=0.0)
+    for t in (t1, t2):
+        assert t["hash_s"] > 0 and t["verify_s"] > 0 and t["pairs"] == 500 and t["objects"] == 100
+    T = bench.extrapolate({"hash_s": 2.0, "band_s": 1.0, "verify_s": 3.0, "nnz": 10, "objects": 5, "pairs": 30},
+                          N=50, nnz=100, P=300)
+    assert T == 100 * 0.2 + 50 * 0.2 + 300 * 0.1

@@ -5,9 +5,11 @@ pair counts, and a CUDA-graph replay of the whole step).
 cosine-small (20,000 tf-idf vectors, 2,048 SRP bits, ~2.7e7 candidate pairs)
 and jaccard-small (2,000 sets, 256 minhashes) are compared with the oracle in
 full: signatures, the candidate set, every pair's Algorithm 1 and Algorithm 2
-outcome, and both output sets.  The 1,000,000-node Chung-Lu workload is
-compared on samples the oracle computes one by one, plus properties that hold
-at any size."""
+outcome, and both output sets.  The 1,000,000-node Chung-Lu workload, the
+1,000,000-point dense workload and the 5,000,000-vector mixed workload (also
+streamed in several batches with its checkpoint record) are compared on
+samples the oracle computes one by one, plus properties that hold at any
+size."""
 import numpy as np
 import pytest
 import torch
@@ -193,29 +195,38 @@ def test_precision_workload_sampled(B):
     assert bool((key[1:] > key[:-1]).all())
 
 
-def test_large_mixed_workload_sampled(B):
-    """5,000,000 tf-idf vectors over a 2^24-term vocabulary, R generated on
-    the device as two-byte codes (68.7 GB), about 1e9 candidates verified by
-    Algorithms 1 and 2 in batches: sampled signature rows bit-exact to the
-    oracle's (its own codes for the terms those rows use), sampled pairs'
-    outcomes of both algorithms recomputed by the oracle, every sampled pair
-    colliding in a band, the candidate list free of duplicates, and the
-    kept counts equal to the statuses."""
+@pytest.fixture(scope="module")
+def large_pipe(B):
+    """The 5e6-vector mixed workload in bench's launch configuration: one
+    batch, lazy hashing, the autotuned plan, one CUDA-graph replay of the
+    whole step after its outputs were poisoned."""
     w = dict(bench.WORKLOADS["large-mixed"])
     dev = torch.device("cuda", 0)
     pipe = bench.LargePipeline(B, torch, w, dev)
-    pipe.step()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pipe.step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        pipe.step()
+    pipe.status.fill_(77)
+    pipe.lstatus.fill_(77)
+    pipe.sig.fill_(0)
+    pipe.n_out.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
     assert B.blsh_status(pipe.ctx) == 0
-    P = pipe.P
-    assert P > 100_000_000 and pipe.batch >= P          # one batch: every pair's outcome is kept
-    rng = np.random.default_rng(3)
-    q = np.sort(rng.choice(P, 3000, replace=False))
-    qd = torch.from_numpy(q).to(dev)
-    sp = u32(pipe.pairs[qd])
-    assert np.all(sp[:, 0] < sp[:, 1])
-    extra = rng.choice(pipe.N, 300, replace=False)
-    ids, inv = np.unique(np.concatenate([sp.reshape(-1), extra]), return_inverse=True)
-    # the sampled objects' rows, with their terms renumbered 0..T-1
+    yield w, pipe
+    del g
+
+
+def large_oracle_view(pipe, w, ids):
+    """The sampled objects' rows with their terms renumbered 0..T-1, and the
+    oracle's own codes for those terms."""
+    dev = pipe.dev
     indptr = pipe.indptr.cpu().numpy()
     rows = [np.arange(indptr[i], indptr[i + 1]) for i in ids]
     sel = torch.from_numpy(np.concatenate(rows)).to(dev)
@@ -224,10 +235,46 @@ def test_large_mixed_workload_sampled(B):
     uterm, tinv = np.unique(terms, return_inverse=True)
     local = synth.CSR(np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64),
                       tinv.astype(np.uint32), vals, len(uterm))
-    bits = w["bits"]
-    Rq = np.stack([O.gaussian_codes(w["r_seed"], 1, bits, row0=int(t))[0] for t in uterm])
+    Rq = np.stack([O.gaussian_codes(w["r_seed"], 1, w["bits"], row0=int(t))[0] for t in uterm])
+    return local, Rq
+
+
+def test_large_mixed_workload_sampled(B, large_pipe):
+    """5,000,000 tf-idf vectors over a 2^24-term vocabulary, R generated on
+    the device as two-byte codes (68.7 GB), about 1e9 candidates verified by
+    Algorithms 1 and 2 with lazy hashing (the first 512 bits of every object,
+    the rest of the objects of the pairs left open): sampled pairs' outcomes
+    of both algorithms recomputed by the oracle from its own full signatures,
+    sampled signature rows bit-exact (the prefix of every row, and all bits
+    of the rows the step hashed in full), every sampled pair colliding in a
+    band, the candidate list free of duplicates, and the kept counts equal to
+    the statuses."""
+    w, pipe = large_pipe
+    dev = pipe.dev
+    P, L = pipe.P, pipe.lazy_bits
+    assert P > 100_000_000 and len(pipe.ranges) == 1 and pipe.batch >= P and 0 < L < w["bits"]
+    rng = np.random.default_rng(3)
+    q = np.sort(rng.choice(P, 3000, replace=False))
+    qd = torch.from_numpy(q).to(dev)
+    sp = u32(pipe.pairs[qd])
+    assert np.all(sp[:, 0] < sp[:, 1])
+    # pairs the lazy prefix left open, so that the resumed path is covered
+    open_q = torch.nonzero(pipe.n_used[:P].to(torch.int64) & 0xFFFF > L).flatten()
+    assert open_q.numel() > 0
+    extra_q = open_q[torch.randperm(open_q.numel(), device=dev)[:500]].sort().values.cpu().numpy()
+    q = np.union1d(q, extra_q)
+    qd = torch.from_numpy(q).to(dev)
+    sp = u32(pipe.pairs[qd])
+    extra = rng.choice(pipe.N, 300, replace=False)
+    ids, inv = np.unique(np.concatenate([sp.reshape(-1), extra]), return_inverse=True)
+    local, Rq = large_oracle_view(pipe, w, ids)
     sig_o = O.srp_sparse_q16(local, Rq)
-    assert np.array_equal(u32(pipe.sig[torch.from_numpy(ids).to(dev)]), sig_o)
+    ids_d = torch.from_numpy(ids).to(dev)
+    got = u32(pipe.sig[ids_d])
+    pw = L // 32
+    assert np.array_equal(got[:, :pw], sig_o[:, :pw])                 # every object's prefix
+    full = pipe.need[ids_d].cpu().numpy().astype(bool)
+    assert full.any() and np.array_equal(got[full], sig_o[full])     # the rows hashed in full
     lp = inv[: 2 * len(q)].reshape(-1, 2).astype(np.uint32)
     r, bands = w["rows"], w["bands"]
 
@@ -255,8 +302,83 @@ def test_large_mixed_workload_sampled(B):
     key, _ = torch.sort((dp[:, 0] << 32) | dp[:, 1])
     assert bool((key[1:] > key[:-1]).all())
     del key, dp
-    # the kept counts are those of the statuses
+    # the kept counts and output sets are those of the statuses
     st = pipe.status[:P]
-    n1 = int(((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).sum().item())
-    n2 = int((pipe.lstatus[:P] == B.LITE_ACCEPT).sum().item())
-    assert [int(x) for x in pipe.kept.cpu()] == [n1, n2]
+    k1 = torch.nonzero((st == B.ACCEPT) | (st == B.ACCEPT_AT_MAX)).flatten()
+    k2 = torch.nonzero(pipe.lstatus[:P] == B.LITE_ACCEPT).flatten()
+    assert pipe.kept_counts() == [k1.numel(), k2.numel()]
+    assert torch.equal(pipe.out1[: k1.numel()], k1) and torch.equal(pipe.out2[: k2.numel()], k2)
+    # the stop histogram counts every pair once
+    assert int(pipe.hist.sum().item()) == P
+
+
+def test_large_mixed_streamed_in_batches(B, large_pipe, tmp_path):
+    """The same candidates verified in several device batches (a cap below
+    P), eagerly with the checkpoint record, interrupted while the second
+    batch is being recorded and resumed (that batch is then redone): every
+    batch's statuses, hashes used, agreements,
+    estimates and Lite outcomes equal those of the single-batch step, the
+    pairs at and around every batch boundary agree with the oracle, and the
+    kept counts and stop histogram add up."""
+    from paper_1110_1328_gb300.batches import Checkpoint
+    w, pipe = large_pipe
+    dev = pipe.dev
+    P = pipe.P
+    ref = {n: getattr(pipe, n)[:P].clone() for n in ("status", "n_used", "m", "lstatus")}
+    ref_est, ref_sim = pipe.est[:P].clone(), pipe.sim[:P].clone()
+    ref_kept, ref_hist = pipe.kept_counts(), pipe.hist.sum(0).cpu()
+    pipe.set_batch(P // 3 + 12_345)
+    assert len(pipe.ranges) == 3
+    boundary = set()
+    for b0, n in pipe.ranges:
+        boundary.update(q for q in range(b0 - 2, b0 + 3) if 0 <= q < P)
+        boundary.update(q for q in range(b0 + n - 2, b0 + n + 2) if 0 <= q < P)
+    boundary = np.array(sorted(boundary))
+    seen, got_b = [], {}
+
+    class Stop(Exception):
+        pass
+
+    def on_batch(b, b0, n, stop_after=None):
+        torch.cuda.synchronize()
+        for name in ("status", "n_used", "m", "lstatus"):
+            assert torch.equal(getattr(pipe, name)[:n], ref[name][b0:b0 + n]), (b, name)
+        kept = (ref["status"][b0:b0 + n] == B.ACCEPT) | (ref["status"][b0:b0 + n] == B.ACCEPT_AT_MAX)
+        assert torch.equal(pipe.est[:n][kept], ref_est[b0:b0 + n][kept])
+        surv = (ref["lstatus"][b0:b0 + n] == B.LITE_ACCEPT) | (ref["lstatus"][b0:b0 + n] == B.LITE_REJECT)
+        assert torch.equal(pipe.sim[:n][surv], ref_sim[b0:b0 + n][surv])
+        sel = boundary[(boundary >= b0) & (boundary < b0 + n)]
+        got_b.update({int(q): (int(pipe.status[q - b0]), int(pipe.lstatus[q - b0])) for q in sel})
+        seen.append(b)
+        if stop_after is not None and b == stop_after:
+            raise Stop()
+
+    ck = Checkpoint(str(tmp_path / "large.json"))
+    with pytest.raises(Stop):
+        pipe.verify_streamed(ck, on_batch=lambda b, b0, n: on_batch(b, b0, n, stop_after=1))
+    assert ck.load(ck_job := json_job(pipe)).next_batch == 1
+    rec = pipe.verify_streamed(ck, on_batch=on_batch)
+    assert seen == [0, 1, 1, 2]
+    assert rec.next_batch == 3 and rec.kept == ref_kept and rec.hist == [int(x) for x in ref_hist]
+    assert ck_job == rec.job
+    # the boundary pairs against the oracle
+    qd = torch.from_numpy(boundary).to(dev)
+    sp = u32(pipe.pairs[qd])
+    ids, inv = np.unique(sp.reshape(-1), return_inverse=True)
+    local, Rq = large_oracle_view(pipe, w, ids)
+    sig_o = O.srp_sparse_q16(local, Rq)
+    lp = inv.reshape(-1, 2).astype(np.uint32)
+    tab = O.tables(O.Params(kind=1, t=w["t"], k=w["k"], n_max=w["n_max"], h=w["h"]))
+    want, lite = O.verify(tab, lp, sig_o), O.verify_lite(tab, lp, sig_o, local)
+    for i, q in enumerate(boundary):
+        assert got_b[int(q)] == (int(want.status[i]), int(lite.status[i])), q
+    # the captured-step path over the same batches gives the same counts
+    pipe.step()
+    assert B.blsh_status(pipe.ctx) == 0
+    assert pipe.kept_counts() == ref_kept
+
+
+def json_job(pipe):
+    w = pipe.w
+    return {"workload": "large-mixed", "n": pipe.N, "seed": w["seed"], "r_seed": w["r_seed"], "P": pipe.P,
+            "batch": pipe.batch, "lazy_bits": pipe.lazy_bits}

@@ -137,8 +137,9 @@ def test_verify_every_plan_matches_oracle(B, ctx, d):
 @pytest.mark.parametrize("d", [TABLE_PARAMS[4], TABLE_PARAMS[7]], ids=["k32-n2048", "k64-n512"])
 def test_verify_large_signature_set_matches_oracle(B, ctx, d):
     """Cosine signature sets too large for L2 (> 64 MB) are verified with the
-    first two words of every row read from a dense plane: the same outputs
-    as the oracle, every plan."""
+    first two words of every row read from a dense plane once the context
+    has reserved it (blsh_ctx_reserve), and from the rows without one: the
+    same outputs as the oracle either way, every plan."""
     p = oracle_params(d)
     sig, pairs = model_signatures(1, d["n_max"], 3001, seed=11)
     W = sig.shape[1]
@@ -149,7 +150,14 @@ def test_verify_large_signature_set_matches_oracle(B, ctx, d):
     pairs = pairs + np.uint32(rows - sig.shape[0])
     pairs = np.concatenate([pairs, rng.integers(0, rows, size=(20000, 2)).astype(np.uint32)])
     want = O.verify(O.tables(p), pairs, big)
+    ctx = B.Context(0)          # a context of its own: no reservation yet
     tab = gpu_tables(B, ctx, d)
+    B.blsh_timing_begin(ctx)
+    res = run_verify(B, ctx, tab, pairs, big)
+    assert [n for n, _ in B.blsh_timing_end(ctx)] == ["verify_kernel"]     # rows read directly
+    assert_same(res, want, None, p)
+    B.blsh_ctx_reserve(ctx, rows)
+    assert B.blsh_ctx_reserved(ctx) == rows
     for plan in (B.blsh_plan(B.PLAN_PLAIN, 1, 128, 32, 0), B.blsh_plan(B.PLAN_PERSISTENT, 1, 256, 37, 0)):
         assert_same(run_verify(B, ctx, tab, pairs, big, plan=plan), want, None, p)
     B.blsh_timing_begin(ctx)
