@@ -422,6 +422,24 @@ BLSH_API int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t
                   int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m, float *est,
                   blsh_plan *best, void *stream);
 
+/* The batching pattern's tuner: the chunk size k ("compare hashes n to
+ * n+k" of Algorithm 1) chosen together with the launch plan.  For each
+ * k = ks[i] (32, 64 or 128, dividing params->n_max; 1 to 8 of them) it builds
+ * the Section 4.3 tables for *params with that k (Lite's h rounded up to a
+ * whole chunk, at most n_max), times every launch plan as blsh_autotune does
+ * on the given inputs (outputs are overwritten), and keeps the fastest
+ * (tables, plan).  *out receives those tables (destroy them with
+ * blsh_tables_destroy), *best (host, may be NULL) the plan, which is also
+ * stored for them in the context; ms_per_k (host float [n_ks], may be NULL)
+ * the best time per call found for each k.  The decisions of Algorithms 1
+ * and 2 depend on k (pairs are tested after every k hashes), so the outputs
+ * of later calls are those of the chosen k.  Synchronises `stream`.
+ * BLSH_EINVAL for a k outside {32, 64, 128} or not dividing n_max. */
+BLSH_API int blsh_autotune_k(blsh_ctx *ctx, const blsh_params *params, const int32_t *ks, int32_t n_ks,
+                             const uint32_t *pairs, int64_t P, const uint32_t *sig, int64_t N, int32_t sig_words,
+                             uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, blsh_tables **out,
+                             blsh_plan *best, float *ms_per_k, void *stream);
+
 /* ---- the classical estimator and the learned prior ------------------------- */
 
 /* The maximum-likelihood estimate of Section 3 over a fixed number of hashes

@@ -90,6 +90,7 @@ def lib():
             "blsh_verify_resume": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_set_plan": ([p, p, p], C.c_int),
             "blsh_autotune": ([p, p, p, i64, p, i64, i32, p, p, p, p, p, p], C.c_int),
+            "blsh_autotune_k": ([p, p, p, i32, p, i64, p, i64, i32, p, p, p, p, p, p, p, p], C.c_int),
             "blsh_compact": ([p, p, i64, p, u32, p, i64, p, p], C.c_int),
             "blsh_compact_noalloc": ([p, i64, p, u32, p, i64, p, p], C.c_int),
             "blsh_estimate_mle": ([p, i32, i32, C.c_double, p, i64, p, p, i64, i32, p, p, p, p], C.c_int),
@@ -487,6 +488,27 @@ def blsh_autotune(ctx: Context, tab: Tables, pairs, sig, status, n_used=None, m=
                              _dev(n_used), _dev(m), _dev(est, torch.float32), C.byref(best), _stream(stream))
     _check(rc, ctx)
     return best
+
+
+def blsh_autotune_k(ctx: Context, params: blsh_params, ks, pairs, sig, status, n_used=None, m=None, est=None,
+                    stream=None):
+    """The chunk size k in ks and the launch plan, tuned together; returns
+    (the chosen k's Tables, the plan, {k: best ms per call})."""
+    P = pairs.shape[0]
+    N, W = sig.shape
+    ks = [int(k) for k in ks]
+    karr = (C.c_int32 * len(ks))(*ks)
+    ms = (C.c_float * len(ks))()
+    best = blsh_plan()
+    h = C.c_void_p()
+    rc = lib().blsh_autotune_k(ctx.handle, C.byref(params), karr, len(ks), _dev(pairs), P, _dev(sig), N, W,
+                               _dev(status, torch.uint8), _dev(n_used), _dev(m), _dev(est, torch.float32),
+                               C.byref(h), C.byref(best), ms, _stream(stream))
+    _check(rc, ctx)
+    par = blsh_params()
+    lv, ties = C.c_int32(), C.c_int32()
+    _check(lib().blsh_tables_download(h, C.byref(par), C.byref(lv), C.byref(ties), None, None, None, None, None))
+    return Tables(h, par), best, {kk: float(v) for kk, v in zip(ks, ms)}
 
 
 def blsh_compact(ctx: Context, status, keep_mask: int, out_idx, n_out, P_dev=None, stream=None):

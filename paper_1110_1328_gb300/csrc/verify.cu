@@ -489,12 +489,14 @@ int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t 
     return BLSH_OK;
 }
 
-// The plan the autotuner chose for these tables, else the default.
+// The plan the autotuner chose for these tables, else the default.  (A
+// plan stored for destroyed tables whose address was reused may not fit the
+// new tables' kind and k; the default is used then.)
 blsh_plan blsh_plan_for(blsh_ctx *ctx, const blsh_tables *tab) {
     blsh_plan plan = blsh_default_plan(tab->p.kind);
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto it = ctx->plans.find(tab);
-    if (it != ctx->plans.end()) plan = it->second;
+    if (it != ctx->plans.end() && blsh_check_plan(it->second, tab->p.kind, tab->p.k) == BLSH_OK) plan = it->second;
     return plan;
 }
 
@@ -522,12 +524,7 @@ extern "C" int blsh_verify(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t
                            uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, uint64_t *stop_hist,
                            void *stream) {
     if (!ctx || !tab) return BLSH_EINVAL;
-    blsh_plan plan = blsh_default_plan(tab->p.kind);
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        auto it = ctx->plans.find(tab);
-        if (it != ctx->plans.end()) plan = it->second;
-    }
+    const blsh_plan plan = blsh_plan_for(ctx, tab);
     return blsh_verify_plan(ctx, tab, &plan, pairs, P, P_dev, sig, N, sig_words, status, n_used, m, est,
                             stop_hist, stream);
 }
@@ -541,11 +538,14 @@ extern "C" int blsh_set_plan(blsh_ctx *ctx, const blsh_tables *tab, const blsh_p
     return BLSH_OK;
 }
 
-extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
-                             const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
-                             uint16_t *n_used, uint16_t *m, float *est, blsh_plan *best, void *stream) {
-    if (!ctx || !tab) return BLSH_EINVAL;
-    blsh_device_guard g(ctx->device);
+namespace {
+
+// Times every candidate launch plan for `tab` on the given pairs (one
+// untimed call, then three timed ones each) and returns the fastest and its
+// time per call.  Outputs are overwritten.
+int tune_plans(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P, const uint32_t *sig,
+               int64_t N, int32_t sig_words, uint8_t *status, uint16_t *n_used, uint16_t *m, float *est,
+               void *stream, blsh_plan *best, float *best_ms_out) {
     cudaStream_t s = blsh_stream(stream);
     std::vector<blsh_plan> cands;
     const int kind = tab->p.kind;
@@ -595,10 +595,77 @@ extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    *best = best_plan;
+    *best_ms_out = best_ms / 3.0f;
+    return BLSH_OK;
+}
+
+}  // namespace
+
+extern "C" int blsh_autotune(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t *pairs, int64_t P,
+                             const uint32_t *sig, int64_t N, int32_t sig_words, uint8_t *status,
+                             uint16_t *n_used, uint16_t *m, float *est, blsh_plan *best, void *stream) {
+    if (!ctx || !tab) return BLSH_EINVAL;
+    blsh_device_guard g(ctx->device);
+    blsh_plan plan;
+    float ms = 0.f;
+    const int rc = tune_plans(ctx, tab, pairs, P, sig, N, sig_words, status, n_used, m, est, stream, &plan, &ms);
+    if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        ctx->plans[tab] = best_plan;
+        ctx->plans[tab] = plan;
     }
+    if (best) *best = plan;
+    return BLSH_OK;
+}
+
+extern "C" int blsh_autotune_k(blsh_ctx *ctx, const blsh_params *params, const int32_t *ks, int32_t n_ks,
+                               const uint32_t *pairs, int64_t P, const uint32_t *sig, int64_t N, int32_t sig_words,
+                               uint8_t *status, uint16_t *n_used, uint16_t *m, float *est, blsh_tables **out,
+                               blsh_plan *best, float *ms_per_k, void *stream) {
+    if (!ctx || !params || !ks || !out) return BLSH_EINVAL;
+    *out = nullptr;
+    if (n_ks < 1 || n_ks > 8) return blsh_fail(ctx, BLSH_EINVAL, "between 1 and 8 chunk sizes");
+    for (int i = 0; i < n_ks; ++i)
+        if ((ks[i] != 32 && ks[i] != 64 && ks[i] != 128) || params->n_max % ks[i])
+            return blsh_fail(ctx, BLSH_EINVAL, "chunk size %d: not 32, 64 or 128, or not dividing n_max", ks[i]);
+    blsh_device_guard g(ctx->device);
+    blsh_tables *best_tab = nullptr;
+    blsh_plan best_plan = blsh_default_plan(params->kind);
+    float best_ms = 1e30f;
+    int rc = BLSH_OK;
+    for (int i = 0; i < n_ks && rc == BLSH_OK; ++i) {
+        blsh_params q = *params;
+        q.k = ks[i];
+        // Lite's h: the same number of hashes, rounded up to a whole chunk
+        q.h = (q.h + q.k - 1) / q.k * q.k;
+        if (q.h > q.n_max) q.h = q.n_max;
+        blsh_tables *tab = nullptr;
+        rc = blsh_tables_build(ctx, &q, &tab, stream);
+        if (rc == BLSH_ENUMERIC) rc = BLSH_OK;   // the table is usable; the caller sees near ties in its download
+        if (rc) break;
+        blsh_plan plan;
+        float ms = 0.f;
+        rc = tune_plans(ctx, tab, pairs, P, sig, N, sig_words, status, n_used, m, est, stream, &plan, &ms);
+        if (ms_per_k) ms_per_k[i] = rc ? -1.f : ms;
+        if (rc == BLSH_OK && ms < best_ms) {
+            if (best_tab) blsh_tables_destroy(best_tab);
+            best_tab = tab;
+            best_plan = plan;
+            best_ms = ms;
+        } else {
+            blsh_tables_destroy(tab);
+        }
+    }
+    if (rc) {
+        if (best_tab) blsh_tables_destroy(best_tab);
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->plans[best_tab] = best_plan;
+    }
+    *out = best_tab;
     if (best) *best = best_plan;
     return BLSH_OK;
 }

@@ -166,6 +166,33 @@ def test_verify_large_signature_set_matches_oracle(B, ctx, d):
     assert_same(res, want, None, p)
 
 
+def test_autotune_k_outputs_are_the_chosen_ks(B, ctx):
+    """The batching pattern's tuner chooses k among 32, 64 and 128 together
+    with the plan; later calls with the returned tables give the oracle's
+    outputs for that k (and Lite's h rounded up to a whole chunk)."""
+    sig, pairs = model_signatures(0, 256, 20001, seed=21)
+    dev = torch.device("cuda")
+    pairs_t = torch.from_numpy(pairs.view(np.int32)).to(dev)
+    sig_t = torch.from_numpy(sig.view(np.int32)).to(dev)
+    P = len(pairs)
+    st = torch.zeros(P, dtype=torch.uint8, device=dev)
+    nu = torch.zeros(P, dtype=torch.int16, device=dev)
+    params = B.make_params(kind=0, t=0.6, k=32, n_max=256, h=64)
+    tab, plan, ms = B.blsh_autotune_k(ctx, params, (32, 64, 128), pairs_t, sig_t, st, nu)
+    k = tab.params.k
+    assert k in (32, 64, 128) and sorted(ms) == [32, 64, 128] and all(v > 0 for v in ms.values())
+    assert tab.params.h == (128 if k == 128 else 64)
+    assert plan.mode in (B.PLAN_PLAIN, B.PLAN_PERSISTENT) and plan.block in (128, 256, 512)
+    p = O.Params(kind=0, t=0.6, k=k, n_max=256, h=tab.params.h)
+    want = O.verify(O.tables(p), pairs, sig)
+    assert_same(run_verify(B, ctx, tab, pairs, sig), want, None, p)
+    for bad in ((48,), (32, 512), ()):
+        with pytest.raises((B.BlshError, ValueError)):
+            B.blsh_autotune_k(ctx, params, bad, pairs_t, sig_t, st, nu)
+    with pytest.raises(B.BlshError):          # 128 does not divide n_max = 320
+        B.blsh_autotune_k(ctx, B.make_params(kind=0, t=0.6, k=32, n_max=320), (32, 128), pairs_t, sig_t, st, nu)
+
+
 def test_verify_device_count_and_capacity(B, ctx):
     d = TABLE_PARAMS[4]
     p = oracle_params(d)
