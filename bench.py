@@ -1183,7 +1183,14 @@ def large_kernel_work(pipe):
     pr = pipe.pairs[b0_last:b0_last + n_last][surv].to(torch.int64) if ns else None
     surv_nnz = int((row_len[pr[:, 0]] + row_len[pr[:, 1]]).sum()) if ns else 0
     work["lite_collect_kernel"] = (scale * (n_last + 8 * ns), "B")
-    work["lite_queue_kernel"] = (scale * (ns * (8 + 16 + 16 + 9) + surv_nnz * 8), "B")
+    # per survivor: its pair, both rows' bounds, the two squared norms (when
+    # formed), sim and status written, and both rows (index and value per
+    # nonzero); the first 2^23 survivors go through the queue (8 B each), the
+    # rest through the in-place pass, which also scans every status
+    per_surv = (8 + 32 + 16 + 9) + (surv_nnz / ns * 8 if ns else 0)
+    n_q = min(ns, 1 << 23)
+    work["lite_queue_kernel"] = (scale * n_q * (per_surv + 8), "B")
+    work["lite_exact_kernel"] = (scale * (n_last + (ns - n_q) * per_surv), "B")
     work["row_norm2_kernel"] = (nnz * 4 + N * 8, "B")
     # banding (cosine: packed band keys, LSD radix passes, emission)
     rows, bands = w["rows"], w["bands"]

@@ -120,8 +120,8 @@ BLSH_API int blsh_ctx_destroy(blsh_ctx *ctx);
 
 /* Reserves the context's per-object buffers for signature sets of up to
  * max_objects rows, so that the hot calls need no allocation: the
- * first-words plane of the verification calls (8 bytes per object; words 0
- * and 1 of every cosine signature row, Algorithm 1's first step) and Lite's
+ * first-words plane of the verification calls (16 bytes per object; words
+ * 0..3 of every cosine signature row, Algorithm 1's first step) and Lite's
  * squared-norm buffer (8 bytes per object; Algorithm 2's exact cosine).  A
  * set-up call: it synchronises the device, frees the previous buffers and
  * allocates the new ones (it never shrinks them; 0 releases them).  A
@@ -335,9 +335,10 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
  * call can follow a producer on the same stream without a host sync.
  * Uses the plan blsh_autotune stored for these tables, else a default.
  * Cosine signature sets larger than 64 MB (N * sig_words * 4 bytes) with
- * N <= blsh_ctx_reserved(ctx): the call first copies words 0 and 1 of every
- * row into the context's plane of N uint2, which stays in L2, and every
- * pair's first step reads them there; with N above the reservation each
+ * sig_words > 4 and N <= blsh_ctx_reserved(ctx): the call first copies words
+ * 0..3 of every row (the first 128 hashes) into the context's plane of N
+ * uint4, which stays in L2, and every pair's first step reads them there;
+ * with N above the reservation each
  * pair reads its rows (same outputs).  The call allocates nothing and does
  * not synchronise, so it can be captured into a CUDA graph.  This holds for
  * every verification entry point below. */

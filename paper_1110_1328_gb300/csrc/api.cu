@@ -123,7 +123,7 @@ extern "C" int blsh_ctx_reserve(blsh_ctx *ctx, int64_t max_objects) {
     ctx->plane = ctx->norm2 = nullptr;
     ctx->plane_cap = ctx->norm2_cap = 0;
     if (max_objects == 0) return BLSH_OK;
-    BLSH_CUDA(ctx, cudaMalloc(&ctx->plane, (size_t)max_objects * sizeof(uint2)));
+    BLSH_CUDA(ctx, cudaMalloc(&ctx->plane, (size_t)max_objects * sizeof(uint4)));
     const cudaError_t e = cudaMalloc(&ctx->norm2, (size_t)max_objects * sizeof(long long));
     if (e != cudaSuccess) {
         cudaFree(ctx->plane);

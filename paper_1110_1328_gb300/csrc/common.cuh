@@ -43,7 +43,7 @@ struct blsh_ctx {
     uint2 *recheck_queue = nullptr;                   // [BLSH_RECHECK_CAP] (row, bit) of undecided SRP signs
     unsigned long long *lite_queue = nullptr;         // [BLSH_LITE_QUEUE_CAP] Lite survivors (pair indices)
     // per-object buffers, sized by blsh_ctx_reserve (never by a hot call)
-    void *plane = nullptr;                            // verification: [plane_cap] first two words of each row
+    void *plane = nullptr;                            // verification: [plane_cap] first four words of each row
     long long plane_cap = 0;
     void *norm2 = nullptr;                            // Lite (cosine): [norm2_cap] rows' squared norms
     long long norm2_cap = 0;

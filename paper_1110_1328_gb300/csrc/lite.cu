@@ -91,78 +91,168 @@ __device__ __forceinline__ long long lower_bound(const uint32_t *L, long long n,
 
 constexpr int kLiteStage = 512;   // longer-row elements a warp stages in shared memory
 
-// The exact similarity of survivor q (the whole warp; w_idx, w_val: the
-// warp's staging area).
+// The sums of one survivor's exact similarity (the whole warp): rows
+// x = [ax, ax+na) and y = [ay, ay+nb) of the CSR; D_out = the intersection
+// size (sets) or D (cosine), and for cosine without have_norms the two
+// squared norms.  The shorter row's elements are spread over the lanes and each
+// is looked up in the longer row by binary search: with the longer row held
+// one element per lane (at most 32 elements: the search steps are shuffles),
+// staged in the warp's shared memory (at most kLiteStage), or read from
+// global memory.  No search touches global memory unless the longer row has
+// more than kLiteStage elements.
 template <bool COSINE>
-__device__ __forceinline__ void lite_exact_pair(const LiteArgs &A, long long q, uint32_t *w_idx, float *w_val) {
+__device__ __forceinline__ void lite_exact_one(const LiteArgs &A, long long ax, long long na, long long ay,
+                                               long long nb, bool have_norms, uint32_t *w_idx, float *w_val,
+                                               long long &D_out, long long &Nx_out, long long &Ny_out) {
     const int lane = threadIdx.x & 31;
-            const uint2 pr = __ldg(A.pairs + q);
-            const long long ax = __ldg(A.indptr + pr.x), ex = __ldg(A.indptr + pr.x + 1);
-            const long long ay = __ldg(A.indptr + pr.y), ey = __ldg(A.indptr + pr.y + 1);
-            long long na = ex - ax, nb = ey - ay;
-            // iterate over the shorter row S, search in the longer row L
-            long long s0 = ax, ns = na, l0 = ay, nl = nb;
-            if (nb < na) { s0 = ay; ns = nb; l0 = ax; nl = na; }
-            const uint32_t *Lidx = A.indices + l0;
-            const float *Lval = COSINE ? A.values + l0 : nullptr;
-            __syncwarp();                                  // the previous pair is done with the stage
-            if (nl <= kLiteStage && ns >= 32) {                 // worth staging: every lane searches
-                for (long long i = lane; i < nl; i += 32) {
-                    w_idx[i] = __ldg(A.indices + l0 + i);
-                    if (COSINE) w_val[i] = __ldg(A.values + l0 + i);
-                }
-                __syncwarp();
-                Lidx = w_idx;
-                if (COSINE) Lval = w_val;
+    // the shorter row S, the longer row L (the sums below do not depend on
+    // which row is which)
+    long long s0 = ax, ns = na, l0 = ay, nl = nb;
+    if (nb < na) { s0 = ay; ns = nb; l0 = ax; nl = na; }
+    long long inter = 0, D = 0, Ns = 0, Nl = 0;
+    if (nl <= 32) {
+        // lane e holds element e of both rows
+        uint32_t si = 0, li = 0;
+        float sv = 0.0f, lv = 0.0f;
+        if (lane < ns) {
+            si = __ldg(A.indices + s0 + lane);
+            if (COSINE) sv = __ldg(A.values + s0 + lane);
+        }
+        if (lane < nl) {
+            li = __ldg(A.indices + l0 + lane);
+            if (COSINE) lv = __ldg(A.values + l0 + lane);
+        }
+        // first position p of L with L[p] >= si: at most 32 candidates, so six
+        // halvings of [lo, hi) settle every lane
+        int lo = 0, hi = (int)nl;
+#pragma unroll
+        for (int it = 0; it < 6; ++it) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t v = __shfl_sync(kFull, li, mid & 31);
+            if (lo < hi) {
+                if (v < si) lo = mid + 1;
+                else hi = mid;
             }
-            double s;
+        }
+        const uint32_t at = __shfl_sync(kFull, li, lo & 31);
+        const bool hit = lane < ns && lo < nl && at == si;
+        if (!COSINE) {
+            inter = __popc(__ballot_sync(kFull, hit));
+        } else {
+            const float atv = __shfl_sync(kFull, lv, lo & 31);
+            D = hit ? fixed_term(sv, atv) : 0;
+            if (!have_norms) {
+                Ns = lane < ns ? fixed_term(sv, sv) : 0;
+                Nl = lane < nl ? fixed_term(lv, lv) : 0;
+            }
+        }
+    } else {
+        const uint32_t *Lidx = A.indices + l0;
+        const float *Lval = COSINE ? A.values + l0 : nullptr;
+        __syncwarp();                                      // the previous survivor is done with the stage
+        if (nl <= kLiteStage) {
+            for (long long i = lane; i < nl; i += 32) {
+                w_idx[i] = __ldg(A.indices + l0 + i);
+                if (COSINE) {
+                    const float v = __ldg(A.values + l0 + i);
+                    w_val[i] = v;
+                    if (!have_norms) Nl += fixed_term(v, v);
+                }
+            }
+            __syncwarp();
+            Lidx = w_idx;
+            if (COSINE) Lval = w_val;
+        } else if (COSINE && !have_norms) {
+#pragma unroll 4
+            for (long long i = lane; i < nl; i += 32) {
+                const float v = __ldg(A.values + l0 + i);
+                Nl += fixed_term(v, v);
+            }
+        }
+#pragma unroll 2
+        for (long long i = lane; i < ns; i += 32) {
+            const uint32_t v = __ldg(A.indices + s0 + i);
+            const long long pos = lower_bound(Lidx, nl, v);
+            const bool hit = pos < nl && Lidx[pos] == v;
             if (!COSINE) {
-                long long inter = 0;
-                for (long long i = lane; i < ns; i += 32) {
-                    const uint32_t v = __ldg(A.indices + s0 + i);
-                    const long long pos = lower_bound(Lidx, nl, v);
-                    inter += (pos < nl && Lidx[pos] == v);
-                }
-                inter = warp_sum(inter);
-                const long long uni = na + nb - inter;
-                s = uni == 0 ? 0.0 : __ddiv_rn((double)inter, (double)uni);
+                inter += hit;
             } else {
-                long long D = 0, Nx = 0, Ny = 0;
-                if (A.norm2 && A.scratch->norm2_valid) {     // the rows' squared norms, formed once per call
-                    Nx = __ldg(A.norm2 + pr.x);
-                    Ny = __ldg(A.norm2 + pr.y);
-                } else {
-#pragma unroll 4
-                    for (long long i = lane; i < na; i += 32) {
-                        const float v = __ldg(A.values + ax + i);
-                        Nx += fixed_term(v, v);
-                    }
-#pragma unroll 4
-                    for (long long i = lane; i < nb; i += 32) {
-                        const float v = __ldg(A.values + ay + i);
-                        Ny += fixed_term(v, v);
-                    }
-                    Nx = warp_sum(Nx);
-                    Ny = warp_sum(Ny);
-                }
-#pragma unroll 4
-                for (long long i = lane; i < ns; i += 32) {
-                    const uint32_t v = __ldg(A.indices + s0 + i);
-                    const long long pos = lower_bound(Lidx, nl, v);
-                    if (pos < nl && Lidx[pos] == v) D += fixed_term(__ldg(A.values + s0 + i), Lval[pos]);
-                }
-                D = warp_sum(D);
-                if (Nx == 0 || Ny == 0) {
-                    s = 0.0;
-                } else {
-                    s = __ddiv_rn(__ll2double_rn(D),
-                                  __dsqrt_rn(__dmul_rn(__ll2double_rn(Nx), __ll2double_rn(Ny))));
-                }
+                const float sv = __ldg(A.values + s0 + i);
+                if (hit) D += fixed_term(sv, Lval[pos]);
+                if (!have_norms) Ns += fixed_term(sv, sv);
             }
-            if (lane == 0) {
-                A.sim[q] = s;
-                A.status[q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
+        }
+    }
+    // the warp's sums (the same in every lane): the intersection size, or D
+    // and the two squared norms (which row is which does not matter: the
+    // similarity uses their product)
+    if (!COSINE) {
+        D_out = nl > 32 ? warp_sum(inter) : inter;
+    } else {
+        D_out = warp_sum(D);
+        if (!have_norms) {
+            Nx_out = warp_sum(Ns);
+            Ny_out = warp_sum(Nl);
+        }
+    }
+}
+
+// The similarity from the sums (one lane per survivor: FP64 is a narrow
+// pipe on this part, so the division and square root run once per survivor
+// rather than once per lane of a warp-wide computation).
+template <bool COSINE>
+__device__ __forceinline__ double lite_similarity(long long D, long long Nx, long long Ny, long long na,
+                                                  long long nb) {
+    if (!COSINE) {
+        const long long uni = na + nb - D;
+        return uni == 0 ? 0.0 : __ddiv_rn((double)D, (double)uni);
+    }
+    if (Nx == 0 || Ny == 0) return 0.0;
+    return __ddiv_rn(__ll2double_rn(D), __dsqrt_rn(__dmul_rn(__ll2double_rn(Nx), __ll2double_rn(Ny))));
+}
+
+// Up to 32 survivors, survivor my_q of lane l (-1: none): their pairs, row
+// bounds and (when formed) squared norms are loaded by all lanes at once, so
+// those dependent loads overlap across the batch; then the warp forms the
+// survivors' sums one after the other, and finally every lane turns its own
+// survivor's sums into the similarity and writes it with the verdict.
+template <bool COSINE>
+__device__ __forceinline__ void lite_batch(const LiteArgs &A, long long my_q, bool have_norms, uint32_t *w_idx,
+                                           float *w_val) {
+    long long ax = 0, ex = 0, ay = 0, ey = 0, nx = 0, ny = 0;
+    if (my_q >= 0) {
+        const uint2 pr = __ldg(A.pairs + my_q);
+        ax = __ldg(A.indptr + pr.x);
+        ex = __ldg(A.indptr + pr.x + 1);
+        ay = __ldg(A.indptr + pr.y);
+        ey = __ldg(A.indptr + pr.y + 1);
+        if (have_norms) {
+            nx = __ldg(A.norm2 + pr.x);
+            ny = __ldg(A.norm2 + pr.y);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    // lane i keeps survivor i's sums
+    long long myD = 0, myNx = nx, myNy = ny;
+    for (unsigned todo = __ballot_sync(kFull, my_q >= 0); todo; todo &= todo - 1) {
+        const int i = __ffs(todo) - 1;
+        const long long a0 = __shfl_sync(kFull, ax, i), a1 = __shfl_sync(kFull, ex, i);
+        const long long b0 = __shfl_sync(kFull, ay, i), b1 = __shfl_sync(kFull, ey, i);
+        long long D = 0, Nx = 0, Ny = 0;
+        lite_exact_one<COSINE>(A, a0, a1 - a0, b0, b1 - b0, have_norms, w_idx, w_val, D, Nx, Ny);
+        if (lane == i) {
+            myD = D;
+            if (!have_norms) {
+                myNx = Nx;
+                myNy = Ny;
             }
+        }
+    }
+    if (my_q >= 0) {
+        const double s = lite_similarity<COSINE>(myD, myNx, myNy, ex - ax, ey - ay);
+        A.sim[my_q] = s;
+        A.status[my_q] = s > A.t ? BLSH_LITE_ACCEPT : BLSH_LITE_REJECT;
+    }
 }
 
 // Each row's sum of fixed_term(v, v) (the squared norm of the exact cosine,
@@ -200,14 +290,18 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
         P = pd < 0 ? 0 : (pd < P ? pd : P);
     }
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     // per warp: the longer row's indices and values, when it has at most
-    // kLiteStage elements (binary searches then run in shared memory)
+    // kLiteStage elements (binary searches then run in shared memory), and
+    // the survivors of the current tile (offsets within it)
     extern __shared__ uint32_t lite_smem[];
-    uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
+    uint32_t *w_idx = lite_smem + warp * 2 * kLiteStage;
     float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
+    uint16_t *w_list = reinterpret_cast<uint16_t *>(lite_smem + (blockDim.x >> 5) * 2 * kLiteStage) + warp * 512;
+    const bool have_norms = COSINE && A.norm2 && A.scratch->norm2_valid;
     // A warp takes kLiteGrab tiles of 512 statuses per grab of the work
-    // counter; a lane reads 16 statuses with one 16-byte load, and the warp
-    // then computes the survivors of the tile one after the other.
+    // counter; a lane reads 16 statuses with one 16-byte load; the tile's
+    // survivors are listed in shared memory and computed 32 at a time.
     for (;;) {
         unsigned long long grab = 0;
         if (lane == 0) grab = atomicAdd(&A.scratch->work2, 1ull);
@@ -229,16 +323,22 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
                 for (int i = 0; i < 16; ++i)
                     if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv |= 1u << i;
             }
-            unsigned lanes = __ballot_sync(kFull, surv != 0);
-            while (lanes) {
-                const int l = __ffs(lanes) - 1;
-                lanes &= lanes - 1;
-                uint32_t bits = __shfl_sync(kFull, surv, l);
-                while (bits) {
-                    const int i = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    lite_exact_pair<COSINE>(A, q0 + 16ll * l + i, w_idx, w_val);
-                }
+            const int c = __popc(surv);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) continue;
+            __syncwarp();                                  // the previous tile's list has been read
+            int slot = incl - c;
+            for (uint32_t b = surv; b; b &= b - 1) w_list[slot++] = (uint16_t)(16 * lane + __ffs(b) - 1);
+            __syncwarp();
+            for (int b0 = 0; b0 < total; b0 += 32) {
+                const long long q = b0 + lane < total ? q0 + w_list[b0 + lane] : -1;
+                lite_batch<COSINE>(A, q, have_norms, w_idx, w_val);
             }
         }
     }
@@ -295,12 +395,17 @@ __global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const
     const unsigned long long total = A.scratch->work3;
     const unsigned long long n = total < BLSH_LITE_QUEUE_CAP ? total : BLSH_LITE_QUEUE_CAP;
     extern __shared__ uint32_t lite_smem[];
+    const int lane = threadIdx.x & 31;
     uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
     float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
+    const bool have_norms = COSINE && A.norm2 && A.scratch->norm2_valid;
+    // 32 consecutive queue entries per warp at a time (one per lane)
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long it = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n;
-         it += nwarps)
-        lite_exact_pair<COSINE>(A, (long long)queue[it], w_idx, w_val);
+    for (unsigned long long base = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += nwarps * 32) {
+        const long long q = base + lane < n ? (long long)queue[base + lane] : -1;
+        lite_batch<COSINE>(A, q, have_norms, w_idx, w_val);
+    }
 }
 
 int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long long *P_dev, int64_t N,
@@ -404,7 +509,8 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
         BLSH_LAUNCHED(ctx, "row_norm2_kernel");
     }
     int occ = 0;
-    const size_t smem = 8 * 2 * kLiteStage * sizeof(uint32_t);   // 32 KB per CTA of 8 warps
+    // per warp of the CTA's 8: the staging area (4 KB) and a tile's survivor list (1 KB)
+    const size_t smem = 8 * (2 * kLiteStage * sizeof(uint32_t) + 512 * sizeof(uint16_t));
     if (values) {
         BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lite_queue_kernel<true>, 256, smem));
         blsh_time_start(ctx, s);

@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 }
             }
         } else {
+            int hj = -1;   // the chunk this lane's pair stopped at in this step (for the histogram)
             if (active) {
-                // The step's words (four, or the plane's two) are counted and
+                // The step's four words (from the rows, or from the plane) are counted and
                 // every completed chunk is tested, recording where each
                 // algorithm stops and why; the outputs of a stop are written
                 // once, after the words.
@@ -207,13 +208,9 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                         if (active) ++j;
                     }
                 };
-                if (PLANE && w == 0) {   // the first two words from the plane (L2-resident)
-                    const uint2 a = __ldg(A.plane + cur_pair.x), b = __ldg(A.plane + cur_pair.y);
-                    words(a.x ^ b.x, a.y ^ b.y, 0u, 0u, 0, 2);
-                    if (active) {
-                        const uint4 c = ldg4(rx), d = ldg4(ry);
-                        words(0u, 0u, c.z ^ d.z, c.w ^ d.w, 2, 4);
-                    }
+                if (PLANE && w == 0) {   // the first four words from the plane (L2-resident)
+                    const uint4 a = __ldg(A.plane + cur_pair.x), b = __ldg(A.plane + cur_pair.y);
+                    words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
                 } else {
                     const uint4 a = ldg4(rx + w), b = ldg4(ry + w);
                     words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
@@ -230,7 +227,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                         // the estimate is an output only for pairs that are kept
                         if (A.est_out && st1 != BLSH_PRUNED)
                             A.est_out[q] = __ldg(A.est_tab + (size_t)j1 * A.est_stride + m1);
-                        atomicAdd(&s_hist[j1], 1u);
+                        hj = j1;
                     }
                 }
                 if (stl >= 0 && g == 0) {
@@ -238,6 +235,12 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                     if (A.ln_used) A.ln_used[q] = (uint16_t)((jl + 1) * A.k);
                 }
             }
+            // the stop histogram: most pairs of a step stop at the same
+            // (first) chunk, so those are added with one shared-memory atomic
+            // per warp; the others one by one (every lane runs this)
+            const unsigned z = __ballot_sync(kFull, hj == 0);
+            if (z && lane == __ffs(z) - 1) atomicAdd(&s_hist[0], (unsigned)__popc(z));
+            if (hj > 0) atomicAdd(&s_hist[hj], 1u);
         }
     };
 
@@ -330,11 +333,11 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             if (s_hist[i]) atomicAdd(A.stop_hist + i, (unsigned long long)s_hist[i]);
 }
 
-// plane[i] = words 0 and 1 of row i
+// plane[i] = words 0..3 of row i
 __global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restrict__ sig, long long N, int W,
-                                                         uint2 *__restrict__ plane) {
+                                                         uint4 *__restrict__ plane) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        plane[i] = __ldg(reinterpret_cast<const uint2 *>(sig + (size_t)i * W));
+        plane[i] = ldg4(sig + (size_t)i * W);
 }
 
 template <int KIND, int G, int U, bool PERSIST, bool PLANE = false>
@@ -419,9 +422,9 @@ int blsh_check_plan(const blsh_plan &plan, int kind, int k) {
 }
 
 // Cosine signatures larger than this do not stay in L2 between the random
-// row reads of the pairs; the first two words of every row then go into a
-// dense plane (8 bytes per object) that does, and the first step of every
-// pair reads them there.
+// row reads of the pairs; the first four words of every row (the first 128
+// hashes) then go into a dense plane (16 bytes per object) that does, and the
+// first step of every pair reads them there.
 constexpr long long kPlaneMinBytes = 64ll << 20;
 
 int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A0, const blsh_plan &plan, cudaStream_t s) {
@@ -431,13 +434,13 @@ int blsh_launch_verify(blsh_ctx *ctx, const VerifyArgs &A0, const blsh_plan &pla
     // the plane lives in the buffer blsh_ctx_reserve allocated; a call with
     // more objects than were reserved reads the rows instead (no allocation
     // here: this is a hot call)
-    if (kind == BLSH_COSINE && A.N * (long long)A.W * 4 > kPlaneMinBytes && ctx->plane_cap >= A.N) {
+    if (kind == BLSH_COSINE && A.W > 4 && A.N * (long long)A.W * 4 > kPlaneMinBytes && ctx->plane_cap >= A.N) {
         const long long blocks = (A.N + 255) / 256, cap = (long long)ctx->sm_count * 8;
         blsh_time_start(ctx, s);
         plane_copy_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(A.sig, A.N, A.W,
-                                                                                  (uint2 *)ctx->plane);
+                                                                                  (uint4 *)ctx->plane);
         BLSH_LAUNCHED(ctx, "plane_copy_kernel");
-        A.plane = (const uint2 *)ctx->plane;
+        A.plane = (const uint4 *)ctx->plane;
     }
     if (plan.mode == BLSH_PLAN_PERSISTENT) return dispatch<true>(ctx, A, plan, kind, s);
     return dispatch<false>(ctx, A, plan, kind, s);

@@ -45,9 +45,9 @@ struct VerifyArgs {
     // objects in need[] (cap_levels == levels: no cap)
     int cap_levels;
     uint8_t *need;
-    // cosine: words 0 and 1 of every row (the first 64 hashes) copied into
-    // a dense plane of N entries, or NULL (set by blsh_launch_verify)
-    const uint2 *plane;
+    // cosine: words 0..3 of every row (the first 128 hashes) copied into a
+    // dense plane of N entries, or NULL (set by blsh_launch_verify)
+    const uint4 *plane;
 };
 
 // BLSH_NEEDS_HASHES (blsh.h): an Algorithm 1 pair that needs hashes beyond

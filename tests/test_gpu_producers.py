@@ -325,6 +325,46 @@ def test_lite_survivors_beyond_queue(B, ctx):
     assert np.array_equal(sim.cpu().numpy(), want.sim)
 
 
+def test_lite_cosine_every_route_with_and_without_norms(B):
+    """Lite's exact cosine through every route of the exact pass: rows of up
+    to 32 terms (held in registers), up to 512 (staged in shared memory) and
+    longer (searched in global memory), paired with each other; 8.5 million
+    survivors, so both the queued pass and the in-place pass run; once with
+    the rows' squared norms formed once per call (a reserved context: the
+    survivors outnumber half the rows) and once formed per pair.
+    Bit-identical similarities."""
+    rng = np.random.default_rng(21)
+    n_obj = 3000
+    kind = rng.random(n_obj)
+    lens = np.where(kind < 0.7, rng.integers(3, 33, n_obj),
+                    np.where(kind < 0.95, rng.integers(33, 513, n_obj), rng.integers(513, 800, n_obj)))
+    rows = [np.sort(rng.choice(5000, int(n), replace=False)).astype(np.uint32) for n in lens]
+    vals = []
+    for n in lens:
+        v = rng.standard_normal(int(n)) * rng.choice([1e-6, 1e-2, 1.0], int(n))
+        vals.append((v / np.linalg.norm(v)).astype(np.float32))
+    csr = synth.CSR(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64), np.concatenate(rows),
+                    np.concatenate(vals), 5000)
+    sig = np.zeros((n_obj, 8), np.uint32)                 # identical signatures: every pair survives pruning
+    pairs = synth.random_pairs(n_obj, 8_500_000, seed=22)
+    p = O.Params(kind=O.COSINE, n_max=256, h=128, t=0.05)
+    want = O.verify_lite(O.tables(p), pairs, sig, csr)
+    assert np.all(want.status != O.PRUNED) and (want.status == O.LITE_ACCEPT).any()
+    ip, ix, val = csr_dev(csr)
+    P = len(pairs)
+    for reserve in (True, False):
+        c = B.Context(0)
+        if reserve:
+            B.blsh_ctx_reserve(c, n_obj)
+        tab = B.blsh_tables_build(c, B.make_params(kind=1, t=0.05, n_max=256, h=128))
+        st = torch.zeros(P, dtype=torch.uint8, device=dev)
+        sim = torch.full((P,), float('nan'), dtype=torch.float64, device=dev)
+        B.blsh_verify_lite(c, tab, t32(pairs), t32(sig), ip, ix, val, st, sim)
+        assert B.blsh_status(c) == 0
+        assert np.array_equal(st.cpu().numpy(), want.status)
+        assert np.array_equal(sim.cpu().numpy(), want.sim)
+
+
 @pytest.mark.parametrize("P", [0, 1, 31, 4097, 1_000_003])
 def test_compact_stable_and_exact(B, ctx, P):
     rng = np.random.default_rng(P)
