@@ -18,7 +18,7 @@ over a 2^24-term vocabulary (Zipf(1.1) term ids, power-law lengths on
 SRP bits over a projection matrix stored as two-byte Gaussian codes generated
 on the device (68.7 GB), banding 16 bits x 5 bands (about 1e9 candidates),
 t = 0.6, eps = 0.03, delta = 0.05, gamma = 0.03, k = 32, Lite h = 128, the
-first 512 bits hashed for every object; candidates verified in device-resident
+first 256 bits hashed for every object; candidates verified in device-resident
 batches sized by free HBM (--batch-pairs caps them).
 
 Output: one JSON line (rank 0).  `value` is candidate pairs verified per
@@ -76,13 +76,22 @@ WORKLOADS = {
                          seed=9, text="verification only: 5,000,000 random 2,048-bit signatures (1.3 GB) and "
                                       "200,000,000 uniform random candidate pairs (HBM-resident, no reuse)"),
     "large-mixed": dict(kind=1, gpu_only=True, n=5_000_000, dim=1 << 24, bits=2048, rows=16, bands=5, t=0.6,
-                        n_max=2048, k=32, h=128, seed=9, r_seed=31, lazy_bits=512,
+                        n_max=2048, k=32, h=128, seed=9, r_seed=31, lazy_bits=256,
                         text="cosine, BayesLSH + Lite on N=5,000,000 tf-idf sparse float32 vectors over a 2^24-term "
                              "vocabulary (Zipf(1.1) ranks, power-law lengths l^-2 on [5, 20,000], 100,000 planted "
                              "near-duplicate groups; drawn on the GPU), 2,048 SRP bits over R as two-byte Gaussian "
                              "codes generated on the device (68.7 GB), banding 16x5, t=0.6, eps=0.03, delta=0.05, "
                              "gamma=0.03, k=32, h=128; candidates verified in device-resident batches sized by "
                              "free HBM"),
+    "large-profile": dict(kind=1, gpu_only=True, n=400_000, dim=1 << 22, bits=512, rows=16, bands=5, t=0.6,
+                          n_max=512, k=32, h=128, seed=9, r_seed=31, lazy_bits=0, n_groups=8000,
+                          text="large-mixed shape for ncu captures: 400,000 tf-idf vectors over 2^22 terms, 512 bits "
+                               "from device-generated two-byte codes (4.3 GB; the code rows the nonzeros touch exceed "
+                               "L2), banding 16x5, t=0.6"),
+    "verify-profile": dict(kind=1, gpu_only=True, n=1_500_000, bits=2048, pairs=50_000_000, t=0.7, n_max=2048,
+                           k=32, h=128, seed=9,
+                           text="verify-large shape for ncu captures: 1,500,000 random 2,048-bit signatures (384 MB) "
+                                "and 50,000,000 random pairs"),
     "jaccard-small": dict(kind=0, n=2000, vocab=10000, n_hashes=256, rows=8, bands=32, t=0.7, n_max=256, k=32,
                           h=64, seed=1,
                           text="jaccard, BayesLSH + Lite: N=2,000 sets over vocab 10,000, lognormal sizes "
@@ -976,8 +985,8 @@ class LargePipeline:
         self.B, self.torch, self.w, self.dev = B, torch, w, device
         t = torch
         self.ctx = B.Context(device.index or 0)
-        self.indptr, self.indices, self.values = synth.large_tfidf_device(n_docs=w["n"], dim=w["dim"],
-                                                                          seed=w["seed"], device=device)
+        self.indptr, self.indices, self.values = synth.large_tfidf_device(
+            n_docs=w["n"], dim=w["dim"], seed=w["seed"], n_groups=w.get("n_groups", 100_000), device=device)
         torch.cuda.synchronize()
         self.N, self.W, self.bits = w["n"], w["bits"] // 32, w["bits"]
         self.nnz = int(self.indptr[-1].item())
@@ -1743,9 +1752,9 @@ def main():
         w["lazy_bits"] = args.lazy_bits
     if args.impl == "reference":
         run_reference(args, w)
-    elif args.workload == "verify-large":
+    elif args.workload in ("verify-large", "verify-profile"):
         run_verify_large(args, w)
-    elif args.workload == "large-mixed":
+    elif args.workload in ("large-mixed", "large-profile"):
         run_large(args, w)
     elif args.workload == "sweep":
         run_sweep(args, w)

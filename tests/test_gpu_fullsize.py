@@ -242,7 +242,7 @@ def large_oracle_view(pipe, w, ids):
 def test_large_mixed_workload_sampled(B, large_pipe):
     """5,000,000 tf-idf vectors over a 2^24-term vocabulary, R generated on
     the device as two-byte codes (68.7 GB), about 1e9 candidates verified by
-    Algorithms 1 and 2 with lazy hashing (the first 512 bits of every object,
+    Algorithms 1 and 2 with lazy hashing (the first 256 bits of every object,
     the rest of the objects of the pairs left open): sampled pairs' outcomes
     of both algorithms recomputed by the oracle from its own full signatures,
     sampled signature rows bit-exact (the prefix of every row, and all bits
