@@ -83,11 +83,11 @@ WORKLOADS = {
                              "codes generated on the device (68.7 GB), banding 16x5, t=0.6, eps=0.03, delta=0.05, "
                              "gamma=0.03, k=32, h=128; candidates verified in device-resident batches sized by "
                              "free HBM"),
-    "large-profile": dict(kind=1, gpu_only=True, n=400_000, dim=1 << 22, bits=512, rows=16, bands=5, t=0.6,
-                          n_max=512, k=32, h=128, seed=9, r_seed=31, lazy_bits=0, n_groups=8000,
-                          text="large-mixed shape for ncu captures: 400,000 tf-idf vectors over 2^22 terms, 512 bits "
-                               "from device-generated two-byte codes (4.3 GB; the code rows the nonzeros touch exceed "
-                               "L2), banding 16x5, t=0.6"),
+    "large-profile": dict(kind=1, gpu_only=True, n=600_000, dim=1 << 19, bits=1024, rows=16, bands=5, t=0.6,
+                          n_max=1024, k=32, h=128, seed=9, r_seed=31, lazy_bits=256, n_groups=10000,
+                          text="large-mixed shape for ncu captures: 600,000 tf-idf vectors over 2^19 terms, 1,024 "
+                               "bits from device-generated two-byte codes (1.1 GB; the code rows the nonzeros touch "
+                               "exceed L2), the 256-bit lazy prefix, banding 16x5, t=0.6"),
     "verify-profile": dict(kind=1, gpu_only=True, n=1_500_000, bits=2048, pairs=50_000_000, t=0.7, n_max=2048,
                            k=32, h=128, seed=9,
                            text="verify-large shape for ncu captures: 1,500,000 random 2,048-bit signatures (384 MB) "

@@ -60,6 +60,9 @@ def lib():
         L.orc_srp_dense.argtypes = [p, i64, i, p, i, p, p]; L.orc_srp_dense.restype = None
         L.orc_lsh_candidates.argtypes = [p, i64, i, i, i, i, p, i64]; L.orc_lsh_candidates.restype = i64
         L.orc_compact.argtypes = [p, i64, C.c_uint32, p]; L.orc_compact.restype = i64
+        L.orc_allpairs_indexed.argtypes = [p, p, p, i64, i64, d, i, p]; L.orc_allpairs_indexed.restype = i
+        L.orc_allpairs_candidates.argtypes = [p, p, p, i64, i64, d, i, p, i64]
+        L.orc_allpairs_candidates.restype = i64
         L.orc_stop_hist.argtypes = [p, i64, i, i, p]; L.orc_stop_hist.restype = None
         L.orc_estimate_mle.argtypes = [i, i, d, p, i64, p, i, p, p, p]; L.orc_estimate_mle.restype = None
         L.orc_fit_beta_prior.argtypes = [p, i64, p]; L.orc_fit_beta_prior.restype = None
@@ -307,6 +310,34 @@ def lsh_candidates(sig: np.ndarray, kind: int, rows: int, bands: int) -> np.ndar
     out = np.zeros((max(n, 1), 2), np.uint32)
     n2 = lib().orc_lsh_candidates(_ptr(sig), N, Wd, kind, rows, bands, _ptr(out), n)
     assert n2 == n
+    return out[:n]
+
+
+def allpairs_indexed(csr, t: float, kind: int) -> np.ndarray:
+    """Per nonzero: 1 if its feature is an indexed feature of its row under
+    AllPairs' prefix filter (features by decreasing frequency; the row's
+    unindexed prefix bounds its contribution below t), else 0.  The
+    comparison algorithm of Section 5.1 (Bayardo et al. 2007)."""
+    indptr = _c(csr.indptr, np.int64); idx = _c(csr.indices, np.uint32)
+    val = None if kind == JACCARD else _c(csr.values, np.float32)
+    out = np.zeros(max(int(indptr[-1]), 1), np.uint8)
+    if lib().orc_allpairs_indexed(_ptr(indptr), _ptr(idx), _ptr(val), len(indptr) - 1, int(csr.dim), float(t),
+                                  kind, _ptr(out)) != 0:
+        raise MemoryError("orc_allpairs_indexed")
+    return out[: int(indptr[-1])]
+
+
+def allpairs_candidates(csr, t: float, kind: int) -> np.ndarray:
+    """AllPairs-style candidates: distinct pairs (x, y), x < y, with an indexed
+    feature of x present in y, sorted by (x, y) (uint32 [P][2])."""
+    indptr = _c(csr.indptr, np.int64); idx = _c(csr.indices, np.uint32)
+    val = None if kind == JACCARD else _c(csr.values, np.float32)
+    N = len(indptr) - 1
+    n = lib().orc_allpairs_candidates(_ptr(indptr), _ptr(idx), _ptr(val), N, int(csr.dim), float(t), kind, None, 0)
+    if n < 0:
+        raise MemoryError("orc_allpairs_candidates")
+    out = np.zeros((max(n, 1), 2), np.uint32)
+    lib().orc_allpairs_candidates(_ptr(indptr), _ptr(idx), _ptr(val), N, int(csr.dim), float(t), kind, _ptr(out), n)
     return out[:n]
 
 

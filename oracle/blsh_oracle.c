@@ -608,6 +608,142 @@ int64_t orc_lsh_candidates(const uint32_t *sig, int64_t N, int sig_words, int ki
 }
 
 /* ------------------------------------------------------------------------- */
+/* AllPairs-style candidate generation by prefix filtering (the candidate      */
+/* generator Section 5.1 pairs with BayesLSH besides LSH: Bayardo, Ma and      */
+/* Srikant, "Scaling up all pairs similarity search", WWW 2007).               */
+/*                                                                             */
+/* Features are ordered by decreasing document frequency (ties: smaller id).   */
+/* Walking a row's features in that order, a running bound b grows by          */
+/* |x_f| * maxabs_f (cosine; maxabs_f = the largest |weight| of f over all      */
+/* rows), or by 1 per element (Jaccard sets); a feature is indexed once b,     */
+/* including it, reaches the row's threshold: t - 1e-9 (cosine), or            */
+/* alpha = ceil(t |x| - 1e-9) elements (Jaccard: J(x,y) >= t needs            */
+/* |x n y| >= t |x|).  The unindexed prefix U(x) then bounds what it can add    */
+/* to any similarity: below t (cosine, sum over U of x_f y_f <= sum |x_f|       */
+/* maxabs_f), or fewer than alpha common elements (Jaccard), so a pair         */
+/* reaching t shares an indexed feature of x.  Rows of more than 4096 elements */
+/* index every feature.  Candidates: the distinct pairs (x, y), x < y, with    */
+/* an indexed feature of x present in y, sorted by (x, y).                     */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_AP_LONG_ROW 4096
+
+static const int64_t *g_ap_df;
+
+static int orc_ap_cmp(const void *pa, const void *pb)
+{
+    uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
+    if (g_ap_df[a] != g_ap_df[b]) return g_ap_df[a] > g_ap_df[b] ? -1 : 1;
+    return a < b ? -1 : (a > b);
+}
+
+/* indexed[e] = 1 if nonzero e's feature is an indexed feature of its row.
+ * values may be NULL for sets (kind == ORC_JACCARD).  Returns 0, or -1 on
+ * allocation failure. */
+int orc_allpairs_indexed(const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
+                         int64_t dim, double t, int kind, uint8_t *indexed)
+{
+    int64_t *df = (int64_t *)calloc((size_t)(dim > 0 ? dim : 1), sizeof(int64_t));
+    double *maxabs = (double *)calloc((size_t)(dim > 0 ? dim : 1), sizeof(double));
+    uint32_t *feat = (uint32_t *)malloc(sizeof(uint32_t) * ORC_AP_LONG_ROW);
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (dim > 0 ? dim : 1));
+    if (!df || !maxabs || !feat || !pos) { free(df); free(maxabs); free(feat); free(pos); return -1; }
+    int64_t nnz = indptr[N];
+    for (int64_t e = 0; e < nnz; e++) {
+        df[indices[e]]++;
+        if (kind == ORC_COSINE) {
+            double a = fabs((double)values[e]);
+            if (a > maxabs[indices[e]]) maxabs[indices[e]] = a;
+        }
+    }
+    g_ap_df = df;
+    for (int64_t x = 0; x < N; x++) {
+        int64_t s = indptr[x], n = indptr[x + 1] - s;
+        if (n > ORC_AP_LONG_ROW) {
+            for (int64_t e = s; e < s + n; e++) indexed[e] = 1;
+            continue;
+        }
+        for (int64_t i = 0; i < n; i++) {
+            feat[i] = indices[s + i];
+            pos[indices[s + i]] = s + i;
+        }
+        qsort(feat, (size_t)n, sizeof(uint32_t), orc_ap_cmp);
+        double b = 0.0;
+        double alpha = ceil(t * (double)n - 1e-9);
+        for (int64_t i = 0; i < n; i++) {
+            int64_t e = pos[feat[i]];
+            if (kind == ORC_COSINE) {
+                b += fabs((double)values[e]) * maxabs[feat[i]];
+                indexed[e] = b >= t - 1e-9;
+            } else {
+                b += 1.0;
+                indexed[e] = b >= alpha;
+            }
+        }
+    }
+    free(df); free(maxabs); free(feat); free(pos);
+    return 0;
+}
+
+/* The candidate pairs (see above) into out [cap][2], sorted by (x, y); returns
+ * their number (which may exceed cap: only the count is then meaningful), or
+ * -1 on allocation failure. */
+int64_t orc_allpairs_candidates(const int64_t *indptr, const uint32_t *indices, const float *values, int64_t N,
+                                int64_t dim, double t, int kind, uint32_t *out, int64_t cap)
+{
+    int64_t nnz = indptr[N];
+    uint8_t *ix = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    int64_t *start = (int64_t *)calloc((size_t)dim + 1, sizeof(int64_t));
+    if (!ix || !start || orc_allpairs_indexed(indptr, indices, values, N, dim, t, kind, ix) != 0) {
+        free(ix); free(start); return -1;
+    }
+    /* inverted lists of the indexed features: rows in increasing order */
+    for (int64_t e = 0; e < nnz; e++)
+        if (ix[e]) start[indices[e] + 1]++;
+    for (int64_t f = 0; f < dim; f++) start[f + 1] += start[f];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (dim > 0 ? dim : 1));
+    uint32_t *rows = (uint32_t *)malloc(sizeof(uint32_t) * (start[dim] > 0 ? start[dim] : 1));
+    uint32_t *seen = (uint32_t *)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
+    if (!fill || !rows || !seen || !cand) {
+        free(ix); free(start); free(fill); free(rows); free(seen); free(cand); return -1;
+    }
+    for (int64_t f = 0; f < dim; f++) fill[f] = start[f];
+    for (int64_t x = 0; x < N; x++)
+        for (int64_t e = indptr[x]; e < indptr[x + 1]; e++)
+            if (ix[e]) rows[fill[indices[e]]++] = (uint32_t)x;
+    for (int64_t x = 0; x < N; x++) seen[x] = UINT32_MAX;
+    int64_t n_all = 0, cap_all = 1024;
+    uint32_t *all = (uint32_t *)malloc(sizeof(uint32_t) * 2 * cap_all);
+    if (!all) { free(ix); free(start); free(fill); free(rows); free(seen); free(cand); return -1; }
+    for (int64_t y = 0; y < N; y++) {
+        int64_t nc = 0;
+        for (int64_t e = indptr[y]; e < indptr[y + 1]; e++) {
+            uint32_t f = indices[e];
+            for (int64_t i = start[f]; i < start[f + 1] && rows[i] < (uint32_t)y; i++) {
+                uint32_t x = rows[i];
+                if (seen[x] != (uint32_t)y) { seen[x] = (uint32_t)y; cand[nc++] = x; }
+            }
+        }
+        for (int64_t i = 0; i < nc; i++) {
+            if (n_all == cap_all) {
+                cap_all *= 2;
+                uint32_t *nw = (uint32_t *)realloc(all, sizeof(uint32_t) * 2 * cap_all);
+                if (!nw) { free(ix); free(start); free(fill); free(rows); free(seen); free(cand); free(all); return -1; }
+                all = nw;
+            }
+            all[2 * n_all] = cand[i];
+            all[2 * n_all + 1] = (uint32_t)y;
+            n_all++;
+        }
+    }
+    qsort(all, (size_t)n_all, 2 * sizeof(uint32_t), orc_pair_cmp);
+    for (int64_t i = 0; i < n_all && i < cap; i++) { out[2 * i] = all[2 * i]; out[2 * i + 1] = all[2 * i + 1]; }
+    free(ix); free(start); free(fill); free(rows); free(seen); free(cand); free(all);
+    return n_all;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Output: the retained pair indices in input order, and the histogram of the  */
 /* chunk at which each pair stopped (the paper's "candidates left vs hashes").  */
 /* ------------------------------------------------------------------------- */
