@@ -621,9 +621,14 @@ int64_t orc_lsh_candidates(const uint32_t *sig, int64_t N, int sig_words, int ki
 /* |x n y| >= t |x|).  The unindexed prefix U(x) then bounds what it can add    */
 /* to any similarity: below t (cosine, sum over U of x_f y_f <= sum |x_f|       */
 /* maxabs_f), or fewer than alpha common elements (Jaccard), so a pair         */
-/* reaching t shares an indexed feature of x.  Rows of more than 4096 elements */
-/* index every feature.  Candidates: the distinct pairs (x, y), x < y, with    */
-/* an indexed feature of x present in y, sorted by (x, y).                     */
+/* reaching t shares an indexed feature of x.  The cosine bound is summed in    */
+/* fixed point, independently of the order of the terms: each term is the      */
+/* exact FP64 product |x_f| maxabs_f scaled by 2^48 and rounded to an integer  */
+/* (capped at 2^50, far above any threshold), and the threshold is             */
+/* ceil((t - 1e-9) 2^48); the rounding (below 2^-49 per term) is far inside    */
+/* the 1e-9 margin.  Rows of more than 4096 elements index every feature.      */
+/* Candidates: the distinct pairs (x, y), x < y, with an indexed feature of x  */
+/* present in y, sorted by (x, y).                                             */
 /* ------------------------------------------------------------------------- */
 
 #define ORC_AP_LONG_ROW 4096
@@ -668,16 +673,20 @@ int orc_allpairs_indexed(const int64_t *indptr, const uint32_t *indices, const f
             pos[indices[s + i]] = s + i;
         }
         qsort(feat, (size_t)n, sizeof(uint32_t), orc_ap_cmp);
-        double b = 0.0;
-        double alpha = ceil(t * (double)n - 1e-9);
+        const double two48 = 281474976710656.0;
+        const int64_t thr = (int64_t)ceil((t - 1e-9) * two48);
+        const double alpha = ceil(t * (double)n - 1e-9);
+        int64_t b = 0;
         for (int64_t i = 0; i < n; i++) {
             int64_t e = pos[feat[i]];
             if (kind == ORC_COSINE) {
-                b += fabs((double)values[e]) * maxabs[feat[i]];
-                indexed[e] = b >= t - 1e-9;
+                int64_t w = llrint(fabs((double)values[e]) * maxabs[feat[i]] * two48);
+                if (w > ((int64_t)1 << 50)) w = (int64_t)1 << 50;
+                b += w;
+                indexed[e] = b >= thr;
             } else {
-                b += 1.0;
-                indexed[e] = b >= alpha;
+                b += 1;
+                indexed[e] = (double)b >= alpha;
             }
         }
     }
