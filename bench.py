@@ -68,6 +68,11 @@ WORKLOADS = {
                              text="cosine-small with the projection matrix stored as two-byte codes "
                                   "(Section 4.3): N=20,000 tf-idf vectors, dim 100,000, 2,048 SRP bits, "
                                   "banding 8x35, t=0.7"),
+    "allpairs-cosine": dict(kind=1, n=20000, dim=100000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
+                            n_max=2048, k=32, h=128, seed=2, lazy_bits=512, candidates="allpairs",
+                            text="cosine-small's 20,000 tf-idf vectors with candidates from AllPairs-style prefix "
+                                 "filtering (Section 5.1's other candidate generator) instead of LSH banding, "
+                                 "then BayesLSH + Lite over them: 2,048 SRP bits, t=0.7"),
     "cosine-profile": dict(kind=1, n=6000, dim=30000, mean_nnz=80.0, bits=2048, rows=8, bands=35, t=0.7,
                            n_max=2048, k=32, h=128, seed=2,
                            text="cosine-small shape at 6,000 vectors over dim 30,000 (R = 245 MB > L2), for "
@@ -185,16 +190,36 @@ class Pipeline:
         t0 = time.perf_counter()
         self.tab = B.blsh_tables_build(self.ctx, params)
         self.tables_ms = (time.perf_counter() - t0) * 1e3
-        self.ws = t.zeros(B.blsh_lsh_candidates_workspace(N, self.kind, w["rows"], w["bands"]), dtype=t.uint8,
-                          device=device)
         self.n_pairs = t.zeros(1, dtype=t.int64, device=device)
-        # size the candidate buffer with a count-only pass
+        self.allpairs = w.get("candidates") == "allpairs"
+        self.dim = objs.dim
+        self.nnz = int(objs.indptr[-1])
         self.hash()
-        B.blsh_lsh_candidates(self.ctx, self.sig, self.kind, w["rows"], w["bands"], None, self.n_pairs, self.ws)
-        B.blsh_status(self.ctx)
+        if self.allpairs:
+            # candidates by prefix filtering: a count-only call sizes the key
+            # buffer, a full one the pair count
+            self.n_dups = t.zeros(1, dtype=t.int64, device=device)
+            ws0 = t.zeros(B.blsh_allpairs_workspace(N, self.nnz, self.dim, 0), dtype=t.uint8, device=device)
+            B.blsh_allpairs_candidates(self.ctx, self.indptr, self.indices, self.values, self.dim, w["t"], self.kind,
+                                       None, self.n_pairs, ws0, 0, self.n_dups, nnz=self.nnz)
+            B.blsh_status(self.ctx)
+            self.max_dups = int(self.n_dups.item())
+            del ws0
+            self.ws = t.zeros(B.blsh_allpairs_workspace(N, self.nnz, self.dim, self.max_dups), dtype=t.uint8,
+                              device=device)
+            self.pairs = t.zeros((max(self.max_dups, 1), 2), dtype=t.int32, device=device)
+            self.band()
+            B.blsh_status(self.ctx)
+        else:
+            self.ws = t.zeros(B.blsh_lsh_candidates_workspace(N, self.kind, w["rows"], w["bands"]), dtype=t.uint8,
+                              device=device)
+            # size the candidate buffer with a count-only pass
+            B.blsh_lsh_candidates(self.ctx, self.sig, self.kind, w["rows"], w["bands"], None, self.n_pairs, self.ws)
+            B.blsh_status(self.ctx)
         self.P = int(self.n_pairs.item())
         cap = self.P + 1024
-        self.pairs = t.zeros((cap, 2), dtype=t.int32, device=device)
+        if not self.allpairs:
+            self.pairs = t.zeros((cap, 2), dtype=t.int32, device=device)
         self.status = t.zeros(cap, dtype=t.uint8, device=device)
         self.n_used = t.zeros(cap, dtype=t.int16, device=device)
         self.m = t.zeros(cap, dtype=t.int16, device=device)
@@ -251,6 +276,11 @@ class Pipeline:
 
     def band(self):
         w = self.w
+        if self.allpairs:
+            self.B.blsh_allpairs_candidates(self.ctx, self.indptr, self.indices, self.values, self.dim, w["t"],
+                                            self.kind, self.pairs, self.n_pairs, self.ws, self.max_dups,
+                                            nnz=self.nnz)
+            return
         self.B.blsh_lsh_candidates(self.ctx, self.sig, self.kind, w["rows"], w["bands"], self.pairs, self.n_pairs,
                                    self.ws)
 
@@ -523,6 +553,29 @@ def kernel_work(B, pipe, w, objs, st, nu, lst, need):
     work[emit + " (write pass)"] = (n * (kb + 4 + 8) + obj_rows + P * 8, "B")
     for ps in (" (count pass)", " (write pass)"):    # the unstaged form
         work["emit_kernel" + ps] = work[emit + ps]
+    if getattr(pipe, "allpairs", False):
+        # prefix filtering instead of banding: per nonzero its index and value
+        # read by the statistics, the prefix pass (flag written) and the index
+        # keys (8 B written); two stable radix sorts of (8 B key + 4 B value)
+        # items, read and written once per 8-bit pass; the candidate keys
+        # (8 B per key with duplicates) written once, then the distinct pairs
+        nnz, dim, dups = pipe.nnz, pipe.dim, pipe.max_dups
+        xb = max(1, int(N).bit_length())
+        p_idx = (xb + max(1, int(dim).bit_length()) + 1 + 7) // 8
+        p_key = (32 + xb + 1 + 7) // 8
+        for name in list(work):
+            if name.startswith(("band_keys", "digit_", "emit_", "class_id")):
+                del work[name]
+        work["ap_stats_kernel"] = (nnz * 8 + dim * 8, "B")
+        work["ap_prefix_warp_kernel"] = (nnz * 9, "B")
+        work["ap_prefix_cta_kernel"] = (nnz * 9, "B")
+        work["ap_index_keys_kernel"] = (nnz * (5 + 8) + N * 16, "B")
+        work["digit_hist_kernel"] = (p_idx * nnz * 8 + p_key * dups * 8, "B")
+        work["digit_scatter_kernel"] = (p_idx * 2 * nnz * 12 + p_key * 2 * dups * 12, "B")
+        work["ap_emit_kernel (count pass)"] = (nnz * 4 + N * 24, "B")
+        work["ap_emit_kernel (write pass)"] = (nnz * 4 + N * 24 + dups * 16, "B")
+        work["ap_mark_kernel"] = (dups * 12, "B")
+        work["ap_write_kernel"] = (dups * 16 + P * 8, "B")
     n_keep = int(kept.sum())
     work["compact_count"] = ((2 if pipe.with_lite else 1) * P, "B")
     work["compact_write"] = ((2 if pipe.with_lite else 1) * P + 8 * n_keep, "B")

@@ -315,6 +315,41 @@ BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, 
                         int32_t rows, int32_t bands, uint32_t *pairs, int64_t cap, int64_t *n_pairs,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* Candidate generation by prefix filtering, the AllPairs method (Bayardo, Ma
+ * and Srikant, WWW 2007) that Section 5.1 pairs with BayesLSH as the other
+ * source of candidates.  Features are ordered by decreasing document
+ * frequency (ties: smaller id); walking a row's features in that order, a
+ * running bound grows by |x_f| * maxabs_f (cosine: maxabs_f = the largest
+ * |weight| of f over all rows; the sum in fixed point, each exact product
+ * scaled by 2^48 and rounded to an integer, capped at 2^50) or by 1 (sets),
+ * and a feature is indexed once the bound including it reaches the row's
+ * threshold (cosine: ceil((t - 1e-9) 2^48); sets: ceil(t |x| - 1e-9)
+ * elements, since J >= t needs |x n y| >= t |x|).  Rows of more than 4096
+ * elements index every feature.  The candidates are the distinct pairs
+ * (x, y), x < y, such that some indexed feature of x occurs in y; every
+ * pair whose cosine (non-negative weights) or Jaccard similarity reaches t
+ * is among them.  They are written to pairs uint32 [cap][2] in increasing
+ * order of (x, y), their number to *n_pairs (device int64).
+ * Rows: indptr int64 [N+1] (indptr[N] = nnz, passed from the host too),
+ * indices uint32 sorted and distinct within a row, features < dim; values
+ * float [nnz] for cosine, NULL for sets.
+ * The pairs are formed by sorting the candidate keys of every (row, shared
+ * indexed feature), duplicates included: max_dups is the capacity of that
+ * key buffer (a part of the workspace).  A call with cap = 0 is a count-only
+ * call: it writes the number of such keys to *n_dups (device int64, may be
+ * NULL otherwise) and 0 to *n_pairs; size max_dups from it and call again.
+ * If the keys exceed max_dups, *n_pairs is 0 and blsh_status reports
+ * BLSH_ETRUNC; if the distinct pairs exceed cap, only cap are written and
+ * blsh_status reports BLSH_ETRUNC.  workspace: blsh_allpairs_workspace(N,
+ * nnz, dim, max_dups) bytes (max_dups = 0 for a count-only call), 256-byte
+ * aligned.  Asynchronous on `stream` (no host synchronisation). */
+BLSH_API int blsh_allpairs_workspace(int64_t N, int64_t nnz, int64_t dim, int64_t max_dups, size_t *bytes);
+BLSH_API int blsh_allpairs_candidates(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indices,
+                                      const float *values, int64_t N, int64_t nnz, int64_t dim, double t,
+                                      int32_t kind,
+                                      int64_t max_dups, uint32_t *pairs, int64_t cap, int64_t *n_pairs,
+                                      int64_t *n_dups, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- verification: Algorithms 1 and 2 ------------------------------------ */
 
 /* Algorithm 1 (BayesLSH) for pairs uint32 [P][2] (x, y) over signatures

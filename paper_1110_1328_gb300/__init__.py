@@ -82,6 +82,9 @@ def lib():
             "blsh_srp_dense_workspace": ([i64, i32, i32, p], C.c_int),
             "blsh_lsh_candidates_workspace": ([i64, i32, i32, i32, p], C.c_int),
             "blsh_lsh_candidates": ([p, p, i64, i32, i32, i32, i32, p, i64, p, p, sz, p], C.c_int),
+            "blsh_allpairs_workspace": ([i64, i64, i64, i64, p], C.c_int),
+            "blsh_allpairs_candidates": ([p, p, p, p, i64, i64, i64, C.c_double, i32, i64, p, i64, p, p, p, sz, p],
+                                         C.c_int),
             "blsh_verify": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_plan": ([p, p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p], C.c_int),
             "blsh_verify_lite": ([p, p, p, i64, p, p, i64, i32, p, p, p, p, p, p, p], C.c_int),
@@ -400,6 +403,30 @@ def blsh_lsh_candidates(ctx: Context, sig, kind: int, rows: int, bands: int, pai
                                    _dev(pairs) if cap else None, cap, _dev(n_pairs, torch.int64),
                                    _dev(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream))
+    _check(rc, ctx)
+
+
+def blsh_allpairs_workspace(N: int, nnz: int, dim: int, max_dups: int) -> int:
+    n = C.c_size_t()
+    _check(lib().blsh_allpairs_workspace(N, nnz, dim, max_dups, C.byref(n)))
+    return n.value
+
+
+def blsh_allpairs_candidates(ctx: Context, indptr, indices, values, dim: int, t: float, kind: int, pairs, n_pairs,
+                             workspace, max_dups: int = 0, n_dups=None, nnz: int | None = None, stream=None):
+    """AllPairs-style prefix-filter candidates (pairs=None: count-only call,
+    n_dups receives the number of candidate keys to size max_dups).  nnz:
+    the nonzero count (default: the length of indices)."""
+    N = indptr.numel() - 1
+    if nnz is None:
+        nnz = indices.numel()
+    cap = pairs.shape[0] if pairs is not None else 0
+    idx = indices if indices.numel() else torch.zeros(1, dtype=torch.int32, device=indptr.device)
+    rc = lib().blsh_allpairs_candidates(ctx.handle, _dev(indptr, torch.int64), _dev(idx),
+                                        None if values is None else _dev(values, torch.float32), N, int(nnz), int(dim),
+                                        float(t), int(kind), int(max_dups), _dev(pairs) if cap else None, cap,
+                                        _dev(n_pairs, torch.int64), _dev(n_dups, torch.int64), _dev(workspace),
+                                        workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, ctx)
 
 

@@ -72,11 +72,13 @@ struct blsh_tables {
     void *dev = nullptr;     // one allocation holding the arrays below
     size_t bytes = 0;
     int32_t *min_matches = nullptr;   // [levels]
+    int32_t *conc_lo = nullptr;       // [levels]: smallest concentrated m (n+1 if none)
+    bool conc_upper = false;          // every level's concentrated m form the range [conc_lo, n]
     uint32_t *conc_bits = nullptr;    // [levels][conc_words]
     float *est = nullptr;             // [levels][n_max+1]
     double *prune_prob = nullptr;     // [levels][n_max+1]
     double *conc_prob = nullptr;      // [levels][n_max+1]
-    int *flags = nullptr;             // [2]: near ties, non-finite / non-monotone
+    int *flags = nullptr;             // [3]: near ties, non-finite / non-monotone, conc not an upper range
 };
 
 // Records `fmt` as the context's last error and returns `code`.

@@ -248,6 +248,35 @@ __device__ __noinline__ double srp_recheck_fp64(const uint32_t *__restrict__ ind
     return d;
 }
 
+// Paired FP32 arithmetic (two lanes of a 64-bit register per instruction,
+// each an IEEE single-precision operation rounded to nearest): the two-byte
+// projection's decode, sum and magnitude for two columns at a time.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long p, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// The two codes of a 32-bit word as the pair (2^23 + low code, 2^23 + high
+// code): each code's bits placed under the exponent of 2^23.
+__device__ __forceinline__ unsigned long long f2_codes(uint32_t w) {
+    return f2_pack(__int_as_float((int)__byte_perm(w, 0x4b00u, 0x5410)),
+                   __int_as_float((int)__byte_perm(w, 0x4b00u, 0x5432)));
+}
+
 // The same computation when bits is a multiple of 128: thread t owns the
 // groups of four columns t, t+T, ... of each row of R (bits 4t..4t+3,
 // 4(t+T).., ...), so every load moves 16 bytes (float R) or 8 bytes (RT =
@@ -279,7 +308,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
     const int words = bits >> 5;
     unsigned long long rechecked = 0, zeros = 0, bad = 0;
     for (long long item = blockIdx.x; item < N * pieces; item += gridDim.x) {
-        const long long row = item / pieces;
+        const long long row = pieces == 1 ? item : item / pieces;   // (a 64-bit division is a long call)
         const int col0 = col_first + (int)(item - row * pieces) * 4 * V * T;
         if (row_mask && !row_mask[row]) continue;
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
@@ -304,6 +333,39 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                     my_ix = 0;
                     my_v = 0.0f;
                 }
+            }
+            if constexpr (Q16) {
+                // the decoded value of code q is (q - 2^15) 2^-12: (2^23 + q) - (2^23 + 2^15),
+                // exact, with the sums kept in units of 2^-12
+                const unsigned long long off2 = f2_pack(-8421376.0f, -8421376.0f);
+                for (int u0 = 0; u0 < cnt; u0 += NB) {
+                    uint2 qb[NB][V];
+                    float vb[NB];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                        vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
+                        const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
+#pragma unroll
+                        for (int g = 0; g < V; ++g) qb[b][g] = __ldg(Rrow + g * T);
+                    }
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const unsigned long long v2 = f2_pack(vb[b], vb[b]);
+                        const unsigned long long av2 = f2_pack(fabsf(vb[b]), fabsf(vb[b]));
+#pragma unroll
+                        for (int g = 0; g < V; ++g) {
+                            const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
+                            const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
+                            float *a = acc + 4 * g, *mg = mag + 4 * g;
+                            f2_unpack(f2_fma(v2, d01, f2_pack(a[0], a[1])), a[0], a[1]);
+                            f2_unpack(f2_fma(v2, d23, f2_pack(a[2], a[3])), a[2], a[3]);
+                            f2_unpack(f2_fma(av2, d01 & 0x7fffffff7fffffffull, f2_pack(mg[0], mg[1])), mg[0], mg[1]);
+                            f2_unpack(f2_fma(av2, d23 & 0x7fffffff7fffffffull, f2_pack(mg[2], mg[3])), mg[2], mg[3]);
+                        }
+                    }
+                }
+                continue;
             }
             for (int u0 = 0; u0 < cnt; u0 += NB) {
                 float4 r[NB][V];

@@ -399,11 +399,15 @@ __global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const
     uint32_t *w_idx = lite_smem + (threadIdx.x >> 5) * 2 * kLiteStage;
     float *w_val = reinterpret_cast<float *>(w_idx + kLiteStage);
     const bool have_norms = COSINE && A.norm2 && A.scratch->norm2_valid;
-    // 32 consecutive queue entries per warp at a time (one per lane)
+    // bs consecutive queue entries per warp at a time (one per lane): 32, or
+    // fewer when the survivors are too few to give every warp a full batch
+    // (a warp computes its batch's survivors one after the other)
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long base = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
-         base += nwarps * 32) {
-        const long long q = base + lane < n ? (long long)queue[base + lane] : -1;
+    unsigned long long bs = (n + nwarps - 1) / nwarps;
+    bs = bs < 1 ? 1 : (bs > 32 ? 32 : bs);
+    for (unsigned long long base = (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * bs; base < n;
+         base += nwarps * bs) {
+        const long long q = lane < bs && base + lane < n ? (long long)queue[base + lane] : -1;
         lite_batch<COSINE>(A, q, have_norms, w_idx, w_val);
     }
 }
@@ -450,6 +454,8 @@ extern "C" int blsh_verify_lite(blsh_ctx *ctx, const blsh_tables *tab, const uin
     A.est_stride = p.n_max + 1;
     A.min_matches = tab->min_matches;
     A.conc_bits = tab->conc_bits;
+    A.conc_lo = tab->conc_lo;
+    A.conc_upper = tab->conc_upper ? 1 : 0;
     A.est_tab = tab->est;
     A.status = status;
     A.n_used = n_used;

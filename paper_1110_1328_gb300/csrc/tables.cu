@@ -84,9 +84,10 @@ struct TabArgs {
     double t, eps, delta, gamma, alpha, beta;
     int32_t *min_matches;
     uint32_t *conc_bits;
+    int32_t *conc_lo;     // [levels]: the smallest concentrated m (n+1 if none)
     float *est;
     double *prune_prob, *conc_prob;
-    int *flags;
+    int *flags;           // [3]: near ties, non-finite / non-monotone, a level whose concentrated m are no upper range
 };
 
 __device__ double mode_estimate(const TabArgs &A, int m, int n) {
@@ -173,6 +174,17 @@ __global__ void __launch_bounds__(256) build_tables_kernel(TabArgs A) {
         }
         A.conc_bits[(size_t)j * A.conc_words + w] = word;
     }
+    // the smallest concentrated m, and whether every m from it up to n is
+    // concentrated (an upper range: the verification kernel then tests m >= it
+    // instead of reading the bitmap)
+    if (threadIdx.x == 0) {
+        int lo = n + 1;
+        for (int m = mm; m <= n; ++m)
+            if (bit[m]) { lo = m; break; }
+        for (int m = lo; m <= n; ++m)
+            if (!bit[m]) { atomicOr(&A.flags[2], 1); break; }
+        A.conc_lo[j] = lo;
+    }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -203,12 +215,13 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     tab->conc_words = (p->n_max + 1 + 31) / 32;
     const size_t L = tab->levels, W = p->n_max + 1;
     const size_t o_mm = 0;
-    const size_t o_conc = align256(o_mm + L * sizeof(int32_t));
+    const size_t o_lo = align256(o_mm + L * sizeof(int32_t));
+    const size_t o_conc = align256(o_lo + L * sizeof(int32_t));
     const size_t o_est = align256(o_conc + L * tab->conc_words * sizeof(uint32_t));
     const size_t o_pr = align256(o_est + L * W * sizeof(float));
     const size_t o_cp = align256(o_pr + L * W * sizeof(double));
     const size_t o_fl = align256(o_cp + L * W * sizeof(double));
-    tab->bytes = align256(o_fl + 2 * sizeof(int));
+    tab->bytes = align256(o_fl + 3 * sizeof(int));
     cudaError_t e = cudaMalloc(&tab->dev, tab->bytes);
     if (e != cudaSuccess) {
         delete tab;
@@ -216,6 +229,7 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     }
     char *base = (char *)tab->dev;
     tab->min_matches = (int32_t *)(base + o_mm);
+    tab->conc_lo = (int32_t *)(base + o_lo);
     tab->conc_bits = (uint32_t *)(base + o_conc);
     tab->est = (float *)(base + o_est);
     tab->prune_prob = (double *)(base + o_pr);
@@ -224,10 +238,10 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     TabArgs A;
     A.kind = p->kind; A.k = p->k; A.n_max = p->n_max; A.levels = tab->levels; A.conc_words = tab->conc_words;
     A.t = p->t; A.eps = p->eps; A.delta = p->delta; A.gamma = p->gamma; A.alpha = p->alpha; A.beta = p->beta;
-    A.min_matches = tab->min_matches; A.conc_bits = tab->conc_bits; A.est = tab->est;
+    A.min_matches = tab->min_matches; A.conc_bits = tab->conc_bits; A.conc_lo = tab->conc_lo; A.est = tab->est;
     A.prune_prob = tab->prune_prob; A.conc_prob = tab->conc_prob; A.flags = tab->flags;
-    int flags[2] = {0, 0};
-    e = cudaMemsetAsync(tab->flags, 0, 2 * sizeof(int), s);
+    int flags[3] = {0, 0, 0};
+    e = cudaMemsetAsync(tab->flags, 0, 3 * sizeof(int), s);
     if (e == cudaSuccess) {
         blsh_time_start(ctx, s);
         build_tables_kernel<<<tab->levels, 256, 0, s>>>(A);
@@ -245,6 +259,7 @@ extern "C" int blsh_tables_build(blsh_ctx *ctx, const blsh_params *p, blsh_table
     }
     tab->near_ties = flags[0];
     tab->numeric_bad = flags[1];
+    tab->conc_upper = flags[2] == 0;
     *out = tab;
     if (flags[1])
         return blsh_fail(ctx, BLSH_ENUMERIC, "inference table: %s",

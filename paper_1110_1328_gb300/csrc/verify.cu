@@ -30,7 +30,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
-template <int KIND, int G, int U, bool PERSIST, bool PLANE>
+template <int KIND, int G, int U, bool PERSIST, bool PLANE, bool FAST = false>
 __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     // minMatches is staged in shared memory; the concentration bitmap (up to
     // tens of KB, consulted only by pairs that pass the pruning test) is
@@ -38,9 +38,11 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     int32_t *s_mm = reinterpret_cast<int32_t *>(smem);
     unsigned *s_hist = reinterpret_cast<unsigned *>(s_mm + A.levels);
+    int32_t *s_clo = reinterpret_cast<int32_t *>(s_hist + A.levels);   // FAST: the concentration thresholds
     for (int i = threadIdx.x; i < A.levels; i += blockDim.x) {
         s_mm[i] = A.min_matches[i];
         s_hist[i] = 0;
+        if (FAST) s_clo[i] = A.conc_lo[i];
     }
     __syncthreads();
 
@@ -208,13 +210,68 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                         if (active) ++j;
                     }
                 };
+                // k = 32 with upper-range concentration sets: the step's four
+                // chunks are tested together, without branches, and the first
+                // chunk at which each algorithm stops is found by bit scans (the
+                // tests and their order are those of the chunk-by-chunk loop)
+                auto fast = [&](uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+                    const int c0 = m + 32 - __popc(x0), c1 = c0 + 32 - __popc(x1);
+                    const int c2 = c1 + 32 - __popc(x2), c3 = c2 + 32 - __popc(x3);
+                    // m after chunk i of the four (selected without a dynamic index,
+                    // which would put an array in local memory)
+                    auto m_at = [&](int i) { return i == 0 ? c0 : i == 1 ? c1 : i == 2 ? c2 : c3; };
+                    unsigned valid = 0, prune = 0, conc = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = j + i;
+                        if (jj < A.levels) {
+                            valid |= 1u << i;
+                            prune |= (unsigned)(m_at(i) < s_mm[jj]) << i;
+                            conc |= (unsigned)(m_at(i) >= s_clo[jj]) << i;
+                        }
+                    }
+                    // the bit of the chunk after which a level limit is reached
+                    auto at = [&](int lim) { const int d = lim - 1 - j; return d >= 0 && d < 4 ? 1u << d : 0u; };
+                    const unsigned last = at(A.levels), cap = at(A.cap_levels), lite_last = at(A.lite_levels);
+                    if (a1) {
+                        const unsigned s1 = (prune | (A.lite ? 0u : conc) | last | cap) & valid;
+                        if (s1) {
+                            const int i = __ffs(s1) - 1;
+                            const unsigned b = 1u << i;
+                            st1 = (prune & b) ? BLSH_PRUNED
+                                  : (!A.lite && (conc & b)) ? BLSH_ACCEPT
+                                  : (last & b) ? (A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX)
+                                               : BLSH_NEEDS_HASHES;
+                            j1 = j + i;
+                            m1 = m_at(i);
+                            a1 = false;
+                        }
+                    }
+                    if (al) {
+                        const unsigned sl = (prune | lite_last) & valid;
+                        if (sl) {
+                            const int i = __ffs(sl) - 1;
+                            stl = (prune >> i) & 1u ? BLSH_PRUNED : BLSH_LITE_SURVIVOR;
+                            jl = j + i;
+                            al = false;
+                        }
+                    }
+                    active = a1 || al;
+                    if (active) {   // all four chunks passed: none was the last level
+                        m = c3;
+                        j += 4;
+                    }
+                };
+                uint4 a, b;
                 if (PLANE && w == 0) {   // the first four words from the plane (L2-resident)
-                    const uint4 a = __ldg(A.plane + cur_pair.x), b = __ldg(A.plane + cur_pair.y);
-                    words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
+                    a = __ldg(A.plane + cur_pair.x);
+                    b = __ldg(A.plane + cur_pair.y);
                 } else {
-                    const uint4 a = ldg4(rx + w), b = ldg4(ry + w);
-                    words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
+                    a = ldg4(rx + w);
+                    b = ldg4(ry + w);
                 }
+                if constexpr (FAST) fast(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+                else words(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w, 0, 4);
                 w += 4;
                 if (st1 >= 0 && g == 0) {
                     A.status[q] = (uint8_t)st1;
@@ -340,10 +397,10 @@ __global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restr
         plane[i] = ldg4(sig + (size_t)i * W);
 }
 
-template <int KIND, int G, int U, bool PERSIST, bool PLANE = false>
+template <int KIND, int G, int U, bool PERSIST, bool PLANE = false, bool FAST = false>
 int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
-    auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE>;
-    const size_t smem = sizeof(int32_t) * A.levels * 2;
+    auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE, FAST>;
+    const size_t smem = sizeof(int32_t) * A.levels * (FAST ? 3 : 2);
     if (smem > 48 * 1024) {
         if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "tables too large for shared memory");
         BLSH_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -372,9 +429,15 @@ int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cud
 
 template <bool PERSIST>
 int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind, cudaStream_t s) {
-    if (kind == BLSH_COSINE)
+    if (kind == BLSH_COSINE) {
+        // k = 32 (one word per chunk) with upper-range concentration sets: the
+        // branch-free four-chunk step
+        if (A.chunk_words == 1 && A.conc_upper)
+            return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, PERSIST, true, true>(ctx, A, plan, s)
+                           : launch_kernel<BLSH_COSINE, 1, 1, PERSIST, false, true>(ctx, A, plan, s);
         return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, PERSIST, true>(ctx, A, plan, s)
                        : launch_kernel<BLSH_COSINE, 1, 1, PERSIST, false>(ctx, A, plan, s);
+    }
     switch (plan.group) {
     case 1: return launch_kernel<BLSH_JACCARD, 1, 8, PERSIST>(ctx, A, plan, s);
     case 4: return launch_kernel<BLSH_JACCARD, 4, 2, PERSIST>(ctx, A, plan, s);
@@ -473,6 +536,8 @@ int blsh_make_verify_args(blsh_ctx *ctx, const blsh_tables *tab, const uint32_t 
     A.est_stride = p.n_max + 1;
     A.min_matches = tab->min_matches;
     A.conc_bits = tab->conc_bits;
+    A.conc_lo = tab->conc_lo;
+    A.conc_upper = tab->conc_upper ? 1 : 0;
     A.est_tab = tab->est;
     A.status = status;
     A.n_used = n_used;

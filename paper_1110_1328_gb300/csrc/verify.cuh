@@ -24,6 +24,8 @@ struct VerifyArgs {
     int est_stride;              // n_max + 1
     const int32_t *min_matches;  // [levels]
     const uint32_t *conc_bits;   // [levels][conc_words]
+    const int32_t *conc_lo;      // [levels]: smallest concentrated m, used when conc_upper
+    int conc_upper;              // every level's concentrated m are the range [conc_lo, n]
     const float *est_tab;        // [levels][est_stride]
     uint8_t *status;
     uint16_t *n_used;

@@ -84,7 +84,7 @@ def _recorded_names():
     return names
 
 
-@pytest.mark.parametrize("workload", ["cosine-small", "cosine-small-q16", "jaccard-small"])
+@pytest.mark.parametrize("workload", ["cosine-small", "cosine-small-q16", "jaccard-small", "allpairs-cosine"])
 def test_modelled_kernels_are_the_recorded_ones(workload):
     """Every kernel the byte model names is a name the library records, so
     the roofline finds its bytes."""
@@ -102,6 +102,8 @@ def test_modelled_kernels_are_the_recorded_ones(workload):
     lst = rng.integers(0, 4, P).astype(np.uint8)
     pipe = _fake_pipe(w, P, 512 if workload == "cosine-small" else 0)
     pipe.with_lite = "lite" in w.get("stages", ("lite",))
+    if w.get("candidates") == "allpairs":
+        pipe.allpairs, pipe.nnz, pipe.dim, pipe.max_dups = True, int(objs.indptr[-1]), objs.dim, 5 * P
     work = bench.kernel_work(B, pipe, w, objs, st, nu, lst, rng.random(300) < 0.1)
     names = _recorded_names()
     missing = [k for k in work if not k.endswith(" gathered") and k not in names]

@@ -110,6 +110,23 @@ def test_full_pipeline_matches_oracle(B, name):
     assert (lite.status == O.LITE_ACCEPT).sum() > 10
 
 
+def test_allpairs_pipeline_matches_oracle(B):
+    """cosine-small's vectors with candidates from the AllPairs-style prefix
+    filter instead of banding, in bench's launch configuration (CUDA-graph
+    replay): the candidate list equal to the oracle's, pair for pair and in
+    order, and every pair's Algorithm 1 and 2 outcome and both output sets
+    equal to the oracle's."""
+    w, objs, hashp, pipe = run_pipeline(B, "allpairs-cosine")
+    sig_o = O.srp_sparse(objs, hashp)
+    pairs_o = O.allpairs_candidates(objs, w["t"], O.COSINE)
+    P = pipe.P
+    assert P == len(pairs_o) and P > 1_000_000
+    pairs_gpu = u32(pipe.pairs[:P])
+    assert np.array_equal(pairs_gpu, pairs_o)
+    want, lite = check_outputs_against_oracle(B, w, objs, pipe, sig_o, pairs_gpu)
+    assert (lite.status == O.LITE_ACCEPT).sum() > 10
+
+
 def test_batching_workload_sampled(B):
     """1,000,000 Chung-Lu adjacency sets, ~1e8 candidate pairs: sampled
     oracle checks (signature rows, pairs' outcomes) and properties of the
