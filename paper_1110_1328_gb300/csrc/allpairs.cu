@@ -499,9 +499,12 @@ extern "C" int blsh_allpairs_candidates(blsh_ctx *ctx, const int64_t *indptr, co
     // 5. sort, keep the distinct keys
     int kc = 0;
     {
-        // keys (x << 32) | y with x < N: 32 + xbits bits, one more for the padding key
-        const int kbits = 32 + xbits + 1 < 64 ? 32 + xbits + 1 : 64;
-        const int rc = blsh_radix::sort(ctx, ck, cv, max_dups, kbits, hist, (uint32_t *)partial64, grand32, s, &kc);
+        // keys (x << 32) | y: the write pass leaves them grouped by y in
+        // increasing order, so a stable sort by x alone (bits 32 .. 32 + xbits,
+        // one more bit for the padding key) orders them by (x, y)
+        const int kbits = xbits + 1 < 32 ? xbits + 1 : 32;
+        const int rc = blsh_radix::sort(ctx, ck, cv, max_dups, kbits, hist, (uint32_t *)partial64, grand32, s, &kc,
+                                        32);
         if (rc) return rc;
     }
     uint32_t *mark = (uint32_t *)(ws + L.mark), *pos = (uint32_t *)(ws + L.pos);

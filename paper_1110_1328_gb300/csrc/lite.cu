@@ -91,42 +91,6 @@ __device__ __forceinline__ long long lower_bound(const uint32_t *L, long long n,
 
 constexpr int kLiteStage = 512;   // longer-row elements a warp stages in shared memory
 
-// The register route (both rows of at most 32 elements, lane e holding
-// element e of the shorter row S (si, sv) and of the longer row L (li, lv)):
-// each lane's element of S is looked up in L by binary search over the lanes;
-// the warp's intersection size (sets, the same in every lane) or the lane's
-// share of D and of the squared norms (cosine, summed by the caller).
-template <bool COSINE>
-__device__ __forceinline__ void lite_short_sums(long long ns, long long nl, uint32_t si, float sv, uint32_t li,
-                                                float lv, bool have_norms, long long &inter, long long &D,
-                                                long long &Ns, long long &Nl) {
-    const int lane = threadIdx.x & 31;
-    // first position p of L with L[p] >= si: at most 32 candidates, so six
-    // halvings of [lo, hi) settle every lane
-    int lo = 0, hi = (int)nl;
-#pragma unroll
-    for (int it = 0; it < 6; ++it) {
-        const int mid = (lo + hi) >> 1;
-        const uint32_t v = __shfl_sync(kFull, li, mid & 31);
-        if (lo < hi) {
-            if (v < si) lo = mid + 1;
-            else hi = mid;
-        }
-    }
-    const uint32_t at = __shfl_sync(kFull, li, lo & 31);
-    const bool hit = lane < ns && lo < nl && at == si;
-    if (!COSINE) {
-        inter = __popc(__ballot_sync(kFull, hit));
-    } else {
-        const float atv = __shfl_sync(kFull, lv, lo & 31);
-        D = hit ? fixed_term(sv, atv) : 0;
-        if (!have_norms) {
-            Ns = lane < ns ? fixed_term(sv, sv) : 0;
-            Nl = lane < nl ? fixed_term(lv, lv) : 0;
-        }
-    }
-}
-
 // The sums of one survivor's exact similarity (the whole warp): rows
 // x = [ax, ax+na) and y = [ay, ay+nb) of the CSR; D_out = the intersection
 // size (sets) or D (cosine), and for cosine without have_norms the two
@@ -158,7 +122,30 @@ __device__ __forceinline__ void lite_exact_one(const LiteArgs &A, long long ax, 
             li = __ldg(A.indices + l0 + lane);
             if (COSINE) lv = __ldg(A.values + l0 + lane);
         }
-        lite_short_sums<COSINE>(ns, nl, si, sv, li, lv, have_norms, inter, D, Ns, Nl);
+        // first position p of L with L[p] >= si: at most 32 candidates, so six
+        // halvings of [lo, hi) settle every lane
+        int lo = 0, hi = (int)nl;
+#pragma unroll
+        for (int it = 0; it < 6; ++it) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t v = __shfl_sync(kFull, li, mid & 31);
+            if (lo < hi) {
+                if (v < si) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        const uint32_t at = __shfl_sync(kFull, li, lo & 31);
+        const bool hit = lane < ns && lo < nl && at == si;
+        if (!COSINE) {
+            inter = __popc(__ballot_sync(kFull, hit));
+        } else {
+            const float atv = __shfl_sync(kFull, lv, lo & 31);
+            D = hit ? fixed_term(sv, atv) : 0;
+            if (!have_norms) {
+                Ns = lane < ns ? fixed_term(sv, sv) : 0;
+                Nl = lane < nl ? fixed_term(lv, lv) : 0;
+            }
+        }
     } else {
         const uint32_t *Lidx = A.indices + l0;
         const float *Lval = COSINE ? A.values + l0 : nullptr;
@@ -247,7 +234,12 @@ __device__ __forceinline__ void lite_batch(const LiteArgs &A, long long my_q, bo
     const int lane = threadIdx.x & 31;
     // lane i keeps survivor i's sums
     long long myD = 0, myNx = nx, myNy = ny;
-    auto keep = [&](int i, long long D, long long Nx, long long Ny) {
+    for (unsigned todo = __ballot_sync(kFull, my_q >= 0); todo; todo &= todo - 1) {
+        const int i = __ffs(todo) - 1;
+        const long long a0 = __shfl_sync(kFull, ax, i), a1 = __shfl_sync(kFull, ex, i);
+        const long long b0 = __shfl_sync(kFull, ay, i), b1 = __shfl_sync(kFull, ey, i);
+        long long D = 0, Nx = 0, Ny = 0;
+        lite_exact_one<COSINE>(A, a0, a1 - a0, b0, b1 - b0, have_norms, w_idx, w_val, D, Nx, Ny);
         if (lane == i) {
             myD = D;
             if (!have_norms) {
@@ -255,78 +247,6 @@ __device__ __forceinline__ void lite_batch(const LiteArgs &A, long long my_q, bo
                 myNy = Ny;
             }
         }
-    };
-    // sums of the cosine route are per lane until reduced
-    auto reduce = [&](long long &inter, long long &D, long long &Ns, long long &Nl, long long nl) {
-        if (!COSINE) return nl > 32 ? warp_sum(inter) : inter;
-        D = warp_sum(D);
-        if (!have_norms) {
-            Ns = warp_sum(Ns);
-            Nl = warp_sum(Nl);
-        }
-        return D;
-    };
-    unsigned todo = __ballot_sync(kFull, my_q >= 0);
-    // survivors whose two rows have at most 32 elements: four at a time, the
-    // rows of all four loaded before any is computed (their load latencies
-    // overlap)
-    unsigned short_rows = __ballot_sync(kFull, my_q >= 0 && ex - ax <= 32 && ey - ay <= 32);
-    todo &= ~short_rows;
-    while (short_rows) {
-        int ids[4];
-        int cnt = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            ids[u] = -1;
-            if (short_rows) {
-                ids[u] = __ffs(short_rows) - 1;
-                short_rows &= short_rows - 1;
-                ++cnt;
-            }
-        }
-        uint32_t si[4], li[4];
-        float sv[4], lv[4];
-        long long ns[4], nl[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            si[u] = li[u] = 0;
-            sv[u] = lv[u] = 0.0f;
-            ns[u] = nl[u] = 0;
-            if (u < cnt) {
-                const int i = ids[u];
-                const long long a0 = __shfl_sync(kFull, ax, i), na = __shfl_sync(kFull, ex, i) - a0;
-                const long long b0 = __shfl_sync(kFull, ay, i), nb = __shfl_sync(kFull, ey, i) - b0;
-                const long long s0 = nb < na ? b0 : a0, l0 = nb < na ? a0 : b0;
-                ns[u] = nb < na ? nb : na;
-                nl[u] = nb < na ? na : nb;
-                if (lane < ns[u]) {
-                    si[u] = __ldg(A.indices + s0 + lane);
-                    if (COSINE) sv[u] = __ldg(A.values + s0 + lane);
-                }
-                if (lane < nl[u]) {
-                    li[u] = __ldg(A.indices + l0 + lane);
-                    if (COSINE) lv[u] = __ldg(A.values + l0 + lane);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (u < cnt) {
-                long long inter = 0, D = 0, Ns = 0, Nl = 0;
-                lite_short_sums<COSINE>(ns[u], nl[u], si[u], sv[u], li[u], lv[u], have_norms, inter, D, Ns, Nl);
-                const long long sum = reduce(inter, D, Ns, Nl, nl[u]);
-                keep(ids[u], sum, Ns, Nl);
-            }
-        }
-    }
-    // the others one after the other (staged or global searches)
-    for (; todo; todo &= todo - 1) {
-        const int i = __ffs(todo) - 1;
-        const long long a0 = __shfl_sync(kFull, ax, i), a1 = __shfl_sync(kFull, ex, i);
-        const long long b0 = __shfl_sync(kFull, ay, i), b1 = __shfl_sync(kFull, ey, i);
-        long long D = 0, Nx = 0, Ny = 0;
-        lite_exact_one<COSINE>(A, a0, a1 - a0, b0, b1 - b0, have_norms, w_idx, w_val, D, Nx, Ny);
-        keep(i, D, Nx, Ny);
     }
     if (my_q >= 0) {
         const double s = lite_similarity<COSINE>(myD, myNx, myNy, ex - ax, ey - ay);
@@ -363,7 +283,7 @@ __global__ void __launch_bounds__(256) row_norm2_kernel(const int64_t *__restric
 }
 
 template <bool COSINE>
-__global__ void __launch_bounds__(256, 3) lite_exact_kernel(const LiteArgs A) {
+__global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
     long long P = A.P;
     if (A.P_dev) {
         const long long pd = *A.P_dev;
@@ -471,7 +391,7 @@ __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, uns
 // survivors of one dense tile (a bucket of near-duplicates) spread over many
 // warps.
 template <bool COSINE>
-__global__ void __launch_bounds__(256, 3) lite_queue_kernel(const LiteArgs A, const unsigned long long *queue) {
+__global__ void __launch_bounds__(256) lite_queue_kernel(const LiteArgs A, const unsigned long long *queue) {
     const unsigned long long total = A.scratch->work3;
     const unsigned long long n = total < BLSH_LITE_QUEUE_CAP ? total : BLSH_LITE_QUEUE_CAP;
     extern __shared__ uint32_t lite_smem[];

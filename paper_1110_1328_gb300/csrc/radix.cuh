@@ -91,17 +91,19 @@ static __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(cons
 inline long long hist_entries(long long n) { return 256 * ((n + kSortTile - 1) / kSortTile); }
 inline long long partial_entries(long long n) { return blsh_scan::tiles_for(hist_entries(n)) + 1; }
 
-// Sorts keys[0][0..n) (and vals[0] alongside) by their low key_bits bits,
-// stably, ping-ponging between buffers 0 and 1; *cur receives the index of
+// Sorts keys[0][0..n) (and vals[0] alongside) by their bits
+// first_bit .. first_bit + key_bits - 1, stably (items equal there keep their
+// order), ping-ponging between buffers 0 and 1; *cur receives the index of
 // the buffer that holds the result.  hist: hist_entries(n) uint32; partial:
 // partial_entries(n) uint32; grand: one uint32 (device).
 inline int sort(blsh_ctx *ctx, unsigned long long *keys[2], uint32_t *vals[2], long long n, int key_bits,
-                uint32_t *hist, uint32_t *partial, uint32_t *grand, cudaStream_t s, int *cur_out) {
+                uint32_t *hist, uint32_t *partial, uint32_t *grand, cudaStream_t s, int *cur_out,
+                int first_bit = 0) {
     const int passes = (key_bits + 7) / 8;
     const long long tiles = (n + kSortTile - 1) / kSortTile;
     int cur = 0;
     for (int pass = 0; pass < passes && n > 0; ++pass) {
-        const int shift = 8 * pass;
+        const int shift = first_bit + 8 * pass;
         blsh_time_start(ctx, s);
         digit_hist_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, (int)tiles);
         BLSH_LAUNCHED(ctx, "digit_hist_kernel");
