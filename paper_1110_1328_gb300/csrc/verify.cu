@@ -30,6 +30,15 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
+// Parked pairs per warp (FAST plain form): at most 31 waiting plus the 32 of
+// a step.
+constexpr int kDefer = 64;
+// Byte offset of the parked-pair area in the dynamic shared memory, after the
+// three per-level arrays (8-byte aligned).
+__host__ __device__ __forceinline__ size_t defer_offset(int levels) {
+    return ((size_t)levels * 3 * sizeof(int32_t) + 7) & ~(size_t)7;
+}
+
 template <int KIND, int G, int U, bool PERSIST, bool PLANE, bool FAST = false>
 __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     // minMatches is staged in shared memory; the concentration bitmap (up to
@@ -39,6 +48,10 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     int32_t *s_mm = reinterpret_cast<int32_t *>(smem);
     unsigned *s_hist = reinterpret_cast<unsigned *>(s_mm + A.levels);
     int32_t *s_clo = reinterpret_cast<int32_t *>(s_hist + A.levels);   // FAST: the concentration thresholds
+    // FAST, plain form: each warp's parked pairs (index, pair, agreements)
+    long long *s_defq = reinterpret_cast<long long *>(smem + defer_offset(A.levels));
+    uint2 *s_defp = reinterpret_cast<uint2 *>(s_defq + (blockDim.x >> 5) * kDefer);
+    int *s_defm = reinterpret_cast<int *>(s_defp + (blockDim.x >> 5) * kDefer);
     for (int i = threadIdx.x; i < A.levels; i += blockDim.x) {
         s_mm[i] = A.min_matches[i];
         s_hist[i] = 0;
@@ -375,12 +388,72 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per_warp;
         uint2 nxt = make_uint2(0u, 0u);
         if (base + grp < P) nxt = __ldg(A.pairs + base + grp);
-        for (; base < P; base += stride) {
-            const uint2 pr = nxt;
-            const long long qq = base + grp;
-            if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
-            if (qq < P) start_pair(qq, pr.x, pr.y);
-            while (__any_sync(kFull, active)) step();
+        if constexpr (FAST) {
+            // Most pairs stop within their first step (the four chunks of the
+            // plane), but a warp would otherwise run its later steps for the
+            // few that do not, with the other lanes idle.  Pairs Algorithm 1
+            // leaves open after the first step (Algorithm 2 decided: h <= 128)
+            // are parked in the warp's part of shared memory with their
+            // agreements so far, and continued 32 at a time, every lane busy.
+            // (Each pair goes through the same chunks and tests, so the outputs
+            // are those of the chunk-by-chunk loop.)
+            const int wib = threadIdx.x >> 5;
+            long long *dq = s_defq + wib * kDefer;
+            uint2 *dp = s_defp + wib * kDefer;
+            int *dm = s_defm + wib * kDefer;
+            int cnt = 0;
+            auto drain = [&](int n) {   // the last n (<= 32) parked pairs, one per lane
+                __syncwarp();
+                if (lane < n) {
+                    const int e = cnt - n + lane;
+                    q = dq[e];
+                    cur_pair = dp[e];
+                    m = dm[e];
+                    rx = A.sig + (size_t)cur_pair.x * A.W;
+                    ry = A.sig + (size_t)cur_pair.y * A.W;
+                    j = 4;
+                    w = 4;
+                    acc = 0;
+                    sub = 0;
+                    a1 = active = true;
+                    al = false;
+                } else {
+                    a1 = al = active = false;
+                }
+                __syncwarp();
+                cnt -= n;
+                while (__any_sync(kFull, active)) step();
+            };
+            for (; base < P; base += stride) {
+                const uint2 pr = nxt;
+                const long long qq = base + grp;
+                if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
+                if (qq < P) start_pair(qq, pr.x, pr.y);
+                if (__any_sync(kFull, active)) step();   // the first four chunks
+                const bool park = active && a1 && !al;
+                const unsigned pmask = __ballot_sync(kFull, park);
+                if (pmask) {
+                    if (park) {
+                        const int e = cnt + __popc(pmask & ((1u << lane) - 1u));
+                        dq[e] = q;
+                        dp[e] = cur_pair;
+                        dm[e] = m;
+                        a1 = active = false;
+                    }
+                    cnt += __popc(pmask);
+                }
+                while (__any_sync(kFull, active)) step();   // pairs Algorithm 2 still holds open
+                if (cnt >= 32) drain(32);
+            }
+            while (cnt > 0) drain(cnt < 32 ? cnt : 32);
+        } else {
+            for (; base < P; base += stride) {
+                const uint2 pr = nxt;
+                const long long qq = base + grp;
+                if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
+                if (qq < P) start_pair(qq, pr.x, pr.y);
+                while (__any_sync(kFull, active)) step();
+            }
         }
     }
 
@@ -400,7 +473,9 @@ __global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restr
 template <int KIND, int G, int U, bool PERSIST, bool PLANE = false, bool FAST = false>
 int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
     auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE, FAST>;
-    const size_t smem = sizeof(int32_t) * A.levels * (FAST ? 3 : 2);
+    const size_t smem = FAST && !PERSIST
+                            ? defer_offset(A.levels) + (size_t)(plan.block / 32) * kDefer * (8 + 8 + 4)
+                            : sizeof(int32_t) * A.levels * (FAST ? 3 : 2);
     if (smem > 48 * 1024) {
         if (smem > ctx->smem_optin) return blsh_fail(ctx, BLSH_EINVAL, "tables too large for shared memory");
         BLSH_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
