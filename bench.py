@@ -401,7 +401,7 @@ class ClockSampler:
 # dram__bytes_write.sum of the bench step under --profile-step); reported as
 # the roofline's traffic for the workload it was taken on (per step, like the
 # algorithmic bytes), and to be taken again whenever the kernel changes.
-NCU_TRAFFIC = {("cosine-small", "srp_sparse4_kernel"): 437.0e6 + 4.1e6}
+NCU_TRAFFIC = {}
 
 
 def load_tensor_peak():
@@ -1540,7 +1540,7 @@ def run_large(args, w):
         "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": args.workload + ": " + w["text"], "objects": pipe.N, "nnz": pipe.nnz,
-                   "candidate_pairs": pipe.P, "batch_pairs": pipe.batch, "batches": nb,
+                   "candidate_pairs": pipe.P, "batch_pairs": pipe.batch, "batches": len(pipe.ranges),
                    "setup_s": round(setup_s, 1), "l2": "flushed between timed steps (256 MB write); the 68.7 GB "
                    "of codes and 1.3 GB of signatures exceed L2", "cuda_graph": graph is not None,
                    "plan": dict(pipe.plan.as_dict(), k=w["k"]), "lazy_bits": L,

@@ -324,27 +324,104 @@ __device__ long long run_end_global(const unsigned long long *keys, long long n,
     return lo;
 }
 
-template <int NW4, bool WRITE>
-__device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigned j, bool live, int i,
-                                          long long p0, long long end, uint32_t x, const uint4 *kx, int full,
-                                          uint32_t pmask, int eqw, uint32_t one, uint32_t high,
-                                          unsigned long long out, unsigned long long &cnt, uint32_t *pairs,
-                                          long long cap) {
-    uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
+// How a pair's key rows are compared at band b: the words of chunks below
+// nf4 (16-byte chunks) hold earlier bands only and are tested without a mask,
+// three operations a word: z = x ^ y, then (z - one) & ~z is OR-ed into t,
+// whose lane high bits show a zero lane (an agreeing band) once t is masked
+// with `high` at the end.  Chunk nf4 is the tail: word q of it is tested
+// under tm[q] (all lanes when the whole word is earlier bands, the low lanes
+// of pmask for the word holding band b's own lane, nothing past it).  For
+// Jaccard class ids word r of the tail (band b) must match.
+struct EmitCmp {
+    int nf4, r;
+    uint32_t tm[4];
+};
+
+__device__ __forceinline__ EmitCmp emit_cmp(int full, uint32_t pmask, uint32_t high) {
+    EmitCmp c;
+    c.nf4 = full >> 2;
+    c.r = full & 3;
 #pragma unroll
-    for (int c = 0; c < NW4; ++c) {
-        const uint4 yv = yrow[c];
-        const uint32_t z[4] = {kx[c].x ^ yv.x, kx[c].y ^ yv.y, kx[c].z ^ yv.z, kx[c].w ^ yv.w};
+    for (int q = 0; q < 4; ++q) c.tm[q] = q < c.r ? high : (q == c.r ? pmask : 0u);
+    return c;
+}
+
+// True when the pair (x, y) is emitted at band b: no earlier band agrees
+// (and, for Jaccard class ids, band b itself agrees).  xrow and yrow are the
+// two key rows (registers or shared memory); NW4 bounds the chunks read.
+template <int NW4, typename XR, typename YR>
+__device__ __forceinline__ bool emit_test(const XR &xrow, const YR &yrow, const EmitCmp &c, bool jac, uint32_t one,
+                                          uint32_t high) {
+    // the unmasked words in four independent chains (one per word of a
+    // chunk), joined and masked with `high` at the end; the tail under tm
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, tt = 0, zr = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int w = 4 * c + q;
-            const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
-            const uint32_t zl = (z[q] - one) & ~z[q];
-            hit |= zl & m;
-            if (w == eqw) eq = zl & high;
+    for (int k = 0; k < NW4; ++k) {
+        if (k <= c.nf4) {
+            const uint4 xv = xrow[k], yv = yrow[k];
+            const uint32_t z0 = xv.x ^ yv.x, z1 = xv.y ^ yv.y, z2 = xv.z ^ yv.z, z3 = xv.w ^ yv.w;
+            if (k < c.nf4) {
+                t0 |= (z0 - one) & ~z0;
+                t1 |= (z1 - one) & ~z1;
+                t2 |= (z2 - one) & ~z2;
+                t3 |= (z3 - one) & ~z3;
+            } else {
+                tt = ((z0 - one) & ~z0 & c.tm[0]) | ((z1 - one) & ~z1 & c.tm[1]) | ((z2 - one) & ~z2 & c.tm[2]) |
+                     ((z3 - one) & ~z3 & c.tm[3]);
+                if (jac) zr = c.r == 0 ? z0 : c.r == 1 ? z1 : c.r == 2 ? z2 : z3;
+            }
         }
     }
-    const bool ok = live && (int)j > i && p0 + (long long)j < end && hit == 0 && eq != 0;
+    return ((((t0 | t1) | (t2 | t3)) & high) | tt) == 0 && (!jac || zr == 0);
+}
+
+// Rows of at most four 16-byte chunks (KW4 <= 4), walk form: the lane's
+// plan as one poison word per key-row word, p[w] nonzero in every lane of a
+// band >= b (0 below, `one` past band b's word).  (x ^ y) | p can be zero
+// only in a lane of an earlier band, so a word's test is three operations
+// without masks or branches; a borrow into a poisoned lane comes only from a
+// zero lane below it, which is a hit already.
+template <int NW4>
+__device__ __forceinline__ bool emit_test_poison(const uint4 *kx, const uint4 *yrow, const uint32_t *p, bool jac,
+                                                 int eqw, uint32_t one, uint32_t high) {
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, zr = 1;
+#pragma unroll
+    for (int k = 0; k < NW4; ++k) {
+        const uint4 yv = yrow[k];
+        const uint32_t z0 = (kx[k].x ^ yv.x) | p[4 * k + 0], z1 = (kx[k].y ^ yv.y) | p[4 * k + 1];
+        const uint32_t z2 = (kx[k].z ^ yv.z) | p[4 * k + 2], z3 = (kx[k].w ^ yv.w) | p[4 * k + 3];
+        t0 |= (z0 - one) & ~z0;
+        t1 |= (z1 - one) & ~z1;
+        t2 |= (z2 - one) & ~z2;
+        t3 |= (z3 - one) & ~z3;
+        if (jac) {   // class id word b (not poisoned by the Jaccard plan) must match
+            const uint32_t e0 = kx[k].x ^ yv.x, e1 = kx[k].y ^ yv.y, e2 = kx[k].z ^ yv.z, e3 = kx[k].w ^ yv.w;
+            zr = eqw == 4 * k ? e0 : eqw == 4 * k + 1 ? e1 : eqw == 4 * k + 2 ? e2 : eqw == 4 * k + 3 ? e3 : zr;
+        }
+    }
+    return (((t0 | t1) | (t2 | t3)) & high) == 0 && (!jac || zr == 0);
+}
+
+// The poison words of a lane at band b (see emit_test_poison): bands 0..b-1
+// are `full` whole words and the low `rest` lanes of word `full`.
+template <int NW>
+__device__ __forceinline__ void emit_poison(uint32_t *p, int full, int rest, int lane_bits, uint32_t one) {
+    const uint32_t partial = rest ? one & ~((1u << (lane_bits * rest)) - 1u) : one;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) p[w] = w < full ? 0u : (w == full ? partial : one);
+}
+
+template <int NW4, bool WRITE, bool PZ>
+__device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigned j, bool live, int i,
+                                          long long p0, long long end, uint32_t x, const uint4 *kx,
+                                          const EmitCmp &cmp, const uint32_t *pz, int eqw, bool jac, uint32_t one,
+                                          uint32_t high, unsigned long long out, unsigned long long &cnt,
+                                          uint32_t *pairs, long long cap) {
+    // the test for every lane (no branch around it), then the lane's range
+    bool pass;
+    if constexpr (PZ) pass = emit_test_poison<NW4>(kx, yrow, pz, jac, eqw, one, high);
+    else pass = emit_test<NW4>(kx, yrow, cmp, jac, one, high);
+    const bool ok = pass && live && (int)j > i && p0 + (long long)j < end;
     if (WRITE && ok) {
         const long long o = (long long)(out + cnt);
         if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
@@ -353,23 +430,22 @@ __device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigne
 }
 
 // The walk of one warp over partners [jmin, jmax) (tile-relative), NW4
-// 16-byte words of key rows compared per pair.  Word w of a lane's row
-// holds bands below its b in full when w < full, in part (the low lanes
-// kept by pmask) when w == full; word eqw (class ids) must match.
-// Partners inside the window come from the stage; partners past it (long
-// buckets) are fetched 32 at a time into the warp's own buffer, one row per
-// lane, so that their loads overlap.
-template <int NW4, bool WRITE>
+// 16-byte words of key rows compared per pair (cmp: the lane's plan for
+// its band).  Partners inside the window come from the stage; partners past
+// it (long buckets) are fetched 32 at a time into the warp's own buffer, one
+// row per lane, so that their loads overlap.
+template <int NW4, bool WRITE, bool PZ>
 __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
                                           uint4 *w_rows, uint32_t *w_ids, const uint32_t *vals, long long p0,
                                           int win, int stride, unsigned jmin, unsigned jmax, bool live, int i,
-                                          long long end, uint32_t x, const uint4 *kx, int full, uint32_t pmask,
-                                          int eqw, uint32_t one, uint32_t high, unsigned long long out,
-                                          unsigned long long &cnt, uint32_t *pairs, long long cap) {
+                                          long long end, uint32_t x, const uint4 *kx, const EmitCmp &cmp,
+                                          const uint32_t *pz, int eqw, bool jac, uint32_t one, uint32_t high,
+                                          unsigned long long out, unsigned long long &cnt, uint32_t *pairs,
+                                          long long cap) {
     const unsigned wend = jmax < (unsigned)win ? jmax : (unsigned)win;
     for (unsigned j = jmin; j < wend; ++j)
-        emit_step<NW4, WRITE>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, full, pmask, eqw, one,
-                              high, out, cnt, pairs, cap);
+        emit_step<NW4, WRITE, PZ>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, cmp, pz, eqw, jac,
+                                  one, high, out, cnt, pairs, cap);
     const int lane = threadIdx.x & 31;
     for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
         __syncwarp();
@@ -383,8 +459,8 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
         __syncwarp();
         const unsigned n = jmax - j0 < 32u ? jmax - j0 : 32u;
         for (unsigned u = 0; u < n; ++u)
-            emit_step<NW4, WRITE>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, full, pmask, eqw,
-                                  one, high, out, cnt, pairs, cap);
+            emit_step<NW4, WRITE, PZ>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, cmp, pz, eqw,
+                                      jac, one, high, out, cnt, pairs, cap);
     }
 }
 
@@ -437,23 +513,8 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
                                           : (int)(key >> A.rows);
             const int full = b / per_word, rest = b % per_word;
             const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
-            const int eqw = A.exact_classes ? b : -1;
             const uint4 *xr = s_ck + (size_t)io * cws, *yr = s_ck + (size_t)j * cws;
-            uint32_t hit = 0, eq = eqw < 0 ? 1u : 0u;
-#pragma unroll
-            for (int c = 0; c < NW4; ++c) {
-                const uint4 xv = xr[c], yv = yr[c];
-                const uint32_t z[4] = {xv.x ^ yv.x, xv.y ^ yv.y, xv.z ^ yv.z, xv.w ^ yv.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int w = 4 * c + q;
-                    const uint32_t m = w < full ? high : (w == full ? pmask : 0u);
-                    const uint32_t zl = (z[q] - one) & ~z[q];
-                    hit |= zl & m;
-                    if (w == eqw) eq = zl & high;
-                }
-            }
-            ok = hit == 0 && eq != 0;
+            ok = emit_test<NW4>(xr, yr, emit_cmp(full, pmask, high), A.exact_classes != 0, one, high);
             x = s_val[io];
             y = s_val[j];
         }
@@ -564,7 +625,6 @@ __global__ void __launch_bounds__(256, 2) emit_warp_kernel(BandArgs A, const uns
         const int full = b / per_word, rest = b % per_word;   // bands 0..b-1: `full` words and `rest` lanes
         const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
         // Jaccard class ids: word b must match too (a key collision is not a bucket)
-        const int eqw = A.exact_classes ? b : -1;
         const int need = A.exact_classes ? b + 1 : full + (rest ? 1 : 0);
         const int nw4 = (__reduce_max_sync(kFull, (unsigned)(live ? need : 0)) + 3) >> 2;
         const unsigned jmin = 1u;
@@ -598,8 +658,15 @@ __global__ void __launch_bounds__(256, 2) emit_warp_kernel(BandArgs A, const uns
             if (!WRITE && live) counts[p0 + i] = w_ids[lane];
             continue;
         }
-#define BLSH_WALK(NW) emit_walk<NW, WRITE>(A, s_ck, s_val, w_rows, w_ids, vals, p0, win, cws, jmin, jmax, live, i, \
-                                           end, x, kx, full, pmask, eqw, one, high, out, cnt, pairs, cap)
+        const EmitCmp cmp = emit_cmp(full, pmask, high);
+        const bool jac = A.exact_classes != 0;
+        const int eqw = jac ? b : -1;
+        // rows of at most four chunks: the plan as poison words (see emit_test_poison)
+        constexpr bool kPZ = KW4 <= 4;
+        uint32_t pz[kPZ ? 16 : 1];
+        if constexpr (kPZ) emit_poison<16>(pz, full, rest, 8 * A.ck_lane, one);
+#define BLSH_WALK(NW) emit_walk<NW, WRITE, kPZ>(A, s_ck, s_val, w_rows, w_ids, vals, p0, win, cws, jmin, jmax, live, \
+                                                i, end, x, kx, cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap)
         if constexpr (KW4 <= 4) {
             switch (nw4) {
             case 0: BLSH_WALK(0); break;

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) srp_sparse_kernel(const int64_t *__restri
                 }
             }
         }
-        const float n = (float)(e - s);
+        const float n = (float)(int)(e - s < (1ll << 30) ? e - s : (1ll << 30));   // 32-bit conversion
         const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
         const int w = t >> 5;
 #pragma unroll
@@ -285,7 +285,11 @@ __device__ __forceinline__ unsigned long long f2_codes(uint32_t w) {
 // per lane (coalesced), and reach the other lanes by shuffles; the gathers
 // of several nonzeros are issued together, so a long row is not a chain of
 // dependent loads, and no barrier is needed.  Every column keeps its sum and
-// the sum of the products' magnitudes for the error bound.  The four bits of
+// the sum of the products' magnitudes for the error bound.  The sum is formed
+// in blocks of 32 nonzeros (a block's FMA chain, then the block added to the
+// total), so a column's result carries at most min(n, 32) + ceil(n / 32)
+// roundings in any chain rather than n: a long row leaves far fewer signs to
+// the FP64 recheck.  The four bits of
 // a group form a nibble; eight lanes OR their nibbles into one signature
 // word with shuffles.  A CTA takes one (row, piece of 4 V T columns) at a
 // time.
@@ -313,9 +317,14 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
         if (row_mask && !row_mask[row]) continue;
         const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
         constexpr bool Q16 = sizeof(RT) == 2;
-        float acc[4 * V], mag[4 * V];
+        float acc[4 * V], mag[4 * V], tot[4 * V];
 #pragma unroll
-        for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = 0.0f;
+        for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = tot[u] = 0.0f;
+        // two-byte codes: the same sums kept as pairs of columns (one 64-bit
+        // register each) for the paired instructions, unpacked once per row
+        unsigned long long acc2[2 * V], mag2[2 * V], tot2[2 * V];
+#pragma unroll
+        for (int u = 0; u < 2 * V; ++u) acc2[u] = mag2[u] = tot2[u] = 0ull;
         // the row's nonzeros 32 at a time: lane l of every warp loads entry
         // l (coalesced), then the gathers of kSrpBatch / V entries are issued
         // together (their indices come by shuffle), so that a long row is not
@@ -357,13 +366,18 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                         for (int g = 0; g < V; ++g) {
                             const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
                             const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
-                            float *a = acc + 4 * g, *mg = mag + 4 * g;
-                            f2_unpack(f2_fma(v2, d01, f2_pack(a[0], a[1])), a[0], a[1]);
-                            f2_unpack(f2_fma(v2, d23, f2_pack(a[2], a[3])), a[2], a[3]);
-                            f2_unpack(f2_fma(av2, d01 & 0x7fffffff7fffffffull, f2_pack(mg[0], mg[1])), mg[0], mg[1]);
-                            f2_unpack(f2_fma(av2, d23 & 0x7fffffff7fffffffull, f2_pack(mg[2], mg[3])), mg[2], mg[3]);
+                            acc2[2 * g] = f2_fma(v2, d01, acc2[2 * g]);
+                            acc2[2 * g + 1] = f2_fma(v2, d23, acc2[2 * g + 1]);
+                            mag2[2 * g] = f2_fma(av2, d01 & 0x7fffffff7fffffffull, mag2[2 * g]);
+                            mag2[2 * g + 1] = f2_fma(av2, d23 & 0x7fffffff7fffffffull, mag2[2 * g + 1]);
                         }
                     }
+                }
+                // the block of (at most) 32 nonzeros into the total
+#pragma unroll
+                for (int u = 0; u < 2 * V; ++u) {
+                    tot2[u] = f2_add(tot2[u], acc2[u]);
+                    acc2[u] = 0ull;
                 }
                 continue;
             }
@@ -409,19 +423,42 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                     }
                 }
             }
+#pragma unroll
+            for (int u = 0; u < 4 * V; ++u) {
+                tot[u] = __fadd_rn(tot[u], acc[u]);
+                acc[u] = 0.0f;
+            }
         }
-        const float n = (float)(e - s);
+        if constexpr (sizeof(RT) == 2) {
+#pragma unroll
+            for (int u = 0; u < 2 * V; ++u) {
+                f2_unpack(tot2[u], tot[2 * u], tot[2 * u + 1]);
+                f2_unpack(mag2[u], mag[2 * u], mag[2 * u + 1]);
+            }
+        }
+        // the row length through a 32-bit integer (a 64-bit conversion would run
+        // on the narrow FP64 pipe); rows past 2^30 count as 2^30, which is long
+        const int len = (int)(e - s < (1ll << 30) ? e - s : (1ll << 30));
+        const float n = (float)len;
         const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
+        // Roundings in a column's sum: a block's chain (at most 32 FMAs, error
+        // <= gamma_32 of its magnitudes) and the chain of block totals (at
+        // most ceil(n / 32) - 1 adds), so |sum - exact| <= (gamma_32 +
+        // gamma_nb + gamma_32 gamma_nb) sum|p|, below 1.12 (min(n, 32) + nb) u
+        // mag when n u <= 0.05 (mag, the computed sum of magnitudes, is within
+        // gamma_n of sum|p|); each rounding near underflow adds at most 2^-150,
+        // and there are at most 2n of them.
+        const float kround = fminf(n, 32.0f) + (float)((len + 31) >> 5);
 #pragma unroll
         for (int g = 0; g < V; ++g) {
             uint32_t nib = 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int u = 4 * g + c;
-                const float bound = 1.25f * n * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
+                const float bound = 1.25f * kround * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
                 bool bit;
-                if (!long_row && fabsf(acc[u]) > bound) {
-                    bit = acc[u] >= 0.0f;
+                if (!long_row && fabsf(tot[u]) > bound) {
+                    bit = tot[u] >= 0.0f;
                 } else {
                     // undecided: queue it for srp_recheck_kernel (bit left 0 here),
                     // or recompute in line if the queue is full
@@ -476,13 +513,25 @@ __global__ void __launch_bounds__(256) srp_recheck_kernel(const uint2 *__restric
          it += warps) {
         const uint2 rj = queue[it];
         const long long s = __ldg(indptr + rj.x), e = __ldg(indptr + rj.x + 1);
+        // lane l sums entries l, l + 32, ... in that order; four of its
+        // gathers are in flight at a time (a product of 0 for entries past
+        // the row leaves the sums unchanged)
         double ps = 0.0, qs = 0.0;
-        for (long long k = s + lane; k < e; k += 32) {
-            const uint32_t ix = __ldg(indices + k);
-            if (ix < dim) {
-                const double p = (double)__ldg(values + k) * r_fp64(R, (size_t)ix * bits + rj.y);
-                ps += p;
-                qs += fabs(p);
+        for (long long k0 = s + lane; k0 < e; k0 += 128) {
+            double p[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long k = k0 + 32 * u;
+                p[u] = 0.0;
+                if (k < e) {
+                    const uint32_t ix = __ldg(indices + k);
+                    if (ix < dim) p[u] = (double)__ldg(values + k) * r_fp64(R, (size_t)ix * bits + rj.y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ps += p[u];
+                qs += fabs(p[u]);
             }
         }
 #pragma unroll

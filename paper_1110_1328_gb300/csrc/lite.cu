@@ -24,7 +24,6 @@
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr double kTwo60 = 1152921504606846976.0;   // 2^60
 
 struct LiteArgs {
     const uint2 *pairs;
@@ -48,8 +47,11 @@ constexpr int kLiteGrab = 16;   // tiles of 512 statuses per grab (this pass see
 // and the 48-bit product is shifted with round-half-to-even (symmetric, as
 // the FP64 conversion rounds).  The same value as the FP64 expression
 // rn((double)u * (double)v * 2^60) (the product of two floats is exact in
-// FP64); that expression is kept for |u v| >= 2^3, where the result would not
-// fit and the conversion saturates.
+// FP64).  Products of |u v| >= 2^2 (outside rows of squared norm below 4)
+// are shifted up as far as they fit and otherwise saturate to the int64
+// limit of their sign, as that conversion does; non-finite inputs saturate
+// by sign.  All integer arithmetic: the FP64 pipe is narrow on this part,
+// and a branch to FP64 code here was executed (predicated) for every term.
 __device__ __forceinline__ long long fixed_term(float u, float v) {
     const uint32_t bu = __float_as_uint(u), bv = __float_as_uint(v);
     int eu = (int)((bu >> 23) & 0xffu), ev = (int)((bv >> 23) & 0xffu);
@@ -60,7 +62,8 @@ __device__ __forceinline__ long long fixed_term(float u, float v) {
     const int sh = eu + ev - 300 + 60;                               // u v 2^60 = prod 2^sh
     unsigned long long r;
     if (sh >= 0) {
-        if (sh > 15) return __double2ll_rn(__dmul_rn(__dmul_rn((double)u, (double)v), kTwo60));
+        if (sh > 15 && (sh >= 63 || (prod >> (63 - sh)) != 0))   // at least 2^63 in magnitude
+            return ((bu ^ bv) >> 31) ? (long long)0x8000000000000000ull : 0x7fffffffffffffffll;
         r = prod << sh;
     } else if (-sh > 48) {
         r = 0;                                                       // below half of 2^0
@@ -197,6 +200,94 @@ __device__ __forceinline__ void lite_exact_one(const LiteArgs &A, long long ax, 
     }
 }
 
+// The sums of up to 32 / W survivors at once, each in its own W-lane
+// segment of the warp (W = 8 or 16), for survivors whose two rows have at
+// most W elements each: the register path of lite_exact_one with the
+// shuffles, the search and the sums kept inside the segment.  sel holds the
+// lanes whose survivors are to be formed; lane i's survivor rows are
+// [ax, ex) and [ay, ey) in lane i.  Segment k takes the k-th survivor left
+// in sel; each survivor's lane receives its sums.
+template <bool COSINE, int W>
+__device__ __forceinline__ void lite_segments(const LiteArgs &A, unsigned sel, long long ax, long long ex,
+                                              long long ay, long long ey, bool have_norms, long long &myD,
+                                              long long &myNx, long long &myNy) {
+    constexpr int S = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int e = lane & (W - 1), seg = lane / W;
+    const unsigned lt = (1u << lane) - 1u;
+    while (sel) {
+        // the first S survivors left: segment seg takes the seg-th of them
+        unsigned taken = sel, rest = sel;
+#pragma unroll
+        for (int k = 0; k < S; ++k) rest &= rest - 1;
+        taken &= ~rest;
+        unsigned m = taken;
+        for (int k = 0; k < seg && m; ++k) m &= m - 1;
+        const int pick = m ? __ffs(m) - 1 : -1;
+        const int src = pick < 0 ? 0 : pick;
+        const long long a0 = __shfl_sync(kFull, ax, src), a1 = __shfl_sync(kFull, ex, src);
+        const long long b0 = __shfl_sync(kFull, ay, src), b1 = __shfl_sync(kFull, ey, src);
+        long long s0 = a0, ns = a1 - a0, l0 = b0, nl = b1 - b0;
+        if (nl < ns) { s0 = b0; ns = b1 - b0; l0 = a0; nl = a1 - a0; }
+        if (pick < 0) ns = nl = 0;
+        uint32_t si = 0, li = 0;
+        float sv = 0.0f, lv = 0.0f;
+        if (e < ns) {
+            si = __ldg(A.indices + s0 + e);
+            if (COSINE) sv = __ldg(A.values + s0 + e);
+        }
+        if (e < nl) {
+            li = __ldg(A.indices + l0 + e);
+            if (COSINE) lv = __ldg(A.values + l0 + e);
+        }
+        // first position p of L with L[p] >= si, among 0..nl (nl <= W)
+        int lo = 0, hi = (int)nl;
+#pragma unroll
+        for (int it = 0; (1 << it) <= W; ++it) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t v = __shfl_sync(kFull, li, mid & (W - 1), W);
+            if (lo < hi) {
+                if (v < si) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        const uint32_t at = __shfl_sync(kFull, li, lo & (W - 1), W);
+        const bool hit = e < ns && lo < nl && at == si;
+        long long D = 0, Ns = 0, Nl = 0;
+        if (!COSINE) {
+            const unsigned segmask = (W == 32 ? kFull : ((1u << W) - 1u)) << (seg * W);
+            D = __popc(__ballot_sync(kFull, hit) & segmask);
+        } else {
+            const float atv = __shfl_sync(kFull, lv, lo & (W - 1), W);
+            D = hit ? fixed_term(sv, atv) : 0;
+            if (!have_norms) {
+                Ns = e < ns ? fixed_term(sv, sv) : 0;
+                Nl = e < nl ? fixed_term(lv, lv) : 0;
+            }
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) {
+                D += __shfl_xor_sync(kFull, D, o);
+                if (!have_norms) {
+                    Ns += __shfl_xor_sync(kFull, Ns, o);
+                    Nl += __shfl_xor_sync(kFull, Nl, o);
+                }
+            }
+        }
+        // survivor i's sums from the first lane of its segment
+        const int from = W * __popc(taken & lt);
+        const long long gD = __shfl_sync(kFull, D, from & 31);
+        const long long gNs = __shfl_sync(kFull, Ns, from & 31), gNl = __shfl_sync(kFull, Nl, from & 31);
+        if ((taken >> lane) & 1u) {
+            myD = gD;
+            if (COSINE && !have_norms) {
+                myNx = gNs;
+                myNy = gNl;
+            }
+        }
+        sel = rest;
+    }
+}
+
 // The similarity from the sums (one lane per survivor: FP64 is a narrow
 // pipe on this part, so the division and square root run once per survivor
 // rather than once per lane of a warp-wide computation).
@@ -234,7 +325,24 @@ __device__ __forceinline__ void lite_batch(const LiteArgs &A, long long my_q, bo
     const int lane = threadIdx.x & 31;
     // lane i keeps survivor i's sums
     long long myD = 0, myNx = nx, myNy = ny;
-    for (unsigned todo = __ballot_sync(kFull, my_q >= 0); todo; todo &= todo - 1) {
+    // survivors whose rows are short share the warp: four at a time when
+    // both rows have at most 8 elements, two when at most 16 (a group too
+    // small to fill the segments joins the next wider one)
+    unsigned todo = __ballot_sync(kFull, my_q >= 0);
+    {
+        const long long longest = ex - ax > ey - ay ? ex - ax : ey - ay;
+        unsigned s8 = __ballot_sync(kFull, my_q >= 0 && longest <= 8);
+        unsigned s16 = __ballot_sync(kFull, my_q >= 0 && longest <= 16) & ~s8;
+        if (__popc(s8) < 3) {
+            s16 |= s8;
+            s8 = 0u;
+        }
+        if (__popc(s16) < 2) s16 = 0u;
+        if (s8) lite_segments<COSINE, 8>(A, s8, ax, ex, ay, ey, have_norms, myD, myNx, myNy);
+        if (s16) lite_segments<COSINE, 16>(A, s16, ax, ex, ay, ey, have_norms, myD, myNx, myNy);
+        todo &= ~(s8 | s16);
+    }
+    for (; todo; todo &= todo - 1) {
         const int i = __ffs(todo) - 1;
         const long long a0 = __shfl_sync(kFull, ax, i), a1 = __shfl_sync(kFull, ex, i);
         const long long b0 = __shfl_sync(kFull, ay, i), b1 = __shfl_sync(kFull, ey, i);
@@ -256,10 +364,16 @@ __device__ __forceinline__ void lite_batch(const LiteArgs &A, long long my_q, bo
 }
 
 // Each row's sum of fixed_term(v, v) (the squared norm of the exact cosine,
-// an integer: independent of the order of the terms): one warp per row.
-// Formed only when there are more survivors than half the rows (the
-// collection pass has counted them); otherwise each survivor forms its two
-// norms itself, which is less work.
+// an integer: independent of the order of the terms).  One warp per group of
+// 32 consecutive rows: lane l holds the end of row l of the group, the warp
+// reads the group's nonzeros 32 at a time (four such reads in flight), finds
+// each element's row by a binary search of the lanes' row ends (shuffles),
+// sums the terms of each row's run of lanes by a segmented scan, and the
+// run's last lane adds the run's sum into the row's 64-bit sum in shared
+// memory (one adding lane per row and read, so no two lanes collide).  Formed
+// only when there are more survivors than half the rows (the collection pass
+// has counted them); otherwise each survivor forms its two norms itself,
+// which is less work.
 __global__ void __launch_bounds__(256) row_norm2_kernel(const int64_t *__restrict__ indptr,
                                                         const float *__restrict__ values, long long N,
                                                         long long *__restrict__ norm2,
@@ -267,18 +381,52 @@ __global__ void __launch_bounds__(256) row_norm2_kernel(const int64_t *__restric
     const bool form = scratch->work3 * 2ull > (unsigned long long)N;
     if (blockIdx.x == 0 && threadIdx.x == 0) scratch->norm2_valid = form ? 1u : 0u;
     if (!form) return;
+    __shared__ unsigned long long part[8][32];
     const int lane = threadIdx.x & 31;
+    unsigned long long *sum = part[threadIdx.x >> 5];
+    const long long groups = (N + 31) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nwarps) {
-        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-        long long acc = 0;
-#pragma unroll 4
-        for (long long i = s + lane; i < e; i += 32) {
-            const float v = __ldg(values + i);
-            acc += fixed_term(v, v);
+    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += nwarps) {
+        const long long r0 = g << 5;
+        const int nr = (int)(N - r0 < 32 ? N - r0 : 32);
+        const long long s = __ldg(indptr + r0);
+        // lanes past the last row repeat its end (the ends stay nondecreasing)
+        const long long end = __ldg(indptr + r0 + (lane < nr ? lane + 1 : nr));
+        const long long e = __shfl_sync(kFull, end, 31);
+        sum[lane] = 0ull;
+        __syncwarp();
+        for (long long c = s; c < e; c += 128) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = c + 32 * u + lane;
+                v[u] = i < e ? __ldg(values + i) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = c + 32 * u + lane;
+                if (c + 32 * u >= e) break;                 // warp-uniform
+                int row = 0;                                // rows of the group ending at or before i
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(kFull, end, row + step - 1) <= i) row += step;
+                unsigned long long term = i < e ? (unsigned long long)fixed_term(v[u], v[u]) : 0ull;
+                // inclusive sums over the lanes of the same row (rows are
+                // nondecreasing across the lanes)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long tv = __shfl_up_sync(kFull, term, o);
+                    const int tr = __shfl_up_sync(kFull, row, o);
+                    if (lane >= o && tr == row) term += tv;
+                }
+                const int next_row = __shfl_down_sync(kFull, row, 1);
+                if (i < e && (lane == 31 || i + 1 == e || next_row != row)) sum[row] += term;
+                __syncwarp();
+            }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) norm2[row] = acc;
+        __syncwarp();
+        if (lane < nr) norm2[r0 + lane] = (long long)sum[lane];
+        __syncwarp();
     }
 }
 
@@ -508,7 +656,7 @@ int lite_exact_pass(blsh_ctx *ctx, const uint2 *pairs, int64_t P, const long lon
     lite_collect_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(L, queue);
     BLSH_LAUNCHED(ctx, "lite_collect_kernel");
     if (L.norm2) {
-        const long long blocks = (N + 7) / 8, cap = (long long)ctx->sm_count * 16;
+        const long long blocks = (N + 255) / 256, cap = (long long)ctx->sm_count * 8;   // 32 rows per warp
         blsh_time_start(ctx, s);
         row_norm2_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
             indptr, values, N, const_cast<long long *>(L.norm2), ctx->scratch);

@@ -20,6 +20,7 @@
 //                 from an atomic counter and hands a new pair to a group as
 //                 soon as its pair stops (pairs stop after very different
 //                 chunk counts: most after the first chunk).
+#include <type_traits>
 #include <vector>
 
 #include "verify.cuh"
@@ -58,6 +59,14 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         if (FAST) s_clo[i] = A.conc_lo[i];
     }
     __syncthreads();
+    // FAST: the thresholds of levels 0..3 in registers for every pair's
+    // first step (j = 0 for all lanes there)
+    int mm0[4], clo0[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        mm0[i] = FAST && i < A.levels ? s_mm[i] : 0;
+        clo0[i] = FAST && i < A.levels ? s_clo[i] : 0;
+    }
 
     long long P = A.P;
     if (A.P_dev) {
@@ -156,7 +165,10 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     };
     // One step for every group of the warp (all lanes execute it, so the
     // group reductions may use full-warp shuffles).
-    auto step = [&]() {
+    // (first: std::true_type for a pair's first step, whose four words come
+    // from the plane and whose levels are 0..3)
+    auto step = [&](auto first) {
+        [[maybe_unused]] constexpr bool kFirst = decltype(first)::value;
         if constexpr (KIND == BLSH_JACCARD) {
             int c = 0;
             if (active) {
@@ -228,6 +240,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 // chunk at which each algorithm stops is found by bit scans (the
                 // tests and their order are those of the chunk-by-chunk loop)
                 auto fast = [&](uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+                    if (kFirst) j = 0, m = 0;
                     const int c0 = m + 32 - __popc(x0), c1 = c0 + 32 - __popc(x1);
                     const int c2 = c1 + 32 - __popc(x2), c3 = c2 + 32 - __popc(x3);
                     // m after chunk i of the four (selected without a dynamic index,
@@ -239,8 +252,8 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                         const int jj = j + i;
                         if (jj < A.levels) {
                             valid |= 1u << i;
-                            prune |= (unsigned)(m_at(i) < s_mm[jj]) << i;
-                            conc |= (unsigned)(m_at(i) >= s_clo[jj]) << i;
+                            prune |= (unsigned)(m_at(i) < (kFirst ? mm0[i] : s_mm[jj])) << i;
+                            conc |= (unsigned)(m_at(i) >= (kFirst ? clo0[i] : s_clo[jj])) << i;
                         }
                     }
                     // the bit of the chunk after which a level limit is reached
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                     }
                 };
                 uint4 a, b;
-                if (PLANE && w == 0) {   // the first four words from the plane (L2-resident)
+                if (PLANE && (kFirst || w == 0)) {   // the first four words from the plane (L2-resident)
                     a = __ldg(A.plane + cur_pair.x);
                     b = __ldg(A.plane + cur_pair.y);
                 } else {
@@ -375,7 +388,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 cpos += want < avail ? want : avail;
             }
             if (!__any_sync(kFull, active)) break;
-            step();
+            step(std::false_type{});
         }
     } else {
         // a fixed share of the pairs per warp: blocks of 32 / G pairs in
@@ -422,14 +435,14 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 }
                 __syncwarp();
                 cnt -= n;
-                while (__any_sync(kFull, active)) step();
+                while (__any_sync(kFull, active)) step(std::false_type{});
             };
             for (; base < P; base += stride) {
                 const uint2 pr = nxt;
                 const long long qq = base + grp;
                 if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
                 if (qq < P) start_pair(qq, pr.x, pr.y);
-                if (__any_sync(kFull, active)) step();   // the first four chunks
+                if (__any_sync(kFull, active)) step(std::true_type{});   // the first four chunks
                 const bool park = active && a1 && !al;
                 const unsigned pmask = __ballot_sync(kFull, park);
                 if (pmask) {
@@ -442,7 +455,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                     }
                     cnt += __popc(pmask);
                 }
-                while (__any_sync(kFull, active)) step();   // pairs Algorithm 2 still holds open
+                while (__any_sync(kFull, active)) step(std::false_type{});   // pairs Algorithm 2 still holds open
                 if (cnt >= 32) drain(32);
             }
             while (cnt > 0) drain(cnt < 32 ? cnt : 32);
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 const long long qq = base + grp;
                 if (base + stride + grp < P) nxt = __ldg(A.pairs + base + stride + grp);
                 if (qq < P) start_pair(qq, pr.x, pr.y);
-                while (__any_sync(kFull, active)) step();
+                while (__any_sync(kFull, active)) step(std::false_type{});
             }
         }
     }
