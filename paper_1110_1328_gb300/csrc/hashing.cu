@@ -1,5 +1,7 @@
 // hashing.cu -- the signature producers: minhash (Section 4.1, "LSH family")
 // and sign random projections of sparse rows (Section 4.2, "LSH family").
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -154,6 +156,7 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 }
 
 constexpr int kSrpMaxPerThread = 16;
+constexpr int kSrpLooseRow = 256;   // rows up to this length use the 2^15 sum|v| magnitude bound (two-byte codes)
 constexpr int kSrpBatch = 8;       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
 constexpr int kSrpChunk = 256;
 
@@ -325,6 +328,13 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
         unsigned long long acc2[2 * V], mag2[2 * V], tot2[2 * V];
 #pragma unroll
         for (int u = 0; u < 2 * V; ++u) acc2[u] = mag2[u] = tot2[u] = 0ull;
+        // Rows of at most kSrpLooseRow nonzeros (two-byte codes): the
+        // magnitude bound 2^15 sum|v_i| (every decoded code has |q - 2^15| <=
+        // 2^15) instead of each column's sum|v_i| |q_ij - 2^15|; about ten
+        // times looser, but the blocked sums keep short rows' bounds small,
+        // and it saves two paired FMAs and four masks per nonzero
+        const bool loose = Q16 && e - s <= kSrpLooseRow;
+        float sav = 0.0f;
         // the row's nonzeros 32 at a time: lane l of every warp loads entry
         // l (coalesced), then the gathers of kSrpBatch / V entries are issued
         // together (their indices come by shuffle), so that a long row is not
@@ -347,32 +357,40 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                 // the decoded value of code q is (q - 2^15) 2^-12: (2^23 + q) - (2^23 + 2^15),
                 // exact, with the sums kept in units of 2^-12
                 const unsigned long long off2 = f2_pack(-8421376.0f, -8421376.0f);
-                for (int u0 = 0; u0 < cnt; u0 += NB) {
-                    uint2 qb[NB][V];
-                    float vb[NB];
+                auto chunk = [&](auto with_mag) {
+                    constexpr bool kMag = decltype(with_mag)::value;
+                    for (int u0 = 0; u0 < cnt; u0 += NB) {
+                        uint2 qb[NB][V];
+                        float vb[NB];
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
-                        vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
-                        const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
+                        for (int b = 0; b < NB; ++b) {
+                            const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                            vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
+                            const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
 #pragma unroll
-                        for (int g = 0; g < V; ++g) qb[b][g] = __ldg(Rrow + g * T);
-                    }
+                            for (int g = 0; g < V; ++g) qb[b][g] = __ldg(Rrow + g * T);
+                        }
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const unsigned long long v2 = f2_pack(vb[b], vb[b]);
-                        const unsigned long long av2 = f2_pack(fabsf(vb[b]), fabsf(vb[b]));
+                        for (int b = 0; b < NB; ++b) {
+                            const unsigned long long v2 = f2_pack(vb[b], vb[b]);
+                            const unsigned long long av2 = f2_pack(fabsf(vb[b]), fabsf(vb[b]));
+                            if (!kMag) sav += fabsf(vb[b]);
 #pragma unroll
-                        for (int g = 0; g < V; ++g) {
-                            const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
-                            const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
-                            acc2[2 * g] = f2_fma(v2, d01, acc2[2 * g]);
-                            acc2[2 * g + 1] = f2_fma(v2, d23, acc2[2 * g + 1]);
-                            mag2[2 * g] = f2_fma(av2, d01 & 0x7fffffff7fffffffull, mag2[2 * g]);
-                            mag2[2 * g + 1] = f2_fma(av2, d23 & 0x7fffffff7fffffffull, mag2[2 * g + 1]);
+                            for (int g = 0; g < V; ++g) {
+                                const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
+                                const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
+                                acc2[2 * g] = f2_fma(v2, d01, acc2[2 * g]);
+                                acc2[2 * g + 1] = f2_fma(v2, d23, acc2[2 * g + 1]);
+                                if (kMag) {
+                                    mag2[2 * g] = f2_fma(av2, d01 & 0x7fffffff7fffffffull, mag2[2 * g]);
+                                    mag2[2 * g + 1] = f2_fma(av2, d23 & 0x7fffffff7fffffffull, mag2[2 * g + 1]);
+                                }
+                            }
                         }
                     }
-                }
+                };
+                if (loose) chunk(std::false_type{});
+                else chunk(std::true_type{});
                 // the block of (at most) 32 nonzeros into the total
 #pragma unroll
                 for (int u = 0; u < 2 * V; ++u) {
@@ -434,6 +452,10 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
             for (int u = 0; u < 2 * V; ++u) {
                 f2_unpack(tot2[u], tot[2 * u], tot[2 * u + 1]);
                 f2_unpack(mag2[u], mag[2 * u], mag[2 * u + 1]);
+            }
+            if (loose) {
+#pragma unroll
+                for (int u = 0; u < 4 * V; ++u) mag[u] = 32768.0f * sav;
             }
         }
         // the row length through a 32-bit integer (a 64-bit conversion would run
@@ -689,14 +711,22 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
                     const RT *R, int64_t dim, int bits, int col0, int ncols, const uint8_t *row_mask,
                     uint32_t *sig, cudaStream_t s) {
     // selected rows (usually few): pieces of 512 columns, one per CTA; all
-    // rows: the whole range per CTA.  T4 = 32 * (largest divisor of
-    // groups/32 up to 8) threads, V = groups / T4 groups of four columns per
-    // thread
+    // rows: the whole range per CTA.  T4 = 32 wt threads, V = groups / T4
+    // groups of four columns per thread: for two-byte codes the fewest warps
+    // that give every thread at most two groups (each nonzero's shuffles and
+    // address then serve eight columns: measured faster, e.g. one warp per
+    // row for 256 columns), otherwise the largest divisor of groups/32 up to 8
     const int piece = row_mask && ncols % 512 == 0 ? 512 : ncols;
     const int pieces = ncols / piece;
     const int groups = piece / 4;
-    int wt = 8;
-    while ((groups / 32) % wt) --wt;
+    int wt = 0;
+    if (sizeof(RT) == 2)
+        for (int c = 1; c <= 8 && !wt; ++c)
+            if ((groups / 32) % c == 0 && groups / (32 * c) <= 2) wt = c;
+    if (!wt) {
+        wt = 8;
+        while ((groups / 32) % wt) --wt;
+    }
     const int T4 = 32 * wt, V = groups / T4;
     if (V < 1 || V > 4) return -1;
     // many small CTAs (rows have very different lengths): 32 per SM measured best

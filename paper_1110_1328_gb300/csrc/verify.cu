@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     uint2 cur_pair = make_uint2(0u, 0u);
     const uint32_t *rx = nullptr, *ry = nullptr;
     int m = 0, j = 0, w = 0, acc = 0, sub = 0;
+    unsigned h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // cosine: stops at levels 0..3 counted by this lane
 
     auto finish = [&](int st) {
         if (g == 0) {
@@ -318,12 +319,14 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                     if (A.ln_used) A.ln_used[q] = (uint16_t)((jl + 1) * A.k);
                 }
             }
-            // the stop histogram: most pairs of a step stop at the same
-            // (first) chunk, so those are added with one shared-memory atomic
-            // per warp; the others one by one (every lane runs this)
-            const unsigned z = __ballot_sync(kFull, hj == 0);
-            if (z && lane == __ffs(z) - 1) atomicAdd(&s_hist[0], (unsigned)__popc(z));
-            if (hj > 0) atomicAdd(&s_hist[hj], 1u);
+            // the stop histogram: stops at levels 0..3 (most pairs) are
+            // counted in the lane's registers and added once per warp at the
+            // end; later levels with a shared-memory atomic
+            h0 += hj == 0;
+            h1 += hj == 1;
+            h2 += hj == 2;
+            h3 += hj == 3;
+            if (hj >= 4) atomicAdd(&s_hist[hj], 1u);
         }
     };
 
@@ -470,6 +473,16 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         }
     }
 
+    {
+        const unsigned c0 = __reduce_add_sync(kFull, h0), c1 = __reduce_add_sync(kFull, h1);
+        const unsigned c2 = __reduce_add_sync(kFull, h2), c3 = __reduce_add_sync(kFull, h3);
+        if (lane == 0) {
+            if (c0) atomicAdd(&s_hist[0], c0);
+            if (c1) atomicAdd(&s_hist[1], c1);
+            if (c2) atomicAdd(&s_hist[2], c2);
+            if (c3) atomicAdd(&s_hist[3], c3);
+        }
+    }
     __syncthreads();
     if (A.stop_hist)
         for (int i = threadIdx.x; i < A.levels; i += blockDim.x)
