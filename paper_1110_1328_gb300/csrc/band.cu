@@ -349,14 +349,14 @@ __device__ __forceinline__ EmitCmp emit_cmp(int full, uint32_t pmask, uint32_t h
 // True when the pair (x, y) is emitted at band b: no earlier band agrees
 // (and, for Jaccard class ids, band b itself agrees).  xrow and yrow are the
 // two key rows (registers or shared memory); NW4 bounds the chunks read.
-template <int NW4, typename XR, typename YR>
+template <int NW4, int K0 = 0, typename XR, typename YR>
 __device__ __forceinline__ bool emit_test(const XR &xrow, const YR &yrow, const EmitCmp &c, bool jac, uint32_t one,
                                           uint32_t high) {
     // the unmasked words in four independent chains (one per word of a
     // chunk), joined and masked with `high` at the end; the tail under tm
     uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, tt = 0, zr = 0;
 #pragma unroll
-    for (int k = 0; k < NW4; ++k) {
+    for (int k = K0; k < NW4; ++k) {
         if (k <= c.nf4) {
             const uint4 xv = xrow[k], yv = yrow[k];
             const uint32_t z0 = xv.x ^ yv.x, z1 = xv.y ^ yv.y, z2 = xv.z ^ yv.z, z3 = xv.w ^ yv.w;
@@ -443,24 +443,80 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
                                           unsigned long long out, unsigned long long &cnt, uint32_t *pairs,
                                           long long cap) {
     const unsigned wend = jmax < (unsigned)win ? jmax : (unsigned)win;
-    for (unsigned j = jmin; j < wend; ++j)
-        emit_step<NW4, WRITE, PZ>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, cmp, pz, eqw, jac,
-                                  one, high, out, cnt, pairs, cap);
     const int lane = threadIdx.x & 31;
-    for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
-        __syncwarp();
-        if (j0 + lane < jmax) {
-            const uint32_t yv = __ldg(vals + p0 + j0 + lane);
-            w_ids[lane] = yv;
-            const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
+    if constexpr (!PZ && NW4 >= 2) {
+        // Long key rows: partners in batches of 32.  Each (lane, partner) is
+        // first tested on the first 16-byte chunk only (bands 0..7 of 16-bit
+        // keys), which settles nearly every pair that agrees in an earlier
+        // band; the rest (noted in `und`) are finished by their own lane at
+        // the end of the batch, and the batch's pairs are then counted, or
+        // written in partner order.
+        const bool more = cmp.nf4 >= 2 || (cmp.nf4 == 1 && (jac || (cmp.tm[0] | cmp.tm[1] | cmp.tm[2] | cmp.tm[3])));
+        auto batch = [&](unsigned j0, unsigned n, const uint4 *rows, int rstride, const uint32_t *ids) {
+            uint32_t keep = 0, und = 0;
+            for (unsigned u = 0; u < n; ++u) {
+                const unsigned j = j0 + u;
+                const uint4 yv = rows[(size_t)u * rstride];
+                const uint32_t z0 = kx[0].x ^ yv.x, z1 = kx[0].y ^ yv.y, z2 = kx[0].z ^ yv.z, z3 = kx[0].w ^ yv.w;
+                const bool whole = cmp.nf4 >= 1;
+                const uint32_t h = ((z0 - one) & ~z0 & (whole ? high : cmp.tm[0])) |
+                                   ((z1 - one) & ~z1 & (whole ? high : cmp.tm[1])) |
+                                   ((z2 - one) & ~z2 & (whole ? high : cmp.tm[2])) |
+                                   ((z3 - one) & ~z3 & (whole ? high : cmp.tm[3]));
+                const uint32_t zr = cmp.r == 0 ? z0 : cmp.r == 1 ? z1 : cmp.r == 2 ? z2 : z3;
+                const bool in = live && (int)j > i && p0 + (long long)j < end;
+                if (in && h == 0) {
+                    if (whole && more) und |= 1u << u;
+                    else if (whole || !jac || zr == 0) keep |= 1u << u;
+                }
+            }
+            for (uint32_t b = und; b; b &= b - 1) {
+                const int u = __ffs(b) - 1;
+                if (emit_test<NW4, 1>(kx, rows + (size_t)u * rstride, cmp, jac, one, high)) keep |= 1u << u;
+            }
+            if (WRITE) {
+                for (uint32_t b = keep; b; b &= b - 1) {
+                    const long long o = (long long)(out + cnt);
+                    if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, ids[__ffs(b) - 1]);
+                    ++cnt;
+                }
+            } else {
+                cnt += __popc(keep);
+            }
+        };
+        for (unsigned j0 = jmin; j0 < wend; j0 += 32)
+            batch(j0, wend - j0 < 32u ? wend - j0 : 32u, s_ck + (size_t)j0 * stride, stride, s_val + j0);
+        for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
+            __syncwarp();
+            if (j0 + lane < jmax) {
+                const uint32_t yv = __ldg(vals + p0 + j0 + lane);
+                w_ids[lane] = yv;
+                const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
 #pragma unroll
-            for (int c = 0; c < NW4; ++c) w_rows[lane * NW4 + c] = __ldg(g + c);
+                for (int c = 0; c < NW4; ++c) w_rows[lane * NW4 + c] = __ldg(g + c);
+            }
+            __syncwarp();
+            batch(j0, jmax - j0 < 32u ? jmax - j0 : 32u, w_rows, NW4, w_ids);
         }
-        __syncwarp();
-        const unsigned n = jmax - j0 < 32u ? jmax - j0 : 32u;
-        for (unsigned u = 0; u < n; ++u)
-            emit_step<NW4, WRITE, PZ>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, cmp, pz, eqw,
+    } else {
+        for (unsigned j = jmin; j < wend; ++j)
+            emit_step<NW4, WRITE, PZ>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, cmp, pz, eqw,
                                       jac, one, high, out, cnt, pairs, cap);
+        for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
+            __syncwarp();
+            if (j0 + lane < jmax) {
+                const uint32_t yv = __ldg(vals + p0 + j0 + lane);
+                w_ids[lane] = yv;
+                const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
+#pragma unroll
+                for (int c = 0; c < NW4; ++c) w_rows[lane * NW4 + c] = __ldg(g + c);
+            }
+            __syncwarp();
+            const unsigned n = jmax - j0 < 32u ? jmax - j0 : 32u;
+            for (unsigned u = 0; u < n; ++u)
+                emit_step<NW4, WRITE, PZ>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, cmp, pz, eqw,
+                                          jac, one, high, out, cnt, pairs, cap);
+        }
     }
 }
 

@@ -31,6 +31,12 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
+// Status of a pair Algorithm 1 leaves open after its first four chunks in
+// the two-pass form (verify_first_kernel, then verify_kernel with OPEN);
+// internal to one call (every such pair is finished, and its status
+// overwritten, before the call returns).
+constexpr uint8_t kOpenStatus = 254;
+
 // Parked pairs per warp (FAST plain form): at most 31 waiting plus the 32 of
 // a step.
 constexpr int kDefer = 64;
@@ -40,7 +46,7 @@ __host__ __device__ __forceinline__ size_t defer_offset(int levels) {
     return ((size_t)levels * 3 * sizeof(int32_t) + 7) & ~(size_t)7;
 }
 
-template <int KIND, int G, int U, bool PERSIST, bool PLANE, bool FAST = false>
+template <int KIND, int G, int U, bool PERSIST, bool PLANE, bool FAST = false, bool OPEN = false>
 __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     // minMatches is staged in shared memory; the concentration bitmap (up to
     // tens of KB, consulted only by pairs that pass the pruning test) is
@@ -84,7 +90,6 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
     uint2 cur_pair = make_uint2(0u, 0u);
     const uint32_t *rx = nullptr, *ry = nullptr;
     int m = 0, j = 0, w = 0, acc = 0, sub = 0;
-    unsigned h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // cosine: stops at levels 0..3 counted by this lane
 
     auto finish = [&](int st) {
         if (g == 0) {
@@ -319,13 +324,17 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                     if (A.ln_used) A.ln_used[q] = (uint16_t)((jl + 1) * A.k);
                 }
             }
-            // the stop histogram: stops at levels 0..3 (most pairs) are
-            // counted in the lane's registers and added once per warp at the
-            // end; later levels with a shared-memory atomic
-            h0 += hj == 0;
-            h1 += hj == 1;
-            h2 += hj == 2;
-            h3 += hj == 3;
+            // the stop histogram: the stops at levels 0..3 (most pairs) by
+            // one ballot per level, lane c adding level c's count (four
+            // different addresses: one atomic instruction, no collision);
+            // later levels one atomic per lane (every lane runs this)
+            unsigned mine = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const unsigned z = __ballot_sync(kFull, hj == c);
+                if (lane == c) mine = (unsigned)__popc(z);
+            }
+            if (mine) atomicAdd(&s_hist[lane], mine);
             if (hj >= 4) atomicAdd(&s_hist[hj], 1u);
         }
     };
@@ -404,7 +413,54 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per_warp;
         uint2 nxt = make_uint2(0u, 0u);
         if (base + grp < P) nxt = __ldg(A.pairs + base + grp);
-        if constexpr (FAST) {
+        if constexpr (OPEN) {
+            // Second pass of the two-pass form: the pairs the first pass left
+            // at kOpenStatus.  A warp scans tiles of 512 statuses (16 per
+            // lane), lists the open ones in its part of shared memory, and
+            // runs them 32 at a time, each from its first step (which repeats
+            // the first pass's arithmetic and leaves the pair open) to its stop.
+            uint16_t *w_list = reinterpret_cast<uint16_t *>(smem + defer_offset(A.levels)) + (threadIdx.x >> 5) * 512;
+            const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+            const bool vec = ((uintptr_t)A.status & 15) == 0;
+            for (long long t0 = wid * 512; t0 < P; t0 += nw * 512) {
+                const long long qs = t0 + 16ll * lane;
+                uint32_t open = 0;
+                if (vec && qs + 16 <= P) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(A.status + qs);
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        open |= (uint32_t)(((wv[i >> 2] >> (8 * (i & 3))) & 0xffu) == kOpenStatus) << i;
+                } else {
+                    for (int i = 0; i < 16; ++i)
+                        if (qs + i < P && A.status[qs + i] == kOpenStatus) open |= 1u << i;
+                }
+                const int c = __popc(open);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                if (total == 0) continue;
+                __syncwarp();                                  // the previous tile's list has been read
+                int slot = incl - c;
+                for (uint32_t bits = open; bits; bits &= bits - 1) w_list[slot++] = (uint16_t)(16 * lane + __ffs(bits) - 1);
+                __syncwarp();
+                for (int b0 = 0; b0 < total; b0 += 32) {
+                    if (b0 + lane < total) {
+                        const long long qq = t0 + w_list[b0 + lane];
+                        const uint2 pr = __ldg(A.pairs + qq);
+                        start_pair(qq, pr.x, pr.y);
+                        al = false;                            // Algorithm 2 was decided in the first pass
+                    }
+                    if (__any_sync(kFull, active)) step(std::true_type{});
+                    while (__any_sync(kFull, active)) step(std::false_type{});
+                }
+            }
+        } else if constexpr (FAST) {
             // Most pairs stop within their first step (the four chunks of the
             // plane), but a warp would otherwise run its later steps for the
             // few that do not, with the other lanes idle.  Pairs Algorithm 1
@@ -473,20 +529,133 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
         }
     }
 
-    {
-        const unsigned c0 = __reduce_add_sync(kFull, h0), c1 = __reduce_add_sync(kFull, h1);
-        const unsigned c2 = __reduce_add_sync(kFull, h2), c3 = __reduce_add_sync(kFull, h3);
-        if (lane == 0) {
-            if (c0) atomicAdd(&s_hist[0], c0);
-            if (c1) atomicAdd(&s_hist[1], c1);
-            if (c2) atomicAdd(&s_hist[2], c2);
-            if (c3) atomicAdd(&s_hist[3], c3);
-        }
-    }
     __syncthreads();
     if (A.stop_hist)
         for (int i = threadIdx.x; i < A.levels; i += blockDim.x)
             if (s_hist[i]) atomicAdd(A.stop_hist + i, (unsigned long long)s_hist[i]);
+}
+
+// Two-pass form, first pass (cosine, k = 32, upper-range concentration sets,
+// Algorithm 2 over at most four chunks): one lane per pair, nothing but the
+// pair's first four chunks (the plane's 16 bytes, or the rows' first 16)
+// and the tests of levels 0..3 with their thresholds in registers -- the
+// decisions of verify_kernel's first step, in the same order.  A pair that
+// stops gets its outputs; a pair Algorithm 1 leaves open is marked
+// kOpenStatus for the second pass (verify_kernel with OPEN).  A lane takes
+// two pairs at a time, so that their loads overlap.  The stops are counted
+// with one ballot per level.
+template <bool PLANE>
+__global__ void __launch_bounds__(256) verify_first_kernel(const VerifyArgs A) {
+    __shared__ unsigned s_h[4];
+    if (threadIdx.x < 4) s_h[threadIdx.x] = 0;
+    int mm[4], clo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        mm[i] = i < A.levels ? __ldg(A.min_matches + i) : 0;
+        clo[i] = i < A.levels ? __ldg(A.conc_lo + i) : 0;
+    }
+    __syncthreads();
+    long long P = A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0 : (pd < P ? pd : P);
+    }
+    const unsigned valid = A.levels >= 4 ? 0xfu : (1u << A.levels) - 1u;
+    // the bit of the chunk after which a level limit is reached
+    auto at = [](int lim) { const int d = lim - 1; return d >= 0 && d < 4 ? 1u << d : 0u; };
+    const unsigned last = at(A.levels), cap = at(A.cap_levels), lite_last = at(A.lite_levels);
+    const int lane = threadIdx.x & 31;
+    // a pair's decisions and outputs, given its first four words; returns the
+    // level it stops at for the histogram (-1: none counted)
+    auto decide = [&](long long q, uint2 pr, uint4 a, uint4 b) -> int {
+        const int c0 = 32 - __popc(a.x ^ b.x), c1 = c0 + 32 - __popc(a.y ^ b.y);
+        const int c2 = c1 + 32 - __popc(a.z ^ b.z), c3 = c2 + 32 - __popc(a.w ^ b.w);
+        auto m_at = [&](int i) { return i == 0 ? c0 : i == 1 ? c1 : i == 2 ? c2 : c3; };
+        unsigned prune = 0, conc = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            prune |= (unsigned)(m_at(i) < mm[i]) << i;
+            conc |= (unsigned)(m_at(i) >= clo[i]) << i;
+        }
+        prune &= valid;
+        conc &= valid;
+        int hj = -1;
+        const unsigned s1 = prune | (A.lite ? 0u : conc) | ((last | cap) & valid);
+        if (s1) {
+            const int i = __ffs(s1) - 1;
+            const unsigned bi = 1u << i;
+            const int st1 = (prune & bi) ? BLSH_PRUNED
+                            : (!A.lite && (conc & bi)) ? BLSH_ACCEPT
+                            : (last & bi) ? (A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX)
+                                          : BLSH_NEEDS_HASHES;
+            const int m1 = m_at(i);
+            A.status[q] = (uint8_t)st1;
+            if (A.n_used) A.n_used[q] = (uint16_t)((i + 1) * A.k);
+            if (A.m_out) A.m_out[q] = (uint16_t)m1;
+            if (st1 == BLSH_NEEDS_HASHES) {
+                A.need[pr.x] = 1;
+                A.need[pr.y] = 1;
+            } else {
+                if (A.est_out && st1 != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + (size_t)i * A.est_stride + m1);
+                hj = i;
+            }
+        } else {
+            A.status[q] = kOpenStatus;
+        }
+        if (A.lite_levels) {
+            const unsigned sl = prune | (lite_last & valid);
+            const int i = __ffs(sl) - 1;   // Algorithm 2 stops within these four chunks
+            A.lstatus[q] = (prune >> i) & 1u ? BLSH_PRUNED : BLSH_LITE_SURVIVOR;
+            if (A.ln_used) A.ln_used[q] = (uint16_t)((i + 1) * A.k);
+        }
+        return hj;
+    };
+    auto bad_pair = [&](long long q) {
+        A.status[q] = BLSH_BAD_PAIR;
+        if (A.n_used) A.n_used[q] = 0;
+        if (A.m_out) A.m_out[q] = 0;
+        if (A.lite_levels) {
+            A.lstatus[q] = BLSH_BAD_PAIR;
+            if (A.ln_used) A.ln_used[q] = 0;
+        }
+        blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
+    };
+    auto row = [&](uint32_t o) { return PLANE ? __ldg(A.plane + o) : ldg4(A.sig + (size_t)o * A.W); };
+    // two pairs per lane at a time (pairs q and q + stride): both pairs'
+    // loads are in flight before either is decided
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < P; base += 2 * stride) {
+        const long long qa = base + lane, qb = base + stride + lane;
+        uint2 pa = make_uint2(0u, 0u), pb = make_uint2(0u, 0u);
+        if (qa < P) pa = __ldg(A.pairs + qa);
+        if (qb < P) pb = __ldg(A.pairs + qb);
+        const bool oka = qa < P && (long long)pa.x < A.N && (long long)pa.y < A.N;
+        const bool okb = qb < P && (long long)pb.x < A.N && (long long)pb.y < A.N;
+        uint4 xa = make_uint4(0u, 0u, 0u, 0u), ya = xa, xb = xa, yb = xa;
+        if (oka) {
+            xa = row(pa.x);
+            ya = row(pa.y);
+        }
+        if (okb) {
+            xb = row(pb.x);
+            yb = row(pb.y);
+        }
+        int ha = -1, hb = -1;
+        if (oka) ha = decide(qa, pa, xa, ya);
+        else if (qa < P) bad_pair(qa);
+        if (okb) hb = decide(qb, pb, xb, yb);
+        else if (qb < P) bad_pair(qb);
+        unsigned mine = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned z = __ballot_sync(kFull, ha == c), z2 = __ballot_sync(kFull, hb == c);
+            if (lane == c) mine = (unsigned)(__popc(z) + __popc(z2));
+        }
+        if (mine) atomicAdd(&s_h[lane], mine);
+    }
+    __syncthreads();
+    if (A.stop_hist && threadIdx.x < 4 && s_h[threadIdx.x])
+        atomicAdd(A.stop_hist + threadIdx.x, (unsigned long long)s_h[threadIdx.x]);
 }
 
 // plane[i] = words 0..3 of row i
@@ -496,10 +665,13 @@ __global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restr
         plane[i] = ldg4(sig + (size_t)i * W);
 }
 
-template <int KIND, int G, int U, bool PERSIST, bool PLANE = false, bool FAST = false>
+template <int KIND, int G, int U, bool PERSIST, bool PLANE = false, bool FAST = false, bool OPEN = false>
 int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cudaStream_t s) {
-    auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE, FAST>;
-    const size_t smem = FAST && !PERSIST
+    auto kern = verify_kernel<KIND, G, U, PERSIST, PLANE, FAST, OPEN>;
+    // FAST plain form: the parked pairs (kDefer per warp) or, in the second
+    // pass of the two-pass form, a tile's open pairs (512 per warp)
+    const size_t smem = OPEN ? defer_offset(A.levels) + (size_t)(plan.block / 32) * 512 * sizeof(uint16_t)
+                        : FAST && !PERSIST
                             ? defer_offset(A.levels) + (size_t)(plan.block / 32) * kDefer * (8 + 8 + 4)
                             : sizeof(int32_t) * A.levels * (FAST ? 3 : 2);
     if (smem > 48 * 1024) {
@@ -533,9 +705,24 @@ int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind
     if (kind == BLSH_COSINE) {
         // k = 32 (one word per chunk) with upper-range concentration sets: the
         // branch-free four-chunk step
-        if (A.chunk_words == 1 && A.conc_upper)
+        if (A.chunk_words == 1 && A.conc_upper) {
+            // plain form with Algorithm 2 (if any) over at most four chunks:
+            // two passes -- every pair's first four chunks in a lean kernel,
+            // then the pairs Algorithm 1 leaves open (a few percent)
+            if (!PERSIST && A.lite_levels <= 4 && (A.lite_levels == 0 || A.lite_levels <= A.levels)) {
+                const long long blocks = (A.P + 255) / 256, cap = (long long)ctx->sm_count * 8;
+                const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+                if (grid == 0) return BLSH_OK;
+                blsh_time_start(ctx, s);
+                if (A.plane) verify_first_kernel<true><<<grid, 256, 0, s>>>(A);
+                else verify_first_kernel<false><<<grid, 256, 0, s>>>(A);
+                BLSH_LAUNCHED(ctx, "verify_first_kernel");
+                return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, false, true, true, true>(ctx, A, plan, s)
+                               : launch_kernel<BLSH_COSINE, 1, 1, false, false, true, true>(ctx, A, plan, s);
+            }
             return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, PERSIST, true, true>(ctx, A, plan, s)
                            : launch_kernel<BLSH_COSINE, 1, 1, PERSIST, false, true>(ctx, A, plan, s);
+        }
         return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, PERSIST, true>(ctx, A, plan, s)
                        : launch_kernel<BLSH_COSINE, 1, 1, PERSIST, false>(ctx, A, plan, s);
     }
