@@ -1236,7 +1236,9 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     the kept indices of every device batch) copied back, all inside the timed
     region; the inputs of step i+1 are copied into a second set of device
     buffers while step i runs (double buffering, one CUDA graph per buffer
-    set).  Returns (ms per step, H2D bytes per step, D2H bytes per step)."""
+    set), and step i's outputs are read while step i+1 runs.  Returns (ms
+    per step, H2D bytes per step, D2H bytes per step, the steps' own device
+    time per step)."""
     pin = lambda x: x.cpu().pin_memory()
     h_in = {k: pin(getattr(pipe, k)) for k in ("indptr", "indices", "values")}
     sets = [pipe.buffer_set(), pipe.new_buffer_set()]
@@ -1260,13 +1262,15 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("end-to-end set-up failed")
     nb = len(pipe.ranges)
-    h_counts = torch.zeros((nb, 2), dtype=torch.int64).pin_memory()
+    h_counts = [torch.zeros((nb, 2), dtype=torch.int64).pin_memory() for _ in range(2)]
     h_out1 = torch.zeros(kept[0] + 1024, dtype=torch.int64).pin_memory()
     h_out2 = torch.zeros(kept[1] + 1024, dtype=torch.int64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
     copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_cnt = [torch.cuda.Event(), torch.cuda.Event()]
     ev_out = [None, None]
+    d2h = [0]
 
     def issue_inputs(b):
         # into set b once the step that last used it, and the copy of its
@@ -1278,29 +1282,12 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
                 sets[b][k].copy_(v, non_blocking=True)
             ev_in[b].record(copy_in)
 
-    torch.cuda.synchronize()
-    d2h = 0
-    t0 = time.perf_counter()
-    issue_inputs(0)
-    for i in range(steps):
-        b = i % 2
-        if i + 1 < steps:
-            issue_inputs(1 - b)
-        stream.wait_event(ev_in[b])
-        if use_graph:
-            graphs[b].replay()
-        else:
-            pipe.use_buffer_set(sets[b])
-            pipe.step()
-        done = torch.cuda.Event()
-        done.record(stream)
-        with torch.cuda.stream(copy_out):
-            copy_out.wait_event(done)
-            h_counts.copy_(sets[b]["n_out"], non_blocking=True)
-        copy_out.synchronize()
+    def finish(b):
+        # the step that ran on set b: its counts on the host, then its output sets
+        ev_cnt[b].synchronize()
         o1 = o2 = 0
         with torch.cuda.stream(copy_out):
-            for (b0, _), (c1, c2) in zip(pipe.ranges, h_counts.tolist()):
+            for (b0, _), (c1, c2) in zip(pipe.ranges, h_counts[b].tolist()):
                 c1, c2 = min(int(c1), h_out1.numel() - o1), min(int(c2), h_out2.numel() - o2)
                 if c1:
                     h_out1[o1:o1 + c1].copy_(sets[b]["out1"][b0:b0 + c1], non_blocking=True)
@@ -1309,13 +1296,46 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
                 o1, o2 = o1 + c1, o2 + c2
             ev_out[b] = torch.cuda.Event()
             ev_out[b].record(copy_out)
-        d2h = 16 * nb + 8 * (o1 + o2)
+        d2h[0] = 16 * nb + 8 * (o1 + o2)
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    issue_inputs(0)
+    for i in range(steps):
+        b = i % 2
+        stream.wait_event(ev_in[b])
+        ev_s[i].record(stream)
+        if use_graph:
+            graphs[b].replay()
+        else:
+            pipe.use_buffer_set(sets[b])
+            pipe.step()
+        ev_e[i].record(stream)
+        done = torch.cuda.Event()
+        done.record(stream)
+        # step i is queued: the host now finishes step i-1 (its counts are on
+        # the host once it completes; its output copies go on the copy-out
+        # stream ahead of anything that waits for step i), then queues step
+        # i's count copy and the inputs of step i+1, so the device always has
+        # the next step waiting and the input copies overlap a running step
+        if i >= 1:
+            finish(1 - b)
+        with torch.cuda.stream(copy_out):
+            copy_out.wait_event(done)
+            h_counts[b].copy_(sets[b]["n_out"], non_blocking=True)
+            ev_cnt[b].record(copy_out)
+        if i + 1 < steps:
+            issue_inputs(1 - b)
+    finish((steps - 1) % 2)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("end-to-end steps failed")
     pipe.use_buffer_set(sets[0])
-    return ms, h2d, d2h
+    device_ms = float(np.mean([s_.elapsed_time(e_) for s_, e_ in zip(ev_s, ev_e)]))
+    return ms, h2d, d2h[0], device_ms
 
 
 def large_kernel_work(pipe):
@@ -1518,7 +1538,7 @@ def run_large(args, w):
         torch.cuda.nvtx.range_pop()
 
     # ---- end to end through the public API, host buffers ----
-    e2e_step, h2d, d2h = large_e2e(B, torch, pipe, stream, args.steps, graph is not None, kept)
+    e2e_step, h2d, d2h, e2e_dev = large_e2e(B, torch, pipe, stream, args.steps, graph is not None, kept)
     e2e_ms = [e2e_step]
     e2e_step = float(np.mean(e2e_ms))
     ms, P_total, e2e_max = combine_ranks(dist, my_ms, pipe.P, e2e_step, dev)
@@ -1572,8 +1592,10 @@ def run_large(args, w):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": {"value": round(e2e_val, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4),
+                "device_ms_per_step": round(e2e_dev, 4),
                 "form": "inputs copied from pinned host memory and output sets copied back every step; step i+1's "
-                        "inputs copied into a second buffer set while step i runs"},
+                        "inputs copied into a second buffer set while step i runs, step i's outputs read while "
+                        "step i+1 runs"},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": roofline,
         "verify_hbm": {"achieved": round(v_ach, 1), "peak": peak, "unit": "GB/s", "frac": round(v_ach / peak, 4),

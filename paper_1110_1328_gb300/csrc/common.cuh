@@ -152,3 +152,23 @@ struct blsh_device_guard {
 };
 
 static inline cudaStream_t blsh_stream(void *s) { return (cudaStream_t)s; }
+
+// Statuses (one byte each) equal to `val` among the 16 bytes of v: bit i of
+// the result for byte i.  Per 32-bit word, x = w ^ (val in every byte); the
+// high bit of a byte of ~(((x & 0x7f..) + 0x7f..) | x) is set exactly when
+// the byte is zero (no carry crosses a byte), and one multiply gathers the
+// four high bits: shifted down by 7 they sit at bits 8k, and the multiplier
+// 1 + 2^7 + 2^14 + 2^21 puts byte k's on bit 21 + k with no other term on
+// bits 21..24.  About two operations a status instead of seven.
+__device__ __forceinline__ uint32_t blsh_eq16(uint4 v, uint32_t val) {
+    const uint32_t rep = val * 0x01010101u;
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t x = w[k] ^ rep;
+        const uint32_t z = ~(((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;
+        r |= ((((z >> 7) * 0x00204081u) >> 21) & 0xfu) << (4 * k);
+    }
+    return r;
+}

@@ -38,9 +38,7 @@ __device__ __forceinline__ uint32_t kept16(const uint8_t *status, long long q0, 
     uint32_t bits = 0;
     if (vec && q0 + 16 <= hi) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(status + q0));
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int i = 0; i < 16; ++i) bits |= (uint32_t)kept((uint8_t)(w[i >> 2] >> (8 * (i & 3))), mask) << i;
+        for (uint32_t m = mask; m; m &= m - 1) bits |= blsh_eq16(v, (uint32_t)(__ffs(m) - 1));   // each kept status
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i)

@@ -462,11 +462,7 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
             const long long qs = q0 + 16ll * lane;
             uint32_t surv = 0;
             if (A.vec && qs + 16 <= P) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(A.status + qs));
-                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    surv |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_LITE_SURVIVOR) << i;
+                surv = blsh_eq16(__ldg(reinterpret_cast<const uint4 *>(A.status + qs)), BLSH_LITE_SURVIVOR);
             } else {
                 for (int i = 0; i < 16; ++i)
                     if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv |= 1u << i;
@@ -493,9 +489,9 @@ __global__ void __launch_bounds__(256) lite_exact_kernel(const LiteArgs A) {
 }
 
 // Survivors into a queue (the context's survivor queue, BLSH_LITE_QUEUE_CAP
-// entries): warps scan tiles of 512 statuses in grid-stride order and append
-// their survivors' indices with one atomic per tile.  Survivors beyond the
-// queue are left for lite_exact_kernel.
+// entries): warps scan groups of four 512-status tiles in grid-stride order
+// and append their survivors' indices with one atomic per group.  Survivors
+// beyond the queue are left for lite_exact_kernel.
 __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, unsigned long long *queue) {
     long long P = A.P;
     if (A.P_dev) {
@@ -504,20 +500,23 @@ __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, uns
     }
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long q0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 512; q0 < P; q0 += nwarps * 512) {
-        const long long qs = q0 + 16ll * lane;
-        uint32_t surv = 0;
-        if (A.vec && qs + 16 <= P) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(A.status + qs));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    // four tiles of 512 statuses per warp at a time: their 16-byte loads are
+    // in flight together, and one atomic reserves queue slots for all four
+    for (long long q0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2048; q0 < P;
+         q0 += nwarps * 2048) {
+        uint32_t surv[4];
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                surv |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_LITE_SURVIVOR) << i;
-        } else {
-            for (int i = 0; i < 16; ++i)
-                if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv |= 1u << i;
+        for (int t = 0; t < 4; ++t) {
+            const long long qs = q0 + 512ll * t + 16ll * lane;
+            surv[t] = 0;
+            if (A.vec && qs + 16 <= P) {
+                surv[t] = blsh_eq16(__ldg(reinterpret_cast<const uint4 *>(A.status + qs)), BLSH_LITE_SURVIVOR);
+            } else {
+                for (int i = 0; i < 16; ++i)
+                    if (qs + i < P && A.status[qs + i] == BLSH_LITE_SURVIVOR) surv[t] |= 1u << i;
+            }
         }
-        const unsigned c = __popc(surv);
+        const unsigned c = __popc(surv[0]) + __popc(surv[1]) + __popc(surv[2]) + __popc(surv[3]);
         unsigned incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -530,8 +529,12 @@ __global__ void __launch_bounds__(256) lite_collect_kernel(const LiteArgs A, uns
         if (lane == 31) base = atomicAdd(&A.scratch->work3, (unsigned long long)total);
         base = __shfl_sync(kFull, base, 31);
         unsigned long long slot = base + incl - c;
-        for (uint32_t b = surv; b; b &= b - 1, ++slot)
-            if (slot < BLSH_LITE_QUEUE_CAP) queue[slot] = (unsigned long long)(qs + __ffs(b) - 1);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const long long qs = q0 + 512ll * t + 16ll * lane;
+            for (uint32_t b = surv[t]; b; b &= b - 1, ++slot)
+                if (slot < BLSH_LITE_QUEUE_CAP) queue[slot] = (unsigned long long)(qs + __ffs(b) - 1);
+        }
     }
 }
 

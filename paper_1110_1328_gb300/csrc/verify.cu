@@ -427,11 +427,7 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
                 const long long qs = t0 + 16ll * lane;
                 uint32_t open = 0;
                 if (vec && qs + 16 <= P) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(A.status + qs);
-                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        open |= (uint32_t)(((wv[i >> 2] >> (8 * (i & 3))) & 0xffu) == kOpenStatus) << i;
+                    open = blsh_eq16(*reinterpret_cast<const uint4 *>(A.status + qs), kOpenStatus);
                 } else {
                     for (int i = 0; i < 16; ++i)
                         if (qs + i < P && A.status[qs + i] == kOpenStatus) open |= 1u << i;
@@ -1049,10 +1045,7 @@ __global__ void __launch_bounds__(256) verify_resume_kernel(const VerifyArgs A, 
         const long long q0 = base + 16ll * lane;
         uint32_t hit = 0;
         if (vec && q0 + 16 <= P) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(A.status + q0);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int i = 0; i < 16; ++i) hit |= (uint32_t)(((w[i >> 2] >> (8 * (i & 3))) & 0xffu) == BLSH_NEEDS_HASHES) << i;
+            hit = blsh_eq16(*reinterpret_cast<const uint4 *>(A.status + q0), BLSH_NEEDS_HASHES);
         } else {
             for (int i = 0; i < 16; ++i)
                 if (q0 + i < P && A.status[q0 + i] == BLSH_NEEDS_HASHES) hit |= 1u << i;
