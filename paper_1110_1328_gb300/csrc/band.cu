@@ -294,11 +294,17 @@ __host__ __device__ inline size_t emit_warp_region(int ck_words, int win) {
     const size_t b = (size_t)win * (stage_stride(ck_words) * 16 + 8 + 4) + 32 * 16 * kw4 + 32 * 4;
     return (b + 15) & ~(size_t)15;
 }
-// (two CTAs of eight warps per SM)
-inline size_t emit_warp_budget(int ck_words) { return ck_words <= 16 ? 13 * 1024 : 14 * 1024; }
-int emit_warp_win(int ck_words) {
+// (two CTAs of eight warps per SM; three for the count pass over key rows
+// of at most 64 bytes, whose smaller window measured faster there -- the
+// window only decides which partners are staged, not which pairs are
+// emitted, so the two passes may differ)
+inline size_t emit_warp_budget(int ck_words, bool count_pass) {
+    return ck_words <= 16 ? (count_pass ? 9 * 1024 : 13 * 1024) : 14 * 1024;
+}
+inline int emit_warp_ctas(int ck_words, bool count_pass) { return ck_words <= 16 && count_pass ? 3 : 2; }
+int emit_warp_win(int ck_words, bool count_pass) {
     int w = 32;
-    while (w < kEmitWinMax && emit_warp_region(ck_words, w + 32) <= emit_warp_budget(ck_words)) w += 32;
+    while (w < kEmitWinMax && emit_warp_region(ck_words, w + 32) <= emit_warp_budget(ck_words, count_pass)) w += 32;
     return w;
 }
 
@@ -601,7 +607,7 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
 // gives each lane one (emit_flat).  Pairs of position i are counted, or
 // written, in partner order, the order emit_kernel uses.
 template <bool WRITE, int KW4>
-__global__ void __launch_bounds__(256, 2) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
+__global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
                                                              const uint32_t *vals, long long n,
                                                              unsigned long long *counts, uint32_t *pairs,
                                                              long long cap, int win_cap,
@@ -911,29 +917,33 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
         BLSH_LAUNCHED(ctx, "class_id_kernel");
     }
     const bool staged = (kind == BLSH_COSINE || A.exact_classes) && A.ck_words <= kStageWords;
-    const int win_cap = staged ? emit_warp_win(A.ck_words) : 0;
-    const size_t smem = staged ? 8 * emit_warp_region(A.ck_words, win_cap) : 0;
-    const unsigned egrid = (unsigned)ctx->sm_count * 2;
+    // per pass: the window, its shared memory and the grid (CTAs per SM)
+    const int win_c = staged ? emit_warp_win(A.ck_words, true) : 0;
+    const int win_w = staged ? emit_warp_win(A.ck_words, false) : 0;
+    const size_t smem_c = staged ? 8 * emit_warp_region(A.ck_words, win_c) : 0;
+    const size_t smem_w = staged ? 8 * emit_warp_region(A.ck_words, win_w) : 0;
+    const unsigned egrid_c = (unsigned)(ctx->sm_count * emit_warp_ctas(A.ck_words, true));
+    const unsigned egrid_w = (unsigned)(ctx->sm_count * emit_warp_ctas(A.ck_words, false));
     // the two chunk counters (count pass, write pass)
     unsigned long long *next_chunk = &ctx->scratch->band_work[0];
     BLSH_CUDA(ctx, cudaMemsetAsync(next_chunk, 0, 2 * sizeof(unsigned long long), s));
     if (staged) {
         if (A.ck_words <= 16) {
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 4>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<true, 4>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
             blsh_time_start(ctx, s);
-            emit_warp_kernel<false, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                win_cap, next_chunk);
+            emit_warp_kernel<false, 4><<<egrid_c, 256, smem_c, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                    win_c, next_chunk);
         } else {
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 8>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<true, 8>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
             blsh_time_start(ctx, s);
-            emit_warp_kernel<false, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                win_cap, next_chunk);
+            emit_warp_kernel<false, 8><<<egrid_c, 256, smem_c, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                                    win_c, next_chunk);
         }
     } else {
         blsh_time_start(ctx, s);
@@ -948,11 +958,11 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     blsh_time_stop(ctx, "exclusive scan (3 launches)");
     blsh_time_start(ctx, s);
     if (staged && A.ck_words <= 16)
-        emit_warp_kernel<true, 4><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                           win_cap, next_chunk + 1);
+        emit_warp_kernel<true, 4><<<egrid_w, 256, smem_w, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                               win_w, next_chunk + 1);
     else if (staged)
-        emit_warp_kernel<true, 8><<<egrid, 256, smem, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                           win_cap, next_chunk + 1);
+        emit_warp_kernel<true, 8><<<egrid_w, 256, smem_w, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
+                                                               win_w, next_chunk + 1);
     else
         emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     BLSH_LAUNCHED(ctx, staged ? "emit_warp_kernel (write pass)" : "emit_kernel (write pass)");

@@ -157,7 +157,9 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 
 constexpr int kSrpMaxPerThread = 16;
 constexpr int kSrpLooseRow = 256;   // rows up to this length use the 2^15 sum|v| magnitude bound (two-byte codes)
-constexpr int kSrpBatch = 8;       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
+constexpr int kSrpBatch = 8;
+constexpr int kSrpGrab = 8;         // (row, piece) items a CTA of srp_sparse4_kernel takes per grab
+constexpr int kSrpLongRow = 1024;   // rows longer than this are projected first       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
 constexpr int kSrpChunk = 256;
 
 template <typename RT>
@@ -294,8 +296,8 @@ __device__ __forceinline__ unsigned long long f2_codes(uint32_t w) {
 // roundings in any chain rather than n: a long row leaves far fewer signs to
 // the FP64 recheck.  The four bits of
 // a group form a nibble; eight lanes OR their nibbles into one signature
-// word with shuffles.  A CTA takes one (row, piece of 4 V T columns) at a
-// time.
+// word with shuffles.  CTAs take (row, piece of 4 V T columns) items
+// kSrpGrab at a time from a counter.
 template <int V, typename RT>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
@@ -304,210 +306,250 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                                                           int col_first, int pieces,
                                                           const uint8_t *__restrict__ row_mask,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
-                                                          uint2 *__restrict__ queue) {
+                                                          uint2 *__restrict__ queue,
+                                                          const uint32_t *__restrict__ long_rows) {
     // columns col_first .. col_first + pieces 4 V T - 1 of the signatures of
-    // the rows row_mask selects (all rows when it is NULL); a CTA takes one
-    // (row, piece of 4 V T columns) at a time, so that a few selected rows
-    // still spread over many CTAs
+    // the rows row_mask selects (all rows when it is NULL); a CTA works on
+    // one (row, piece of 4 V T columns) at a time, so that a few selected
+    // rows still spread over many CTAs
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int words = bits >> 5;
     unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    for (long long item = blockIdx.x; item < N * pieces; item += gridDim.x) {
-        const long long row = pieces == 1 ? item : item / pieces;   // (a 64-bit division is a long call)
-        const int col0 = col_first + (int)(item - row * pieces) * 4 * V * T;
-        if (row_mask && !row_mask[row]) continue;
-        const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-        constexpr bool Q16 = sizeof(RT) == 2;
-        float acc[4 * V], mag[4 * V], tot[4 * V];
+    // items are handed out kSrpGrab at a time from a counter: row lengths
+    // follow a power law (a single row can hold more work than a thousand
+    // average ones), and a fixed share per CTA left most of the GPU idle
+    // while the CTAs that drew the longest rows finished
+    __shared__ unsigned long long s_next;
+    // the listed long rows first (srp_long_rows_kernel; none if the list
+    // overflowed), then every row, skipping those already done
+    const unsigned long long listed = scratch->long_count;
+    const long long n_long = listed <= BLSH_LONG_ROWS_CAP ? (long long)listed : 0;
+    const long long items_long = n_long * pieces;
+    const long long items = items_long + N * pieces;
+    for (;;) {
+        __syncthreads();                                   // every thread has read the previous grab
+        if (threadIdx.x == 0) s_next = atomicAdd(&scratch->hash_work, (unsigned long long)kSrpGrab);
+        __syncthreads();
+        const long long g0 = (long long)s_next;
+        if (g0 >= items) break;
+        const long long g1 = g0 + kSrpGrab < items ? g0 + kSrpGrab : items;
+        for (long long item = g0; item < g1; ++item) {
+            const bool in_list = item < items_long;
+            const long long it = in_list ? item : item - items_long;
+            const long long slot = pieces == 1 ? it : it / pieces;      // (a 64-bit division is a long call)
+            const long long row = in_list ? (long long)__ldg(long_rows + slot) : slot;
+            const int col0 = col_first + (int)(it - slot * pieces) * 4 * V * T;
+            if (!in_list && row_mask && !row_mask[row]) continue;
+            const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
+            if (!in_list && n_long > 0 && e - s > kSrpLongRow) continue;   // projected from the list
+            constexpr bool Q16 = sizeof(RT) == 2;
+            float acc[4 * V], mag[4 * V], tot[4 * V];
 #pragma unroll
-        for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = tot[u] = 0.0f;
-        // two-byte codes: the same sums kept as pairs of columns (one 64-bit
-        // register each) for the paired instructions, unpacked once per row
-        unsigned long long acc2[2 * V], mag2[2 * V], tot2[2 * V];
+            for (int u = 0; u < 4 * V; ++u) acc[u] = mag[u] = tot[u] = 0.0f;
+            // two-byte codes: the same sums kept as pairs of columns (one 64-bit
+            // register each) for the paired instructions, unpacked once per row
+            unsigned long long acc2[2 * V], mag2[2 * V], tot2[2 * V];
 #pragma unroll
-        for (int u = 0; u < 2 * V; ++u) acc2[u] = mag2[u] = tot2[u] = 0ull;
-        // Rows of at most kSrpLooseRow nonzeros (two-byte codes): the
-        // magnitude bound 2^15 sum|v_i| (every decoded code has |q - 2^15| <=
-        // 2^15) instead of each column's sum|v_i| |q_ij - 2^15|; about ten
-        // times looser, but the blocked sums keep short rows' bounds small,
-        // and it saves two paired FMAs and four masks per nonzero
-        const bool loose = Q16 && e - s <= kSrpLooseRow;
-        float sav = 0.0f;
-        // the row's nonzeros 32 at a time: lane l of every warp loads entry
-        // l (coalesced), then the gathers of kSrpBatch / V entries are issued
-        // together (their indices come by shuffle), so that a long row is not
-        // a chain of dependent loads
-        constexpr int NB = kSrpBatch / V > 0 ? kSrpBatch / V : 1;
-        for (long long k0 = s; k0 < e; k0 += 32) {
-            const int cnt = e - k0 < 32 ? (int)(e - k0) : 32;
-            uint32_t my_ix = 0;
-            float my_v = 0.0f;
-            if (lane < cnt) {
-                my_ix = __ldg(indices + k0 + lane);
-                my_v = __ldg(values + k0 + lane);
-                if (my_ix >= dim) {   // malformed entry: counted once, contributes nothing
-                    bad += t < 32;
-                    my_ix = 0;
-                    my_v = 0.0f;
+            for (int u = 0; u < 2 * V; ++u) acc2[u] = mag2[u] = tot2[u] = 0ull;
+            // Rows of at most kSrpLooseRow nonzeros (two-byte codes): the
+            // magnitude bound 2^15 sum|v_i| (every decoded code has |q - 2^15| <=
+            // 2^15) instead of each column's sum|v_i| |q_ij - 2^15|; about ten
+            // times looser, but the blocked sums keep short rows' bounds small,
+            // and it saves two paired FMAs and four masks per nonzero
+            const bool loose = Q16 && e - s <= kSrpLooseRow;
+            float sav = 0.0f;
+            // the row's nonzeros 32 at a time: lane l of every warp loads entry
+            // l (coalesced), then the gathers of kSrpBatch / V entries are issued
+            // together (their indices come by shuffle), so that a long row is not
+            // a chain of dependent loads
+            constexpr int NB = kSrpBatch / V > 0 ? kSrpBatch / V : 1;
+            for (long long k0 = s; k0 < e; k0 += 32) {
+                const int cnt = e - k0 < 32 ? (int)(e - k0) : 32;
+                uint32_t my_ix = 0;
+                float my_v = 0.0f;
+                if (lane < cnt) {
+                    my_ix = __ldg(indices + k0 + lane);
+                    my_v = __ldg(values + k0 + lane);
+                    if (my_ix >= dim) {   // malformed entry: counted once, contributes nothing
+                        bad += t < 32;
+                        my_ix = 0;
+                        my_v = 0.0f;
+                    }
                 }
-            }
-            if constexpr (Q16) {
-                // the decoded value of code q is (q - 2^15) 2^-12: (2^23 + q) - (2^23 + 2^15),
-                // exact, with the sums kept in units of 2^-12
-                const unsigned long long off2 = f2_pack(-8421376.0f, -8421376.0f);
-                auto chunk = [&](auto with_mag) {
-                    constexpr bool kMag = decltype(with_mag)::value;
-                    for (int u0 = 0; u0 < cnt; u0 += NB) {
-                        uint2 qb[NB][V];
-                        float vb[NB];
+                if constexpr (Q16) {
+                    // the decoded value of code q is (q - 2^15) 2^-12: (2^23 + q) - (2^23 + 2^15),
+                    // exact, with the sums kept in units of 2^-12
+                    const unsigned long long off2 = f2_pack(-8421376.0f, -8421376.0f);
+                    auto chunk = [&](auto with_mag) {
+                        constexpr bool kMag = decltype(with_mag)::value;
+                        for (int u0 = 0; u0 < cnt; u0 += NB) {
+                            uint2 qb[NB][V];
+                            float vb[NB];
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
-                            vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
-                            const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
+                            for (int b = 0; b < NB; ++b) {
+                                const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                                vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
+                                const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
 #pragma unroll
-                            for (int g = 0; g < V; ++g) qb[b][g] = __ldg(Rrow + g * T);
-                        }
+                                for (int g = 0; g < V; ++g) qb[b][g] = __ldg(Rrow + g * T);
+                            }
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            const unsigned long long v2 = f2_pack(vb[b], vb[b]);
-                            const unsigned long long av2 = f2_pack(fabsf(vb[b]), fabsf(vb[b]));
-                            if (!kMag) sav += fabsf(vb[b]);
+                            for (int b = 0; b < NB; ++b) {
+                                const unsigned long long v2 = f2_pack(vb[b], vb[b]);
+                                const unsigned long long av2 = f2_pack(fabsf(vb[b]), fabsf(vb[b]));
+                                if (!kMag) sav += fabsf(vb[b]);
 #pragma unroll
-                            for (int g = 0; g < V; ++g) {
-                                const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
-                                const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
-                                acc2[2 * g] = f2_fma(v2, d01, acc2[2 * g]);
-                                acc2[2 * g + 1] = f2_fma(v2, d23, acc2[2 * g + 1]);
-                                if (kMag) {
-                                    mag2[2 * g] = f2_fma(av2, d01 & 0x7fffffff7fffffffull, mag2[2 * g]);
-                                    mag2[2 * g + 1] = f2_fma(av2, d23 & 0x7fffffff7fffffffull, mag2[2 * g + 1]);
+                                for (int g = 0; g < V; ++g) {
+                                    const unsigned long long d01 = f2_add(f2_codes(qb[b][g].x), off2);
+                                    const unsigned long long d23 = f2_add(f2_codes(qb[b][g].y), off2);
+                                    acc2[2 * g] = f2_fma(v2, d01, acc2[2 * g]);
+                                    acc2[2 * g + 1] = f2_fma(v2, d23, acc2[2 * g + 1]);
+                                    if (kMag) {
+                                        mag2[2 * g] = f2_fma(av2, d01 & 0x7fffffff7fffffffull, mag2[2 * g]);
+                                        mag2[2 * g + 1] = f2_fma(av2, d23 & 0x7fffffff7fffffffull, mag2[2 * g + 1]);
+                                    }
                                 }
                             }
                         }
+                    };
+                    if (loose) chunk(std::false_type{});
+                    else chunk(std::true_type{});
+                    // the block of (at most) 32 nonzeros into the total
+#pragma unroll
+                    for (int u = 0; u < 2 * V; ++u) {
+                        tot2[u] = f2_add(tot2[u], acc2[u]);
+                        acc2[u] = 0ull;
                     }
-                };
-                if (loose) chunk(std::false_type{});
-                else chunk(std::true_type{});
-                // the block of (at most) 32 nonzeros into the total
-#pragma unroll
-                for (int u = 0; u < 2 * V; ++u) {
-                    tot2[u] = f2_add(tot2[u], acc2[u]);
-                    acc2[u] = 0ull;
+                    continue;
                 }
-                continue;
-            }
-            for (int u0 = 0; u0 < cnt; u0 += NB) {
-                float4 r[NB][V];
-                float vb[NB];
+                for (int u0 = 0; u0 < cnt; u0 += NB) {
+                    float4 r[NB][V];
+                    float vb[NB];
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
-                    vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
-                    if constexpr (Q16) {
-                        // four codes per load; a code q stands for (q - 2^15) 2^-12, and
-                        // the float with bit pattern 0x4b000000 | q is 2^23 + q, so
-                        // subtracting 2^23 + 2^15 gives q - 2^15 exactly (sums scaled by 2^12)
-                        const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
+                    for (int b = 0; b < NB; ++b) {
+                        const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                        vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
+                        if constexpr (Q16) {
+                            // four codes per load; a code q stands for (q - 2^15) 2^-12, and
+                            // the float with bit pattern 0x4b000000 | q is 2^23 + q, so
+                            // subtracting 2^23 + 2^15 gives q - 2^15 exactly (sums scaled by 2^12)
+                            const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
+#pragma unroll
+                            for (int g = 0; g < V; ++g) {
+                                const uint2 q = __ldg(Rrow + g * T);
+                                r[b][g] = make_float4(__int_as_float(0x4b000000u | (q.x & 0xffffu)) - 8421376.0f,
+                                                      __int_as_float(0x4b000000u | (q.x >> 16)) - 8421376.0f,
+                                                      __int_as_float(0x4b000000u | (q.y & 0xffffu)) - 8421376.0f,
+                                                      __int_as_float(0x4b000000u | (q.y >> 16)) - 8421376.0f);
+                            }
+                        } else {
+                            const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
+#pragma unroll
+                            for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const float v = vb[b], av = fabsf(v);
 #pragma unroll
                         for (int g = 0; g < V; ++g) {
-                            const uint2 q = __ldg(Rrow + g * T);
-                            r[b][g] = make_float4(__int_as_float(0x4b000000u | (q.x & 0xffffu)) - 8421376.0f,
-                                                  __int_as_float(0x4b000000u | (q.x >> 16)) - 8421376.0f,
-                                                  __int_as_float(0x4b000000u | (q.y & 0xffffu)) - 8421376.0f,
-                                                  __int_as_float(0x4b000000u | (q.y >> 16)) - 8421376.0f);
+                            acc[4 * g + 0] = __fmaf_rn(v, r[b][g].x, acc[4 * g + 0]);
+                            acc[4 * g + 1] = __fmaf_rn(v, r[b][g].y, acc[4 * g + 1]);
+                            acc[4 * g + 2] = __fmaf_rn(v, r[b][g].z, acc[4 * g + 2]);
+                            acc[4 * g + 3] = __fmaf_rn(v, r[b][g].w, acc[4 * g + 3]);
+                            mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[b][g].x), mag[4 * g + 0]);
+                            mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[b][g].y), mag[4 * g + 1]);
+                            mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[b][g].z), mag[4 * g + 2]);
+                            mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[b][g].w), mag[4 * g + 3]);
                         }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4 * V; ++u) {
+                    tot[u] = __fadd_rn(tot[u], acc[u]);
+                    acc[u] = 0.0f;
+                }
+            }
+            if constexpr (sizeof(RT) == 2) {
+#pragma unroll
+                for (int u = 0; u < 2 * V; ++u) {
+                    f2_unpack(tot2[u], tot[2 * u], tot[2 * u + 1]);
+                    f2_unpack(mag2[u], mag[2 * u], mag[2 * u + 1]);
+                }
+                if (loose) {
+#pragma unroll
+                    for (int u = 0; u < 4 * V; ++u) mag[u] = 32768.0f * sav;
+                }
+            }
+            // the row length through a 32-bit integer (a 64-bit conversion would run
+            // on the narrow FP64 pipe); rows past 2^30 count as 2^30, which is long
+            const int len = (int)(e - s < (1ll << 30) ? e - s : (1ll << 30));
+            const float n = (float)len;
+            const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
+            // Roundings in a column's sum: a block's chain (at most 32 FMAs, error
+            // <= gamma_32 of its magnitudes) and the chain of block totals (at
+            // most ceil(n / 32) - 1 adds), so |sum - exact| <= (gamma_32 +
+            // gamma_nb + gamma_32 gamma_nb) sum|p|, below 1.12 (min(n, 32) + nb) u
+            // mag when n u <= 0.05 (mag, the computed sum of magnitudes, is within
+            // gamma_n of sum|p|); each rounding near underflow adds at most 2^-150,
+            // and there are at most 2n of them.
+            const float kround = fminf(n, 32.0f) + (float)((len + 31) >> 5);
+#pragma unroll
+            for (int g = 0; g < V; ++g) {
+                uint32_t nib = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int u = 4 * g + c;
+                    const float bound = 1.25f * kround * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
+                    bool bit;
+                    if (!long_row && fabsf(tot[u]) > bound) {
+                        bit = tot[u] >= 0.0f;
                     } else {
-                        const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
-#pragma unroll
-                        for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
+                        // undecided: queue it for srp_recheck_kernel (bit left 0 here),
+                        // or recompute in line if the queue is full
+                        const uint32_t j = col0 + 4 * (t + g * T) + c;
+                        const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
+                        if (slot < BLSH_RECHECK_CAP) {
+                            queue[slot] = make_uint2((uint32_t)row, j);
+                            bit = false;
+                        } else {
+                            const double d = srp_recheck_fp64<RT>(indices, values, s, e, R, dim, bits, j);
+                            bit = d >= 0.0;
+                            ++rechecked;
+                            zeros += d == 0.0;
+                        }
                     }
+                    nib |= (uint32_t)bit << c;
                 }
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const float v = vb[b], av = fabsf(v);
-#pragma unroll
-                    for (int g = 0; g < V; ++g) {
-                        acc[4 * g + 0] = __fmaf_rn(v, r[b][g].x, acc[4 * g + 0]);
-                        acc[4 * g + 1] = __fmaf_rn(v, r[b][g].y, acc[4 * g + 1]);
-                        acc[4 * g + 2] = __fmaf_rn(v, r[b][g].z, acc[4 * g + 2]);
-                        acc[4 * g + 3] = __fmaf_rn(v, r[b][g].w, acc[4 * g + 3]);
-                        mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[b][g].x), mag[4 * g + 0]);
-                        mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[b][g].y), mag[4 * g + 1]);
-                        mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[b][g].z), mag[4 * g + 2]);
-                        mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[b][g].w), mag[4 * g + 3]);
-                    }
-                }
+                uint32_t word = nib << (4 * (lane & 7));
+                word |= __shfl_xor_sync(kFull, word, 1);
+                word |= __shfl_xor_sync(kFull, word, 2);
+                word |= __shfl_xor_sync(kFull, word, 4);
+                if ((lane & 7) == 0) sig[(size_t)row * words + (col0 >> 5) + ((t + g * T) >> 3)] = word;
             }
-#pragma unroll
-            for (int u = 0; u < 4 * V; ++u) {
-                tot[u] = __fadd_rn(tot[u], acc[u]);
-                acc[u] = 0.0f;
-            }
-        }
-        if constexpr (sizeof(RT) == 2) {
-#pragma unroll
-            for (int u = 0; u < 2 * V; ++u) {
-                f2_unpack(tot2[u], tot[2 * u], tot[2 * u + 1]);
-                f2_unpack(mag2[u], mag[2 * u], mag[2 * u + 1]);
-            }
-            if (loose) {
-#pragma unroll
-                for (int u = 0; u < 4 * V; ++u) mag[u] = 32768.0f * sav;
-            }
-        }
-        // the row length through a 32-bit integer (a 64-bit conversion would run
-        // on the narrow FP64 pipe); rows past 2^30 count as 2^30, which is long
-        const int len = (int)(e - s < (1ll << 30) ? e - s : (1ll << 30));
-        const float n = (float)len;
-        const bool long_row = n * 5.9604644775390625e-8f > 0.05f;   // the 1.25 slack needs n u <= 0.05
-        // Roundings in a column's sum: a block's chain (at most 32 FMAs, error
-        // <= gamma_32 of its magnitudes) and the chain of block totals (at
-        // most ceil(n / 32) - 1 adds), so |sum - exact| <= (gamma_32 +
-        // gamma_nb + gamma_32 gamma_nb) sum|p|, below 1.12 (min(n, 32) + nb) u
-        // mag when n u <= 0.05 (mag, the computed sum of magnitudes, is within
-        // gamma_n of sum|p|); each rounding near underflow adds at most 2^-150,
-        // and there are at most 2n of them.
-        const float kround = fminf(n, 32.0f) + (float)((len + 31) >> 5);
-#pragma unroll
-        for (int g = 0; g < V; ++g) {
-            uint32_t nib = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int u = 4 * g + c;
-                const float bound = 1.25f * kround * 5.9604644775390625e-8f * mag[u] + n * 1.4e-45f;
-                bool bit;
-                if (!long_row && fabsf(tot[u]) > bound) {
-                    bit = tot[u] >= 0.0f;
-                } else {
-                    // undecided: queue it for srp_recheck_kernel (bit left 0 here),
-                    // or recompute in line if the queue is full
-                    const uint32_t j = col0 + 4 * (t + g * T) + c;
-                    const unsigned long long slot = atomicAdd(&scratch->recheck_count, 1ull);
-                    if (slot < BLSH_RECHECK_CAP) {
-                        queue[slot] = make_uint2((uint32_t)row, j);
-                        bit = false;
-                    } else {
-                        const double d = srp_recheck_fp64<RT>(indices, values, s, e, R, dim, bits, j);
-                        bit = d >= 0.0;
-                        ++rechecked;
-                        zeros += d == 0.0;
-                    }
-                }
-                nib |= (uint32_t)bit << c;
-            }
-            uint32_t word = nib << (4 * (lane & 7));
-            word |= __shfl_xor_sync(kFull, word, 1);
-            word |= __shfl_xor_sync(kFull, word, 2);
-            word |= __shfl_xor_sync(kFull, word, 4);
-            if ((lane & 7) == 0) sig[(size_t)row * words + (col0 >> 5) + ((t + g * T) >> 3)] = word;
         }
     }
     if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
     if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
     if (zeros) atomicAdd(&scratch->counters[3], zeros);
+}
+
+// The rows longer than kSrpLongRow nonzeros (of those row_mask selects):
+// srp_sparse4_kernel projects them before all others, so that no long row
+// starts last.  Rows past the list's capacity leave the list unused.
+__global__ void __launch_bounds__(256) srp_long_rows_kernel(const int64_t *__restrict__ indptr, long long N,
+                                                            const uint8_t *__restrict__ row_mask,
+                                                            uint32_t *__restrict__ long_rows,
+                                                            blsh_dev_scratch *scratch) {
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
+         row += (long long)gridDim.x * blockDim.x) {
+        if (__ldg(indptr + row + 1) - __ldg(indptr + row) > kSrpLongRow && (!row_mask || row_mask[row])) {
+            const unsigned long long slot = atomicAdd(&scratch->long_count, 1ull);
+            if (slot < BLSH_LONG_ROWS_CAP) long_rows[slot] = (uint32_t)row;
+        }
+    }
 }
 
 // The queued signs: one warp per (row, bit).  The lanes form the row's exact
@@ -733,15 +775,23 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N * pieces < cap ? N * pieces : cap);
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->hash_work, 0, 2 * sizeof(unsigned long long), s));  // + long_count
     uint2 *q = ctx->recheck_queue;
     blsh_dev_scratch *scr = ctx->scratch;
+    {
+        const long long blocks = (N + 255) / 256, lcap = (long long)ctx->sm_count * 4;
+        blsh_time_start(ctx, s);
+        srp_long_rows_kernel<<<(unsigned)(blocks < lcap ? blocks : lcap), 256, 0, s>>>(indptr, N, row_mask,
+                                                                                      ctx->long_rows, scr);
+        BLSH_LAUNCHED(ctx, "srp_long_rows_kernel");
+    }
     const char *name = sizeof(RT) == 2 ? "srp_sparse4_kernel (two-byte codes)" : "srp_sparse4_kernel";
     blsh_time_start(ctx, s);
     switch (V) {
-    case 1: srp_sparse4_kernel<1, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    case 2: srp_sparse4_kernel<2, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    case 3: srp_sparse4_kernel<3, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
-    default: srp_sparse4_kernel<4, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q); break;
+    case 1: srp_sparse4_kernel<1, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
+    case 2: srp_sparse4_kernel<2, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
+    case 3: srp_sparse4_kernel<3, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
+    default: srp_sparse4_kernel<4, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
     }
     BLSH_LAUNCHED(ctx, name);
     blsh_time_start(ctx, s);

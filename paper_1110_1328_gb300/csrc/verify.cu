@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
 // decisions of verify_kernel's first step, in the same order.  A pair that
 // stops gets its outputs; a pair Algorithm 1 leaves open is marked
 // kOpenStatus for the second pass (verify_kernel with OPEN).  A lane takes
-// two pairs at a time, so that their loads overlap.  The stops are counted
-// with one ballot per level.
+// two pairs at a time, so that their loads overlap.  Each lane counts its
+// stops per level in registers; the warp adds them once at the end.
 template <bool PLANE>
 __global__ void __launch_bounds__(256) verify_first_kernel(const VerifyArgs A) {
     __shared__ unsigned s_h[4];
@@ -617,6 +617,7 @@ __global__ void __launch_bounds__(256) verify_first_kernel(const VerifyArgs A) {
         blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
     };
     auto row = [&](uint32_t o) { return PLANE ? __ldg(A.plane + o) : ldg4(A.sig + (size_t)o * A.W); };
+    unsigned hc0 = 0, hc1 = 0, hc2 = 0, hc3 = 0;   // this lane's stops at levels 0..3
     // two pairs per lane at a time (pairs q and q + stride): both pairs'
     // loads are in flight before either is decided
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -641,12 +642,15 @@ __global__ void __launch_bounds__(256) verify_first_kernel(const VerifyArgs A) {
         else if (qa < P) bad_pair(qa);
         if (okb) hb = decide(qb, pb, xb, yb);
         else if (qb < P) bad_pair(qb);
-        unsigned mine = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned z = __ballot_sync(kFull, ha == c), z2 = __ballot_sync(kFull, hb == c);
-            if (lane == c) mine = (unsigned)(__popc(z) + __popc(z2));
-        }
+        hc0 += (ha == 0) + (hb == 0);
+        hc1 += (ha == 1) + (hb == 1);
+        hc2 += (ha == 2) + (hb == 2);
+        hc3 += (ha == 3) + (hb == 3);
+    }
+    {
+        const unsigned c0 = __reduce_add_sync(kFull, hc0), c1 = __reduce_add_sync(kFull, hc1);
+        const unsigned c2 = __reduce_add_sync(kFull, hc2), c3 = __reduce_add_sync(kFull, hc3);
+        const unsigned mine = lane == 0 ? c0 : lane == 1 ? c1 : lane == 2 ? c2 : lane == 3 ? c3 : 0u;
         if (mine) atomicAdd(&s_h[lane], mine);
     }
     __syncthreads();
