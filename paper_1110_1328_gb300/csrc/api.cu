@@ -82,20 +82,11 @@ extern "C" int blsh_ctx_create(blsh_ctx **out, int device) {
         delete ctx;
         return BLSH_ENOMEM;
     }
-    if (cudaMalloc((void **)&ctx->long_rows, sizeof(uint32_t) * BLSH_LONG_ROWS_CAP) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(ctx->scratch);
-        cudaFree(ctx->recheck_queue);
-        cudaFree(ctx->lite_queue);
-        delete ctx;
-        return BLSH_ENOMEM;
-    }
     if (cudaMemset(ctx->scratch, 0, sizeof(blsh_dev_scratch)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(ctx->scratch);
         cudaFree(ctx->recheck_queue);
         cudaFree(ctx->lite_queue);
-        cudaFree(ctx->long_rows);
         delete ctx;
         return BLSH_EDEVICE;
     }
@@ -115,7 +106,6 @@ extern "C" int blsh_ctx_destroy(blsh_ctx *ctx) {
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->recheck_queue) cudaFree(ctx->recheck_queue);
         if (ctx->lite_queue) cudaFree(ctx->lite_queue);
-        if (ctx->long_rows) cudaFree(ctx->long_rows);
     }
     delete ctx;
     return BLSH_OK;

@@ -17,7 +17,6 @@
 #define BLSH_MAX_NMAX 4096
 #define BLSH_COMPACT_MAX_CTAS 2048
 #define BLSH_RECHECK_CAP (1u << 20)   // queued SRP sign rechecks per call (8 MiB per context)
-#define BLSH_LONG_ROWS_CAP (1u << 16) // listed long rows of a sparse projection call (256 KiB per context)
 #define BLSH_LITE_QUEUE_CAP (1u << 23) // queued Lite survivors per call (64 MiB per context)
 
 // Device-side scratch owned by a context.  Every call zeroes what it uses
@@ -32,7 +31,6 @@ struct blsh_dev_scratch {
     unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
     unsigned long long band_work[2];   // banding: next chunk of positions (count pass, write pass)
     unsigned long long hash_work;      // sparse projection: next (row, piece) item handed out
-    unsigned long long long_count;     // sparse projection: long rows listed (may exceed the list)
     unsigned int norm2_valid;          // Lite: the rows' squared norms were formed for this call
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA
 };
@@ -44,7 +42,6 @@ struct blsh_ctx {
     size_t smem_optin = 0;
     blsh_dev_scratch *scratch = nullptr;
     uint2 *recheck_queue = nullptr;                   // [BLSH_RECHECK_CAP] (row, bit) of undecided SRP signs
-    uint32_t *long_rows = nullptr;                    // [BLSH_LONG_ROWS_CAP] long rows, projected first
     unsigned long long *lite_queue = nullptr;         // [BLSH_LITE_QUEUE_CAP] Lite survivors (pair indices)
     // per-object buffers, sized by blsh_ctx_reserve (never by a hot call)
     void *plane = nullptr;                            // verification: [plane_cap] first four words of each row

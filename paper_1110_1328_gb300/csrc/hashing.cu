@@ -158,8 +158,7 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 constexpr int kSrpMaxPerThread = 16;
 constexpr int kSrpLooseRow = 256;   // rows up to this length use the 2^15 sum|v| magnitude bound (two-byte codes)
 constexpr int kSrpBatch = 8;
-constexpr int kSrpGrab = 8;         // (row, piece) items a CTA of srp_sparse4_kernel takes per grab
-constexpr int kSrpLongRow = 1024;   // rows longer than this are projected first       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
+constexpr int kSrpGrab = 8;         // (row, piece) items a CTA of srp_sparse4_kernel takes per grab       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
 constexpr int kSrpChunk = 256;
 
 template <typename RT>
@@ -296,8 +295,8 @@ __device__ __forceinline__ unsigned long long f2_codes(uint32_t w) {
 // roundings in any chain rather than n: a long row leaves far fewer signs to
 // the FP64 recheck.  The four bits of
 // a group form a nibble; eight lanes OR their nibbles into one signature
-// word with shuffles.  CTAs take (row, piece of 4 V T columns) items
-// kSrpGrab at a time from a counter.
+// word with shuffles.  CTAs take (row, piece of 4 V T columns) items from a
+// counter, kSrpGrab at a time (a fixed share per CTA when there are few).
 template <int V, typename RT>
 __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restrict__ indptr,
                                                           const uint32_t *__restrict__ indices,
@@ -306,8 +305,7 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                                                           int col_first, int pieces,
                                                           const uint8_t *__restrict__ row_mask,
                                                           uint32_t *__restrict__ sig, blsh_dev_scratch *scratch,
-                                                          uint2 *__restrict__ queue,
-                                                          const uint32_t *__restrict__ long_rows) {
+                                                          uint2 *__restrict__ queue, int grab) {
     // columns col_first .. col_first + pieces 4 V T - 1 of the signatures of
     // the rows row_mask selects (all rows when it is NULL); a CTA works on
     // one (row, piece of 4 V T columns) at a time, so that a few selected
@@ -317,33 +315,35 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
     const int lane = t & 31;
     const int words = bits >> 5;
     unsigned long long rechecked = 0, zeros = 0, bad = 0;
-    // items are handed out kSrpGrab at a time from a counter: row lengths
+    // items are handed out `grab` at a time from a counter: row lengths
     // follow a power law (a single row can hold more work than a thousand
     // average ones), and a fixed share per CTA left most of the GPU idle
     // while the CTAs that drew the longest rows finished
+    // (grab == 0: a fixed share per CTA, items blockIdx.x, blockIdx.x +
+    // gridDim.x, ...: few items per CTA, where a counter would cost more
+    // than it balances)
     __shared__ unsigned long long s_next;
-    // the listed long rows first (srp_long_rows_kernel; none if the list
-    // overflowed), then every row, skipping those already done
-    const unsigned long long listed = scratch->long_count;
-    const long long n_long = listed <= BLSH_LONG_ROWS_CAP ? (long long)listed : 0;
-    const long long items_long = n_long * pieces;
-    const long long items = items_long + N * pieces;
+    const long long items = N * pieces;
+    long long next_static = blockIdx.x;
     for (;;) {
-        __syncthreads();                                   // every thread has read the previous grab
-        if (threadIdx.x == 0) s_next = atomicAdd(&scratch->hash_work, (unsigned long long)kSrpGrab);
-        __syncthreads();
-        const long long g0 = (long long)s_next;
+        long long g0, g1;
+        if (grab > 0) {
+            __syncthreads();                               // every thread has read the previous grab
+            if (threadIdx.x == 0) s_next = atomicAdd(&scratch->hash_work, (unsigned long long)grab);
+            __syncthreads();
+            g0 = (long long)s_next;
+            g1 = g0 + grab < items ? g0 + grab : items;
+        } else {
+            g0 = next_static;
+            g1 = g0 + 1;
+            next_static += gridDim.x;
+        }
         if (g0 >= items) break;
-        const long long g1 = g0 + kSrpGrab < items ? g0 + kSrpGrab : items;
         for (long long item = g0; item < g1; ++item) {
-            const bool in_list = item < items_long;
-            const long long it = in_list ? item : item - items_long;
-            const long long slot = pieces == 1 ? it : it / pieces;      // (a 64-bit division is a long call)
-            const long long row = in_list ? (long long)__ldg(long_rows + slot) : slot;
-            const int col0 = col_first + (int)(it - slot * pieces) * 4 * V * T;
-            if (!in_list && row_mask && !row_mask[row]) continue;
+            const long long row = pieces == 1 ? item : item / pieces;   // (a 64-bit division is a long call)
+            const int col0 = col_first + (int)(item - row * pieces) * 4 * V * T;
+            if (row_mask && !row_mask[row]) continue;
             const long long s = __ldg(indptr + row), e = __ldg(indptr + row + 1);
-            if (!in_list && n_long > 0 && e - s > kSrpLongRow) continue;   // projected from the list
             constexpr bool Q16 = sizeof(RT) == 2;
             float acc[4 * V], mag[4 * V], tot[4 * V];
 #pragma unroll
@@ -534,22 +534,6 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
     if (bad) blsh_dev_error(scratch, BLSH_ERANGE, 0, bad);
     if (rechecked) atomicAdd(&scratch->counters[2], rechecked);
     if (zeros) atomicAdd(&scratch->counters[3], zeros);
-}
-
-// The rows longer than kSrpLongRow nonzeros (of those row_mask selects):
-// srp_sparse4_kernel projects them before all others, so that no long row
-// starts last.  Rows past the list's capacity leave the list unused.
-__global__ void __launch_bounds__(256) srp_long_rows_kernel(const int64_t *__restrict__ indptr, long long N,
-                                                            const uint8_t *__restrict__ row_mask,
-                                                            uint32_t *__restrict__ long_rows,
-                                                            blsh_dev_scratch *scratch) {
-    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
-         row += (long long)gridDim.x * blockDim.x) {
-        if (__ldg(indptr + row + 1) - __ldg(indptr + row) > kSrpLongRow && (!row_mask || row_mask[row])) {
-            const unsigned long long slot = atomicAdd(&scratch->long_count, 1ull);
-            if (slot < BLSH_LONG_ROWS_CAP) long_rows[slot] = (uint32_t)row;
-        }
-    }
 }
 
 // The queued signs: one warp per (row, bit).  The lanes form the row's exact
@@ -774,24 +758,20 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
     // many small CTAs (rows have very different lengths): 32 per SM measured best
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N * pieces < cap ? N * pieces : cap);
+    // items from a counter, kSrpGrab per grab, where each CTA has many of
+    // them (at least 64); otherwise a fixed share per CTA
+    const int grab = N * pieces >= 64ll * grid ? kSrpGrab : 0;
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
-    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->hash_work, 0, 2 * sizeof(unsigned long long), s));  // + long_count
+    BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->hash_work, 0, sizeof(unsigned long long), s));
     uint2 *q = ctx->recheck_queue;
     blsh_dev_scratch *scr = ctx->scratch;
-    {
-        const long long blocks = (N + 255) / 256, lcap = (long long)ctx->sm_count * 4;
-        blsh_time_start(ctx, s);
-        srp_long_rows_kernel<<<(unsigned)(blocks < lcap ? blocks : lcap), 256, 0, s>>>(indptr, N, row_mask,
-                                                                                      ctx->long_rows, scr);
-        BLSH_LAUNCHED(ctx, "srp_long_rows_kernel");
-    }
     const char *name = sizeof(RT) == 2 ? "srp_sparse4_kernel (two-byte codes)" : "srp_sparse4_kernel";
     blsh_time_start(ctx, s);
     switch (V) {
-    case 1: srp_sparse4_kernel<1, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
-    case 2: srp_sparse4_kernel<2, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
-    case 3: srp_sparse4_kernel<3, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
-    default: srp_sparse4_kernel<4, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, ctx->long_rows); break;
+    case 1: srp_sparse4_kernel<1, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, grab); break;
+    case 2: srp_sparse4_kernel<2, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, grab); break;
+    case 3: srp_sparse4_kernel<3, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, grab); break;
+    default: srp_sparse4_kernel<4, RT><<<grid, T4, 0, s>>>(indptr, indices, values, N, R, dim, bits, col0, pieces, row_mask, sig, scr, q, grab); break;
     }
     BLSH_LAUNCHED(ctx, name);
     blsh_time_start(ctx, s);

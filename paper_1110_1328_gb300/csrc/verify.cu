@@ -420,40 +420,46 @@ __global__ void __launch_bounds__(512) verify_kernel(const VerifyArgs A) {
             // runs them 32 at a time, each from its first step (which repeats
             // the first pass's arithmetic and leaves the pair open) to its stop.
             uint16_t *w_list = reinterpret_cast<uint16_t *>(smem + defer_offset(A.levels)) + (threadIdx.x >> 5) * 512;
-            const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-            const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
             const bool vec = ((uintptr_t)A.status & 15) == 0;
-            for (long long t0 = wid * 512; t0 < P; t0 += nw * 512) {
-                const long long qs = t0 + 16ll * lane;
-                uint32_t open = 0;
-                if (vec && qs + 16 <= P) {
-                    open = blsh_eq16(*reinterpret_cast<const uint4 *>(A.status + qs), kOpenStatus);
-                } else {
-                    for (int i = 0; i < 16; ++i)
-                        if (qs + i < P && A.status[qs + i] == kOpenStatus) open |= 1u << i;
-                }
-                const int c = __popc(open);
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int total = __shfl_sync(kFull, incl, 31);
-                if (total == 0) continue;
-                __syncwarp();                                  // the previous tile's list has been read
-                int slot = incl - c;
-                for (uint32_t bits = open; bits; bits &= bits - 1) w_list[slot++] = (uint16_t)(16 * lane + __ffs(bits) - 1);
-                __syncwarp();
-                for (int b0 = 0; b0 < total; b0 += 32) {
-                    if (b0 + lane < total) {
-                        const long long qq = t0 + w_list[b0 + lane];
-                        const uint2 pr = __ldg(A.pairs + qq);
-                        start_pair(qq, pr.x, pr.y);
-                        al = false;                            // Algorithm 2 was decided in the first pass
+            // tiles from a counter (open pairs cluster where near-duplicate
+            // groups put many similar pairs together)
+            for (;;) {
+                unsigned long long tg = 0;
+                if (lane == 0) tg = atomicAdd(&A.scratch->work, 1ull);
+                const long long g0 = (long long)__shfl_sync(kFull, tg, 0) * 2048;   // four tiles per grab
+                if (g0 >= P) break;
+                for (long long t0 = g0; t0 < g0 + 2048 && t0 < P; t0 += 512) {
+                    const long long qs = t0 + 16ll * lane;
+                    uint32_t open = 0;
+                    if (vec && qs + 16 <= P) {
+                        open = blsh_eq16(*reinterpret_cast<const uint4 *>(A.status + qs), kOpenStatus);
+                    } else {
+                        for (int i = 0; i < 16; ++i)
+                            if (qs + i < P && A.status[qs + i] == kOpenStatus) open |= 1u << i;
                     }
-                    if (__any_sync(kFull, active)) step(std::true_type{});
-                    while (__any_sync(kFull, active)) step(std::false_type{});
+                    const int c = __popc(open);
+                    int incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int total = __shfl_sync(kFull, incl, 31);
+                    if (total == 0) continue;
+                    __syncwarp();                                  // the previous tile's list has been read
+                    int slot = incl - c;
+                    for (uint32_t bits = open; bits; bits &= bits - 1) w_list[slot++] = (uint16_t)(16 * lane + __ffs(bits) - 1);
+                    __syncwarp();
+                    for (int b0 = 0; b0 < total; b0 += 32) {
+                        if (b0 + lane < total) {
+                            const long long qq = t0 + w_list[b0 + lane];
+                            const uint2 pr = __ldg(A.pairs + qq);
+                            start_pair(qq, pr.x, pr.y);
+                            al = false;                            // Algorithm 2 was decided in the first pass
+                        }
+                        if (__any_sync(kFull, active)) step(std::true_type{});
+                        while (__any_sync(kFull, active)) step(std::false_type{});
+                    }
                 }
             }
         } else if constexpr (FAST) {
@@ -694,6 +700,7 @@ int launch_kernel(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, cud
         if (grid > cap) grid = cap;
     }
     if (grid == 0) return BLSH_OK;
+    if (OPEN) BLSH_CUDA(ctx, cudaMemsetAsync(&A.scratch->work, 0, sizeof(unsigned long long), s));   // tile counter
     blsh_time_start(ctx, s);
     kern<<<(unsigned)grid, plan.block, smem, s>>>(A);
     BLSH_LAUNCHED(ctx, "verify_kernel");
