@@ -758,9 +758,11 @@ int srp_sparse_cols(blsh_ctx *ctx, const int64_t *indptr, const uint32_t *indice
     // many small CTAs (rows have very different lengths): 32 per SM measured best
     const long long cap = (long long)ctx->sm_count * 32;
     const unsigned grid = (unsigned)(N * pieces < cap ? N * pieces : cap);
-    // items from a counter, kSrpGrab per grab, where each CTA has many of
-    // them (at least 64); otherwise a fixed share per CTA
-    const int grab = N * pieces >= 64ll * grid ? kSrpGrab : 0;
+    // items from a counter where each CTA has many of them (at least 256;
+    // otherwise a fixed share per CTA): kSrpGrab per grab, eight times as
+    // many when a row mask selects the rows (most items of a grab are then
+    // skipped at once)
+    const int grab = N * pieces >= 256ll * grid ? (row_mask ? 8 * kSrpGrab : kSrpGrab) : 0;
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->recheck_count, 0, sizeof(unsigned long long), s));
     BLSH_CUDA(ctx, cudaMemsetAsync(&ctx->scratch->hash_work, 0, sizeof(unsigned long long), s));
     uint2 *q = ctx->recheck_queue;

@@ -14,6 +14,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortPerThread = 16;
 constexpr int kSortTile = kSortThreads * kSortPerThread;   // 4096 items per CTA
 constexpr int kWarps = kSortThreads / 32;
+static_assert(kSortThreads == 256, "digit_scatter_kernel gives each of the 256 digits one thread");
 
 // ---- stable LSD radix sort, one 8-bit digit per pass ----------------------
 
@@ -31,30 +32,41 @@ static __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const u
     hist[(size_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
 
-// Scatter with stable ranks: warp w handles the contiguous items
-// [w*512, (w+1)*512) of the tile, 32 at a time; lanes holding the same digit
-// are ranked with __match_any_sync, running counts per (warp, digit) live in
-// shared memory, and warps are then offset by the counts of lower warps.
+// Scatter with stable ranks, through shared memory.  Warp w ranks the
+// contiguous items [w*512, (w+1)*512) of the tile, 32 at a time: lanes
+// holding the same digit are ranked with __match_any_sync and running counts
+// per (warp, digit) live in shared memory; only the digits and ranks stay in
+// registers.  The warps' counts are then offset by those of lower warps, the
+// tile's digit totals scanned, and every item placed in shared memory in
+// digit order (its tile items re-read, from L2); finally consecutive threads
+// write consecutive positions, so each digit's run of the tile goes out in
+// coalesced stores.  Equal digits keep the tile's order (warp, then round,
+// then lane), so the sort is stable.
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(unsigned long long) + sizeof(uint32_t)) +
+                                (size_t)kWarps * 256 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
 static __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(const unsigned long long *keys_in,
                                                                      const uint32_t *vals_in, long long n,
                                                                      int shift, const uint32_t *offsets, int tiles,
                                                                      unsigned long long *keys_out,
                                                                      uint32_t *vals_out) {
-    __shared__ uint32_t cnt[kWarps][256];
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(sm);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + kSortTile);
+    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(s_val + kSortTile);
+    uint32_t *s_start = reinterpret_cast<uint32_t *>(cnt + kWarps);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
     __syncwarp();
-    const long long base = (long long)blockIdx.x * kSortTile + (long long)w * (kSortTile / kWarps);
-    unsigned long long k[kSortPerThread];
-    uint32_t v[kSortPerThread], rank[kSortPerThread];
+    const long long tile0 = (long long)blockIdx.x * kSortTile;
+    const long long base = tile0 + (long long)w * (kSortTile / kWarps);
+    uint32_t dig[kSortPerThread], rank[kSortPerThread];
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kSortPerThread; ++r) {
         const long long p = base + r * 32 + lane;
         const bool ok = p < n;
-        k[r] = ok ? keys_in[p] : 0ull;
-        v[r] = ok ? vals_in[p] : 0u;
-        const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & 255u) : 256u;
+        const uint32_t d = ok ? (uint32_t)((keys_in[p] >> shift) & 255u) : 256u;
+        dig[r] = d;
         const unsigned peers = __match_any_sync(kFull, d);
         const uint32_t before = ok ? cnt[w][d] : 0u;
         rank[r] = before + __popc(peers & lt);
@@ -63,28 +75,39 @@ static __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(cons
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, per digit
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
-        uint32_t s = 0;
+    // per digit: exclusive prefix over warps, then the tile's digit totals scanned
+    uint32_t total = 0;
+    {
+        const int d = threadIdx.x;   // kSortThreads == 256: one digit per thread
         for (int ww = 0; ww < kWarps; ++ww) {
             const uint32_t c = cnt[ww][d];
-            cnt[ww][d] = s;
-            s += c;
+            cnt[ww][d] = total;
+            total += c;
         }
     }
+    const uint32_t start = blsh_scan::block_exclusive<uint32_t>(total, nullptr);
+    s_start[threadIdx.x] = start;
     __syncthreads();
+    // the tile in digit order in shared memory
 #pragma unroll
     for (int r = 0; r < kSortPerThread; ++r) {
         const long long p = base + r * 32 + lane;
         if (p < n) {
-            const uint32_t d = (uint32_t)((k[r] >> shift) & 255u);
-            const long long dst = (long long)offsets[(size_t)d * tiles + blockIdx.x] + cnt[w][d] + rank[r];
-            keys_out[dst] = k[r];
-            vals_out[dst] = v[r];
+            const uint32_t pos = s_start[dig[r]] + cnt[w][dig[r]] + rank[r];
+            s_key[pos] = keys_in[p];
+            s_val[pos] = vals_in[p];
         }
     }
+    __syncthreads();
+    const int tn = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+    for (int i = threadIdx.x; i < tn; i += kSortThreads) {
+        const unsigned long long k = s_key[i];
+        const uint32_t d = (uint32_t)((k >> shift) & 255u);
+        const long long dst = (long long)offsets[(size_t)d * tiles + blockIdx.x] + (i - (int)s_start[d]);
+        keys_out[dst] = k;
+        vals_out[dst] = s_val[i];
+    }
 }
-
 
 // Entries of hist (256 per tile) and of the scan's partial sums that sort()
 // needs for n items.
@@ -101,6 +124,8 @@ inline int sort(blsh_ctx *ctx, unsigned long long *keys[2], uint32_t *vals[2], l
                 int first_bit = 0) {
     const int passes = (key_bits + 7) / 8;
     const long long tiles = (n + kSortTile - 1) / kSortTile;
+    BLSH_CUDA(ctx, cudaFuncSetAttribute(digit_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kScatterSmem));
     int cur = 0;
     for (int pass = 0; pass < passes && n > 0; ++pass) {
         const int shift = first_bit + 8 * pass;
@@ -112,8 +137,8 @@ inline int sort(blsh_ctx *ctx, unsigned long long *keys[2], uint32_t *vals[2], l
         ctx->launches.fetch_add(3, std::memory_order_relaxed);
         blsh_time_stop(ctx, "exclusive scan (3 launches)");
         blsh_time_start(ctx, s);
-        digit_scatter_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], n, shift, hist,
-                                                                      (int)tiles, keys[cur ^ 1], vals[cur ^ 1]);
+        digit_scatter_kernel<<<(unsigned)tiles, kSortThreads, kScatterSmem, s>>>(
+            keys[cur], vals[cur], n, shift, hist, (int)tiles, keys[cur ^ 1], vals[cur ^ 1]);
         BLSH_LAUNCHED(ctx, "digit_scatter_kernel");
         cur ^= 1;
     }
