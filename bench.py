@@ -418,6 +418,44 @@ def load_tensor_peak():
         return 1900.0, "fallback"
 
 
+def bind_numa(torch, dev) -> dict:
+    """Restrict this process to the host CPUs of the GPU's own NUMA node, so
+    that pinned host buffers allocated afterwards (first touch) sit in the
+    memory next to the GPU's host link rather than behind the inter-socket
+    link.  Reads the node from sysfs by the GPU's PCI address; leaves the
+    affinity alone where sysfs gives no node.  Returns what it found."""
+    info = {"node": None, "cpus": None, "bound": False}
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        addr = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        base = "/sys/bus/pci/devices/" + addr
+        info["pci"] = addr
+        with open(base + "/numa_node") as f:
+            node = int(f.read().strip())
+        info["node"] = node
+        if node < 0:
+            return info
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        allowed = os.sched_getaffinity(0)
+        use = cpus & allowed
+        info["cpus"] = len(use)
+        info["allowed"] = len(allowed)
+        if use and use != allowed:
+            os.sched_setaffinity(0, use)
+            info["bound"] = True
+    except (OSError, ValueError, AttributeError) as e:
+        info["error"] = type(e).__name__
+    return info
+
+
 def measure_plain(B, torch, pipe, flush, stream, stage_ms, step_ms, reps: int = 2):
     """The plain GPU form of the same step: eager launches (no CUDA graph),
     every hash of every object computed up front (no lazy hashing), the
@@ -1242,7 +1280,9 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     buffers while step i runs (double buffering, one CUDA graph per buffer
     set), and step i's outputs are read while step i+1 runs.  Returns (ms
     per step, H2D bytes per step, D2H bytes per step, the steps' own device
-    time per step, the device's wait for a step's inputs per step)."""
+    time per step, the device's wait for a step's inputs per step, the
+    input copy's own rate in GB/s when timed alone, and per step the input
+    copy's duration, its end relative to its step's start and the wait)."""
     pin = lambda x: x.cpu().pin_memory()
     h_in = {k: pin(getattr(pipe, k)) for k in ("indptr", "indices", "values")}
     sets = [pipe.buffer_set(), pipe.new_buffer_set()]
@@ -1276,15 +1316,21 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     ev_out = [None, None]
     d2h = [0]
 
+    copy_ev = []      # (start, end) of every input copy on the copy-in stream
+
     def issue_inputs(b):
         # into set b once the step that last used it, and the copy of its
         # outputs, are done
         with torch.cuda.stream(copy_in):
             if ev_out[b] is not None:
                 copy_in.wait_event(ev_out[b])
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(copy_in)
             for k, v in h_in.items():
                 sets[b][k].copy_(v, non_blocking=True)
+            c1.record(copy_in)
             ev_in[b].record(copy_in)
+            copy_ev.append((c0, c1))
 
     def finish(b):
         # the step that ran on set b: its counts on the host, then its output sets
@@ -1302,6 +1348,17 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
             ev_out[b].record(copy_out)
         d2h[0] = 16 * nb + 8 * (o1 + o2)
 
+    # the host link alone: the step's input copy timed by itself (twice)
+    link = []
+    for _ in range(2):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(copy_in):
+            a.record(copy_in)
+            for k, v in h_in.items():
+                sets[0][k].copy_(v, non_blocking=True)
+            z.record(copy_in)
+        z.synchronize()
+        link.append(h2d / (a.elapsed_time(z) * 1e6))
     ev_w = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -1342,7 +1399,12 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     pipe.use_buffer_set(sets[0])
     device_ms = float(np.mean([s_.elapsed_time(e_) for s_, e_ in zip(ev_s, ev_e)]))
     wait_ms = float(np.mean([w_.elapsed_time(s_) for w_, s_ in zip(ev_w, ev_s)]))
-    return ms, h2d, d2h[0], device_ms, wait_ms
+    # each input copy's duration, and how long before its step's start it ended
+    copy_ms = [a.elapsed_time(z) for a, z in copy_ev]
+    lead_ms = [z.elapsed_time(s_) for (a, z), s_ in zip(copy_ev, ev_s)]
+    diag = {"input_copy_ms": [round(v, 3) for v in copy_ms], "copy_end_to_step_start_ms": [round(v, 3) for v in lead_ms],
+            "input_wait_ms": [round(w_.elapsed_time(s_), 3) for w_, s_ in zip(ev_w, ev_s)]}
+    return ms, h2d, d2h[0], device_ms, wait_ms, max(link), diag
 
 
 def large_kernel_work(pipe):
@@ -1445,6 +1507,7 @@ def run_large(args, w):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    numa = bind_numa(torch, dev)
     B.lib()
     if world > 1:      # replicas: each rank its own batch of objects
         w = dict(w, seed=w["seed"] + 1000 * rank)
@@ -1545,7 +1608,7 @@ def run_large(args, w):
         torch.cuda.nvtx.range_pop()
 
     # ---- end to end through the public API, host buffers ----
-    e2e_step, h2d, d2h, e2e_dev, e2e_wait = large_e2e(B, torch, pipe, stream, args.steps, graph is not None, kept)
+    e2e_step, h2d, d2h, e2e_dev, e2e_wait, e2e_link, e2e_diag = large_e2e(B, torch, pipe, stream, args.steps, graph is not None, kept)
     e2e_ms = [e2e_step]
     e2e_step = float(np.mean(e2e_ms))
     ms, P_total, e2e_max = combine_ranks(dist, my_ms, pipe.P, e2e_step, dev)
@@ -1600,6 +1663,7 @@ def run_large(args, w):
         "e2e": {"value": round(e2e_val, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4),
                 "device_ms_per_step": round(e2e_dev, 4), "input_wait_ms_per_step": round(e2e_wait, 4),
+                "h2d_gbs_alone": round(e2e_link, 1), "host_numa": numa, "per_step": e2e_diag,
                 "form": "inputs copied from pinned host memory and output sets copied back every step; step i+1's "
                         "inputs copied into a second buffer set while step i runs, step i's outputs read while "
                         "step i+1 runs"},

@@ -299,7 +299,12 @@ BLSH_API int blsh_srp_dense(blsh_ctx *ctx, const float *X, int64_t N, int32_t d,
 
 /* ---- candidate generation (Section 2, "Candidate generation via LSH") ---- */
 
-/* Workspace bytes blsh_lsh_candidates needs for these sizes. */
+/* Workspace bytes blsh_lsh_candidates takes for these sizes.  The last
+ * 64 * N * bands of them are a keep record: the emission's count pass notes
+ * there which pairs it keeps, so that its write pass writes them without
+ * testing them again.  A workspace smaller by up to that much is accepted;
+ * the positions the record then does not cover are tested again (same
+ * output, more time), and bytes beyond the size returned extend the record. */
 BLSH_API int blsh_lsh_candidates_workspace(int64_t N, int32_t kind, int32_t rows, int32_t bands, size_t *bytes);
 
 /* Band b of object i is its hashes b*rows .. b*rows+rows-1; objects that
@@ -309,8 +314,9 @@ BLSH_API int blsh_lsh_candidates_workspace(int64_t N, int32_t kind, int32_t rows
  * and the number of distinct pairs into *n_pairs (device int64).  If that
  * number exceeds cap only the first cap pairs are written and blsh_status
  * reports BLSH_ETRUNC.  Band keys are compared in full (no hash collisions
- * can merge buckets).  Cosine: rows <= 32.  workspace: device, at least
- * blsh_lsh_candidates_workspace() bytes, 256-byte aligned. */
+ * can merge buckets).  Cosine: rows <= 32.  workspace: device, 256-byte
+ * aligned, blsh_lsh_candidates_workspace() bytes less at most the keep
+ * record's 64 * N * bands (BLSH_ETRUNC below that). */
 BLSH_API int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N, int32_t sig_words, int32_t kind,
                         int32_t rows, int32_t bands, uint32_t *pairs, int64_t cap, int64_t *n_pairs,
                         void *workspace, size_t workspace_bytes, void *stream);

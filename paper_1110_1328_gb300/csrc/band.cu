@@ -418,7 +418,7 @@ __device__ __forceinline__ void emit_poison(uint32_t *p, int full, int rest, int
 }
 
 template <int NW4, bool WRITE, bool PZ>
-__device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigned j, bool live, int i,
+__device__ __forceinline__ bool emit_step(const uint4 *yrow, uint32_t y, unsigned j, bool live, int i,
                                           long long p0, long long end, uint32_t x, const uint4 *kx,
                                           const EmitCmp &cmp, const uint32_t *pz, int eqw, bool jac, uint32_t one,
                                           uint32_t high, unsigned long long out, unsigned long long &cnt,
@@ -433,13 +433,16 @@ __device__ __forceinline__ void emit_step(const uint4 *yrow, uint32_t y, unsigne
         if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
     }
     cnt += ok;
+    return ok;
 }
 
 // The walk of one warp over partners [jmin, jmax) (tile-relative), NW4
 // 16-byte words of key rows compared per pair (cmp: the lane's plan for
 // its band).  Partners inside the window come from the stage; partners past
 // it (long buckets) are fetched 32 at a time into the warp's own buffer, one
-// row per lane, so that their loads overlap.
+// row per lane, so that their loads overlap.  With a keep record (rec, count
+// pass) each lane also stores which partners it keeps: bit t of word
+// rec[32 w + lane] is partner jmin + 32 w + t.
 template <int NW4, bool WRITE, bool PZ>
 __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
                                           uint4 *w_rows, uint32_t *w_ids, const uint32_t *vals, long long p0,
@@ -447,9 +450,27 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
                                           long long end, uint32_t x, const uint4 *kx, const EmitCmp &cmp,
                                           const uint32_t *pz, int eqw, bool jac, uint32_t one, uint32_t high,
                                           unsigned long long out, unsigned long long &cnt, uint32_t *pairs,
-                                          long long cap) {
+                                          long long cap, uint32_t *rec) {
     const unsigned wend = jmax < (unsigned)win ? jmax : (unsigned)win;
     const int lane = threadIdx.x & 31;
+    // the lane's record word being filled (index ridx) and its bits
+    unsigned ridx = 0;
+    uint32_t racc = 0;
+    // partners g0 .. g0 + n - 1 (relative to jmin, n <= 32) with the kept ones in `keep`
+    auto rec_put = [&](unsigned g0, unsigned n, uint32_t keep) {
+        const unsigned w = g0 >> 5, sh = g0 & 31;
+        if (w != ridx) {
+            rec[(size_t)ridx * 32 + lane] = racc;
+            racc = 0;
+            ridx = w;
+        }
+        racc |= keep << sh;
+        if (sh + n > 32) {
+            rec[(size_t)ridx * 32 + lane] = racc;
+            ++ridx;
+            racc = keep >> (32 - sh);
+        }
+    };
     if constexpr (!PZ && NW4 >= 2) {
         // Long key rows: partners in batches of 32.  Each (lane, partner) is
         // first tested on the first 16-byte chunk only (bands 0..7 of 16-bit
@@ -480,6 +501,7 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
                 const int u = __ffs(b) - 1;
                 if (emit_test<NW4, 1>(kx, rows + (size_t)u * rstride, cmp, jac, one, high)) keep |= 1u << u;
             }
+            if (!WRITE && rec) rec_put(j0 - jmin, n, keep);
             if (WRITE) {
                 for (uint32_t b = keep; b; b &= b - 1) {
                     const long long o = (long long)(out + cnt);
@@ -504,10 +526,22 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
             __syncwarp();
             batch(j0, jmax - j0 < 32u ? jmax - j0 : 32u, w_rows, NW4, w_ids);
         }
+        if (!WRITE && rec && jmax > jmin) rec[(size_t)ridx * 32 + lane] = racc;   // the last word
     } else {
-        for (unsigned j = jmin; j < wend; ++j)
-            emit_step<NW4, WRITE, PZ>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx, cmp, pz, eqw,
-                                      jac, one, high, out, cnt, pairs, cap);
+        // one kept bit per step into the lane's record word
+        auto rec_bit = [&](unsigned j, bool ok) {
+            const unsigned g = j - jmin;
+            racc |= (uint32_t)ok << (g & 31);
+            if ((g & 31) == 31) {
+                rec[(size_t)(g >> 5) * 32 + lane] = racc;
+                racc = 0;
+            }
+        };
+        for (unsigned j = jmin; j < wend; ++j) {
+            const bool ok = emit_step<NW4, WRITE, PZ>(s_ck + (size_t)j * stride, s_val[j], j, live, i, p0, end, x, kx,
+                                                      cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap);
+            if (!WRITE && rec) rec_bit(j, ok);
+        }
         for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
             __syncwarp();
             if (j0 + lane < jmax) {
@@ -519,9 +553,32 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
             }
             __syncwarp();
             const unsigned n = jmax - j0 < 32u ? jmax - j0 : 32u;
-            for (unsigned u = 0; u < n; ++u)
-                emit_step<NW4, WRITE, PZ>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx, cmp, pz, eqw,
-                                          jac, one, high, out, cnt, pairs, cap);
+            for (unsigned u = 0; u < n; ++u) {
+                const bool ok = emit_step<NW4, WRITE, PZ>(w_rows + u * NW4, w_ids[u], j0 + u, live, i, p0, end, x, kx,
+                                                          cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap);
+                if (!WRITE && rec) rec_bit(j0 + u, ok);
+            }
+        }
+        // the last, partly filled word (a full one was stored by rec_bit)
+        if (!WRITE && rec && jmax > jmin && ((jmax - jmin) & 31)) rec[(size_t)((jmax - jmin) >> 5) * 32 + lane] = racc;
+    }
+}
+
+// The write pass of a walk the count pass recorded: lane l's partners are the
+// set bits of rec[32 w + l] (partner jmin + 32 w + t for bit t), written in
+// partner order from its offset `out`; no key rows are read.
+__device__ __forceinline__ void emit_replay_walk(const uint32_t *rec, unsigned words, unsigned jmin,
+                                                 const uint32_t *s_val, const uint32_t *vals, long long p0, int win,
+                                                 uint32_t x, unsigned long long out, uint32_t *pairs, long long cap) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long cnt = 0;
+    for (unsigned w = 0; w < words; ++w) {
+        for (uint32_t bits = rec[(size_t)w * 32 + lane]; bits; bits &= bits - 1) {
+            const unsigned j = jmin + 32 * w + (unsigned)(__ffs(bits) - 1);
+            const uint32_t y = (int)j < win ? s_val[j] : __ldg(vals + p0 + j);
+            const long long o = (long long)(out + cnt);
+            if (o < cap) reinterpret_cast<uint2 *>(pairs)[o] = make_uint2(x, y);
+            ++cnt;
         }
     }
 }
@@ -534,13 +591,15 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
 // output offset plus the kept pairs of that owner before it: those of
 // earlier steps (acc[owner], kept in shared memory) and those of lower lanes
 // in this step (lanes of one owner are contiguous).  All partners are
-// staged (the caller checks).
+// staged (the caller checks).  With a keep record (rec), the count pass
+// stores each step's ballot of kept pairs as one word and the write pass
+// takes its pairs from those words instead of testing them again.
 template <int NW4, bool WRITE>
 __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
                                           const unsigned long long *s_key, uint32_t *acc, int cws, int warp,
                                           bool live, int i, long long end, long long p0, unsigned long long out,
                                           uint32_t one, uint32_t high, int per_word, uint32_t *pairs,
-                                          long long cap) {
+                                          long long cap, uint32_t *rec) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned mine = live ? (unsigned)(end - p0 - i - 1) : 0u;
@@ -570,17 +629,22 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
         bool ok = false;
         uint32_t x = 0, y = 0;
         if (valid) {
-            const unsigned long long key = s_key[io];
-            const int b = A.exact_classes ? (A.band_bits == 0 ? 0 : (int)(key >> (32 - A.band_bits)))
-                                          : (int)(key >> A.rows);
-            const int full = b / per_word, rest = b % per_word;
-            const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
-            const uint4 *xr = s_ck + (size_t)io * cws, *yr = s_ck + (size_t)j * cws;
-            ok = emit_test<NW4>(xr, yr, emit_cmp(full, pmask, high), A.exact_classes != 0, one, high);
+            if (WRITE && rec) {
+                ok = (rec[t0 >> 5] >> lane) & 1u;
+            } else {
+                const unsigned long long key = s_key[io];
+                const int b = A.exact_classes ? (A.band_bits == 0 ? 0 : (int)(key >> (32 - A.band_bits)))
+                                              : (int)(key >> A.rows);
+                const int full = b / per_word, rest = b % per_word;
+                const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
+                const uint4 *xr = s_ck + (size_t)io * cws, *yr = s_ck + (size_t)j * cws;
+                ok = emit_test<NW4>(xr, yr, emit_cmp(full, pmask, high), A.exact_classes != 0, one, high);
+            }
             x = s_val[io];
             y = s_val[j];
         }
         const unsigned okm = __ballot_sync(kFull, ok);
+        if (!WRITE && rec && lane == 0) rec[t0 >> 5] = okm;
         const unsigned seg = __match_any_sync(kFull, valid ? o : 32 + lane);
         if (WRITE && ok) {
             const long long slot = (long long)(out_o + acc[o] + __popc(okm & seg & lt));
@@ -606,12 +670,23 @@ __device__ __forceinline__ void emit_flat(const BandArgs &A, const uint4 *s_ck, 
 // the bands before its b.  Where they are short it numbers the pairs and
 // gives each lane one (emit_flat).  Pairs of position i are counted, or
 // written, in partner order, the order emit_kernel uses.
+//
+// Keep record: the count pass stores which pairs it keeps, one bit per
+// tested pair, so that the write pass only writes them.  A chunk takes its
+// words (emit_flat: one per step; the walk: 32 per 32 partners) from a
+// counter in the record area rec[0, rec_cap); rec_off[chunk] is its first
+// word times 2 plus 1 if it went flat, or ~0 where the area was full (the
+// write pass then tests that chunk's pairs again).  With rec == NULL
+// nothing is recorded.
 template <bool WRITE, int KW4>
 __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_kernel(BandArgs A, const unsigned long long *keys,
                                                              const uint32_t *vals, long long n,
                                                              unsigned long long *counts, uint32_t *pairs,
                                                              long long cap, int win_cap,
-                                                             unsigned long long *next_chunk) {
+                                                             unsigned long long *next_chunk, uint32_t *rec,
+                                                             unsigned long long *rec_off,
+                                                             unsigned long long rec_cap,
+                                                             unsigned long long *rec_next) {
     extern __shared__ uint4 s_all[];
     const int cw4 = A.ck_words >> 2, cws = stage_stride(A.ck_words);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -634,6 +709,9 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
         if ((long long)c >= chunks) break;
         const long long p0 = (long long)c << 5;
         int win = (int)(n - p0 < win_cap ? n - p0 : win_cap);
+        // write pass: a recorded chunk needs no key rows and no tests
+        const unsigned long long ro = WRITE && rec ? rec_off[c] : ~0ull;
+        const bool replay = ro != ~0ull;
         __syncwarp();                                     // the previous chunk is done with the stage
         // keys first; ids and key rows only as far as the chunk's buckets
         // reach inside the window (all of it if one runs past it)
@@ -655,8 +733,10 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
         for (int k = lane; k < win; k += 32) {
             const uint32_t v = vals[p0 + k];
             s_val[k] = v;
-            const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
-            for (int q = 0; q < cw4; ++q) s_ck[(size_t)k * cws + q] = __ldg(src + q);
+            if (!replay) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(A.ck + (size_t)v * A.ck_words);
+                for (int q = 0; q < cw4; ++q) s_ck[(size_t)k * cws + q] = __ldg(src + q);
+            }
         }
         __syncwarp();
         const int tile = win < 32 ? win : 32;
@@ -680,9 +760,11 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
             }
             end = p0 + lo;
             if (lo == win && end < n) end = run_end_global(keys, n, end, key);
+            if (!replay) {
 #pragma unroll
-            for (int c = 0; c < KW4; ++c)
-                if (c < cw4) kx[c] = s_ck[(size_t)i * cws + c];
+                for (int c = 0; c < KW4; ++c)
+                    if (c < cw4) kx[c] = s_ck[(size_t)i * cws + c];
+            }
         }
         const int full = b / per_word, rest = b % per_word;   // bands 0..b-1: `full` words and `rest` lanes
         const uint32_t pmask = rest ? ((1u << (8 * A.ck_lane * rest)) - 1u) & high : 0u;
@@ -696,9 +778,30 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
         // small buckets: number the pairs and give each lane one (the walk
         // below would spend a step per partner position on mostly idle lanes)
         const unsigned pairs_w = __reduce_add_sync(kFull, live ? (unsigned)(end - p0 - i - 1) : 0u);
-        if (jmax <= (unsigned)win && 5ull * ((pairs_w + 31) / 32) < 2ull * (jmax - jmin)) {
+        const bool flat = replay ? (ro & 1ull) != 0
+                                 : jmax <= (unsigned)win && 5ull * ((pairs_w + 31) / 32) < 2ull * (jmax - jmin);
+        uint32_t *crec = nullptr;                         // this chunk's record words
+        if (replay) {
+            crec = rec + (ro >> 1);
+        } else if (!WRITE && rec) {
+            const unsigned long long words =
+                flat ? (pairs_w + 31) / 32 : (jmax > jmin ? 32ull * ((jmax - jmin + 31) / 32) : 0ull);
+            unsigned long long off = 0;
+            if (lane == 0) {
+                off = atomicAdd(rec_next, words);
+                rec_off[c] = off + words <= rec_cap ? off << 1 | (flat ? 1ull : 0ull) : ~0ull;
+            }
+            off = __shfl_sync(kFull, off, 0);
+            if (off + words <= rec_cap) crec = rec + off;
+        }
+        if (replay && !flat) {
+            emit_replay_walk(crec, jmax > jmin ? (jmax - jmin + 31) / 32 : 0u, jmin, s_val, vals, p0, win, x, out,
+                             pairs, cap);
+            continue;
+        }
+        if (flat) {
 #define BLSH_FLAT(NW) emit_flat<NW, WRITE>(A, s_ck, s_val, s_key, w_ids, cws, 0, live, i, end, p0, out, one, high, \
-                                           per_word, pairs, cap)
+                                           per_word, pairs, cap, crec)
             if constexpr (KW4 <= 4) {
                 switch (nw4) {
                 case 0: BLSH_FLAT(0); break;
@@ -728,7 +831,7 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
         uint32_t pz[kPZ ? 16 : 1];
         if constexpr (kPZ) emit_poison<16>(pz, full, rest, 8 * A.ck_lane, one);
 #define BLSH_WALK(NW) emit_walk<NW, WRITE, kPZ>(A, s_ck, s_val, w_rows, w_ids, vals, p0, win, cws, jmin, jmax, live, \
-                                                i, end, x, kx, cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap)
+                                                i, end, x, kx, cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap, crec)
         if constexpr (KW4 <= 4) {
             switch (nw4) {
             case 0: BLSH_WALK(0); break;
@@ -804,8 +907,12 @@ __global__ void check_cap_kernel(const long long *n_pairs, long long cap, blsh_d
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t keys0, keys1, vals0, vals1, bk, ck, counts, hist, partial, grand, total;
+    size_t keys0, keys1, vals0, vals1, bk, ck, counts, hist, partial, grand, rec_off, rec, total;
 };
+
+// The emission's keep record (emit_warp_kernel): 16 words per position by
+// default; bytes a caller's workspace has beyond rec go to it.
+constexpr size_t kRecBytesPerPos = 64;
 
 // Jaccard class-id rows: one 32-bit id per band, rounded to 16 bytes.
 int jac_row_words(int bands) { return (bands + 3) & ~3; }
@@ -829,7 +936,9 @@ Layout layout(long long N, int kind, int rows, int bands) {
     L.hist = o; o = up256(o + hist_n * 4);
     L.partial = o; o = up256(o + part * 8);
     L.grand = o; o = up256(o + 16);
-    L.total = o;
+    L.rec_off = o; o = up256(o + ((n + 31) / 32) * 8);
+    L.rec = o;
+    L.total = o + (size_t)n * kRecBytesPerPos;
     return L;
 }
 
@@ -866,8 +975,8 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     if (!blsh_aligned(n_pairs, 8) || !blsh_aligned(workspace, 256) || !blsh_aligned(pairs, 8))
         return blsh_fail(ctx, BLSH_EINVAL, "misaligned pointer");
     const Layout L = layout(N, kind, rows, bands);
-    if (!workspace || workspace_bytes < L.total)
-        return blsh_fail(ctx, BLSH_ETRUNC, "workspace needs %zu bytes", L.total);
+    if (!workspace || workspace_bytes < L.rec)
+        return blsh_fail(ctx, BLSH_ETRUNC, "workspace needs %zu bytes", L.rec);
     blsh_device_guard g(ctx->device);
     cudaStream_t s = blsh_stream(stream);
     const long long n = N * bands;
@@ -924,9 +1033,14 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     const size_t smem_w = staged ? 8 * emit_warp_region(A.ck_words, win_w) : 0;
     const unsigned egrid_c = (unsigned)(ctx->sm_count * emit_warp_ctas(A.ck_words, true));
     const unsigned egrid_w = (unsigned)(ctx->sm_count * emit_warp_ctas(A.ck_words, false));
-    // the two chunk counters (count pass, write pass)
+    // the two chunk counters (count pass, write pass) and the record's
     unsigned long long *next_chunk = &ctx->scratch->band_work[0];
-    BLSH_CUDA(ctx, cudaMemsetAsync(next_chunk, 0, 2 * sizeof(unsigned long long), s));
+    BLSH_CUDA(ctx, cudaMemsetAsync(next_chunk, 0, 3 * sizeof(unsigned long long), s));
+    // the keep record: the workspace past L.rec, in 4-byte words
+    const unsigned long long rec_cap = (workspace_bytes - L.rec) / 4;
+    uint32_t *rec = staged && rec_cap > 0 ? (uint32_t *)(ws + L.rec) : nullptr;
+    unsigned long long *rec_off = (unsigned long long *)(ws + L.rec_off);
+    unsigned long long *rec_next = &ctx->scratch->band_work[2];
     if (staged) {
         if (A.ck_words <= 16) {
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 4>,
@@ -935,7 +1049,8 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
             blsh_time_start(ctx, s);
             emit_warp_kernel<false, 4><<<egrid_c, 256, smem_c, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                    win_c, next_chunk);
+                                                                    win_c, next_chunk, rec, rec_off, rec_cap,
+                                                                    rec_next);
         } else {
             BLSH_CUDA(ctx, cudaFuncSetAttribute(emit_warp_kernel<false, 8>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
@@ -943,7 +1058,8 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
             blsh_time_start(ctx, s);
             emit_warp_kernel<false, 8><<<egrid_c, 256, smem_c, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                                    win_c, next_chunk);
+                                                                    win_c, next_chunk, rec, rec_off, rec_cap,
+                                                                    rec_next);
         }
     } else {
         blsh_time_start(ctx, s);
@@ -959,10 +1075,10 @@ extern "C" int blsh_lsh_candidates(blsh_ctx *ctx, const uint32_t *sig, int64_t N
     blsh_time_start(ctx, s);
     if (staged && A.ck_words <= 16)
         emit_warp_kernel<true, 4><<<egrid_w, 256, smem_w, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                               win_w, next_chunk + 1);
+                                                               win_w, next_chunk + 1, rec, rec_off, rec_cap, rec_next);
     else if (staged)
         emit_warp_kernel<true, 8><<<egrid_w, 256, smem_w, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap,
-                                                               win_w, next_chunk + 1);
+                                                               win_w, next_chunk + 1, rec, rec_off, rec_cap, rec_next);
     else
         emit_kernel<true><<<grid, 256, 0, s>>>(A, keys[cur], vals[cur], n, counts, pairs, cap);
     BLSH_LAUNCHED(ctx, staged ? "emit_warp_kernel (write pass)" : "emit_kernel (write pass)");

@@ -29,7 +29,7 @@ struct blsh_dev_scratch {
     unsigned long long work2;          // lite: next survivor tile handed out
     unsigned long long work3;          // lite: survivors queued
     unsigned long long recheck_count;  // SRP: signs queued for an FP64 recheck
-    unsigned long long band_work[2];   // banding: next chunk of positions (count pass, write pass)
+    unsigned long long band_work[3];   // banding: next chunk of positions (count pass, write pass), record words used
     unsigned long long hash_work;      // sparse projection: next (row, piece) item handed out
     unsigned int norm2_valid;          // Lite: the rows' squared norms were formed for this call
     long long cta_counts[BLSH_COMPACT_MAX_CTAS];  // compaction: kept items per CTA

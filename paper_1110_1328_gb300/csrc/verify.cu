@@ -664,6 +664,233 @@ __global__ void __launch_bounds__(256) verify_first_kernel(const VerifyArgs A) {
         atomicAdd(A.stop_hist + threadIdx.x, (unsigned long long)s_h[threadIdx.x]);
 }
 
+// The first pass's tests on packed counts.  With k = 32 the cumulative
+// disagreements after chunk i are D_i = 32(i+1) - m_i <= 128; the four levels
+// sit in two words, level 2w in the low and level 2w+1 in the high half of
+// word w, and each of Algorithm 1's tests is an add in every half whose bit 15
+// gives the answer (no carry leaves a half: every half stays below 2^16):
+//   prune_i  m_i <  mm_i   <=>  D_i >  32(i+1) - mm_i  =: dmax_i   (D_i + 0x7fff - dmax_i >= 0x8000)
+//   conc_i   m_i >= clo_i  <=>  D_i <  32(i+1) - clo_i + 1 =: e_i  (0x7fff + e_i - D_i >= 0x8000)
+// with dmax_i clamped to [-1, 0x7fff] and e_i to [0, 0x7fff]: a level beyond
+// the table's (or, in Algorithm 2, every level's concentration test) gets the
+// constant that never fires.
+struct FirstConsts {
+    unsigned kp[2];      // halves 0x7fff - dmax_i
+    unsigned ec[2];      // halves 0x7fff + e_i
+    unsigned stop[2];    // bit 15 of a half: the level limit or the hash cap is reached there
+    unsigned last[2];    // bit 15: the level limit
+    unsigned llast[2];   // bit 15: Algorithm 2's level limit
+    int lastcode;        // status of a pair reaching the level limit undecided
+};
+
+// One pair's first-pass decisions: st (kOpenStatus when Algorithm 1 goes on
+// past the fourth chunk), the level i it stops at and its agreements m
+// there; Algorithm 2's status ls and level il.
+struct FirstOut {
+    int st, i, m, ls, il;
+};
+
+__device__ __forceinline__ FirstConsts first_consts(const VerifyArgs &A) {
+    auto at = [](int lim) { const int d = lim - 1; return d >= 0 && d < 4 ? 1u << d : 0u; };
+    const unsigned valid = A.levels >= 4 ? 0xfu : (1u << A.levels) - 1u;
+    const unsigned last = at(A.levels) & valid, stop = (at(A.levels) | at(A.cap_levels)) & valid;
+    const unsigned llast = at(A.lite_levels) & valid;
+    FirstConsts c = {};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int w = i >> 1, h = (i & 1) * 16;
+        long long dmax = 0x7fff, e = 0;
+        if (i < A.levels) {
+            dmax = 32ll * (i + 1) - __ldg(A.min_matches + i);
+            dmax = dmax < -1 ? -1 : dmax > 0x7fff ? 0x7fff : dmax;
+            if (!A.lite) {
+                e = 32ll * (i + 1) - __ldg(A.conc_lo + i) + 1;
+                e = e < 0 ? 0 : e > 0x7fff ? 0x7fff : e;
+            }
+        }
+        c.kp[w] |= (unsigned)(0x7fff - dmax) << h;
+        c.ec[w] |= (unsigned)(0x7fff + e) << h;
+        const unsigned bit = 0x8000u << h;
+        if ((stop >> i) & 1u) c.stop[w] |= bit;
+        if ((last >> i) & 1u) c.last[w] |= bit;
+        if ((llast >> i) & 1u) c.llast[w] |= bit;
+    }
+    c.lastcode = A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX;
+    return c;
+}
+
+__device__ __forceinline__ FirstOut first_decide(const FirstConsts &c, uint4 a, uint4 b) {
+    constexpr unsigned M = 0x80008000u;
+    const unsigned d0 = __popc(a.x ^ b.x), d1 = __popc(a.y ^ b.y), d2 = __popc(a.z ^ b.z), d3 = __popc(a.w ^ b.w);
+    const unsigned e1 = d0 + d1, e2 = e1 + d2;
+    const unsigned w0 = d0 | e1 << 16, w1 = e2 | (e2 + d3) << 16;   // D_0 | D_1, D_2 | D_3
+    const unsigned p0 = (w0 + c.kp[0]) & M, p1 = (w1 + c.kp[1]) & M;
+    const unsigned q0 = (c.ec[0] - w0) & M, q1 = (c.ec[1] - w1) & M;
+    const unsigned s0 = p0 | q0 | c.stop[0], s1 = p1 | q1 | c.stop[1];
+    FirstOut o;
+    o.st = kOpenStatus;
+    o.i = 0;
+    o.m = 0;
+    if (s0 | s1) {   // the first level with a decision (or the limit)
+        const bool lo = s0 != 0;
+        const unsigned s = lo ? s0 : s1, w = lo ? w0 : w1, p = lo ? p0 : p1, q = lo ? q0 : q1;
+        const unsigned l = lo ? c.last[0] : c.last[1];
+        const int h = (s & 0x8000u) ? 0 : 16;
+        o.i = (lo ? 0 : 2) + (h >> 4);
+        o.m = 32 * (o.i + 1) - (int)((w >> h) & 0xffffu);
+        o.st = ((p >> h) & 0x8000u)   ? BLSH_PRUNED
+               : ((q >> h) & 0x8000u) ? BLSH_ACCEPT
+               : ((l >> h) & 0x8000u) ? c.lastcode
+                                      : BLSH_NEEDS_HASHES;
+    }
+    // Algorithm 2 (fused): its first prune, else its level limit
+    const unsigned t0 = p0 | c.llast[0], t1 = p1 | c.llast[1];
+    const bool lo2 = t0 != 0;
+    const unsigned t = lo2 ? t0 : t1, pp = lo2 ? p0 : p1;
+    const int h2 = (t & 0x8000u) ? 0 : 16;
+    o.il = (lo2 ? 0 : 2) + (h2 >> 4);
+    o.ls = ((pp >> h2) & 0x8000u) ? BLSH_PRUNED : BLSH_LITE_SURVIVOR;
+    return o;
+}
+
+// Two-pass form, first pass with four consecutive pairs per lane: the four
+// pairs' indices in two 16-byte loads, their eight rows gathered before any
+// is decided, and one store per output array for the four (4 statuses in a
+// word, 4 counts in 8 bytes); the decisions are those of verify_first_kernel
+// (first_decide).  A pair Algorithm 1 leaves open gets kOpenStatus here and
+// everything else from the second pass.  Used when P < 2^31 and every output
+// array is aligned for its four-pair store; a quad naming an object >= N and
+// the last P mod 4 pairs go one pair at a time.  The pair list is read and
+// the outputs written with streaming hints, so that the rows (or the plane)
+// keep L2.
+template <bool PLANE>
+__global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) {
+    __shared__ unsigned s_h[4];
+    if (threadIdx.x < 4) s_h[threadIdx.x] = 0;
+    const FirstConsts c = first_consts(A);
+    __syncthreads();
+    unsigned P = (unsigned)A.P;
+    if (A.P_dev) {
+        const long long pd = *A.P_dev;
+        P = pd < 0 ? 0u : (pd < A.P ? (unsigned)pd : P);
+    }
+    const unsigned long long N = (unsigned long long)A.N;
+    const int k = A.k;
+    auto row = [&](uint32_t o) { return PLANE ? __ldg(A.plane + o) : ldg4(A.sig + (size_t)o * A.W); };
+    // stops at levels 0..3 in 16-bit fields (levels 0, 1 in h01; 2, 3 in
+    // h23), added into hc every 8192 quads (at most 4 a quad: no overflow)
+    unsigned h01 = 0, h23 = 0, hc0 = 0, hc1 = 0, hc2 = 0, hc3 = 0, iters = 0;
+    auto count = [&](const FirstOut &o) {
+        if (o.st != kOpenStatus && o.st != BLSH_NEEDS_HASHES) {
+            if (o.i < 2) h01 += 1u << (o.i << 4);
+            else h23 += 1u << ((o.i - 2) << 4);
+        }
+    };
+    auto flush = [&]() {
+        hc0 += h01 & 0xffffu;
+        hc1 += h01 >> 16;
+        hc2 += h23 & 0xffffu;
+        hc3 += h23 >> 16;
+        h01 = h23 = 0;
+    };
+    // the outputs no packed store carries: the need flags and the estimates
+    auto side = [&](unsigned q, const FirstOut &o, unsigned x, unsigned y) {
+        if (o.st == BLSH_NEEDS_HASHES) {
+            A.need[x] = 1;
+            A.need[y] = 1;
+        } else if (A.est_out && o.st != kOpenStatus && o.st != BLSH_PRUNED) {
+            A.est_out[q] = __ldg(A.est_tab + o.i * A.est_stride + o.m);
+        }
+    };
+    auto one = [&](unsigned q, uint2 pr) {
+        if ((unsigned long long)pr.x < N && (unsigned long long)pr.y < N) {
+            const FirstOut o = first_decide(c, row(pr.x), row(pr.y));
+            A.status[q] = (uint8_t)o.st;
+            if (o.st != kOpenStatus) {
+                if (A.n_used) A.n_used[q] = (uint16_t)((o.i + 1) * k);
+                if (A.m_out) A.m_out[q] = (uint16_t)o.m;
+            }
+            if (A.lite_levels) {
+                A.lstatus[q] = (uint8_t)o.ls;
+                if (A.ln_used) A.ln_used[q] = (uint16_t)((o.il + 1) * k);
+            }
+            side(q, o, pr.x, pr.y);
+            count(o);
+        } else {
+            A.status[q] = BLSH_BAD_PAIR;
+            if (A.n_used) A.n_used[q] = 0;
+            if (A.m_out) A.m_out[q] = 0;
+            if (A.lite_levels) {
+                A.lstatus[q] = BLSH_BAD_PAIR;
+                if (A.ln_used) A.ln_used[q] = 0;
+            }
+            blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
+        }
+    };
+    const unsigned nq = P >> 2, tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (unsigned g = tid; g < nq; g += nt) {
+        const uint4 *pp = reinterpret_cast<const uint4 *>(A.pairs) + 2 * (size_t)g;
+        const uint4 u = __ldcs(pp), v = __ldcs(pp + 1);
+        const unsigned mx = max(max(max(u.x, u.y), max(u.z, u.w)), max(max(v.x, v.y), max(v.z, v.w)));
+        const unsigned q = g << 2;
+        if ((unsigned long long)mx < N) {
+            const uint4 a0 = row(u.x), b0 = row(u.y), a1 = row(u.z), b1 = row(u.w);
+            const uint4 a2 = row(v.x), b2 = row(v.y), a3 = row(v.z), b3 = row(v.w);
+            const FirstOut o0 = first_decide(c, a0, b0), o1 = first_decide(c, a1, b1);
+            const FirstOut o2 = first_decide(c, a2, b2), o3 = first_decide(c, a3, b3);
+            __stcs(reinterpret_cast<unsigned *>(A.status) + g,
+                   (unsigned)o0.st | (unsigned)o1.st << 8 | (unsigned)o2.st << 16 | (unsigned)o3.st << 24);
+            if (A.n_used)
+                __stcs(reinterpret_cast<uint2 *>(A.n_used) + g,
+                       make_uint2((unsigned)((o0.i + 1) * k) | (unsigned)((o1.i + 1) * k) << 16,
+                                  (unsigned)((o2.i + 1) * k) | (unsigned)((o3.i + 1) * k) << 16));
+            if (A.m_out)
+                __stcs(reinterpret_cast<uint2 *>(A.m_out) + g,
+                       make_uint2((unsigned)o0.m | (unsigned)o1.m << 16, (unsigned)o2.m | (unsigned)o3.m << 16));
+            if (A.lite_levels) {
+                __stcs(reinterpret_cast<unsigned *>(A.lstatus) + g,
+                       (unsigned)o0.ls | (unsigned)o1.ls << 8 | (unsigned)o2.ls << 16 | (unsigned)o3.ls << 24);
+                if (A.ln_used)
+                    __stcs(reinterpret_cast<uint2 *>(A.ln_used) + g,
+                           make_uint2((unsigned)((o0.il + 1) * k) | (unsigned)((o1.il + 1) * k) << 16,
+                                      (unsigned)((o2.il + 1) * k) | (unsigned)((o3.il + 1) * k) << 16));
+            }
+            side(q, o0, u.x, u.y);
+            side(q + 1, o1, u.z, u.w);
+            side(q + 2, o2, v.x, v.y);
+            side(q + 3, o3, v.z, v.w);
+            count(o0);
+            count(o1);
+            count(o2);
+            count(o3);
+        } else {
+            one(q, make_uint2(u.x, u.y));
+            one(q + 1, make_uint2(u.z, u.w));
+            one(q + 2, make_uint2(v.x, v.y));
+            one(q + 3, make_uint2(v.z, v.w));
+        }
+        if (++iters == 8192) {
+            flush();
+            iters = 0;
+        }
+    }
+    if (tid < P - (nq << 2)) {   // the last P mod 4 pairs
+        const unsigned q = (nq << 2) + tid;
+        one(q, __ldg(A.pairs + q));
+    }
+    flush();
+    {
+        const int lane = threadIdx.x & 31;
+        const unsigned c0 = __reduce_add_sync(kFull, hc0), c1 = __reduce_add_sync(kFull, hc1);
+        const unsigned c2 = __reduce_add_sync(kFull, hc2), c3 = __reduce_add_sync(kFull, hc3);
+        const unsigned mine = lane == 0 ? c0 : lane == 1 ? c1 : lane == 2 ? c2 : lane == 3 ? c3 : 0u;
+        if (mine) atomicAdd(&s_h[lane], mine);
+    }
+    __syncthreads();
+    if (A.stop_hist && threadIdx.x < 4 && s_h[threadIdx.x])
+        atomicAdd(A.stop_hist + threadIdx.x, (unsigned long long)s_h[threadIdx.x]);
+}
+
 // plane[i] = words 0..3 of row i
 __global__ void __launch_bounds__(256) plane_copy_kernel(const uint32_t *__restrict__ sig, long long N, int W,
                                                          uint4 *__restrict__ plane) {
@@ -717,12 +944,35 @@ int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind
             // two passes -- every pair's first four chunks in a lean kernel,
             // then the pairs Algorithm 1 leaves open (a few percent)
             if (!PERSIST && A.lite_levels <= 4 && (A.lite_levels == 0 || A.lite_levels <= A.levels)) {
-                const long long blocks = (A.P + 255) / 256, cap = (long long)ctx->sm_count * 8;
-                const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
-                if (grid == 0) return BLSH_OK;
-                blsh_time_start(ctx, s);
-                if (A.plane) verify_first_kernel<true><<<grid, 256, 0, s>>>(A);
-                else verify_first_kernel<false><<<grid, 256, 0, s>>>(A);
+                // four pairs a lane where the outputs take the packed stores
+                const bool quad = A.P < (1ll << 31) && blsh_aligned(A.pairs, 16) && blsh_aligned(A.status, 4) &&
+                                  blsh_aligned(A.n_used, 8) && blsh_aligned(A.m_out, 8) &&
+                                  (!A.lite_levels || (blsh_aligned(A.lstatus, 4) && blsh_aligned(A.ln_used, 8)));
+                if (quad) {
+                    // one wave of resident CTAs; each lane loops over quads
+                    static int occ[2] = {0, 0};
+                    if (!occ[A.plane != nullptr]) {
+                        int o = 0;
+                        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                           &o, A.plane ? verify_first4_kernel<true> : verify_first4_kernel<false>,
+                                           256, 0));
+                        occ[A.plane != nullptr] = o < 1 ? 1 : o;
+                    }
+                    if (A.P == 0) return BLSH_OK;
+                    const long long blocks = (A.P / 4 + 255) / 256 > 0 ? (A.P / 4 + 255) / 256 : 1;
+                    const long long cap = (long long)ctx->sm_count * occ[A.plane != nullptr];
+                    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+                    blsh_time_start(ctx, s);
+                    if (A.plane) verify_first4_kernel<true><<<grid, 256, 0, s>>>(A);
+                    else verify_first4_kernel<false><<<grid, 256, 0, s>>>(A);
+                } else {
+                    const long long blocks = (A.P + 255) / 256, cap = (long long)ctx->sm_count * 8;
+                    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+                    if (grid == 0) return BLSH_OK;
+                    blsh_time_start(ctx, s);
+                    if (A.plane) verify_first_kernel<true><<<grid, 256, 0, s>>>(A);
+                    else verify_first_kernel<false><<<grid, 256, 0, s>>>(A);
+                }
                 BLSH_LAUNCHED(ctx, "verify_first_kernel");
                 return A.plane ? launch_kernel<BLSH_COSINE, 1, 1, false, true, true, true>(ctx, A, plan, s)
                                : launch_kernel<BLSH_COSINE, 1, 1, false, false, true, true>(ctx, A, plan, s);

@@ -134,9 +134,11 @@ def test_srp_dense_bit_exact(B, ctx, n, d, bits, tc, margin):
         assert c[2] < 0.05 * n * bits + bits
 
 
-def gpu_candidates(B, ctx, sig, kind, rows, bands, cap=None):
+def gpu_candidates(B, ctx, sig, kind, rows, bands, cap=None, ws_bytes=None):
     N = sig.shape[0]
-    ws = torch.zeros(B.blsh_lsh_candidates_workspace(N, kind, rows, bands), dtype=torch.uint8, device=dev)
+    if ws_bytes is None:
+        ws_bytes = B.blsh_lsh_candidates_workspace(N, kind, rows, bands)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device=dev)
     n = torch.zeros(1, dtype=torch.int64, device=dev)
     if cap is None:
         # count-only call first (capacity 0), then the real one
@@ -210,6 +212,36 @@ def test_banding_cosine_bit_exact(B, ctx):
         rc, n, got = gpu_candidates(B, ctx, sig, 1, rows, bands)
         assert rc == 0 and n == len(want)
         assert np.array_equal(sorted_pairs(got), sorted_pairs(want))
+
+
+def test_banding_keep_record_same_output(B, ctx):
+    """The emission's count pass records which pairs it keeps, in the
+    workspace's last 64 N bands bytes, and its write pass replays the record
+    instead of testing again; a workspace without that area, or with only part
+    of it (the positions past its end are tested again), must give the same
+    pairs in the same order, and the oracle's set."""
+    vecs = synth.tfidf_vectors(n_docs=3000, dim=30000, mean_nnz=80, n_groups=100, seed=3)
+    csig = O.srp_sparse(vecs, synth.gaussian_matrix(30000, 512, seed=4))
+    sets = synth.jaccard_sets(n_sets=2000, vocab=10000, mean_size=50, n_groups=200, seed=1)
+    a, b = synth.minhash_coeffs(256, seed=2)
+    jsig = O.minhash(sets, a, b)
+    for kind, sig, rows, bands in ((1, csig, 8, 35), (1, csig, 2, 3), (1, csig, 12, 40), (1, csig, 17, 30),
+                                   (1, csig, 5, 7), (0, jsig, 8, 32)):
+        N = sig.shape[0]
+        full = B.blsh_lsh_candidates_workspace(N, kind, rows, bands)
+        rec = 64 * N * bands
+        outs = []
+        for extra in (rec, 0, 4096, rec // 40):
+            rc, n, got = gpu_candidates(B, ctx, sig, kind, rows, bands, ws_bytes=full - rec + extra)
+            assert rc == 0
+            outs.append(got)
+        for got in outs[1:]:
+            assert np.array_equal(got, outs[0])
+        want = O.lsh_candidates(sig, O.JACCARD if kind == 0 else O.COSINE, rows, bands)
+        assert len(outs[0]) == len(want) and np.array_equal(sorted_pairs(outs[0]), sorted_pairs(want))
+    with pytest.raises(B.BlshError):          # short of the part before the record
+        gpu_candidates(B, ctx, csig, 1, 8, 35, ws_bytes=B.blsh_lsh_candidates_workspace(3000, 1, 8, 35)
+                       - 64 * 3000 * 35 - 256)
 
 
 def test_banding_buckets_and_truncation(B, ctx):

@@ -394,3 +394,49 @@ def test_capped_then_resume_equals_full(B, ctx, kind):
             assert np.array_equal(np.isnan(a_), np.isnan(b_)) and np.array_equal(a_[~np.isnan(a_)], b_[~np.isnan(b_)])
         else:
             assert np.array_equal(a_, b_)
+
+
+@pytest.mark.parametrize("off", [0, 1, 2], ids=["aligned", "shift1", "shift2"])
+def test_first_pass_forms_match_oracle(B, ctx, off):
+    """The two-pass cosine form (k = 32, plain plan): with the pair list and
+    every output array aligned for four-pair stores the first pass takes four
+    pairs a lane, otherwise one; both give the oracle's outputs, for pair
+    counts that leave every remainder mod 4, with an object index >= N in
+    one pair (its quad goes pair by pair) and a device pair count."""
+    d = TABLE_PARAMS[4]
+    p = oracle_params(d)
+    sig, pairs = model_signatures(1, d["n_max"], 4003, seed=31)
+    rng = np.random.default_rng(3)
+    pairs = np.concatenate([pairs, rng.integers(0, sig.shape[0], size=(3000, 2)).astype(np.uint32)])
+    pairs[17] = (1, sig.shape[0] + 5)
+    tab = gpu_tables(B, ctx, d)
+    dev = torch.device("cuda")
+    plan = B.blsh_plan(B.PLAN_PLAIN, 1, 256, 32, 0)
+    sig_t = torch.from_numpy(sig.view(np.int32)).to(dev)
+    for P in (len(pairs), len(pairs) - 1, len(pairs) - 2, len(pairs) - 3, 3, 1):
+        want = O.verify(O.tables(p), pairs[:P], sig)
+        cap = P + 8
+        pt = torch.zeros((cap + off, 2), dtype=torch.int32, device=dev)
+        pt[off:off + P] = torch.from_numpy(pairs[:P].view(np.int32)).to(dev)
+        st = torch.full((cap + off,), 77, dtype=torch.uint8, device=dev)
+        nu = torch.zeros(cap + off, dtype=torch.int16, device=dev)
+        m = torch.zeros(cap + off, dtype=torch.int16, device=dev)
+        est = torch.full((cap + off,), float("nan"), dtype=torch.float32, device=dev)
+        hist = torch.zeros(tab.levels, dtype=torch.int64, device=dev)
+        pd = torch.tensor([P], dtype=torch.int64, device=dev)
+        B.blsh_verify(ctx, tab, pt[off:], sig_t, st[off:], nu[off:], m[off:], est[off:], hist, P_dev=pd, plan=plan)
+        rc = B.blsh_status(ctx)
+        if P > 17:
+            assert rc == B.ERANGE
+            assert B.blsh_status(ctx) == 0
+        else:
+            assert rc == 0
+        s = st.cpu().numpy()[off:]
+        assert np.array_equal(s[:P], want.status) and np.all(s[P:] == 77) and np.all(st.cpu().numpy()[:off] == 77)
+        good = np.array([not (P > 17 and q == 17) for q in range(P)], bool)
+        assert np.array_equal(nu.cpu().numpy().view(np.uint16)[off:off + P][good], want.n_used[good])
+        assert np.array_equal(m.cpu().numpy().view(np.uint16)[off:off + P][good], want.m[good])
+        e = est.cpu().numpy()[off:off + P]
+        ok = ~np.isnan(want.est)
+        assert np.array_equal(np.isnan(e), ~ok) and np.max(np.abs(e[ok] - want.est[ok]), initial=0) <= EST_TOL
+        assert np.array_equal(hist.cpu().numpy(), O.stop_hist(want.n_used[good], p.k, p.levels).astype(np.int64))
