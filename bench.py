@@ -1271,21 +1271,30 @@ class LargePipeline:
         return np.concatenate(o1) if o1 else np.zeros(0, np.int64), np.concatenate(o2) if o2 else np.zeros(0, np.int64)
 
 
-def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
+def large_e2e(B, torch, pipe, stream, steps, use_graph, kept, depth=3):
     """The large workload end to end through the API with host buffers, as a
     batch pipeline runs it: every step's inputs (the CSR rows, 1.18 GB) are
     copied from pinned host memory and its two output sets (the counts, then
     the kept indices of every device batch) copied back, all inside the timed
-    region; the inputs of step i+1 are copied into a second set of device
-    buffers while step i runs (double buffering, one CUDA graph per buffer
-    set), and step i's outputs are read while step i+1 runs.  Returns (ms
-    per step, H2D bytes per step, D2H bytes per step, the steps' own device
-    time per step, the device's wait for a step's inputs per step, the
-    input copy's own rate in GB/s when timed alone, and per step the input
-    copy's duration, its end relative to its step's start and the wait)."""
+    region.  The device buffers form a ring of `depth` sets (one CUDA graph
+    per set; two if a third does not fit): the inputs of step i + depth - 1
+    are copied while step i runs, so a host copy that runs slow for a while
+    (the host link is shared) has depth - 1 steps to finish, and step i's
+    outputs are read while step i + 1 runs.  Returns (ms per step, H2D bytes
+    per step, D2H bytes per step, the steps' own device time per step, the
+    device's wait for a step's inputs per step, the input copy's own rate in
+    GB/s when timed alone, and per step the input copy's duration, its end
+    relative to its step's start and the wait, with the ring's depth)."""
     pin = lambda x: x.cpu().pin_memory()
     h_in = {k: pin(getattr(pipe, k)) for k in ("indptr", "indices", "values")}
     sets = [pipe.buffer_set(), pipe.new_buffer_set()]
+    while len(sets) < depth:
+        try:
+            sets.append(pipe.new_buffer_set())
+        except torch.cuda.OutOfMemoryError:
+            torch.cuda.empty_cache()
+            break
+    D = len(sets)
     graphs = []
     for bs in sets:
         pipe.use_buffer_set(bs)
@@ -1306,16 +1315,15 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     if B.blsh_status(pipe.ctx) != 0:
         raise RuntimeError("end-to-end set-up failed")
     nb = len(pipe.ranges)
-    h_counts = [torch.zeros((nb, 2), dtype=torch.int64).pin_memory() for _ in range(2)]
+    h_counts = [torch.zeros((nb, 2), dtype=torch.int64).pin_memory() for _ in range(D)]
     h_out1 = torch.zeros(kept[0] + 1024, dtype=torch.int64).pin_memory()
     h_out2 = torch.zeros(kept[1] + 1024, dtype=torch.int64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
     copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_cnt = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_out = [None, None]
+    ev_in = [torch.cuda.Event() for _ in range(D)]
+    ev_cnt = [torch.cuda.Event() for _ in range(D)]
+    ev_out = [None] * D
     d2h = [0]
-
     copy_ev = []      # (start, end) of every input copy on the copy-in stream
 
     def issue_inputs(b):
@@ -1348,7 +1356,7 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
             ev_out[b].record(copy_out)
         d2h[0] = 16 * nb + 8 * (o1 + o2)
 
-    # the host link alone: the step's input copy timed by itself (twice)
+    # the link alone: the step's input copy timed by itself (twice)
     link = []
     for _ in range(2):
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1364,9 +1372,10 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    issue_inputs(0)
+    for j in range(min(D - 1, steps)):
+        issue_inputs(j)
     for i in range(steps):
-        b = i % 2
+        b = i % D
         ev_w[i].record(stream)
         stream.wait_event(ev_in[b])
         ev_s[i].record(stream)
@@ -1381,17 +1390,18 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
         # step i is queued: the host now finishes step i-1 (its counts are on
         # the host once it completes; its output copies go on the copy-out
         # stream ahead of anything that waits for step i), then queues step
-        # i's count copy and the inputs of step i+1, so the device always has
-        # the next step waiting and the input copies overlap a running step
+        # i's count copy and the inputs of step i + D - 1 into step i-1's set,
+        # so the device always has the next step waiting and the input copies
+        # overlap running steps
         if i >= 1:
-            finish(1 - b)
+            finish((i - 1) % D)
         with torch.cuda.stream(copy_out):
             copy_out.wait_event(done)
             h_counts[b].copy_(sets[b]["n_out"], non_blocking=True)
             ev_cnt[b].record(copy_out)
-        if i + 1 < steps:
-            issue_inputs(1 - b)
-    finish((steps - 1) % 2)
+        if i + D - 1 < steps:
+            issue_inputs((i + D - 1) % D)
+    finish((steps - 1) % D)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     if B.blsh_status(pipe.ctx) != 0:
@@ -1402,8 +1412,10 @@ def large_e2e(B, torch, pipe, stream, steps, use_graph, kept):
     # each input copy's duration, and how long before its step's start it ended
     copy_ms = [a.elapsed_time(z) for a, z in copy_ev]
     lead_ms = [z.elapsed_time(s_) for (a, z), s_ in zip(copy_ev, ev_s)]
-    diag = {"input_copy_ms": [round(v, 3) for v in copy_ms], "copy_end_to_step_start_ms": [round(v, 3) for v in lead_ms],
+    diag = {"depth": D, "input_copy_ms": [round(v, 3) for v in copy_ms],
+            "copy_end_to_step_start_ms": [round(v, 3) for v in lead_ms],
             "input_wait_ms": [round(w_.elapsed_time(s_), 3) for w_, s_ in zip(ev_w, ev_s)]}
+    del sets, graphs
     return ms, h2d, d2h[0], device_ms, wait_ms, max(link), diag
 
 
@@ -1664,9 +1676,9 @@ def run_large(args, w):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_step, 4),
                 "device_ms_per_step": round(e2e_dev, 4), "input_wait_ms_per_step": round(e2e_wait, 4),
                 "h2d_gbs_alone": round(e2e_link, 1), "host_numa": numa, "per_step": e2e_diag,
-                "form": "inputs copied from pinned host memory and output sets copied back every step; step i+1's "
-                        "inputs copied into a second buffer set while step i runs, step i's outputs read while "
-                        "step i+1 runs"},
+                "form": "inputs copied from pinned host memory and output sets copied back every step; a ring of "
+                        "device buffer sets (per_step.depth), step i + depth - 1's inputs copied while step i runs, "
+                        "step i's outputs read while step i+1 runs"},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": roofline,
         "verify_hbm": {"achieved": round(v_ach, 1), "peak": peak, "unit": "GB/s", "frac": round(v_ach / peak, 4),

@@ -287,11 +287,12 @@ constexpr int kStageWords = 32;          // key rows of up to 128 bytes take thi
 __host__ __device__ inline int stage_stride(int ck_words) { return (ck_words >> 2) | 1; }
 
 // emit_warp_kernel: one warp's part of shared memory (16-byte aligned) for a
-// window of `win` positions, and the largest window (a multiple of 32) that
-// fits the warp's budget.
+// window of `win` positions (key rows, keys, ids), the rows and ids of 32
+// partners past the window and 32 words of kept bits, and the largest window
+// (a multiple of 32) that fits the warp's budget.
 __host__ __device__ inline size_t emit_warp_region(int ck_words, int win) {
     const int kw4 = ck_words <= 16 ? 4 : 8;
-    const size_t b = (size_t)win * (stage_stride(ck_words) * 16 + 8 + 4) + 32 * 16 * kw4 + 32 * 4;
+    const size_t b = (size_t)win * (stage_stride(ck_words) * 16 + 8 + 4) + 32 * 16 * kw4 + 2 * 32 * 4;
     return (b + 15) & ~(size_t)15;
 }
 // (two CTAs of eight warps per SM; three for the count pass over key rows
@@ -436,6 +437,21 @@ __device__ __forceinline__ bool emit_step(const uint4 *yrow, uint32_t y, unsigne
     return ok;
 }
 
+// Position of set bit number k (from 0, lowest first) of m; k < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, unsigned k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned c = (unsigned)__popc(m & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // The walk of one warp over partners [jmin, jmax) (tile-relative), NW4
 // 16-byte words of key rows compared per pair (cmp: the lane's plan for
 // its band).  Partners inside the window come from the stage; partners past
@@ -445,7 +461,8 @@ __device__ __forceinline__ bool emit_step(const uint4 *yrow, uint32_t y, unsigne
 // rec[32 w + lane] is partner jmin + 32 w + t.
 template <int NW4, bool WRITE, bool PZ>
 __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, const uint32_t *s_val,
-                                          uint4 *w_rows, uint32_t *w_ids, const uint32_t *vals, long long p0,
+                                          uint4 *w_rows, uint32_t *w_ids, uint32_t *s_und, const uint32_t *vals,
+                                          long long p0,
                                           int win, int stride, unsigned jmin, unsigned jmax, bool live, int i,
                                           long long end, uint32_t x, const uint4 *kx, const EmitCmp &cmp,
                                           const uint32_t *pz, int eqw, bool jac, uint32_t one, uint32_t high,
@@ -479,27 +496,86 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
         // the end of the batch, and the batch's pairs are then counted, or
         // written in partner order.
         const bool more = cmp.nf4 >= 2 || (cmp.nf4 == 1 && (jac || (cmp.tm[0] | cmp.tm[1] | cmp.tm[2] | cmp.tm[3])));
+        // the lane's partners: jlo <= j < jhi (none for an idle lane)
+        const unsigned jlo = (unsigned)i + 1u, jhi = live ? (unsigned)(end - p0) : 0u;
+        const bool whole = cmp.nf4 >= 1;
+        const uint32_t m0 = whole ? high : cmp.tm[0], m1 = whole ? high : cmp.tm[1];
+        const uint32_t m2 = whole ? high : cmp.tm[2], m3 = whole ? high : cmp.tm[3];
+        const bool need_zr = !whole && jac;     // band b's own class id, in the first chunk
         auto batch = [&](unsigned j0, unsigned n, const uint4 *rows, int rstride, const uint32_t *ids) {
-            uint32_t keep = 0, und = 0;
+            // bit u: no earlier band of the first chunk agrees (hz), band b's
+            // class id agrees (zm, Jaccard in the first chunk only)
+            uint32_t hz = 0, zm = 0;
             for (unsigned u = 0; u < n; ++u) {
-                const unsigned j = j0 + u;
                 const uint4 yv = rows[(size_t)u * rstride];
                 const uint32_t z0 = kx[0].x ^ yv.x, z1 = kx[0].y ^ yv.y, z2 = kx[0].z ^ yv.z, z3 = kx[0].w ^ yv.w;
-                const bool whole = cmp.nf4 >= 1;
-                const uint32_t h = ((z0 - one) & ~z0 & (whole ? high : cmp.tm[0])) |
-                                   ((z1 - one) & ~z1 & (whole ? high : cmp.tm[1])) |
-                                   ((z2 - one) & ~z2 & (whole ? high : cmp.tm[2])) |
-                                   ((z3 - one) & ~z3 & (whole ? high : cmp.tm[3]));
-                const uint32_t zr = cmp.r == 0 ? z0 : cmp.r == 1 ? z1 : cmp.r == 2 ? z2 : z3;
-                const bool in = live && (int)j > i && p0 + (long long)j < end;
-                if (in && h == 0) {
-                    if (whole && more) und |= 1u << u;
-                    else if (whole || !jac || zr == 0) keep |= 1u << u;
+                const uint32_t h = ((z0 - one) & ~z0 & m0) | ((z1 - one) & ~z1 & m1) | ((z2 - one) & ~z2 & m2) |
+                                   ((z3 - one) & ~z3 & m3);
+                hz |= (uint32_t)(h == 0) << u;
+                if (need_zr) {
+                    const uint32_t zr = cmp.r == 0 ? z0 : cmp.r == 1 ? z1 : cmp.r == 2 ? z2 : z3;
+                    zm |= (uint32_t)(zr == 0) << u;
                 }
             }
-            for (uint32_t b = und; b; b &= b - 1) {
-                const int u = __ffs(b) - 1;
-                if (emit_test<NW4, 1>(kx, rows + (size_t)u * rstride, cmp, jac, one, high)) keep |= 1u << u;
+            // partners j0 + u inside [jlo, jhi)
+            const unsigned lo = jlo > j0 ? (jlo - j0 < 32u ? jlo - j0 : 32u) : 0u;
+            const unsigned hi = jhi > j0 ? (jhi - j0 < n ? jhi - j0 : n) : 0u;
+            const uint32_t below_hi = hi >= 32u ? ~0u : (1u << hi) - 1u;
+            const uint32_t below_lo = lo >= 32u ? ~0u : (1u << lo) - 1u;
+            hz &= below_hi & ~below_lo;
+            uint32_t keep = 0, und = 0;
+            if (whole && more) und = hz;
+            else keep = need_zr ? hz & zm : hz;
+            // The undecided (lane, partner) tests.  Where they are uneven
+            // (the lane with the most has over 1.25 times the rounds of 32
+            // that the warp's total takes, plus one) they are spread evenly
+            // over the warp: numbered lane by
+            // lane, test t goes to lane t mod 32, which reads both key rows
+            // from shared memory and sets the kept bit in the owner's word of
+            // s_und.  Otherwise every lane finishes its own.
+            const unsigned nu = (unsigned)__popc(und);
+            unsigned incl = nu;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned off = incl - nu, total = __shfl_sync(kFull, incl, 31);
+            const unsigned most = __reduce_max_sync(kFull, nu);
+            const unsigned rounds = (total + 31) / 32;
+            if (most > rounds + rounds / 4 + 1) {
+                s_und[lane] = 0;
+                __syncwarp();
+                const int my_full = 4 * cmp.nf4 + cmp.r;
+                const uint32_t my_pm = cmp.r == 0 ? cmp.tm[0] : cmp.r == 1 ? cmp.tm[1] : cmp.r == 2 ? cmp.tm[2] : cmp.tm[3];
+                for (unsigned t0 = 0; t0 < total; t0 += 32) {
+                    const unsigned t = t0 + lane;
+                    int o = 0;                            // the last lane whose first test is <= t
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const unsigned oc = __shfl_sync(kFull, off, o + step);
+                        if (oc <= t) o += step;
+                    }
+                    const unsigned k = t - __shfl_sync(kFull, off, o);
+                    const uint32_t um = __shfl_sync(kFull, und, o);
+                    const int full_o = __shfl_sync(kFull, my_full, o);
+                    const uint32_t pm_o = __shfl_sync(kFull, my_pm, o);
+                    if (t < total) {
+                        const int u = nth_set_bit(um, k);
+                        const uint4 *xr = s_ck + (size_t)o * stride;   // position o of the chunk
+                        if (emit_test<NW4, 1>(xr, rows + (size_t)u * rstride, emit_cmp(full_o, pm_o, high), jac, one,
+                                              high))
+                            atomicOr(&s_und[o], 1u << u);
+                    }
+                }
+                __syncwarp();
+                keep |= s_und[lane];
+                __syncwarp();
+            } else {
+                for (uint32_t b = und; b; b &= b - 1) {
+                    const int u = __ffs(b) - 1;
+                    if (emit_test<NW4, 1>(kx, rows + (size_t)u * rstride, cmp, jac, one, high)) keep |= 1u << u;
+                }
             }
             if (!WRITE && rec) rec_put(j0 - jmin, n, keep);
             if (WRITE) {
@@ -512,19 +588,38 @@ __device__ __forceinline__ void emit_walk(const BandArgs &A, const uint4 *s_ck, 
                 cnt += __popc(keep);
             }
         };
-        for (unsigned j0 = jmin; j0 < wend; j0 += 32)
-            batch(j0, wend - j0 < 32u ? wend - j0 : 32u, s_ck + (size_t)j0 * stride, stride, s_val + j0);
-        for (unsigned j0 = jmin > (unsigned)win ? jmin : (unsigned)win; j0 < jmax; j0 += 32) {
-            __syncwarp();
-            if (j0 + lane < jmax) {
-                const uint32_t yv = __ldg(vals + p0 + j0 + lane);
-                w_ids[lane] = yv;
-                const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
+        // one call site for both kinds of batch (the code is large): partners
+        // inside the window from the stage, past it fetched into the warp's
+        // buffer (whole key rows: cw4 chunks, at most NW4)
+        const int cw4 = A.ck_words >> 2;
+        for (unsigned j0 = jmin; j0 < jmax;) {
+            const uint4 *rows;
+            int rstride;
+            const uint32_t *ids;
+            unsigned n;
+            if (j0 < wend) {
+                n = wend - j0 < 32u ? wend - j0 : 32u;
+                rows = s_ck + (size_t)j0 * stride;
+                rstride = stride;
+                ids = s_val + j0;
+            } else {
+                n = jmax - j0 < 32u ? jmax - j0 : 32u;
+                __syncwarp();
+                if (j0 + lane < jmax) {
+                    const uint32_t yv = __ldg(vals + p0 + j0 + lane);
+                    w_ids[lane] = yv;
+                    const uint4 *g = reinterpret_cast<const uint4 *>(A.ck + (size_t)yv * A.ck_words);
 #pragma unroll
-                for (int c = 0; c < NW4; ++c) w_rows[lane * NW4 + c] = __ldg(g + c);
+                    for (int c = 0; c < NW4; ++c)
+                        if (c < cw4) w_rows[lane * NW4 + c] = __ldg(g + c);
+                }
+                __syncwarp();
+                rows = w_rows;
+                rstride = NW4;
+                ids = w_ids;
             }
-            __syncwarp();
-            batch(j0, jmax - j0 < 32u ? jmax - j0 : 32u, w_rows, NW4, w_ids);
+            batch(j0, n, rows, rstride, ids);
+            j0 += n;
         }
         if (!WRITE && rec && jmax > jmin) rec[(size_t)ridx * 32 + lane] = racc;   // the last word
     } else {
@@ -691,13 +786,14 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
     const int cw4 = A.ck_words >> 2, cws = stage_stride(A.ck_words);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // the warp's region: [win_cap][cws] key rows, [32][KW4] partner rows,
-    // keys [win_cap], object ids [win_cap], ids or counts [32]
+    // keys [win_cap], object ids [win_cap], ids or counts [32], kept bits [32]
     const size_t region = emit_warp_region(A.ck_words, win_cap);
     uint4 *s_ck = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(s_all) + warp * region);
     uint4 *w_rows = s_ck + (size_t)win_cap * cws;
     unsigned long long *s_key = reinterpret_cast<unsigned long long *>(w_rows + 32 * KW4);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + win_cap);
     uint32_t *w_ids = s_val + win_cap;
+    uint32_t *s_und = w_ids + 32;
     const uint32_t one = A.ck_lane == 1 ? 0x01010101u : (A.ck_lane == 2 ? 0x00010001u : 1u);
     const uint32_t high = one << (8 * A.ck_lane - 1);
     const int per_word = 4 / A.ck_lane;
@@ -830,7 +926,7 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
         constexpr bool kPZ = KW4 <= 4;
         uint32_t pz[kPZ ? 16 : 1];
         if constexpr (kPZ) emit_poison<16>(pz, full, rest, 8 * A.ck_lane, one);
-#define BLSH_WALK(NW) emit_walk<NW, WRITE, kPZ>(A, s_ck, s_val, w_rows, w_ids, vals, p0, win, cws, jmin, jmax, live, \
+#define BLSH_WALK(NW) emit_walk<NW, WRITE, kPZ>(A, s_ck, s_val, w_rows, w_ids, s_und, vals, p0, win, cws, jmin, jmax, live, \
                                                 i, end, x, kx, cmp, pz, eqw, jac, one, high, out, cnt, pairs, cap, crec)
         if constexpr (KW4 <= 4) {
             switch (nw4) {
@@ -841,13 +937,11 @@ __global__ void __launch_bounds__(256, (KW4 <= 4 && !WRITE) ? 3 : 2) emit_warp_k
             default: BLSH_WALK(4); break;
             }
         } else {
-            switch (nw4) {
-            case 0: BLSH_WALK(0); break;
-            case 1: case 2: BLSH_WALK(2); break;
-            case 3: case 4: BLSH_WALK(4); break;
-            case 5: case 6: BLSH_WALK(6); break;
-            default: BLSH_WALK(8); break;
-            }
+            // rows of 5-8 chunks: the walk reads chunk 0 of every pair and
+            // the rest only for the few pairs it leaves undecided, so one
+            // form (NW4 = 8, chunks past the plan skipped) serves every band
+            if (nw4 == 0) BLSH_WALK(0);
+            else BLSH_WALK(8);
         }
 #undef BLSH_WALK
         if (!WRITE && live) counts[p0 + i] = cnt;

@@ -158,7 +158,7 @@ __device__ __forceinline__ float r_fp32(const uint16_t *R, size_t i) {
 constexpr int kSrpMaxPerThread = 16;
 constexpr int kSrpLooseRow = 256;   // rows up to this length use the 2^15 sum|v| magnitude bound (two-byte codes)
 constexpr int kSrpBatch = 8;
-constexpr int kSrpGrab = 8;         // (row, piece) items a CTA of srp_sparse4_kernel takes per grab       // float4 gathers of R in flight per thread (srp_sparse4_kernel)
+constexpr int kSrpGrab = 8;         // (row, piece) items a CTA of srp_sparse4_kernel takes per grab
 constexpr int kSrpChunk = 256;
 
 template <typename RT>

@@ -421,10 +421,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) srp_dense_tc_persistent(
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
-// Queued signs: eight lanes per (row, bit), lane g of the group owning
-// coordinates [g d/8, (g+1) d/8).  Three stages, each with a rigorous bound:
-//   FP32 partial sums (any summation order errs by at most (d+8) u sum|p|);
-//   if undecided, FP64 partial sums of the exact products (error at most
+// Queued signs: eight lanes per (row, bit).  Three stages, each with a
+// rigorous bound:
+//   FP32 partial sums, lane g of the group taking the 16-byte pieces 8i + g
+//   of both rows (any summation order errs by at most (d+8) u sum|p|);
+//   if undecided, FP64 partial sums of the exact products, lane g owning
+//   coordinates [g d/8, (g+1) d/8) (error at most
 //   (d+8) 2^-53 sum|p|, so a sign it decides is the sign of the exact sum and
 //   of the oracle's sum, which errs by less);
 //   if still undecided (exact ties such as zero rows), the FP64 sum over
@@ -449,13 +451,19 @@ __global__ void __launch_bounds__(256) srp_dense_recheck_kernel(const uint2 *__r
         const bool live = it < n;
         uint2 rj = make_uint2(0u, 0u);
         if (live) rj = queue[it];
-        const float *x = X + (size_t)rj.x * d + g * per;
-        const float *r = Rt + (size_t)rj.y * d + g * per;
+        const float *xr = X + (size_t)rj.x * d, *rr = Rt + (size_t)rj.y * d;
+        const float *x = xr + g * per;
+        const float *r = rr + g * per;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        // FP32 stage: the group's eight lanes read 128 contiguous bytes of each
+        // row per step (lane g the 16 bytes at 4 (8 i + g)); the bound holds
+        // for any order of the terms
         if (live)
-            for (int c = 0; c < per; c += 4) {
-                const float4 u = __ldg(reinterpret_cast<const float4 *>(x + c));
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(r + c));
+#pragma unroll 4
+            for (int i = 0; i < per / 4; ++i) {
+                const int c = (8 * i + g) * 4;
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(xr + c));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(rr + c));
                 a0 = __fmaf_rn(u.x, v.x, a0); a1 = __fmaf_rn(u.y, v.y, a1);
                 a2 = __fmaf_rn(u.z, v.z, a2); a3 = __fmaf_rn(u.w, v.w, a3);
                 m0 = __fmaf_rn(fabsf(u.x), fabsf(v.x), m0); m1 = __fmaf_rn(fabsf(u.y), fabsf(v.y), m1);

@@ -109,7 +109,7 @@ def test_srp_sparse_recheck_queue(B, ctx, n_docs):
     (3000, 64, 128, False, 0.0),      # CUDA-core path (bits not a multiple of 256)
     (300, 64, 256, True, 0.0),        # tensor cores, one K stage, ragged last row tile
     (3000, 256, 1024, True, 0.0),     # tensor cores, four K stages, four bit tiles
-    (3000, 256, 1024, True, 1e-3),    # the spec margin (wider than the error bound)
+    (3000, 256, 1024, True, 1e-3),    # the precision workload's margin (wider than the error bound)
     (1000, 128, 512, True, 0.0),
 ])
 def test_srp_dense_bit_exact(B, ctx, n, d, bits, tc, margin):
