@@ -401,8 +401,7 @@ class ClockSampler:
 # dram__bytes_write.sum of the bench step under --profile-step); reported as
 # the roofline's traffic for the workload it was taken on (per step, like the
 # algorithmic bytes), and to be taken again whenever the kernel changes.
-NCU_TRAFFIC = {("large-mixed", "srp_sparse4_kernel (two-byte codes)"): 27486.8e6 + 329.0e6,
-               ("cosine-small", "srp_sparse4_kernel"): 436.7e6 + 3.8e6}
+NCU_TRAFFIC = {("large-mixed", "srp_sparse4_kernel (two-byte codes)"): (20874986240 + 163516160) + (6676972544 + 165890816)}
 
 
 def load_tensor_peak():
