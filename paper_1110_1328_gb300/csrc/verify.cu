@@ -1335,8 +1335,12 @@ __global__ void __launch_bounds__(256) verify_resume_kernel(const VerifyArgs A, 
                     m += carry;
                     int s = -1;
                     if (j < A.levels) {
+                        // concentration: m >= conc_lo[j] where every level's set is an upper range
+                        const bool conc = A.conc_upper
+                                              ? m >= __ldg(A.conc_lo + j)
+                                              : (__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u;
                         if (m < __ldg(A.min_matches + j)) s = BLSH_PRUNED;
-                        else if ((__ldg(A.conc_bits + j * A.conc_words + (m >> 5)) >> (m & 31)) & 1u) s = BLSH_ACCEPT;
+                        else if (conc) s = BLSH_ACCEPT;
                         else if (j + 1 == A.levels) s = BLSH_ACCEPT_AT_MAX;
                     }
                     const unsigned stop = __ballot_sync(kFull, s >= 0);
