@@ -528,15 +528,19 @@ def csr_rows_bytes(indptr, indices, rows, ncols, esize):
 
 def verification_totals(work, timed):
     """The verification stage's algorithmic bytes and device time per step:
-    every verification kernel that ran (the two-pass form's first pass,
-    verify_kernel, the lazy form's resume).  With the two-pass form the
-    bytes are split between its passes for the per-kernel figures."""
+    every verification kernel that ran (the two-pass form in one kernel, or
+    its first pass and verify_kernel, the lazy form's resume).  With two
+    kernels the bytes are split between the passes for the per-kernel
+    figures."""
     total = work["verify_kernel"][0]
     first = work.pop("verify_first_kernel", (0, "B"))[0]
     if "verify_first_kernel" in timed:
         work["verify_first_kernel"] = (first, "B")
         work["verify_kernel"] = (total - first, "B")
-    names = [n for n in ("verify_first_kernel", "verify_kernel", "verify_resume_kernel") if n in timed]
+    if "verify_tile_kernel" in timed:     # both passes in one kernel
+        work["verify_tile_kernel"] = (total, "B")
+    names = [n for n in ("verify_tile_kernel", "verify_first_kernel", "verify_kernel", "verify_resume_kernel")
+             if n in timed]
     vbytes = total + work.get("verify_resume_kernel", (0, "B"))[0]
     v_ms = sum(timed[n][1] for n in names)
     return vbytes, v_ms, " + ".join(names)
@@ -1070,7 +1074,7 @@ def run_verify_large(args, w):
     kept = int(((stn == B.ACCEPT) | (stn == B.ACCEPT_AT_MAX)).sum())
     alg = P * (8 + 5) + 4 * kept + chunks * (w["k"] // 4)
     sector = P * (8 + 9) + P * 2 * 32
-    v_names = [n for n in ("verify_first_kernel", "verify_kernel") if n in kern]
+    v_names = [n for n in ("verify_tile_kernel", "verify_first_kernel", "verify_kernel") if n in kern]
     vk = sum(kern[n] for n in v_names) or ms
     print(json.dumps({"metric": METRIC, "value": round(P / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),

@@ -32,10 +32,14 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
 // Status of a pair Algorithm 1 leaves open after its first four chunks in
-// the two-pass form (verify_first_kernel, then verify_kernel with OPEN);
-// internal to one call (every such pair is finished, and its status
-// overwritten, before the call returns).
-constexpr uint8_t kOpenStatus = 254;
+// the two-pass form (verify_tile_kernel, or verify_first_kernel then
+// verify_kernel with OPEN); internal to one call (every such pair is
+// finished, and its status overwritten, before the call returns).  It differs
+// from every other status, BLSH_LITE_SURVIVOR (254) included: a Lite
+// survivor is decided, not open.
+constexpr uint8_t kOpenStatus = 252;
+static_assert(kOpenStatus != BLSH_LITE_SURVIVOR && kOpenStatus != BLSH_NEEDS_HASHES && kOpenStatus != BLSH_BAD_PAIR,
+              "the open status must differ from every other status");
 
 // Parked pairs per warp (FAST plain form): at most 31 waiting plus the 32 of
 // a step.
@@ -688,6 +692,7 @@ struct FirstConsts {
 // there; Algorithm 2's status ls and level il.
 struct FirstOut {
     int st, i, m, ls, il;
+    int m4;   // agreements after chunk 3 (where Algorithm 1 goes on from an open pair)
 };
 
 __device__ __forceinline__ FirstConsts first_consts(const VerifyArgs &A) {
@@ -731,6 +736,7 @@ __device__ __forceinline__ FirstOut first_decide(const FirstConsts &c, uint4 a, 
     o.st = kOpenStatus;
     o.i = 0;
     o.m = 0;
+    o.m4 = 128 - (int)(w1 >> 16);
     if (s0 | s1) {   // the first level with a decision (or the limit)
         const bool lo = s0 != 0;
         const unsigned s = lo ? s0 : s1, w = lo ? w0 : w1, p = lo ? p0 : p1, q = lo ? q0 : q1;
@@ -753,20 +759,36 @@ __device__ __forceinline__ FirstOut first_decide(const FirstConsts &c, uint4 a, 
     return o;
 }
 
-// Two-pass form, first pass with four consecutive pairs per lane: the four
-// pairs' indices in two 16-byte loads, their eight rows gathered before any
-// is decided, and one store per output array for the four (4 statuses in a
-// word, 4 counts in 8 bytes); the decisions are those of verify_first_kernel
-// (first_decide).  A pair Algorithm 1 leaves open gets kOpenStatus here and
-// everything else from the second pass.  Used when P < 2^31 and every output
-// array is aligned for its four-pair store; a quad naming an object >= N and
-// the last P mod 4 pairs go one pair at a time.  The pair list is read and
-// the outputs written with streaming hints, so that the rows (or the plane)
-// keep L2.
+// The two passes in one kernel, where every output array takes packed
+// four-pair stores and P < 2^31.  A warp takes tiles of kTilePairs
+// consecutive pairs from a counter.  It runs the first pass over its tile
+// four pairs a lane (their indices in two 16-byte loads, their eight rows
+// gathered before any is decided, one store per output array for the four:
+// 4 statuses in a word, 4 counts in 8 bytes; the decisions of
+// verify_first_kernel, taken by first_decide), four quads a lane, and keeps
+// the pairs Algorithm 1 leaves open after four chunks in its part of shared
+// memory (the pair's offset in the tile and its agreements so far); then it
+// continues them 32 at a time, a lane each, from chunk 4 on, with the tests
+// of verify_kernel's step (four chunks a step, thresholds in shared memory)
+// until each stops.  The open pairs' outputs land in the sectors the first
+// pass wrote a moment before, still in L2; a second kernel would scan every
+// status again and read each such sector back from DRAM to change a few
+// bytes of it.
+constexpr int kTilePairs = 512;
+
 template <bool PLANE>
-__global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) {
-    __shared__ unsigned s_h[4];
-    if (threadIdx.x < 4) s_h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(256) verify_tile_kernel(const VerifyArgs A) {
+    extern __shared__ int32_t s_tab[];
+    // minMatches and the concentration bounds of every level, the stop
+    // histogram, then each warp's open list: (offset in the tile) | m << 16
+    int32_t *s_mm = s_tab, *s_clo = s_tab + A.levels;
+    unsigned *s_hist = reinterpret_cast<unsigned *>(s_tab + 2 * A.levels);
+    uint32_t *s_open = reinterpret_cast<uint32_t *>(s_tab + 3 * A.levels) + (threadIdx.x >> 5) * kTilePairs;
+    for (int i = threadIdx.x; i < A.levels; i += blockDim.x) {
+        s_mm[i] = __ldg(A.min_matches + i);
+        s_clo[i] = __ldg(A.conc_lo + i);
+        s_hist[i] = 0;
+    }
     const FirstConsts c = first_consts(A);
     __syncthreads();
     unsigned P = (unsigned)A.P;
@@ -775,10 +797,9 @@ __global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) 
         P = pd < 0 ? 0u : (pd < A.P ? (unsigned)pd : P);
     }
     const unsigned long long N = (unsigned long long)A.N;
-    const int k = A.k;
+    const int k = A.k, lane = threadIdx.x & 31;
     auto row = [&](uint32_t o) { return PLANE ? __ldg(A.plane + o) : ldg4(A.sig + (size_t)o * A.W); };
-    // stops at levels 0..3 in 16-bit fields (levels 0, 1 in h01; 2, 3 in
-    // h23), added into hc every 8192 quads (at most 4 a quad: no overflow)
+    // stops at levels 0..3 in 16-bit fields, added into hc every 8192 quads
     unsigned h01 = 0, h23 = 0, hc0 = 0, hc1 = 0, hc2 = 0, hc3 = 0, iters = 0;
     auto count = [&](const FirstOut &o) {
         if (o.st != kOpenStatus && o.st != BLSH_NEEDS_HASHES) {
@@ -793,7 +814,6 @@ __global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) 
         hc3 += h23 >> 16;
         h01 = h23 = 0;
     };
-    // the outputs no packed store carries: the need flags and the estimates
     auto side = [&](unsigned q, const FirstOut &o, unsigned x, unsigned y) {
         if (o.st == BLSH_NEEDS_HASHES) {
             A.need[x] = 1;
@@ -802,7 +822,9 @@ __global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) 
             A.est_out[q] = __ldg(A.est_tab + o.i * A.est_stride + o.m);
         }
     };
-    auto one = [&](unsigned q, uint2 pr) {
+    // one pair by itself (a tail, or a quad naming an object >= N); returns
+    // whether it is open
+    auto one = [&](unsigned q, uint2 pr, int &m4) -> bool {
         if ((unsigned long long)pr.x < N && (unsigned long long)pr.y < N) {
             const FirstOut o = first_decide(c, row(pr.x), row(pr.y));
             A.status[q] = (uint8_t)o.st;
@@ -816,79 +838,199 @@ __global__ void __launch_bounds__(256) verify_first4_kernel(const VerifyArgs A) 
             }
             side(q, o, pr.x, pr.y);
             count(o);
-        } else {
-            A.status[q] = BLSH_BAD_PAIR;
-            if (A.n_used) A.n_used[q] = 0;
-            if (A.m_out) A.m_out[q] = 0;
-            if (A.lite_levels) {
-                A.lstatus[q] = BLSH_BAD_PAIR;
-                if (A.ln_used) A.ln_used[q] = 0;
-            }
-            blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
+            m4 = o.m4;
+            return o.st == kOpenStatus;
         }
+        A.status[q] = BLSH_BAD_PAIR;
+        if (A.n_used) A.n_used[q] = 0;
+        if (A.m_out) A.m_out[q] = 0;
+        if (A.lite_levels) {
+            A.lstatus[q] = BLSH_BAD_PAIR;
+            if (A.ln_used) A.ln_used[q] = 0;
+        }
+        blsh_dev_error(A.scratch, BLSH_ERANGE, 0, 1ull);
+        return false;
     };
-    const unsigned nq = P >> 2, tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    for (unsigned g = tid; g < nq; g += nt) {
-        const uint4 *pp = reinterpret_cast<const uint4 *>(A.pairs) + 2 * (size_t)g;
-        const uint4 u = __ldcs(pp), v = __ldcs(pp + 1);
-        const unsigned mx = max(max(max(u.x, u.y), max(u.z, u.w)), max(max(v.x, v.y), max(v.z, v.w)));
-        const unsigned q = g << 2;
-        if ((unsigned long long)mx < N) {
-            const uint4 a0 = row(u.x), b0 = row(u.y), a1 = row(u.z), b1 = row(u.w);
-            const uint4 a2 = row(v.x), b2 = row(v.y), a3 = row(v.z), b3 = row(v.w);
-            const FirstOut o0 = first_decide(c, a0, b0), o1 = first_decide(c, a1, b1);
-            const FirstOut o2 = first_decide(c, a2, b2), o3 = first_decide(c, a3, b3);
-            __stcs(reinterpret_cast<unsigned *>(A.status) + g,
-                   (unsigned)o0.st | (unsigned)o1.st << 8 | (unsigned)o2.st << 16 | (unsigned)o3.st << 24);
-            if (A.n_used)
-                __stcs(reinterpret_cast<uint2 *>(A.n_used) + g,
-                       make_uint2((unsigned)((o0.i + 1) * k) | (unsigned)((o1.i + 1) * k) << 16,
-                                  (unsigned)((o2.i + 1) * k) | (unsigned)((o3.i + 1) * k) << 16));
-            if (A.m_out)
-                __stcs(reinterpret_cast<uint2 *>(A.m_out) + g,
-                       make_uint2((unsigned)o0.m | (unsigned)o1.m << 16, (unsigned)o2.m | (unsigned)o3.m << 16));
-            if (A.lite_levels) {
-                __stcs(reinterpret_cast<unsigned *>(A.lstatus) + g,
-                       (unsigned)o0.ls | (unsigned)o1.ls << 8 | (unsigned)o2.ls << 16 | (unsigned)o3.ls << 24);
-                if (A.ln_used)
-                    __stcs(reinterpret_cast<uint2 *>(A.ln_used) + g,
-                           make_uint2((unsigned)((o0.il + 1) * k) | (unsigned)((o1.il + 1) * k) << 16,
-                                      (unsigned)((o2.il + 1) * k) | (unsigned)((o3.il + 1) * k) << 16));
+    auto at = [](int lim, int j) { const int d = lim - 1 - j; return d >= 0 && d < 4 ? 1u << d : 0u; };
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&A.scratch->work, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if (t * kTilePairs >= P) break;
+        const unsigned base = (unsigned)t * kTilePairs;
+        int n_open = 0;   // the warp's open pairs in this tile so far
+        __syncwarp();     // the previous tile's list has been read
+#pragma unroll 1
+        for (int r = 0; r < kTilePairs / 128; ++r) {
+            const unsigned q = base + 128u * r + 4u * lane;
+            unsigned om = 0;   // which of the lane's four pairs are open
+            int m4[4] = {0, 0, 0, 0};
+            if (q + 4 <= P) {
+                const uint4 *pp = reinterpret_cast<const uint4 *>(A.pairs) + (q >> 1);
+                const uint4 u = __ldcs(pp), v = __ldcs(pp + 1);
+                const unsigned mx = max(max(max(u.x, u.y), max(u.z, u.w)), max(max(v.x, v.y), max(v.z, v.w)));
+                if ((unsigned long long)mx < N) {
+                    const uint4 a0 = row(u.x), b0 = row(u.y), a1 = row(u.z), b1 = row(u.w);
+                    const uint4 a2 = row(v.x), b2 = row(v.y), a3 = row(v.z), b3 = row(v.w);
+                    const FirstOut o0 = first_decide(c, a0, b0), o1 = first_decide(c, a1, b1);
+                    const FirstOut o2 = first_decide(c, a2, b2), o3 = first_decide(c, a3, b3);
+                    const unsigned g = q >> 2;
+                    reinterpret_cast<unsigned *>(A.status)[g] =
+                        (unsigned)o0.st | (unsigned)o1.st << 8 | (unsigned)o2.st << 16 | (unsigned)o3.st << 24;
+                    if (A.n_used)
+                        reinterpret_cast<uint2 *>(A.n_used)[g] =
+                            make_uint2((unsigned)((o0.i + 1) * k) | (unsigned)((o1.i + 1) * k) << 16,
+                                       (unsigned)((o2.i + 1) * k) | (unsigned)((o3.i + 1) * k) << 16);
+                    if (A.m_out)
+                        reinterpret_cast<uint2 *>(A.m_out)[g] =
+                            make_uint2((unsigned)o0.m | (unsigned)o1.m << 16, (unsigned)o2.m | (unsigned)o3.m << 16);
+                    if (A.lite_levels) {
+                        reinterpret_cast<unsigned *>(A.lstatus)[g] =
+                            (unsigned)o0.ls | (unsigned)o1.ls << 8 | (unsigned)o2.ls << 16 | (unsigned)o3.ls << 24;
+                        if (A.ln_used)
+                            reinterpret_cast<uint2 *>(A.ln_used)[g] =
+                                make_uint2((unsigned)((o0.il + 1) * k) | (unsigned)((o1.il + 1) * k) << 16,
+                                           (unsigned)((o2.il + 1) * k) | (unsigned)((o3.il + 1) * k) << 16);
+                    }
+                    side(q, o0, u.x, u.y);
+                    side(q + 1, o1, u.z, u.w);
+                    side(q + 2, o2, v.x, v.y);
+                    side(q + 3, o3, v.z, v.w);
+                    count(o0);
+                    count(o1);
+                    count(o2);
+                    count(o3);
+                    om = (unsigned)(o0.st == kOpenStatus) | (unsigned)(o1.st == kOpenStatus) << 1 |
+                         (unsigned)(o2.st == kOpenStatus) << 2 | (unsigned)(o3.st == kOpenStatus) << 3;
+                    m4[0] = o0.m4;
+                    m4[1] = o1.m4;
+                    m4[2] = o2.m4;
+                    m4[3] = o3.m4;
+                } else {
+                    om = (unsigned)one(q, make_uint2(u.x, u.y), m4[0]) | (unsigned)one(q + 1, make_uint2(u.z, u.w), m4[1]) << 1 |
+                         (unsigned)one(q + 2, make_uint2(v.x, v.y), m4[2]) << 2 |
+                         (unsigned)one(q + 3, make_uint2(v.z, v.w), m4[3]) << 3;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (q + i < P) om |= (unsigned)one(q + i, __ldg(A.pairs + q + i), m4[i]) << i;
             }
-            side(q, o0, u.x, u.y);
-            side(q + 1, o1, u.z, u.w);
-            side(q + 2, o2, v.x, v.y);
-            side(q + 3, o3, v.z, v.w);
-            count(o0);
-            count(o1);
-            count(o2);
-            count(o3);
-        } else {
-            one(q, make_uint2(u.x, u.y));
-            one(q + 1, make_uint2(u.z, u.w));
-            one(q + 2, make_uint2(v.x, v.y));
-            one(q + 3, make_uint2(v.z, v.w));
+            // the open pairs into the warp's list, in lane order
+            const int cnt = __popc(om);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int slot = n_open + incl - cnt;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((om >> i) & 1u) {
+                    if (slot < kTilePairs && q + i - base < kTilePairs) s_open[slot] = (q + i - base) | (uint32_t)m4[i] << 16;
+                    else blsh_dev_error(A.scratch, BLSH_EDEVICE, -1, 0ull);   // (self-check: no slot)
+                    ++slot;
+                }
+            n_open += __shfl_sync(kFull, incl, 31);
+            if (++iters == 8192) {
+                flush();
+                iters = 0;
+            }
         }
-        if (++iters == 8192) {
-            flush();
-            iters = 0;
+        __syncwarp();
+        // the tile's open pairs, a lane each, from chunk 4 (the four chunk
+        // tests of a step together, the first stop by a bit scan)
+        for (int b0 = 0; b0 < n_open; b0 += 32) {
+            bool act = b0 + lane < n_open;
+            unsigned q = 0;
+            int m = 0, j = 4;
+            uint2 pr = make_uint2(0u, 0u);
+            const uint32_t *rx = A.sig, *ry = A.sig;
+            if (act) {
+                const uint32_t e = s_open[b0 + lane];
+                q = base + (e & 0xffffu);
+                m = (int)(e >> 16);
+                // self-checks (a failed one reports BLSH_EDEVICE and skips the
+                // access): the pair lies below P and names objects below N, a
+                // step's words lie inside the row, an estimate inside the table
+                if (q >= P) {
+                    blsh_dev_error(A.scratch, BLSH_EDEVICE, -1, 0ull);
+                    act = false;
+                } else {
+                    pr = __ldg(A.pairs + q);
+                    if ((unsigned long long)pr.x >= N || (unsigned long long)pr.y >= N) {
+                        blsh_dev_error(A.scratch, BLSH_EDEVICE, -1, 0ull);
+                        act = false;
+                    }
+                }
+                rx = A.sig + (size_t)pr.x * A.W;
+                ry = A.sig + (size_t)pr.y * A.W;
+            }
+            while (__any_sync(kFull, act)) {
+                if (act && j + 3 >= A.W) {
+                    blsh_dev_error(A.scratch, BLSH_EDEVICE, -1, 0ull);
+                    act = false;
+                }
+                if (act) {
+                    const uint4 a = ldg4(rx + j), b = ldg4(ry + j);   // k = 32: chunk j is word j
+                    const int c0 = m + 32 - __popc(a.x ^ b.x), c1 = c0 + 32 - __popc(a.y ^ b.y);
+                    const int c2 = c1 + 32 - __popc(a.z ^ b.z), c3 = c2 + 32 - __popc(a.w ^ b.w);
+                    auto m_at = [&](int i) { return i == 0 ? c0 : i == 1 ? c1 : i == 2 ? c2 : c3; };
+                    unsigned valid = 0, prune = 0, conc = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = j + i;
+                        if (jj < A.levels) {
+                            valid |= 1u << i;
+                            prune |= (unsigned)(m_at(i) < s_mm[jj]) << i;
+                            conc |= (unsigned)(m_at(i) >= s_clo[jj]) << i;
+                        }
+                    }
+                    const unsigned last = at(A.levels, j), cap = at(A.cap_levels, j);
+                    const unsigned s1 = (prune | (A.lite ? 0u : conc) | last | cap) & valid;
+                    if (s1) {
+                        const int i = __ffs(s1) - 1;
+                        const unsigned bi = 1u << i;
+                        const int st = (prune & bi) ? BLSH_PRUNED
+                                       : (!A.lite && (conc & bi)) ? BLSH_ACCEPT
+                                       : (last & bi) ? (A.lite ? BLSH_LITE_SURVIVOR : BLSH_ACCEPT_AT_MAX)
+                                                     : BLSH_NEEDS_HASHES;
+                        const int js = j + i, ms = m_at(i);
+                        A.status[q] = (uint8_t)st;
+                        if (A.n_used) A.n_used[q] = (uint16_t)((js + 1) * k);
+                        if (A.m_out) A.m_out[q] = (uint16_t)ms;
+                        if (st == BLSH_NEEDS_HASHES) {
+                            A.need[pr.x] = 1;
+                            A.need[pr.y] = 1;
+                        } else {
+                            if (js >= A.levels || ms >= A.est_stride) {
+                                blsh_dev_error(A.scratch, BLSH_EDEVICE, -1, 0ull);
+                            } else {
+                                if (A.est_out && st != BLSH_PRUNED) A.est_out[q] = __ldg(A.est_tab + js * A.est_stride + ms);
+                                atomicAdd(&s_hist[js], 1u);
+                            }
+                        }
+                        act = false;
+                    } else {
+                        m = c3;
+                        j += 4;
+                    }
+                }
+            }
         }
-    }
-    if (tid < P - (nq << 2)) {   // the last P mod 4 pairs
-        const unsigned q = (nq << 2) + tid;
-        one(q, __ldg(A.pairs + q));
     }
     flush();
     {
-        const int lane = threadIdx.x & 31;
         const unsigned c0 = __reduce_add_sync(kFull, hc0), c1 = __reduce_add_sync(kFull, hc1);
         const unsigned c2 = __reduce_add_sync(kFull, hc2), c3 = __reduce_add_sync(kFull, hc3);
         const unsigned mine = lane == 0 ? c0 : lane == 1 ? c1 : lane == 2 ? c2 : lane == 3 ? c3 : 0u;
-        if (mine) atomicAdd(&s_h[lane], mine);
+        if (mine && lane < A.levels) atomicAdd(&s_hist[lane], mine);
     }
     __syncthreads();
-    if (A.stop_hist && threadIdx.x < 4 && s_h[threadIdx.x])
-        atomicAdd(A.stop_hist + threadIdx.x, (unsigned long long)s_h[threadIdx.x]);
+    if (A.stop_hist)
+        for (int i = threadIdx.x; i < A.levels; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(A.stop_hist + i, (unsigned long long)s_hist[i]);
 }
 
 // plane[i] = words 0..3 of row i
@@ -949,22 +1091,23 @@ int dispatch(blsh_ctx *ctx, const VerifyArgs &A, const blsh_plan &plan, int kind
                                   blsh_aligned(A.n_used, 8) && blsh_aligned(A.m_out, 8) &&
                                   (!A.lite_levels || (blsh_aligned(A.lstatus, 4) && blsh_aligned(A.ln_used, 8)));
                 if (quad) {
-                    // one wave of resident CTAs; each lane loops over quads
-                    static int occ[2] = {0, 0};
-                    if (!occ[A.plane != nullptr]) {
-                        int o = 0;
-                        BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                           &o, A.plane ? verify_first4_kernel<true> : verify_first4_kernel<false>,
-                                           256, 0));
-                        occ[A.plane != nullptr] = o < 1 ? 1 : o;
-                    }
+                    // both passes in one kernel (verify_tile_kernel): one wave
+                    // of resident CTAs, warps taking tiles from a counter
                     if (A.P == 0) return BLSH_OK;
-                    const long long blocks = (A.P / 4 + 255) / 256 > 0 ? (A.P / 4 + 255) / 256 : 1;
-                    const long long cap = (long long)ctx->sm_count * occ[A.plane != nullptr];
+                    const size_t smem = (size_t)A.levels * 3 * sizeof(int32_t) + 8 * kTilePairs * sizeof(uint32_t);
+                    int occ = 0;
+                    BLSH_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                       &occ, A.plane ? verify_tile_kernel<true> : verify_tile_kernel<false>, 256, smem));
+                    if (occ < 1) occ = 1;
+                    const long long tiles = (A.P + kTilePairs - 1) / kTilePairs;
+                    const long long blocks = (tiles + 7) / 8, cap = (long long)ctx->sm_count * occ;
                     const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+                    BLSH_CUDA(ctx, cudaMemsetAsync(&A.scratch->work, 0, sizeof(unsigned long long), s));   // tile counter
                     blsh_time_start(ctx, s);
-                    if (A.plane) verify_first4_kernel<true><<<grid, 256, 0, s>>>(A);
-                    else verify_first4_kernel<false><<<grid, 256, 0, s>>>(A);
+                    if (A.plane) verify_tile_kernel<true><<<grid, 256, smem, s>>>(A);
+                    else verify_tile_kernel<false><<<grid, 256, smem, s>>>(A);
+                    BLSH_LAUNCHED(ctx, "verify_tile_kernel");
+                    return BLSH_OK;
                 } else {
                     const long long blocks = (A.P + 255) / 256, cap = (long long)ctx->sm_count * 8;
                     const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);

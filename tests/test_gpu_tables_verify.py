@@ -281,6 +281,14 @@ def test_lite_form_every_cosine_plan(B, ctx):
     B.blsh_verify_lite(ctx, tab, pt, stt, ip, ix, val, st, sim)
     assert B.blsh_status(ctx) == 0
     assert np.array_equal(st.cpu().numpy(), want.status)
+    # each launch form explicitly: the plain one runs the two-pass kernel,
+    # where a survivor of the pruning loop is decided, not open
+    for plan in (B.blsh_plan(B.PLAN_PLAIN, 1, 256, 32, 0), B.blsh_plan(B.PLAN_PERSISTENT, 1, 256, 64, 0)):
+        B.blsh_set_plan(ctx, tab, plan)
+        st.fill_(77)
+        B.blsh_verify_lite(ctx, tab, pt, stt, ip, ix, val, st, sim)
+        assert B.blsh_status(ctx) == 0
+        assert np.array_equal(st.cpu().numpy(), want.status)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
