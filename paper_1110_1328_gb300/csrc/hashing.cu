@@ -422,54 +422,39 @@ __global__ void __launch_bounds__(256) srp_sparse4_kernel(const int64_t *__restr
                         tot2[u] = f2_add(tot2[u], acc2[u]);
                         acc2[u] = 0ull;
                     }
-                    continue;
-                }
-                for (int u0 = 0; u0 < cnt; u0 += NB) {
-                    float4 r[NB][V];
-                    float vb[NB];
+                } else {   // float R: 16-byte loads of four columns
+                    for (int u0 = 0; u0 < cnt; u0 += NB) {
+                        float4 r[NB][V];
+                        float vb[NB];
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
-                        vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
-                        if constexpr (Q16) {
-                            // four codes per load; a code q stands for (q - 2^15) 2^-12, and
-                            // the float with bit pattern 0x4b000000 | q is 2^23 + q, so
-                            // subtracting 2^23 + 2^15 gives q - 2^15 exactly (sums scaled by 2^12)
-                            const uint2 *Rrow = reinterpret_cast<const uint2 *>(R + (size_t)ix * bits + col0) + t;
-#pragma unroll
-                            for (int g = 0; g < V; ++g) {
-                                const uint2 q = __ldg(Rrow + g * T);
-                                r[b][g] = make_float4(__int_as_float(0x4b000000u | (q.x & 0xffffu)) - 8421376.0f,
-                                                      __int_as_float(0x4b000000u | (q.x >> 16)) - 8421376.0f,
-                                                      __int_as_float(0x4b000000u | (q.y & 0xffffu)) - 8421376.0f,
-                                                      __int_as_float(0x4b000000u | (q.y >> 16)) - 8421376.0f);
-                            }
-                        } else {
+                        for (int b = 0; b < NB; ++b) {
+                            const uint32_t ix = __shfl_sync(kFull, my_ix, (u0 + b) & 31);
+                            vb[b] = __shfl_sync(kFull, my_v, (u0 + b) & 31);   // 0 past the row's end
                             const float4 *Rrow = reinterpret_cast<const float4 *>(R + (size_t)ix * bits + col0) + t;
 #pragma unroll
                             for (int g = 0; g < V; ++g) r[b][g] = __ldg(Rrow + g * T);
                         }
-                    }
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const float v = vb[b], av = fabsf(v);
+                        for (int b = 0; b < NB; ++b) {
+                            const float v = vb[b], av = fabsf(v);
 #pragma unroll
-                        for (int g = 0; g < V; ++g) {
-                            acc[4 * g + 0] = __fmaf_rn(v, r[b][g].x, acc[4 * g + 0]);
-                            acc[4 * g + 1] = __fmaf_rn(v, r[b][g].y, acc[4 * g + 1]);
-                            acc[4 * g + 2] = __fmaf_rn(v, r[b][g].z, acc[4 * g + 2]);
-                            acc[4 * g + 3] = __fmaf_rn(v, r[b][g].w, acc[4 * g + 3]);
-                            mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[b][g].x), mag[4 * g + 0]);
-                            mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[b][g].y), mag[4 * g + 1]);
-                            mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[b][g].z), mag[4 * g + 2]);
-                            mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[b][g].w), mag[4 * g + 3]);
+                            for (int g = 0; g < V; ++g) {
+                                acc[4 * g + 0] = __fmaf_rn(v, r[b][g].x, acc[4 * g + 0]);
+                                acc[4 * g + 1] = __fmaf_rn(v, r[b][g].y, acc[4 * g + 1]);
+                                acc[4 * g + 2] = __fmaf_rn(v, r[b][g].z, acc[4 * g + 2]);
+                                acc[4 * g + 3] = __fmaf_rn(v, r[b][g].w, acc[4 * g + 3]);
+                                mag[4 * g + 0] = __fmaf_rn(av, fabsf(r[b][g].x), mag[4 * g + 0]);
+                                mag[4 * g + 1] = __fmaf_rn(av, fabsf(r[b][g].y), mag[4 * g + 1]);
+                                mag[4 * g + 2] = __fmaf_rn(av, fabsf(r[b][g].z), mag[4 * g + 2]);
+                                mag[4 * g + 3] = __fmaf_rn(av, fabsf(r[b][g].w), mag[4 * g + 3]);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int u = 0; u < 4 * V; ++u) {
-                    tot[u] = __fadd_rn(tot[u], acc[u]);
-                    acc[u] = 0.0f;
+                    for (int u = 0; u < 4 * V; ++u) {
+                        tot[u] = __fadd_rn(tot[u], acc[u]);
+                        acc[u] = 0.0f;
+                    }
                 }
             }
             if constexpr (sizeof(RT) == 2) {
