@@ -15,7 +15,11 @@
 //
 // Two launch forms:
 //   PLAIN      -- one group per pair, grid covers all pairs; a warp lives as
-//                 long as its slowest pair.
+//                 long as its slowest pair.  For cosine with k = 32 it runs
+//                 in two passes: every pair's first four chunks, then the
+//                 pairs still open (verify_tile_kernel does both, tile by
+//                 tile; verify_first_kernel then verify_kernel's OPEN form
+//                 where the outputs take no packed stores).
 //   PERSISTENT -- one wave of CTAs; each warp takes `grab` pairs at a time
 //                 from an atomic counter and hands a new pair to a group as
 //                 soon as its pair stops (pairs stop after very different
