@@ -16,7 +16,9 @@
 //      or 32-bit lanes (by `rows`), compared four / two / one band at a time
 //      with a SWAR zero-lane test on the XOR of two rows; Jaccard 64-bit band
 //      hashes, confirmed by comparing the hashes themselves, so a hash
-//      collision never merges buckets.
+//      collision never merges buckets.  The count pass records which pairs
+//      it keeps (one bit per tested pair, in the workspace's keep record),
+//      and the write pass writes those pairs without testing them again.
 #include "common.cuh"
 #include "radix.cuh"
 #include "scan.cuh"
